@@ -1,0 +1,63 @@
+"""Fourier local Laplacian filtering in float64 (oracle; test infrastructure only).
+
+Sec. III-A of the paper.  The output local Laplacian pyramid is defined by
+Eq. (13): at level l and pixel p, the Laplacian coefficient of the image
+remapped about g = G_l[I]_p.  Substituting the sine series of the remap
+detail (Eq. (11)) makes every term separable into a per-pixel coefficient
+and a pyramid of the input only, which is Eq. (14).  In this package's
+parametrisation (r_g(i) = i + f(i - g), f ~= sum_k a_k sin(omega_k d)):
+
+    L_l[O]_p = L_l[I]_p
+             + sum_k a_k [ cos(omega_k g) L_l[sin(omega_k I)]_p
+                         - sin(omega_k g) L_l[cos(omega_k I)]_p ],   l < top
+    L_top[O] = G_top[I],
+
+where L_l[sin(omega_k I)] = S~_{l,k} - up(S~_{l+1,k}) with
+S~_{l,k} = G_l[sin(omega_k I)] and C~_{l,k} = G_l[cos(omega_k I)] (the
+Gaussian Fourier pyramids of Fig. 1), and the output is the collapse of
+Eq. (4).  At l = 0 the paper drops the S~_0 / C~_0 terms because
+r(I, I_p) = I makes them cancel; this oracle keeps them and evaluates the
+general form at every level (the cancellation is checked by a test).
+"""
+
+import numpy as np
+
+from .pyramid import gaussian_pyramid, laplacian_from_gaussian, collapse
+from .remap import omegas
+
+
+def fourier_llf_levels(img, levels, a, T):
+    """Return (output Laplacian pyramid, level-0 Fourier term) for one plane.
+
+    ``img``: 2-D float array.  ``a``: Fourier sine coefficients a_1..a_K.
+    The second value is the part of L_0[O] - L_0[I] that comes from the
+    level-0 pyramids S~_0, C~_0 (zero up to rounding by r(I, I_p) = I).
+    """
+    img = np.asarray(img, dtype=np.float64)
+    g = gaussian_pyramid(img, levels)
+    lap_i = laplacian_from_gaussian(g)
+    out = [lap_i[l].copy() for l in range(levels - 1)]
+    level0_term = np.zeros_like(img)
+    for ak, om in zip(a, omegas(T, len(a))):
+        c_pyr = gaussian_pyramid(np.cos(om * img), levels)   # C~_{l,k}
+        s_pyr = gaussian_pyramid(np.sin(om * img), levels)   # S~_{l,k}
+        lap_c = laplacian_from_gaussian(c_pyr)
+        lap_s = laplacian_from_gaussian(s_pyr)
+        for l in range(levels - 1):
+            cg, sg = np.cos(om * g[l]), np.sin(om * g[l])     # per-pixel coefficients
+            out[l] += ak * (cg * lap_s[l] - sg * lap_c[l])
+        level0_term += ak * (np.cos(om * img) * s_pyr[0] - np.sin(om * img) * c_pyr[0])
+    out.append(g[-1])                                         # L_top[O] = G_top[I]
+    return out, level0_term
+
+
+def fourier_llf(img, levels, a, T):
+    """Fourier LLF of a plane (H, W) or of planar channels (C, H, W).
+
+    Each channel is filtered independently.  float64 in, float64 out.
+    """
+    img = np.asarray(img, dtype=np.float64)
+    if img.ndim == 3:
+        return np.stack([fourier_llf(ch, levels, a, T) for ch in img])
+    lap_o, _ = fourier_llf_levels(img, levels, a, T)
+    return collapse(lap_o)
