@@ -1,0 +1,163 @@
+/*
+ * fllf.h -- C ABI of the GB300 Fourier local Laplacian filter (libfllf.so).
+ *
+ * The filter is Fourier LLF (Sumiya, Otsuka, Maeda, Fukushima, "Gaussian
+ * Fourier Pyramid for Local Laplacian Filter", IEEE SPL, arXiv 2206.04681).
+ * Local Laplacian filtering (Sec. II-C) remaps the input about every
+ * pyramid coefficient's own Gaussian value g = G_l[I]_p and keeps the
+ * remapped Laplacian coefficient; Fourier LLF expands the remap detail in a
+ * sine series (Eqs. (9)-(11)) so that only 2K+1 pyramids are needed
+ * (Eq. (14), Fig. 1).  With the remap
+ *
+ *     r_g(i) = i + f(i - g),  f(d) = (m - 1) d exp(-d^2 / (2 sigma_r^2)),
+ *     f(d) ~= sum_{k=1..K} a_k sin(omega_k d),  omega_k = 2 pi k / T,
+ *
+ * every output Laplacian level below the top is
+ *
+ *     L_l[O] = L_l[I] + sum_k a_k [cos(omega_k G_l[I]) L_l[sin(omega_k I)]
+ *                                - sin(omega_k G_l[I]) L_l[cos(omega_k I)]],
+ *
+ * the top level is G_top[I], and O is the collapse of Eq. (4).  Pyramids use
+ * the 5-tap binomial kernel [1 4 6 4 1]/16 with reflect-101 borders at every
+ * level; coarse sizes are ceil(n/2).
+ *
+ * Conventions for every entry point:
+ *   - Every call returns an fllf_status; no C++ exception crosses the ABI.
+ *     On an error, fllf_last_error() returns a thread-local description.
+ *   - Images are planar float32, C x H x W, contiguous (row pitch W, plane
+ *     pitch H*W).  Values are expected in [0, 1] (the period T is chosen for
+ *     that range); values outside it are filtered as-is, without clamping.
+ *   - Device pointers are CUDA device addresses on the plan's device; host
+ *     pointers are ordinary (preferably pinned) host memory.
+ *   - Stream arguments are cudaStream_t passed as void* (NULL = legacy
+ *     default stream).  Device-pointer calls only enqueue work on that
+ *     stream; results are valid once the stream reaches that point.
+ *   - Output buffers are written only when the call returns FLLF_OK.
+ */
+#ifndef FLLF_H
+#define FLLF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  FLLF_OK = 0,
+  FLLF_EINVAL = 1,   /* invalid argument or parameter set */
+  FLLF_ENOMEM = 2,   /* device or host allocation failed; nothing leaked */
+  FLLF_ECUDA = 3,    /* a CUDA call failed; see fllf_last_error() */
+  FLLF_EAGAIN = 4,   /* asynchronous work still pending */
+  FLLF_ETIMEOUT = 5, /* a bounded wait ran out */
+  FLLF_EBUSY = 6     /* no slot or memory free and the queue is full */
+} fllf_status;
+
+/* Storage type of the 2K Gaussian Fourier pyramids (Sec. III-A, Fig. 1).
+ * Arithmetic is float32 in every mode; the guide pyramid G_l[I], the
+ * residual collapse and the output are always float32. */
+typedef enum { FLLF_FP32 = 0, FLLF_FP16 = 1, FLLF_BF16 = 2 } fllf_precision;
+
+/* How a_k is obtained from (m, sigma_r, T, K). */
+typedef enum {
+  FLLF_COEFF_QUADRATURE = 0, /* (2/T) * integral over one period of f(x) sin(omega_k x) */
+  FLLF_COEFF_CLOSED_FORM = 1 /* Eqs. (9)-(11): (m-1) 2 sigma_r^2 alpha_k omega_k */
+} fllf_coeff_mode;
+
+typedef struct {
+  int H, W;          /* image size, >= 1 each */
+  int C;             /* planes filtered independently (1 = gray, 3 = planar RGB), 1..64 */
+  int levels;        /* pyramid levels including level 0; 1..16 (top = levels-1) */
+  int K;             /* Fourier orders, 1..64 (2K+1 pyramids) */
+  double m;          /* remap gain: 1 = identity, > 1 enhances, < 1 smooths */
+  double sigma_r;    /* remap range scale, > 0 */
+  double T;          /* Fourier period, > 0 (2 covers differences in [-1, 1]) */
+  int precision;     /* fllf_precision */
+  int coeff_mode;    /* fllf_coeff_mode */
+} fllf_params;
+
+typedef struct fllf_plan fllf_plan;
+
+/* Human-readable name of a status code (static string). */
+const char *fllf_status_str(fllf_status s);
+
+/* Detail text of the last error raised on the calling thread ("" if none). */
+const char *fllf_last_error(void);
+
+/* Checks a parameter set: FLLF_OK or FLLF_EINVAL with the reason. */
+fllf_status fllf_params_validate(const fllf_params *p);
+
+/* Fourier sine coefficients a_1..a_K of the remap detail f for this
+ * parameter set, in float64 (Eqs. (9)-(11); quadrature or closed form per
+ * coeff_mode).  a_out: host array of p->K doubles, written on FLLF_OK. */
+fllf_status fllf_coeffs(const fllf_params *p, double *a_out);
+
+/* Bytes of device scratch a plan for this parameter set allocates: the
+ * guide pyramid G_l (l >= 1), the Fourier pyramids Z_l (K complex planes
+ * per level l >= 1, in the storage precision) and the residual pyramid
+ * E_l = O_l - G_l (1 <= l <= levels-2), for all C planes.  0 if invalid. */
+size_t fllf_plan_scratch_bytes(const fllf_params *p);
+
+/* Creates a plan on CUDA device `device`: validates p, computes a_k on the
+ * host in float64, uploads them as float32, and allocates the scratch.
+ * On failure nothing stays allocated and *out is NULL.  The caller owns the
+ * plan and frees it with fllf_plan_destroy. */
+fllf_status fllf_plan_create(const fllf_params *p, int device, fllf_plan **out);
+
+/* Frees the plan and its scratch; NULL is accepted.  The caller must make
+ * sure no work of the plan is still running on any stream. */
+fllf_status fllf_plan_destroy(fllf_plan *plan);
+
+/* Copies the plan's parameters / float64 coefficients (K doubles). */
+fllf_status fllf_plan_params(const fllf_plan *plan, fllf_params *out);
+fllf_status fllf_plan_coeffs(const fllf_plan *plan, double *a_out);
+
+/* Filters one C x H x W image: d_in -> d_out, both device pointers on the
+ * plan's device, non-overlapping (d_in == d_out is FLLF_EINVAL).  Enqueues
+ * the kernels on `stream` and returns; the plan's scratch is in use until
+ * the stream passes this work, so one plan must not run concurrently on two
+ * streams. */
+fllf_status fllf_run(fllf_plan *plan, const float *d_in, float *d_out, void *stream);
+
+/* End-to-end variant for host buffers: copies h_in to a plan-owned device
+ * buffer, filters, copies the result to h_out and waits for the stream.
+ * Allocates the two device I/O buffers on first use (kept by the plan). */
+fllf_status fllf_run_host(fllf_plan *plan, const float *h_in, float *h_out, void *stream);
+
+/* Asynchronous form of fllf_run: enqueues the work and records a
+ * completion event; *ticket identifies it for fllf_poll. */
+fllf_status fllf_submit(fllf_plan *plan, const float *d_in, float *d_out, void *stream,
+                        uint64_t *ticket);
+
+/* Waits up to timeout_us microseconds (0 = just test, < 0 = no limit) for
+ * a submitted ticket.  FLLF_OK: done (ticket consumed); FLLF_EAGAIN: still
+ * running after a zero timeout; FLLF_ETIMEOUT: still running after a
+ * positive timeout; FLLF_EINVAL: unknown or already consumed ticket;
+ * FLLF_ECUDA: the work failed on the device. */
+fllf_status fllf_poll(uint64_t ticket, int timeout_us);
+
+/* ---- Diagnostics: per-stage device timing -------------------------------
+ * Stage kinds of the path (Fig. 1 read as a pipeline): */
+enum {
+  FLLF_STAGE_UP0 = 0,   /* level 0 -> 1: trig of I + REDUCE of I and the 2K Fourier images */
+  FLLF_STAGE_UP = 1,    /* level l -> l+1 REDUCE of G_l and Z_l (Eq. (1)) */
+  FLLF_STAGE_DOWN = 2,  /* level l >= 1: Eq. (14) product-sum fused with the collapse */
+  FLLF_STAGE_DOWN0 = 3, /* level 0: Eq. (14) l = 0 case + final collapse, writes O */
+  FLLF_NSTAGE = 4
+};
+
+/* When enabled, every run of the plan records CUDA events around each
+ * kernel launch on the run's stream.  Adds no synchronisation. */
+fllf_status fllf_plan_enable_timing(fllf_plan *plan, int enable);
+
+/* Waits for the recorded events, then writes per stage kind the summed
+ * kernel time in milliseconds (ms[FLLF_NSTAGE]) and the number of launches
+ * (launches[FLLF_NSTAGE]) since the last call, and clears the record. */
+fllf_status fllf_plan_stage_times(fllf_plan *plan, double *ms, int *launches);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FLLF_H */

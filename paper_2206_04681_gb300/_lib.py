@@ -1,0 +1,169 @@
+"""ctypes binding of libfllf.so (include/fllf.h).
+
+Argument marshalling only: every step of the filter runs in the library's
+CUDA kernels.  The functions keep the C names; a non-OK status raises
+``FllfError`` carrying the status and ``fllf_last_error()``.  If the shared
+library is missing, loading fails loudly (there is no fallback).
+"""
+
+import ctypes
+import os
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(PKG, "libfllf.so")
+
+FLLF_OK, FLLF_EINVAL, FLLF_ENOMEM, FLLF_ECUDA, FLLF_EAGAIN, FLLF_ETIMEOUT, FLLF_EBUSY = range(7)
+FLLF_FP32, FLLF_FP16, FLLF_BF16 = 0, 1, 2
+FLLF_COEFF_QUADRATURE, FLLF_COEFF_CLOSED_FORM = 0, 1
+PRECISIONS = {"fp32": FLLF_FP32, "fp16": FLLF_FP16, "bf16": FLLF_BF16}
+
+
+class FllfError(RuntimeError):
+    def __init__(self, status, detail):
+        super().__init__(f"{status_name(status)}: {detail}")
+        self.status = status
+        self.detail = detail
+
+
+class fllf_params(ctypes.Structure):
+    _fields_ = [("H", ctypes.c_int), ("W", ctypes.c_int), ("C", ctypes.c_int),
+                ("levels", ctypes.c_int), ("K", ctypes.c_int),
+                ("m", ctypes.c_double), ("sigma_r", ctypes.c_double), ("T", ctypes.c_double),
+                ("precision", ctypes.c_int), ("coeff_mode", ctypes.c_int)]
+
+
+_P = ctypes.c_void_p
+_SIGS = {
+    "fllf_status_str": (ctypes.c_char_p, [ctypes.c_int]),
+    "fllf_last_error": (ctypes.c_char_p, []),
+    "fllf_params_validate": (ctypes.c_int, [ctypes.POINTER(fllf_params)]),
+    "fllf_coeffs": (ctypes.c_int, [ctypes.POINTER(fllf_params), ctypes.POINTER(ctypes.c_double)]),
+    "fllf_plan_scratch_bytes": (ctypes.c_size_t, [ctypes.POINTER(fllf_params)]),
+    "fllf_plan_create": (ctypes.c_int, [ctypes.POINTER(fllf_params), ctypes.c_int,
+                                        ctypes.POINTER(_P)]),
+    "fllf_plan_destroy": (ctypes.c_int, [_P]),
+    "fllf_plan_params": (ctypes.c_int, [_P, ctypes.POINTER(fllf_params)]),
+    "fllf_plan_coeffs": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_double)]),
+    "fllf_run": (ctypes.c_int, [_P, _P, _P, _P]),
+    "fllf_run_host": (ctypes.c_int, [_P, _P, _P, _P]),
+    "fllf_submit": (ctypes.c_int, [_P, _P, _P, _P, ctypes.POINTER(ctypes.c_uint64)]),
+    "fllf_poll": (ctypes.c_int, [ctypes.c_uint64, ctypes.c_int]),
+    "fllf_plan_enable_timing": (ctypes.c_int, [_P, ctypes.c_int]),
+    "fllf_plan_stage_times": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_double),
+                                             ctypes.POINTER(ctypes.c_int)]),
+}
+
+STAGES = ("up0", "up", "down", "down0")
+
+_lib = None
+
+
+def lib():
+    """The loaded libfllf.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(
+                f"{LIB_PATH} is missing: build it with paper_2206_04681_gb300.build.build_library() "
+                "(or __graft_entry__.build()); there is no non-CUDA fallback")
+        handle = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            fn = getattr(handle, name, None)
+            if fn is not None:
+                fn.restype = res
+                fn.argtypes = args
+        _lib = handle
+    return _lib
+
+
+def status_name(s):
+    try:
+        return lib().fllf_status_str(s).decode()
+    except Exception:  # library not loadable: still name the code
+        return f"status {s}"
+
+
+def _check(status):
+    if status != FLLF_OK:
+        raise FllfError(status, lib().fllf_last_error().decode())
+    return status
+
+
+def make_params(H, W, C=1, levels=5, K=8, m=3.0, sigma_r=0.2, T=2.0, precision=FLLF_FP32,
+                coeff_mode=FLLF_COEFF_QUADRATURE):
+    if isinstance(precision, str):
+        precision = PRECISIONS[precision]
+    return fllf_params(int(H), int(W), int(C), int(levels), int(K), float(m), float(sigma_r),
+                       float(T), int(precision), int(coeff_mode))
+
+
+def fllf_params_validate(p):
+    return lib().fllf_params_validate(ctypes.byref(p))
+
+
+def fllf_coeffs(p):
+    out = (ctypes.c_double * p.K)()
+    _check(lib().fllf_coeffs(ctypes.byref(p), out))
+    return list(out)
+
+
+def fllf_plan_scratch_bytes(p):
+    return int(lib().fllf_plan_scratch_bytes(ctypes.byref(p)))
+
+
+def fllf_plan_create(p, device=0):
+    h = _P()
+    _check(lib().fllf_plan_create(ctypes.byref(p), int(device), ctypes.byref(h)))
+    return h
+
+
+def fllf_plan_destroy(plan):
+    _check(lib().fllf_plan_destroy(plan))
+
+
+def fllf_plan_params(plan):
+    out = fllf_params()
+    _check(lib().fllf_plan_params(plan, ctypes.byref(out)))
+    return out
+
+
+def fllf_plan_coeffs(plan):
+    p = fllf_plan_params(plan)
+    out = (ctypes.c_double * p.K)()
+    _check(lib().fllf_plan_coeffs(plan, out))
+    return list(out)
+
+
+def fllf_run(plan, d_in, d_out, stream=0):
+    _check(lib().fllf_run(plan, _P(d_in), _P(d_out), _P(stream)))
+
+
+def fllf_run_host(plan, h_in, h_out, stream=0):
+    _check(lib().fllf_run_host(plan, _P(h_in), _P(h_out), _P(stream)))
+
+
+def fllf_submit(plan, d_in, d_out, stream=0):
+    t = ctypes.c_uint64()
+    _check(lib().fllf_submit(plan, _P(d_in), _P(d_out), _P(stream), ctypes.byref(t)))
+    return t.value
+
+
+def fllf_plan_enable_timing(plan, enable=True):
+    _check(lib().fllf_plan_enable_timing(plan, int(bool(enable))))
+
+
+def fllf_plan_stage_times(plan):
+    """{stage name: (total ms, launches)} since the previous call."""
+    ms = (ctypes.c_double * len(STAGES))()
+    n = (ctypes.c_int * len(STAGES))()
+    _check(lib().fllf_plan_stage_times(plan, ms, n))
+    return {name: (ms[i], n[i]) for i, name in enumerate(STAGES)}
+
+
+def fllf_poll(ticket, timeout_us=-1):
+    """Returns the raw status (FLLF_OK, FLLF_EAGAIN, FLLF_ETIMEOUT) or raises."""
+    s = lib().fllf_poll(ctypes.c_uint64(ticket), int(timeout_us))
+    if s in (FLLF_OK, FLLF_EAGAIN, FLLF_ETIMEOUT):
+        return s
+    _check(s)
+    return s

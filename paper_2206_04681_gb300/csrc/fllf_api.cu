@@ -1,0 +1,547 @@
+// fllf_api.cu -- the C ABI of include/fllf.h: parameters, coefficients, plans,
+// run / submit / poll.  Host code; the kernels live in fllf_kernels_*.cu.
+#include <cuda_runtime.h>
+
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <string>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "fllf.h"
+#include "fllf_internal.h"
+#include "fllf_launch.h"
+
+namespace {
+
+thread_local std::string g_last_error;
+
+fllf_status fail(fllf_status s, const std::string& why) {
+  g_last_error = why;
+  return s;
+}
+
+fllf_status cuda_fail(cudaError_t e, const char* what) {
+  return fail(FLLF_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+// Keeps the caller's current device across a call that switches devices.
+struct DeviceGuard {
+  int prev = -1;
+  bool ok = false;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    ok = cudaSetDevice(dev) == cudaSuccess;
+  }
+  ~DeviceGuard() {
+    if (prev >= 0) cudaSetDevice(prev);
+  }
+};
+
+}  // namespace
+
+namespace fllf {
+
+void set_last_error(const std::string& s) { g_last_error = s; }
+
+// ---- Fourier coefficients (Eqs. (9)-(11)) ------------------------------------------
+// Gauss-Legendre nodes on [-1, 1]: roots of P_n by Newton's method from the
+// asymptotic guesses cos(pi (i - 1/4) / (n + 1/2)); P_n and P_n' from the
+// three-term recurrence (j+1) P_{j+1} = (2j+1) x P_j - j P_{j-1}.
+static void gauss_legendre(int n, std::vector<double>& x, std::vector<double>& w) {
+  x.assign(n, 0.0);
+  w.assign(n, 0.0);
+  const double pi = 3.14159265358979323846;
+  for (int i = 0; i < (n + 1) / 2; ++i) {
+    double z = std::cos(pi * (i + 0.75) / (n + 0.5));
+    double dp = 0.0;
+    for (int it = 0; it < 100; ++it) {
+      double p0 = 1.0, p1 = z;
+      for (int j = 1; j < n; ++j) {
+        const double p2 = ((2.0 * j + 1.0) * z * p1 - j * p0) / (j + 1.0);
+        p0 = p1;
+        p1 = p2;
+      }
+      dp = n * (z * p1 - p0) / (z * z - 1.0);
+      const double dz = p1 / dp;
+      z -= dz;
+      if (std::fabs(dz) < 1e-16) break;
+    }
+    x[i] = -z;
+    x[n - 1 - i] = z;
+    w[i] = w[n - 1 - i] = 2.0 / ((1.0 - z * z) * dp * dp);
+  }
+}
+
+void compute_coeffs(const fllf_params& p, double* a) {
+  const double pi = 3.14159265358979323846;
+  const int K = p.K;
+  const double s = p.sigma_r, T = p.T, g = p.m - 1.0;
+  if (p.coeff_mode == FLLF_COEFF_CLOSED_FORM) {
+    for (int k = 1; k <= K; ++k) {
+      const double om = 2.0 * pi * k / T;
+      const double alpha = s * std::sqrt(2.0 * pi) / T * std::exp(-0.5 * (om * s) * (om * s));
+      a[k - 1] = g * 2.0 * s * s * alpha * om;
+    }
+    return;
+  }
+  // (2/T) * integral_{-T/2}^{T/2} f(x) sin(w_k x) dx; the integrand is even,
+  // so integrate over [0, T/2] and double.  512 panels x 16 nodes.
+  const int panels = 512, nodes = 16;
+  std::vector<double> gx, gw;
+  gauss_legendre(nodes, gx, gw);
+  for (int k = 0; k < K; ++k) a[k] = 0.0;
+  const double h = (T / 2.0) / panels;
+  for (int q = 0; q < panels; ++q) {
+    const double lo = q * h, mid = lo + 0.5 * h;
+    for (int i = 0; i < nodes; ++i) {
+      const double x = mid + 0.5 * h * gx[i];
+      const double wq = 0.5 * h * gw[i];
+      const double fx = g * x * std::exp(-x * x / (2.0 * s * s));
+      for (int k = 1; k <= K; ++k) a[k - 1] += wq * fx * std::sin(2.0 * pi * k / T * x);
+    }
+  }
+  for (int k = 0; k < K; ++k) a[k] *= 2.0 * (2.0 / T);
+}
+
+fllf_status validate(const fllf_params* p) {
+  if (!p) return fail(FLLF_EINVAL, "params is NULL");
+  if (p->H < 1 || p->W < 1 || p->H > 65536 || p->W > 65536)
+    return fail(FLLF_EINVAL, "H and W must be in [1, 65536]");
+  if (p->C < 1 || p->C > 64) return fail(FLLF_EINVAL, "C must be in [1, 64]");
+  if (p->levels < 1 || p->levels > 16) return fail(FLLF_EINVAL, "levels must be in [1, 16]");
+  if (p->K < 1 || p->K > 64) return fail(FLLF_EINVAL, "K must be in [1, 64]");
+  if (!std::isfinite(p->m)) return fail(FLLF_EINVAL, "m must be finite");
+  if (!(p->sigma_r > 0.0) || !std::isfinite(p->sigma_r))
+    return fail(FLLF_EINVAL, "sigma_r must be finite and > 0");
+  if (!(p->T > 0.0) || !std::isfinite(p->T)) return fail(FLLF_EINVAL, "T must be finite and > 0");
+  if (p->precision < FLLF_FP32 || p->precision > FLLF_BF16)
+    return fail(FLLF_EINVAL, "precision must be FLLF_FP32, FLLF_FP16 or FLLF_BF16");
+  if (p->coeff_mode != FLLF_COEFF_QUADRATURE && p->coeff_mode != FLLF_COEFF_CLOSED_FORM)
+    return fail(FLLF_EINVAL, "coeff_mode must be quadrature or closed form");
+  return FLLF_OK;
+}
+
+// Scratch layout: per level l = 1..levels-1, G_l, Z_l and (l <= levels-2) E_l
+// for all planes, each buffer 256-byte aligned; row pitch rounded up to 16
+// elements so that rows start on 64-byte (G, E) / 64-128-byte (Z) boundaries.
+static size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+size_t layout(const fllf_params& p, std::vector<Level>* out) {
+  const size_t zsize = p.precision == FLLF_FP32 ? 8 : 4;
+  size_t off = 0;
+  int h = p.H, w = p.W;
+  if (out) out->assign(p.levels, Level{});
+  for (int l = 0; l < p.levels; ++l) {
+    Level lv{};
+    lv.h = h;
+    lv.w = w;
+    if (l > 0) {
+      lv.pitch = (w + 15) & ~15;
+      lv.gplane = (long long)h * lv.pitch;
+      lv.zk = (long long)h * lv.pitch;
+      lv.zplane = lv.zk * p.K;
+      const size_t gbytes = align256(sizeof(float) * (size_t)lv.gplane * p.C);
+      const size_t zbytes = align256(zsize * (size_t)lv.zplane * p.C);
+      lv.G = reinterpret_cast<float*>(off);
+      off += gbytes;
+      lv.Z = reinterpret_cast<void*>(off);
+      off += zbytes;
+      if (l <= p.levels - 2) {
+        lv.E = reinterpret_cast<float*>(off);
+        off += gbytes;
+      }
+    } else {
+      lv.pitch = w;
+      lv.gplane = (long long)h * w;
+    }
+    if (out) (*out)[l] = lv;
+    h = (h + 1) / 2;
+    w = (w + 1) / 2;
+  }
+  return off;
+}
+
+// Every level buffer must lie inside the scratch allocation.
+bool check_layout(const fllf_params& p, const std::vector<Level>& lv, const unsigned char* base,
+                  size_t bytes) {
+  const size_t zsize = p.precision == FLLF_FP32 ? 8 : 4;
+  auto inside = [&](const void* ptr, size_t n) {
+    const unsigned char* q = static_cast<const unsigned char*>(ptr);
+    return q != nullptr && q >= base && q + n <= base + bytes;
+  };
+  for (int l = 1; l < p.levels; ++l) {
+    const size_t g = sizeof(float) * (size_t)lv[l].gplane * p.C;
+    const size_t z = zsize * (size_t)lv[l].zplane * p.C;
+    if (lv[l].pitch < lv[l].w) return false;
+    if (!inside(lv[l].G, g) || !inside(lv[l].Z, z)) return false;
+    if (l <= p.levels - 2 && !inside(lv[l].E, g)) return false;
+    if (l == p.levels - 1 && lv[l].E != nullptr) return false;
+  }
+  return true;
+}
+
+}  // namespace fllf
+
+using namespace fllf;
+
+struct fllf_plan {
+  fllf_params p{};
+  int device = 0;
+  std::vector<double> a64;
+  float* d_a = nullptr;
+  unsigned char* scratch = nullptr;
+  size_t scratch_bytes = 0;
+  std::vector<Level> lv;  // device addresses
+  float* d_io_in = nullptr;
+  float* d_io_out = nullptr;
+  StageTimer* timer = nullptr;  // per-stage timing diagnostics (optional)
+};
+
+namespace {
+
+std::mutex g_ticket_mu;
+std::unordered_map<uint64_t, std::pair<cudaEvent_t, int>> g_tickets;
+uint64_t g_next_ticket = 1;
+
+void free_plan(fllf_plan* pl) {
+  if (!pl) return;
+  if (pl->d_a) cudaFree(pl->d_a);
+  if (pl->scratch) cudaFree(pl->scratch);
+  if (pl->d_io_in) cudaFree(pl->d_io_in);
+  if (pl->d_io_out) cudaFree(pl->d_io_out);
+  delete pl->timer;
+  delete pl;
+}
+
+cudaError_t launch_stage_up0(int prec, const Up0Args& a, int planes, cudaStream_t s) {
+  switch (prec) {
+    case FLLF_FP16: return launch_up0_f16(a, planes, s);
+    case FLLF_BF16: return launch_up0_bf16(a, planes, s);
+    default: return launch_up0_f32(a, planes, s);
+  }
+}
+cudaError_t launch_stage_up(int prec, const UpArgs& a, int planes, cudaStream_t s) {
+  switch (prec) {
+    case FLLF_FP16: return launch_up_f16(a, planes, s);
+    case FLLF_BF16: return launch_up_bf16(a, planes, s);
+    default: return launch_up_f32(a, planes, s);
+  }
+}
+cudaError_t launch_stage_down(int prec, const DownArgs& a, int planes, cudaStream_t s) {
+  switch (prec) {
+    case FLLF_FP16: return launch_down_f16(a, planes, s);
+    case FLLF_BF16: return launch_down_bf16(a, planes, s);
+    default: return launch_down_f32(a, planes, s);
+  }
+}
+cudaError_t launch_stage_down0(int prec, const Down0Args& a, int planes, cudaStream_t s) {
+  switch (prec) {
+    case FLLF_FP16: return launch_down0_f16(a, planes, s);
+    case FLLF_BF16: return launch_down0_bf16(a, planes, s);
+    default: return launch_down0_f32(a, planes, s);
+  }
+}
+
+}  // namespace
+
+namespace fllf {
+
+// Enqueues the whole path for one image on `s` (plan scratch must be free).
+cudaError_t enqueue_path(const fllf_params& p, const std::vector<Level>& lv, const float* d_a,
+                         const float* d_in, float* d_out, cudaStream_t s, StageHook* hook) {
+  const int L = p.levels, C = p.C, prec = p.precision;
+  const float turns = (float)(2.0 / p.T);
+  if (L == 1) {
+    // Only the top level: L_0[O] = G_0[I] = I.
+    return cudaMemcpyAsync(d_out, d_in, sizeof(float) * (size_t)p.H * p.W * C,
+                           cudaMemcpyDeviceToDevice, s);
+  }
+  auto mark = [&](int st, bool b) {
+    if (hook) hook->mark(st, b, s);
+  };
+  cudaError_t e;
+  Up0Args u0{d_in, p.H, p.W, lv[1], p.K, turns};
+  mark(FLLF_STAGE_UP0, true);
+  if ((e = launch_stage_up0(prec, u0, C, s)) != cudaSuccess) return e;
+  mark(FLLF_STAGE_UP0, false);
+  for (int l = 1; l <= L - 2; ++l) {
+    UpArgs u{lv[l], lv[l + 1], p.K, (l + 1 <= L - 2) ? 1 : 0};
+    mark(FLLF_STAGE_UP, true);
+    if ((e = launch_stage_up(prec, u, C, s)) != cudaSuccess) return e;
+    mark(FLLF_STAGE_UP, false);
+  }
+  for (int l = L - 2; l >= 1; --l) {
+    DownArgs d{lv[l], lv[l + 1], d_a, p.K, turns, (l + 1 <= L - 2) ? 1 : 0};
+    mark(FLLF_STAGE_DOWN, true);
+    if ((e = launch_stage_down(prec, d, C, s)) != cudaSuccess) return e;
+    mark(FLLF_STAGE_DOWN, false);
+  }
+  Down0Args d0{d_in, d_out, p.H, p.W, lv[1], d_a, p.K, turns, (L >= 3) ? 1 : 0};
+  mark(FLLF_STAGE_DOWN0, true);
+  if ((e = launch_stage_down0(prec, d0, C, s)) != cudaSuccess) return e;
+  mark(FLLF_STAGE_DOWN0, false);
+  return cudaSuccess;
+}
+
+
+
+}  // namespace fllf
+
+extern "C" {
+
+const char* fllf_status_str(fllf_status s) {
+  switch (s) {
+    case FLLF_OK: return "FLLF_OK";
+    case FLLF_EINVAL: return "FLLF_EINVAL";
+    case FLLF_ENOMEM: return "FLLF_ENOMEM";
+    case FLLF_ECUDA: return "FLLF_ECUDA";
+    case FLLF_EAGAIN: return "FLLF_EAGAIN";
+    case FLLF_ETIMEOUT: return "FLLF_ETIMEOUT";
+    case FLLF_EBUSY: return "FLLF_EBUSY";
+  }
+  return "FLLF_UNKNOWN";
+}
+
+const char* fllf_last_error(void) { return g_last_error.c_str(); }
+
+fllf_status fllf_params_validate(const fllf_params* p) { return validate(p); }
+
+fllf_status fllf_coeffs(const fllf_params* p, double* a_out) {
+  fllf_status st = validate(p);
+  if (st != FLLF_OK) return st;
+  if (!a_out) return fail(FLLF_EINVAL, "a_out is NULL");
+  compute_coeffs(*p, a_out);
+  return FLLF_OK;
+}
+
+size_t fllf_plan_scratch_bytes(const fllf_params* p) {
+  if (validate(p) != FLLF_OK) return 0;
+  return layout(*p, nullptr);
+}
+
+fllf_status fllf_plan_create(const fllf_params* p, int device, fllf_plan** out) {
+  if (!out) return fail(FLLF_EINVAL, "out is NULL");
+  *out = nullptr;
+  fllf_status st = validate(p);
+  if (st != FLLF_OK) return st;
+  int ndev = 0;
+  cudaError_t e = cudaGetDeviceCount(&ndev);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDeviceCount");
+  if (device < 0 || device >= ndev) return fail(FLLF_EINVAL, "device out of range");
+  DeviceGuard guard(device);
+  if (!guard.ok) return fail(FLLF_ECUDA, "cudaSetDevice failed");
+
+  fllf_plan* pl = new (std::nothrow) fllf_plan();
+  if (!pl) return fail(FLLF_ENOMEM, "host allocation of the plan failed");
+  pl->p = *p;
+  pl->device = device;
+  pl->a64.assign(p->K, 0.0);
+  compute_coeffs(*p, pl->a64.data());
+  std::vector<float> a32(p->K);
+  for (int k = 0; k < p->K; ++k) a32[k] = (float)pl->a64[k];
+
+  if ((e = cudaMalloc(&pl->d_a, sizeof(float) * p->K)) != cudaSuccess) {
+    free_plan(pl);
+    return fail(FLLF_ENOMEM, std::string("coefficient allocation: ") + cudaGetErrorString(e));
+  }
+  if ((e = cudaMemcpy(pl->d_a, a32.data(), sizeof(float) * p->K, cudaMemcpyHostToDevice)) !=
+      cudaSuccess) {
+    free_plan(pl);
+    return cuda_fail(e, "coefficient upload");
+  }
+  std::vector<Level> rel;
+  pl->scratch_bytes = layout(*p, &rel);
+  if (pl->scratch_bytes) {
+    if ((e = cudaMalloc(&pl->scratch, pl->scratch_bytes)) != cudaSuccess) {
+      cudaGetLastError();
+      free_plan(pl);
+      return fail(FLLF_ENOMEM, std::string("scratch allocation: ") + cudaGetErrorString(e));
+    }
+  }
+  // layout() returns byte offsets (the first buffer sits at offset 0): rebase
+  // by level role -- G and Z exist at every level l >= 1, E at 1 <= l <= L-2.
+  pl->lv = rel;
+  const int L = p->levels;
+  for (int l = 0; l < L; ++l) {
+    Level& lv = pl->lv[l];
+    if (l == 0) {
+      lv.G = nullptr;
+      lv.Z = nullptr;
+      lv.E = nullptr;
+      continue;
+    }
+    lv.G = reinterpret_cast<float*>(pl->scratch + reinterpret_cast<size_t>(rel[l].G));
+    lv.Z = pl->scratch + reinterpret_cast<size_t>(rel[l].Z);
+    lv.E = (l <= L - 2) ? reinterpret_cast<float*>(pl->scratch + reinterpret_cast<size_t>(rel[l].E))
+                        : nullptr;
+  }
+  if (!check_layout(*p, pl->lv, pl->scratch, pl->scratch_bytes)) {
+    free_plan(pl);
+    return fail(FLLF_EINVAL, "internal error: scratch layout outside the allocation");
+  }
+  *out = pl;
+  return FLLF_OK;
+}
+
+fllf_status fllf_plan_destroy(fllf_plan* plan) {
+  if (!plan) return FLLF_OK;
+  DeviceGuard guard(plan->device);
+  free_plan(plan);
+  return FLLF_OK;
+}
+
+fllf_status fllf_plan_params(const fllf_plan* plan, fllf_params* out) {
+  if (!plan || !out) return fail(FLLF_EINVAL, "plan or out is NULL");
+  *out = plan->p;
+  return FLLF_OK;
+}
+
+fllf_status fllf_plan_coeffs(const fllf_plan* plan, double* a_out) {
+  if (!plan || !a_out) return fail(FLLF_EINVAL, "plan or a_out is NULL");
+  std::memcpy(a_out, plan->a64.data(), sizeof(double) * plan->p.K);
+  return FLLF_OK;
+}
+
+fllf_status fllf_run(fllf_plan* plan, const float* d_in, float* d_out, void* stream) {
+  if (!plan) return fail(FLLF_EINVAL, "plan is NULL");
+  if (!d_in || !d_out) return fail(FLLF_EINVAL, "input or output pointer is NULL");
+  const size_t n = (size_t)plan->p.H * plan->p.W * plan->p.C;
+  const char *a = reinterpret_cast<const char*>(d_in), *b = reinterpret_cast<const char*>(d_out);
+  if (a < b + n * sizeof(float) && b < a + n * sizeof(float))
+    return fail(FLLF_EINVAL, "input and output buffers overlap");
+  DeviceGuard guard(plan->device);
+  if (!guard.ok) return fail(FLLF_ECUDA, "cudaSetDevice failed");
+  cudaError_t e = enqueue_path(plan->p, plan->lv, plan->d_a, d_in, d_out,
+                               reinterpret_cast<cudaStream_t>(stream), plan->timer);
+  if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
+  return FLLF_OK;
+}
+
+fllf_status fllf_run_host(fllf_plan* plan, const float* h_in, float* h_out, void* stream) {
+  if (!plan) return fail(FLLF_EINVAL, "plan is NULL");
+  if (!h_in || !h_out) return fail(FLLF_EINVAL, "input or output pointer is NULL");
+  DeviceGuard guard(plan->device);
+  if (!guard.ok) return fail(FLLF_ECUDA, "cudaSetDevice failed");
+  const size_t bytes = sizeof(float) * (size_t)plan->p.H * plan->p.W * plan->p.C;
+  cudaError_t e;
+  if (!plan->d_io_in) {
+    if ((e = cudaMalloc(&plan->d_io_in, bytes)) != cudaSuccess) {
+      cudaGetLastError();
+      plan->d_io_in = nullptr;
+      return fail(FLLF_ENOMEM, "device input buffer allocation failed");
+    }
+  }
+  if (!plan->d_io_out) {
+    if ((e = cudaMalloc(&plan->d_io_out, bytes)) != cudaSuccess) {
+      cudaGetLastError();
+      plan->d_io_out = nullptr;
+      return fail(FLLF_ENOMEM, "device output buffer allocation failed");
+    }
+  }
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  if ((e = cudaMemcpyAsync(plan->d_io_in, h_in, bytes, cudaMemcpyHostToDevice, s)) != cudaSuccess)
+    return cuda_fail(e, "host-to-device copy");
+  if ((e = enqueue_path(plan->p, plan->lv, plan->d_a, plan->d_io_in, plan->d_io_out, s,
+                        plan->timer)) != cudaSuccess)
+    return cuda_fail(e, "kernel launch");
+  if ((e = cudaMemcpyAsync(h_out, plan->d_io_out, bytes, cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+    return cuda_fail(e, "device-to-host copy");
+  if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_fail(e, "stream synchronize");
+  return FLLF_OK;
+}
+
+fllf_status fllf_submit(fllf_plan* plan, const float* d_in, float* d_out, void* stream,
+                        uint64_t* ticket) {
+  if (!ticket) return fail(FLLF_EINVAL, "ticket is NULL");
+  fllf_status st = fllf_run(plan, d_in, d_out, stream);
+  if (st != FLLF_OK) return st;
+  DeviceGuard guard(plan->device);
+  cudaEvent_t ev;
+  cudaError_t e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaEventCreate");
+  if ((e = cudaEventRecord(ev, reinterpret_cast<cudaStream_t>(stream))) != cudaSuccess) {
+    cudaEventDestroy(ev);
+    return cuda_fail(e, "cudaEventRecord");
+  }
+  std::lock_guard<std::mutex> lk(g_ticket_mu);
+  *ticket = g_next_ticket++;
+  g_tickets[*ticket] = {ev, plan->device};
+  return FLLF_OK;
+}
+
+fllf_status fllf_poll(uint64_t ticket, int timeout_us) {
+  cudaEvent_t ev;
+  int dev;
+  {
+    std::lock_guard<std::mutex> lk(g_ticket_mu);
+    auto it = g_tickets.find(ticket);
+    if (it == g_tickets.end()) return fail(FLLF_EINVAL, "unknown or consumed ticket");
+    ev = it->second.first;
+    dev = it->second.second;
+  }
+  DeviceGuard guard(dev);
+  const auto t0 = std::chrono::steady_clock::now();
+  for (;;) {
+    cudaError_t e = cudaEventQuery(ev);
+    if (e == cudaSuccess || (e != cudaErrorNotReady)) {
+      std::lock_guard<std::mutex> lk(g_ticket_mu);
+      g_tickets.erase(ticket);
+      cudaEventDestroy(ev);
+      if (e != cudaSuccess) return cuda_fail(e, "submitted work failed");
+      return FLLF_OK;
+    }
+    if (timeout_us == 0) return FLLF_EAGAIN;
+    const auto us = std::chrono::duration_cast<std::chrono::microseconds>(
+                        std::chrono::steady_clock::now() - t0).count();
+    if (timeout_us > 0 && us >= timeout_us) return fail(FLLF_ETIMEOUT, "ticket still pending");
+    std::this_thread::sleep_for(std::chrono::microseconds(20));
+  }
+}
+
+fllf_status fllf_plan_enable_timing(fllf_plan* plan, int enable) {
+  if (!plan) return fail(FLLF_EINVAL, "plan is NULL");
+  DeviceGuard guard(plan->device);
+  if (enable && !plan->timer) plan->timer = new (std::nothrow) StageTimer();
+  if (enable && !plan->timer) return fail(FLLF_ENOMEM, "timer allocation failed");
+  if (!enable) {
+    delete plan->timer;
+    plan->timer = nullptr;
+  }
+  return FLLF_OK;
+}
+
+fllf_status fllf_plan_stage_times(fllf_plan* plan, double* ms, int* launches) {
+  if (!plan || !ms || !launches) return fail(FLLF_EINVAL, "plan, ms or launches is NULL");
+  for (int i = 0; i < FLLF_NSTAGE; ++i) {
+    ms[i] = 0.0;
+    launches[i] = 0;
+  }
+  if (!plan->timer) return FLLF_OK;
+  DeviceGuard guard(plan->device);
+  StageTimer* t = plan->timer;
+  fllf_status st = FLLF_OK;
+  for (auto& p : t->pending) {
+    float x = 0.f;
+    cudaError_t e = cudaEventSynchronize(p.e);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&x, p.b, p.e);
+    if (e != cudaSuccess) {
+      st = cuda_fail(e, "stage timing");
+    } else {
+      ms[p.stage] += x;
+      launches[p.stage] += 1;
+    }
+    t->pool.push_back(p.b);
+    t->pool.push_back(p.e);
+  }
+  t->pending.clear();
+  if (t->failed) st = fail(FLLF_ECUDA, "event creation failed during timing");
+  t->failed = false;
+  return st;
+}
+
+}  // extern "C"

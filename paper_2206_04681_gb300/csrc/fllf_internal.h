@@ -1,0 +1,70 @@
+// fllf_internal.h -- host helpers shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <string>
+#include <vector>
+
+#include "fllf.h"
+#include "fllf_device.cuh"
+
+namespace fllf {
+
+void set_last_error(const std::string& s);
+fllf_status validate(const fllf_params* p);
+// a_1..a_K in float64 (quadrature over one period, or the closed form).
+void compute_coeffs(const fllf_params& p, double* a);
+// Scratch layout of a plan; returns its size in bytes.  With `out`, fills
+// the per-level descriptors with offsets (to be rebased on the allocation).
+size_t layout(const fllf_params& p, std::vector<Level>* out);
+// Optional hook called before and after every kernel launch of a path
+// (stage kind, begin?) -- used by the per-stage timing diagnostics.
+struct StageHook {
+  virtual ~StageHook() = default;
+  virtual void mark(int stage, bool begin, cudaStream_t s) = 0;
+};
+
+// Records a pair of events around every launch; events are pooled per plan.
+struct StageTimer : StageHook {
+  struct Pair { int stage; cudaEvent_t b, e; };
+  std::vector<cudaEvent_t> pool;
+  std::vector<Pair> pending;
+  cudaEvent_t open = nullptr;
+  bool failed = false;
+  cudaEvent_t get() {
+    if (!pool.empty()) {
+      cudaEvent_t ev = pool.back();
+      pool.pop_back();
+      return ev;
+    }
+    cudaEvent_t ev = nullptr;
+    if (cudaEventCreate(&ev) != cudaSuccess) failed = true;
+    return ev;
+  }
+  void mark(int stage, bool begin, cudaStream_t s) override {
+    cudaEvent_t ev = get();
+    if (!ev) return;
+    cudaEventRecord(ev, s);
+    if (begin) {
+      open = ev;
+    } else if (open) {
+      pending.push_back({stage, open, ev});
+      open = nullptr;
+    }
+  }
+  ~StageTimer() override {
+    for (auto& p : pending) {
+      cudaEventDestroy(p.b);
+      cudaEventDestroy(p.e);
+    }
+    for (auto ev : pool) cudaEventDestroy(ev);
+  }
+};
+
+// Enqueues the whole Fourier LLF path of one image on stream s.
+cudaError_t enqueue_path(const fllf_params& p, const std::vector<Level>& lv, const float* d_a,
+                         const float* d_in, float* d_out, cudaStream_t s,
+                         StageHook* hook = nullptr);
+
+}  // namespace fllf

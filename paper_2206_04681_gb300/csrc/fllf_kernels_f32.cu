@@ -1,0 +1,4 @@
+// Per-stage kernels with the Fourier pyramids stored as float.
+#define FLLF_STORAGE float
+#define FLLF_LAUNCH_NAME(stage) launch_##stage##_f32
+#include "fllf_kernels.inl"

@@ -1,0 +1,21 @@
+// fllf_launch.h -- host-side launchers of the per-stage kernels (internal).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "fllf_device.cuh"
+
+namespace fllf {
+
+// One set of launchers per storage precision of the Fourier pyramids.
+#define FLLF_DECLARE_LAUNCHERS(suffix)                                                       \
+  cudaError_t launch_up0_##suffix(const Up0Args& a, int planes, cudaStream_t s);            \
+  cudaError_t launch_up_##suffix(const UpArgs& a, int planes, cudaStream_t s);              \
+  cudaError_t launch_down_##suffix(const DownArgs& a, int planes, cudaStream_t s);          \
+  cudaError_t launch_down0_##suffix(const Down0Args& a, int planes, cudaStream_t s);
+FLLF_DECLARE_LAUNCHERS(f32)
+FLLF_DECLARE_LAUNCHERS(f16)
+FLLF_DECLARE_LAUNCHERS(bf16)
+#undef FLLF_DECLARE_LAUNCHERS
+
+}  // namespace fllf

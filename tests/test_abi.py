@@ -1,0 +1,99 @@
+"""CPU-side checks of the C ABI: the library loads, exports every declared
+symbol, and its host-only calls (validation, coefficients, scratch sizing,
+status names) behave as include/fllf.h states.  No kernel runs here."""
+
+import ctypes
+import glob
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle as o
+import paper_2206_04681_gb300 as pkg
+from paper_2206_04681_gb300 import build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build.build_library()
+    return pkg.lib()
+
+
+def declared_functions():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = open(h).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        names |= set(re.findall(r"\b(fllf_[a-z0-9_]+)\s*\(", text))
+    return sorted(names)
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared_functions()
+    assert "fllf_run" in names and "fllf_plan_create" in names
+    missing = [n for n in names if not hasattr(lib, n)]
+    assert not missing, f"declared but not exported: {missing}"
+
+
+def test_status_names(lib):
+    assert lib.fllf_status_str(0) == b"FLLF_OK"
+    assert lib.fllf_status_str(1) == b"FLLF_EINVAL"
+    assert lib.fllf_status_str(6) == b"FLLF_EBUSY"
+
+
+@pytest.mark.parametrize("m,sigma,T,K", [(3.0, 0.1, 2.0, 4), (3.0, 0.2, 2.0, 8),
+                                         (0.5, 0.4, 2.0, 16), (4.0, 0.05, 2.0, 64),
+                                         (7.0, 30.0, 405.9, 10)])
+def test_host_coefficients_match_oracle(lib, m, sigma, T, K):
+    p = pkg.make_params(64, 64, 1, 4, K, m, sigma, T)
+    got = np.array(pkg.fllf_coeffs(p))
+    np.testing.assert_allclose(got, o.coeffs_quadrature(m, sigma, T, K), rtol=0,
+                               atol=1e-12 * max(1.0, abs(m - 1) * sigma))
+    p.coeff_mode = pkg.FLLF_COEFF_CLOSED_FORM
+    got = np.array(pkg.fllf_coeffs(p))
+    np.testing.assert_allclose(got, o.coeffs_closed_form(m, sigma, T, K), rtol=1e-13, atol=1e-16)
+
+
+@pytest.mark.parametrize("field,value", [("H", 0), ("W", -3), ("C", 0), ("C", 65), ("levels", 0),
+                                         ("levels", 17), ("K", 0), ("K", 65), ("sigma_r", 0.0),
+                                         ("T", -1.0), ("m", float("nan")), ("precision", 3),
+                                         ("coeff_mode", 2)])
+def test_invalid_params_rejected(lib, field, value):
+    p = pkg.make_params(32, 32, 1, 4, 4)
+    setattr(p, field, value)
+    assert pkg.fllf_params_validate(p) == pkg.FLLF_EINVAL
+    assert pkg.fllf_plan_scratch_bytes(p) == 0
+    assert lib.fllf_last_error() != b""
+    with pytest.raises(pkg.FllfError) as e:
+        pkg.fllf_coeffs(p)
+    assert e.value.status == pkg.FLLF_EINVAL
+
+
+def test_scratch_bytes_formula(lib):
+    # G (float), Z (K complex) per level l >= 1, E for 1 <= l <= levels-2,
+    # pitch rounded to 16 elements, each buffer 256-byte aligned.
+    def expect(H, W, C, L, K, zbytes):
+        total, h, w = 0, H, W
+        a = lambda x: (x + 255) // 256 * 256
+        for l in range(L):
+            if l > 0:
+                pitch = (w + 15) // 16 * 16
+                g = a(4 * h * pitch * C)
+                total += g + a(zbytes * K * h * pitch * C) + (g if l <= L - 2 else 0)
+            h, w = (h + 1) // 2, (w + 1) // 2
+        return total
+    for prec, zb in (("fp32", 8), ("fp16", 4), ("bf16", 4)):
+        p = pkg.make_params(2160, 3840, 3, 8, 8, precision=prec)
+        assert pkg.fllf_plan_scratch_bytes(p) == expect(2160, 3840, 3, 8, 8, zb)
+    p = pkg.make_params(7, 5, 1, 1, 3)
+    assert pkg.fllf_plan_scratch_bytes(p) == 0
+
+
+def test_null_arguments_rejected(lib):
+    assert lib.fllf_plan_destroy(None) == pkg.FLLF_OK
+    assert lib.fllf_run(None, None, None, None) == pkg.FLLF_EINVAL
+    assert lib.fllf_poll(ctypes.c_uint64(123456789), 0) == pkg.FLLF_EINVAL
