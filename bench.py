@@ -1,0 +1,410 @@
+#!/usr/bin/env python3
+"""Benchmark of the Fourier LLF hot path on GB300 (one JSON line on stdout).
+
+Workload: one 3840 x 2160 RGB frame (planar float32, synthetic, seeded;
+40 polygons, texture and noise), every channel filtered independently,
+8 pyramid levels, K = 8 Fourier orders, m = 3, sigma_r = 0.2, T = 2.
+A step is one pass of the whole path (all kernels) over one frame.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp32|fp16|bf16]
+    python bench.py --impl reference ...     # the float64 CPU oracle, timed on host cores
+
+Multi-GPU runs (torchrun, one rank per GPU) are replicas: each rank filters
+its own frames, no collective on the data path (weak scaling); the timed
+region is bracketed by barriers and the slowest rank's time is reported.
+"""
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Mpixel/s Fourier LLF K=8 4K RGB at PSNR≥60dB vs FP64; serving p50/p99 ms"
+UNIT = "Mpixel/s"
+WORKLOAD = dict(H=2160, W=3840, C=3, polygons=40, seed=2, levels=8, K=8, m=3.0, sigma_r=0.2, T=2.0)
+N_FRAMES = 4          # distinct input/output frames cycled per step (4 x 99.5 MB > 129 MB L2)
+STAGES = ("up0", "up", "down", "down0")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--precision", choices=["fp32", "fp16", "bf16"], default="fp32")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-variants", action="store_true")
+    return ap.parse_args()
+
+
+def level_sizes(H, W, L):
+    out, h, w = [], H, W
+    for _ in range(L):
+        out.append((h, w))
+        h, w = (h + 1) // 2, (w + 1) // 2
+    return out
+
+
+def stage_work(cfg, zbytes):
+    """Algorithmic FP32 ops and bytes per stage kind for one frame (all planes).
+
+    Ops (FMA = 1; the method's separable stencil count):
+      trig per evaluated pixel      16 (sincospi) + 2 (K - 1) (Chebyshev, cos and sin)
+      REDUCE per output per image   13 (2 horizontal x 4 + vertical 4 + scale)
+      EXPAND-combine per fine pixel
+        per complex order           9 at level 0 (6 expand + 3 product-accumulate),
+                                    11 at level >= 1 (+2 for Z_l - up(Z_{l+1}))
+        residual expand + add       4
+    Bytes: each input element read once and each output written once.
+    """
+    L, K, C = cfg["levels"], cfg["K"], cfg["C"]
+    sz = level_sizes(cfg["H"], cfg["W"], L)
+    n = [h * w for h, w in sz]
+    trig = 16 + 2 * (K - 1)
+    ops = dict.fromkeys(STAGES, 0.0)
+    byt = dict.fromkeys(STAGES, 0.0)
+    ops["up0"] = n[0] * trig + n[1] * 13 * (2 * K + 1)
+    byt["up0"] = 4 * n[0] + 4 * n[1] + zbytes * K * n[1]
+    for l in range(1, L - 1):
+        g = 1 if l + 1 <= L - 2 else 0
+        ops["up"] += n[l + 1] * 13 * (2 * K + g)
+        byt["up"] += (4 * n[l] * g + zbytes * K * n[l]) + (4 * n[l + 1] * g + zbytes * K * n[l + 1])
+    for l in range(1, L - 1):
+        e = 1 if l + 1 <= L - 2 else 0
+        ops["down"] += n[l] * (trig + 11 * K + 4 * e)
+        byt["down"] += (4 * n[l] + zbytes * K * n[l] + zbytes * K * n[l + 1] + 4 * n[l + 1] * e
+                        + 4 * n[l])
+    e1 = 1 if L >= 3 else 0
+    ops["down0"] = n[0] * (trig + 9 * K + 4 * e1)
+    byt["down0"] = 4 * n[0] + zbytes * K * n[1] + 4 * n[1] * e1 + 4 * n[0]
+    return {k: v * C for k, v in ops.items()}, {k: v * C for k, v in byt.items()}
+
+
+def hbm_min_bytes(cfg):
+    """Input read + output write + guide pyramid (levels >= 1) written once and read once."""
+    sz = level_sizes(cfg["H"], cfg["W"], cfg["levels"])
+    guide = sum(h * w for h, w in sz[1:])
+    return cfg["C"] * (4 * cfg["H"] * cfg["W"] * 2 + 2 * 4 * guide)
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle-reason samples during the timed region."""
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100", "-f", self.path],
+                stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.15)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 8:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[0]) for r in rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[4 + i].lower() == "active"})
+        loaded = [s for s in sm if mx and s >= 0.5 * max(mx)] or sm
+        return {"sm_mhz": statistics.median(loaded) if loaded else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows)}
+
+
+def cpu_oracle_sample():
+    """Float64 oracle on channel 0 of the 4K frame (one of three planes)."""
+    import numpy as np
+    import oracle
+    from paper_2206_04681_gb300.synth import synth_image
+    cfg = WORKLOAD
+    img = synth_image(cfg["H"], cfg["W"], cfg["C"], cfg["polygons"], cfg["seed"])
+    a = oracle.coeffs_quadrature(cfg["m"], cfg["sigma_r"], cfg["T"], cfg["K"])
+    t0 = time.perf_counter()
+    oracle.fourier_llf(img[0].astype(np.float64), cfg["levels"], a, cfg["T"])
+    dt = time.perf_counter() - t0
+    frame_s = dt * cfg["C"]
+    return {"value": cfg["H"] * cfg["W"] / frame_s / 1e6, "unit": UNIT, "cores": 1,
+            "kind": "oracle",
+            "sample": f"float64 numpy oracle, channel 0 of the 3840x2160x3 frame "
+                      f"({dt:.1f} s; frame time = 3 x plane time)"}
+
+
+def run_reference(args):
+    """Reference arm: the float64 CPU oracle as it stands, on host cores."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import numpy as np
+    import oracle
+    from paper_2206_04681_gb300.synth import synth_image
+    cfg = WORKLOAD
+    img = synth_image(cfg["H"], cfg["W"], cfg["C"], cfg["polygons"], cfg["seed"])
+    a = oracle.coeffs_quadrature(cfg["m"], cfg["sigma_r"], cfg["T"], cfg["K"])
+    # each step: one plane of a 960 x 540 crop (a bounded sample of the frame)
+    crop = img[0, 810:1350, 1440:2400].astype(np.float64)
+    for _ in range(args.warmup):
+        oracle.fourier_llf(crop, cfg["levels"], a, cfg["T"])
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.fourier_llf(crop, cfg["levels"], a, cfg["T"])
+    dt = (time.perf_counter() - t0) / args.steps
+    value = crop.size / (dt * cfg["C"]) / 1e6   # a pixel counts once over its 3 channels
+    sample = "float64 numpy oracle on one plane of a 960x540 crop per step (RGB time = 3 x plane)"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": "uhd_rgb_3840x2160x3_L8_K8", "H": cfg["H"], "W": cfg["W"],
+                       "C": cfg["C"], "levels": cfg["levels"], "K": cfg["K"], "m": cfg["m"],
+                       "sigma_r": cfg["sigma_r"], "T": cfg["T"], "sample": "960x540 crop, 1 plane"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def time_precision(pkg, torch, cfg, precision, frames, steps, warmup, stream, device):
+    p = pkg.make_params(cfg["H"], cfg["W"], cfg["C"], cfg["levels"], cfg["K"], cfg["m"],
+                        cfg["sigma_r"], cfg["T"], precision)
+    plan = pkg.fllf_plan_create(p, device)
+    outs = [torch.empty_like(f) for f in frames]
+    try:
+        with torch.cuda.stream(stream):
+            for i in range(warmup):
+                pkg.fllf_run(plan, frames[i % len(frames)].data_ptr(),
+                             outs[i % len(frames)].data_ptr(), stream.cuda_stream)
+            stream.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for i in range(steps):
+                pkg.fllf_run(plan, frames[i % len(frames)].data_ptr(),
+                             outs[i % len(frames)].data_ptr(), stream.cuda_stream)
+            e1.record(stream)
+            e1.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+    finally:
+        pkg.fllf_plan_destroy(plan)
+    return ms
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    import paper_2206_04681_gb300 as pkg
+    from paper_2206_04681_gb300 import build
+    from paper_2206_04681_gb300.synth import synth_image
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    device = local
+
+    build.build_library()
+    cfg = WORKLOAD
+    img = synth_image(cfg["H"], cfg["W"], cfg["C"], cfg["polygons"], cfg["seed"] + rank)
+    base = torch.from_numpy(img).cuda()
+    frames = [base.clone() for _ in range(N_FRAMES)]
+    outs = [torch.empty_like(base) for _ in range(N_FRAMES)]
+    stream = torch.cuda.Stream()
+
+    p = pkg.make_params(cfg["H"], cfg["W"], cfg["C"], cfg["levels"], cfg["K"], cfg["m"],
+                        cfg["sigma_r"], cfg["T"], args.precision)
+    plan = pkg.fllf_plan_create(p, device)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    with torch.cuda.stream(stream):
+        for i in range(args.warmup):
+            pkg.fllf_run(plan, frames[i % N_FRAMES].data_ptr(), outs[i % N_FRAMES].data_ptr(),
+                         stream.cuda_stream)
+    stream.synchronize()
+    torch.cuda.synchronize()
+
+    pkg.fllf_plan_enable_timing(plan, True)
+    pkg.fllf_plan_stage_times(plan)                  # clear
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(stream):
+        e0.record(stream)
+        for i in range(args.steps):
+            pkg.fllf_run(plan, frames[i % N_FRAMES].data_ptr(), outs[i % N_FRAMES].data_ptr(),
+                         stream.cuda_stream)
+        e1.record(stream)
+    e1.synchronize()
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    total_ms = e0.elapsed_time(e1)
+    stage = pkg.fllf_plan_stage_times(plan)
+    pkg.fllf_plan_enable_timing(plan, False)
+    if world > 1:
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_step = total_ms / args.steps
+    pixels = cfg["H"] * cfg["W"]
+    value = world * pixels / (ms_step * 1e-3) / 1e6
+
+    # end to end through the C ABI with host buffers (copies inside the timed region)
+    hin = torch.from_numpy(img).pin_memory()
+    hout = torch.empty_like(hin).pin_memory()
+    e2e_steps = max(3, min(50, args.steps // 20))
+    for _ in range(2):
+        pkg.fllf_run_host(plan, hin.data_ptr(), hout.data_ptr(), stream.cuda_stream)
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        pkg.fllf_run_host(plan, hin.data_ptr(), hout.data_ptr(), stream.cuda_stream)
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    if world > 1:
+        t = torch.tensor([e2e_s], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    pkg.fllf_plan_destroy(plan)
+
+    zbytes = 8 if args.precision == "fp32" else 4
+    ops, byt = stage_work(cfg, zbytes)
+    dom = max(STAGES, key=lambda s: stage[s][0])
+    dom_ms, dom_launches = stage[dom]
+    per_launch_s = dom_ms / max(dom_launches, 1) * 1e-3
+    launches_per_step = {s: stage[s][1] / args.steps for s in STAGES}
+    ops_launch = ops[dom] / max(launches_per_step[dom], 1)
+    byt_launch = byt[dom] / max(launches_per_step[dom], 1)
+    sms = torch.cuda.get_device_properties(device).multi_processor_count
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        pass
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    hbm_src = "measured" if "hbm_gbs" in peaks else "fallback"
+    mhz = (clk or {}).get("sm_mhz") or peaks.get("clocks_under_load", {}).get("sm_mhz_median") or 1900.0
+    alu_peak = sms * 128 * mhz * 1e6 / 1e12           # FP32 lane-ops/s (FMA = 1), in T
+    alu_ach = ops_launch / per_launch_s / 1e12
+    hbm_ach = byt_launch / per_launch_s / 1e9
+    alu_frac, hbm_frac = alu_ach / alu_peak, hbm_ach / hbm_peak
+    if alu_frac >= hbm_frac:
+        roof = {"bound": "alu", "achieved": alu_ach, "peak": alu_peak, "unit": "Top/s",
+                "frac": alu_frac, "traffic": None, "kernel": dom,
+                "peak_source": f"{sms} SMs x 128 FP32 lanes x {mhz:.0f} MHz (median SM clock "
+                               "sampled in this run)",
+                "hbm_alt": {"achieved": hbm_ach, "peak": hbm_peak, "unit": "GB/s",
+                            "frac": hbm_frac, "peak_source": hbm_src}}
+    else:
+        roof = {"bound": "hbm", "achieved": hbm_ach, "peak": hbm_peak, "unit": "GB/s",
+                "frac": hbm_frac, "traffic": None, "kernel": dom, "peak_source": hbm_src,
+                "alu_alt": {"achieved": alu_ach, "peak": alu_peak, "unit": "Top/s",
+                            "frac": alu_frac}}
+    traffic_file = os.path.join(ROOT, "profiles", "dram_traffic.txt")
+    try:
+        tr = json.load(open(traffic_file))
+        key = f"{dom}:{args.precision}"
+        if key in tr and tr[key].get("kernel_rev") == kernel_revision():
+            roof["traffic"] = tr[key]["bytes_per_launch"]
+    except (OSError, ValueError):
+        pass
+    hbm_min = hbm_min_bytes(cfg)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "uhd_rgb_3840x2160x3_L8_K8", "H": cfg["H"], "W": cfg["W"],
+                   "C": cfg["C"], "levels": cfg["levels"], "K": cfg["K"], "m": cfg["m"],
+                   "sigma_r": cfg["sigma_r"], "T": cfg["T"],
+                   "pyramid_storage": args.precision,
+                   "parallelism": "replicas" if world > 1 else "single",
+                   "l2": f"inputs cycled over {N_FRAMES} frames ({N_FRAMES * 99.5:.0f} MB) plus "
+                         "the plan scratch per step; working set > 129 MB L2"},
+        "e2e": {"value": world * pixels / e2e_s / 1e6, "unit": UNIT,
+                "h2d_bytes_per_step": int(hin.numel() * 4), "d2h_bytes_per_step": int(hout.numel() * 4)},
+        "gpu_launches": int(sum(stage[s][1] for s in STAGES)),
+        "roofline": roof,
+        "hbm_min_roofline": {"bytes_per_step": hbm_min, "achieved": hbm_min / (ms_step * 1e-3) / 1e9,
+                             "peak": hbm_peak, "unit": "GB/s",
+                             "frac": hbm_min / (ms_step * 1e-3) / 1e9 / hbm_peak},
+        "stages_ms_per_step": {s: stage[s][0] / args.steps for s in STAGES},
+        "clocks": clk,
+    }
+    if rank == 0 and not args.no_variants and world == 1:
+        variants = {}
+        for prec in ("fp32", "fp16", "bf16"):
+            if prec == args.precision:
+                continue
+            ms = time_precision(pkg, torch, cfg, prec, frames, min(args.steps, 500), 10, stream, device)
+            variants[prec] = {"ms_per_step": ms, "value": pixels / (ms * 1e-3) / 1e6}
+        line["precision_variants"] = variants
+    if rank == 0 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_oracle_sample()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def kernel_revision():
+    """Hash of the CUDA sources, to tell whether stored ncu traffic is current."""
+    import hashlib
+    h = hashlib.sha1()
+    csrc = os.path.join(ROOT, "paper_2206_04681_gb300", "csrc")
+    for name in sorted(os.listdir(csrc)):
+        if name.endswith((".cu", ".cuh", ".inl", ".h")):
+            h.update(open(os.path.join(csrc, name), "rb").read())
+    return h.hexdigest()[:12]
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())
