@@ -137,6 +137,32 @@ fllf_status fllf_submit(fllf_plan *plan, const float *d_in, float *d_out, void *
  * FLLF_ECUDA: the work failed on the device. */
 fllf_status fllf_poll(uint64_t ticket, int timeout_us);
 
+/* ---- Filtering without any device allocation -------------------------------
+ * The paper has no counterpart to this entry point; it exists for callers
+ * that cannot call cudaMalloc (code running inside a memory pool or an
+ * allocator it does not own, real-time loops where an allocation could block
+ * or fragment memory, plugin hosts that hand out only the image buffers).
+ *
+ * fllf_run_noalloc filters one C x H x W image (d_in -> d_out, device
+ * pointers on the current device, non-overlapping) exactly like fllf_run
+ * with a plan of the same parameters, but keeps the coefficients and the
+ * guide, Fourier and residual pyramids in one fixed device array compiled
+ * into the library (FLLF_NOALLOC_SCRATCH_BYTES per GPU, held by every GPU
+ * that loads the library until the process exits).  It allocates no device
+ * memory and enqueues on `stream`.
+ *   - Returns FLLF_EINVAL, with the byte counts in fllf_last_error(), when
+ *     the parameter set needs more scratch than the array holds
+ *     (fllf_plan_scratch_bytes(p) + 256 bytes must fit), and for the usual
+ *     invalid arguments.
+ *   - All calls on one GPU share the array, which keeps the last call's
+ *     contents; calls whose GPU work overlaps (two streams or threads)
+ *     race on it, so serialise them.  Nothing in it must start at zero.
+ *   - The first call on a device looks up the array's device address with
+ *     cudaGetSymbolAddress on the current device (this may load the
+ *     module), so make the first call before any stream capture. */
+#define FLLF_NOALLOC_SCRATCH_BYTES (32u << 20)
+fllf_status fllf_run_noalloc(const fllf_params *p, const float *d_in, float *d_out, void *stream);
+
 /* ---- Diagnostics: per-stage device timing -------------------------------
  * Stage kinds of the path (Fig. 1 read as a pipeline): */
 enum {

@@ -48,6 +48,7 @@ _SIGS = {
     "fllf_run_host": (ctypes.c_int, [_P, _P, _P, _P]),
     "fllf_submit": (ctypes.c_int, [_P, _P, _P, _P, ctypes.POINTER(ctypes.c_uint64)]),
     "fllf_poll": (ctypes.c_int, [ctypes.c_uint64, ctypes.c_int]),
+    "fllf_run_noalloc": (ctypes.c_int, [ctypes.POINTER(fllf_params), _P, _P, _P]),
     "fllf_plan_enable_timing": (ctypes.c_int, [_P, ctypes.c_int]),
     "fllf_plan_stage_times": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_double),
                                              ctypes.POINTER(ctypes.c_int)]),
@@ -146,6 +147,14 @@ def fllf_submit(plan, d_in, d_out, stream=0):
     t = ctypes.c_uint64()
     _check(lib().fllf_submit(plan, _P(d_in), _P(d_out), _P(stream), ctypes.byref(t)))
     return t.value
+
+
+NOALLOC_SCRATCH_BYTES = 32 << 20
+
+
+def fllf_run_noalloc(p, d_in, d_out, stream=0):
+    """Filter with the library's fixed device scratch array (no allocation)."""
+    _check(lib().fllf_run_noalloc(ctypes.byref(p), _P(d_in), _P(d_out), _P(stream)))
 
 
 def fllf_plan_enable_timing(plan, enable=True):

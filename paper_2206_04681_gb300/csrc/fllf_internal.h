@@ -18,6 +18,9 @@ void compute_coeffs(const fllf_params& p, double* a);
 // Scratch layout of a plan; returns its size in bytes.  With `out`, fills
 // the per-level descriptors with offsets (to be rebased on the allocation).
 size_t layout(const fllf_params& p, std::vector<Level>* out);
+// True when every level buffer of `lv` lies inside [base, base + bytes).
+bool check_layout(const fllf_params& p, const std::vector<Level>& lv, const unsigned char* base,
+                  size_t bytes);
 // Optional hook called before and after every kernel launch of a path
 // (stage kind, begin?) -- used by the per-stage timing diagnostics.
 struct StageHook {
