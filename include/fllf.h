@@ -152,7 +152,7 @@ fllf_status fllf_poll(uint64_t ticket, int timeout_us);
  * memory and enqueues on `stream`.
  *   - Returns FLLF_EINVAL, with the byte counts in fllf_last_error(), when
  *     the parameter set needs more scratch than the array holds
- *     (fllf_plan_scratch_bytes(p) + 256 bytes must fit), and for the usual
+ *     (fllf_plan_scratch_bytes(p) + 512 bytes must fit), and for the usual
  *     invalid arguments.
  *   - All calls on one GPU share the array, which keeps the last call's
  *     contents; calls whose GPU work overlaps (two streams or threads)

@@ -200,17 +200,25 @@ struct fllf_plan {
   float* d_io_in = nullptr;
   float* d_io_out = nullptr;
   StageTimer* timer = nullptr;  // per-stage timing diagnostics (optional)
+  PathMaps maps;                // TMA tensor maps of the level buffers
+  unsigned* d_fault = nullptr;  // device word set by a kernel whose bounded wait ran out
 };
 
 namespace {
 
 std::mutex g_ticket_mu;
-std::unordered_map<uint64_t, std::pair<cudaEvent_t, int>> g_tickets;
+struct Ticket {
+  cudaEvent_t ev;
+  int device;
+  fllf_plan* plan;
+};
+std::unordered_map<uint64_t, Ticket> g_tickets;
 uint64_t g_next_ticket = 1;
 
 void free_plan(fllf_plan* pl) {
   if (!pl) return;
   if (pl->d_a) cudaFree(pl->d_a);
+  if (pl->d_fault) cudaFree(pl->d_fault);
   if (pl->scratch) cudaFree(pl->scratch);
   if (pl->d_io_in) cudaFree(pl->d_io_in);
   if (pl->d_io_out) cudaFree(pl->d_io_out);
@@ -218,79 +226,20 @@ void free_plan(fllf_plan* pl) {
   delete pl;
 }
 
-cudaError_t launch_stage_up0(int prec, const Up0Args& a, int planes, cudaStream_t s) {
-  switch (prec) {
-    case FLLF_FP16: return launch_up0_f16(a, planes, s);
-    case FLLF_BF16: return launch_up0_bf16(a, planes, s);
-    default: return launch_up0_f32(a, planes, s);
-  }
-}
-cudaError_t launch_stage_up(int prec, const UpArgs& a, int planes, cudaStream_t s) {
-  switch (prec) {
-    case FLLF_FP16: return launch_up_f16(a, planes, s);
-    case FLLF_BF16: return launch_up_bf16(a, planes, s);
-    default: return launch_up_f32(a, planes, s);
-  }
-}
-cudaError_t launch_stage_down(int prec, const DownArgs& a, int planes, cudaStream_t s) {
-  switch (prec) {
-    case FLLF_FP16: return launch_down_f16(a, planes, s);
-    case FLLF_BF16: return launch_down_bf16(a, planes, s);
-    default: return launch_down_f32(a, planes, s);
-  }
-}
-cudaError_t launch_stage_down0(int prec, const Down0Args& a, int planes, cudaStream_t s) {
-  switch (prec) {
-    case FLLF_FP16: return launch_down0_f16(a, planes, s);
-    case FLLF_BF16: return launch_down0_bf16(a, planes, s);
-    default: return launch_down0_f32(a, planes, s);
-  }
-}
-
 }  // namespace
 
-namespace fllf {
 
-// Enqueues the whole path for one image on `s` (plan scratch must be free).
-cudaError_t enqueue_path(const fllf_params& p, const std::vector<Level>& lv, const float* d_a,
-                         const float* d_in, float* d_out, cudaStream_t s, StageHook* hook) {
-  const int L = p.levels, C = p.C, prec = p.precision;
-  const float turns = (float)(2.0 / p.T);
-  if (L == 1) {
-    // Only the top level: L_0[O] = G_0[I] = I.
-    return cudaMemcpyAsync(d_out, d_in, sizeof(float) * (size_t)p.H * p.W * C,
-                           cudaMemcpyDeviceToDevice, s);
+// Reads and clears the plan's fault word (after the plan's work completed).
+static fllf_status check_fault(fllf_plan* plan) {
+  unsigned f = 0;
+  cudaError_t e = cudaMemcpy(&f, plan->d_fault, sizeof(unsigned), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(e, "fault word read");
+  if (f) {
+    cudaMemset(plan->d_fault, 0, sizeof(unsigned));
+    return fail(FLLF_ETIMEOUT, "a kernel's bounded wait for a shared-memory copy ran out");
   }
-  auto mark = [&](int st, bool b) {
-    if (hook) hook->mark(st, b, s);
-  };
-  cudaError_t e;
-  Up0Args u0{d_in, p.H, p.W, lv[1], p.K, turns};
-  mark(FLLF_STAGE_UP0, true);
-  if ((e = launch_stage_up0(prec, u0, C, s)) != cudaSuccess) return e;
-  mark(FLLF_STAGE_UP0, false);
-  for (int l = 1; l <= L - 2; ++l) {
-    UpArgs u{lv[l], lv[l + 1], p.K, (l + 1 <= L - 2) ? 1 : 0};
-    mark(FLLF_STAGE_UP, true);
-    if ((e = launch_stage_up(prec, u, C, s)) != cudaSuccess) return e;
-    mark(FLLF_STAGE_UP, false);
-  }
-  for (int l = L - 2; l >= 1; --l) {
-    DownArgs d{lv[l], lv[l + 1], d_a, p.K, turns, (l + 1 <= L - 2) ? 1 : 0};
-    mark(FLLF_STAGE_DOWN, true);
-    if ((e = launch_stage_down(prec, d, C, s)) != cudaSuccess) return e;
-    mark(FLLF_STAGE_DOWN, false);
-  }
-  Down0Args d0{d_in, d_out, p.H, p.W, lv[1], d_a, p.K, turns, (L >= 3) ? 1 : 0};
-  mark(FLLF_STAGE_DOWN0, true);
-  if ((e = launch_stage_down0(prec, d0, C, s)) != cudaSuccess) return e;
-  mark(FLLF_STAGE_DOWN0, false);
-  return cudaSuccess;
+  return FLLF_OK;
 }
-
-
-
-}  // namespace fllf
 
 extern "C" {
 
@@ -384,6 +333,20 @@ fllf_status fllf_plan_create(const fllf_params* p, int device, fllf_plan** out) 
     free_plan(pl);
     return fail(FLLF_EINVAL, "internal error: scratch layout outside the allocation");
   }
+  if ((e = cudaMalloc(&pl->d_fault, 256)) != cudaSuccess) {
+    cudaGetLastError();
+    pl->d_fault = nullptr;
+    free_plan(pl);
+    return fail(FLLF_ENOMEM, "fault word allocation failed");
+  }
+  if ((e = cudaMemset(pl->d_fault, 0, 256)) != cudaSuccess) {
+    free_plan(pl);
+    return cuda_fail(e, "fault word clear");
+  }
+  if (p->levels > 1 && !build_maps(*p, pl->lv, &pl->maps)) {
+    free_plan(pl);
+    return fail(FLLF_ECUDA, "TMA tensor map encoding failed (cuTensorMapEncodeTiled)");
+  }
   *out = pl;
   return FLLF_OK;
 }
@@ -416,7 +379,7 @@ fllf_status fllf_run(fllf_plan* plan, const float* d_in, float* d_out, void* str
     return fail(FLLF_EINVAL, "input and output buffers overlap");
   DeviceGuard guard(plan->device);
   if (!guard.ok) return fail(FLLF_ECUDA, "cudaSetDevice failed");
-  cudaError_t e = enqueue_path(plan->p, plan->lv, plan->d_a, d_in, d_out,
+  cudaError_t e = enqueue_path(plan->p, plan->lv, plan->maps, plan->d_a, plan->d_fault, d_in, d_out,
                                reinterpret_cast<cudaStream_t>(stream), plan->timer);
   if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
   return FLLF_OK;
@@ -446,13 +409,13 @@ fllf_status fllf_run_host(fllf_plan* plan, const float* h_in, float* h_out, void
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   if ((e = cudaMemcpyAsync(plan->d_io_in, h_in, bytes, cudaMemcpyHostToDevice, s)) != cudaSuccess)
     return cuda_fail(e, "host-to-device copy");
-  if ((e = enqueue_path(plan->p, plan->lv, plan->d_a, plan->d_io_in, plan->d_io_out, s,
-                        plan->timer)) != cudaSuccess)
+  if ((e = enqueue_path(plan->p, plan->lv, plan->maps, plan->d_a, plan->d_fault, plan->d_io_in,
+                        plan->d_io_out, s, plan->timer)) != cudaSuccess)
     return cuda_fail(e, "kernel launch");
   if ((e = cudaMemcpyAsync(h_out, plan->d_io_out, bytes, cudaMemcpyDeviceToHost, s)) != cudaSuccess)
     return cuda_fail(e, "device-to-host copy");
   if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_fail(e, "stream synchronize");
-  return FLLF_OK;
+  return check_fault(plan);
 }
 
 fllf_status fllf_submit(fllf_plan* plan, const float* d_in, float* d_out, void* stream,
@@ -470,30 +433,30 @@ fllf_status fllf_submit(fllf_plan* plan, const float* d_in, float* d_out, void* 
   }
   std::lock_guard<std::mutex> lk(g_ticket_mu);
   *ticket = g_next_ticket++;
-  g_tickets[*ticket] = {ev, plan->device};
+  g_tickets[*ticket] = Ticket{ev, plan->device, plan};
   return FLLF_OK;
 }
 
 fllf_status fllf_poll(uint64_t ticket, int timeout_us) {
-  cudaEvent_t ev;
-  int dev;
+  Ticket tk;
   {
     std::lock_guard<std::mutex> lk(g_ticket_mu);
     auto it = g_tickets.find(ticket);
     if (it == g_tickets.end()) return fail(FLLF_EINVAL, "unknown or consumed ticket");
-    ev = it->second.first;
-    dev = it->second.second;
+    tk = it->second;
   }
-  DeviceGuard guard(dev);
+  DeviceGuard guard(tk.device);
   const auto t0 = std::chrono::steady_clock::now();
   for (;;) {
-    cudaError_t e = cudaEventQuery(ev);
+    cudaError_t e = cudaEventQuery(tk.ev);
     if (e == cudaSuccess || (e != cudaErrorNotReady)) {
-      std::lock_guard<std::mutex> lk(g_ticket_mu);
-      g_tickets.erase(ticket);
-      cudaEventDestroy(ev);
+      {
+        std::lock_guard<std::mutex> lk(g_ticket_mu);
+        g_tickets.erase(ticket);
+      }
+      cudaEventDestroy(tk.ev);
       if (e != cudaSuccess) return cuda_fail(e, "submitted work failed");
-      return FLLF_OK;
+      return check_fault(tk.plan);
     }
     if (timeout_us == 0) return FLLF_EAGAIN;
     const auto us = std::chrono::duration_cast<std::chrono::microseconds>(

@@ -65,9 +65,20 @@ struct StageTimer : StageHook {
   }
 };
 
-// Enqueues the whole Fourier LLF path of one image on stream s.
-cudaError_t enqueue_path(const fllf_params& p, const std::vector<Level>& lv, const float* d_a,
-                         const float* d_in, float* d_out, cudaStream_t s,
-                         StageHook* hook = nullptr);
+// TMA tensor maps of a plan's pyramid levels (indexed by level).
+struct PathMaps {
+  std::vector<CUtensorMap> z_dn;  // Z_l read as the coarse level of a combine
+  std::vector<CUtensorMap> e_dn;  // E_l read as the coarse level of a combine
+  std::vector<CUtensorMap> z_up;  // Z_l read as the source of a REDUCE
+  std::vector<CUtensorMap> g_up;  // G_l read as the source of a REDUCE
+};
+// Encodes the maps for the level buffers in `lv` (device addresses).
+bool build_maps(const fllf_params& p, const std::vector<Level>& lv, PathMaps* m);
+
+// Enqueues the whole Fourier LLF path of one image on stream s.  `fault`
+// is a device word that kernels set when a bounded wait runs out.
+cudaError_t enqueue_path(const fllf_params& p, const std::vector<Level>& lv, const PathMaps& maps,
+                         const float* d_a, unsigned* fault, const float* d_in, float* d_out,
+                         cudaStream_t s, StageHook* hook = nullptr);
 
 }  // namespace fllf

@@ -1,56 +1,575 @@
-// fllf_kernels.inl -- per-stage __global__ kernels for one storage type
-// FLLF_STORAGE; included by one translation unit per precision.
+// fllf_kernels.inl -- the four persistent kernels of the path for one storage
+// type FLLF_STORAGE; included by one translation unit per precision.
+//
+// Every kernel is persistent: CTA b handles tiles b, b + gridDim.x, ... as a
+// stream of (tile, chunk) work items, two shared-memory buffers deep, so the
+// TMA copy of the next item overlaps the computation of the current one.
 #include "fllf_launch.h"
 
 namespace fllf {
 
+namespace {
+
+// Waits (bounded) for a TMA copy still in flight before a CTA leaves early.
+__device__ __forceinline__ void drain(uint64_t* b, uint32_t parity) {
+  const long long t0 = clock64();
+  while (!mbar_test(b, parity) && clock64() - t0 < kWaitCycles) {
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+// up0: level 0 -> 1.  Item (row r, segment s) holds 11 fine pixels of one
+// staged input row; it evaluates e^{i k w_1 x} for k = 1..K with the
+// Chebyshev recurrence z_{k+1} = 2 cos(w_1 x) z_k - z_{k-1} (one packed FMA
+// per order) from one hardware sincos per pixel and writes 4 horizontally
+// reduced complex values per order to column-major staging; the vertical
+// pass finishes REDUCE (Eq. (1)) and stores G_1 and Z_1.
 template <typename S>
-__global__ void __launch_bounds__(kThreads) k_up0(const Up0Args a) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  up0_tile<S>(a, blockIdx.x, blockIdx.y, blockIdx.z, smem);
+__global__ void __launch_bounds__(kThreads) k_up0(const __grid_constant__ Up0Args a) {
+  using CT = typename Cplx<S>::T;
+  using SM = Smem<sizeof(CT)>;
+  extern __shared__ __align__(128) unsigned char smem[];
+  float* itb[2] = {reinterpret_cast<float*>(smem), reinterpret_cast<float*>(smem + SM::up0_it)};
+  float2* hz = reinterpret_cast<float2*>(smem + 2 * SM::up0_it);
+  float* hg = reinterpret_cast<float*>(smem + 2 * SM::up0_it + align128(SM::up0_hz));
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + 2 * SM::up0_it + align128(SM::up0_hz) +
+                                              align128(SM::up0_hg));
+  const int tid = threadIdx.x;
+  const int ntx = cdiv(a.dst.w, kUpTW), nty = cdiv(a.dst.h, kUpTH);
+  const int ntiles = ntx * nty * a.planes;
+  const int nch = cdiv(a.K, kKC);
+  if (tid == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  auto issue = [&](int t, int buf) {
+    const int tx = t % ntx, r = t / ntx, ty = r % nty, pl = r / nty;
+    mbar_expect_tx(&bar[buf], sizeof(float) * kUpIR * kUpIW);
+    tma_load3(itb[buf], &a.imap, 2 * tx * kUpTW - 4, 2 * ty * kUpTH - 2, pl, &bar[buf]);
+  };
+  if (a.use_tma && tid == 0 && (int)blockIdx.x < ntiles) issue(blockIdx.x, 0);
+
+  int n = 0;
+  for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++n) {
+    const int buf = n & 1;
+    const int tx = t % ntx, rt = t / ntx, ty = rt % nty, pl = rt / nty;
+    const int X1 = tx * kUpTW, Y1 = ty * kUpTH;
+    const int xs = 2 * X1 - 4, ys = 2 * Y1 - 2;
+    float* it = itb[buf];
+    if (a.use_tma) {
+      const int tn = t + gridDim.x;
+      if (tid == 0 && tn < ntiles) {
+        fence_proxy_async();
+        issue(tn, buf ^ 1);
+      }
+      if (!mbar_wait_cta(&bar[buf], (n >> 1) & 1, a.fault)) {
+        if (tid == 0 && tn < ntiles) drain(&bar[buf ^ 1], ((n + 1) >> 1) & 1);
+        return;
+      }
+      fix_borders(it, 1, kUpIR, kUpIW, xs, ys, a.w0, a.h0,
+                  [&](int y) { return refl101(y, a.h0); }, [&](int x) { return refl101(x, a.w0); });
+    } else {
+      const float* Ip = a.I + (long long)pl * a.h0 * a.w0;
+      for (int idx = tid; idx < kUpIR * kUpIW; idx += kThreads) {
+        const int rr = idx / kUpIW, cc = idx - rr * kUpIW;
+        it[idx] = __ldg(Ip + (long long)refl_fast(ys + rr, a.h0) * a.w0 + refl_fast(xs + cc, a.w0));
+      }
+      __syncthreads();
+    }
+
+    const bool item = tid < kUpItems;
+    const int r = tid % kUpIR, s = tid / kUpIR;
+    float2 zc[kUpIPX], zp[kUpIPX], tc[kUpIPX];
+    if (item) {
+      float v[kUpIPX];
+#pragma unroll
+      for (int j = 0; j < kUpIPX; ++j) v[j] = it[r * kUpIW + 2 + 2 * kUpRun * s + j];
+#pragma unroll
+      for (int j = 0; j < kUpIPX; ++j) {
+        const float2 z = cos_sin_turns(a.turns * v[j]);
+        zc[j] = z;
+        zp[j] = make_float2(1.f, 0.f);
+        tc[j] = splat(2.f * z.x);
+      }
+#pragma unroll
+      for (int q = 0; q < kUpRun; ++q)
+        hg[(kUpRun * s + q) * kUpCS + r] =
+            tap5(v[2 * q], v[2 * q + 1], v[2 * q + 2], v[2 * q + 3], v[2 * q + 4]);
+    }
+    for (int ch = 0; ch < nch; ++ch) {
+      if (item) {
+#pragma unroll
+        for (int kk = 0; kk < kKC; ++kk) {
+#pragma unroll
+          for (int q = 0; q < kUpRun; ++q)
+            hz[(kk * kUpTW + kUpRun * s + q) * kUpCS + r] =
+                tap5(zc[2 * q], zc[2 * q + 1], zc[2 * q + 2], zc[2 * q + 3], zc[2 * q + 4]);
+#pragma unroll
+          for (int j = 0; j < kUpIPX; ++j) {
+            const float2 zn = fma2(tc[j], zc[j], make_float2(-zp[j].x, -zp[j].y));
+            zp[j] = zc[j];
+            zc[j] = zn;
+          }
+        }
+      }
+      __syncthreads();
+      {
+        // vertical: thread (order kk, column col, row group grp)
+        const int kk = tid / (2 * kUpTW), grp = (tid / kUpTW) & 1, col = tid % kUpTW;
+        const int k = ch * kKC + kk, x = X1 + col;
+        if (k < a.K && x < a.dst.w) {
+          CT* Zk = reinterpret_cast<CT*>(a.dst.Z) + (long long)pl * a.dst.zplane +
+                   (long long)k * a.dst.zk + x;
+          const float4* p = reinterpret_cast<const float4*>(hz + (kk * kUpTW + col) * kUpCS + 2 * kUpVRows * grp);
+          float2 w[2 * kUpVRows + 4];
+#pragma unroll
+          for (int u = 0; u < kUpVRows + 2; ++u) {
+            const float4 q4 = p[u];
+            w[2 * u] = make_float2(q4.x, q4.y);
+            w[2 * u + 1] = make_float2(q4.z, q4.w);
+          }
+#pragma unroll
+          for (int j = 0; j < kUpVRows; ++j) {
+            const int y = Y1 + grp * kUpVRows + j;
+            if (y < a.dst.h)
+              Cplx<S>::st(Zk + (long long)y * a.dst.pitch,
+                          mul2(splat(1.f / 256.f), tap5(w[2 * j], w[2 * j + 1], w[2 * j + 2], w[2 * j + 3], w[2 * j + 4])));
+          }
+        }
+        if (ch == 0 && tid < 2 * kUpTW) {
+          const int g2 = tid / kUpTW, c2 = tid % kUpTW, xg = X1 + c2;
+          if (xg < a.dst.w) {
+            float* G = a.dst.G + (long long)pl * a.dst.gplane + xg;
+            const float2* p = reinterpret_cast<const float2*>(hg + c2 * kUpCS + 2 * kUpVRows * g2);
+            float w[2 * kUpVRows + 4];
+#pragma unroll
+            for (int u = 0; u < kUpVRows + 2; ++u) {
+              const float2 q2 = p[u];
+              w[2 * u] = q2.x;
+              w[2 * u + 1] = q2.y;
+            }
+#pragma unroll
+            for (int j = 0; j < kUpVRows; ++j) {
+              const int y = Y1 + g2 * kUpVRows + j;
+              if (y < a.dst.h)
+                G[(long long)y * a.dst.pitch] =
+                    (1.f / 256.f) * tap5(w[2 * j], w[2 * j + 1], w[2 * j + 2], w[2 * j + 3], w[2 * j + 4]);
+            }
+          }
+        }
+      }
+      __syncthreads();
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+// up: level l -> l+1 for l >= 1 (REDUCE of G_l and the K complex planes).
+// Work item = (tile, chunk of KCU orders).  TMA stages the 35 x 68 source
+// box of each order of the chunk (plus G_l with chunk 0); the vertical pass
+// reads one staged column per thread and keeps the reduced rows in
+// registers; the horizontal pass reads 5 staged columns per output.
+template <typename S>
+__global__ void __launch_bounds__(kThreads) k_up(const __grid_constant__ UpArgs a) {
+  using CT = typename Cplx<S>::T;
+  using SM = Smem<sizeof(CT)>;
+  constexpr int KCU = SM::up_kc;
+  constexpr int RG = kThreads / (KCU * kRsVW);  // vertical row groups
+  constexpr int VOUT = kRsTH / RG;              // coarse rows per vertical thread
+  constexpr int HQ = kThreads / (KCU * kRsTW);  // horizontal row groups
+  constexpr int HOUT = kRsTH / HQ;
+  static_assert(RG * KCU * kRsVW == kThreads, "vertical mapping");
+  static_assert(kRsTH % HQ == 0, "horizontal mapping");
+  extern __shared__ __align__(128) unsigned char smem[];
+  unsigned char* bufs[2] = {smem, smem + SM::up_buf};
+  float2* vb = reinterpret_cast<float2*>(smem + 2 * SM::up_buf);
+  float* vg = reinterpret_cast<float*>(smem + 2 * SM::up_buf + SM::up_vb);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + 2 * SM::up_buf + SM::up_vb + SM::up_vg);
+  const int tid = threadIdx.x;
+  const int ntx = cdiv(a.dst.w, kRsTW), nty = cdiv(a.dst.h, kRsTH);
+  const int ntiles = ntx * nty * a.planes;
+  const int nch = cdiv(a.K, KCU);
+  // Work items are (tile, chunk of orders) pairs: orders reduce independently,
+  // so small levels still spread over many CTAs.
+  const int total = ntiles * nch;
+  if ((int)blockIdx.x >= total) return;
+  const int nitems = (total - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x;
+  if (tid == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  auto issue = [&](int i, int buf) {
+    const int gi = (int)blockIdx.x + i * (int)gridDim.x, t = gi / nch, ch = gi % nch;
+    const int tx = t % ntx, r = t / ntx, ty = r % nty, pl = r / nty;
+    const int x = 2 * tx * kRsTW - 4, y = 2 * ty * kRsTH - 2;
+    const bool g = ch == 0 && a.write_g;
+    mbar_expect_tx(&bar[buf], (uint32_t)(sizeof(CT) * KCU * kRsIR * kRsBW +
+                                         (g ? sizeof(float) * kRsIR * kRsBW : 0)));
+    tma_load3(bufs[buf], &a.zmap, x, y, pl * a.K + ch * KCU, &bar[buf]);
+    if (g) tma_load3(bufs[buf] + SM::up_src, &a.gmap, x, y, pl, &bar[buf]);
+  };
+  if (tid == 0) issue(0, 0);
+  for (int i = 0; i < nitems; ++i) {
+    const int buf = i & 1;
+    const int gi = (int)blockIdx.x + i * (int)gridDim.x, t = gi / nch, ch = gi % nch;
+    const int tx = t % ntx, rt = t / ntx, ty = rt % nty, pl = rt / nty;
+    const int X1 = tx * kRsTW, Y1 = ty * kRsTH;
+    const int xs = 2 * X1 - 4, ys = 2 * Y1 - 2;
+    const bool g = ch == 0 && a.write_g;
+    if (tid == 0 && i + 1 < nitems) {
+      fence_proxy_async();
+      issue(i + 1, buf ^ 1);
+    }
+    if (!mbar_wait_cta(&bar[buf], (i >> 1) & 1, a.fault)) {
+      if (tid == 0 && i + 1 < nitems) drain(&bar[buf ^ 1], ((i + 1) >> 1) & 1);
+      return;
+    }
+    CT* src = reinterpret_cast<CT*>(bufs[buf]);
+    float* gsrc = reinterpret_cast<float*>(bufs[buf] + SM::up_src);
+    auto my = [&](int y) { return refl101(y, a.src.h); };
+    auto mx = [&](int x) { return refl101(x, a.src.w); };
+    fix_borders(src, KCU, kRsIR, kRsBW, xs, ys, a.src.w, a.src.h, my, mx);
+    if (g) fix_borders(gsrc, 1, kRsIR, kRsBW, xs, ys, a.src.w, a.src.h, my, mx);
+
+    {  // vertical half
+      const int rg = tid / (KCU * kRsVW), kk = (tid / kRsVW) % KCU, c = tid % kRsVW;
+      const CT* col = src + (kk * kRsIR + 2 * VOUT * rg) * kRsBW + c + 2;
+      float2 v[2 * VOUT + 3];
+#pragma unroll
+      for (int u = 0; u < 2 * VOUT + 3; ++u) v[u] = Cplx<S>::cvt(col[u * kRsBW]);
+#pragma unroll
+      for (int j = 0; j < VOUT; ++j)
+        vb[(kk * kRsTH + VOUT * rg + j) * kRsVW + c] =
+            tap5(v[2 * j], v[2 * j + 1], v[2 * j + 2], v[2 * j + 3], v[2 * j + 4]);
+      if (g) {
+        const int grp = tid / kRsVW, cg = tid % kRsVW;  // 4 groups x 4 coarse rows
+        const float* gc = gsrc + (8 * grp) * kRsBW + cg + 2;
+        float u[11];
+#pragma unroll
+        for (int q = 0; q < 11; ++q) u[q] = gc[q * kRsBW];
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+          vg[(4 * grp + j) * kRsVW + cg] = tap5(u[2 * j], u[2 * j + 1], u[2 * j + 2], u[2 * j + 3], u[2 * j + 4]);
+      }
+    }
+    __syncthreads();
+    {  // horizontal half
+      if (tid < KCU * kRsTW * HQ) {
+        const int hk = tid / (kRsTW * HQ), rem = tid % (kRsTW * HQ);
+        const int hq = rem / kRsTW, ic = rem % kRsTW;
+        const int k = ch * KCU + hk, x = X1 + ic;
+        if (k < a.K && x < a.dst.w) {
+          CT* Zk = reinterpret_cast<CT*>(a.dst.Z) + (long long)pl * a.dst.zplane +
+                   (long long)k * a.dst.zk + x;
+#pragma unroll
+          for (int j = 0; j < HOUT; ++j) {
+            const int jr = hq * HOUT + j, y = Y1 + jr;
+            if (y < a.dst.h) {
+              const float2* p = vb + (hk * kRsTH + jr) * kRsVW + 2 * ic;
+              const float4 q0 = *reinterpret_cast<const float4*>(p);
+              const float4 q1 = *reinterpret_cast<const float4*>(p + 2);
+              const float2 o = tap5(make_float2(q0.x, q0.y), make_float2(q0.z, q0.w),
+                                    make_float2(q1.x, q1.y), make_float2(q1.z, q1.w), p[4]);
+              Cplx<S>::st(Zk + (long long)y * a.dst.pitch, mul2(splat(1.f / 256.f), o));
+            }
+          }
+        }
+      }
+      if (g && tid < 2 * kRsTW) {
+        const int half = tid / kRsTW, ic = tid % kRsTW, x = X1 + ic;
+        if (x < a.dst.w) {
+          float* G = a.dst.G + (long long)pl * a.dst.gplane + x;
+#pragma unroll
+          for (int j = 0; j < kRsTH / 2; ++j) {
+            const int jr = half * (kRsTH / 2) + j, y = Y1 + jr;
+            if (y < a.dst.h) {
+              const float* p = vg + jr * kRsVW + 2 * ic;
+              G[(long long)y * a.dst.pitch] = (1.f / 256.f) * tap5(p[0], p[1], p[2], p[3], p[4]);
+            }
+          }
+        }
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+// Combine (Eq. (14) product-sum fused with the residual collapse).
+// A thread owns fine rows 2j, 2j+1 and fine columns 4c..4c+3 of the tile
+// (tile origin 64*tx-6), i.e. coarse rows j-1..j+1 and coarse columns
+// 2c-1..2c+2, which sit at staged rows tr..tr+2 and columns 2tc..2tc+3.
+// EXPAND of the 3 x 4 complex window runs on (C~, S~) pairs with packed
+// FP32x2 arithmetic; the per-pixel trig state (cos, -sin) of the two fine
+// rows and the accumulators are (even row, odd row) pairs, advanced by
+// complex rotation.  EXPAND weights 1/8 (1, 6, 1) at even fine positions and
+// 1/2 (1, 1) at odd ones per axis are folded into the coefficients.
+__device__ __forceinline__ float2 expand_scale_pair(int q) {
+  return (q & 1) ? make_float2(1.f / 16.f, 1.f / 4.f) : make_float2(1.f / 64.f, 1.f / 16.f);
+}
+
+template <typename S, bool LEVEL0>
+__device__ __forceinline__ void combine_body(const CUtensorMap* zmap, const CUtensorMap* emap,
+                                             const Level* fine, const float* I, float* O, int h,
+                                             int w, int planes, const Level& coarse,
+                                             const float* acoef, int K, float turns, int has_e,
+                                             unsigned* fault) {
+  using CT = typename Cplx<S>::T;
+  using SM = Smem<sizeof(CT)>;
+  extern __shared__ __align__(128) unsigned char smem[];
+  unsigned char* bufs[2] = {smem, smem + SM::dn_buf};
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + 2 * SM::dn_buf);
+  const int tid = threadIdx.x;
+  const int ntx = cdiv(w + kDnX0, kDnOW), nty = cdiv(h, kDnOH);
+  const int ntiles = ntx * nty * planes;
+  const int nch = cdiv(K, kKC);
+  if ((int)blockIdx.x >= ntiles) return;
+  const int nmine = (ntiles - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x;
+  const int nitems = nmine * nch;
+  if (tid == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  auto issue = [&](int i, int buf) {
+    const int t = (int)blockIdx.x + (i / nch) * (int)gridDim.x, ch = i % nch;
+    const int tx = t % ntx, r = t / ntx, ty = r % nty, pl = r / nty;
+    const int cx0 = (tx * kDnOW - kDnX0) / 2 - 1, cy0 = ty * (kDnOH / 2) - 1;
+    const bool e = ch == 0 && has_e;
+    mbar_expect_tx(&bar[buf], (uint32_t)(sizeof(CT) * kKC * kDnCH * kDnCW +
+                                         (e ? sizeof(float) * kDnCH * kDnCW : 0)));
+    tma_load3(bufs[buf], zmap, cx0, cy0, pl * K + ch * kKC, &bar[buf]);
+    if (e) tma_load3(bufs[buf] + SM::dn_z, emap, cx0, cy0, pl, &bar[buf]);
+  };
+  if (tid == 0) issue(0, 0);
+
+  const int tc = tid % (kDnOW / 4), tr = tid / (kDnOW / 4);
+  float2 cc[4], ns[4], c1[4], s1[4], ns1[4], acc[4];
+  int xq[4], y0c = 0, y1c = 0, fy = 0, fx = 0, pl = 0;
+  for (int i = 0; i < nitems; ++i) {
+    const int buf = i & 1;
+    const int t = (int)blockIdx.x + (i / nch) * (int)gridDim.x, ch = i % nch;
+    const int tx = t % ntx, rt = t / ntx, ty = rt % nty;
+    pl = rt / nty;
+    const int X0 = tx * kDnOW - kDnX0, Y0 = ty * kDnOH;
+    const int cx0 = X0 / 2 - 1, cy0 = Y0 / 2 - 1;
+    if (tid == 0 && i + 1 < nitems) {
+      fence_proxy_async();
+      issue(i + 1, buf ^ 1);
+    }
+    if (ch == 0) {
+      // Per-tile state: guide value g, trig state (cos, -sin) for k = 1, accumulators.
+      fy = Y0 + 2 * tr;
+      fx = X0 + 4 * tc;
+      y0c = min(fy, h - 1);
+      y1c = min(fy + 1, h - 1);
+      const long long gpitch = LEVEL0 ? (long long)w : (long long)fine->pitch;
+      const float* gsrc = LEVEL0 ? I + (long long)pl * h * w : fine->G + (long long)pl * fine->gplane;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        xq[q] = min(max(fx + q, 0), w - 1);
+        const float g0 = __ldg(gsrc + y0c * gpitch + xq[q]);
+        const float g1 = __ldg(gsrc + y1c * gpitch + xq[q]);
+        const float2 z0 = cos_sin_turns(turns * g0), z1 = cos_sin_turns(turns * g1);
+        c1[q] = make_float2(z0.x, z1.x);
+        s1[q] = make_float2(z0.y, z1.y);
+        ns1[q] = make_float2(-z0.y, -z1.y);
+        cc[q] = c1[q];
+        ns[q] = ns1[q];
+        acc[q] = LEVEL0 ? make_float2(g0, g1) : splat(0.f);
+      }
+    }
+    if (!mbar_wait_cta(&bar[buf], (i >> 1) & 1, fault)) {
+      if (tid == 0 && i + 1 < nitems) drain(&bar[buf ^ 1], ((i + 1) >> 1) & 1);
+      return;
+    }
+    CT* zb = reinterpret_cast<CT*>(bufs[buf]);
+    float* eb = reinterpret_cast<float*>(bufs[buf] + SM::dn_z);
+    auto my = [&](int y) { return ext_coarse(y, coarse.h, h); };
+    auto mx = [&](int x) { return ext_coarse(x, coarse.w, w); };
+    fix_borders(zb, kKC, kDnCH, kDnCW, cx0, cy0, coarse.w, coarse.h, my, mx);
+    if (ch == 0 && has_e) {
+      fix_borders(eb, 1, kDnCH, kDnCW, cx0, cy0, coarse.w, coarse.h, my, mx);
+      float v[3][4];
+#pragma unroll
+      for (int r = 0; r < 3; ++r) {
+        // 8-byte aligned (2*tc floats): two float2 reads
+        const float2* q2 = reinterpret_cast<const float2*>(eb + (tr + r) * kDnCW + 2 * tc);
+        const float2 qa = q2[0], qb = q2[1];
+        v[r][0] = qa.x; v[r][1] = qa.y; v[r][2] = qb.x; v[r][3] = qb.y;
+      }
+      float2 p[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) p[q] = make_float2(fmaf(6.f, v[1][q], v[0][q] + v[2][q]), v[1][q] + v[2][q]);
+      const float2 u0 = fma2(splat(6.f), p[1], add2(p[0], p[2]));
+      const float2 u1 = add2(p[1], p[2]);
+      const float2 u2 = fma2(splat(6.f), p[2], add2(p[1], p[3]));
+      const float2 u3 = add2(p[2], p[3]);
+      acc[0] = fma2(expand_scale_pair(0), u0, acc[0]);
+      acc[1] = fma2(expand_scale_pair(1), u1, acc[1]);
+      acc[2] = fma2(expand_scale_pair(2), u2, acc[2]);
+      acc[3] = fma2(expand_scale_pair(3), u3, acc[3]);
+    }
+#pragma unroll
+    for (int kk = 0; kk < kKC; ++kk) {
+      const int k = ch * kKC + kk;
+      if (k < K) {
+        const float ak = __ldg(acoef + k);
+        const CT* zw = zb + kk * kDnCH * kDnCW + tr * kDnCW + 2 * tc;
+        float2 wv[3][4];
+#pragma unroll
+        for (int r = 0; r < 3; ++r) {
+          if constexpr (sizeof(CT) == 8) {
+            // 16-byte aligned: (tr*36 + 2*tc) complex of 8 bytes
+            const float4 qa = *reinterpret_cast<const float4*>(zw + r * kDnCW);
+            const float4 qb = *reinterpret_cast<const float4*>(zw + r * kDnCW + 2);
+            wv[r][0] = make_float2(qa.x, qa.y); wv[r][1] = make_float2(qa.z, qa.w);
+            wv[r][2] = make_float2(qb.x, qb.y); wv[r][3] = make_float2(qb.z, qb.w);
+          } else {
+            // 8-byte aligned: two pairs of 4-byte complex samples
+            const uint2 qa = *reinterpret_cast<const uint2*>(zw + r * kDnCW);
+            const uint2 qb = *reinterpret_cast<const uint2*>(zw + r * kDnCW + 2);
+            wv[r][0] = Cplx<S>::cvt(*reinterpret_cast<const CT*>(&qa.x));
+            wv[r][1] = Cplx<S>::cvt(*reinterpret_cast<const CT*>(&qa.y));
+            wv[r][2] = Cplx<S>::cvt(*reinterpret_cast<const CT*>(&qb.x));
+            wv[r][3] = Cplx<S>::cvt(*reinterpret_cast<const CT*>(&qb.y));
+          }
+        }
+        float2 ve[4], vo[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          ve[q] = fma2(splat(6.f), wv[1][q], add2(wv[0][q], wv[2][q]));
+          vo[q] = add2(wv[1][q], wv[2][q]);
+        }
+        float2 ue[4], uo[4];
+        ue[0] = fma2(splat(6.f), ve[1], add2(ve[0], ve[2]));
+        ue[1] = add2(ve[1], ve[2]);
+        ue[2] = fma2(splat(6.f), ve[2], add2(ve[1], ve[3]));
+        ue[3] = add2(ve[2], ve[3]);
+        uo[0] = fma2(splat(6.f), vo[1], add2(vo[0], vo[2]));
+        uo[1] = add2(vo[1], vo[2]);
+        uo[2] = fma2(splat(6.f), vo[2], add2(vo[1], vo[3]));
+        uo[3] = add2(vo[2], vo[3]);
+        const float2 ce0 = mul2(splat(-ak), expand_scale_pair(0));
+        const float2 ce1 = mul2(splat(-ak), expand_scale_pair(1));
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          // cos(k w g) up(S~) - sin(k w g) up(C~) for the two fine rows
+          const float2 tq = make_float2(fmaf(cc[q].x, ue[q].y, ns[q].x * ue[q].x),
+                                        fmaf(cc[q].y, uo[q].y, ns[q].y * uo[q].x));
+          acc[q] = fma2((q & 1) ? ce1 : ce0, tq, acc[q]);
+        }
+        if constexpr (!LEVEL0) {
+          const CT* Zk = reinterpret_cast<const CT*>(fine->Z) + (long long)pl * fine->zplane +
+                         (long long)k * fine->zk;
+          const CT* r0 = Zk + (long long)y0c * fine->pitch;
+          const CT* r1 = Zk + (long long)y1c * fine->pitch;
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const float2 z0 = Cplx<S>::cvt(r0[xq[q]]), z1 = Cplx<S>::cvt(r1[xq[q]]);
+            const float2 tq = make_float2(fmaf(cc[q].x, z0.y, ns[q].x * z0.x),
+                                          fmaf(cc[q].y, z1.y, ns[q].y * z1.x));
+            acc[q] = fma2(splat(ak), tq, acc[q]);
+          }
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const float2 cn = fma2(cc[q], c1[q], mul2(ns[q], s1[q]));
+          const float2 nn = fma2(ns[q], c1[q], mul2(cc[q], ns1[q]));
+          cc[q] = cn;
+          ns[q] = nn;
+        }
+      }
+    }
+    if (ch == nch - 1) {
+      float* dst;
+      long long dpitch;
+      if constexpr (LEVEL0) {
+        dst = O + (long long)pl * h * w;
+        dpitch = w;
+      } else {
+        dst = fine->E + (long long)pl * fine->gplane;
+        dpitch = fine->pitch;
+      }
+#pragma unroll
+      for (int rr = 0; rr < 2; ++rr) {
+        const int y = fy + rr;
+        if (y < h) {
+          float* d = dst + (long long)y * dpitch;
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const int x = fx + q;
+            if (x >= 0 && x < w) d[x] = rr ? acc[q].y : acc[q].x;
+          }
+        }
+      }
+    }
+    __syncthreads();
+  }
 }
 
 template <typename S>
-__global__ void __launch_bounds__(kThreads) k_up(const UpArgs a) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  up_tile<S>(a, blockIdx.x, blockIdx.y, blockIdx.z, smem);
+__global__ void __launch_bounds__(kThreads) k_down(const __grid_constant__ DownArgs a) {
+  combine_body<S, false>(&a.zmap, &a.emap, &a.fine, nullptr, nullptr, a.fine.h, a.fine.w, a.planes,
+                         a.coarse, a.a, a.K, a.turns, a.has_e, a.fault);
 }
 
 template <typename S>
-__global__ void __launch_bounds__(kThreads) k_down(const DownArgs a) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  down_tile<S>(a, blockIdx.x, blockIdx.y, blockIdx.z, smem);
+__global__ void __launch_bounds__(kThreads, 3) k_down0(const __grid_constant__ Down0Args a) {
+  combine_body<S, true>(&a.zmap, &a.emap, nullptr, a.I, a.O, a.h0, a.w0, a.planes, a.coarse, a.a,
+                        a.K, a.turns, a.has_e, a.fault);
 }
 
-template <typename S>
-__global__ void __launch_bounds__(kThreads) k_down0(const Down0Args a) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  down0_tile<S>(a, blockIdx.x, blockIdx.y, blockIdx.z, smem);
+// Persistent grid: at most (resident CTAs per SM) x (SMs) CTAs.
+template <typename Kern>
+int persistent_grid(Kern kern, size_t smem, int tiles) {
+  static int cached = 0;
+  if (cached == 0) {
+    int dev = 0, sms = 0, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, kThreads, smem);
+    cached = (per > 0 ? per : 1) * (sms > 0 ? sms : 1);
+  }
+  return tiles < cached ? tiles : cached;
 }
 
-static inline unsigned cdiv(int a, int b) { return (unsigned)((a + b - 1) / b); }
+}  // namespace
 
-cudaError_t FLLF_LAUNCH_NAME(up0)(const Up0Args& a, int planes, cudaStream_t s) {
-  dim3 grid(cdiv(a.dst.w, kUpTW), cdiv(a.dst.h, kUpTH), planes);
-  k_up0<FLLF_STORAGE><<<grid, kThreads, kUpSmemBytes, s>>>(a);
+using CTS = typename Cplx<FLLF_STORAGE>::T;
+using SMS = Smem<sizeof(CTS)>;
+
+cudaError_t FLLF_LAUNCH_NAME(up0)(const Up0Args& a, cudaStream_t s) {
+  const int tiles = cdiv(a.dst.w, kUpTW) * cdiv(a.dst.h, kUpTH) * a.planes;
+  const int grid = persistent_grid(k_up0<FLLF_STORAGE>, SMS::up0, tiles);
+  k_up0<FLLF_STORAGE><<<grid, kThreads, SMS::up0, s>>>(a);
   return cudaGetLastError();
 }
 
-cudaError_t FLLF_LAUNCH_NAME(up)(const UpArgs& a, int planes, cudaStream_t s) {
-  dim3 grid(cdiv(a.dst.w, kUpTW), cdiv(a.dst.h, kUpTH), planes);
-  k_up<FLLF_STORAGE><<<grid, kThreads, kUpSmemBytes, s>>>(a);
+cudaError_t FLLF_LAUNCH_NAME(up)(const UpArgs& a, cudaStream_t s) {
+  const int items = cdiv(a.dst.w, kRsTW) * cdiv(a.dst.h, kRsTH) * a.planes * cdiv(a.K, SMS::up_kc);
+  const int grid = persistent_grid(k_up<FLLF_STORAGE>, SMS::up, items);
+  k_up<FLLF_STORAGE><<<grid, kThreads, SMS::up, s>>>(a);
   return cudaGetLastError();
 }
 
-cudaError_t FLLF_LAUNCH_NAME(down)(const DownArgs& a, int planes, cudaStream_t s) {
-  dim3 grid(cdiv(a.fine.w, kDnOW), cdiv(a.fine.h, kDnOH), planes);
-  k_down<FLLF_STORAGE><<<grid, kThreads, kDnSmemBytes, s>>>(a);
+cudaError_t FLLF_LAUNCH_NAME(down)(const DownArgs& a, cudaStream_t s) {
+  const int tiles = cdiv(a.fine.w + kDnX0, kDnOW) * cdiv(a.fine.h, kDnOH) * a.planes;
+  const int grid = persistent_grid(k_down<FLLF_STORAGE>, SMS::dn, tiles);
+  k_down<FLLF_STORAGE><<<grid, kThreads, SMS::dn, s>>>(a);
   return cudaGetLastError();
 }
 
-cudaError_t FLLF_LAUNCH_NAME(down0)(const Down0Args& a, int planes, cudaStream_t s) {
-  dim3 grid(cdiv(a.w0, kDnOW), cdiv(a.h0, kDnOH), planes);
-  k_down0<FLLF_STORAGE><<<grid, kThreads, kDnSmemBytes, s>>>(a);
+cudaError_t FLLF_LAUNCH_NAME(down0)(const Down0Args& a, cudaStream_t s) {
+  const int tiles = cdiv(a.w0 + kDnX0, kDnOW) * cdiv(a.h0, kDnOH) * a.planes;
+  const int grid = persistent_grid(k_down0<FLLF_STORAGE>, SMS::dn, tiles);
+  k_down0<FLLF_STORAGE><<<grid, kThreads, SMS::dn, s>>>(a);
   return cudaGetLastError();
 }
 

@@ -8,11 +8,11 @@
 namespace fllf {
 
 // One set of launchers per storage precision of the Fourier pyramids.
-#define FLLF_DECLARE_LAUNCHERS(suffix)                                                       \
-  cudaError_t launch_up0_##suffix(const Up0Args& a, int planes, cudaStream_t s);            \
-  cudaError_t launch_up_##suffix(const UpArgs& a, int planes, cudaStream_t s);              \
-  cudaError_t launch_down_##suffix(const DownArgs& a, int planes, cudaStream_t s);          \
-  cudaError_t launch_down0_##suffix(const Down0Args& a, int planes, cudaStream_t s);
+#define FLLF_DECLARE_LAUNCHERS(suffix)                                    \
+  cudaError_t launch_up0_##suffix(const Up0Args& a, cudaStream_t s);     \
+  cudaError_t launch_up_##suffix(const UpArgs& a, cudaStream_t s);       \
+  cudaError_t launch_down_##suffix(const DownArgs& a, cudaStream_t s);   \
+  cudaError_t launch_down0_##suffix(const Down0Args& a, cudaStream_t s);
 FLLF_DECLARE_LAUNCHERS(f32)
 FLLF_DECLARE_LAUNCHERS(f16)
 FLLF_DECLARE_LAUNCHERS(bf16)

@@ -38,7 +38,7 @@ constexpr int kMaxDevices = 64;
 std::mutex g_noalloc_mu;
 unsigned char* g_noalloc_ptr[kMaxDevices] = {};
 
-constexpr size_t kCoeffBytes = 256;  // a_1..a_64 as float32, ahead of the pyramids
+constexpr size_t kHeadBytes = 512;  // a_1..a_64 (float32) at 0, fault word at 256, then the pyramids
 
 fllf_status noalloc_fail(fllf_status s, const std::string& why) {
   fllf::set_last_error(why);
@@ -58,9 +58,9 @@ extern "C" fllf_status fllf_run_noalloc(const fllf_params* p, const float* d_in,
 
   std::vector<fllf::Level> lv;
   const size_t need = fllf::layout(*p, &lv);
-  if (need + kCoeffBytes > (size_t)FLLF_NOALLOC_SCRATCH_BYTES)
+  if (need + kHeadBytes > (size_t)FLLF_NOALLOC_SCRATCH_BYTES)
     return noalloc_fail(FLLF_EINVAL,
-                        "fllf_run_noalloc: this image needs " + std::to_string(need + kCoeffBytes) +
+                        "fllf_run_noalloc: this image needs " + std::to_string(need + kHeadBytes) +
                             " bytes of scratch, above the fixed " +
                             std::to_string((size_t)FLLF_NOALLOC_SCRATCH_BYTES) + "-byte array");
 
@@ -96,7 +96,8 @@ extern "C" fllf_status fllf_run_noalloc(const fllf_params* p, const float* d_in,
   if (e != cudaSuccess)
     return noalloc_fail(FLLF_ECUDA, std::string("coefficient upload: ") + cudaGetErrorString(e));
 
-  unsigned char* pyr = base + kCoeffBytes;
+  unsigned char* pyr = base + kHeadBytes;
+  unsigned* fault = reinterpret_cast<unsigned*>(base + 256);
   const int L = p->levels;
   for (int l = 0; l < L; ++l) {
     fllf::Level& v = lv[l];
@@ -110,10 +111,13 @@ extern "C" fllf_status fllf_run_noalloc(const fllf_params* p, const float* d_in,
     v.Z = pyr + reinterpret_cast<size_t>(v.Z);
     v.E = (l <= L - 2) ? reinterpret_cast<float*>(pyr + reinterpret_cast<size_t>(v.E)) : nullptr;
   }
-  if (!fllf::check_layout(*p, lv, pyr, (size_t)FLLF_NOALLOC_SCRATCH_BYTES - kCoeffBytes))
+  if (!fllf::check_layout(*p, lv, pyr, (size_t)FLLF_NOALLOC_SCRATCH_BYTES - kHeadBytes))
     return noalloc_fail(FLLF_EINVAL, "internal error: scratch layout outside the fixed array");
+  fllf::PathMaps maps;
+  if (L > 1 && !fllf::build_maps(*p, lv, &maps))
+    return noalloc_fail(FLLF_ECUDA, "TMA tensor map encoding failed (cuTensorMapEncodeTiled)");
 
-  e = fllf::enqueue_path(*p, lv, d_a, d_in, d_out, s);
+  e = fllf::enqueue_path(*p, lv, maps, d_a, fault, d_in, d_out, s);
   if (e != cudaSuccess) return noalloc_fail(FLLF_ECUDA, std::string("kernel launch: ") + cudaGetErrorString(e));
   return FLLF_OK;
 }

@@ -1,0 +1,198 @@
+// fllf_path.cu -- host side of the path: TMA tensor maps of the pyramid
+// levels and the launch sequence of one image (up pass, then down pass).
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_runtime.h>
+
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "fllf.h"
+#include "fllf_internal.h"
+#include "fllf_launch.h"
+
+namespace fllf {
+
+namespace {
+
+PFN_cuTensorMapEncodeTiled_v12000 encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  });
+  return fn;
+}
+
+// 3-D tiled map (x = column, y = row, z = plane) with zero fill outside.
+bool encode3(CUtensorMap* m, CUtensorMapDataType dt, size_t esize, const void* base, uint64_t w,
+             uint64_t h, uint64_t planes, uint64_t row_bytes, uint64_t plane_bytes, uint32_t bx,
+             uint32_t by, uint32_t bz) {
+  auto enc = encoder();
+  if (!enc) return false;
+  cuuint64_t dims[3] = {w, h, planes};
+  cuuint64_t strides[2] = {row_bytes, plane_bytes};
+  cuuint32_t box[3] = {bx, by, bz};
+  cuuint32_t estr[3] = {1, 1, 1};
+  (void)esize;
+  return enc(m, dt, 3, const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+             CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+cudaError_t launch_up0(int prec, const Up0Args& a, cudaStream_t s) {
+  switch (prec) {
+    case FLLF_FP16: return launch_up0_f16(a, s);
+    case FLLF_BF16: return launch_up0_bf16(a, s);
+    default: return launch_up0_f32(a, s);
+  }
+}
+cudaError_t launch_up(int prec, const UpArgs& a, cudaStream_t s) {
+  switch (prec) {
+    case FLLF_FP16: return launch_up_f16(a, s);
+    case FLLF_BF16: return launch_up_bf16(a, s);
+    default: return launch_up_f32(a, s);
+  }
+}
+cudaError_t launch_down(int prec, const DownArgs& a, cudaStream_t s) {
+  switch (prec) {
+    case FLLF_FP16: return launch_down_f16(a, s);
+    case FLLF_BF16: return launch_down_bf16(a, s);
+    default: return launch_down_f32(a, s);
+  }
+}
+cudaError_t launch_down0(int prec, const Down0Args& a, cudaStream_t s) {
+  switch (prec) {
+    case FLLF_FP16: return launch_down0_f16(a, s);
+    case FLLF_BF16: return launch_down0_bf16(a, s);
+    default: return launch_down0_f32(a, s);
+  }
+}
+
+}  // namespace
+
+bool build_maps(const fllf_params& p, const std::vector<Level>& lv, PathMaps* m) {
+  const int L = p.levels;
+  m->z_dn.assign(L, CUtensorMap{});
+  m->e_dn.assign(L, CUtensorMap{});
+  m->z_up.assign(L, CUtensorMap{});
+  m->g_up.assign(L, CUtensorMap{});
+  const bool f32 = p.precision == FLLF_FP32;
+  const size_t zs = f32 ? 8 : 4;
+  const CUtensorMapDataType zdt = f32 ? CU_TENSOR_MAP_DATA_TYPE_INT64 : CU_TENSOR_MAP_DATA_TYPE_UINT32;
+  const uint32_t up_kc = f32 ? 1 : 2;
+  for (int l = 1; l < L; ++l) {
+    const Level& v = lv[l];
+    const uint64_t zrow = zs * v.pitch, zplane = zs * (uint64_t)v.zk;
+    const uint64_t grow = 4ull * v.pitch, gplane = 4ull * (uint64_t)v.gplane;
+    const uint64_t zplanes = (uint64_t)p.K * p.C;
+    // as the coarse level of a combine: 36 x 18 window, kKC orders
+    if (!encode3(&m->z_dn[l], zdt, zs, v.Z, v.w, v.h, zplanes, zrow, zplane, kDnCW, kDnCH, kKC))
+      return false;
+    // as the source of a REDUCE: 68 x 35 box, up_kc orders; plus the guide
+    if (l <= L - 2) {
+      if (!encode3(&m->z_up[l], zdt, zs, v.Z, v.w, v.h, zplanes, zrow, zplane, kRsBW, kRsIR, up_kc))
+        return false;
+      if (!encode3(&m->g_up[l], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, v.G, v.w, v.h, p.C, grow, gplane,
+                   kRsBW, kRsIR, 1))
+        return false;
+    }
+    if (v.E) {
+      if (!encode3(&m->e_dn[l], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, v.E, v.w, v.h, p.C, grow, gplane,
+                   kDnCW, kDnCH, 1))
+        return false;
+    }
+  }
+  return true;
+}
+
+cudaError_t enqueue_path(const fllf_params& p, const std::vector<Level>& lv, const PathMaps& maps,
+                         const float* d_a, unsigned* fault, const float* d_in, float* d_out,
+                         cudaStream_t s, StageHook* hook) {
+  const int L = p.levels, C = p.C, prec = p.precision;
+  const float turns = (float)(2.0 / p.T);
+  if (L == 1) {
+    // Only the top level: L_0[O] = G_0[I] = I.
+    return cudaMemcpyAsync(d_out, d_in, sizeof(float) * (size_t)p.H * p.W * C,
+                           cudaMemcpyDeviceToDevice, s);
+  }
+  auto mark = [&](int st, bool b) {
+    if (hook) hook->mark(st, b, s);
+  };
+  cudaError_t e;
+
+  Up0Args u0{};
+  u0.I = d_in;
+  u0.h0 = p.H;
+  u0.w0 = p.W;
+  u0.planes = C;
+  u0.dst = lv[1];
+  u0.K = p.K;
+  u0.turns = turns;
+  u0.fault = fault;
+  u0.use_tma = ((p.W % 4) == 0 && (reinterpret_cast<uintptr_t>(d_in) & 15) == 0 &&
+                encode3(&u0.imap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, d_in, p.W, p.H, C,
+                        4ull * p.W, 4ull * p.W * p.H, kUpIW, kUpIR, 1))
+                   ? 1
+                   : 0;
+  mark(FLLF_STAGE_UP0, true);
+  if ((e = launch_up0(prec, u0, s)) != cudaSuccess) return e;
+  mark(FLLF_STAGE_UP0, false);
+
+  for (int l = 1; l <= L - 2; ++l) {
+    UpArgs u{};
+    u.zmap = maps.z_up[l];
+    u.gmap = maps.g_up[l];
+    u.src = lv[l];
+    u.dst = lv[l + 1];
+    u.planes = C;
+    u.K = p.K;
+    u.write_g = (l + 1 <= L - 2) ? 1 : 0;
+    u.fault = fault;
+    mark(FLLF_STAGE_UP, true);
+    if ((e = launch_up(prec, u, s)) != cudaSuccess) return e;
+    mark(FLLF_STAGE_UP, false);
+  }
+  for (int l = L - 2; l >= 1; --l) {
+    DownArgs d{};
+    d.zmap = maps.z_dn[l + 1];
+    d.emap = maps.e_dn[l + 1];
+    d.fine = lv[l];
+    d.coarse = lv[l + 1];
+    d.a = d_a;
+    d.planes = C;
+    d.K = p.K;
+    d.turns = turns;
+    d.has_e = (l + 1 <= L - 2) ? 1 : 0;
+    d.fault = fault;
+    mark(FLLF_STAGE_DOWN, true);
+    if ((e = launch_down(prec, d, s)) != cudaSuccess) return e;
+    mark(FLLF_STAGE_DOWN, false);
+  }
+  Down0Args d0{};
+  d0.zmap = maps.z_dn[1];
+  d0.emap = maps.e_dn[1];
+  d0.I = d_in;
+  d0.O = d_out;
+  d0.h0 = p.H;
+  d0.w0 = p.W;
+  d0.planes = C;
+  d0.coarse = lv[1];
+  d0.a = d_a;
+  d0.K = p.K;
+  d0.turns = turns;
+  d0.has_e = (L >= 3) ? 1 : 0;
+  d0.fault = fault;
+  mark(FLLF_STAGE_DOWN0, true);
+  if ((e = launch_down0(prec, d0, s)) != cudaSuccess) return e;
+  mark(FLLF_STAGE_DOWN0, false);
+  return cudaSuccess;
+}
+
+}  // namespace fllf

@@ -57,7 +57,7 @@ def test_matches_fllf_run_on_two_calls_in_a_row():
          pkg.make_params(97, 131, 1, 5, 5, 0.6, 0.3, 2.0, "fp16")),
     ]
     for img, p in cases:
-        assert pkg.fllf_plan_scratch_bytes(p) + 256 <= pkg.NOALLOC_SCRATCH_BYTES
+        assert pkg.fllf_plan_scratch_bytes(p) + 512 <= pkg.NOALLOC_SCRATCH_BYTES
     refs = [_with_plan(img, p) for img, p in cases]
     outs = [_no_alloc(img, p) for img, p in cases]     # two calls in a row
     for out, ref in zip(outs, refs):
