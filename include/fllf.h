@@ -170,7 +170,8 @@ enum {
   FLLF_STAGE_UP = 1,    /* level l -> l+1 REDUCE of G_l and Z_l (Eq. (1)) */
   FLLF_STAGE_DOWN = 2,  /* level l >= 1: Eq. (14) product-sum fused with the collapse */
   FLLF_STAGE_DOWN0 = 3, /* level 0: Eq. (14) l = 0 case + final collapse, writes O */
-  FLLF_NSTAGE = 4
+  FLLF_STAGE_CHAIN = 4, /* the small levels (REDUCE up, then combines down) in one launch */
+  FLLF_NSTAGE = 5
 };
 
 /* When enabled, every run of the plan records CUDA events around each

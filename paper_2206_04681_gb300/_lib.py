@@ -54,7 +54,7 @@ _SIGS = {
                                              ctypes.POINTER(ctypes.c_int)]),
 }
 
-STAGES = ("up0", "up", "down", "down0")
+STAGES = ("up0", "up", "down", "down0", "chain")
 
 _lib = None
 

@@ -235,7 +235,7 @@ static fllf_status check_fault(fllf_plan* plan) {
   cudaError_t e = cudaMemcpy(&f, plan->d_fault, sizeof(unsigned), cudaMemcpyDeviceToHost);
   if (e != cudaSuccess) return cuda_fail(e, "fault word read");
   if (f) {
-    cudaMemset(plan->d_fault, 0, sizeof(unsigned));
+    cudaMemset(plan->d_fault, 0, 256);  // fault word and the grid-barrier words
     return fail(FLLF_ETIMEOUT, "a kernel's bounded wait for a shared-memory copy ran out");
   }
   return FLLF_OK;

@@ -115,6 +115,17 @@ struct Down0Args {
   unsigned* fault;
 };
 
+// Chained small levels: REDUCE stages then combine stages in one cooperative
+// launch, with a grid barrier between consecutive stages.
+constexpr int kChainMax = 12;
+struct ChainArgs {
+  UpArgs up[kChainMax];     // REDUCE stages, finest first
+  DownArgs dn[kChainMax];   // combine stages, coarsest first
+  int n_up, n_dn;
+  unsigned* sync;           // grid barrier: [0] arrivals, [1] generation (zeroed by the plan)
+  unsigned* fault;
+};
+
 // ---- tiling constants ---------------------------------------------------------------
 constexpr int kKC = 4;                    // complex orders per combine / up0 chunk
 
@@ -278,35 +289,33 @@ __device__ __forceinline__ bool mbar_wait_cta(uint64_t* b, uint32_t parity, unsi
 // Rewrites the out-of-range cells of a staged box (planes x bh x bw elements
 // of type E, box origin (x0, y0), valid extent w x h) from their sources
 // under `map` (reflect-101 or the EXPAND extension): rows first, then
-// columns, so that corners take both mappings.  Cells whose source lies
-// outside the box keep TMA's zero fill (they feed no stored output).
+// columns, so that corners take both mappings.  Only the out-of-range rows
+// and columns are visited.  Cells whose source lies outside the box keep
+// TMA's zero fill (they feed no stored output).
 template <typename E, typename MapY, typename MapX>
 __device__ __forceinline__ void fix_borders(E* buf, int planes, int bh, int bw, int x0, int y0,
                                             int w, int h, MapY mapy, MapX mapx) {
-  const int n = planes * bh * bw;
-  const bool rows = y0 < 0 || y0 + bh > h;
-  const bool cols = x0 < 0 || x0 + bw > w;
-  if (rows) {
+  const int top = min(max(-y0, 0), bh), bot = min(max(y0 + bh - h, 0), bh - top);
+  const int lft = min(max(-x0, 0), bw), rgt = min(max(x0 + bw - w, 0), bw - lft);
+  if (top + bot > 0) {
+    const int nr = top + bot, n = planes * nr * bw;
     for (int idx = threadIdx.x; idx < n; idx += kThreads) {
-      const int pl = idx / (bh * bw), rem = idx - pl * bh * bw;
-      const int r = rem / bw, c = rem - r * bw;
-      const int y = y0 + r;
-      if (y < 0 || y >= h) {
-        const int sr = mapy(y) - y0;
-        if (sr >= 0 && sr < bh) buf[(pl * bh + r) * bw + c] = buf[(pl * bh + sr) * bw + c];
-      }
+      const int pl = idx / (nr * bw), rem = idx - pl * nr * bw;
+      const int ri = rem / bw, c = rem - ri * bw;
+      const int r = ri < top ? ri : bh - bot + (ri - top);
+      const int sr = mapy(y0 + r) - y0;
+      if (sr >= 0 && sr < bh) buf[(pl * bh + r) * bw + c] = buf[(pl * bh + sr) * bw + c];
     }
     __syncthreads();
   }
-  if (cols) {
+  if (lft + rgt > 0) {
+    const int nc = lft + rgt, n = planes * bh * nc;
     for (int idx = threadIdx.x; idx < n; idx += kThreads) {
-      const int pl = idx / (bh * bw), rem = idx - pl * bh * bw;
-      const int r = rem / bw, c = rem - r * bw;
-      const int x = x0 + c;
-      if (x < 0 || x >= w) {
-        const int sc = mapx(x) - x0;
-        if (sc >= 0 && sc < bw) buf[(pl * bh + r) * bw + c] = buf[(pl * bh + r) * bw + sc];
-      }
+      const int pl = idx / (bh * nc), rem = idx - pl * bh * nc;
+      const int r = rem / nc, ci = rem - r * nc;
+      const int c = ci < lft ? ci : bw - rgt + (ci - lft);
+      const int sc = mapx(x0 + c) - x0;
+      if (sc >= 0 && sc < bw) buf[(pl * bh + r) * bw + c] = buf[(pl * bh + r) * bw + sc];
     }
     __syncthreads();
   }

@@ -17,6 +17,13 @@ __device__ __forceinline__ void drain(uint64_t* b, uint32_t parity) {
   }
 }
 
+// Completed uses of the two TMA buffers of a CTA (identical in every thread);
+// the parity of a buffer's next phase is use[buf] & 1.  Carried across the
+// stages of the chained kernel.
+struct Pipe {
+  uint32_t use[2];
+};
+
 // ---------------------------------------------------------------------------------------
 // up0: level 0 -> 1.  Item (row r, segment s) holds 11 fine pixels of one
 // staged input row; it evaluates e^{i k w_1 x} for k = 1..K with the
@@ -171,8 +178,9 @@ __global__ void __launch_bounds__(kThreads) k_up0(const __grid_constant__ Up0Arg
 // box of each order of the chunk (plus G_l with chunk 0); the vertical pass
 // reads one staged column per thread and keeps the reduced rows in
 // registers; the horizontal pass reads 5 staged columns per output.
-template <typename S>
-__global__ void __launch_bounds__(kThreads) k_up(const __grid_constant__ UpArgs a) {
+template <typename S, bool COH>
+__device__ __forceinline__ bool stage_up(const UpArgs& a, unsigned char* smem, uint64_t* bar, Pipe& pp,
+                                         int b, int G) {
   using CT = typename Cplx<S>::T;
   using SM = Smem<sizeof(CT)>;
   constexpr int KCU = SM::up_kc;
@@ -182,11 +190,9 @@ __global__ void __launch_bounds__(kThreads) k_up(const __grid_constant__ UpArgs 
   constexpr int HOUT = kRsTH / HQ;
   static_assert(RG * KCU * kRsVW == kThreads, "vertical mapping");
   static_assert(kRsTH % HQ == 0, "horizontal mapping");
-  extern __shared__ __align__(128) unsigned char smem[];
   unsigned char* bufs[2] = {smem, smem + SM::up_buf};
   float2* vb = reinterpret_cast<float2*>(smem + 2 * SM::up_buf);
   float* vg = reinterpret_cast<float*>(smem + 2 * SM::up_buf + SM::up_vb);
-  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + 2 * SM::up_buf + SM::up_vb + SM::up_vg);
   const int tid = threadIdx.x;
   const int ntx = cdiv(a.dst.w, kRsTW), nty = cdiv(a.dst.h, kRsTH);
   const int ntiles = ntx * nty * a.planes;
@@ -194,16 +200,9 @@ __global__ void __launch_bounds__(kThreads) k_up(const __grid_constant__ UpArgs 
   // Work items are (tile, chunk of orders) pairs: orders reduce independently,
   // so small levels still spread over many CTAs.
   const int total = ntiles * nch;
-  if ((int)blockIdx.x >= total) return;
-  const int nitems = (total - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x;
-  if (tid == 0) {
-    mbar_init(&bar[0], 1);
-    mbar_init(&bar[1], 1);
-    fence_mbar_init();
-  }
-  __syncthreads();
+  const int nitems = b < total ? (total - b + G - 1) / G : 0;
   auto issue = [&](int i, int buf) {
-    const int gi = (int)blockIdx.x + i * (int)gridDim.x, t = gi / nch, ch = gi % nch;
+    const int gi = b + i * G, t = gi / nch, ch = gi % nch;
     const int tx = t % ntx, r = t / ntx, ty = r % nty, pl = r / nty;
     const int x = 2 * tx * kRsTW - 4, y = 2 * ty * kRsTH - 2;
     const bool g = ch == 0 && a.write_g;
@@ -212,10 +211,13 @@ __global__ void __launch_bounds__(kThreads) k_up(const __grid_constant__ UpArgs 
     tma_load3(bufs[buf], &a.zmap, x, y, pl * a.K + ch * KCU, &bar[buf]);
     if (g) tma_load3(bufs[buf] + SM::up_src, &a.gmap, x, y, pl, &bar[buf]);
   };
-  if (tid == 0) issue(0, 0);
+  if (tid == 0 && nitems > 0) {
+    fence_proxy_async();
+    issue(0, 0);
+  }
   for (int i = 0; i < nitems; ++i) {
     const int buf = i & 1;
-    const int gi = (int)blockIdx.x + i * (int)gridDim.x, t = gi / nch, ch = gi % nch;
+    const int gi = b + i * G, t = gi / nch, ch = gi % nch;
     const int tx = t % ntx, rt = t / ntx, ty = rt % nty, pl = rt / nty;
     const int X1 = tx * kRsTW, Y1 = ty * kRsTH;
     const int xs = 2 * X1 - 4, ys = 2 * Y1 - 2;
@@ -224,10 +226,11 @@ __global__ void __launch_bounds__(kThreads) k_up(const __grid_constant__ UpArgs 
       fence_proxy_async();
       issue(i + 1, buf ^ 1);
     }
-    if (!mbar_wait_cta(&bar[buf], (i >> 1) & 1, a.fault)) {
-      if (tid == 0 && i + 1 < nitems) drain(&bar[buf ^ 1], ((i + 1) >> 1) & 1);
-      return;
+    if (!mbar_wait_cta(&bar[buf], pp.use[buf] & 1, a.fault)) {
+      if (tid == 0 && i + 1 < nitems) drain(&bar[buf ^ 1], pp.use[buf ^ 1] & 1);
+      return false;
     }
+    ++pp.use[buf];
     CT* src = reinterpret_cast<CT*>(bufs[buf]);
     float* gsrc = reinterpret_cast<float*>(bufs[buf] + SM::up_src);
     auto my = [&](int y) { return refl101(y, a.src.h); };
@@ -296,7 +299,24 @@ __global__ void __launch_bounds__(kThreads) k_up(const __grid_constant__ UpArgs 
     }
     __syncthreads();
   }
+  return true;
 }
+
+template <typename S>
+__global__ void __launch_bounds__(kThreads) k_up(const __grid_constant__ UpArgs a) {
+  using SM = Smem<sizeof(typename Cplx<S>::T)>;
+  extern __shared__ __align__(128) unsigned char smem[];
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + SM::up - 64);
+  if (threadIdx.x == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  Pipe pp{{0u, 0u}};
+  stage_up<S, false>(a, smem, bar, pp, blockIdx.x, gridDim.x);
+}
+
 
 // ---------------------------------------------------------------------------------------
 // Combine (Eq. (14) product-sum fused with the residual collapse).
@@ -312,32 +332,24 @@ __device__ __forceinline__ float2 expand_scale_pair(int q) {
   return (q & 1) ? make_float2(1.f / 16.f, 1.f / 4.f) : make_float2(1.f / 64.f, 1.f / 16.f);
 }
 
-template <typename S, bool LEVEL0>
-__device__ __forceinline__ void combine_body(const CUtensorMap* zmap, const CUtensorMap* emap,
-                                             const Level* fine, const float* I, float* O, int h,
-                                             int w, int planes, const Level& coarse,
-                                             const float* acoef, int K, float turns, int has_e,
-                                             unsigned* fault) {
+template <typename S, bool LEVEL0, bool COH>
+__device__ __forceinline__ bool stage_combine(const CUtensorMap* zmap, const CUtensorMap* emap,
+                                              const Level* fine, const float* I, float* O, int h,
+                                              int w, int planes, const Level& coarse,
+                                              const float* acoef, int K, float turns, int has_e,
+                                              unsigned* fault, unsigned char* smem, uint64_t* bar,
+                                              Pipe& pp, int b, int G) {
   using CT = typename Cplx<S>::T;
   using SM = Smem<sizeof(CT)>;
-  extern __shared__ __align__(128) unsigned char smem[];
   unsigned char* bufs[2] = {smem, smem + SM::dn_buf};
-  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + 2 * SM::dn_buf);
   const int tid = threadIdx.x;
   const int ntx = cdiv(w + kDnX0, kDnOW), nty = cdiv(h, kDnOH);
   const int ntiles = ntx * nty * planes;
   const int nch = cdiv(K, kKC);
-  if ((int)blockIdx.x >= ntiles) return;
-  const int nmine = (ntiles - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x;
+  const int nmine = b < ntiles ? (ntiles - b + G - 1) / G : 0;
   const int nitems = nmine * nch;
-  if (tid == 0) {
-    mbar_init(&bar[0], 1);
-    mbar_init(&bar[1], 1);
-    fence_mbar_init();
-  }
-  __syncthreads();
   auto issue = [&](int i, int buf) {
-    const int t = (int)blockIdx.x + (i / nch) * (int)gridDim.x, ch = i % nch;
+    const int t = b + (i / nch) * G, ch = i % nch;
     const int tx = t % ntx, r = t / ntx, ty = r % nty, pl = r / nty;
     const int cx0 = (tx * kDnOW - kDnX0) / 2 - 1, cy0 = ty * (kDnOH / 2) - 1;
     const bool e = ch == 0 && has_e;
@@ -346,14 +358,17 @@ __device__ __forceinline__ void combine_body(const CUtensorMap* zmap, const CUte
     tma_load3(bufs[buf], zmap, cx0, cy0, pl * K + ch * kKC, &bar[buf]);
     if (e) tma_load3(bufs[buf] + SM::dn_z, emap, cx0, cy0, pl, &bar[buf]);
   };
-  if (tid == 0) issue(0, 0);
+  if (tid == 0 && nitems > 0) {
+    fence_proxy_async();
+    issue(0, 0);
+  }
 
   const int tc = tid % (kDnOW / 4), tr = tid / (kDnOW / 4);
   float2 cc[4], ns[4], c1[4], s1[4], ns1[4], acc[4];
   int xq[4], y0c = 0, y1c = 0, fy = 0, fx = 0, pl = 0;
   for (int i = 0; i < nitems; ++i) {
     const int buf = i & 1;
-    const int t = (int)blockIdx.x + (i / nch) * (int)gridDim.x, ch = i % nch;
+    const int t = b + (i / nch) * G, ch = i % nch;
     const int tx = t % ntx, rt = t / ntx, ty = rt % nty;
     pl = rt / nty;
     const int X0 = tx * kDnOW - kDnX0, Y0 = ty * kDnOH;
@@ -373,8 +388,8 @@ __device__ __forceinline__ void combine_body(const CUtensorMap* zmap, const CUte
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
         xq[q] = min(max(fx + q, 0), w - 1);
-        const float g0 = __ldg(gsrc + y0c * gpitch + xq[q]);
-        const float g1 = __ldg(gsrc + y1c * gpitch + xq[q]);
+        const float g0 = COH ? __ldcg(gsrc + y0c * gpitch + xq[q]) : __ldg(gsrc + y0c * gpitch + xq[q]);
+        const float g1 = COH ? __ldcg(gsrc + y1c * gpitch + xq[q]) : __ldg(gsrc + y1c * gpitch + xq[q]);
         const float2 z0 = cos_sin_turns(turns * g0), z1 = cos_sin_turns(turns * g1);
         c1[q] = make_float2(z0.x, z1.x);
         s1[q] = make_float2(z0.y, z1.y);
@@ -384,10 +399,11 @@ __device__ __forceinline__ void combine_body(const CUtensorMap* zmap, const CUte
         acc[q] = LEVEL0 ? make_float2(g0, g1) : splat(0.f);
       }
     }
-    if (!mbar_wait_cta(&bar[buf], (i >> 1) & 1, fault)) {
-      if (tid == 0 && i + 1 < nitems) drain(&bar[buf ^ 1], ((i + 1) >> 1) & 1);
-      return;
+    if (!mbar_wait_cta(&bar[buf], pp.use[buf] & 1, fault)) {
+      if (tid == 0 && i + 1 < nitems) drain(&bar[buf ^ 1], pp.use[buf ^ 1] & 1);
+      return false;
     }
+    ++pp.use[buf];
     CT* zb = reinterpret_cast<CT*>(bufs[buf]);
     float* eb = reinterpret_cast<float*>(bufs[buf] + SM::dn_z);
     auto my = [&](int y) { return ext_coarse(y, coarse.h, h); };
@@ -471,7 +487,24 @@ __device__ __forceinline__ void combine_body(const CUtensorMap* zmap, const CUte
           const CT* r1 = Zk + (long long)y1c * fine->pitch;
 #pragma unroll
           for (int q = 0; q < 4; ++q) {
-            const float2 z0 = Cplx<S>::cvt(r0[xq[q]]), z1 = Cplx<S>::cvt(r1[xq[q]]);
+            CT zz0, zz1;
+            if constexpr (COH) {
+              if constexpr (sizeof(CT) == 8) {
+                const float2 f0 = __ldcg(reinterpret_cast<const float2*>(r0 + xq[q]));
+                const float2 f1 = __ldcg(reinterpret_cast<const float2*>(r1 + xq[q]));
+                zz0 = *reinterpret_cast<const CT*>(&f0);
+                zz1 = *reinterpret_cast<const CT*>(&f1);
+              } else {
+                const unsigned u0 = __ldcg(reinterpret_cast<const unsigned*>(r0 + xq[q]));
+                const unsigned u1 = __ldcg(reinterpret_cast<const unsigned*>(r1 + xq[q]));
+                zz0 = *reinterpret_cast<const CT*>(&u0);
+                zz1 = *reinterpret_cast<const CT*>(&u1);
+              }
+            } else {
+              zz0 = r0[xq[q]];
+              zz1 = r1[xq[q]];
+            }
+            const float2 z0 = Cplx<S>::cvt(zz0), z1 = Cplx<S>::cvt(zz1);
             const float2 tq = make_float2(fmaf(cc[q].x, z0.y, ns[q].x * z0.x),
                                           fmaf(cc[q].y, z1.y, ns[q].y * z1.x));
             acc[q] = fma2(splat(ak), tq, acc[q]);
@@ -511,18 +544,107 @@ __device__ __forceinline__ void combine_body(const CUtensorMap* zmap, const CUte
     }
     __syncthreads();
   }
+  return true;
 }
 
 template <typename S>
 __global__ void __launch_bounds__(kThreads) k_down(const __grid_constant__ DownArgs a) {
-  combine_body<S, false>(&a.zmap, &a.emap, &a.fine, nullptr, nullptr, a.fine.h, a.fine.w, a.planes,
-                         a.coarse, a.a, a.K, a.turns, a.has_e, a.fault);
+  using SM = Smem<sizeof(typename Cplx<S>::T)>;
+  extern __shared__ __align__(128) unsigned char smem[];
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + SM::dn - 64);
+  if (threadIdx.x == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  Pipe pp{{0u, 0u}};
+  stage_combine<S, false, false>(&a.zmap, &a.emap, &a.fine, nullptr, nullptr, a.fine.h, a.fine.w,
+                                 a.planes, a.coarse, a.a, a.K, a.turns, a.has_e, a.fault, smem, bar,
+                                 pp, blockIdx.x, gridDim.x);
 }
 
 template <typename S>
 __global__ void __launch_bounds__(kThreads, 3) k_down0(const __grid_constant__ Down0Args a) {
-  combine_body<S, true>(&a.zmap, &a.emap, nullptr, a.I, a.O, a.h0, a.w0, a.planes, a.coarse, a.a,
-                        a.K, a.turns, a.has_e, a.fault);
+  using SM = Smem<sizeof(typename Cplx<S>::T)>;
+  extern __shared__ __align__(128) unsigned char smem[];
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + SM::dn - 64);
+  if (threadIdx.x == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  Pipe pp{{0u, 0u}};
+  stage_combine<S, true, false>(&a.zmap, &a.emap, nullptr, a.I, a.O, a.h0, a.w0, a.planes,
+                                a.coarse, a.a, a.K, a.turns, a.has_e, a.fault, smem, bar, pp,
+                                blockIdx.x, gridDim.x);
+}
+
+// Grid-wide barrier of a cooperative launch (all CTAs resident), bounded:
+// arrival counter + generation word; every thread first orders its global
+// stores before later TMA (async proxy) reads of other CTAs.
+__device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ bool grid_barrier(unsigned* count, unsigned* gen, unsigned nblocks,
+                                             unsigned* fault) {
+  asm volatile("fence.proxy.async.global;" ::: "memory");
+  __syncthreads();
+  int ok = 1;
+  if (threadIdx.x == 0) {
+    __threadfence();
+    const unsigned g = ld_acquire(gen);
+    if (atomicAdd(count, 1u) + 1u == nblocks) {
+      atomicExch(count, 0u);
+      __threadfence();
+      atomicAdd(gen, 1u);
+    } else {
+      const long long t0 = clock64();
+      while (ld_acquire(gen) == g) {
+        __nanosleep(32);
+        if (clock64() - t0 > kWaitCycles) {
+          ok = 0;
+          atomicOr(fault, 2u);
+          break;
+        }
+      }
+    }
+    __threadfence();
+  }
+  return __syncthreads_or(!ok) == 0;
+}
+
+// All stages from level c0 down: REDUCE c0 -> ... -> top, then the combines
+// top-1 ... c0, in one cooperative launch with grid barriers between stages.
+template <typename S>
+__global__ void __launch_bounds__(kThreads) k_chain(const __grid_constant__ ChainArgs a) {
+  using SM = Smem<sizeof(typename Cplx<S>::T)>;
+  constexpr size_t kS = SM::up > SM::dn ? SM::up : SM::dn;
+  extern __shared__ __align__(128) unsigned char smem[];
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + kS - 64);
+  if (threadIdx.x == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  Pipe pp{{0u, 0u}};
+  const int b = blockIdx.x, G = gridDim.x;
+  for (int st = 0; st < a.n_up; ++st) {
+    if (!stage_up<S, true>(a.up[st], smem, bar, pp, b, G)) return;
+    if (!grid_barrier(a.sync, a.sync + 1, G, a.fault)) return;
+  }
+  for (int st = 0; st < a.n_dn; ++st) {
+    const DownArgs& d = a.dn[st];
+    if (!stage_combine<S, false, true>(&d.zmap, &d.emap, &d.fine, nullptr, nullptr, d.fine.h,
+                                       d.fine.w, d.planes, d.coarse, d.a, d.K, d.turns, d.has_e,
+                                       d.fault, smem, bar, pp, b, G))
+      return;
+    if (st + 1 < a.n_dn && !grid_barrier(a.sync, a.sync + 1, G, a.fault)) return;
+  }
 }
 
 // Persistent grid: at most (resident CTAs per SM) x (SMs) CTAs.
@@ -571,6 +693,24 @@ cudaError_t FLLF_LAUNCH_NAME(down0)(const Down0Args& a, cudaStream_t s) {
   const int grid = persistent_grid(k_down0<FLLF_STORAGE>, SMS::dn, tiles);
   k_down0<FLLF_STORAGE><<<grid, kThreads, SMS::dn, s>>>(a);
   return cudaGetLastError();
+}
+
+cudaError_t FLLF_LAUNCH_NAME(chain)(const ChainArgs& a, cudaStream_t s) {
+  constexpr size_t kChainSmem = SMS::up > SMS::dn ? SMS::up : SMS::dn;
+  static int grid = 0;
+  const size_t smem = kChainSmem;
+  if (grid == 0) {
+    int dev = 0, sms = 0, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaFuncSetAttribute(k_chain<FLLF_STORAGE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kChainSmem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_chain<FLLF_STORAGE>, kThreads, kChainSmem);
+    grid = (per > 0 ? per : 1) * (sms > 0 ? sms : 1);
+  }
+  void* args[] = {const_cast<ChainArgs*>(&a)};
+  cudaError_t e = cudaLaunchCooperativeKernel(reinterpret_cast<const void*>(k_chain<FLLF_STORAGE>),
+                                              dim3(grid), dim3(kThreads), args, smem, s);
+  return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 }  // namespace fllf

@@ -12,7 +12,8 @@ namespace fllf {
   cudaError_t launch_up0_##suffix(const Up0Args& a, cudaStream_t s);     \
   cudaError_t launch_up_##suffix(const UpArgs& a, cudaStream_t s);       \
   cudaError_t launch_down_##suffix(const DownArgs& a, cudaStream_t s);   \
-  cudaError_t launch_down0_##suffix(const Down0Args& a, cudaStream_t s);
+  cudaError_t launch_down0_##suffix(const Down0Args& a, cudaStream_t s);   \
+  cudaError_t launch_chain_##suffix(const ChainArgs& a, cudaStream_t s);
 FLLF_DECLARE_LAUNCHERS(f32)
 FLLF_DECLARE_LAUNCHERS(f16)
 FLLF_DECLARE_LAUNCHERS(bf16)

@@ -38,7 +38,7 @@ constexpr int kMaxDevices = 64;
 std::mutex g_noalloc_mu;
 unsigned char* g_noalloc_ptr[kMaxDevices] = {};
 
-constexpr size_t kHeadBytes = 512;  // a_1..a_64 (float32) at 0, fault word at 256, then the pyramids
+constexpr size_t kHeadBytes = 512;  // a_1..a_64 (float32) at 0, fault and barrier words at 256, then the pyramids
 
 fllf_status noalloc_fail(fllf_status s, const std::string& why) {
   fllf::set_last_error(why);

@@ -4,6 +4,7 @@
 #include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 
+#include <cstdlib>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -65,6 +66,13 @@ cudaError_t launch_down(int prec, const DownArgs& a, cudaStream_t s) {
     case FLLF_FP16: return launch_down_f16(a, s);
     case FLLF_BF16: return launch_down_bf16(a, s);
     default: return launch_down_f32(a, s);
+  }
+}
+cudaError_t launch_chain(int prec, const ChainArgs& a, cudaStream_t s) {
+  switch (prec) {
+    case FLLF_FP16: return launch_chain_f16(a, s);
+    case FLLF_BF16: return launch_chain_bf16(a, s);
+    default: return launch_chain_f32(a, s);
   }
 }
 cudaError_t launch_down0(int prec, const Down0Args& a, cudaStream_t s) {
@@ -145,7 +153,21 @@ cudaError_t enqueue_path(const fllf_params& p, const std::vector<Level>& lv, con
   if ((e = launch_up0(prec, u0, s)) != cudaSuccess) return e;
   mark(FLLF_STAGE_UP0, false);
 
-  for (int l = 1; l <= L - 2; ++l) {
+  // Levels >= c0 run as one chained cooperative launch: from the first level
+  // (>= 2) whose pixels over all planes fit in 2^21, the REDUCE stages up to
+  // the top and the combines back down to c0.
+  static const long long chain_px = [] {
+    const char* v = getenv("FLLF_CHAIN_PIXELS");  // tuning override of the 2^21 threshold
+    return v ? atoll(v) : (1ll << 21);
+  }();
+  int c0 = L - 1;
+  for (int l = 2; l <= L - 2; ++l)
+    if ((long long)lv[l].h * lv[l].w * C <= chain_px) {
+      c0 = l;
+      break;
+    }
+  if (L - 1 - c0 > kChainMax) c0 = L - 1 - kChainMax;
+  auto up_args = [&](int l) {
     UpArgs u{};
     u.zmap = maps.z_up[l];
     u.gmap = maps.g_up[l];
@@ -155,11 +177,9 @@ cudaError_t enqueue_path(const fllf_params& p, const std::vector<Level>& lv, con
     u.K = p.K;
     u.write_g = (l + 1 <= L - 2) ? 1 : 0;
     u.fault = fault;
-    mark(FLLF_STAGE_UP, true);
-    if ((e = launch_up(prec, u, s)) != cudaSuccess) return e;
-    mark(FLLF_STAGE_UP, false);
-  }
-  for (int l = L - 2; l >= 1; --l) {
+    return u;
+  };
+  auto down_args = [&](int l) {
     DownArgs d{};
     d.zmap = maps.z_dn[l + 1];
     d.emap = maps.e_dn[l + 1];
@@ -171,6 +191,26 @@ cudaError_t enqueue_path(const fllf_params& p, const std::vector<Level>& lv, con
     d.turns = turns;
     d.has_e = (l + 1 <= L - 2) ? 1 : 0;
     d.fault = fault;
+    return d;
+  };
+  for (int l = 1; l <= L - 2 && l < c0; ++l) {
+    const UpArgs u = up_args(l);
+    mark(FLLF_STAGE_UP, true);
+    if ((e = launch_up(prec, u, s)) != cudaSuccess) return e;
+    mark(FLLF_STAGE_UP, false);
+  }
+  if (c0 <= L - 2) {
+    ChainArgs ca{};
+    for (int l = c0; l <= L - 2; ++l) ca.up[ca.n_up++] = up_args(l);
+    for (int l = L - 2; l >= c0; --l) ca.dn[ca.n_dn++] = down_args(l);
+    ca.sync = fault + 32;
+    ca.fault = fault;
+    mark(FLLF_STAGE_CHAIN, true);
+    if ((e = launch_chain(prec, ca, s)) != cudaSuccess) return e;
+    mark(FLLF_STAGE_CHAIN, false);
+  }
+  for (int l = (c0 <= L - 2 ? c0 - 1 : L - 2); l >= 1; --l) {
+    const DownArgs d = down_args(l);
     mark(FLLF_STAGE_DOWN, true);
     if ((e = launch_down(prec, d, s)) != cudaSuccess) return e;
     mark(FLLF_STAGE_DOWN, false);
