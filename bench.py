@@ -42,6 +42,8 @@ def parse():
     ap.add_argument("--precision", choices=["fp32", "fp16", "bf16"], default="fp32")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--workload", choices=["uhd", "batch"], default="uhd",
+                    help="uhd: the 4K RGB headline; batch: 64 mixed images, batched vs looped")
     return ap.parse_args()
 
 
@@ -399,10 +401,74 @@ def kernel_revision():
     return h.hexdigest()[:12]
 
 
+def run_batch(args):
+    """64 mixed-size images (own K, sigma_r, m, levels): one batched pass per
+    step (one launch per stage kind, CUDA graph) against looping fllf_run."""
+    import torch
+    import paper_2206_04681_gb300 as pkg
+    from paper_2206_04681_gb300 import build
+    from paper_2206_04681_gb300.synth import batch_workload, synth_image
+    build.build_library()
+    torch.cuda.set_device(0)
+    items = batch_workload(64, seed=4)
+    plans, ins, outs = [], [], []
+    for it in items:
+        p = pkg.make_params(it["H"], it["W"], it["C"], it["levels"], it["K"], it["m"],
+                            it["sigma_r"], it["T"], args.precision)
+        plans.append(pkg.fllf_plan_create(p, 0))
+        x = torch.from_numpy(synth_image(it["H"], it["W"], it["C"], it["polygons"], it["seed"])).cuda()
+        ins.append(x)
+        outs.append(torch.empty_like(x))
+    pixels = sum(it["H"] * it["W"] for it in items)
+    stream = torch.cuda.Stream()
+    batch = pkg.fllf_batch_create(plans)
+    pin = [x.data_ptr() for x in ins]
+    pout = [y.data_ptr() for y in outs]
+
+    def timed(step, steps, warmup):
+        with torch.cuda.stream(stream):
+            for _ in range(warmup):
+                step()
+            stream.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(steps):
+                step()
+            e1.record(stream)
+            e1.synchronize()
+        return e0.elapsed_time(e1) / steps
+
+    steps = max(3, min(args.steps, 50))
+    warm = max(3, min(args.warmup, 5))
+    clocks = ClockSampler(0)
+    clocks.start()
+    ms_batch = timed(lambda: pkg.fllf_batch_run(batch, pin, pout, stream.cuda_stream), steps, warm)
+    clk = clocks.stop()
+    pkg.fllf_batch_check(batch)
+    ms_loop = timed(lambda: [pkg.fllf_run(p, a, b, stream.cuda_stream)
+                             for p, a, b in zip(plans, pin, pout)], steps, warm)
+    pkg.fllf_batch_destroy(batch)
+    for p in plans:
+        pkg.fllf_plan_destroy(p)
+    line = {"metric": "Mpixel/s Fourier LLF, 64 mixed-size images (batched)", "value": pixels / ms_batch / 1e3,
+            "unit": UNIT, "n_gpus": 1, "steps": steps, "warmup": warm, "ms_per_step": ms_batch,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": "batch64_mixed_sizes", "images": len(items), "pixels": pixels,
+                       "sides": "log-uniform 256..4096, aspect 0.5..2", "K": "4 or 8",
+                       "pyramid_storage": args.precision},
+            "looped_per_image": {"ms_per_step": ms_loop, "value": pixels / ms_loop / 1e3},
+            "speedup_vs_loop": ms_loop / ms_batch, "clocks": clk}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "batch":
+        return run_batch(args)
     return run_ours(args)
 
 

@@ -137,6 +137,33 @@ fllf_status fllf_submit(fllf_plan *plan, const float *d_in, float *d_out, void *
  * FLLF_ECUDA: the work failed on the device. */
 fllf_status fllf_poll(uint64_t ticket, int timeout_us);
 
+/* ---- Batched execution ------------------------------------------------------
+ * A batch groups n plans (same device and storage precision; each with its
+ * own size, levels, K and remap) so that one launch per stage kind covers
+ * every image: the REDUCE and combine work items of all images share the
+ * persistent grids, which keeps the GPU full when images are small or at the
+ * small pyramid levels.  The launch sequence is captured in a CUDA graph at
+ * the first run and replayed afterwards.  The batch uses the plans' scratch:
+ * a plan must not run on its own while a batch that holds it is running, and
+ * the plans must outlive the batch. */
+typedef struct fllf_batch fllf_batch;
+
+/* Builds the batch's argument tables (device memory owned by the batch). */
+fllf_status fllf_batch_create(fllf_plan *const *plans, int n, fllf_batch **out);
+
+/* Frees the batch (not the plans); NULL is accepted. */
+fllf_status fllf_batch_destroy(fllf_batch *batch);
+
+/* Filters image i of the batch from d_in[i] to d_out[i] (device pointers,
+ * planar C x H x W of plan i, non-overlapping) for every i, enqueued on
+ * `stream`.  Host arrays d_in / d_out are read before the call returns. */
+fllf_status fllf_batch_run(fllf_batch *batch, const float *const *d_in, float *const *d_out,
+                           void *stream);
+
+/* After the batch's work completed: FLLF_ETIMEOUT if a kernel's bounded wait
+ * ran out (the status is then cleared), else FLLF_OK. */
+fllf_status fllf_batch_check(fllf_batch *batch);
+
 /* ---- Filtering without any device allocation -------------------------------
  * The paper has no counterpart to this entry point; it exists for callers
  * that cannot call cudaMalloc (code running inside a memory pool or an

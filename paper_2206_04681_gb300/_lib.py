@@ -48,6 +48,10 @@ _SIGS = {
     "fllf_run_host": (ctypes.c_int, [_P, _P, _P, _P]),
     "fllf_submit": (ctypes.c_int, [_P, _P, _P, _P, ctypes.POINTER(ctypes.c_uint64)]),
     "fllf_poll": (ctypes.c_int, [ctypes.c_uint64, ctypes.c_int]),
+    "fllf_batch_create": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int, ctypes.POINTER(_P)]),
+    "fllf_batch_destroy": (ctypes.c_int, [_P]),
+    "fllf_batch_run": (ctypes.c_int, [_P, ctypes.POINTER(_P), ctypes.POINTER(_P), _P]),
+    "fllf_batch_check": (ctypes.c_int, [_P]),
     "fllf_run_noalloc": (ctypes.c_int, [ctypes.POINTER(fllf_params), _P, _P, _P]),
     "fllf_plan_enable_timing": (ctypes.c_int, [_P, ctypes.c_int]),
     "fllf_plan_stage_times": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_double),
@@ -147,6 +151,28 @@ def fllf_submit(plan, d_in, d_out, stream=0):
     t = ctypes.c_uint64()
     _check(lib().fllf_submit(plan, _P(d_in), _P(d_out), _P(stream), ctypes.byref(t)))
     return t.value
+
+
+def fllf_batch_create(plans):
+    arr = (_P * len(plans))(*[p.value if isinstance(p, _P) else p for p in plans])
+    h = _P()
+    _check(lib().fllf_batch_create(arr, len(plans), ctypes.byref(h)))
+    return h
+
+
+def fllf_batch_destroy(batch):
+    _check(lib().fllf_batch_destroy(batch))
+
+
+def fllf_batch_run(batch, d_in, d_out, stream=0):
+    """d_in, d_out: sequences of device addresses (one per plan of the batch)."""
+    ins = (_P * len(d_in))(*d_in)
+    outs = (_P * len(d_out))(*d_out)
+    _check(lib().fllf_batch_run(batch, ins, outs, _P(stream)))
+
+
+def fllf_batch_check(batch):
+    _check(lib().fllf_batch_check(batch))
 
 
 NOALLOC_SCRATCH_BYTES = 32 << 20

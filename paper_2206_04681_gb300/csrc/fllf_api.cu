@@ -189,20 +189,7 @@ bool check_layout(const fllf_params& p, const std::vector<Level>& lv, const unsi
 
 using namespace fllf;
 
-struct fllf_plan {
-  fllf_params p{};
-  int device = 0;
-  std::vector<double> a64;
-  float* d_a = nullptr;
-  unsigned char* scratch = nullptr;
-  size_t scratch_bytes = 0;
-  std::vector<Level> lv;  // device addresses
-  float* d_io_in = nullptr;
-  float* d_io_out = nullptr;
-  StageTimer* timer = nullptr;  // per-stage timing diagnostics (optional)
-  PathMaps maps;                // TMA tensor maps of the level buffers
-  unsigned* d_fault = nullptr;  // device word set by a kernel whose bounded wait ran out
-};
+
 
 namespace {
 

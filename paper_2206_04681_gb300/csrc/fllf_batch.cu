@@ -1,0 +1,392 @@
+// fllf_batch.cu -- batched execution of many plans: one launch per stage kind
+// covers every image (uneven sizes, own K / sigma_r / m / levels), and the
+// launch sequence is captured once in a CUDA graph.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "fllf.h"
+#include "fllf_internal.h"
+#include "fllf_launch.h"
+
+using namespace fllf;
+
+namespace {
+
+enum StageKind { kUp0 = 0, kUp = 1, kDown = 2, kDown0 = 3 };
+
+struct StageRec {
+  int kind;
+  size_t args_off;    // byte offset of the argument table in the device block
+  size_t prefix_off;  // byte offset of the prefix sums
+  int n, total;
+};
+
+// Work-item counts; these mirror the device-side definitions exactly.
+int up0_items_h(const Level& l1, int planes) { return cdiv(l1.w, kUpTW) * cdiv(l1.h, kUpTH) * planes; }
+int up_items_h(const Level& dst, int planes, int K, int prec) {
+  const int kcu = prec == FLLF_FP32 ? Smem<8>::up_kc : Smem<4>::up_kc;
+  return cdiv(dst.w, kRsTW) * cdiv(dst.h, kRsTH) * planes * cdiv(K, kcu);
+}
+int combine_tiles_h(int h, int w, int planes) { return cdiv(w + kDnX0, kDnOW) * cdiv(h, kDnOH) * planes; }
+
+template <typename T>
+size_t push(std::vector<unsigned char>& blob, const T* data, size_t n, size_t align) {
+  size_t off = (blob.size() + align - 1) / align * align;
+  blob.resize(off + sizeof(T) * n);
+  std::copy(reinterpret_cast<const unsigned char*>(data), reinterpret_cast<const unsigned char*>(data + n),
+            blob.begin() + off);
+  return off;
+}
+
+fllf_status bfail(fllf_status s, const std::string& why) {
+  set_last_error(why);
+  return s;
+}
+
+}  // namespace
+
+struct fllf_batch {
+  std::vector<fllf_plan*> plans;
+  int device = 0, precision = 0;
+  std::vector<StageRec> stages;
+  unsigned char* d_mem = nullptr;
+  size_t mem_bytes = 0;
+  unsigned* d_fault = nullptr;
+  // Per-run tables: level-0 input / output pointers (pinned host mirrors).
+  std::vector<int> up0_img, down0_img;  // image index of each entry
+  size_t up0_off = 0, down0_off = 0;    // device offsets of those tables
+  Up0Args* h_up0 = nullptr;
+  Down0Args* h_down0 = nullptr;
+  std::vector<int> copy_img;            // images with a single level (output = input)
+  cudaEvent_t copied = nullptr;
+  bool copied_pending = false;
+  cudaStream_t cap = nullptr;
+  cudaGraphExec_t graph = nullptr;
+};
+
+static void free_batch(fllf_batch* b) {
+  if (!b) return;
+  if (b->graph) cudaGraphExecDestroy(b->graph);
+  if (b->cap) cudaStreamDestroy(b->cap);
+  if (b->copied) cudaEventDestroy(b->copied);
+  if (b->h_up0) cudaFreeHost(b->h_up0);
+  if (b->h_down0) cudaFreeHost(b->h_down0);
+  if (b->d_mem) cudaFree(b->d_mem);
+  delete b;
+}
+
+static cudaError_t launch_stage(const fllf_batch* b, const StageRec& st, cudaStream_t s) {
+  const int prec = b->precision;
+  const int* prefix = reinterpret_cast<const int*>(b->d_mem + st.prefix_off);
+  switch (st.kind) {
+    case kUp0: {
+      BatchTable<Up0Args> t{reinterpret_cast<const Up0Args*>(b->d_mem + st.args_off), prefix, st.n, st.total};
+      return prec == FLLF_FP16 ? launch_up0_batch_f16(t, s)
+             : prec == FLLF_BF16 ? launch_up0_batch_bf16(t, s) : launch_up0_batch_f32(t, s);
+    }
+    case kUp: {
+      BatchTable<UpArgs> t{reinterpret_cast<const UpArgs*>(b->d_mem + st.args_off), prefix, st.n, st.total};
+      return prec == FLLF_FP16 ? launch_up_batch_f16(t, s)
+             : prec == FLLF_BF16 ? launch_up_batch_bf16(t, s) : launch_up_batch_f32(t, s);
+    }
+    case kDown: {
+      BatchTable<DownArgs> t{reinterpret_cast<const DownArgs*>(b->d_mem + st.args_off), prefix, st.n, st.total};
+      return prec == FLLF_FP16 ? launch_down_batch_f16(t, s)
+             : prec == FLLF_BF16 ? launch_down_batch_bf16(t, s) : launch_down_batch_f32(t, s);
+    }
+    default: {
+      BatchTable<Down0Args> t{reinterpret_cast<const Down0Args*>(b->d_mem + st.args_off), prefix, st.n, st.total};
+      return prec == FLLF_FP16 ? launch_down0_batch_f16(t, s)
+             : prec == FLLF_BF16 ? launch_down0_batch_bf16(t, s) : launch_down0_batch_f32(t, s);
+    }
+  }
+}
+
+extern "C" {
+
+fllf_status fllf_batch_create(fllf_plan* const* plans, int n, fllf_batch** out) {
+  if (!out) return bfail(FLLF_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (!plans || n < 1 || n > 4096) return bfail(FLLF_EINVAL, "need 1..4096 plans");
+  for (int i = 0; i < n; ++i)
+    if (!plans[i]) return bfail(FLLF_EINVAL, "plan is NULL");
+  const int dev = plans[0]->device, prec = plans[0]->p.precision;
+  for (int i = 1; i < n; ++i)
+    if (plans[i]->device != dev || plans[i]->p.precision != prec)
+      return bfail(FLLF_EINVAL, "all plans of a batch need the same device and precision");
+  int prev = -1;
+  cudaGetDevice(&prev);
+  if (cudaSetDevice(dev) != cudaSuccess) return bfail(FLLF_ECUDA, "cudaSetDevice failed");
+  struct Restore {
+    int d;
+    ~Restore() {
+      if (d >= 0) cudaSetDevice(d);
+    }
+  } restore{prev};
+
+  fllf_batch* b = new (std::nothrow) fllf_batch();
+  if (!b) return bfail(FLLF_ENOMEM, "batch allocation failed");
+  b->plans.assign(plans, plans + n);
+  b->device = dev;
+  b->precision = prec;
+  int maxL = 1;
+  for (auto* p : b->plans) maxL = std::max(maxL, p->p.levels);
+
+  // Build every table in one host blob, then upload it once.
+  std::vector<unsigned char> blob;
+  std::vector<std::vector<int>> prefixes;
+  auto add_stage = [&](int kind, auto& args, std::vector<int>& counts) {
+    if (args.empty()) return;
+    StageRec st{};
+    st.kind = kind;
+    st.n = (int)args.size();
+    std::vector<int> pre(st.n + 1, 0);
+    for (int j = 0; j < st.n; ++j) pre[j + 1] = pre[j] + counts[j];
+    st.total = pre[st.n];
+    st.args_off = push(blob, args.data(), args.size(), 128);
+    st.prefix_off = push(blob, pre.data(), pre.size(), 16);
+    b->stages.push_back(st);
+  };
+  // The fault/status block sits first.
+  std::vector<unsigned> status(64, 0u);
+  const size_t status_off = push(blob, status.data(), status.size(), 256);
+
+  {
+    std::vector<Up0Args> args;
+    std::vector<int> counts;
+    for (int i = 0; i < n; ++i) {
+      const fllf_plan* pl = b->plans[i];
+      if (pl->p.levels < 2) {
+        b->copy_img.push_back(i);
+        continue;
+      }
+      Up0Args u{};
+      u.h0 = pl->p.H;
+      u.w0 = pl->p.W;
+      u.planes = pl->p.C;
+      u.dst = pl->lv[1];
+      u.K = pl->p.K;
+      u.turns = (float)(2.0 / pl->p.T);
+      u.use_tma = 0;
+      args.push_back(u);
+      counts.push_back(up0_items_h(pl->lv[1], pl->p.C));
+      b->up0_img.push_back(i);
+    }
+    add_stage(kUp0, args, counts);
+    if (!args.empty()) b->up0_off = b->stages.back().args_off;
+  }
+  for (int l = 1; l <= maxL - 2; ++l) {
+    std::vector<UpArgs> args;
+    std::vector<int> counts;
+    for (int i = 0; i < n; ++i) {
+      const fllf_plan* pl = b->plans[i];
+      const int L = pl->p.levels;
+      if (l > L - 2) continue;
+      UpArgs u{};
+      u.zmap = pl->maps.z_up[l];
+      u.gmap = pl->maps.g_up[l];
+      u.src = pl->lv[l];
+      u.dst = pl->lv[l + 1];
+      u.planes = pl->p.C;
+      u.K = pl->p.K;
+      u.write_g = (l + 1 <= L - 2) ? 1 : 0;
+      args.push_back(u);
+      counts.push_back(up_items_h(pl->lv[l + 1], pl->p.C, pl->p.K, prec));
+    }
+    add_stage(kUp, args, counts);
+  }
+  for (int l = maxL - 2; l >= 1; --l) {
+    std::vector<DownArgs> args;
+    std::vector<int> counts;
+    for (int i = 0; i < n; ++i) {
+      const fllf_plan* pl = b->plans[i];
+      const int L = pl->p.levels;
+      if (l > L - 2) continue;
+      DownArgs d{};
+      d.zmap = pl->maps.z_dn[l + 1];
+      d.emap = pl->maps.e_dn[l + 1];
+      d.fine = pl->lv[l];
+      d.coarse = pl->lv[l + 1];
+      d.a = pl->d_a;
+      d.planes = pl->p.C;
+      d.K = pl->p.K;
+      d.turns = (float)(2.0 / pl->p.T);
+      d.has_e = (l + 1 <= L - 2) ? 1 : 0;
+      args.push_back(d);
+      counts.push_back(combine_tiles_h(pl->lv[l].h, pl->lv[l].w, pl->p.C));
+    }
+    add_stage(kDown, args, counts);
+  }
+  {
+    std::vector<Down0Args> args;
+    std::vector<int> counts;
+    for (int idx : b->up0_img) {
+      const fllf_plan* pl = b->plans[idx];
+      Down0Args d{};
+      d.zmap = pl->maps.z_dn[1];
+      d.emap = pl->maps.e_dn[1];
+      d.h0 = pl->p.H;
+      d.w0 = pl->p.W;
+      d.planes = pl->p.C;
+      d.coarse = pl->lv[1];
+      d.a = pl->d_a;
+      d.K = pl->p.K;
+      d.turns = (float)(2.0 / pl->p.T);
+      d.has_e = pl->p.levels >= 3 ? 1 : 0;
+      args.push_back(d);
+      counts.push_back(combine_tiles_h(pl->p.H, pl->p.W, pl->p.C));
+      b->down0_img.push_back(idx);
+    }
+    add_stage(kDown0, args, counts);
+    if (!args.empty()) b->down0_off = b->stages.back().args_off;
+  }
+
+  cudaError_t e;
+  b->mem_bytes = blob.size();
+  if ((e = cudaMalloc(&b->d_mem, b->mem_bytes)) != cudaSuccess) {
+    cudaGetLastError();
+    b->d_mem = nullptr;
+    free_batch(b);
+    return bfail(FLLF_ENOMEM, "batch table allocation failed");
+  }
+  b->d_fault = reinterpret_cast<unsigned*>(b->d_mem + status_off);
+  // Point every argument block's fault word at the batch status block.
+  for (const StageRec& st : b->stages) {
+    for (int j = 0; j < st.n; ++j) {
+      unsigned char* base = blob.data() + st.args_off;
+      switch (st.kind) {
+        case kUp0: reinterpret_cast<Up0Args*>(base)[j].fault = b->d_fault; break;
+        case kUp: reinterpret_cast<UpArgs*>(base)[j].fault = b->d_fault; break;
+        case kDown: reinterpret_cast<DownArgs*>(base)[j].fault = b->d_fault; break;
+        default: reinterpret_cast<Down0Args*>(base)[j].fault = b->d_fault; break;
+      }
+    }
+  }
+  if ((e = cudaMemcpy(b->d_mem, blob.data(), b->mem_bytes, cudaMemcpyHostToDevice)) != cudaSuccess) {
+    free_batch(b);
+    return bfail(FLLF_ECUDA, std::string("batch table upload: ") + cudaGetErrorString(e));
+  }
+  const size_t nu = std::max<size_t>(1, b->up0_img.size());
+  if (cudaMallocHost(&b->h_up0, sizeof(Up0Args) * nu) != cudaSuccess ||
+      cudaMallocHost(&b->h_down0, sizeof(Down0Args) * nu) != cudaSuccess) {
+    cudaGetLastError();
+    free_batch(b);
+    return bfail(FLLF_ENOMEM, "pinned host tables");
+  }
+  if (!b->up0_img.empty()) {
+    std::copy(reinterpret_cast<const Up0Args*>(blob.data() + b->up0_off),
+              reinterpret_cast<const Up0Args*>(blob.data() + b->up0_off) + b->up0_img.size(), b->h_up0);
+    std::copy(reinterpret_cast<const Down0Args*>(blob.data() + b->down0_off),
+              reinterpret_cast<const Down0Args*>(blob.data() + b->down0_off) + b->down0_img.size(),
+              b->h_down0);
+  }
+  if (cudaEventCreateWithFlags(&b->copied, cudaEventDisableTiming) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) != cudaSuccess) {
+    free_batch(b);
+    return bfail(FLLF_ECUDA, "batch event / stream creation failed");
+  }
+  *out = b;
+  return FLLF_OK;
+}
+
+fllf_status fllf_batch_destroy(fllf_batch* b) {
+  if (!b) return FLLF_OK;
+  int prev = -1;
+  cudaGetDevice(&prev);
+  cudaSetDevice(b->device);
+  free_batch(b);
+  if (prev >= 0) cudaSetDevice(prev);
+  return FLLF_OK;
+}
+
+fllf_status fllf_batch_run(fllf_batch* b, const float* const* d_in, float* const* d_out, void* stream) {
+  if (!b || !d_in || !d_out) return bfail(FLLF_EINVAL, "batch, d_in or d_out is NULL");
+  const int n = (int)b->plans.size();
+  for (int i = 0; i < n; ++i) {
+    if (!d_in[i] || !d_out[i]) return bfail(FLLF_EINVAL, "an image pointer is NULL");
+    const fllf_params& p = b->plans[i]->p;
+    const size_t bytes = sizeof(float) * (size_t)p.H * p.W * p.C;
+    const char *x = reinterpret_cast<const char*>(d_in[i]), *y = reinterpret_cast<const char*>(d_out[i]);
+    if (x < y + bytes && y < x + bytes) return bfail(FLLF_EINVAL, "input and output buffers overlap");
+  }
+  int prev = -1;
+  cudaGetDevice(&prev);
+  if (cudaSetDevice(b->device) != cudaSuccess) return bfail(FLLF_ECUDA, "cudaSetDevice failed");
+  struct Restore {
+    int d;
+    ~Restore() {
+      if (d >= 0) cudaSetDevice(d);
+    }
+  } restore{prev};
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  cudaError_t e;
+  // The pinned mirrors may still feed the previous run's copies.
+  if (b->copied_pending && (e = cudaEventSynchronize(b->copied)) != cudaSuccess)
+    return bfail(FLLF_ECUDA, std::string("batch copy wait: ") + cudaGetErrorString(e));
+  for (size_t j = 0; j < b->up0_img.size(); ++j) {
+    b->h_up0[j].I = d_in[b->up0_img[j]];
+    b->h_down0[j].I = d_in[b->down0_img[j]];
+    b->h_down0[j].O = d_out[b->down0_img[j]];
+  }
+  if (!b->up0_img.empty()) {
+    if ((e = cudaMemcpyAsync(b->d_mem + b->up0_off, b->h_up0, sizeof(Up0Args) * b->up0_img.size(),
+                             cudaMemcpyHostToDevice, s)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(b->d_mem + b->down0_off, b->h_down0,
+                             sizeof(Down0Args) * b->down0_img.size(), cudaMemcpyHostToDevice, s)) !=
+            cudaSuccess)
+      return bfail(FLLF_ECUDA, std::string("batch table update: ") + cudaGetErrorString(e));
+  }
+  if ((e = cudaEventRecord(b->copied, s)) != cudaSuccess)
+    return bfail(FLLF_ECUDA, std::string("batch event: ") + cudaGetErrorString(e));
+  b->copied_pending = true;
+  for (int i : b->copy_img) {
+    const fllf_params& p = b->plans[i]->p;
+    if ((e = cudaMemcpyAsync(d_out[i], d_in[i], sizeof(float) * (size_t)p.H * p.W * p.C,
+                             cudaMemcpyDeviceToDevice, s)) != cudaSuccess)
+      return bfail(FLLF_ECUDA, std::string("single-level copy: ") + cudaGetErrorString(e));
+  }
+  if (b->stages.empty()) return FLLF_OK;
+  if (!b->graph) {
+    // Capture the launch sequence once; tables are read from device memory,
+    // so the graph stays valid for every later run.
+    cudaGraph_t g = nullptr;
+    if ((e = cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeRelaxed)) != cudaSuccess)
+      return bfail(FLLF_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+    cudaError_t le = cudaSuccess;
+    for (const StageRec& st : b->stages)
+      if ((le = launch_stage(b, st, b->cap)) != cudaSuccess) break;
+    e = cudaStreamEndCapture(b->cap, &g);
+    if (le != cudaSuccess || e != cudaSuccess) {
+      if (g) cudaGraphDestroy(g);
+      return bfail(FLLF_ECUDA, std::string("graph capture: ") +
+                                   cudaGetErrorString(le != cudaSuccess ? le : e));
+    }
+    e = cudaGraphInstantiate(&b->graph, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+      b->graph = nullptr;
+      return bfail(FLLF_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+    }
+  }
+  if ((e = cudaGraphLaunch(b->graph, s)) != cudaSuccess)
+    return bfail(FLLF_ECUDA, std::string("graph launch: ") + cudaGetErrorString(e));
+  return FLLF_OK;
+}
+
+fllf_status fllf_batch_check(fllf_batch* b) {
+  if (!b) return bfail(FLLF_EINVAL, "batch is NULL");
+  unsigned f = 0;
+  cudaError_t e = cudaMemcpy(&f, b->d_fault, sizeof(unsigned), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return bfail(FLLF_ECUDA, std::string("fault word read: ") + cudaGetErrorString(e));
+  if (f) {
+    cudaMemset(b->d_fault, 0, 256);
+    return bfail(FLLF_ETIMEOUT, "a kernel's bounded wait for a shared-memory copy ran out");
+  }
+  return FLLF_OK;
+}
+
+}  // extern "C"

@@ -115,6 +115,16 @@ struct Down0Args {
   unsigned* fault;
 };
 
+// Batched stage launch: argument blocks of the images that have the stage
+// (device memory) and exclusive prefix sums of their work-item counts
+// (prefix[0] = 0, prefix[n] = total).
+template <typename A>
+struct BatchTable {
+  const A* args;
+  const int* prefix;
+  int n, total;
+};
+
 // Chained small levels: REDUCE stages then combine stages in one cooperative
 // launch, with a grid barrier between consecutive stages.
 constexpr int kChainMax = 12;

@@ -82,3 +82,20 @@ cudaError_t enqueue_path(const fllf_params& p, const std::vector<Level>& lv, con
                          cudaStream_t s, StageHook* hook = nullptr);
 
 }  // namespace fllf
+
+// A filter plan (opaque to callers): parameters, float32 coefficients on the
+// device, the scratch pyramids, their TMA maps and a device status block.
+struct fllf_plan {
+  fllf_params p{};
+  int device = 0;
+  std::vector<double> a64;
+  float* d_a = nullptr;
+  unsigned char* scratch = nullptr;
+  size_t scratch_bytes = 0;
+  std::vector<fllf::Level> lv;    // device addresses
+  float* d_io_in = nullptr;
+  float* d_io_out = nullptr;
+  fllf::StageTimer* timer = nullptr;  // per-stage timing diagnostics (optional)
+  fllf::PathMaps maps;                // TMA tensor maps of the level buffers
+  unsigned* d_fault = nullptr;        // device status block (fault word, grid-barrier words)
+};

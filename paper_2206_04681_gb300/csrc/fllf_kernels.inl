@@ -1,9 +1,14 @@
-// fllf_kernels.inl -- the four persistent kernels of the path for one storage
-// type FLLF_STORAGE; included by one translation unit per precision.
+// fllf_kernels.inl -- the kernels of the path for one storage type
+// FLLF_STORAGE; included by one translation unit per precision.
 //
-// Every kernel is persistent: CTA b handles tiles b, b + gridDim.x, ... as a
-// stream of (tile, chunk) work items, two shared-memory buffers deep, so the
-// TMA copy of the next item overlaps the computation of the current one.
+// Every stage is a persistent device function over a stream of work items
+// (tiles, or (tile, chunk of orders) pairs).  CTA b of a grid of G takes
+// items b, b + G, ...; a 2-deep ring of shared-memory buffers keeps the TMA
+// copy of the next item in flight while the current one is computed.  Items
+// are mapped to their image by a resolver: one image for the per-image
+// kernels (arguments in the parameter block), many images for the batched
+// kernels (argument tables in device memory, with prefix sums of the item
+// counts).
 #include "fllf_launch.h"
 
 namespace fllf {
@@ -24,57 +29,87 @@ struct Pipe {
   uint32_t use[2];
 };
 
-// ---------------------------------------------------------------------------------------
-// up0: level 0 -> 1.  Item (row r, segment s) holds 11 fine pixels of one
-// staged input row; it evaluates e^{i k w_1 x} for k = 1..K with the
-// Chebyshev recurrence z_{k+1} = 2 cos(w_1 x) z_k - z_{k-1} (one packed FMA
-// per order) from one hardware sincos per pixel and writes 4 horizontally
-// reduced complex values per order to column-major staging; the vertical
-// pass finishes REDUCE (Eq. (1)) and stores G_1 and Z_1.
-template <typename S>
-__global__ void __launch_bounds__(kThreads) k_up0(const __grid_constant__ Up0Args a) {
-  using CT = typename Cplx<S>::T;
-  using SM = Smem<sizeof(CT)>;
-  extern __shared__ __align__(128) unsigned char smem[];
-  float* itb[2] = {reinterpret_cast<float*>(smem), reinterpret_cast<float*>(smem + SM::up0_it)};
-  float2* hz = reinterpret_cast<float2*>(smem + 2 * SM::up0_it);
-  float* hg = reinterpret_cast<float*>(smem + 2 * SM::up0_it + align128(SM::up0_hz));
-  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + 2 * SM::up0_it + align128(SM::up0_hz) +
-                                              align128(SM::up0_hg));
-  const int tid = threadIdx.x;
-  const int ntx = cdiv(a.dst.w, kUpTW), nty = cdiv(a.dst.h, kUpTH);
-  const int ntiles = ntx * nty * a.planes;
-  const int nch = cdiv(a.K, kKC);
-  if (tid == 0) {
+__device__ __forceinline__ void init_bars(uint64_t* bar) {
+  if (threadIdx.x == 0) {
     mbar_init(&bar[0], 1);
     mbar_init(&bar[1], 1);
     fence_mbar_init();
   }
   __syncthreads();
-  auto issue = [&](int t, int buf) {
+}
+
+// Entry j of a prefix table holding item x (prefix[0] = 0, prefix[n] = total).
+__device__ __forceinline__ int find_entry(const int* prefix, int n, int x) {
+  int lo = 0, hi = n - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (__ldg(prefix + mid) <= x) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+// ---------------------------------------------------------------------------------------
+// up0: level 0 -> 1.  Item = tile of 32 x 14 level-1 outputs.  Item (row r,
+// segment s) of the horizontal pass holds 11 fine pixels of one staged input
+// row; it evaluates e^{i k w_1 x} for k = 1..K with the Chebyshev recurrence
+// z_{k+1} = 2 cos(w_1 x) z_k - z_{k-1} (one packed FMA per order) from one
+// hardware sincos per pixel and writes 4 horizontally reduced complex values
+// per order to column-major staging; the vertical pass finishes REDUCE
+// (Eq. (1)) and stores G_1 and Z_1.
+__device__ __forceinline__ int up0_tiles(const Up0Args& a) {
+  return cdiv(a.dst.w, kUpTW) * cdiv(a.dst.h, kUpTH) * a.planes;
+}
+
+template <typename S, typename Res>
+__device__ __forceinline__ bool stage_up0(Res res, int total, unsigned char* smem, uint64_t* bar,
+                                          Pipe& pp, int b, int G) {
+  using CT = typename Cplx<S>::T;
+  using SM = Smem<sizeof(CT)>;
+  float* itb[2] = {reinterpret_cast<float*>(smem), reinterpret_cast<float*>(smem + SM::up0_it)};
+  float2* hz = reinterpret_cast<float2*>(smem + 2 * SM::up0_it);
+  float* hg = reinterpret_cast<float*>(smem + 2 * SM::up0_it + align128(SM::up0_hz));
+  const int tid = threadIdx.x;
+  auto issue = [&](const Up0Args& a, int t, int buf) {
+    const int ntx = cdiv(a.dst.w, kUpTW), nty = cdiv(a.dst.h, kUpTH);
     const int tx = t % ntx, r = t / ntx, ty = r % nty, pl = r / nty;
     mbar_expect_tx(&bar[buf], sizeof(float) * kUpIR * kUpIW);
     tma_load3(itb[buf], &a.imap, 2 * tx * kUpTW - 4, 2 * ty * kUpTH - 2, pl, &bar[buf]);
   };
-  if (a.use_tma && tid == 0 && (int)blockIdx.x < ntiles) issue(blockIdx.x, 0);
-
+  if (b < total && tid == 0) {
+    int lt;
+    const Up0Args* a0 = res(b, lt);
+    if (a0->use_tma) {
+      fence_proxy_async();
+      issue(*a0, lt, 0);
+    }
+  }
   int n = 0;
-  for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++n) {
+  for (int gt = b; gt < total; gt += G, ++n) {
     const int buf = n & 1;
+    int t;
+    const Up0Args& a = *res(gt, t);
+    const int ntx = cdiv(a.dst.w, kUpTW), nty = cdiv(a.dst.h, kUpTH);
     const int tx = t % ntx, rt = t / ntx, ty = rt % nty, pl = rt / nty;
     const int X1 = tx * kUpTW, Y1 = ty * kUpTH;
     const int xs = 2 * X1 - 4, ys = 2 * Y1 - 2;
+    const int nch = cdiv(a.K, kKC);
     float* it = itb[buf];
-    if (a.use_tma) {
-      const int tn = t + gridDim.x;
-      if (tid == 0 && tn < ntiles) {
+    const int gn = gt + G;
+    if (tid == 0 && gn < total) {
+      int tn;
+      const Up0Args* an = res(gn, tn);
+      if (an->use_tma) {
         fence_proxy_async();
-        issue(tn, buf ^ 1);
+        issue(*an, tn, buf ^ 1);
       }
-      if (!mbar_wait_cta(&bar[buf], (n >> 1) & 1, a.fault)) {
-        if (tid == 0 && tn < ntiles) drain(&bar[buf ^ 1], ((n + 1) >> 1) & 1);
-        return;
+    }
+    if (a.use_tma) {
+      if (!mbar_wait_cta(&bar[buf], pp.use[buf] & 1, a.fault)) {
+        if (tid == 0 && gn < total) drain(&bar[buf ^ 1], pp.use[buf ^ 1] & 1);
+        return false;
       }
+      ++pp.use[buf];
       fix_borders(it, 1, kUpIR, kUpIW, xs, ys, a.w0, a.h0,
                   [&](int y) { return refl101(y, a.h0); }, [&](int x) { return refl101(x, a.w0); });
     } else {
@@ -129,7 +164,8 @@ __global__ void __launch_bounds__(kThreads) k_up0(const __grid_constant__ Up0Arg
         if (k < a.K && x < a.dst.w) {
           CT* Zk = reinterpret_cast<CT*>(a.dst.Z) + (long long)pl * a.dst.zplane +
                    (long long)k * a.dst.zk + x;
-          const float4* p = reinterpret_cast<const float4*>(hz + (kk * kUpTW + col) * kUpCS + 2 * kUpVRows * grp);
+          const float4* p =
+              reinterpret_cast<const float4*>(hz + (kk * kUpTW + col) * kUpCS + 2 * kUpVRows * grp);
           float2 w[2 * kUpVRows + 4];
 #pragma unroll
           for (int u = 0; u < kUpVRows + 2; ++u) {
@@ -142,13 +178,14 @@ __global__ void __launch_bounds__(kThreads) k_up0(const __grid_constant__ Up0Arg
             const int y = Y1 + grp * kUpVRows + j;
             if (y < a.dst.h)
               Cplx<S>::st(Zk + (long long)y * a.dst.pitch,
-                          mul2(splat(1.f / 256.f), tap5(w[2 * j], w[2 * j + 1], w[2 * j + 2], w[2 * j + 3], w[2 * j + 4])));
+                          mul2(splat(1.f / 256.f),
+                               tap5(w[2 * j], w[2 * j + 1], w[2 * j + 2], w[2 * j + 3], w[2 * j + 4])));
           }
         }
         if (ch == 0 && tid < 2 * kUpTW) {
           const int g2 = tid / kUpTW, c2 = tid % kUpTW, xg = X1 + c2;
           if (xg < a.dst.w) {
-            float* G = a.dst.G + (long long)pl * a.dst.gplane + xg;
+            float* Gp = a.dst.G + (long long)pl * a.dst.gplane + xg;
             const float2* p = reinterpret_cast<const float2*>(hg + c2 * kUpCS + 2 * kUpVRows * g2);
             float w[2 * kUpVRows + 4];
 #pragma unroll
@@ -161,7 +198,7 @@ __global__ void __launch_bounds__(kThreads) k_up0(const __grid_constant__ Up0Arg
             for (int j = 0; j < kUpVRows; ++j) {
               const int y = Y1 + g2 * kUpVRows + j;
               if (y < a.dst.h)
-                G[(long long)y * a.dst.pitch] =
+                Gp[(long long)y * a.dst.pitch] =
                     (1.f / 256.f) * tap5(w[2 * j], w[2 * j + 1], w[2 * j + 2], w[2 * j + 3], w[2 * j + 4]);
             }
           }
@@ -170,17 +207,25 @@ __global__ void __launch_bounds__(kThreads) k_up0(const __grid_constant__ Up0Arg
       __syncthreads();
     }
   }
+  return true;
 }
 
 // ---------------------------------------------------------------------------------------
 // up: level l -> l+1 for l >= 1 (REDUCE of G_l and the K complex planes).
-// Work item = (tile, chunk of KCU orders).  TMA stages the 35 x 68 source
-// box of each order of the chunk (plus G_l with chunk 0); the vertical pass
-// reads one staged column per thread and keeps the reduced rows in
-// registers; the horizontal pass reads 5 staged columns per output.
-template <typename S, bool COH>
-__device__ __forceinline__ bool stage_up(const UpArgs& a, unsigned char* smem, uint64_t* bar, Pipe& pp,
-                                         int b, int G) {
+// Item = (tile of 30 x 16 coarse outputs, chunk of KCU orders): orders reduce
+// independently, so small levels still spread over many CTAs.  TMA stages
+// the 35 x 68 source box of each order of the chunk (plus G_l with chunk 0);
+// the vertical pass reads one staged column per thread and keeps the reduced
+// rows in registers; the horizontal pass reads 5 staged columns per output.
+template <typename S>
+__device__ __forceinline__ int up_items(const UpArgs& a) {
+  return cdiv(a.dst.w, kRsTW) * cdiv(a.dst.h, kRsTH) * a.planes *
+         cdiv(a.K, Smem<sizeof(typename Cplx<S>::T)>::up_kc);
+}
+
+template <typename S, typename Res>
+__device__ __forceinline__ bool stage_up(Res res, int total, unsigned char* smem, uint64_t* bar,
+                                         Pipe& pp, int b, int G) {
   using CT = typename Cplx<S>::T;
   using SM = Smem<sizeof(CT)>;
   constexpr int KCU = SM::up_kc;
@@ -194,15 +239,12 @@ __device__ __forceinline__ bool stage_up(const UpArgs& a, unsigned char* smem, u
   float2* vb = reinterpret_cast<float2*>(smem + 2 * SM::up_buf);
   float* vg = reinterpret_cast<float*>(smem + 2 * SM::up_buf + SM::up_vb);
   const int tid = threadIdx.x;
-  const int ntx = cdiv(a.dst.w, kRsTW), nty = cdiv(a.dst.h, kRsTH);
-  const int ntiles = ntx * nty * a.planes;
-  const int nch = cdiv(a.K, KCU);
-  // Work items are (tile, chunk of orders) pairs: orders reduce independently,
-  // so small levels still spread over many CTAs.
-  const int total = ntiles * nch;
   const int nitems = b < total ? (total - b + G - 1) / G : 0;
-  auto issue = [&](int i, int buf) {
-    const int gi = b + i * G, t = gi / nch, ch = gi % nch;
+  auto issue = [&](int gi, int buf) {
+    int li;
+    const UpArgs& a = *res(gi, li);
+    const int nch = cdiv(a.K, KCU), t = li / nch, ch = li % nch;
+    const int ntx = cdiv(a.dst.w, kRsTW), nty = cdiv(a.dst.h, kRsTH);
     const int tx = t % ntx, r = t / ntx, ty = r % nty, pl = r / nty;
     const int x = 2 * tx * kRsTW - 4, y = 2 * ty * kRsTH - 2;
     const bool g = ch == 0 && a.write_g;
@@ -213,18 +255,21 @@ __device__ __forceinline__ bool stage_up(const UpArgs& a, unsigned char* smem, u
   };
   if (tid == 0 && nitems > 0) {
     fence_proxy_async();
-    issue(0, 0);
+    issue(b, 0);
   }
   for (int i = 0; i < nitems; ++i) {
     const int buf = i & 1;
-    const int gi = b + i * G, t = gi / nch, ch = gi % nch;
+    int li;
+    const UpArgs& a = *res(b + i * G, li);
+    const int nch = cdiv(a.K, KCU), t = li / nch, ch = li % nch;
+    const int ntx = cdiv(a.dst.w, kRsTW), nty = cdiv(a.dst.h, kRsTH);
     const int tx = t % ntx, rt = t / ntx, ty = rt % nty, pl = rt / nty;
     const int X1 = tx * kRsTW, Y1 = ty * kRsTH;
     const int xs = 2 * X1 - 4, ys = 2 * Y1 - 2;
     const bool g = ch == 0 && a.write_g;
     if (tid == 0 && i + 1 < nitems) {
       fence_proxy_async();
-      issue(i + 1, buf ^ 1);
+      issue(b + (i + 1) * G, buf ^ 1);
     }
     if (!mbar_wait_cta(&bar[buf], pp.use[buf] & 1, a.fault)) {
       if (tid == 0 && i + 1 < nitems) drain(&bar[buf ^ 1], pp.use[buf ^ 1] & 1);
@@ -285,13 +330,13 @@ __device__ __forceinline__ bool stage_up(const UpArgs& a, unsigned char* smem, u
       if (g && tid < 2 * kRsTW) {
         const int half = tid / kRsTW, ic = tid % kRsTW, x = X1 + ic;
         if (x < a.dst.w) {
-          float* G = a.dst.G + (long long)pl * a.dst.gplane + x;
+          float* Gp = a.dst.G + (long long)pl * a.dst.gplane + x;
 #pragma unroll
           for (int j = 0; j < kRsTH / 2; ++j) {
             const int jr = half * (kRsTH / 2) + j, y = Y1 + jr;
             if (y < a.dst.h) {
               const float* p = vg + jr * kRsVW + 2 * ic;
-              G[(long long)y * a.dst.pitch] = (1.f / 256.f) * tap5(p[0], p[1], p[2], p[3], p[4]);
+              Gp[(long long)y * a.dst.pitch] = (1.f / 256.f) * tap5(p[0], p[1], p[2], p[3], p[4]);
             }
           }
         }
@@ -302,95 +347,110 @@ __device__ __forceinline__ bool stage_up(const UpArgs& a, unsigned char* smem, u
   return true;
 }
 
-template <typename S>
-__global__ void __launch_bounds__(kThreads) k_up(const __grid_constant__ UpArgs a) {
-  using SM = Smem<sizeof(typename Cplx<S>::T)>;
-  extern __shared__ __align__(128) unsigned char smem[];
-  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + SM::up - 64);
-  if (threadIdx.x == 0) {
-    mbar_init(&bar[0], 1);
-    mbar_init(&bar[1], 1);
-    fence_mbar_init();
-  }
-  __syncthreads();
-  Pipe pp{{0u, 0u}};
-  stage_up<S, false>(a, smem, bar, pp, blockIdx.x, gridDim.x);
-}
-
-
 // ---------------------------------------------------------------------------------------
 // Combine (Eq. (14) product-sum fused with the residual collapse).
-// A thread owns fine rows 2j, 2j+1 and fine columns 4c..4c+3 of the tile
-// (tile origin 64*tx-6), i.e. coarse rows j-1..j+1 and coarse columns
-// 2c-1..2c+2, which sit at staged rows tr..tr+2 and columns 2tc..2tc+3.
-// EXPAND of the 3 x 4 complex window runs on (C~, S~) pairs with packed
-// FP32x2 arithmetic; the per-pixel trig state (cos, -sin) of the two fine
-// rows and the accumulators are (even row, odd row) pairs, advanced by
-// complex rotation.  EXPAND weights 1/8 (1, 6, 1) at even fine positions and
-// 1/2 (1, 1) at odd ones per axis are folded into the coefficients.
+// Item = (tile of 64 x 32 fine pixels, chunk of kKC orders); the chunks of a
+// tile run back to back on one CTA, which keeps the per-pixel state in
+// registers.  A thread owns fine rows 2j, 2j+1 and fine columns 4c..4c+3 of
+// the tile (tile origin 64*tx-6), i.e. coarse rows j-1..j+1 and coarse
+// columns 2c-1..2c+2, which sit at staged rows tr..tr+2 and columns
+// 2tc..2tc+3.  EXPAND of the 3 x 4 complex window runs on (C~, S~) pairs
+// with packed FP32x2 arithmetic; the per-pixel trig state (cos, -sin) of the
+// two fine rows and the accumulators are (even row, odd row) pairs, advanced
+// by complex rotation.  EXPAND weights 1/8 (1, 6, 1) at even fine positions
+// and 1/2 (1, 1) at odd ones per axis are folded into the coefficients.
 __device__ __forceinline__ float2 expand_scale_pair(int q) {
   return (q & 1) ? make_float2(1.f / 16.f, 1.f / 4.f) : make_float2(1.f / 64.f, 1.f / 16.f);
 }
 
-template <typename S, bool LEVEL0, bool COH>
-__device__ __forceinline__ bool stage_combine(const CUtensorMap* zmap, const CUtensorMap* emap,
-                                              const Level* fine, const float* I, float* O, int h,
-                                              int w, int planes, const Level& coarse,
-                                              const float* acoef, int K, float turns, int has_e,
-                                              unsigned* fault, unsigned char* smem, uint64_t* bar,
+// Uniform view of the level >= 1 and level-0 combine arguments.
+struct CombineView {
+  const CUtensorMap* zmap;
+  const CUtensorMap* emap;
+  const Level* fine;    // level >= 1 only
+  const float* I;       // level 0 only
+  float* O;             // level 0 only
+  const Level* coarse;
+  const float* a;
+  unsigned* fault;
+  int h, w, planes, K, has_e;
+  float turns;
+};
+__device__ __forceinline__ CombineView view_of(const DownArgs& d) {
+  return CombineView{&d.zmap, &d.emap, &d.fine, nullptr, nullptr, &d.coarse, d.a, d.fault,
+                     d.fine.h, d.fine.w, d.planes, d.K, d.has_e, d.turns};
+}
+__device__ __forceinline__ CombineView view_of(const Down0Args& d) {
+  return CombineView{&d.zmap, &d.emap, nullptr, d.I, d.O, &d.coarse, d.a, d.fault,
+                     d.h0, d.w0, d.planes, d.K, d.has_e, d.turns};
+}
+__device__ __forceinline__ int combine_tiles(const CombineView& v) {
+  return cdiv(v.w + kDnX0, kDnOW) * cdiv(v.h, kDnOH) * v.planes;
+}
+
+template <typename S, bool LEVEL0, bool COH, typename Res>
+__device__ __forceinline__ bool stage_combine(Res res, int total, unsigned char* smem, uint64_t* bar,
                                               Pipe& pp, int b, int G) {
   using CT = typename Cplx<S>::T;
   using SM = Smem<sizeof(CT)>;
   unsigned char* bufs[2] = {smem, smem + SM::dn_buf};
   const int tid = threadIdx.x;
-  const int ntx = cdiv(w + kDnX0, kDnOW), nty = cdiv(h, kDnOH);
-  const int ntiles = ntx * nty * planes;
-  const int nch = cdiv(K, kKC);
-  const int nmine = b < ntiles ? (ntiles - b + G - 1) / G : 0;
-  const int nitems = nmine * nch;
-  auto issue = [&](int i, int buf) {
-    const int t = b + (i / nch) * G, ch = i % nch;
-    const int tx = t % ntx, r = t / ntx, ty = r % nty, pl = r / nty;
+  if (b >= total) return true;
+  auto issue = [&](const CombineView& v, int lt, int ch, int buf) {
+    const int ntx = cdiv(v.w + kDnX0, kDnOW), nty = cdiv(v.h, kDnOH);
+    const int tx = lt % ntx, r = lt / ntx, ty = r % nty, pl = r / nty;
     const int cx0 = (tx * kDnOW - kDnX0) / 2 - 1, cy0 = ty * (kDnOH / 2) - 1;
-    const bool e = ch == 0 && has_e;
+    const bool e = ch == 0 && v.has_e;
     mbar_expect_tx(&bar[buf], (uint32_t)(sizeof(CT) * kKC * kDnCH * kDnCW +
                                          (e ? sizeof(float) * kDnCH * kDnCW : 0)));
-    tma_load3(bufs[buf], zmap, cx0, cy0, pl * K + ch * kKC, &bar[buf]);
-    if (e) tma_load3(bufs[buf] + SM::dn_z, emap, cx0, cy0, pl, &bar[buf]);
+    tma_load3(bufs[buf], v.zmap, cx0, cy0, pl * v.K + ch * kKC, &bar[buf]);
+    if (e) tma_load3(bufs[buf] + SM::dn_z, v.emap, cx0, cy0, pl, &bar[buf]);
   };
-  if (tid == 0 && nitems > 0) {
+  int t = b, lt = 0, ch = 0;
+  CombineView v = res(t, lt);
+  int nch = cdiv(v.K, kKC);
+  if (tid == 0) {
     fence_proxy_async();
-    issue(0, 0);
+    issue(v, lt, 0, 0);
   }
 
   const int tc = tid % (kDnOW / 4), tr = tid / (kDnOW / 4);
   float2 cc[4], ns[4], c1[4], s1[4], ns1[4], acc[4];
   int xq[4], y0c = 0, y1c = 0, fy = 0, fx = 0, pl = 0;
-  for (int i = 0; i < nitems; ++i) {
+  for (int i = 0;; ++i) {
     const int buf = i & 1;
-    const int t = b + (i / nch) * G, ch = i % nch;
-    const int tx = t % ntx, rt = t / ntx, ty = rt % nty;
+    const int ntx = cdiv(v.w + kDnX0, kDnOW), nty = cdiv(v.h, kDnOH);
+    const int tx = lt % ntx, rt = lt / ntx, ty = rt % nty;
     pl = rt / nty;
     const int X0 = tx * kDnOW - kDnX0, Y0 = ty * kDnOH;
     const int cx0 = X0 / 2 - 1, cy0 = Y0 / 2 - 1;
-    if (tid == 0 && i + 1 < nitems) {
+    const bool more_chunks = ch + 1 < nch;
+    const bool has_next = more_chunks || t + G < total;
+    if (tid == 0 && has_next) {
       fence_proxy_async();
-      issue(i + 1, buf ^ 1);
+      if (more_chunks) {
+        issue(v, lt, ch + 1, buf ^ 1);
+      } else {
+        int ln;
+        const CombineView vn = res(t + G, ln);
+        issue(vn, ln, 0, buf ^ 1);
+      }
     }
+    const int h = v.h, w = v.w;
     if (ch == 0) {
       // Per-tile state: guide value g, trig state (cos, -sin) for k = 1, accumulators.
       fy = Y0 + 2 * tr;
       fx = X0 + 4 * tc;
       y0c = min(fy, h - 1);
       y1c = min(fy + 1, h - 1);
-      const long long gpitch = LEVEL0 ? (long long)w : (long long)fine->pitch;
-      const float* gsrc = LEVEL0 ? I + (long long)pl * h * w : fine->G + (long long)pl * fine->gplane;
+      const long long gpitch = LEVEL0 ? (long long)w : (long long)v.fine->pitch;
+      const float* gsrc = LEVEL0 ? v.I + (long long)pl * h * w : v.fine->G + (long long)pl * v.fine->gplane;
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
         xq[q] = min(max(fx + q, 0), w - 1);
         const float g0 = COH ? __ldcg(gsrc + y0c * gpitch + xq[q]) : __ldg(gsrc + y0c * gpitch + xq[q]);
         const float g1 = COH ? __ldcg(gsrc + y1c * gpitch + xq[q]) : __ldg(gsrc + y1c * gpitch + xq[q]);
-        const float2 z0 = cos_sin_turns(turns * g0), z1 = cos_sin_turns(turns * g1);
+        const float2 z0 = cos_sin_turns(v.turns * g0), z1 = cos_sin_turns(v.turns * g1);
         c1[q] = make_float2(z0.x, z1.x);
         s1[q] = make_float2(z0.y, z1.y);
         ns1[q] = make_float2(-z0.y, -z1.y);
@@ -399,43 +459,40 @@ __device__ __forceinline__ bool stage_combine(const CUtensorMap* zmap, const CUt
         acc[q] = LEVEL0 ? make_float2(g0, g1) : splat(0.f);
       }
     }
-    if (!mbar_wait_cta(&bar[buf], pp.use[buf] & 1, fault)) {
-      if (tid == 0 && i + 1 < nitems) drain(&bar[buf ^ 1], pp.use[buf ^ 1] & 1);
+    if (!mbar_wait_cta(&bar[buf], pp.use[buf] & 1, v.fault)) {
+      if (tid == 0 && has_next) drain(&bar[buf ^ 1], pp.use[buf ^ 1] & 1);
       return false;
     }
     ++pp.use[buf];
     CT* zb = reinterpret_cast<CT*>(bufs[buf]);
     float* eb = reinterpret_cast<float*>(bufs[buf] + SM::dn_z);
+    const Level& coarse = *v.coarse;
     auto my = [&](int y) { return ext_coarse(y, coarse.h, h); };
     auto mx = [&](int x) { return ext_coarse(x, coarse.w, w); };
     fix_borders(zb, kKC, kDnCH, kDnCW, cx0, cy0, coarse.w, coarse.h, my, mx);
-    if (ch == 0 && has_e) {
+    if (ch == 0 && v.has_e) {
       fix_borders(eb, 1, kDnCH, kDnCW, cx0, cy0, coarse.w, coarse.h, my, mx);
-      float v[3][4];
+      float e3[3][4];
 #pragma unroll
       for (int r = 0; r < 3; ++r) {
         // 8-byte aligned (2*tc floats): two float2 reads
         const float2* q2 = reinterpret_cast<const float2*>(eb + (tr + r) * kDnCW + 2 * tc);
         const float2 qa = q2[0], qb = q2[1];
-        v[r][0] = qa.x; v[r][1] = qa.y; v[r][2] = qb.x; v[r][3] = qb.y;
+        e3[r][0] = qa.x; e3[r][1] = qa.y; e3[r][2] = qb.x; e3[r][3] = qb.y;
       }
       float2 p[4];
 #pragma unroll
-      for (int q = 0; q < 4; ++q) p[q] = make_float2(fmaf(6.f, v[1][q], v[0][q] + v[2][q]), v[1][q] + v[2][q]);
-      const float2 u0 = fma2(splat(6.f), p[1], add2(p[0], p[2]));
-      const float2 u1 = add2(p[1], p[2]);
-      const float2 u2 = fma2(splat(6.f), p[2], add2(p[1], p[3]));
-      const float2 u3 = add2(p[2], p[3]);
-      acc[0] = fma2(expand_scale_pair(0), u0, acc[0]);
-      acc[1] = fma2(expand_scale_pair(1), u1, acc[1]);
-      acc[2] = fma2(expand_scale_pair(2), u2, acc[2]);
-      acc[3] = fma2(expand_scale_pair(3), u3, acc[3]);
+      for (int q = 0; q < 4; ++q) p[q] = make_float2(fmaf(6.f, e3[1][q], e3[0][q] + e3[2][q]), e3[1][q] + e3[2][q]);
+      acc[0] = fma2(expand_scale_pair(0), fma2(splat(6.f), p[1], add2(p[0], p[2])), acc[0]);
+      acc[1] = fma2(expand_scale_pair(1), add2(p[1], p[2]), acc[1]);
+      acc[2] = fma2(expand_scale_pair(2), fma2(splat(6.f), p[2], add2(p[1], p[3])), acc[2]);
+      acc[3] = fma2(expand_scale_pair(3), add2(p[2], p[3]), acc[3]);
     }
 #pragma unroll
     for (int kk = 0; kk < kKC; ++kk) {
       const int k = ch * kKC + kk;
-      if (k < K) {
-        const float ak = __ldg(acoef + k);
+      if (k < v.K) {
+        const float ak = __ldg(v.a + k);
         const CT* zw = zb + kk * kDnCH * kDnCW + tr * kDnCW + 2 * tc;
         float2 wv[3][4];
 #pragma unroll
@@ -481,10 +538,10 @@ __device__ __forceinline__ bool stage_combine(const CUtensorMap* zmap, const CUt
           acc[q] = fma2((q & 1) ? ce1 : ce0, tq, acc[q]);
         }
         if constexpr (!LEVEL0) {
-          const CT* Zk = reinterpret_cast<const CT*>(fine->Z) + (long long)pl * fine->zplane +
-                         (long long)k * fine->zk;
-          const CT* r0 = Zk + (long long)y0c * fine->pitch;
-          const CT* r1 = Zk + (long long)y1c * fine->pitch;
+          const CT* Zk = reinterpret_cast<const CT*>(v.fine->Z) + (long long)pl * v.fine->zplane +
+                         (long long)k * v.fine->zk;
+          const CT* r0 = Zk + (long long)y0c * v.fine->pitch;
+          const CT* r1 = Zk + (long long)y1c * v.fine->pitch;
 #pragma unroll
           for (int q = 0; q < 4; ++q) {
             CT zz0, zz1;
@@ -519,15 +576,15 @@ __device__ __forceinline__ bool stage_combine(const CUtensorMap* zmap, const CUt
         }
       }
     }
-    if (ch == nch - 1) {
+    if (!more_chunks) {
       float* dst;
       long long dpitch;
       if constexpr (LEVEL0) {
-        dst = O + (long long)pl * h * w;
+        dst = v.O + (long long)pl * h * w;
         dpitch = w;
       } else {
-        dst = fine->E + (long long)pl * fine->gplane;
-        dpitch = fine->pitch;
+        dst = v.fine->E + (long long)pl * v.fine->gplane;
+        dpitch = v.fine->pitch;
       }
 #pragma unroll
       for (int rr = 0; rr < 2; ++rr) {
@@ -543,8 +600,41 @@ __device__ __forceinline__ bool stage_combine(const CUtensorMap* zmap, const CUt
       }
     }
     __syncthreads();
+    if (more_chunks) {
+      ++ch;
+    } else {
+      t += G;
+      if (t >= total) break;
+      v = res(t, lt);
+      ch = 0;
+      nch = cdiv(v.K, kKC);
+    }
   }
   return true;
+}
+
+// ---------------------------------------------------------------------------------------
+// Per-image kernels (arguments in the parameter block).
+template <typename S>
+__global__ void __launch_bounds__(kThreads) k_up0(const __grid_constant__ Up0Args a) {
+  using SM = Smem<sizeof(typename Cplx<S>::T)>;
+  extern __shared__ __align__(128) unsigned char smem[];
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + SM::up0 - 64);
+  init_bars(bar);
+  Pipe pp{{0u, 0u}};
+  stage_up0<S>([&](int g, int& l) { l = g; return &a; }, up0_tiles(a), smem, bar, pp, blockIdx.x,
+               gridDim.x);
+}
+
+template <typename S>
+__global__ void __launch_bounds__(kThreads) k_up(const __grid_constant__ UpArgs a) {
+  using SM = Smem<sizeof(typename Cplx<S>::T)>;
+  extern __shared__ __align__(128) unsigned char smem[];
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + SM::up - 64);
+  init_bars(bar);
+  Pipe pp{{0u, 0u}};
+  stage_up<S>([&](int g, int& l) { l = g; return &a; }, up_items<S>(a), smem, bar, pp, blockIdx.x,
+              gridDim.x);
 }
 
 template <typename S>
@@ -552,15 +642,10 @@ __global__ void __launch_bounds__(kThreads) k_down(const __grid_constant__ DownA
   using SM = Smem<sizeof(typename Cplx<S>::T)>;
   extern __shared__ __align__(128) unsigned char smem[];
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem + SM::dn - 64);
-  if (threadIdx.x == 0) {
-    mbar_init(&bar[0], 1);
-    mbar_init(&bar[1], 1);
-    fence_mbar_init();
-  }
-  __syncthreads();
+  init_bars(bar);
   Pipe pp{{0u, 0u}};
-  stage_combine<S, false, false>(&a.zmap, &a.emap, &a.fine, nullptr, nullptr, a.fine.h, a.fine.w,
-                                 a.planes, a.coarse, a.a, a.K, a.turns, a.has_e, a.fault, smem, bar,
+  const CombineView v = view_of(a);
+  stage_combine<S, false, false>([&](int g, int& l) { l = g; return v; }, combine_tiles(v), smem, bar,
                                  pp, blockIdx.x, gridDim.x);
 }
 
@@ -569,18 +654,100 @@ __global__ void __launch_bounds__(kThreads, 3) k_down0(const __grid_constant__ D
   using SM = Smem<sizeof(typename Cplx<S>::T)>;
   extern __shared__ __align__(128) unsigned char smem[];
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem + SM::dn - 64);
-  if (threadIdx.x == 0) {
-    mbar_init(&bar[0], 1);
-    mbar_init(&bar[1], 1);
-    fence_mbar_init();
-  }
-  __syncthreads();
+  init_bars(bar);
   Pipe pp{{0u, 0u}};
-  stage_combine<S, true, false>(&a.zmap, &a.emap, nullptr, a.I, a.O, a.h0, a.w0, a.planes,
-                                a.coarse, a.a, a.K, a.turns, a.has_e, a.fault, smem, bar, pp,
-                                blockIdx.x, gridDim.x);
+  const CombineView v = view_of(a);
+  stage_combine<S, true, false>([&](int g, int& l) { l = g; return v; }, combine_tiles(v), smem, bar,
+                                pp, blockIdx.x, gridDim.x);
 }
 
+// ---------------------------------------------------------------------------------------
+// Batched kernels: one launch per stage kind covers every image of a batch.
+// Their tensor maps live in device memory; the thread that issues the copies
+// orders them for the tensor-map proxy before first use.
+__device__ __forceinline__ void fence_tensormap(const void* map) {
+  asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(map) : "memory");
+}
+template <typename A, typename F>
+__device__ __forceinline__ void fence_maps(const BatchTable<A>& tb, F maps) {
+  if (threadIdx.x == 0)
+    for (int j = 0; j < tb.n; ++j) maps(tb.args[j]);
+}
+template <typename S>
+__global__ void __launch_bounds__(kThreads) k_up0_batch(const BatchTable<Up0Args> tb) {
+  using SM = Smem<sizeof(typename Cplx<S>::T)>;
+  extern __shared__ __align__(128) unsigned char smem[];
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + SM::up0 - 64);
+  init_bars(bar);
+  Pipe pp{{0u, 0u}};
+  stage_up0<S>([&](int g, int& l) {
+                 const int j = find_entry(tb.prefix, tb.n, g);
+                 l = g - __ldg(tb.prefix + j);
+                 return tb.args + j;
+               },
+               tb.total, smem, bar, pp, blockIdx.x, gridDim.x);
+}
+
+template <typename S>
+__global__ void __launch_bounds__(kThreads) k_up_batch(const BatchTable<UpArgs> tb) {
+  using SM = Smem<sizeof(typename Cplx<S>::T)>;
+  extern __shared__ __align__(128) unsigned char smem[];
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + SM::up - 64);
+  fence_maps(tb, [](const UpArgs& a) {
+    fence_tensormap(&a.zmap);
+    fence_tensormap(&a.gmap);
+  });
+  init_bars(bar);
+  Pipe pp{{0u, 0u}};
+  stage_up<S>([&](int g, int& l) {
+                const int j = find_entry(tb.prefix, tb.n, g);
+                l = g - __ldg(tb.prefix + j);
+                return tb.args + j;
+              },
+              tb.total, smem, bar, pp, blockIdx.x, gridDim.x);
+}
+
+template <typename S>
+__global__ void __launch_bounds__(kThreads) k_down_batch(const BatchTable<DownArgs> tb) {
+  using SM = Smem<sizeof(typename Cplx<S>::T)>;
+  extern __shared__ __align__(128) unsigned char smem[];
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + SM::dn - 64);
+  fence_maps(tb, [](const DownArgs& a) {
+    fence_tensormap(&a.zmap);
+    fence_tensormap(&a.emap);
+  });
+  init_bars(bar);
+  Pipe pp{{0u, 0u}};
+  stage_combine<S, false, false>(
+      [&](int g, int& l) {
+        const int j = find_entry(tb.prefix, tb.n, g);
+        l = g - __ldg(tb.prefix + j);
+        return view_of(tb.args[j]);
+      },
+      tb.total, smem, bar, pp, blockIdx.x, gridDim.x);
+}
+
+template <typename S>
+__global__ void __launch_bounds__(kThreads, 3) k_down0_batch(const BatchTable<Down0Args> tb) {
+  using SM = Smem<sizeof(typename Cplx<S>::T)>;
+  extern __shared__ __align__(128) unsigned char smem[];
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + SM::dn - 64);
+  fence_maps(tb, [](const Down0Args& a) {
+    fence_tensormap(&a.zmap);
+    fence_tensormap(&a.emap);
+  });
+  init_bars(bar);
+  Pipe pp{{0u, 0u}};
+  stage_combine<S, true, false>(
+      [&](int g, int& l) {
+        const int j = find_entry(tb.prefix, tb.n, g);
+        l = g - __ldg(tb.prefix + j);
+        return view_of(tb.args[j]);
+      },
+      tb.total, smem, bar, pp, blockIdx.x, gridDim.x);
+}
+
+// ---------------------------------------------------------------------------------------
 // Grid-wide barrier of a cooperative launch (all CTAs resident), bounded:
 // arrival counter + generation word; every thread first orders its global
 // stores before later TMA (async proxy) reads of other CTAs.
@@ -625,23 +792,19 @@ __global__ void __launch_bounds__(kThreads) k_chain(const __grid_constant__ Chai
   constexpr size_t kS = SM::up > SM::dn ? SM::up : SM::dn;
   extern __shared__ __align__(128) unsigned char smem[];
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem + kS - 64);
-  if (threadIdx.x == 0) {
-    mbar_init(&bar[0], 1);
-    mbar_init(&bar[1], 1);
-    fence_mbar_init();
-  }
-  __syncthreads();
+  init_bars(bar);
   Pipe pp{{0u, 0u}};
   const int b = blockIdx.x, G = gridDim.x;
   for (int st = 0; st < a.n_up; ++st) {
-    if (!stage_up<S, true>(a.up[st], smem, bar, pp, b, G)) return;
+    const UpArgs* u = &a.up[st];
+    if (!stage_up<S>([&](int g, int& l) { l = g; return u; }, up_items<S>(*u), smem, bar, pp, b, G))
+      return;
     if (!grid_barrier(a.sync, a.sync + 1, G, a.fault)) return;
   }
   for (int st = 0; st < a.n_dn; ++st) {
-    const DownArgs& d = a.dn[st];
-    if (!stage_combine<S, false, true>(&d.zmap, &d.emap, &d.fine, nullptr, nullptr, d.fine.h,
-                                       d.fine.w, d.planes, d.coarse, d.a, d.K, d.turns, d.has_e,
-                                       d.fault, smem, bar, pp, b, G))
+    const CombineView v = view_of(a.dn[st]);
+    if (!stage_combine<S, false, true>([&](int g, int& l) { l = g; return v; }, combine_tiles(v),
+                                       smem, bar, pp, b, G))
       return;
     if (st + 1 < a.n_dn && !grid_barrier(a.sync, a.sync + 1, G, a.fault)) return;
   }
@@ -649,7 +812,7 @@ __global__ void __launch_bounds__(kThreads) k_chain(const __grid_constant__ Chai
 
 // Persistent grid: at most (resident CTAs per SM) x (SMs) CTAs.
 template <typename Kern>
-int persistent_grid(Kern kern, size_t smem, int tiles) {
+int persistent_grid(Kern kern, size_t smem, int items) {
   static int cached = 0;
   if (cached == 0) {
     int dev = 0, sms = 0, per = 0;
@@ -659,7 +822,7 @@ int persistent_grid(Kern kern, size_t smem, int tiles) {
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, kThreads, smem);
     cached = (per > 0 ? per : 1) * (sms > 0 ? sms : 1);
   }
-  return tiles < cached ? tiles : cached;
+  return items < cached ? items : cached;
 }
 
 }  // namespace
@@ -698,19 +861,45 @@ cudaError_t FLLF_LAUNCH_NAME(down0)(const Down0Args& a, cudaStream_t s) {
 cudaError_t FLLF_LAUNCH_NAME(chain)(const ChainArgs& a, cudaStream_t s) {
   constexpr size_t kChainSmem = SMS::up > SMS::dn ? SMS::up : SMS::dn;
   static int grid = 0;
-  const size_t smem = kChainSmem;
   if (grid == 0) {
     int dev = 0, sms = 0, per = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaFuncSetAttribute(k_chain<FLLF_STORAGE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kChainSmem);
+    cudaFuncSetAttribute(k_chain<FLLF_STORAGE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)kChainSmem);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_chain<FLLF_STORAGE>, kThreads, kChainSmem);
     grid = (per > 0 ? per : 1) * (sms > 0 ? sms : 1);
   }
   void* args[] = {const_cast<ChainArgs*>(&a)};
   cudaError_t e = cudaLaunchCooperativeKernel(reinterpret_cast<const void*>(k_chain<FLLF_STORAGE>),
-                                              dim3(grid), dim3(kThreads), args, smem, s);
+                                              dim3(grid), dim3(kThreads), args, kChainSmem, s);
   return e != cudaSuccess ? e : cudaGetLastError();
+}
+
+// Batched launches: the grid covers every work item of the table.
+cudaError_t FLLF_LAUNCH_NAME(up0_batch)(const BatchTable<Up0Args>& tb, cudaStream_t s) {
+  if (tb.total <= 0) return cudaSuccess;
+  const int grid = persistent_grid(k_up0_batch<FLLF_STORAGE>, SMS::up0, tb.total);
+  k_up0_batch<FLLF_STORAGE><<<grid, kThreads, SMS::up0, s>>>(tb);
+  return cudaGetLastError();
+}
+cudaError_t FLLF_LAUNCH_NAME(up_batch)(const BatchTable<UpArgs>& tb, cudaStream_t s) {
+  if (tb.total <= 0) return cudaSuccess;
+  const int grid = persistent_grid(k_up_batch<FLLF_STORAGE>, SMS::up, tb.total);
+  k_up_batch<FLLF_STORAGE><<<grid, kThreads, SMS::up, s>>>(tb);
+  return cudaGetLastError();
+}
+cudaError_t FLLF_LAUNCH_NAME(down_batch)(const BatchTable<DownArgs>& tb, cudaStream_t s) {
+  if (tb.total <= 0) return cudaSuccess;
+  const int grid = persistent_grid(k_down_batch<FLLF_STORAGE>, SMS::dn, tb.total);
+  k_down_batch<FLLF_STORAGE><<<grid, kThreads, SMS::dn, s>>>(tb);
+  return cudaGetLastError();
+}
+cudaError_t FLLF_LAUNCH_NAME(down0_batch)(const BatchTable<Down0Args>& tb, cudaStream_t s) {
+  if (tb.total <= 0) return cudaSuccess;
+  const int grid = persistent_grid(k_down0_batch<FLLF_STORAGE>, SMS::dn, tb.total);
+  k_down0_batch<FLLF_STORAGE><<<grid, kThreads, SMS::dn, s>>>(tb);
+  return cudaGetLastError();
 }
 
 }  // namespace fllf
