@@ -164,6 +164,58 @@ fllf_status fllf_batch_run(fllf_batch *batch, const float *const *d_in, float *c
  * ran out (the status is then cleared), else FLLF_OK. */
 fllf_status fllf_batch_check(fllf_batch *batch);
 
+/* ---- Serving: continuous batching of filter requests ----------------------
+ * A server owns one device memory pool of `hbm_budget` bytes (allocated at
+ * creation) and a worker thread.  Requests (any size, levels, K, remap,
+ * storage precision) wait in a FIFO queue; the worker admits them as slots
+ * (at most `max_slots` requests admitted and not finished) and pool memory
+ * for their pyramids free up, builds their plans inside the pool (no device
+ * allocation per request), and launches each group admitted together as a
+ * batched wave on one of `max_waves` streams, so requests that arrive while
+ * others run are admitted and overlap them on the device.  A request's
+ * result does not depend on the other requests it shares a wave with.
+ * Latency is measured from fllf_server_submit to the worker seeing the
+ * request's wave complete. */
+typedef struct fllf_server fllf_server;
+
+typedef struct {
+  uint64_t submitted, completed, rejected;
+  double p50_ms, p99_ms, mean_ms, max_ms; /* latency of completed requests */
+  double mpixel_per_s;   /* H*W of completed requests / (last completion - first submit) */
+  size_t pool_bytes, pool_peak_bytes;
+  int max_active;        /* peak number of admitted, unfinished requests */
+  int waves;             /* waves launched */
+} fllf_server_stats;
+
+/* Creates a server on `device`.  hbm_budget: pool bytes (>= 1 MiB); max_slots:
+ * 1..4096; max_queue: pending requests before FLLF_EBUSY (>= 1);
+ * max_waves: concurrent waves (streams), 1..16. */
+fllf_status fllf_server_create(int device, size_t hbm_budget, int max_slots, int max_queue,
+                               int max_waves, fllf_server **out);
+
+/* Stops the worker after the waves in flight finish, and frees the server.
+ * Requests not yet admitted are cancelled; NULL is accepted.  No call on the
+ * server may run concurrently with or after this one. */
+fllf_status fllf_server_destroy(fllf_server *server);
+
+/* Queues a request: d_in (read) and d_out (written) are caller-owned device
+ * buffers (planar C x H x W float32, non-overlapping) that must stay valid
+ * until fllf_server_poll returns FLLF_OK for the ticket.  FLLF_EBUSY: the
+ * queue is full; FLLF_ENOMEM: the request can never fit in the pool. */
+fllf_status fllf_server_submit(fllf_server *server, const fllf_params *p, const float *d_in,
+                               float *d_out, uint64_t *ticket);
+
+/* Waits up to timeout_us (0 = test only, < 0 = no limit) for a request.
+ * FLLF_OK: finished, d_out holds the result (ticket consumed);
+ * FLLF_EAGAIN / FLLF_ETIMEOUT: still pending; FLLF_EINVAL: unknown ticket;
+ * FLLF_ECUDA: the request's wave failed, or one of its kernels' bounded waits
+ * gave up (ticket consumed, d_out undefined).  Thread-safe. */
+fllf_status fllf_server_poll(fllf_server *server, uint64_t ticket, int timeout_us);
+
+/* Statistics since creation or the last reset. */
+fllf_status fllf_server_stats_get(fllf_server *server, fllf_server_stats *out);
+fllf_status fllf_server_stats_reset(fllf_server *server);
+
 /* ---- Filtering without any device allocation -------------------------------
  * The paper has no counterpart to this entry point; it exists for callers
  * that cannot call cudaMalloc (code running inside a memory pool or an

@@ -11,7 +11,10 @@ from ._lib import (FllfError, fllf_params, make_params, lib, fllf_params_validat
                    fllf_plan_scratch_bytes, fllf_plan_create, fllf_plan_destroy,
                    fllf_plan_params, fllf_plan_coeffs, fllf_run, fllf_run_host, fllf_submit,
                    fllf_poll, fllf_batch_create, fllf_batch_destroy, fllf_batch_run,
-                   fllf_batch_check, fllf_run_noalloc, NOALLOC_SCRATCH_BYTES, fllf_plan_enable_timing, fllf_plan_stage_times, STAGES,
+                   fllf_batch_check, fllf_run_noalloc, NOALLOC_SCRATCH_BYTES,
+                   fllf_plan_enable_timing, fllf_plan_stage_times, STAGES,
+                   fllf_server_stats, fllf_server_create, fllf_server_destroy, fllf_server_submit,
+                   fllf_server_poll, fllf_server_stats_get, fllf_server_stats_reset,
                    FLLF_OK, FLLF_EINVAL, FLLF_ENOMEM, FLLF_ECUDA, FLLF_EAGAIN,
                    FLLF_ETIMEOUT, FLLF_EBUSY, FLLF_FP32, FLLF_FP16, FLLF_BF16,
                    FLLF_COEFF_QUADRATURE, FLLF_COEFF_CLOSED_FORM, PRECISIONS)

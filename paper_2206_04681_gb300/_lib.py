@@ -32,6 +32,18 @@ class fllf_params(ctypes.Structure):
                 ("precision", ctypes.c_int), ("coeff_mode", ctypes.c_int)]
 
 
+class fllf_server_stats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_uint64), ("completed", ctypes.c_uint64),
+                ("rejected", ctypes.c_uint64), ("p50_ms", ctypes.c_double),
+                ("p99_ms", ctypes.c_double), ("mean_ms", ctypes.c_double),
+                ("max_ms", ctypes.c_double), ("mpixel_per_s", ctypes.c_double),
+                ("pool_bytes", ctypes.c_size_t), ("pool_peak_bytes", ctypes.c_size_t),
+                ("max_active", ctypes.c_int), ("waves", ctypes.c_int)]
+
+    def as_dict(self):
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
 _P = ctypes.c_void_p
 _SIGS = {
     "fllf_status_str": (ctypes.c_char_p, [ctypes.c_int]),
@@ -53,6 +65,14 @@ _SIGS = {
     "fllf_batch_run": (ctypes.c_int, [_P, ctypes.POINTER(_P), ctypes.POINTER(_P), _P]),
     "fllf_batch_check": (ctypes.c_int, [_P]),
     "fllf_run_noalloc": (ctypes.c_int, [ctypes.POINTER(fllf_params), _P, _P, _P]),
+    "fllf_server_create": (ctypes.c_int, [ctypes.c_int, ctypes.c_size_t, ctypes.c_int,
+                                          ctypes.c_int, ctypes.c_int, ctypes.POINTER(_P)]),
+    "fllf_server_destroy": (ctypes.c_int, [_P]),
+    "fllf_server_submit": (ctypes.c_int, [_P, ctypes.POINTER(fllf_params), _P, _P,
+                                          ctypes.POINTER(ctypes.c_uint64)]),
+    "fllf_server_poll": (ctypes.c_int, [_P, ctypes.c_uint64, ctypes.c_int]),
+    "fllf_server_stats_get": (ctypes.c_int, [_P, ctypes.POINTER(fllf_server_stats)]),
+    "fllf_server_stats_reset": (ctypes.c_int, [_P]),
     "fllf_plan_enable_timing": (ctypes.c_int, [_P, ctypes.c_int]),
     "fllf_plan_stage_times": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_double),
                                              ctypes.POINTER(ctypes.c_int)]),
@@ -202,3 +222,42 @@ def fllf_poll(ticket, timeout_us=-1):
         return s
     _check(s)
     return s
+
+
+def fllf_server_create(hbm_budget, max_slots=64, max_queue=4096, max_waves=2, device=0):
+    h = _P()
+    _check(lib().fllf_server_create(int(device), int(hbm_budget), int(max_slots), int(max_queue),
+                                    int(max_waves), ctypes.byref(h)))
+    return h
+
+
+def fllf_server_destroy(server):
+    _check(lib().fllf_server_destroy(server))
+
+
+def fllf_server_submit(server, p, d_in, d_out):
+    """Queues one image (device buffers); returns its ticket.  Raises FllfError
+    with FLLF_EBUSY when the queue is full and FLLF_ENOMEM when the request can
+    never fit the server's pool."""
+    t = ctypes.c_uint64()
+    _check(lib().fllf_server_submit(server, ctypes.byref(p), _P(d_in), _P(d_out), ctypes.byref(t)))
+    return t.value
+
+
+def fllf_server_poll(server, ticket, timeout_us=-1):
+    """Returns FLLF_OK (done; the ticket is consumed), FLLF_EAGAIN or FLLF_ETIMEOUT; raises on failure."""
+    s = lib().fllf_server_poll(server, ctypes.c_uint64(ticket), int(timeout_us))
+    if s in (FLLF_OK, FLLF_EAGAIN, FLLF_ETIMEOUT):
+        return s
+    _check(s)
+    return s
+
+
+def fllf_server_stats_get(server):
+    st = fllf_server_stats()
+    _check(lib().fllf_server_stats_get(server, ctypes.byref(st)))
+    return st.as_dict()
+
+
+def fllf_server_stats_reset(server):
+    _check(lib().fllf_server_stats_reset(server))

@@ -1,6 +1,6 @@
 // fllf_batch.cu -- batched execution of many plans: one launch per stage kind
-// covers every image (uneven sizes, own K / sigma_r / m / levels), and the
-// launch sequence is captured once in a CUDA graph.
+// covers every image (uneven sizes, own K / sigma_r / m / levels); the
+// launch sequence of a batch object is captured once in a CUDA graph.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -12,18 +12,9 @@
 #include "fllf_internal.h"
 #include "fllf_launch.h"
 
-using namespace fllf;
+namespace fllf {
 
 namespace {
-
-enum StageKind { kUp0 = 0, kUp = 1, kDown = 2, kDown0 = 3 };
-
-struct StageRec {
-  int kind;
-  size_t args_off;    // byte offset of the argument table in the device block
-  size_t prefix_off;  // byte offset of the prefix sums
-  int n, total;
-};
 
 // Work-item counts; these mirror the device-side definitions exactly.
 int up0_items_h(const Level& l1, int planes) { return cdiv(l1.w, kUpTW) * cdiv(l1.h, kUpTH) * planes; }
@@ -35,33 +26,222 @@ int combine_tiles_h(int h, int w, int planes) { return cdiv(w + kDnX0, kDnOW) * 
 
 template <typename T>
 size_t push(std::vector<unsigned char>& blob, const T* data, size_t n, size_t align) {
-  size_t off = (blob.size() + align - 1) / align * align;
+  const size_t off = (blob.size() + align - 1) / align * align;
   blob.resize(off + sizeof(T) * n);
   std::copy(reinterpret_cast<const unsigned char*>(data), reinterpret_cast<const unsigned char*>(data + n),
             blob.begin() + off);
   return off;
 }
 
+cudaError_t launch_stage_at(const unsigned char* d_base, const StageRec& st, int prec, cudaStream_t s) {
+  const int* prefix = reinterpret_cast<const int*>(d_base + st.prefix_off);
+  switch (st.kind) {
+    case kStageUp0: {
+      BatchTable<Up0Args> t{reinterpret_cast<const Up0Args*>(d_base + st.args_off), prefix, st.n, st.total};
+      return prec == FLLF_FP16 ? launch_up0_batch_f16(t, s)
+             : prec == FLLF_BF16 ? launch_up0_batch_bf16(t, s) : launch_up0_batch_f32(t, s);
+    }
+    case kStageUp: {
+      BatchTable<UpArgs> t{reinterpret_cast<const UpArgs*>(d_base + st.args_off), prefix, st.n, st.total};
+      return prec == FLLF_FP16 ? launch_up_batch_f16(t, s)
+             : prec == FLLF_BF16 ? launch_up_batch_bf16(t, s) : launch_up_batch_f32(t, s);
+    }
+    case kStageDown: {
+      BatchTable<DownArgs> t{reinterpret_cast<const DownArgs*>(d_base + st.args_off), prefix, st.n, st.total};
+      return prec == FLLF_FP16 ? launch_down_batch_f16(t, s)
+             : prec == FLLF_BF16 ? launch_down_batch_bf16(t, s) : launch_down_batch_f32(t, s);
+    }
+    default: {
+      BatchTable<Down0Args> t{reinterpret_cast<const Down0Args*>(d_base + st.args_off), prefix, st.n, st.total};
+      return prec == FLLF_FP16 ? launch_down0_batch_f16(t, s)
+             : prec == FLLF_BF16 ? launch_down0_batch_bf16(t, s) : launch_down0_batch_f32(t, s);
+    }
+  }
+}
+
+}  // namespace
+
+void build_batch_blob(const std::vector<const fllf_plan*>& plans, int prec, BatchBlob* out) {
+  out->stages.clear();
+  out->up0_img.clear();
+  out->down0_img.clear();
+  out->copy_img.clear();
+  out->up0_off = out->down0_off = 0;
+  std::vector<unsigned char>& blob = out->blob;
+  blob.clear();
+  int maxL = 1;
+  for (const fllf_plan* p : plans) maxL = std::max(maxL, p->p.levels);
+  auto add_stage = [&](int kind, const auto& args, const std::vector<int>& counts) {
+    if (args.empty()) return;
+    StageRec st{};
+    st.kind = kind;
+    st.n = (int)args.size();
+    std::vector<int> pre(st.n + 1, 0);
+    for (int j = 0; j < st.n; ++j) pre[j + 1] = pre[j] + counts[j];
+    st.total = pre[st.n];
+    st.args_off = push(blob, args.data(), args.size(), 128);
+    st.prefix_off = push(blob, pre.data(), pre.size(), 16);
+    out->stages.push_back(st);
+  };
+  // A 256-byte status block first (fault word, barrier words).
+  const std::vector<unsigned> status(64, 0u);
+  out->status_off = push(blob, status.data(), status.size(), 256);
+  {
+    std::vector<Up0Args> args;
+    std::vector<int> counts;
+    for (int i = 0; i < (int)plans.size(); ++i) {
+      const fllf_plan* pl = plans[i];
+      if (pl->p.levels < 2) {
+        out->copy_img.push_back(i);
+        continue;
+      }
+      Up0Args u{};
+      u.h0 = pl->p.H;
+      u.w0 = pl->p.W;
+      u.planes = pl->p.C;
+      u.dst = pl->lv[1];
+      u.K = pl->p.K;
+      u.turns = (float)(2.0 / pl->p.T);
+      u.use_tma = 0;  // the input changes per run: plain loads, no per-run tensor map
+      args.push_back(u);
+      counts.push_back(up0_items_h(pl->lv[1], pl->p.C));
+      out->up0_img.push_back(i);
+    }
+    add_stage(kStageUp0, args, counts);
+    if (!args.empty()) out->up0_off = out->stages.back().args_off;
+  }
+  for (int l = 1; l <= maxL - 2; ++l) {
+    std::vector<UpArgs> args;
+    std::vector<int> counts;
+    for (const fllf_plan* pl : plans) {
+      const int L = pl->p.levels;
+      if (l > L - 2) continue;
+      UpArgs u{};
+      u.zmap = pl->maps.z_up[l];
+      u.gmap = pl->maps.g_up[l];
+      u.src = pl->lv[l];
+      u.dst = pl->lv[l + 1];
+      u.planes = pl->p.C;
+      u.K = pl->p.K;
+      u.write_g = (l + 1 <= L - 2) ? 1 : 0;
+      args.push_back(u);
+      counts.push_back(up_items_h(pl->lv[l + 1], pl->p.C, pl->p.K, prec));
+    }
+    add_stage(kStageUp, args, counts);
+  }
+  for (int l = maxL - 2; l >= 1; --l) {
+    std::vector<DownArgs> args;
+    std::vector<int> counts;
+    for (const fllf_plan* pl : plans) {
+      const int L = pl->p.levels;
+      if (l > L - 2) continue;
+      DownArgs d{};
+      d.zmap = pl->maps.z_dn[l + 1];
+      d.emap = pl->maps.e_dn[l + 1];
+      d.fine = pl->lv[l];
+      d.coarse = pl->lv[l + 1];
+      d.a = pl->d_a;
+      d.planes = pl->p.C;
+      d.K = pl->p.K;
+      d.turns = (float)(2.0 / pl->p.T);
+      d.has_e = (l + 1 <= L - 2) ? 1 : 0;
+      args.push_back(d);
+      counts.push_back(combine_tiles_h(pl->lv[l].h, pl->lv[l].w, pl->p.C));
+    }
+    add_stage(kStageDown, args, counts);
+  }
+  {
+    std::vector<Down0Args> args;
+    std::vector<int> counts;
+    for (int idx : out->up0_img) {
+      const fllf_plan* pl = plans[idx];
+      Down0Args d{};
+      d.zmap = pl->maps.z_dn[1];
+      d.emap = pl->maps.e_dn[1];
+      d.h0 = pl->p.H;
+      d.w0 = pl->p.W;
+      d.planes = pl->p.C;
+      d.coarse = pl->lv[1];
+      d.a = pl->d_a;
+      d.K = pl->p.K;
+      d.turns = (float)(2.0 / pl->p.T);
+      d.has_e = pl->p.levels >= 3 ? 1 : 0;
+      args.push_back(d);
+      counts.push_back(combine_tiles_h(pl->p.H, pl->p.W, pl->p.C));
+      out->down0_img.push_back(idx);
+    }
+    add_stage(kStageDown0, args, counts);
+    if (!args.empty()) out->down0_off = out->stages.back().args_off;
+  }
+}
+
+void set_blob_fault(BatchBlob& bb, unsigned* d_fault) {
+  for (const StageRec& st : bb.stages) {
+    unsigned char* base = bb.blob.data() + st.args_off;
+    for (int j = 0; j < st.n; ++j) {
+      switch (st.kind) {
+        case kStageUp0: reinterpret_cast<Up0Args*>(base)[j].fault = d_fault; break;
+        case kStageUp: reinterpret_cast<UpArgs*>(base)[j].fault = d_fault; break;
+        case kStageDown: reinterpret_cast<DownArgs*>(base)[j].fault = d_fault; break;
+        default: reinterpret_cast<Down0Args*>(base)[j].fault = d_fault; break;
+      }
+    }
+  }
+}
+
+void set_blob_io(BatchBlob& bb, const float* const* d_in, float* const* d_out) {
+  if (bb.up0_img.empty()) return;
+  Up0Args* u = reinterpret_cast<Up0Args*>(bb.blob.data() + bb.up0_off);
+  Down0Args* d = reinterpret_cast<Down0Args*>(bb.blob.data() + bb.down0_off);
+  for (size_t j = 0; j < bb.up0_img.size(); ++j) {
+    u[j].I = d_in[bb.up0_img[j]];
+    d[j].I = d_in[bb.down0_img[j]];
+    d[j].O = d_out[bb.down0_img[j]];
+  }
+}
+
+cudaError_t launch_batch_stages(const std::vector<StageRec>& stages, const unsigned char* d_base,
+                                int prec, cudaStream_t s) {
+  for (const StageRec& st : stages) {
+    const cudaError_t e = launch_stage_at(d_base, st, prec, s);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+}  // namespace fllf
+
+using namespace fllf;
+
+namespace {
+
 fllf_status bfail(fllf_status s, const std::string& why) {
   set_last_error(why);
   return s;
 }
+
+struct DeviceScope {
+  int prev = -1;
+  bool ok = false;
+  explicit DeviceScope(int dev) {
+    cudaGetDevice(&prev);
+    ok = cudaSetDevice(dev) == cudaSuccess;
+  }
+  ~DeviceScope() {
+    if (prev >= 0) cudaSetDevice(prev);
+  }
+};
 
 }  // namespace
 
 struct fllf_batch {
   std::vector<fllf_plan*> plans;
   int device = 0, precision = 0;
-  std::vector<StageRec> stages;
-  unsigned char* d_mem = nullptr;
-  size_t mem_bytes = 0;
+  BatchBlob bb;
+  unsigned char* d_mem = nullptr;  // device copy of the tables
   unsigned* d_fault = nullptr;
-  // Per-run tables: level-0 input / output pointers (pinned host mirrors).
-  std::vector<int> up0_img, down0_img;  // image index of each entry
-  size_t up0_off = 0, down0_off = 0;    // device offsets of those tables
-  Up0Args* h_up0 = nullptr;
+  Up0Args* h_up0 = nullptr;        // pinned per-run mirrors of the level-0 tables
   Down0Args* h_down0 = nullptr;
-  std::vector<int> copy_img;            // images with a single level (output = input)
   cudaEvent_t copied = nullptr;
   bool copied_pending = false;
   cudaStream_t cap = nullptr;
@@ -79,33 +259,6 @@ static void free_batch(fllf_batch* b) {
   delete b;
 }
 
-static cudaError_t launch_stage(const fllf_batch* b, const StageRec& st, cudaStream_t s) {
-  const int prec = b->precision;
-  const int* prefix = reinterpret_cast<const int*>(b->d_mem + st.prefix_off);
-  switch (st.kind) {
-    case kUp0: {
-      BatchTable<Up0Args> t{reinterpret_cast<const Up0Args*>(b->d_mem + st.args_off), prefix, st.n, st.total};
-      return prec == FLLF_FP16 ? launch_up0_batch_f16(t, s)
-             : prec == FLLF_BF16 ? launch_up0_batch_bf16(t, s) : launch_up0_batch_f32(t, s);
-    }
-    case kUp: {
-      BatchTable<UpArgs> t{reinterpret_cast<const UpArgs*>(b->d_mem + st.args_off), prefix, st.n, st.total};
-      return prec == FLLF_FP16 ? launch_up_batch_f16(t, s)
-             : prec == FLLF_BF16 ? launch_up_batch_bf16(t, s) : launch_up_batch_f32(t, s);
-    }
-    case kDown: {
-      BatchTable<DownArgs> t{reinterpret_cast<const DownArgs*>(b->d_mem + st.args_off), prefix, st.n, st.total};
-      return prec == FLLF_FP16 ? launch_down_batch_f16(t, s)
-             : prec == FLLF_BF16 ? launch_down_batch_bf16(t, s) : launch_down_batch_f32(t, s);
-    }
-    default: {
-      BatchTable<Down0Args> t{reinterpret_cast<const Down0Args*>(b->d_mem + st.args_off), prefix, st.n, st.total};
-      return prec == FLLF_FP16 ? launch_down0_batch_f16(t, s)
-             : prec == FLLF_BF16 ? launch_down0_batch_bf16(t, s) : launch_down0_batch_f32(t, s);
-    }
-  }
-}
-
 extern "C" {
 
 fllf_status fllf_batch_create(fllf_plan* const* plans, int n, fllf_batch** out) {
@@ -118,171 +271,40 @@ fllf_status fllf_batch_create(fllf_plan* const* plans, int n, fllf_batch** out) 
   for (int i = 1; i < n; ++i)
     if (plans[i]->device != dev || plans[i]->p.precision != prec)
       return bfail(FLLF_EINVAL, "all plans of a batch need the same device and precision");
-  int prev = -1;
-  cudaGetDevice(&prev);
-  if (cudaSetDevice(dev) != cudaSuccess) return bfail(FLLF_ECUDA, "cudaSetDevice failed");
-  struct Restore {
-    int d;
-    ~Restore() {
-      if (d >= 0) cudaSetDevice(d);
-    }
-  } restore{prev};
-
+  DeviceScope scope(dev);
+  if (!scope.ok) return bfail(FLLF_ECUDA, "cudaSetDevice failed");
   fllf_batch* b = new (std::nothrow) fllf_batch();
   if (!b) return bfail(FLLF_ENOMEM, "batch allocation failed");
   b->plans.assign(plans, plans + n);
   b->device = dev;
   b->precision = prec;
-  int maxL = 1;
-  for (auto* p : b->plans) maxL = std::max(maxL, p->p.levels);
-
-  // Build every table in one host blob, then upload it once.
-  std::vector<unsigned char> blob;
-  std::vector<std::vector<int>> prefixes;
-  auto add_stage = [&](int kind, auto& args, std::vector<int>& counts) {
-    if (args.empty()) return;
-    StageRec st{};
-    st.kind = kind;
-    st.n = (int)args.size();
-    std::vector<int> pre(st.n + 1, 0);
-    for (int j = 0; j < st.n; ++j) pre[j + 1] = pre[j] + counts[j];
-    st.total = pre[st.n];
-    st.args_off = push(blob, args.data(), args.size(), 128);
-    st.prefix_off = push(blob, pre.data(), pre.size(), 16);
-    b->stages.push_back(st);
-  };
-  // The fault/status block sits first.
-  std::vector<unsigned> status(64, 0u);
-  const size_t status_off = push(blob, status.data(), status.size(), 256);
-
-  {
-    std::vector<Up0Args> args;
-    std::vector<int> counts;
-    for (int i = 0; i < n; ++i) {
-      const fllf_plan* pl = b->plans[i];
-      if (pl->p.levels < 2) {
-        b->copy_img.push_back(i);
-        continue;
-      }
-      Up0Args u{};
-      u.h0 = pl->p.H;
-      u.w0 = pl->p.W;
-      u.planes = pl->p.C;
-      u.dst = pl->lv[1];
-      u.K = pl->p.K;
-      u.turns = (float)(2.0 / pl->p.T);
-      u.use_tma = 0;
-      args.push_back(u);
-      counts.push_back(up0_items_h(pl->lv[1], pl->p.C));
-      b->up0_img.push_back(i);
-    }
-    add_stage(kUp0, args, counts);
-    if (!args.empty()) b->up0_off = b->stages.back().args_off;
-  }
-  for (int l = 1; l <= maxL - 2; ++l) {
-    std::vector<UpArgs> args;
-    std::vector<int> counts;
-    for (int i = 0; i < n; ++i) {
-      const fllf_plan* pl = b->plans[i];
-      const int L = pl->p.levels;
-      if (l > L - 2) continue;
-      UpArgs u{};
-      u.zmap = pl->maps.z_up[l];
-      u.gmap = pl->maps.g_up[l];
-      u.src = pl->lv[l];
-      u.dst = pl->lv[l + 1];
-      u.planes = pl->p.C;
-      u.K = pl->p.K;
-      u.write_g = (l + 1 <= L - 2) ? 1 : 0;
-      args.push_back(u);
-      counts.push_back(up_items_h(pl->lv[l + 1], pl->p.C, pl->p.K, prec));
-    }
-    add_stage(kUp, args, counts);
-  }
-  for (int l = maxL - 2; l >= 1; --l) {
-    std::vector<DownArgs> args;
-    std::vector<int> counts;
-    for (int i = 0; i < n; ++i) {
-      const fllf_plan* pl = b->plans[i];
-      const int L = pl->p.levels;
-      if (l > L - 2) continue;
-      DownArgs d{};
-      d.zmap = pl->maps.z_dn[l + 1];
-      d.emap = pl->maps.e_dn[l + 1];
-      d.fine = pl->lv[l];
-      d.coarse = pl->lv[l + 1];
-      d.a = pl->d_a;
-      d.planes = pl->p.C;
-      d.K = pl->p.K;
-      d.turns = (float)(2.0 / pl->p.T);
-      d.has_e = (l + 1 <= L - 2) ? 1 : 0;
-      args.push_back(d);
-      counts.push_back(combine_tiles_h(pl->lv[l].h, pl->lv[l].w, pl->p.C));
-    }
-    add_stage(kDown, args, counts);
-  }
-  {
-    std::vector<Down0Args> args;
-    std::vector<int> counts;
-    for (int idx : b->up0_img) {
-      const fllf_plan* pl = b->plans[idx];
-      Down0Args d{};
-      d.zmap = pl->maps.z_dn[1];
-      d.emap = pl->maps.e_dn[1];
-      d.h0 = pl->p.H;
-      d.w0 = pl->p.W;
-      d.planes = pl->p.C;
-      d.coarse = pl->lv[1];
-      d.a = pl->d_a;
-      d.K = pl->p.K;
-      d.turns = (float)(2.0 / pl->p.T);
-      d.has_e = pl->p.levels >= 3 ? 1 : 0;
-      args.push_back(d);
-      counts.push_back(combine_tiles_h(pl->p.H, pl->p.W, pl->p.C));
-      b->down0_img.push_back(idx);
-    }
-    add_stage(kDown0, args, counts);
-    if (!args.empty()) b->down0_off = b->stages.back().args_off;
-  }
-
+  build_batch_blob(std::vector<const fllf_plan*>(plans, plans + n), prec, &b->bb);
   cudaError_t e;
-  b->mem_bytes = blob.size();
-  if ((e = cudaMalloc(&b->d_mem, b->mem_bytes)) != cudaSuccess) {
+  if ((e = cudaMalloc(&b->d_mem, b->bb.blob.size())) != cudaSuccess) {
     cudaGetLastError();
     b->d_mem = nullptr;
     free_batch(b);
     return bfail(FLLF_ENOMEM, "batch table allocation failed");
   }
-  b->d_fault = reinterpret_cast<unsigned*>(b->d_mem + status_off);
-  // Point every argument block's fault word at the batch status block.
-  for (const StageRec& st : b->stages) {
-    for (int j = 0; j < st.n; ++j) {
-      unsigned char* base = blob.data() + st.args_off;
-      switch (st.kind) {
-        case kUp0: reinterpret_cast<Up0Args*>(base)[j].fault = b->d_fault; break;
-        case kUp: reinterpret_cast<UpArgs*>(base)[j].fault = b->d_fault; break;
-        case kDown: reinterpret_cast<DownArgs*>(base)[j].fault = b->d_fault; break;
-        default: reinterpret_cast<Down0Args*>(base)[j].fault = b->d_fault; break;
-      }
-    }
-  }
-  if ((e = cudaMemcpy(b->d_mem, blob.data(), b->mem_bytes, cudaMemcpyHostToDevice)) != cudaSuccess) {
+  b->d_fault = reinterpret_cast<unsigned*>(b->d_mem + b->bb.status_off);
+  set_blob_fault(b->bb, b->d_fault);
+  if ((e = cudaMemcpy(b->d_mem, b->bb.blob.data(), b->bb.blob.size(), cudaMemcpyHostToDevice)) !=
+      cudaSuccess) {
     free_batch(b);
     return bfail(FLLF_ECUDA, std::string("batch table upload: ") + cudaGetErrorString(e));
   }
-  const size_t nu = std::max<size_t>(1, b->up0_img.size());
+  const size_t nu = std::max<size_t>(1, b->bb.up0_img.size());
   if (cudaMallocHost(&b->h_up0, sizeof(Up0Args) * nu) != cudaSuccess ||
       cudaMallocHost(&b->h_down0, sizeof(Down0Args) * nu) != cudaSuccess) {
     cudaGetLastError();
     free_batch(b);
     return bfail(FLLF_ENOMEM, "pinned host tables");
   }
-  if (!b->up0_img.empty()) {
-    std::copy(reinterpret_cast<const Up0Args*>(blob.data() + b->up0_off),
-              reinterpret_cast<const Up0Args*>(blob.data() + b->up0_off) + b->up0_img.size(), b->h_up0);
-    std::copy(reinterpret_cast<const Down0Args*>(blob.data() + b->down0_off),
-              reinterpret_cast<const Down0Args*>(blob.data() + b->down0_off) + b->down0_img.size(),
-              b->h_down0);
+  if (!b->bb.up0_img.empty()) {
+    const Up0Args* u = reinterpret_cast<const Up0Args*>(b->bb.blob.data() + b->bb.up0_off);
+    const Down0Args* d = reinterpret_cast<const Down0Args*>(b->bb.blob.data() + b->bb.down0_off);
+    std::copy(u, u + b->bb.up0_img.size(), b->h_up0);
+    std::copy(d, d + b->bb.down0_img.size(), b->h_down0);
   }
   if (cudaEventCreateWithFlags(&b->copied, cudaEventDisableTiming) != cudaSuccess ||
       cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) != cudaSuccess) {
@@ -295,11 +317,8 @@ fllf_status fllf_batch_create(fllf_plan* const* plans, int n, fllf_batch** out) 
 
 fllf_status fllf_batch_destroy(fllf_batch* b) {
   if (!b) return FLLF_OK;
-  int prev = -1;
-  cudaGetDevice(&prev);
-  cudaSetDevice(b->device);
+  DeviceScope scope(b->device);
   free_batch(b);
-  if (prev >= 0) cudaSetDevice(prev);
   return FLLF_OK;
 }
 
@@ -313,52 +332,44 @@ fllf_status fllf_batch_run(fllf_batch* b, const float* const* d_in, float* const
     const char *x = reinterpret_cast<const char*>(d_in[i]), *y = reinterpret_cast<const char*>(d_out[i]);
     if (x < y + bytes && y < x + bytes) return bfail(FLLF_EINVAL, "input and output buffers overlap");
   }
-  int prev = -1;
-  cudaGetDevice(&prev);
-  if (cudaSetDevice(b->device) != cudaSuccess) return bfail(FLLF_ECUDA, "cudaSetDevice failed");
-  struct Restore {
-    int d;
-    ~Restore() {
-      if (d >= 0) cudaSetDevice(d);
-    }
-  } restore{prev};
+  DeviceScope scope(b->device);
+  if (!scope.ok) return bfail(FLLF_ECUDA, "cudaSetDevice failed");
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   cudaError_t e;
   // The pinned mirrors may still feed the previous run's copies.
   if (b->copied_pending && (e = cudaEventSynchronize(b->copied)) != cudaSuccess)
     return bfail(FLLF_ECUDA, std::string("batch copy wait: ") + cudaGetErrorString(e));
-  for (size_t j = 0; j < b->up0_img.size(); ++j) {
-    b->h_up0[j].I = d_in[b->up0_img[j]];
-    b->h_down0[j].I = d_in[b->down0_img[j]];
-    b->h_down0[j].O = d_out[b->down0_img[j]];
+  const BatchBlob& bb = b->bb;
+  for (size_t j = 0; j < bb.up0_img.size(); ++j) {
+    b->h_up0[j].I = d_in[bb.up0_img[j]];
+    b->h_down0[j].I = d_in[bb.down0_img[j]];
+    b->h_down0[j].O = d_out[bb.down0_img[j]];
   }
-  if (!b->up0_img.empty()) {
-    if ((e = cudaMemcpyAsync(b->d_mem + b->up0_off, b->h_up0, sizeof(Up0Args) * b->up0_img.size(),
+  if (!bb.up0_img.empty()) {
+    if ((e = cudaMemcpyAsync(b->d_mem + bb.up0_off, b->h_up0, sizeof(Up0Args) * bb.up0_img.size(),
                              cudaMemcpyHostToDevice, s)) != cudaSuccess ||
-        (e = cudaMemcpyAsync(b->d_mem + b->down0_off, b->h_down0,
-                             sizeof(Down0Args) * b->down0_img.size(), cudaMemcpyHostToDevice, s)) !=
+        (e = cudaMemcpyAsync(b->d_mem + bb.down0_off, b->h_down0,
+                             sizeof(Down0Args) * bb.down0_img.size(), cudaMemcpyHostToDevice, s)) !=
             cudaSuccess)
       return bfail(FLLF_ECUDA, std::string("batch table update: ") + cudaGetErrorString(e));
   }
   if ((e = cudaEventRecord(b->copied, s)) != cudaSuccess)
     return bfail(FLLF_ECUDA, std::string("batch event: ") + cudaGetErrorString(e));
   b->copied_pending = true;
-  for (int i : b->copy_img) {
+  for (int i : bb.copy_img) {
     const fllf_params& p = b->plans[i]->p;
     if ((e = cudaMemcpyAsync(d_out[i], d_in[i], sizeof(float) * (size_t)p.H * p.W * p.C,
                              cudaMemcpyDeviceToDevice, s)) != cudaSuccess)
       return bfail(FLLF_ECUDA, std::string("single-level copy: ") + cudaGetErrorString(e));
   }
-  if (b->stages.empty()) return FLLF_OK;
+  if (bb.stages.empty()) return FLLF_OK;
   if (!b->graph) {
-    // Capture the launch sequence once; tables are read from device memory,
-    // so the graph stays valid for every later run.
+    // Capture the launch sequence once; the tables are read from device
+    // memory, so the graph stays valid for every later run.
     cudaGraph_t g = nullptr;
     if ((e = cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeRelaxed)) != cudaSuccess)
       return bfail(FLLF_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e));
-    cudaError_t le = cudaSuccess;
-    for (const StageRec& st : b->stages)
-      if ((le = launch_stage(b, st, b->cap)) != cudaSuccess) break;
+    const cudaError_t le = launch_batch_stages(bb.stages, b->d_mem, b->precision, b->cap);
     e = cudaStreamEndCapture(b->cap, &g);
     if (le != cudaSuccess || e != cudaSuccess) {
       if (g) cudaGraphDestroy(g);
@@ -379,8 +390,9 @@ fllf_status fllf_batch_run(fllf_batch* b, const float* const* d_in, float* const
 
 fllf_status fllf_batch_check(fllf_batch* b) {
   if (!b) return bfail(FLLF_EINVAL, "batch is NULL");
+  DeviceScope scope(b->device);
   unsigned f = 0;
-  cudaError_t e = cudaMemcpy(&f, b->d_fault, sizeof(unsigned), cudaMemcpyDeviceToHost);
+  const cudaError_t e = cudaMemcpy(&f, b->d_fault, sizeof(unsigned), cudaMemcpyDeviceToHost);
   if (e != cudaSuccess) return bfail(FLLF_ECUDA, std::string("fault word read: ") + cudaGetErrorString(e));
   if (f) {
     cudaMemset(b->d_fault, 0, 256);

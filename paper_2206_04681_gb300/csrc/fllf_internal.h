@@ -81,6 +81,30 @@ cudaError_t enqueue_path(const fllf_params& p, const std::vector<Level>& lv, con
                          const float* d_a, unsigned* fault, const float* d_in, float* d_out,
                          cudaStream_t s, StageHook* hook = nullptr);
 
+// ---- batched argument tables (shared by batches and the server) ---------------
+enum BatchStageKind { kStageUp0 = 0, kStageUp = 1, kStageDown = 2, kStageDown0 = 3 };
+struct StageRec {
+  int kind;
+  size_t args_off;    // byte offset of the argument blocks in the table image
+  size_t prefix_off;  // byte offset of the work-item prefix sums
+  int n, total;
+};
+struct BatchBlob {
+  std::vector<unsigned char> blob;  // host image of the device tables
+  std::vector<StageRec> stages;     // launch order
+  std::vector<int> up0_img, down0_img, copy_img;
+  size_t up0_off = 0, down0_off = 0, status_off = 0;
+};
+// Argument tables for `plans` (same storage precision `prec`).
+void build_batch_blob(const std::vector<const fllf_plan*>& plans, int prec, BatchBlob* out);
+// Points every argument block's fault word at d_fault.
+void set_blob_fault(BatchBlob& bb, unsigned* d_fault);
+// Writes the level-0 input / output pointers of each image.
+void set_blob_io(BatchBlob& bb, const float* const* d_in, float* const* d_out);
+// Enqueues the batched stage kernels reading the tables uploaded at d_base.
+cudaError_t launch_batch_stages(const std::vector<StageRec>& stages, const unsigned char* d_base,
+                                int prec, cudaStream_t s);
+
 }  // namespace fllf
 
 // A filter plan (opaque to callers): parameters, float32 coefficients on the
