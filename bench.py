@@ -42,8 +42,16 @@ def parse():
     ap.add_argument("--precision", choices=["fp32", "fp16", "bf16"], default="fp32")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
-    ap.add_argument("--workload", choices=["uhd", "batch"], default="uhd",
-                    help="uhd: the 4K RGB headline; batch: 64 mixed images, batched vs looped")
+    ap.add_argument("--workload", choices=["uhd", "batch", "serve"], default="uhd",
+                    help="uhd: the 4K RGB headline (plus a short served stream); batch: 64 mixed "
+                         "images, batched vs looped; serve: Poisson request streams")
+    ap.add_argument("--serve-seconds", type=float, default=None,
+                    help="length of each served stream (default 30 s; 4 s in the uhd line)")
+    ap.add_argument("--serve-rates", type=str, default=None,
+                    help="comma-separated arrival rates in requests/s, or max for a backlog "
+                         "(default 50,100,200,400,max)")
+    ap.add_argument("--serve-precision", choices=["fp32", "fp16", "bf16"], default="fp16")
+    ap.add_argument("--no-serve", action="store_true")
     return ap.parse_args()
 
 
@@ -381,6 +389,9 @@ def run_ours(args):
             ms = time_precision(pkg, torch, cfg, prec, frames, min(args.steps, 500), 10, stream, device)
             variants[prec] = {"ms_per_step": ms, "value": pixels / (ms * 1e-3) / 1e6}
         line["precision_variants"] = variants
+    if rank == 0 and world == 1 and not args.no_serve:
+        line["serving"] = serving_summary(pkg, torch, device, args.serve_precision,
+                                          seconds=args.serve_seconds or 4.0)
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_oracle_sample()
     if rank == 0:
@@ -462,6 +473,192 @@ def run_batch(args):
     print(json.dumps(line), flush=True)
     return 0
 
+SERVE = dict(rates=(50, 100, 200, 400, "max"), seconds=30.0, seed=5, budget=120 << 30,
+             max_slots=64, max_queue=256, max_waves=3, psnr_sample=32)
+
+
+def _oracle_psnr_job(job):
+    """Float64 oracle on one served request's input; returns (PSNR dB, max-abs)."""
+    import numpy as np
+    import oracle
+    x, y, levels, K, m, sigma_r, T = job
+    a = oracle.coeffs_quadrature(m, sigma_r, T, K)
+    ref = oracle.fourier_llf(x.astype(np.float64), levels, a, T)
+    err = y.astype(np.float64) - ref
+    mse = float(np.mean(err ** 2))
+    return (float("inf") if mse == 0 else 10 * np.log10(1.0 / mse)), float(np.max(np.abs(err)))
+
+
+def serve_canvas(torch, device):
+    """8192 x 8192 x 3 synthetic canvas on the device (a 4096^2 frame, 40
+    polygons, mirrored 2 x 2); requests are cropped from it."""
+    from paper_2206_04681_gb300.synth import synth_image
+    img = torch.from_numpy(synth_image(4096, 4096, 3, 40, seed=SERVE["seed"])).to(device)
+    top = torch.cat([img, img.flip(2)], 2)
+    return torch.cat([top, top.flip(1)], 1).contiguous()
+
+
+def serve_stream(pkg, torch, server, canvas, reqs, precision, keep, saturate=False):
+    """Replays an arrival schedule in real time against the server.
+
+    At each arrival the client crops its image from the canvas into a fresh
+    device buffer and submits it; finished tickets are polled without
+    blocking.  With `saturate`, every request is due at once and a full
+    queue (FLLF_EBUSY) makes the client wait and retry instead of dropping
+    the request.  Returns client-side latencies (scheduled arrival -> poll
+    OK), the count of rejected submissions and the kept (input, output)
+    pairs."""
+    import numpy as np
+    rng = np.random.default_rng(SERVE["seed"] + 1)
+    copy_stream = torch.cuda.Stream()
+    inflight, kept, lat, rejected = {}, {}, [], 0
+    pkg.fllf_server_stats_reset(server)
+    t0 = time.perf_counter()
+    i = 0
+    while i < len(reqs) or inflight:
+        now = time.perf_counter() - t0
+        while i < len(reqs) and (saturate or reqs[i]["t"] <= now):
+            if saturate and len(inflight) >= 96:   # client window: bounds the buffers held
+                break
+            r = reqs[i]
+            H, W, C = r["H"], r["W"], r["C"]
+            y0 = int(rng.integers(0, canvas.shape[1] - H + 1))
+            x0 = int(rng.integers(0, canvas.shape[2] - W + 1))
+            with torch.cuda.stream(copy_stream):
+                x = canvas[:C, y0:y0 + H, x0:x0 + W].contiguous()
+                y = torch.empty_like(x)
+            copy_stream.synchronize()
+            p = pkg.make_params(H, W, C, r["levels"], r["K"], r["m"], r["sigma_r"], r["T"], precision)
+            try:
+                t = pkg.fllf_server_submit(server, p, x.data_ptr(), y.data_ptr())
+                inflight[t] = (i, x, y)
+            except pkg.FllfError as e:
+                if e.status != pkg.FLLF_EBUSY:
+                    raise
+                if saturate:
+                    break           # queue full: poll, then retry this request
+                rejected += 1
+            i += 1
+        for t in list(inflight):
+            if pkg.fllf_server_poll(server, t, 0) == pkg.FLLF_OK:
+                idx, x, y = inflight.pop(t)
+                lat.append((time.perf_counter() - t0 - (0.0 if saturate else reqs[idx]["t"])) * 1e3)
+                if idx in keep:
+                    kept[idx] = (x.cpu().numpy(), y.cpu().numpy())
+        if saturate:
+            nxt = 5e-5
+        else:
+            nxt = reqs[i]["t"] - (time.perf_counter() - t0) if i < len(reqs) else 1.0
+        time.sleep(min(max(nxt, 0.0), 2e-4))
+    return lat, rejected, kept
+
+
+def serve_warmup(pkg, torch, server, canvas, precision):
+    """Untimed requests first: module loading, first-touch of the pool and
+    the caching allocator's blocks stay out of the measured latencies."""
+    from paper_2206_04681_gb300.synth import request_stream
+    serve_stream(pkg, torch, server, canvas, request_stream(200, 0.3, seed=SERVE["seed"] + 100),
+                 precision, set(), saturate=True)
+
+
+def serve_rate(pkg, torch, server, canvas, rate, seconds, precision, n_check, pool):
+    """One Poisson stream at `rate` requests/s (rate "max": the same stream at
+    400/s submitted as a backlog, to measure capacity); a JSON-ready summary."""
+    import numpy as np
+    from paper_2206_04681_gb300.synth import request_stream
+    saturate = rate == "max"
+    reqs = request_stream(400 if saturate else rate, seconds, seed=SERVE["seed"])
+    order = sorted(range(len(reqs)), key=lambda j: reqs[j]["H"] * reqs[j]["W"] * reqs[j]["C"])
+    keep = set(order[:n_check])
+    serve_warmup(pkg, torch, server, canvas, precision)
+    lat, rejected, kept = serve_stream(pkg, torch, server, canvas, reqs, precision, keep, saturate)
+    st = pkg.fllf_server_stats_get(server)
+    offered = None if saturate else sum(r["H"] * r["W"] for r in reqs) / seconds / 1e6
+    out = {"rate_per_s": rate, "seconds": seconds, "requests": len(reqs), "rejected": rejected,
+           "completed": st["completed"], "mpixel_per_s": st["mpixel_per_s"],
+           "offered_mpixel_per_s": offered,
+           "latency_ms": {"p50": st["p50_ms"], "p99": st["p99_ms"], "mean": st["mean_ms"],
+                          "max": st["max_ms"], "measured": "submit -> completion (server)"},
+           "client_latency_ms": {"p50": float(np.percentile(lat, 50)) if lat else None,
+                                 "p99": float(np.percentile(lat, 99)) if lat else None,
+                                 "measured": "scheduled arrival -> poll OK (client)"},
+           "waves": st["waves"], "max_active": st["max_active"],
+           "pool_peak_gb": st["pool_peak_bytes"] / 1e9}
+    if kept and pool is not None:
+        jobs = [(kept[j][0], kept[j][1], reqs[j]["levels"], reqs[j]["K"], reqs[j]["m"],
+                 reqs[j]["sigma_r"], reqs[j]["T"]) for j in sorted(kept)]
+        res = pool.map(_oracle_psnr_job, jobs)
+        out["psnr_vs_fp64"] = {"requests": len(res), "min_db": min(r[0] for r in res),
+                               "max_abs": max(r[1] for r in res),
+                               "sample": f"the {len(res)} smallest requests of the stream"}
+    return out
+
+
+def make_server(pkg, device):
+    return pkg.fllf_server_create(SERVE["budget"], SERVE["max_slots"], SERVE["max_queue"],
+                                  SERVE["max_waves"], device)
+
+
+def oracle_pool():
+    """Process pool for the oracle checks (spawned, so it is safe after CUDA use)."""
+    import multiprocessing as mp
+    return mp.get_context("spawn").Pool(max(1, min(16, os.cpu_count() or 1)))
+
+
+def serving_summary(pkg, torch, device, precision, rate=200, seconds=4.0, n_check=8):
+    """A short served stream for the headline line."""
+    pool = oracle_pool()
+    server = make_server(pkg, device)
+    try:
+        canvas = serve_canvas(torch, device)
+        out = serve_rate(pkg, torch, server, canvas, rate, seconds, precision, n_check, pool)
+    finally:
+        pkg.fllf_server_destroy(server)
+        pool.close()
+    out["pyramid_storage"] = precision
+    out["budget_gb"] = SERVE["budget"] / 2 ** 30
+    return out
+
+
+def run_serve(args):
+    """Poisson streams of mixed requests (sides 512..8192, C 1 or 3, K 4/8/16,
+    random remap) through the continuous-batching server, one per rate."""
+    import torch
+    import paper_2206_04681_gb300 as pkg
+    from paper_2206_04681_gb300 import build
+    pool = oracle_pool()
+    build.build_library()
+    torch.cuda.set_device(0)
+    rates = ([r if r == "max" else float(r) for r in args.serve_rates.split(",")]
+             if args.serve_rates else list(SERVE["rates"]))
+    seconds = args.serve_seconds or SERVE["seconds"]
+    server = make_server(pkg, 0)
+    clocks = ClockSampler(0)
+    try:
+        canvas = serve_canvas(torch, 0)
+        clocks.start()
+        runs = [serve_rate(pkg, torch, server, canvas, r, seconds, args.serve_precision,
+                           SERVE["psnr_sample"], pool) for r in rates]
+        clk = clocks.stop()
+    finally:
+        pkg.fllf_server_destroy(server)
+        pool.close()
+    best = max(runs, key=lambda r: r["mpixel_per_s"])   # the backlog run: capacity
+    line = {"metric": "Mpixel/s and p50/p99 ms, served Fourier LLF requests (Poisson arrivals)",
+            "value": best["mpixel_per_s"], "unit": UNIT, "n_gpus": 1, "steps": len(runs),
+            "warmup": 0, "ms_per_step": None, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "served_poisson_512_8192", "rates": list(rates),
+                       "seconds_per_rate": seconds, "pyramid_storage": args.serve_precision,
+                       "budget_gb": SERVE["budget"] / 2 ** 30, "max_slots": SERVE["max_slots"],
+                       "max_waves": SERVE["max_waves"],
+                       "value": "highest Mpixel/s over the runs (the backlog run measures capacity)",
+                       "requests": "sides log-uniform 512..8192, aspect 0.5..2, C 1 or 3, "
+                                   "K 4/8/16, sigma_r U[0.05,0.4], m U[0.5,4], T 2"},
+            "runs": runs, "clocks": clk}
+    print(json.dumps(line), flush=True)
+    return 0
+
 
 def main():
     args = parse()
@@ -469,6 +666,8 @@ def main():
         return run_reference(args)
     if args.workload == "batch":
         return run_batch(args)
+    if args.workload == "serve":
+        return run_serve(args)
     return run_ours(args)
 
 

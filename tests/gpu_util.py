@@ -3,6 +3,7 @@ device memory and compare with the float64 oracle."""
 
 import numpy as np
 
+import oracle as o
 import paper_2206_04681_gb300 as pkg
 
 
@@ -23,9 +24,9 @@ def gpu_filter(img, levels, K, m, sigma_r, T=2.0, precision="fp32", runs=1):
             pkg.run_tensor(plan, x, y)
             torch.cuda.synchronize()
             outs.append(y.cpu().numpy())
-        a = np.array(pkg.fllf_plan_coeffs(plan))
     finally:
         pkg.fllf_plan_destroy(plan)
+    a = np.array(o.coeffs_quadrature(m, sigma_r, T, K))  # the oracle's own a_k
     return (outs[0] if runs == 1 else outs), a
 
 

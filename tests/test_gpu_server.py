@@ -94,7 +94,7 @@ def test_served_results_match_oracle():
         reqs = [_request(c, 300 + i, "fp32") for i, c in enumerate(MIX[:6])]
         _serve(server, reqs)
         for (p, img, x, y) in reqs:
-            a = np.array(pkg.fllf_coeffs(p))
+            a = np.array(o.coeffs_quadrature(p.m, p.sigma_r, p.T, p.K))
             ref = o.fourier_llf(img.astype(np.float64), p.levels, a, 2.0)
             assert float(np.max(np.abs(y.cpu().numpy() - ref))) <= 1e-4
     finally:
