@@ -402,12 +402,13 @@ def run_ours(args):
 
 
 def kernel_revision():
-    """Hash of the CUDA sources, to tell whether stored ncu traffic is current."""
+    """Hash of the kernel sources and of the launch path, to tell whether
+    stored ncu traffic still describes the kernels that run."""
     import hashlib
     h = hashlib.sha1()
     csrc = os.path.join(ROOT, "paper_2206_04681_gb300", "csrc")
     for name in sorted(os.listdir(csrc)):
-        if name.endswith((".cu", ".cuh", ".inl", ".h")):
+        if name.startswith(("fllf_kernels", "fllf_device", "fllf_path")):
             h.update(open(os.path.join(csrc, name), "rb").read())
     return h.hexdigest()[:12]
 
