@@ -147,9 +147,15 @@ constexpr int kUpIR = 2 * kUpTH + 3;      // fine input rows (31)
 constexpr int kUpIPX = 2 * kUpRun + 3;    // fine inputs per item (11)
 constexpr int kUpItems = kUpIR * kUpSeg;  // 248 horizontal items
 constexpr int kUpVRows = kUpTH / 2;       // coarse rows per vertical thread (7)
-constexpr int kUpCS = 34;                 // staged rows per column (odd multiple of 16 B)
+constexpr int kUpCS = 36;                 // staged rows per column (36 x 8 B: 2 mod 8 bank groups)
 constexpr int kUpIW = 72;                 // staged input columns (box from 2*X1-4, 16-B aligned)
 static_assert(kUpItems <= kThreads, "REDUCE items exceed the block");
+static_assert(kUpSeg * 32 == kThreads && kUpIR <= 32, "up0 items: one warp per run segment, one lane per row");
+static_assert(kKC * 2 * kUpRun == 32 && kUpRun * kUpVRows <= 32, "up0 vertical pass: one warp per segment");
+static_assert(2 * kUpVRows + 2 * (kUpVRows + 2) <= kUpCS && 4 * (kUpVRows - 1) + 8 <= kUpCS &&
+                  kUpIR <= kUpCS,
+              "up0 vertical reads stay in the staged column");
+static_assert(2 * kUpRun * (kUpSeg - 1) + 16 <= kUpIW, "up0 run reads stay inside the staged row");
 static_assert(kKC * kUpTW * 2 == kThreads, "vertical REDUCE mapping");
 
 // up (levels >= 1): 30 x 16 coarse outputs per tile.

@@ -121,13 +121,27 @@ __device__ __forceinline__ bool stage_up0(Res res, int total, unsigned char* sme
       __syncthreads();
     }
 
-    const bool item = tid < kUpItems;
-    const int r = tid % kUpIR, s = tid / kUpIR;
+    // Warp s owns coarse columns 4s .. 4s+3 of the tile, and does both passes
+    // for them; only a warp sync separates the passes.
+    // Horizontal pass: lane r takes fine row r of the run segment. The run's 11
+    // inputs (columns 8s+2 .. 8s+12 of the staged row) are read as four 16-byte
+    // words: rows are 72 floats apart, so scalar reads of consecutive rows
+    // would hit the same 4 banks.
+    const int r = tid & 31, s = tid >> 5;
+    const bool item = r < kUpIR;
+    float2* hzw = hz + s * (kKC * kUpRun * kUpCS);  // [order][column][fine row]
+    float* hgw = hg + s * (kUpRun * kUpCS);          // [column][fine row]
     float2 zc[kUpIPX], zp[kUpIPX], tc[kUpIPX];
     if (item) {
       float v[kUpIPX];
-#pragma unroll
-      for (int j = 0; j < kUpIPX; ++j) v[j] = it[r * kUpIW + 2 + 2 * kUpRun * s + j];
+      {
+        const float4* row = reinterpret_cast<const float4*>(it + r * kUpIW + 2 * kUpRun * s);
+        const float4 q0 = row[0], q1 = row[1], q2 = row[2], q3 = row[3];
+        v[0] = q0.z; v[1] = q0.w;
+        v[2] = q1.x; v[3] = q1.y; v[4] = q1.z; v[5] = q1.w;
+        v[6] = q2.x; v[7] = q2.y; v[8] = q2.z; v[9] = q2.w;
+        v[10] = q3.x;
+      }
 #pragma unroll
       for (int j = 0; j < kUpIPX; ++j) {
         const float2 z = cos_sin_turns(a.turns * v[j]);
@@ -137,16 +151,23 @@ __device__ __forceinline__ bool stage_up0(Res res, int total, unsigned char* sme
       }
 #pragma unroll
       for (int q = 0; q < kUpRun; ++q)
-        hg[(kUpRun * s + q) * kUpCS + r] =
-            tap5(v[2 * q], v[2 * q + 1], v[2 * q + 2], v[2 * q + 3], v[2 * q + 4]);
+        hgw[q * kUpCS + r] = tap5(v[2 * q], v[2 * q + 1], v[2 * q + 2], v[2 * q + 3], v[2 * q + 4]);
     }
+    // Every warp has read its inputs: the buffer may be refilled (the TMA
+    // load of the tile after next is issued after this barrier).
+    __syncthreads();
+    // Vertical pass: lane = (order kk, row group grp, column q). With a column
+    // stride of 36 float2 the 8 lanes of a quarter-warp read 8 distinct
+    // 16-byte bank groups.
+    const int vq = tid & 3, vgrp = (tid >> 2) & 1, vkk = (tid >> 3) & 3;
+    const int xo = X1 + kUpRun * s + vq;
     for (int ch = 0; ch < nch; ++ch) {
       if (item) {
 #pragma unroll
         for (int kk = 0; kk < kKC; ++kk) {
 #pragma unroll
           for (int q = 0; q < kUpRun; ++q)
-            hz[(kk * kUpTW + kUpRun * s + q) * kUpCS + r] =
+            hzw[(kk * kUpRun + q) * kUpCS + r] =
                 tap5(zc[2 * q], zc[2 * q + 1], zc[2 * q + 2], zc[2 * q + 3], zc[2 * q + 4]);
 #pragma unroll
           for (int j = 0; j < kUpIPX; ++j) {
@@ -156,16 +177,14 @@ __device__ __forceinline__ bool stage_up0(Res res, int total, unsigned char* sme
           }
         }
       }
-      __syncthreads();
+      __syncwarp();
       {
-        // vertical: thread (order kk, column col, row group grp)
-        const int kk = tid / (2 * kUpTW), grp = (tid / kUpTW) & 1, col = tid % kUpTW;
-        const int k = ch * kKC + kk, x = X1 + col;
-        if (k < a.K && x < a.dst.w) {
+        const int k = ch * kKC + vkk;
+        if (k < a.K && xo < a.dst.w) {
           CT* Zk = reinterpret_cast<CT*>(a.dst.Z) + (long long)pl * a.dst.zplane +
-                   (long long)k * a.dst.zk + x;
+                   (long long)k * a.dst.zk + xo;
           const float4* p =
-              reinterpret_cast<const float4*>(hz + (kk * kUpTW + col) * kUpCS + 2 * kUpVRows * grp);
+              reinterpret_cast<const float4*>(hzw + (vkk * kUpRun + vq) * kUpCS + 2 * kUpVRows * vgrp);
           float2 w[2 * kUpVRows + 4];
 #pragma unroll
           for (int u = 0; u < kUpVRows + 2; ++u) {
@@ -175,28 +194,29 @@ __device__ __forceinline__ bool stage_up0(Res res, int total, unsigned char* sme
           }
 #pragma unroll
           for (int j = 0; j < kUpVRows; ++j) {
-            const int y = Y1 + grp * kUpVRows + j;
+            const int y = Y1 + vgrp * kUpVRows + j;
             if (y < a.dst.h)
               Cplx<S>::st(Zk + (long long)y * a.dst.pitch,
                           mul2(splat(1.f / 256.f),
                                tap5(w[2 * j], w[2 * j + 1], w[2 * j + 2], w[2 * j + 3], w[2 * j + 4])));
           }
         }
-        if (ch == 0 && tid < 2 * kUpTW) {
-          const int g2 = tid / kUpTW, c2 = tid % kUpTW, xg = X1 + c2;
+        if (ch == 0 && tid % 32 < kUpRun * kUpVRows) {
+          // guide: lane = (column gq, pair of coarse rows gp)
+          const int gq = (tid & 31) % kUpRun, gp = (tid & 31) / kUpRun, xg = X1 + kUpRun * s + gq;
           if (xg < a.dst.w) {
             float* Gp = a.dst.G + (long long)pl * a.dst.gplane + xg;
-            const float2* p = reinterpret_cast<const float2*>(hg + c2 * kUpCS + 2 * kUpVRows * g2);
-            float w[2 * kUpVRows + 4];
+            const float2* p = reinterpret_cast<const float2*>(hgw + gq * kUpCS + 4 * gp);
+            float w[8];  // staged rows 4gp .. 4gp+7 (6 used for the two outputs' taps + 1)
 #pragma unroll
-            for (int u = 0; u < kUpVRows + 2; ++u) {
+            for (int u = 0; u < 4; ++u) {
               const float2 q2 = p[u];
               w[2 * u] = q2.x;
               w[2 * u + 1] = q2.y;
             }
 #pragma unroll
-            for (int j = 0; j < kUpVRows; ++j) {
-              const int y = Y1 + g2 * kUpVRows + j;
+            for (int j = 0; j < 2; ++j) {
+              const int y = Y1 + 2 * gp + j;
               if (y < a.dst.h)
                 Gp[(long long)y * a.dst.pitch] =
                     (1.f / 256.f) * tap5(w[2 * j], w[2 * j + 1], w[2 * j + 2], w[2 * j + 3], w[2 * j + 4]);
@@ -204,7 +224,7 @@ __device__ __forceinline__ bool stage_up0(Res res, int total, unsigned char* sme
           }
         }
       }
-      __syncthreads();
+      __syncwarp();
     }
   }
   return true;
