@@ -96,6 +96,7 @@ void build_batch_blob(const std::vector<const fllf_plan*>& plans, int prec, Batc
         continue;
       }
       Up0Args u{};
+      u.a = pl->d_a;
       u.h0 = pl->p.H;
       u.w0 = pl->p.W;
       u.planes = pl->p.C;

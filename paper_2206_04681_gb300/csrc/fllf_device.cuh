@@ -71,6 +71,7 @@ struct Level {
 struct Up0Args {
   CUtensorMap imap;     // level-0 input (valid when use_tma)
   const float* I;       // level-0 input planes, pitch w0, plane stride h0*w0
+  const float* a;       // a_1..a_K (float32): order k is stored as a_k Z_{1,k}
   int h0, w0, planes;
   Level dst;            // level 1
   int K;
@@ -112,6 +113,24 @@ struct Down0Args {
   int K;
   float turns;
   int has_e;            // E_1 exists (levels >= 3)
+  unsigned* fault;
+};
+
+// Fused combine of levels 1 and 0 (levels >= 3): the level-1 combine runs on
+// the window of level-1 cells that the level-0 EXPAND reads, so E_1 stays in
+// shared memory.
+struct Down10Args {
+  CUtensorMap z1map;    // Z_1 as the coarse window of level 0 (36 x 18 x kKC)
+  CUtensorMap g1map;    // G_1 on the same window (36 x 18)
+  CUtensorMap z2map;    // Z_2 window of the level-1 cells (20 x 11 x kKC)
+  CUtensorMap e2map;    // E_2 on the level-2 window (20 x 11)
+  const float* I;       // level-0 input, pitch w0
+  float* O;             // level-0 output, pitch w0
+  int h0, w0, planes;
+  Level l1, l2;         // levels 1 and 2
+  int K;
+  float turns;
+  int has_e2;           // E_2 exists (levels >= 4)
   unsigned* fault;
 };
 
@@ -171,6 +190,14 @@ constexpr int kDnCW = 36;                 // staged coarse columns (34 used)
 constexpr int kDnCH = kDnOH / 2 + 2;      // staged coarse rows (18)
 constexpr int kDnX0 = 6;                  // fine tile origin offset
 static_assert((kDnOW / 4) * (kDnOH / 2) == kThreads, "combine thread mapping");
+// fused level-1/level-0 combine: the level-2 window of the level-1 cells
+// (origin (cx0/2 - 2, (cy0 - 1)/2), 19 x 11 used) and the 2 x 2 cell blocks
+// of the level-1 threads over the 34 x 18 used level-1 cells.
+constexpr int kD2W = 20, kD2H = 11;
+constexpr int kB1X = 17, kB1Y = 9;
+static_assert(kB1X * kB1Y <= kThreads && 2 * kB1X == kDnCW - 2 && 2 * kB1Y == kDnCH,
+              "level-1 blocks cover the used window");
+static_assert(kB1X + 2 < kD2W && kB1Y + 1 < kD2H, "level-1 blocks read inside the level-2 window");
 
 __host__ __device__ constexpr int cdiv(int a, int b) { return (a + b - 1) / b; }
 __host__ __device__ constexpr size_t align128(size_t x) { return (x + 127) & ~size_t(127); }
@@ -196,6 +223,14 @@ struct Smem {
   static constexpr size_t dn_e = align128(sizeof(float) * kDnCH * kDnCW);
   static constexpr size_t dn_buf = dn_z + dn_e;
   static constexpr size_t dn = 2 * dn_buf + 64;
+  // fused level-1/level-0 combine
+  static constexpr size_t d10_z1 = dn_z;
+  static constexpr size_t d10_z2 = align128((size_t)ESZ * kKC * kD2H * kD2W);
+  static constexpr size_t d10_g1 = align128(sizeof(float) * kDnCH * kDnCW);
+  static constexpr size_t d10_e2 = align128(sizeof(float) * kD2H * kD2W);
+  static constexpr size_t d10_buf = d10_z1 + d10_z2 + d10_g1 + d10_e2;
+  static constexpr size_t d10_e1 = align128(sizeof(float) * kDnCH * kDnCW);
+  static constexpr size_t d10 = 2 * d10_buf + d10_e1 + 64;
 };
 
 // ---- small helpers ------------------------------------------------------------------
@@ -235,6 +270,14 @@ __device__ __forceinline__ float2 cos_sin_turns(float t) {
   const float cq = copysignf(q * rsqrtf(q), c);
   return make_float2(fabsf(s) < 0.5f ? cq : c, s);
 }
+
+// Horner step over the orders, P <- P w + D (complex), and Im(P w).  With
+// w = e^{-i w_1 g} and D_k the a_k-weighted Fourier difference of order k,
+// running k = K .. 1 gives sum_k Im(w^k D_k) = Im(P w).
+__device__ __forceinline__ float2 horner(float2 P, float2 w, float2 D) {
+  return make_float2(fmaf(P.x, w.x, fmaf(-P.y, w.y, D.x)), fmaf(P.x, w.y, fmaf(P.y, w.x, D.y)));
+}
+__device__ __forceinline__ float im_mul(float2 P, float2 w) { return fmaf(P.x, w.y, P.y * w.x); }
 
 // 5-tap binomial sums without the 1/16.
 __device__ __forceinline__ float tap5(float a, float b, float c, float d, float e) {

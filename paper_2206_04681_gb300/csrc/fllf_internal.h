@@ -71,6 +71,10 @@ struct PathMaps {
   std::vector<CUtensorMap> e_dn;  // E_l read as the coarse level of a combine
   std::vector<CUtensorMap> z_up;  // Z_l read as the source of a REDUCE
   std::vector<CUtensorMap> g_up;  // G_l read as the source of a REDUCE
+  // fused level-1/level-0 combine (levels >= 3)
+  CUtensorMap g1_d10{};           // G_1 on the level-1 window
+  CUtensorMap z2_d10{};           // Z_2 on the level-2 window
+  CUtensorMap e2_d10{};           // E_2 on the level-2 window (levels >= 4)
 };
 // Encodes the maps for the level buffers in `lv` (device addresses).
 bool build_maps(const fllf_params& p, const std::vector<Level>& lv, PathMaps* m);

@@ -181,6 +181,8 @@ __device__ __forceinline__ bool stage_up0(Res res, int total, unsigned char* sme
       {
         const int k = ch * kKC + vkk;
         if (k < a.K && xo < a.dst.w) {
+          // order k is stored weighted by its coefficient: a_k Z_{1,k}
+          const float sk = __ldg(a.a + k) * (1.f / 256.f);
           CT* Zk = reinterpret_cast<CT*>(a.dst.Z) + (long long)pl * a.dst.zplane +
                    (long long)k * a.dst.zk + xo;
           const float4* p =
@@ -197,8 +199,7 @@ __device__ __forceinline__ bool stage_up0(Res res, int total, unsigned char* sme
             const int y = Y1 + vgrp * kUpVRows + j;
             if (y < a.dst.h)
               Cplx<S>::st(Zk + (long long)y * a.dst.pitch,
-                          mul2(splat(1.f / 256.f),
-                               tap5(w[2 * j], w[2 * j + 1], w[2 * j + 2], w[2 * j + 3], w[2 * j + 4])));
+                          mul2(splat(sk), tap5(w[2 * j], w[2 * j + 1], w[2 * j + 2], w[2 * j + 3], w[2 * j + 4])));
           }
         }
         if (ch == 0 && tid % 32 < kUpRun * kUpVRows) {
@@ -370,17 +371,86 @@ __device__ __forceinline__ bool stage_up(Res res, int total, unsigned char* smem
 // ---------------------------------------------------------------------------------------
 // Combine (Eq. (14) product-sum fused with the residual collapse).
 // Item = (tile of 64 x 32 fine pixels, chunk of kKC orders); the chunks of a
-// tile run back to back on one CTA, which keeps the per-pixel state in
-// registers.  A thread owns fine rows 2j, 2j+1 and fine columns 4c..4c+3 of
-// the tile (tile origin 64*tx-6), i.e. coarse rows j-1..j+1 and coarse
-// columns 2c-1..2c+2, which sit at staged rows tr..tr+2 and columns
-// 2tc..2tc+3.  EXPAND of the 3 x 4 complex window runs on (C~, S~) pairs
-// with packed FP32x2 arithmetic; the per-pixel trig state (cos, -sin) of the
-// two fine rows and the accumulators are (even row, odd row) pairs, advanced
-// by complex rotation.  EXPAND weights 1/8 (1, 6, 1) at even fine positions
-// and 1/2 (1, 1) at odd ones per axis are folded into the coefficients.
+// tile run back to back on one CTA, from the highest order down, which keeps
+// the per-pixel state in registers.  The stored Fourier planes carry their
+// coefficient (a_k Z_{l,k}), so with w = e^{-i w_1 g} the sum of Eq. (14) is
+// evaluated by Horner's rule over the orders: P <- P w + D_k, sum = Im(P w),
+// where D_k = a_k (Z_{l,k} - up Z_{l+1,k}) at level l >= 1 and
+// D_k = -a_k up Z_{1,k} at level 0 (the Z_0 term cancels).  A thread owns
+// fine rows 2j, 2j+1 and fine columns 4c..4c+3 of the tile (tile origin
+// 64*tx-6), i.e. coarse rows j-1..j+1 and coarse columns 2c-1..2c+2, which sit
+// at staged rows tr..tr+2 and columns 2tc..2tc+3.  EXPAND weights 1/8 (1, 6, 1)
+// at even fine positions and 1/2 (1, 1) at odd ones per axis are applied
+// after the sum at level 0 (they are the same for every order) and per order
+// at level >= 1.
 __device__ __forceinline__ float2 expand_scale_pair(int q) {
   return (q & 1) ? make_float2(1.f / 16.f, 1.f / 4.f) : make_float2(1.f / 64.f, 1.f / 16.f);
+}
+
+// Unscaled EXPAND of the staged 3 x 4 complex window at zw (row pitch kDnCW)
+// to the 2 x 4 fine pixels of a combine thread: ue (even fine row), uo (odd).
+template <typename S>
+__device__ __forceinline__ void expand_2x4(const typename Cplx<S>::T* zw, float2 ue[4], float2 uo[4]) {
+  using CT = typename Cplx<S>::T;
+  float2 wv[3][4];
+#pragma unroll
+  for (int r = 0; r < 3; ++r) {
+    if constexpr (sizeof(CT) == 8) {
+      // 16-byte aligned: (row*36 + 2*tc) complex of 8 bytes
+      const float4 qa = *reinterpret_cast<const float4*>(zw + r * kDnCW);
+      const float4 qb = *reinterpret_cast<const float4*>(zw + r * kDnCW + 2);
+      wv[r][0] = make_float2(qa.x, qa.y); wv[r][1] = make_float2(qa.z, qa.w);
+      wv[r][2] = make_float2(qb.x, qb.y); wv[r][3] = make_float2(qb.z, qb.w);
+    } else {
+      // 8-byte aligned: two pairs of 4-byte complex samples
+      const uint2 qa = *reinterpret_cast<const uint2*>(zw + r * kDnCW);
+      const uint2 qb = *reinterpret_cast<const uint2*>(zw + r * kDnCW + 2);
+      wv[r][0] = Cplx<S>::cvt(*reinterpret_cast<const CT*>(&qa.x));
+      wv[r][1] = Cplx<S>::cvt(*reinterpret_cast<const CT*>(&qa.y));
+      wv[r][2] = Cplx<S>::cvt(*reinterpret_cast<const CT*>(&qb.x));
+      wv[r][3] = Cplx<S>::cvt(*reinterpret_cast<const CT*>(&qb.y));
+    }
+  }
+  float2 ve[4], vo[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    ve[q] = fma2(splat(6.f), wv[1][q], add2(wv[0][q], wv[2][q]));
+    vo[q] = add2(wv[1][q], wv[2][q]);
+  }
+  ue[0] = fma2(splat(6.f), ve[1], add2(ve[0], ve[2]));
+  ue[1] = add2(ve[1], ve[2]);
+  ue[2] = fma2(splat(6.f), ve[2], add2(ve[1], ve[3]));
+  ue[3] = add2(ve[2], ve[3]);
+  uo[0] = fma2(splat(6.f), vo[1], add2(vo[0], vo[2]));
+  uo[1] = add2(vo[1], vo[2]);
+  uo[2] = fma2(splat(6.f), vo[2], add2(vo[1], vo[3]));
+  uo[3] = add2(vo[2], vo[3]);
+}
+
+// Residual EXPAND up(E) at the 2 x 4 fine pixels of a combine thread from the
+// staged 3 x 4 float window at eb (row pitch kDnCW), scaled: (even, odd) rows.
+__device__ __forceinline__ void expand_e_2x4(const float* eb, float2 out[4]) {
+  float e3[3][4];
+#pragma unroll
+  for (int r = 0; r < 3; ++r) {
+    // 8-byte aligned (2*tc floats): two float2 reads
+    const float2* q2 = reinterpret_cast<const float2*>(eb + r * kDnCW);
+    const float2 qa = q2[0], qb = q2[1];
+    e3[r][0] = qa.x; e3[r][1] = qa.y; e3[r][2] = qb.x; e3[r][3] = qb.y;
+  }
+  float2 p[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) p[q] = make_float2(fmaf(6.f, e3[1][q], e3[0][q] + e3[2][q]), e3[1][q] + e3[2][q]);
+  out[0] = mul2(expand_scale_pair(0), fma2(splat(6.f), p[1], add2(p[0], p[2])));
+  out[1] = mul2(expand_scale_pair(1), add2(p[1], p[2]));
+  out[2] = mul2(expand_scale_pair(2), fma2(splat(6.f), p[2], add2(p[1], p[3])));
+  out[3] = mul2(expand_scale_pair(3), add2(p[2], p[3]));
+}
+
+// e^{-i pi t} as (cos, -sin).
+__device__ __forceinline__ float2 conj_turns(float t) {
+  const float2 z = cos_sin_turns(t);
+  return make_float2(z.x, -z.y);
 }
 
 // Uniform view of the level >= 1 and level-0 combine arguments.
@@ -391,22 +461,22 @@ struct CombineView {
   const float* I;       // level 0 only
   float* O;             // level 0 only
   const Level* coarse;
-  const float* a;
   unsigned* fault;
   int h, w, planes, K, has_e;
   float turns;
 };
 __device__ __forceinline__ CombineView view_of(const DownArgs& d) {
-  return CombineView{&d.zmap, &d.emap, &d.fine, nullptr, nullptr, &d.coarse, d.a, d.fault,
+  return CombineView{&d.zmap, &d.emap, &d.fine, nullptr, nullptr, &d.coarse, d.fault,
                      d.fine.h, d.fine.w, d.planes, d.K, d.has_e, d.turns};
 }
 __device__ __forceinline__ CombineView view_of(const Down0Args& d) {
-  return CombineView{&d.zmap, &d.emap, nullptr, d.I, d.O, &d.coarse, d.a, d.fault,
+  return CombineView{&d.zmap, &d.emap, nullptr, d.I, d.O, &d.coarse, d.fault,
                      d.h0, d.w0, d.planes, d.K, d.has_e, d.turns};
 }
-__device__ __forceinline__ int combine_tiles(const CombineView& v) {
-  return cdiv(v.w + kDnX0, kDnOW) * cdiv(v.h, kDnOH) * v.planes;
+__device__ __forceinline__ int combine_tiles(int h, int w, int planes) {
+  return cdiv(w + kDnX0, kDnOW) * cdiv(h, kDnOH) * planes;
 }
+__device__ __forceinline__ int combine_tiles(const CombineView& v) { return combine_tiles(v.h, v.w, v.planes); }
 
 template <typename S, bool LEVEL0, bool COH, typename Res>
 __device__ __forceinline__ bool stage_combine(Res res, int total, unsigned char* smem, uint64_t* bar,
@@ -416,26 +486,26 @@ __device__ __forceinline__ bool stage_combine(Res res, int total, unsigned char*
   unsigned char* bufs[2] = {smem, smem + SM::dn_buf};
   const int tid = threadIdx.x;
   if (b >= total) return true;
-  auto issue = [&](const CombineView& v, int lt, int ch, int buf) {
+  auto issue = [&](const CombineView& v, int lt, int ch, bool first, int buf) {
     const int ntx = cdiv(v.w + kDnX0, kDnOW), nty = cdiv(v.h, kDnOH);
     const int tx = lt % ntx, r = lt / ntx, ty = r % nty, pl = r / nty;
     const int cx0 = (tx * kDnOW - kDnX0) / 2 - 1, cy0 = ty * (kDnOH / 2) - 1;
-    const bool e = ch == 0 && v.has_e;
+    const bool e = first && v.has_e;
     mbar_expect_tx(&bar[buf], (uint32_t)(sizeof(CT) * kKC * kDnCH * kDnCW +
                                          (e ? sizeof(float) * kDnCH * kDnCW : 0)));
     tma_load3(bufs[buf], v.zmap, cx0, cy0, pl * v.K + ch * kKC, &bar[buf]);
     if (e) tma_load3(bufs[buf] + SM::dn_z, v.emap, cx0, cy0, pl, &bar[buf]);
   };
-  int t = b, lt = 0, ch = 0;
+  int t = b, lt = 0;
   CombineView v = res(t, lt);
-  int nch = cdiv(v.K, kKC);
+  int nch = cdiv(v.K, kKC), ch = nch - 1;
   if (tid == 0) {
     fence_proxy_async();
-    issue(v, lt, 0, 0);
+    issue(v, lt, ch, true, 0);
   }
 
   const int tc = tid % (kDnOW / 4), tr = tid / (kDnOW / 4);
-  float2 cc[4], ns[4], c1[4], s1[4], ns1[4], acc[4];
+  float2 we[4], wo[4], Pe[4], Po[4], base[4];
   int xq[4], y0c = 0, y1c = 0, fy = 0, fx = 0, pl = 0;
   for (int i = 0;; ++i) {
     const int buf = i & 1;
@@ -444,21 +514,21 @@ __device__ __forceinline__ bool stage_combine(Res res, int total, unsigned char*
     pl = rt / nty;
     const int X0 = tx * kDnOW - kDnX0, Y0 = ty * kDnOH;
     const int cx0 = X0 / 2 - 1, cy0 = Y0 / 2 - 1;
-    const bool more_chunks = ch + 1 < nch;
-    const bool has_next = more_chunks || t + G < total;
+    const bool first = ch == nch - 1, last = ch == 0;
+    const bool has_next = !last || t + G < total;
     if (tid == 0 && has_next) {
       fence_proxy_async();
-      if (more_chunks) {
-        issue(v, lt, ch + 1, buf ^ 1);
+      if (!last) {
+        issue(v, lt, ch - 1, false, buf ^ 1);
       } else {
         int ln;
         const CombineView vn = res(t + G, ln);
-        issue(vn, ln, 0, buf ^ 1);
+        issue(vn, ln, cdiv(vn.K, kKC) - 1, true, buf ^ 1);
       }
     }
     const int h = v.h, w = v.w;
-    if (ch == 0) {
-      // Per-tile state: guide value g, trig state (cos, -sin) for k = 1, accumulators.
+    if (first) {
+      // Per-tile state: e^{-i w_1 g} from the guide value g, Horner sums, base value.
       fy = Y0 + 2 * tr;
       fx = X0 + 4 * tc;
       y0c = min(fy, h - 1);
@@ -470,13 +540,10 @@ __device__ __forceinline__ bool stage_combine(Res res, int total, unsigned char*
         xq[q] = min(max(fx + q, 0), w - 1);
         const float g0 = COH ? __ldcg(gsrc + y0c * gpitch + xq[q]) : __ldg(gsrc + y0c * gpitch + xq[q]);
         const float g1 = COH ? __ldcg(gsrc + y1c * gpitch + xq[q]) : __ldg(gsrc + y1c * gpitch + xq[q]);
-        const float2 z0 = cos_sin_turns(v.turns * g0), z1 = cos_sin_turns(v.turns * g1);
-        c1[q] = make_float2(z0.x, z1.x);
-        s1[q] = make_float2(z0.y, z1.y);
-        ns1[q] = make_float2(-z0.y, -z1.y);
-        cc[q] = c1[q];
-        ns[q] = ns1[q];
-        acc[q] = LEVEL0 ? make_float2(g0, g1) : splat(0.f);
+        we[q] = conj_turns(v.turns * g0);
+        wo[q] = conj_turns(v.turns * g1);
+        Pe[q] = Po[q] = splat(0.f);
+        base[q] = LEVEL0 ? make_float2(g0, g1) : splat(0.f);
       }
     }
     if (!mbar_wait_cta(&bar[buf], pp.use[buf] & 1, v.fault)) {
@@ -490,74 +557,26 @@ __device__ __forceinline__ bool stage_combine(Res res, int total, unsigned char*
     auto my = [&](int y) { return ext_coarse(y, coarse.h, h); };
     auto mx = [&](int x) { return ext_coarse(x, coarse.w, w); };
     fix_borders(zb, kKC, kDnCH, kDnCW, cx0, cy0, coarse.w, coarse.h, my, mx);
-    if (ch == 0 && v.has_e) {
+    if (first && v.has_e) {
       fix_borders(eb, 1, kDnCH, kDnCW, cx0, cy0, coarse.w, coarse.h, my, mx);
-      float e3[3][4];
+      float2 ue[4];
+      expand_e_2x4(eb + tr * kDnCW + 2 * tc, ue);
 #pragma unroll
-      for (int r = 0; r < 3; ++r) {
-        // 8-byte aligned (2*tc floats): two float2 reads
-        const float2* q2 = reinterpret_cast<const float2*>(eb + (tr + r) * kDnCW + 2 * tc);
-        const float2 qa = q2[0], qb = q2[1];
-        e3[r][0] = qa.x; e3[r][1] = qa.y; e3[r][2] = qb.x; e3[r][3] = qb.y;
-      }
-      float2 p[4];
-#pragma unroll
-      for (int q = 0; q < 4; ++q) p[q] = make_float2(fmaf(6.f, e3[1][q], e3[0][q] + e3[2][q]), e3[1][q] + e3[2][q]);
-      acc[0] = fma2(expand_scale_pair(0), fma2(splat(6.f), p[1], add2(p[0], p[2])), acc[0]);
-      acc[1] = fma2(expand_scale_pair(1), add2(p[1], p[2]), acc[1]);
-      acc[2] = fma2(expand_scale_pair(2), fma2(splat(6.f), p[2], add2(p[1], p[3])), acc[2]);
-      acc[3] = fma2(expand_scale_pair(3), add2(p[2], p[3]), acc[3]);
+      for (int q = 0; q < 4; ++q) base[q] = add2(base[q], ue[q]);
     }
 #pragma unroll
-    for (int kk = 0; kk < kKC; ++kk) {
+    for (int kk = kKC - 1; kk >= 0; --kk) {
       const int k = ch * kKC + kk;
       if (k < v.K) {
-        const float ak = __ldg(v.a + k);
-        const CT* zw = zb + kk * kDnCH * kDnCW + tr * kDnCW + 2 * tc;
-        float2 wv[3][4];
-#pragma unroll
-        for (int r = 0; r < 3; ++r) {
-          if constexpr (sizeof(CT) == 8) {
-            // 16-byte aligned: (tr*36 + 2*tc) complex of 8 bytes
-            const float4 qa = *reinterpret_cast<const float4*>(zw + r * kDnCW);
-            const float4 qb = *reinterpret_cast<const float4*>(zw + r * kDnCW + 2);
-            wv[r][0] = make_float2(qa.x, qa.y); wv[r][1] = make_float2(qa.z, qa.w);
-            wv[r][2] = make_float2(qb.x, qb.y); wv[r][3] = make_float2(qb.z, qb.w);
-          } else {
-            // 8-byte aligned: two pairs of 4-byte complex samples
-            const uint2 qa = *reinterpret_cast<const uint2*>(zw + r * kDnCW);
-            const uint2 qb = *reinterpret_cast<const uint2*>(zw + r * kDnCW + 2);
-            wv[r][0] = Cplx<S>::cvt(*reinterpret_cast<const CT*>(&qa.x));
-            wv[r][1] = Cplx<S>::cvt(*reinterpret_cast<const CT*>(&qa.y));
-            wv[r][2] = Cplx<S>::cvt(*reinterpret_cast<const CT*>(&qb.x));
-            wv[r][3] = Cplx<S>::cvt(*reinterpret_cast<const CT*>(&qb.y));
-          }
-        }
-        float2 ve[4], vo[4];
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          ve[q] = fma2(splat(6.f), wv[1][q], add2(wv[0][q], wv[2][q]));
-          vo[q] = add2(wv[1][q], wv[2][q]);
-        }
         float2 ue[4], uo[4];
-        ue[0] = fma2(splat(6.f), ve[1], add2(ve[0], ve[2]));
-        ue[1] = add2(ve[1], ve[2]);
-        ue[2] = fma2(splat(6.f), ve[2], add2(ve[1], ve[3]));
-        ue[3] = add2(ve[2], ve[3]);
-        uo[0] = fma2(splat(6.f), vo[1], add2(vo[0], vo[2]));
-        uo[1] = add2(vo[1], vo[2]);
-        uo[2] = fma2(splat(6.f), vo[2], add2(vo[1], vo[3]));
-        uo[3] = add2(vo[2], vo[3]);
-        const float2 ce0 = mul2(splat(-ak), expand_scale_pair(0));
-        const float2 ce1 = mul2(splat(-ak), expand_scale_pair(1));
+        expand_2x4<S>(zb + kk * kDnCH * kDnCW + tr * kDnCW + 2 * tc, ue, uo);
+        if constexpr (LEVEL0) {
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          // cos(k w g) up(S~) - sin(k w g) up(C~) for the two fine rows
-          const float2 tq = make_float2(fmaf(cc[q].x, ue[q].y, ns[q].x * ue[q].x),
-                                        fmaf(cc[q].y, uo[q].y, ns[q].y * uo[q].x));
-          acc[q] = fma2((q & 1) ? ce1 : ce0, tq, acc[q]);
-        }
-        if constexpr (!LEVEL0) {
+          for (int q = 0; q < 4; ++q) {
+            Pe[q] = horner(Pe[q], we[q], ue[q]);
+            Po[q] = horner(Po[q], wo[q], uo[q]);
+          }
+        } else {
           const CT* Zk = reinterpret_cast<const CT*>(v.fine->Z) + (long long)pl * v.fine->zplane +
                          (long long)k * v.fine->zk;
           const CT* r0 = Zk + (long long)y0c * v.fine->pitch;
@@ -581,22 +600,16 @@ __device__ __forceinline__ bool stage_combine(Res res, int total, unsigned char*
               zz0 = r0[xq[q]];
               zz1 = r1[xq[q]];
             }
-            const float2 z0 = Cplx<S>::cvt(zz0), z1 = Cplx<S>::cvt(zz1);
-            const float2 tq = make_float2(fmaf(cc[q].x, z0.y, ns[q].x * z0.x),
-                                          fmaf(cc[q].y, z1.y, ns[q].y * z1.x));
-            acc[q] = fma2(splat(ak), tq, acc[q]);
+            const float2 sc = expand_scale_pair(q);
+            const float2 de = fma2(splat(-sc.x), ue[q], Cplx<S>::cvt(zz0));
+            const float2 dd = fma2(splat(-sc.y), uo[q], Cplx<S>::cvt(zz1));
+            Pe[q] = horner(Pe[q], we[q], de);
+            Po[q] = horner(Po[q], wo[q], dd);
           }
-        }
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          const float2 cn = fma2(cc[q], c1[q], mul2(ns[q], s1[q]));
-          const float2 nn = fma2(ns[q], c1[q], mul2(cc[q], ns1[q]));
-          cc[q] = cn;
-          ns[q] = nn;
         }
       }
     }
-    if (!more_chunks) {
+    if (last) {
       float* dst;
       long long dpitch;
       if constexpr (LEVEL0) {
@@ -614,20 +627,265 @@ __device__ __forceinline__ bool stage_combine(Res res, int total, unsigned char*
 #pragma unroll
           for (int q = 0; q < 4; ++q) {
             const int x = fx + q;
-            if (x >= 0 && x < w) d[x] = rr ? acc[q].y : acc[q].x;
+            float delta = rr ? im_mul(Po[q], wo[q]) : im_mul(Pe[q], we[q]);
+            // level 0: the EXPAND weight and the sign of D_k are applied here
+            if constexpr (LEVEL0) delta *= -(rr ? expand_scale_pair(q).y : expand_scale_pair(q).x);
+            if (x >= 0 && x < w) d[x] = (rr ? base[q].y : base[q].x) + delta;
           }
         }
       }
     }
     __syncthreads();
-    if (more_chunks) {
-      ++ch;
+    if (!last) {
+      --ch;
     } else {
       t += G;
       if (t >= total) break;
       v = res(t, lt);
-      ch = 0;
       nch = cdiv(v.K, kKC);
+      ch = nch - 1;
+    }
+  }
+  return true;
+}
+
+// ---------------------------------------------------------------------------------------
+// Fused combine at levels 1 and 0 (Eq. (14), both cases; levels >= 3).
+// Item = (tile of 64 x 32 level-0 pixels, chunk of kKC orders) as in the
+// level-0 combine.  The level-0 EXPAND reads the 36 x 18 staged window of
+// level-1 cells from (cx0, cy0) = (X0/2 - 1, Y0/2 - 1), and E_1 is needed on
+// exactly that window, so the tile first runs the level-1 combine there: it
+// reads the same staged Z_1 cells as the fine values of level 1, G_1 on the
+// window (with the first chunk), and the 20 x 11 window of level-2 cells
+// from (cx0/2 - 2, (cy0 - 1)/2) holding Z_2 and E_2.  Thread b < 153 owns the
+// 2 x 2 level-1 cells (2 br + rr, 2 bc + cc).  cy0 is odd and cx0 even, so
+// rr = 0 is an odd level-1 row (level-2 window rows br, br+1, weights
+// 1/2 (1, 1)) and rr = 1 an even one (rows br..br+2, 1/8 (1, 6, 1)); cc = 0
+// is an even column (window columns bc+1..bc+3) and cc = 1 an odd one
+// (bc+2, bc+3).  After the last chunk the level-1 threads write
+// E_1 = Delta_1 + up(E_2) to shared memory, the out-of-range cells take their
+// EXPAND sources, and every thread finishes O = I + Delta_0 + up(E_1) for its
+// 2 x 4 level-0 pixels.  E_1 never goes to memory, and each Z_1 sample is
+// read once for both levels.
+template <typename S, typename Res>
+__device__ __forceinline__ bool stage_down10(Res res, int total, unsigned char* smem, uint64_t* bar,
+                                            Pipe& pp, int b, int G) {
+  using CT = typename Cplx<S>::T;
+  using SM = Smem<sizeof(CT)>;
+  unsigned char* bufs[2] = {smem, smem + SM::d10_buf};
+  float* e1 = reinterpret_cast<float*>(smem + 2 * SM::d10_buf);
+  const int tid = threadIdx.x;
+  if (b >= total) return true;
+  auto issue = [&](const Down10Args& a, int lt, int ch, bool first, int buf) {
+    const int ntx = cdiv(a.w0 + kDnX0, kDnOW), nty = cdiv(a.h0, kDnOH);
+    const int tx = lt % ntx, r = lt / ntx, ty = r % nty, pl = r / nty;
+    const int cx0 = (tx * kDnOW - kDnX0) / 2 - 1, cy0 = ty * (kDnOH / 2) - 1;
+    const int c2x = cx0 / 2 - 2, c2y = (cy0 - 1) / 2;
+    const bool e2 = first && a.has_e2;
+    uint32_t bytes = (uint32_t)(sizeof(CT) * kKC * (kDnCH * kDnCW + kD2H * kD2W));
+    if (first) bytes += (uint32_t)(sizeof(float) * kDnCH * kDnCW);
+    if (e2) bytes += (uint32_t)(sizeof(float) * kD2H * kD2W);
+    mbar_expect_tx(&bar[buf], bytes);
+    unsigned char* p = bufs[buf];
+    const int z = pl * a.K + ch * kKC;
+    tma_load3(p, &a.z1map, cx0, cy0, z, &bar[buf]);
+    tma_load3(p + SM::d10_z1, &a.z2map, c2x, c2y, z, &bar[buf]);
+    if (first) tma_load3(p + SM::d10_z1 + SM::d10_z2, &a.g1map, cx0, cy0, pl, &bar[buf]);
+    if (e2) tma_load3(p + SM::d10_z1 + SM::d10_z2 + SM::d10_g1, &a.e2map, c2x, c2y, pl, &bar[buf]);
+  };
+  int t = b, lt = 0;
+  const Down10Args* a = res(t, lt);
+  int nch = cdiv(a->K, kKC), ch = nch - 1;
+  if (tid == 0) {
+    fence_proxy_async();
+    issue(*a, lt, ch, true, 0);
+  }
+
+  const int tc = tid % (kDnOW / 4), tr = tid / (kDnOW / 4);
+  const bool l1t = tid < kB1X * kB1Y;
+  const int bc = tid % kB1X, br = tid / kB1X;
+  float2 we[4], wo[4], Pe[4], Po[4], base[4];
+  float2 w1[2][2], P1[2][2];
+  float up_e2[2][2];
+  int fy = 0, fx = 0, pl = 0;
+  for (int i = 0;; ++i) {
+    const int buf = i & 1;
+    const int h0 = a->h0, w0 = a->w0;
+    const int ntx = cdiv(w0 + kDnX0, kDnOW), nty = cdiv(h0, kDnOH);
+    const int tx = lt % ntx, rt = lt / ntx, ty = rt % nty;
+    pl = rt / nty;
+    const int X0 = tx * kDnOW - kDnX0, Y0 = ty * kDnOH;
+    const int cx0 = X0 / 2 - 1, cy0 = Y0 / 2 - 1;
+    const int c2x = cx0 / 2 - 2, c2y = (cy0 - 1) / 2;
+    const bool first = ch == nch - 1, last = ch == 0;
+    const bool has_next = !last || t + G < total;
+    if (tid == 0 && has_next) {
+      fence_proxy_async();
+      if (!last) {
+        issue(*a, lt, ch - 1, false, buf ^ 1);
+      } else {
+        int ln;
+        const Down10Args* an = res(t + G, ln);
+        issue(*an, ln, cdiv(an->K, kKC) - 1, true, buf ^ 1);
+      }
+    }
+    if (first) {
+      // level-0 state: e^{-i w_1 I}, Horner sums, and I itself
+      fy = Y0 + 2 * tr;
+      fx = X0 + 4 * tc;
+      const int y0c = min(fy, h0 - 1), y1c = min(fy + 1, h0 - 1);
+      const float* Ip = a->I + (long long)pl * h0 * w0;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int xq = min(max(fx + q, 0), w0 - 1);
+        const float g0 = __ldg(Ip + (long long)y0c * w0 + xq);
+        const float g1 = __ldg(Ip + (long long)y1c * w0 + xq);
+        we[q] = conj_turns(a->turns * g0);
+        wo[q] = conj_turns(a->turns * g1);
+        Pe[q] = Po[q] = splat(0.f);
+        base[q] = make_float2(g0, g1);
+      }
+    }
+    if (!mbar_wait_cta(&bar[buf], pp.use[buf] & 1, a->fault)) {
+      if (tid == 0 && has_next) drain(&bar[buf ^ 1], pp.use[buf ^ 1] & 1);
+      return false;
+    }
+    ++pp.use[buf];
+    CT* z1b = reinterpret_cast<CT*>(bufs[buf]);
+    CT* z2b = reinterpret_cast<CT*>(bufs[buf] + SM::d10_z1);
+    const float* g1b = reinterpret_cast<const float*>(bufs[buf] + SM::d10_z1 + SM::d10_z2);
+    float* e2b = reinterpret_cast<float*>(bufs[buf] + SM::d10_z1 + SM::d10_z2 + SM::d10_g1);
+    const Level& L1 = a->l1;
+    const Level& L2 = a->l2;
+    auto my1 = [&](int y) { return ext_coarse(y, L1.h, h0); };
+    auto mx1 = [&](int x) { return ext_coarse(x, L1.w, w0); };
+    auto my2 = [&](int y) { return ext_coarse(y, L2.h, L1.h); };
+    auto mx2 = [&](int x) { return ext_coarse(x, L2.w, L1.w); };
+    fix_borders(z1b, kKC, kDnCH, kDnCW, cx0, cy0, L1.w, L1.h, my1, mx1);
+    fix_borders(z2b, kKC, kD2H, kD2W, c2x, c2y, L2.w, L2.h, my2, mx2);
+    if (first && a->has_e2) fix_borders(e2b, 1, kD2H, kD2W, c2x, c2y, L2.w, L2.h, my2, mx2);
+
+    // level-1 combine on the window cells (Horner over this chunk's orders)
+    if (l1t) {
+      if (first) {
+#pragma unroll
+        for (int rr = 0; rr < 2; ++rr)
+#pragma unroll
+          for (int cc = 0; cc < 2; ++cc) {
+            w1[rr][cc] = conj_turns(a->turns * g1b[(2 * br + rr) * kDnCW + 2 * bc + cc]);
+            P1[rr][cc] = splat(0.f);
+            up_e2[rr][cc] = 0.f;
+          }
+        if (a->has_e2) {
+          const float* ew = e2b + br * kD2W + bc + 1;
+          float vo[3], ve[3];
+#pragma unroll
+          for (int c = 0; c < 3; ++c) {
+            const float e0 = ew[c], e1v = ew[kD2W + c], e2v = ew[2 * kD2W + c];
+            vo[c] = e0 + e1v;
+            ve[c] = fmaf(6.f, e1v, e0 + e2v);
+          }
+          up_e2[0][0] = (1.f / 16.f) * fmaf(6.f, vo[1], vo[0] + vo[2]);
+          up_e2[0][1] = (1.f / 4.f) * (vo[1] + vo[2]);
+          up_e2[1][0] = (1.f / 64.f) * fmaf(6.f, ve[1], ve[0] + ve[2]);
+          up_e2[1][1] = (1.f / 16.f) * (ve[1] + ve[2]);
+        }
+      }
+#pragma unroll
+      for (int kk = kKC - 1; kk >= 0; --kk) {
+        const int k = ch * kKC + kk;
+        if (k < a->K) {
+          const CT* zw = z2b + kk * kD2H * kD2W + br * kD2W + bc + 1;
+          float2 vo[3], ve[3];
+#pragma unroll
+          for (int c = 0; c < 3; ++c) {
+            const float2 q0 = Cplx<S>::cvt(zw[c]);
+            const float2 q1 = Cplx<S>::cvt(zw[kD2W + c]);
+            const float2 q2 = Cplx<S>::cvt(zw[2 * kD2W + c]);
+            vo[c] = add2(q0, q1);
+            ve[c] = fma2(splat(6.f), q1, add2(q0, q2));
+          }
+          float2 U[2][2];
+          U[0][0] = mul2(splat(1.f / 16.f), fma2(splat(6.f), vo[1], add2(vo[0], vo[2])));
+          U[0][1] = mul2(splat(1.f / 4.f), add2(vo[1], vo[2]));
+          U[1][0] = mul2(splat(1.f / 64.f), fma2(splat(6.f), ve[1], add2(ve[0], ve[2])));
+          U[1][1] = mul2(splat(1.f / 16.f), add2(ve[1], ve[2]));
+          const CT* zc = z1b + kk * kDnCH * kDnCW + 2 * br * kDnCW + 2 * bc;
+#pragma unroll
+          for (int rr = 0; rr < 2; ++rr) {
+            float2 f[2];
+            if constexpr (sizeof(CT) == 8) {
+              const float4 q = *reinterpret_cast<const float4*>(zc + rr * kDnCW);  // 16-byte aligned
+              f[0] = make_float2(q.x, q.y);
+              f[1] = make_float2(q.z, q.w);
+            } else {
+              const uint2 q = *reinterpret_cast<const uint2*>(zc + rr * kDnCW);  // 8-byte aligned
+              f[0] = Cplx<S>::cvt(*reinterpret_cast<const CT*>(&q.x));
+              f[1] = Cplx<S>::cvt(*reinterpret_cast<const CT*>(&q.y));
+            }
+#pragma unroll
+            for (int cc = 0; cc < 2; ++cc)
+              P1[rr][cc] = horner(P1[rr][cc], w1[rr][cc], add2(f[cc], make_float2(-U[rr][cc].x, -U[rr][cc].y)));
+          }
+        }
+      }
+    }
+
+    // level-0 combine (Horner over this chunk's orders)
+#pragma unroll
+    for (int kk = kKC - 1; kk >= 0; --kk) {
+      const int k = ch * kKC + kk;
+      if (k < a->K) {
+        float2 ue[4], uo[4];
+        expand_2x4<S>(z1b + kk * kDnCH * kDnCW + tr * kDnCW + 2 * tc, ue, uo);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          Pe[q] = horner(Pe[q], we[q], ue[q]);
+          Po[q] = horner(Po[q], wo[q], uo[q]);
+        }
+      }
+    }
+
+    if (last) {
+      if (l1t) {
+#pragma unroll
+        for (int rr = 0; rr < 2; ++rr)
+#pragma unroll
+          for (int cc = 0; cc < 2; ++cc) {
+            const int y1 = cy0 + 2 * br + rr, x1 = cx0 + 2 * bc + cc;
+            if (y1 >= 0 && y1 < L1.h && x1 >= 0 && x1 < L1.w)
+              e1[(2 * br + rr) * kDnCW + 2 * bc + cc] = im_mul(P1[rr][cc], w1[rr][cc]) + up_e2[rr][cc];
+          }
+      }
+      __syncthreads();
+      fix_borders(e1, 1, kDnCH, kDnCW, cx0, cy0, L1.w, L1.h, my1, mx1);
+      float2 ue[4];
+      expand_e_2x4(e1 + tr * kDnCW + 2 * tc, ue);
+      float* dst = a->O + (long long)pl * h0 * w0;
+#pragma unroll
+      for (int rr = 0; rr < 2; ++rr) {
+        const int y = fy + rr;
+        if (y < h0) {
+          float* d = dst + (long long)y * w0;
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const int x = fx + q;
+            const float2 sc = expand_scale_pair(q);
+            const float delta = rr ? -sc.y * im_mul(Po[q], wo[q]) : -sc.x * im_mul(Pe[q], we[q]);
+            if (x >= 0 && x < w0) d[x] = (rr ? base[q].y + ue[q].y : base[q].x + ue[q].x) + delta;
+          }
+        }
+      }
+    }
+    __syncthreads();
+    if (!last) {
+      --ch;
+    } else {
+      t += G;
+      if (t >= total) break;
+      a = res(t, lt);
+      nch = cdiv(a->K, kKC);
+      ch = nch - 1;
     }
   }
   return true;
@@ -679,6 +937,17 @@ __global__ void __launch_bounds__(kThreads, 3) k_down0(const __grid_constant__ D
   const CombineView v = view_of(a);
   stage_combine<S, true, false>([&](int g, int& l) { l = g; return v; }, combine_tiles(v), smem, bar,
                                 pp, blockIdx.x, gridDim.x);
+}
+
+template <typename S>
+__global__ void __launch_bounds__(kThreads, 2) k_down10(const __grid_constant__ Down10Args a) {
+  using SM = Smem<sizeof(typename Cplx<S>::T)>;
+  extern __shared__ __align__(128) unsigned char smem[];
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + SM::d10 - 64);
+  init_bars(bar);
+  Pipe pp{{0u, 0u}};
+  stage_down10<S>([&](int g, int& l) { l = g; return &a; }, combine_tiles(a.h0, a.w0, a.planes), smem, bar,
+                  pp, blockIdx.x, gridDim.x);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -875,6 +1144,13 @@ cudaError_t FLLF_LAUNCH_NAME(down0)(const Down0Args& a, cudaStream_t s) {
   const int tiles = cdiv(a.w0 + kDnX0, kDnOW) * cdiv(a.h0, kDnOH) * a.planes;
   const int grid = persistent_grid(k_down0<FLLF_STORAGE>, SMS::dn, tiles);
   k_down0<FLLF_STORAGE><<<grid, kThreads, SMS::dn, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t FLLF_LAUNCH_NAME(down10)(const Down10Args& a, cudaStream_t s) {
+  const int tiles = cdiv(a.w0 + kDnX0, kDnOW) * cdiv(a.h0, kDnOH) * a.planes;
+  const int grid = persistent_grid(k_down10<FLLF_STORAGE>, SMS::d10, tiles);
+  k_down10<FLLF_STORAGE><<<grid, kThreads, SMS::d10, s>>>(a);
   return cudaGetLastError();
 }
 

@@ -13,6 +13,7 @@ namespace fllf {
   cudaError_t launch_up_##suffix(const UpArgs& a, cudaStream_t s);       \
   cudaError_t launch_down_##suffix(const DownArgs& a, cudaStream_t s);   \
   cudaError_t launch_down0_##suffix(const Down0Args& a, cudaStream_t s);   \
+  cudaError_t launch_down10_##suffix(const Down10Args& a, cudaStream_t s); \
   cudaError_t launch_chain_##suffix(const ChainArgs& a, cudaStream_t s);                  \
   cudaError_t launch_up0_batch_##suffix(const BatchTable<Up0Args>& t, cudaStream_t s);   \
   cudaError_t launch_up_batch_##suffix(const BatchTable<UpArgs>& t, cudaStream_t s);     \

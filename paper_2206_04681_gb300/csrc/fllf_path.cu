@@ -75,6 +75,13 @@ cudaError_t launch_chain(int prec, const ChainArgs& a, cudaStream_t s) {
     default: return launch_chain_f32(a, s);
   }
 }
+cudaError_t launch_down10(int prec, const Down10Args& a, cudaStream_t s) {
+  switch (prec) {
+    case FLLF_FP16: return launch_down10_f16(a, s);
+    case FLLF_BF16: return launch_down10_bf16(a, s);
+    default: return launch_down10_f32(a, s);
+  }
+}
 cudaError_t launch_down0(int prec, const Down0Args& a, cudaStream_t s) {
   switch (prec) {
     case FLLF_FP16: return launch_down0_f16(a, s);
@@ -117,6 +124,21 @@ bool build_maps(const fllf_params& p, const std::vector<Level>& lv, PathMaps* m)
         return false;
     }
   }
+  if (L >= 3) {
+    // fused level-1/level-0 combine: G_1 on the 36 x 18 level-1 window, Z_2 and
+    // E_2 on the 20 x 11 level-2 window
+    const Level& v1 = lv[1];
+    const Level& v2 = lv[2];
+    if (!encode3(&m->g1_d10, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, v1.G, v1.w, v1.h, p.C, 4ull * v1.pitch,
+                 4ull * (uint64_t)v1.gplane, kDnCW, kDnCH, 1))
+      return false;
+    if (!encode3(&m->z2_d10, zdt, zs, v2.Z, v2.w, v2.h, (uint64_t)p.K * p.C, zs * v2.pitch,
+                 zs * (uint64_t)v2.zk, kD2W, kD2H, kKC))
+      return false;
+    if (v2.E && !encode3(&m->e2_d10, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, v2.E, v2.w, v2.h, p.C,
+                         4ull * v2.pitch, 4ull * (uint64_t)v2.gplane, kD2W, kD2H, 1))
+      return false;
+  }
   return true;
 }
 
@@ -137,6 +159,7 @@ cudaError_t enqueue_path(const fllf_params& p, const std::vector<Level>& lv, con
 
   Up0Args u0{};
   u0.I = d_in;
+  u0.a = d_a;
   u0.h0 = p.H;
   u0.w0 = p.W;
   u0.planes = C;
@@ -209,11 +232,35 @@ cudaError_t enqueue_path(const fllf_params& p, const std::vector<Level>& lv, con
     if ((e = launch_chain(prec, ca, s)) != cudaSuccess) return e;
     mark(FLLF_STAGE_CHAIN, false);
   }
-  for (int l = (c0 <= L - 2 ? c0 - 1 : L - 2); l >= 1; --l) {
+  // With levels >= 3 the level-1 combine runs inside the level-0 tiles.
+  const int down_lo = L >= 3 ? 2 : 1;
+  for (int l = (c0 <= L - 2 ? c0 - 1 : L - 2); l >= down_lo; --l) {
     const DownArgs d = down_args(l);
     mark(FLLF_STAGE_DOWN, true);
     if ((e = launch_down(prec, d, s)) != cudaSuccess) return e;
     mark(FLLF_STAGE_DOWN, false);
+  }
+  if (L >= 3) {
+    Down10Args d{};
+    d.z1map = maps.z_dn[1];
+    d.g1map = maps.g1_d10;
+    d.z2map = maps.z2_d10;
+    d.e2map = maps.e2_d10;
+    d.I = d_in;
+    d.O = d_out;
+    d.h0 = p.H;
+    d.w0 = p.W;
+    d.planes = C;
+    d.l1 = lv[1];
+    d.l2 = lv[2];
+    d.K = p.K;
+    d.turns = turns;
+    d.has_e2 = (L >= 4) ? 1 : 0;
+    d.fault = fault;
+    mark(FLLF_STAGE_DOWN0, true);
+    if ((e = launch_down10(prec, d, s)) != cudaSuccess) return e;
+    mark(FLLF_STAGE_DOWN0, false);
+    return cudaSuccess;
   }
   Down0Args d0{};
   d0.zmap = maps.z_dn[1];
