@@ -18,9 +18,9 @@ namespace {
 
 // Work-item counts; these mirror the device-side definitions exactly.
 int up0_items_h(const Level& l1, int planes) { return cdiv(l1.w, kUpTW) * cdiv(l1.h, kUpTH) * planes; }
-int up_items_h(const Level& dst, int planes, int K, int prec) {
+int up_items_h(const Level& dst, int planes, int K, int write_g, int prec) {
   const int kcu = prec == FLLF_FP32 ? Smem<8>::up_kc : Smem<4>::up_kc;
-  return cdiv(dst.w, kRsTW) * cdiv(dst.h, kRsTH) * planes * cdiv(K, kcu);
+  return cdiv(dst.w, kRsTW) * cdiv(dst.h, kRsTH) * planes * (cdiv(K, kcu) + (write_g ? 1 : 0));
 }
 int combine_tiles_h(int h, int w, int planes) { return cdiv(w + kDnX0, kDnOW) * cdiv(h, kDnOH) * planes; }
 
@@ -126,7 +126,7 @@ void build_batch_blob(const std::vector<const fllf_plan*>& plans, int prec, Batc
       u.K = pl->p.K;
       u.write_g = (l + 1 <= L - 2) ? 1 : 0;
       args.push_back(u);
-      counts.push_back(up_items_h(pl->lv[l + 1], pl->p.C, pl->p.K, prec));
+      counts.push_back(up_items_h(pl->lv[l + 1], pl->p.C, pl->p.K, u.write_g, prec));
     }
     add_stage(kStageUp, args, counts);
   }

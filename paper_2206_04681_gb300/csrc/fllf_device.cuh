@@ -67,7 +67,9 @@ struct Level {
 };
 
 // Kernel arguments.  Tensor maps describe the level buffers as 3-D tensors
-// (x = column, y = row, z = plane); Z maps have z = plane * K + k.
+// (x = column, y = row, z = plane); Z maps read by a REDUCE have
+// z = plane * K + k, Z maps read by a combine are 4-D (column, row, order,
+// plane), so that orders k >= K of a chunk read as zeros.
 struct Up0Args {
   CUtensorMap imap;     // level-0 input (valid when use_tma)
   const float* I;       // level-0 input planes, pitch w0, plane stride h0*w0
@@ -120,6 +122,7 @@ struct Down0Args {
 // the window of level-1 cells that the level-0 EXPAND reads, so E_1 stays in
 // shared memory.
 struct Down10Args {
+  CUtensorMap imap;     // level-0 input tile (68 x 32 from (X0 - 2, Y0); valid when use_tma)
   CUtensorMap z1map;    // Z_1 as the coarse window of level 0 (36 x 18 x kKC)
   CUtensorMap g1map;    // G_1 on the same window (36 x 18)
   CUtensorMap z2map;    // Z_2 window of the level-1 cells (20 x 11 x kKC)
@@ -131,6 +134,7 @@ struct Down10Args {
   int K;
   float turns;
   int has_e2;           // E_2 exists (levels >= 4)
+  int use_tma;          // input rows 16-byte aligned (w0 % 4 == 0, aligned base)
   unsigned* fault;
 };
 
@@ -182,6 +186,7 @@ constexpr int kRsTW = 30, kRsTH = 16;
 constexpr int kRsIR = 2 * kRsTH + 3;      // fine rows read (35)
 constexpr int kRsBW = 68;                 // staged fine columns (box from 2*X1-4)
 constexpr int kRsVW = 64;                 // vertical-pass columns (63 used)
+constexpr int kUpSlots = 4;               // TMA ring slots of the REDUCE stage (3 loads in flight)
 
 // combine: 64 x 32 fine outputs per tile; fine tile origin 64*tx-6 so that the
 // coarse window origin 32*tx-4 is 16-byte aligned for both element sizes.
@@ -195,9 +200,12 @@ static_assert((kDnOW / 4) * (kDnOH / 2) == kThreads, "combine thread mapping");
 // of the level-1 threads over the 34 x 18 used level-1 cells.
 constexpr int kD2W = 20, kD2H = 11;
 constexpr int kB1X = 17, kB1Y = 9;
+constexpr int kB1PerWarp = 20;            // level-1 blocks per warp (lanes 0..19)
+constexpr int kD0IW = kDnOW + 4;          // staged level-0 input columns (from X0 - 2)
 static_assert(kB1X * kB1Y <= kThreads && 2 * kB1X == kDnCW - 2 && 2 * kB1Y == kDnCH,
               "level-1 blocks cover the used window");
 static_assert(kB1X + 2 < kD2W && kB1Y + 1 < kD2H, "level-1 blocks read inside the level-2 window");
+static_assert(kB1PerWarp * (kThreads / 32) >= kB1X * kB1Y && kB1PerWarp <= 32, "level-1 blocks over the warps");
 
 __host__ __device__ constexpr int cdiv(int a, int b) { return (a + b - 1) / b; }
 __host__ __device__ constexpr size_t align128(size_t x) { return (x + 127) & ~size_t(127); }
@@ -212,12 +220,12 @@ struct Smem {
   static constexpr size_t up0 = 2 * up0_it + align128(up0_hz) + align128(up0_hg) + 64;
   // up
   static constexpr int up_kc = ESZ == 8 ? 1 : 2;  // orders per chunk
-  static constexpr size_t up_src = align128((size_t)ESZ * up_kc * kRsIR * kRsBW);
-  static constexpr size_t up_g = align128(sizeof(float) * kRsIR * kRsBW);
-  static constexpr size_t up_buf = up_src + up_g;
+  // ring slot: one chunk of orders, or the guide plane (smaller)
+  static constexpr size_t up_slot = align128((size_t)ESZ * up_kc * kRsIR * kRsBW);
   static constexpr size_t up_vb = align128(sizeof(float2) * up_kc * kRsTH * kRsVW);
   static constexpr size_t up_vg = align128(sizeof(float) * kRsTH * kRsVW);
-  static constexpr size_t up = 2 * up_buf + up_vb + up_vg + 64;
+  static constexpr size_t up = kUpSlots * up_slot + up_vb + up_vg + 64;
+  static_assert(sizeof(float) * kRsIR * kRsBW <= up_slot, "the guide box fits a ring slot");
   // combine
   static constexpr size_t dn_z = align128((size_t)ESZ * kKC * kDnCH * kDnCW);
   static constexpr size_t dn_e = align128(sizeof(float) * kDnCH * kDnCW);
@@ -228,7 +236,8 @@ struct Smem {
   static constexpr size_t d10_z2 = align128((size_t)ESZ * kKC * kD2H * kD2W);
   static constexpr size_t d10_g1 = align128(sizeof(float) * kDnCH * kDnCW);
   static constexpr size_t d10_e2 = align128(sizeof(float) * kD2H * kD2W);
-  static constexpr size_t d10_buf = d10_z1 + d10_z2 + d10_g1 + d10_e2;
+  static constexpr size_t d10_i = align128(sizeof(float) * kDnOH * kD0IW);
+  static constexpr size_t d10_buf = d10_z1 + d10_z2 + d10_g1 + d10_e2 + d10_i;
   static constexpr size_t d10_e1 = align128(sizeof(float) * kDnCH * kDnCW);
   static constexpr size_t d10 = 2 * d10_buf + d10_e1 + 64;
 };
@@ -325,6 +334,15 @@ __device__ __forceinline__ void tma_load3(void* dst, const CUtensorMap* map, int
       : "memory");
 }
 
+__device__ __forceinline__ void tma_load4(void* dst, const CUtensorMap* map, int x, int y, int z, int v,
+                                          uint64_t* b) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(saddr(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(v), "r"(saddr(b))
+      : "memory");
+}
+
 // Bounded wait on an mbarrier phase (about 2 s of SM clock).  The outcome is
 // made uniform over the CTA; on a timeout the fault word records it and the
 // caller leaves the kernel.
@@ -343,6 +361,23 @@ __device__ __forceinline__ bool mbar_wait_cta(uint64_t* b, uint32_t parity, unsi
   const int all = __syncthreads_and(ok);
   if (!all && threadIdx.x == 0 && fault) atomicOr(fault, 1u);
   return all != 0;
+}
+
+// Bounded wait on an mbarrier phase by the calling thread alone (no CTA
+// barrier).  On a timeout, or once another thread of the CTA has timed out,
+// the fault word and the CTA's shared abort flag are set; the CTA leaves at
+// its next barrier, where every thread reads the flag.
+__device__ __forceinline__ void mbar_wait_thread(uint64_t* b, uint32_t parity, unsigned* fault,
+                                                 volatile int* abort) {
+  if (mbar_test(b, parity)) return;
+  const long long t0 = clock64();
+  while (!mbar_test(b, parity)) {
+    if (*abort || clock64() - t0 > kWaitCycles) {
+      if (fault) atomicOr(fault, 1u);
+      *abort = 1;
+      return;
+    }
+  }
 }
 
 // Rewrites the out-of-range cells of a staged box (planes x bh x bw elements

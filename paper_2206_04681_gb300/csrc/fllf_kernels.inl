@@ -22,17 +22,24 @@ __device__ __forceinline__ void drain(uint64_t* b, uint32_t parity) {
   }
 }
 
-// Completed uses of the two TMA buffers of a CTA (identical in every thread);
+// Completed uses of the TMA buffers of a CTA (identical in every thread);
 // the parity of a buffer's next phase is use[buf] & 1.  Carried across the
 // stages of the chained kernel.
 struct Pipe {
-  uint32_t use[2];
+  uint32_t use[kUpSlots];
 };
 
+// bar[0 .. kUpSlots-1]: the buffers' mbarriers (the combine stages use the
+// first two); bar[6] holds the CTA's abort flag (an int) for the stages that
+// wait per thread.
+static_assert(kUpSlots <= 6, "barrier area: 64 bytes");
+__device__ __forceinline__ volatile int* abort_flag(uint64_t* bar) {
+  return reinterpret_cast<volatile int*>(&bar[6]);
+}
 __device__ __forceinline__ void init_bars(uint64_t* bar) {
   if (threadIdx.x == 0) {
-    mbar_init(&bar[0], 1);
-    mbar_init(&bar[1], 1);
+    for (int j = 0; j < kUpSlots; ++j) mbar_init(&bar[j], 1);
+    *abort_flag(bar) = 0;
     fence_mbar_init();
   }
   __syncthreads();
@@ -66,7 +73,7 @@ __device__ __forceinline__ bool stage_up0(Res res, int total, unsigned char* sme
                                           Pipe& pp, int b, int G) {
   using CT = typename Cplx<S>::T;
   using SM = Smem<sizeof(CT)>;
-  float* itb[2] = {reinterpret_cast<float*>(smem), reinterpret_cast<float*>(smem + SM::up0_it)};
+  auto itb = [&](int buf) { return reinterpret_cast<float*>(smem + buf * SM::up0_it); };
   float2* hz = reinterpret_cast<float2*>(smem + 2 * SM::up0_it);
   float* hg = reinterpret_cast<float*>(smem + 2 * SM::up0_it + align128(SM::up0_hz));
   const int tid = threadIdx.x;
@@ -74,7 +81,7 @@ __device__ __forceinline__ bool stage_up0(Res res, int total, unsigned char* sme
     const int ntx = cdiv(a.dst.w, kUpTW), nty = cdiv(a.dst.h, kUpTH);
     const int tx = t % ntx, r = t / ntx, ty = r % nty, pl = r / nty;
     mbar_expect_tx(&bar[buf], sizeof(float) * kUpIR * kUpIW);
-    tma_load3(itb[buf], &a.imap, 2 * tx * kUpTW - 4, 2 * ty * kUpTH - 2, pl, &bar[buf]);
+    tma_load3(itb(buf), &a.imap, 2 * tx * kUpTW - 4, 2 * ty * kUpTH - 2, pl, &bar[buf]);
   };
   if (b < total && tid == 0) {
     int lt;
@@ -94,7 +101,7 @@ __device__ __forceinline__ bool stage_up0(Res res, int total, unsigned char* sme
     const int X1 = tx * kUpTW, Y1 = ty * kUpTH;
     const int xs = 2 * X1 - 4, ys = 2 * Y1 - 2;
     const int nch = cdiv(a.K, kKC);
-    float* it = itb[buf];
+    float* it = itb(buf);
     const int gn = gt + G;
     if (tid == 0 && gn < total) {
       int tn;
@@ -233,15 +240,20 @@ __device__ __forceinline__ bool stage_up0(Res res, int total, unsigned char* sme
 
 // ---------------------------------------------------------------------------------------
 // up: level l -> l+1 for l >= 1 (REDUCE of G_l and the K complex planes).
-// Item = (tile of 30 x 16 coarse outputs, chunk of KCU orders): orders reduce
-// independently, so small levels still spread over many CTAs.  TMA stages
-// the 35 x 68 source box of each order of the chunk (plus G_l with chunk 0);
-// the vertical pass reads one staged column per thread and keeps the reduced
-// rows in registers; the horizontal pass reads 5 staged columns per output.
+// Item = (tile of 30 x 16 coarse outputs, chunk): chunks 0 .. nch-1 hold KCU
+// orders each, and chunk nch (when G_{l+1} is needed) the guide plane; items
+// reduce independently, so small levels still spread over many CTAs.  TMA
+// stages the 35 x 68 source box of an item into a ring of kUpSlots buffers,
+// kUpSlots - 1 items ahead of the one being reduced; the vertical pass reads
+// one staged column per thread and keeps the reduced rows in registers, the
+// horizontal pass reads 5 staged columns per output.
+template <typename S>
+__device__ __forceinline__ int up_chunks(const UpArgs& a) {
+  return cdiv(a.K, Smem<sizeof(typename Cplx<S>::T)>::up_kc) + (a.write_g ? 1 : 0);
+}
 template <typename S>
 __device__ __forceinline__ int up_items(const UpArgs& a) {
-  return cdiv(a.dst.w, kRsTW) * cdiv(a.dst.h, kRsTH) * a.planes *
-         cdiv(a.K, Smem<sizeof(typename Cplx<S>::T)>::up_kc);
+  return cdiv(a.dst.w, kRsTW) * cdiv(a.dst.h, kRsTH) * a.planes * up_chunks<S>(a);
 }
 
 template <typename S, typename Res>
@@ -256,78 +268,65 @@ __device__ __forceinline__ bool stage_up(Res res, int total, unsigned char* smem
   constexpr int HOUT = kRsTH / HQ;
   static_assert(RG * KCU * kRsVW == kThreads, "vertical mapping");
   static_assert(kRsTH % HQ == 0, "horizontal mapping");
-  unsigned char* bufs[2] = {smem, smem + SM::up_buf};
-  float2* vb = reinterpret_cast<float2*>(smem + 2 * SM::up_buf);
-  float* vg = reinterpret_cast<float*>(smem + 2 * SM::up_buf + SM::up_vb);
+  float2* vb = reinterpret_cast<float2*>(smem + kUpSlots * SM::up_slot);
+  float* vg = reinterpret_cast<float*>(smem + kUpSlots * SM::up_slot + SM::up_vb);
+  volatile int* abortp = abort_flag(bar);
   const int tid = threadIdx.x;
   const int nitems = b < total ? (total - b + G - 1) / G : 0;
-  auto issue = [&](int gi, int buf) {
+  auto issue = [&](int gi, int slot) {
     int li;
     const UpArgs& a = *res(gi, li);
-    const int nch = cdiv(a.K, KCU), t = li / nch, ch = li % nch;
+    const int nci = up_chunks<S>(a), nch = cdiv(a.K, KCU), t = li / nci, ch = li % nci;
     const int ntx = cdiv(a.dst.w, kRsTW), nty = cdiv(a.dst.h, kRsTH);
     const int tx = t % ntx, r = t / ntx, ty = r % nty, pl = r / nty;
     const int x = 2 * tx * kRsTW - 4, y = 2 * ty * kRsTH - 2;
-    const bool g = ch == 0 && a.write_g;
-    mbar_expect_tx(&bar[buf], (uint32_t)(sizeof(CT) * KCU * kRsIR * kRsBW +
-                                         (g ? sizeof(float) * kRsIR * kRsBW : 0)));
-    tma_load3(bufs[buf], &a.zmap, x, y, pl * a.K + ch * KCU, &bar[buf]);
-    if (g) tma_load3(bufs[buf] + SM::up_src, &a.gmap, x, y, pl, &bar[buf]);
+    unsigned char* dst = smem + slot * SM::up_slot;
+    if (ch < nch) {
+      mbar_expect_tx(&bar[slot], (uint32_t)(sizeof(CT) * KCU * kRsIR * kRsBW));
+      tma_load3(dst, &a.zmap, x, y, pl * a.K + ch * KCU, &bar[slot]);
+    } else {
+      mbar_expect_tx(&bar[slot], (uint32_t)(sizeof(float) * kRsIR * kRsBW));
+      tma_load3(dst, &a.gmap, x, y, pl, &bar[slot]);
+    }
   };
-  if (tid == 0 && nitems > 0) {
+  if (tid == 0) {
     fence_proxy_async();
-    issue(b, 0);
+    for (int j = 0; j < kUpSlots - 1 && j < nitems; ++j) issue(b + j * G, j);
   }
   for (int i = 0; i < nitems; ++i) {
-    const int buf = i & 1;
+    const int slot = i % kUpSlots;
     int li;
     const UpArgs& a = *res(b + i * G, li);
-    const int nch = cdiv(a.K, KCU), t = li / nch, ch = li % nch;
+    const int nci = up_chunks<S>(a), nch = cdiv(a.K, KCU), t = li / nci, ch = li % nci;
     const int ntx = cdiv(a.dst.w, kRsTW), nty = cdiv(a.dst.h, kRsTH);
     const int tx = t % ntx, rt = t / ntx, ty = rt % nty, pl = rt / nty;
     const int X1 = tx * kRsTW, Y1 = ty * kRsTH;
     const int xs = 2 * X1 - 4, ys = 2 * Y1 - 2;
-    const bool g = ch == 0 && a.write_g;
-    if (tid == 0 && i + 1 < nitems) {
+    if (tid == 0 && i + kUpSlots - 1 < nitems) {
       fence_proxy_async();
-      issue(b + (i + 1) * G, buf ^ 1);
+      issue(b + (i + kUpSlots - 1) * G, (i + kUpSlots - 1) % kUpSlots);
     }
-    if (!mbar_wait_cta(&bar[buf], pp.use[buf] & 1, a.fault)) {
-      if (tid == 0 && i + 1 < nitems) drain(&bar[buf ^ 1], pp.use[buf ^ 1] & 1);
-      return false;
-    }
-    ++pp.use[buf];
-    CT* src = reinterpret_cast<CT*>(bufs[buf]);
-    float* gsrc = reinterpret_cast<float*>(bufs[buf] + SM::up_src);
+    mbar_wait_thread(&bar[slot], pp.use[slot] & 1, a.fault, abortp);
+    ++pp.use[slot];
+    unsigned char* buf = smem + slot * SM::up_slot;
     auto my = [&](int y) { return refl101(y, a.src.h); };
     auto mx = [&](int x) { return refl101(x, a.src.w); };
-    fix_borders(src, KCU, kRsIR, kRsBW, xs, ys, a.src.w, a.src.h, my, mx);
-    if (g) fix_borders(gsrc, 1, kRsIR, kRsBW, xs, ys, a.src.w, a.src.h, my, mx);
-
-    {  // vertical half
-      const int rg = tid / (KCU * kRsVW), kk = (tid / kRsVW) % KCU, c = tid % kRsVW;
-      const CT* col = src + (kk * kRsIR + 2 * VOUT * rg) * kRsBW + c + 2;
-      float2 v[2 * VOUT + 3];
+    if (ch < nch) {
+      CT* src = reinterpret_cast<CT*>(buf);
+      fix_borders(src, KCU, kRsIR, kRsBW, xs, ys, a.src.w, a.src.h, my, mx);
+      {  // vertical half
+        const int rg = tid / (KCU * kRsVW), kk = (tid / kRsVW) % KCU, c = tid % kRsVW;
+        const CT* col = src + (kk * kRsIR + 2 * VOUT * rg) * kRsBW + c + 2;
+        float2 v[2 * VOUT + 3];
 #pragma unroll
-      for (int u = 0; u < 2 * VOUT + 3; ++u) v[u] = Cplx<S>::cvt(col[u * kRsBW]);
+        for (int u = 0; u < 2 * VOUT + 3; ++u) v[u] = Cplx<S>::cvt(col[u * kRsBW]);
 #pragma unroll
-      for (int j = 0; j < VOUT; ++j)
-        vb[(kk * kRsTH + VOUT * rg + j) * kRsVW + c] =
-            tap5(v[2 * j], v[2 * j + 1], v[2 * j + 2], v[2 * j + 3], v[2 * j + 4]);
-      if (g) {
-        const int grp = tid / kRsVW, cg = tid % kRsVW;  // 4 groups x 4 coarse rows
-        const float* gc = gsrc + (8 * grp) * kRsBW + cg + 2;
-        float u[11];
-#pragma unroll
-        for (int q = 0; q < 11; ++q) u[q] = gc[q * kRsBW];
-#pragma unroll
-        for (int j = 0; j < 4; ++j)
-          vg[(4 * grp + j) * kRsVW + cg] = tap5(u[2 * j], u[2 * j + 1], u[2 * j + 2], u[2 * j + 3], u[2 * j + 4]);
+        for (int j = 0; j < VOUT; ++j)
+          vb[(kk * kRsTH + VOUT * rg + j) * kRsVW + c] =
+              tap5(v[2 * j], v[2 * j + 1], v[2 * j + 2], v[2 * j + 3], v[2 * j + 4]);
       }
-    }
-    __syncthreads();
-    {  // horizontal half
-      if (tid < KCU * kRsTW * HQ) {
+      __syncthreads();
+      if (tid < KCU * kRsTW * HQ) {  // horizontal half
         const int hk = tid / (kRsTW * HQ), rem = tid % (kRsTW * HQ);
         const int hq = rem / kRsTW, ic = rem % kRsTW;
         const int k = ch * KCU + hk, x = X1 + ic;
@@ -348,13 +347,27 @@ __device__ __forceinline__ bool stage_up(Res res, int total, unsigned char* smem
           }
         }
       }
-      if (g && tid < 2 * kRsTW) {
-        const int half = tid / kRsTW, ic = tid % kRsTW, x = X1 + ic;
+    } else {
+      float* gsrc = reinterpret_cast<float*>(buf);
+      fix_borders(gsrc, 1, kRsIR, kRsBW, xs, ys, a.src.w, a.src.h, my, mx);
+      {  // vertical half: 4 groups x 4 coarse rows x 64 columns
+        const int grp = tid / kRsVW, cg = tid % kRsVW;
+        const float* gc = gsrc + (8 * grp) * kRsBW + cg + 2;
+        float u[11];
+#pragma unroll
+        for (int q = 0; q < 11; ++q) u[q] = gc[q * kRsBW];
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+          vg[(4 * grp + j) * kRsVW + cg] = tap5(u[2 * j], u[2 * j + 1], u[2 * j + 2], u[2 * j + 3], u[2 * j + 4]);
+      }
+      __syncthreads();
+      if (tid < kRsTW * 8) {  // horizontal half: 8 groups x 2 coarse rows x 30 columns
+        const int hq = tid / kRsTW, ic = tid % kRsTW, x = X1 + ic;
         if (x < a.dst.w) {
           float* Gp = a.dst.G + (long long)pl * a.dst.gplane + x;
 #pragma unroll
-          for (int j = 0; j < kRsTH / 2; ++j) {
-            const int jr = half * (kRsTH / 2) + j, y = Y1 + jr;
+          for (int j = 0; j < 2; ++j) {
+            const int jr = 2 * hq + j, y = Y1 + jr;
             if (y < a.dst.h) {
               const float* p = vg + jr * kRsVW + 2 * ic;
               Gp[(long long)y * a.dst.pitch] = (1.f / 256.f) * tap5(p[0], p[1], p[2], p[3], p[4]);
@@ -364,6 +377,13 @@ __device__ __forceinline__ bool stage_up(Res res, int total, unsigned char* smem
       }
     }
     __syncthreads();
+    if (*abortp) {
+      // leave with no copy in flight
+      if (tid == 0)
+        for (int j = i + 1; j < nitems && j < i + kUpSlots; ++j)
+          drain(&bar[j % kUpSlots], pp.use[j % kUpSlots] & 1);
+      return false;
+    }
   }
   return true;
 }
@@ -483,7 +503,7 @@ __device__ __forceinline__ bool stage_combine(Res res, int total, unsigned char*
                                               Pipe& pp, int b, int G) {
   using CT = typename Cplx<S>::T;
   using SM = Smem<sizeof(CT)>;
-  unsigned char* bufs[2] = {smem, smem + SM::dn_buf};
+  auto bufp = [&](int buf) { return smem + buf * SM::dn_buf; };
   const int tid = threadIdx.x;
   if (b >= total) return true;
   auto issue = [&](const CombineView& v, int lt, int ch, bool first, int buf) {
@@ -493,8 +513,8 @@ __device__ __forceinline__ bool stage_combine(Res res, int total, unsigned char*
     const bool e = first && v.has_e;
     mbar_expect_tx(&bar[buf], (uint32_t)(sizeof(CT) * kKC * kDnCH * kDnCW +
                                          (e ? sizeof(float) * kDnCH * kDnCW : 0)));
-    tma_load3(bufs[buf], v.zmap, cx0, cy0, pl * v.K + ch * kKC, &bar[buf]);
-    if (e) tma_load3(bufs[buf] + SM::dn_z, v.emap, cx0, cy0, pl, &bar[buf]);
+    tma_load4(bufp(buf), v.zmap, cx0, cy0, ch * kKC, pl, &bar[buf]);
+    if (e) tma_load3(bufp(buf) + SM::dn_z, v.emap, cx0, cy0, pl, &bar[buf]);
   };
   int t = b, lt = 0;
   CombineView v = res(t, lt);
@@ -551,8 +571,8 @@ __device__ __forceinline__ bool stage_combine(Res res, int total, unsigned char*
       return false;
     }
     ++pp.use[buf];
-    CT* zb = reinterpret_cast<CT*>(bufs[buf]);
-    float* eb = reinterpret_cast<float*>(bufs[buf] + SM::dn_z);
+    CT* zb = reinterpret_cast<CT*>(bufp(buf));
+    float* eb = reinterpret_cast<float*>(bufp(buf) + SM::dn_z);
     const Level& coarse = *v.coarse;
     auto my = [&](int y) { return ext_coarse(y, coarse.h, h); };
     auto mx = [&](int x) { return ext_coarse(x, coarse.w, w); };
@@ -564,48 +584,55 @@ __device__ __forceinline__ bool stage_combine(Res res, int total, unsigned char*
 #pragma unroll
       for (int q = 0; q < 4; ++q) base[q] = add2(base[q], ue[q]);
     }
+    // Orders k >= K of the highest chunk are staged as zeros (4-D map) and
+    // come first in the descending Horner run, where they leave P at zero.
+    const CT* zw = zb + tr * kDnCW + 2 * tc;
+    if constexpr (LEVEL0) {
 #pragma unroll
-    for (int kk = kKC - 1; kk >= 0; --kk) {
-      const int k = ch * kKC + kk;
-      if (k < v.K) {
+      for (int kk = kKC - 1; kk >= 0; --kk) {
         float2 ue[4], uo[4];
-        expand_2x4<S>(zb + kk * kDnCH * kDnCW + tr * kDnCW + 2 * tc, ue, uo);
-        if constexpr (LEVEL0) {
+        expand_2x4<S>(zw + kk * kDnCH * kDnCW, ue, uo);
 #pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            Pe[q] = horner(Pe[q], we[q], ue[q]);
-            Po[q] = horner(Po[q], wo[q], uo[q]);
-          }
-        } else {
-          const CT* Zk = reinterpret_cast<const CT*>(v.fine->Z) + (long long)pl * v.fine->zplane +
-                         (long long)k * v.fine->zk;
-          const CT* r0 = Zk + (long long)y0c * v.fine->pitch;
-          const CT* r1 = Zk + (long long)y1c * v.fine->pitch;
+        for (int q = 0; q < 4; ++q) {
+          Pe[q] = horner(Pe[q], we[q], ue[q]);
+          Po[q] = horner(Po[q], wo[q], uo[q]);
+        }
+      }
+    } else {
+      // one order at a time: the fine-level loads of all orders would not fit in registers
+#pragma unroll 1
+      for (int kk = kKC - 1; kk >= 0; --kk) {
+        float2 ue[4], uo[4];
+        expand_2x4<S>(zw + kk * kDnCH * kDnCW, ue, uo);
+        const int k = ch * kKC + kk;
+        const bool kin = k < v.K;
+        const CT* Zk = reinterpret_cast<const CT*>(v.fine->Z) + (long long)pl * v.fine->zplane +
+                       (long long)(kin ? k : 0) * v.fine->zk;
+        const CT* r0 = Zk + (long long)y0c * v.fine->pitch;
+        const CT* r1 = Zk + (long long)y1c * v.fine->pitch;
 #pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            CT zz0, zz1;
-            if constexpr (COH) {
-              if constexpr (sizeof(CT) == 8) {
-                const float2 f0 = __ldcg(reinterpret_cast<const float2*>(r0 + xq[q]));
-                const float2 f1 = __ldcg(reinterpret_cast<const float2*>(r1 + xq[q]));
-                zz0 = *reinterpret_cast<const CT*>(&f0);
-                zz1 = *reinterpret_cast<const CT*>(&f1);
-              } else {
-                const unsigned u0 = __ldcg(reinterpret_cast<const unsigned*>(r0 + xq[q]));
-                const unsigned u1 = __ldcg(reinterpret_cast<const unsigned*>(r1 + xq[q]));
-                zz0 = *reinterpret_cast<const CT*>(&u0);
-                zz1 = *reinterpret_cast<const CT*>(&u1);
-              }
+        for (int q = 0; q < 4; ++q) {
+          CT zz0, zz1;
+          if constexpr (COH) {
+            if constexpr (sizeof(CT) == 8) {
+              const float2 f0 = __ldcg(reinterpret_cast<const float2*>(r0 + xq[q]));
+              const float2 f1 = __ldcg(reinterpret_cast<const float2*>(r1 + xq[q]));
+              zz0 = *reinterpret_cast<const CT*>(&f0);
+              zz1 = *reinterpret_cast<const CT*>(&f1);
             } else {
-              zz0 = r0[xq[q]];
-              zz1 = r1[xq[q]];
+              const unsigned u0 = __ldcg(reinterpret_cast<const unsigned*>(r0 + xq[q]));
+              const unsigned u1 = __ldcg(reinterpret_cast<const unsigned*>(r1 + xq[q]));
+              zz0 = *reinterpret_cast<const CT*>(&u0);
+              zz1 = *reinterpret_cast<const CT*>(&u1);
             }
-            const float2 sc = expand_scale_pair(q);
-            const float2 de = fma2(splat(-sc.x), ue[q], Cplx<S>::cvt(zz0));
-            const float2 dd = fma2(splat(-sc.y), uo[q], Cplx<S>::cvt(zz1));
-            Pe[q] = horner(Pe[q], we[q], de);
-            Po[q] = horner(Po[q], wo[q], dd);
+          } else {
+            zz0 = r0[xq[q]];
+            zz1 = r1[xq[q]];
           }
+          const float2 sc = expand_scale_pair(q);
+          const float2 z0 = kin ? Cplx<S>::cvt(zz0) : splat(0.f), z1 = kin ? Cplx<S>::cvt(zz1) : splat(0.f);
+          Pe[q] = horner(Pe[q], we[q], fma2(splat(-sc.x), ue[q], z0));
+          Po[q] = horner(Po[q], wo[q], fma2(splat(-sc.y), uo[q], z1));
         }
       }
     }
@@ -672,8 +699,11 @@ __device__ __forceinline__ bool stage_down10(Res res, int total, unsigned char* 
                                             Pipe& pp, int b, int G) {
   using CT = typename Cplx<S>::T;
   using SM = Smem<sizeof(CT)>;
-  unsigned char* bufs[2] = {smem, smem + SM::d10_buf};
+  constexpr size_t kOffG1 = SM::d10_z1 + SM::d10_z2, kOffE2 = kOffG1 + SM::d10_g1;
+  constexpr size_t kOffI = kOffE2 + SM::d10_e2;
+  auto bufp = [&](int buf) { return smem + buf * SM::d10_buf; };
   float* e1 = reinterpret_cast<float*>(smem + 2 * SM::d10_buf);
+  volatile int* abortp = abort_flag(bar);
   const int tid = threadIdx.x;
   if (b >= total) return true;
   auto issue = [&](const Down10Args& a, int lt, int ch, bool first, int buf) {
@@ -681,17 +711,19 @@ __device__ __forceinline__ bool stage_down10(Res res, int total, unsigned char* 
     const int tx = lt % ntx, r = lt / ntx, ty = r % nty, pl = r / nty;
     const int cx0 = (tx * kDnOW - kDnX0) / 2 - 1, cy0 = ty * (kDnOH / 2) - 1;
     const int c2x = cx0 / 2 - 2, c2y = (cy0 - 1) / 2;
-    const bool e2 = first && a.has_e2;
+    const bool e2 = first && a.has_e2, in = first && a.use_tma;
     uint32_t bytes = (uint32_t)(sizeof(CT) * kKC * (kDnCH * kDnCW + kD2H * kD2W));
     if (first) bytes += (uint32_t)(sizeof(float) * kDnCH * kDnCW);
     if (e2) bytes += (uint32_t)(sizeof(float) * kD2H * kD2W);
+    if (in) bytes += (uint32_t)(sizeof(float) * kDnOH * kD0IW);
     mbar_expect_tx(&bar[buf], bytes);
-    unsigned char* p = bufs[buf];
-    const int z = pl * a.K + ch * kKC;
-    tma_load3(p, &a.z1map, cx0, cy0, z, &bar[buf]);
-    tma_load3(p + SM::d10_z1, &a.z2map, c2x, c2y, z, &bar[buf]);
-    if (first) tma_load3(p + SM::d10_z1 + SM::d10_z2, &a.g1map, cx0, cy0, pl, &bar[buf]);
-    if (e2) tma_load3(p + SM::d10_z1 + SM::d10_z2 + SM::d10_g1, &a.e2map, c2x, c2y, pl, &bar[buf]);
+    unsigned char* p = bufp(buf);
+    tma_load4(p, &a.z1map, cx0, cy0, ch * kKC, pl, &bar[buf]);
+    tma_load4(p + SM::d10_z1, &a.z2map, c2x, c2y, ch * kKC, pl, &bar[buf]);
+    if (first) tma_load3(p + kOffG1, &a.g1map, cx0, cy0, pl, &bar[buf]);
+    if (e2) tma_load3(p + kOffE2, &a.e2map, c2x, c2y, pl, &bar[buf]);
+    // level-0 input from X0 - 2 = 64 tx - 8 (x 4 bytes: 16-byte aligned)
+    if (in) tma_load3(p + kOffI, &a.imap, tx * kDnOW - kDnX0 - 2, ty * kDnOH, pl, &bar[buf]);
   };
   int t = b, lt = 0;
   const Down10Args* a = res(t, lt);
@@ -702,8 +734,10 @@ __device__ __forceinline__ bool stage_down10(Res res, int total, unsigned char* 
   }
 
   const int tc = tid % (kDnOW / 4), tr = tid / (kDnOW / 4);
-  const bool l1t = tid < kB1X * kB1Y;
-  const int bc = tid % kB1X, br = tid / kB1X;
+  // level-1 blocks 20 w .. 20 w + 19 on lanes 0..19 of warp w
+  const int lane = tid & 31, b1 = (tid >> 5) * kB1PerWarp + lane;
+  const bool l1t = lane < kB1PerWarp && b1 < kB1X * kB1Y;
+  const int bc = b1 % kB1X, br = b1 / kB1X;
   float2 we[4], wo[4], Pe[4], Po[4], base[4];
   float2 w1[2][2], P1[2][2];
   float up_e2[2][2];
@@ -729,32 +763,44 @@ __device__ __forceinline__ bool stage_down10(Res res, int total, unsigned char* 
         issue(*an, ln, cdiv(an->K, kKC) - 1, true, buf ^ 1);
       }
     }
+    // level-0 state: e^{-i w_1 I}, Horner sums, and I itself
+    auto init0 = [&](int q, float g0, float g1) {
+      we[q] = conj_turns(a->turns * g0);
+      wo[q] = conj_turns(a->turns * g1);
+      Pe[q] = Po[q] = splat(0.f);
+      base[q] = make_float2(g0, g1);
+    };
     if (first) {
-      // level-0 state: e^{-i w_1 I}, Horner sums, and I itself
       fy = Y0 + 2 * tr;
       fx = X0 + 4 * tc;
-      const int y0c = min(fy, h0 - 1), y1c = min(fy + 1, h0 - 1);
-      const float* Ip = a->I + (long long)pl * h0 * w0;
+      if (!a->use_tma) {
+        const int y0c = min(fy, h0 - 1), y1c = min(fy + 1, h0 - 1);
+        const float* Ip = a->I + (long long)pl * h0 * w0;
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const int xq = min(max(fx + q, 0), w0 - 1);
-        const float g0 = __ldg(Ip + (long long)y0c * w0 + xq);
-        const float g1 = __ldg(Ip + (long long)y1c * w0 + xq);
-        we[q] = conj_turns(a->turns * g0);
-        wo[q] = conj_turns(a->turns * g1);
-        Pe[q] = Po[q] = splat(0.f);
-        base[q] = make_float2(g0, g1);
+        for (int q = 0; q < 4; ++q) {
+          const int xq = min(max(fx + q, 0), w0 - 1);
+          init0(q, __ldg(Ip + (long long)y0c * w0 + xq), __ldg(Ip + (long long)y1c * w0 + xq));
+        }
       }
     }
-    if (!mbar_wait_cta(&bar[buf], pp.use[buf] & 1, a->fault)) {
-      if (tid == 0 && has_next) drain(&bar[buf ^ 1], pp.use[buf ^ 1] & 1);
-      return false;
-    }
+    mbar_wait_thread(&bar[buf], pp.use[buf] & 1, a->fault, abortp);
     ++pp.use[buf];
-    CT* z1b = reinterpret_cast<CT*>(bufs[buf]);
-    CT* z2b = reinterpret_cast<CT*>(bufs[buf] + SM::d10_z1);
-    const float* g1b = reinterpret_cast<const float*>(bufs[buf] + SM::d10_z1 + SM::d10_z2);
-    float* e2b = reinterpret_cast<float*>(bufs[buf] + SM::d10_z1 + SM::d10_z2 + SM::d10_g1);
+    CT* z1b = reinterpret_cast<CT*>(bufp(buf));
+    CT* z2b = reinterpret_cast<CT*>(bufp(buf) + SM::d10_z1);
+    const float* g1b = reinterpret_cast<const float*>(bufp(buf) + kOffG1);
+    float* e2b = reinterpret_cast<float*>(bufp(buf) + kOffE2);
+    if (first && a->use_tma) {
+      // staged input: fine pixel (fy + rr, fx + q) at row 2 tr + rr, column 4 tc + 2 + q
+      // (zero outside the image; those pixels are not stored)
+      const float* ib = reinterpret_cast<const float*>(bufp(buf) + kOffI) + 2 * tr * kD0IW + 4 * tc + 2;
+      const float2 a0 = *reinterpret_cast<const float2*>(ib), a1 = *reinterpret_cast<const float2*>(ib + 2);
+      const float2 c0 = *reinterpret_cast<const float2*>(ib + kD0IW);
+      const float2 c1 = *reinterpret_cast<const float2*>(ib + kD0IW + 2);
+      init0(0, a0.x, c0.x);
+      init0(1, a0.y, c0.y);
+      init0(2, a1.x, c1.x);
+      init0(3, a1.y, c1.y);
+    }
     const Level& L1 = a->l1;
     const Level& L2 = a->l2;
     auto my1 = [&](int y) { return ext_coarse(y, L1.h, h0); };
@@ -791,11 +837,13 @@ __device__ __forceinline__ bool stage_down10(Res res, int total, unsigned char* 
           up_e2[1][1] = (1.f / 16.f) * (ve[1] + ve[2]);
         }
       }
+      // orders k >= K read as zeros (4-D maps) and leave P at zero
+      const CT* zw2 = z2b + br * kD2W + bc + 1;
+      const CT* zc1 = z1b + 2 * br * kDnCW + 2 * bc;
 #pragma unroll
       for (int kk = kKC - 1; kk >= 0; --kk) {
-        const int k = ch * kKC + kk;
-        if (k < a->K) {
-          const CT* zw = z2b + kk * kD2H * kD2W + br * kD2W + bc + 1;
+        {
+          const CT* zw = zw2 + kk * kD2H * kD2W;
           float2 vo[3], ve[3];
 #pragma unroll
           for (int c = 0; c < 3; ++c) {
@@ -810,7 +858,7 @@ __device__ __forceinline__ bool stage_down10(Res res, int total, unsigned char* 
           U[0][1] = mul2(splat(1.f / 4.f), add2(vo[1], vo[2]));
           U[1][0] = mul2(splat(1.f / 64.f), fma2(splat(6.f), ve[1], add2(ve[0], ve[2])));
           U[1][1] = mul2(splat(1.f / 16.f), add2(ve[1], ve[2]));
-          const CT* zc = z1b + kk * kDnCH * kDnCW + 2 * br * kDnCW + 2 * bc;
+          const CT* zc = zc1 + kk * kDnCH * kDnCW;
 #pragma unroll
           for (int rr = 0; rr < 2; ++rr) {
             float2 f[2];
@@ -832,17 +880,15 @@ __device__ __forceinline__ bool stage_down10(Res res, int total, unsigned char* 
     }
 
     // level-0 combine (Horner over this chunk's orders)
+    const CT* zw0 = z1b + tr * kDnCW + 2 * tc;
 #pragma unroll
     for (int kk = kKC - 1; kk >= 0; --kk) {
-      const int k = ch * kKC + kk;
-      if (k < a->K) {
-        float2 ue[4], uo[4];
-        expand_2x4<S>(z1b + kk * kDnCH * kDnCW + tr * kDnCW + 2 * tc, ue, uo);
+      float2 ue[4], uo[4];
+      expand_2x4<S>(zw0 + kk * kDnCH * kDnCW, ue, uo);
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          Pe[q] = horner(Pe[q], we[q], ue[q]);
-          Po[q] = horner(Po[q], wo[q], uo[q]);
-        }
+      for (int q = 0; q < 4; ++q) {
+        Pe[q] = horner(Pe[q], we[q], ue[q]);
+        Po[q] = horner(Po[q], wo[q], uo[q]);
       }
     }
 
@@ -878,6 +924,10 @@ __device__ __forceinline__ bool stage_down10(Res res, int total, unsigned char* 
       }
     }
     __syncthreads();
+    if (*abortp) {
+      if (tid == 0 && has_next) drain(&bar[buf ^ 1], pp.use[buf ^ 1] & 1);
+      return false;
+    }
     if (!last) {
       --ch;
     } else {
@@ -899,7 +949,7 @@ __global__ void __launch_bounds__(kThreads) k_up0(const __grid_constant__ Up0Arg
   extern __shared__ __align__(128) unsigned char smem[];
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem + SM::up0 - 64);
   init_bars(bar);
-  Pipe pp{{0u, 0u}};
+  Pipe pp{};
   stage_up0<S>([&](int g, int& l) { l = g; return &a; }, up0_tiles(a), smem, bar, pp, blockIdx.x,
                gridDim.x);
 }
@@ -910,18 +960,18 @@ __global__ void __launch_bounds__(kThreads) k_up(const __grid_constant__ UpArgs 
   extern __shared__ __align__(128) unsigned char smem[];
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem + SM::up - 64);
   init_bars(bar);
-  Pipe pp{{0u, 0u}};
+  Pipe pp{};
   stage_up<S>([&](int g, int& l) { l = g; return &a; }, up_items<S>(a), smem, bar, pp, blockIdx.x,
               gridDim.x);
 }
 
 template <typename S>
-__global__ void __launch_bounds__(kThreads) k_down(const __grid_constant__ DownArgs a) {
+__global__ void __launch_bounds__(kThreads, 2) k_down(const __grid_constant__ DownArgs a) {
   using SM = Smem<sizeof(typename Cplx<S>::T)>;
   extern __shared__ __align__(128) unsigned char smem[];
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem + SM::dn - 64);
   init_bars(bar);
-  Pipe pp{{0u, 0u}};
+  Pipe pp{};
   const CombineView v = view_of(a);
   stage_combine<S, false, false>([&](int g, int& l) { l = g; return v; }, combine_tiles(v), smem, bar,
                                  pp, blockIdx.x, gridDim.x);
@@ -933,7 +983,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_down0(const __grid_constant__ D
   extern __shared__ __align__(128) unsigned char smem[];
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem + SM::dn - 64);
   init_bars(bar);
-  Pipe pp{{0u, 0u}};
+  Pipe pp{};
   const CombineView v = view_of(a);
   stage_combine<S, true, false>([&](int g, int& l) { l = g; return v; }, combine_tiles(v), smem, bar,
                                 pp, blockIdx.x, gridDim.x);
@@ -945,7 +995,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_down10(const __grid_constant__ 
   extern __shared__ __align__(128) unsigned char smem[];
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem + SM::d10 - 64);
   init_bars(bar);
-  Pipe pp{{0u, 0u}};
+  Pipe pp{};
   stage_down10<S>([&](int g, int& l) { l = g; return &a; }, combine_tiles(a.h0, a.w0, a.planes), smem, bar,
                   pp, blockIdx.x, gridDim.x);
 }
@@ -968,7 +1018,7 @@ __global__ void __launch_bounds__(kThreads) k_up0_batch(const BatchTable<Up0Args
   extern __shared__ __align__(128) unsigned char smem[];
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem + SM::up0 - 64);
   init_bars(bar);
-  Pipe pp{{0u, 0u}};
+  Pipe pp{};
   stage_up0<S>([&](int g, int& l) {
                  const int j = find_entry(tb.prefix, tb.n, g);
                  l = g - __ldg(tb.prefix + j);
@@ -987,7 +1037,7 @@ __global__ void __launch_bounds__(kThreads) k_up_batch(const BatchTable<UpArgs> 
     fence_tensormap(&a.gmap);
   });
   init_bars(bar);
-  Pipe pp{{0u, 0u}};
+  Pipe pp{};
   stage_up<S>([&](int g, int& l) {
                 const int j = find_entry(tb.prefix, tb.n, g);
                 l = g - __ldg(tb.prefix + j);
@@ -997,7 +1047,7 @@ __global__ void __launch_bounds__(kThreads) k_up_batch(const BatchTable<UpArgs> 
 }
 
 template <typename S>
-__global__ void __launch_bounds__(kThreads) k_down_batch(const BatchTable<DownArgs> tb) {
+__global__ void __launch_bounds__(kThreads, 2) k_down_batch(const BatchTable<DownArgs> tb) {
   using SM = Smem<sizeof(typename Cplx<S>::T)>;
   extern __shared__ __align__(128) unsigned char smem[];
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem + SM::dn - 64);
@@ -1006,7 +1056,7 @@ __global__ void __launch_bounds__(kThreads) k_down_batch(const BatchTable<DownAr
     fence_tensormap(&a.emap);
   });
   init_bars(bar);
-  Pipe pp{{0u, 0u}};
+  Pipe pp{};
   stage_combine<S, false, false>(
       [&](int g, int& l) {
         const int j = find_entry(tb.prefix, tb.n, g);
@@ -1026,7 +1076,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_down0_batch(const BatchTable<Do
     fence_tensormap(&a.emap);
   });
   init_bars(bar);
-  Pipe pp{{0u, 0u}};
+  Pipe pp{};
   stage_combine<S, true, false>(
       [&](int g, int& l) {
         const int j = find_entry(tb.prefix, tb.n, g);
@@ -1076,13 +1126,13 @@ __device__ __forceinline__ bool grid_barrier(unsigned* count, unsigned* gen, uns
 // All stages from level c0 down: REDUCE c0 -> ... -> top, then the combines
 // top-1 ... c0, in one cooperative launch with grid barriers between stages.
 template <typename S>
-__global__ void __launch_bounds__(kThreads) k_chain(const __grid_constant__ ChainArgs a) {
+__global__ void __launch_bounds__(kThreads, 2) k_chain(const __grid_constant__ ChainArgs a) {
   using SM = Smem<sizeof(typename Cplx<S>::T)>;
   constexpr size_t kS = SM::up > SM::dn ? SM::up : SM::dn;
   extern __shared__ __align__(128) unsigned char smem[];
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem + kS - 64);
   init_bars(bar);
-  Pipe pp{{0u, 0u}};
+  Pipe pp{};
   const int b = blockIdx.x, G = gridDim.x;
   for (int st = 0; st < a.n_up; ++st) {
     const UpArgs* u = &a.up[st];
@@ -1127,7 +1177,8 @@ cudaError_t FLLF_LAUNCH_NAME(up0)(const Up0Args& a, cudaStream_t s) {
 }
 
 cudaError_t FLLF_LAUNCH_NAME(up)(const UpArgs& a, cudaStream_t s) {
-  const int items = cdiv(a.dst.w, kRsTW) * cdiv(a.dst.h, kRsTH) * a.planes * cdiv(a.K, SMS::up_kc);
+  const int items = cdiv(a.dst.w, kRsTW) * cdiv(a.dst.h, kRsTH) * a.planes *
+                    (cdiv(a.K, SMS::up_kc) + (a.write_g ? 1 : 0));
   const int grid = persistent_grid(k_up<FLLF_STORAGE>, SMS::up, items);
   k_up<FLLF_STORAGE><<<grid, kThreads, SMS::up, s>>>(a);
   return cudaGetLastError();

@@ -32,6 +32,21 @@ PFN_cuTensorMapEncodeTiled_v12000 encoder() {
 }
 
 // 3-D tiled map (x = column, y = row, z = plane) with zero fill outside.
+// 4-D tiled map of a Fourier level (x = column, y = row, z = order, w = plane).
+bool encode4(CUtensorMap* m, CUtensorMapDataType dt, const void* base, uint64_t w, uint64_t h,
+             uint64_t K, uint64_t planes, uint64_t row_bytes, uint64_t order_bytes, uint64_t plane_bytes,
+             uint32_t bx, uint32_t by, uint32_t bz) {
+  auto enc = encoder();
+  if (!enc) return false;
+  cuuint64_t dims[4] = {w, h, K, planes};
+  cuuint64_t strides[3] = {row_bytes, order_bytes, plane_bytes};
+  cuuint32_t box[4] = {bx, by, bz, 1};
+  cuuint32_t estr[4] = {1, 1, 1, 1};
+  return enc(m, dt, 4, const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+             CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 bool encode3(CUtensorMap* m, CUtensorMapDataType dt, size_t esize, const void* base, uint64_t w,
              uint64_t h, uint64_t planes, uint64_t row_bytes, uint64_t plane_bytes, uint32_t bx,
              uint32_t by, uint32_t bz) {
@@ -108,7 +123,8 @@ bool build_maps(const fllf_params& p, const std::vector<Level>& lv, PathMaps* m)
     const uint64_t grow = 4ull * v.pitch, gplane = 4ull * (uint64_t)v.gplane;
     const uint64_t zplanes = (uint64_t)p.K * p.C;
     // as the coarse level of a combine: 36 x 18 window, kKC orders
-    if (!encode3(&m->z_dn[l], zdt, zs, v.Z, v.w, v.h, zplanes, zrow, zplane, kDnCW, kDnCH, kKC))
+    if (!encode4(&m->z_dn[l], zdt, v.Z, v.w, v.h, p.K, p.C, zrow, zs * (uint64_t)v.zk,
+                 zs * (uint64_t)v.zplane, kDnCW, kDnCH, kKC))
       return false;
     // as the source of a REDUCE: 68 x 35 box, up_kc orders; plus the guide
     if (l <= L - 2) {
@@ -132,8 +148,8 @@ bool build_maps(const fllf_params& p, const std::vector<Level>& lv, PathMaps* m)
     if (!encode3(&m->g1_d10, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, v1.G, v1.w, v1.h, p.C, 4ull * v1.pitch,
                  4ull * (uint64_t)v1.gplane, kDnCW, kDnCH, 1))
       return false;
-    if (!encode3(&m->z2_d10, zdt, zs, v2.Z, v2.w, v2.h, (uint64_t)p.K * p.C, zs * v2.pitch,
-                 zs * (uint64_t)v2.zk, kD2W, kD2H, kKC))
+    if (!encode4(&m->z2_d10, zdt, v2.Z, v2.w, v2.h, p.K, p.C, zs * v2.pitch, zs * (uint64_t)v2.zk,
+                 zs * (uint64_t)v2.zplane, kD2W, kD2H, kKC))
       return false;
     if (v2.E && !encode3(&m->e2_d10, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, v2.E, v2.w, v2.h, p.C,
                          4ull * v2.pitch, 4ull * (uint64_t)v2.gplane, kD2W, kD2H, 1))
@@ -256,6 +272,10 @@ cudaError_t enqueue_path(const fllf_params& p, const std::vector<Level>& lv, con
     d.K = p.K;
     d.turns = turns;
     d.has_e2 = (L >= 4) ? 1 : 0;
+    d.use_tma = (u0.use_tma && encode3(&d.imap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, d_in, p.W, p.H, C,
+                                       4ull * p.W, 4ull * p.W * p.H, kD0IW, kDnOH, 1))
+                    ? 1
+                    : 0;
     d.fault = fault;
     mark(FLLF_STAGE_DOWN0, true);
     if ((e = launch_down10(prec, d, s)) != cudaSuccess) return e;
