@@ -137,11 +137,12 @@ void build_batch_blob(const std::vector<const fllf_plan*>& plans, int prec, Batc
       const int L = pl->p.levels;
       if (l > L - 2) continue;
       DownArgs d{};
-      d.zmap = pl->maps.z_dn[l + 1];
+      d.zmap = pl->maps.z_dn1[l + 1];
       d.emap = pl->maps.e_dn[l + 1];
+      d.zfmap = pl->maps.z_fn[l];
+      d.gfmap = pl->maps.g_fn[l];
       d.fine = pl->lv[l];
       d.coarse = pl->lv[l + 1];
-      d.a = pl->d_a;
       d.planes = pl->p.C;
       d.K = pl->p.K;
       d.turns = (float)(2.0 / pl->p.T);
@@ -163,7 +164,6 @@ void build_batch_blob(const std::vector<const fllf_plan*>& plans, int prec, Batc
       d.w0 = pl->p.W;
       d.planes = pl->p.C;
       d.coarse = pl->lv[1];
-      d.a = pl->d_a;
       d.K = pl->p.K;
       d.turns = (float)(2.0 / pl->p.T);
       d.has_e = pl->p.levels >= 3 ? 1 : 0;

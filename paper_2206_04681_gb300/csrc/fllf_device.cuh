@@ -93,11 +93,12 @@ struct UpArgs {
 };
 
 struct DownArgs {
-  CUtensorMap zmap;     // coarse Z_{l+1}
-  CUtensorMap emap;     // coarse E_{l+1}
+  CUtensorMap zmap;     // coarse Z_{l+1}: 36 x 18 x kKC1 window
+  CUtensorMap emap;     // coarse E_{l+1}: 36 x 18 window
+  CUtensorMap zfmap;    // fine Z_l: 68 x 32 x kKC1 box from (X0 - 2, Y0)
+  CUtensorMap gfmap;    // fine G_l: 68 x 32 box from (X0 - 2, Y0)
   Level fine;           // level l >= 1: G, Z read, E written
   Level coarse;         // level l+1
-  const float* a;       // a_1..a_K (float32)
   int planes, K;
   float turns;
   int has_e;            // E_{l+1} exists (l+1 <= levels-2)
@@ -111,7 +112,6 @@ struct Down0Args {
   float* O;             // level-0 output, pitch w0
   int h0, w0, planes;
   Level coarse;         // level 1
-  const float* a;
   int K;
   float turns;
   int has_e;            // E_1 exists (levels >= 3)
@@ -201,6 +201,7 @@ static_assert((kDnOW / 4) * (kDnOH / 2) == kThreads, "combine thread mapping");
 constexpr int kD2W = 20, kD2H = 11;
 constexpr int kB1X = 17, kB1Y = 9;
 constexpr int kB1PerWarp = 20;            // level-1 blocks per warp (lanes 0..19)
+constexpr int kKC1 = 2;                   // orders per chunk of the level >= 1 combine
 constexpr int kD0IW = kDnOW + 4;          // staged level-0 input columns (from X0 - 2)
 static_assert(kB1X * kB1Y <= kThreads && 2 * kB1X == kDnCW - 2 && 2 * kB1Y == kDnCH,
               "level-1 blocks cover the used window");
@@ -231,6 +232,13 @@ struct Smem {
   static constexpr size_t dn_e = align128(sizeof(float) * kDnCH * kDnCW);
   static constexpr size_t dn_buf = dn_z + dn_e;
   static constexpr size_t dn = 2 * dn_buf + 64;
+  // combine at level >= 1: fine Z_l and G_l boxes, coarse Z_{l+1} and E_{l+1} windows
+  static constexpr size_t dn1_zf = align128((size_t)ESZ * kKC1 * kDnOH * kD0IW);
+  static constexpr size_t dn1_zc = align128((size_t)ESZ * kKC1 * kDnCH * kDnCW);
+  static constexpr size_t dn1_e = align128(sizeof(float) * kDnCH * kDnCW);
+  static constexpr size_t dn1_g = align128(sizeof(float) * kDnOH * kD0IW);
+  static constexpr size_t dn1_buf = dn1_zf + dn1_zc + dn1_e + dn1_g;
+  static constexpr size_t dn1 = 2 * dn1_buf + 64;
   // fused level-1/level-0 combine
   static constexpr size_t d10_z1 = dn_z;
   static constexpr size_t d10_z2 = align128((size_t)ESZ * kKC * kD2H * kD2W);
@@ -258,6 +266,33 @@ __device__ __forceinline__ int ext_coarse(int j, int m, int n) {
   if (j < 0) return 1;
   if (j >= m) return (n & 1) ? m - 2 : m - 1;
   return j;
+}
+
+// x / d and x % d for 0 <= x < 2^22 and 1 <= d (work-item and tile indices):
+// the float quotient is off by at most one, which one correction step fixes.
+// A few instructions instead of the generic 32-bit division sequence.
+__device__ __forceinline__ int div_fast(int x, int d, int& rem) {
+  int q = __float2int_rz(__int2float_rn(x) * __frcp_rn(__int2float_rn(d)));
+  int r = x - q * d;
+  if (r < 0) {
+    --q;
+    r += d;
+  } else if (r >= d) {
+    ++q;
+    r -= d;
+  }
+  rem = r;
+  return q;
+}
+// Tile t of a grid ntx x nty x planes (x fastest).
+struct TileXY {
+  int tx, ty, pl;
+};
+__device__ __forceinline__ TileXY tile_of(int t, int ntx, int nty) {
+  TileXY o;
+  const int r = div_fast(t, ntx, o.tx);
+  o.pl = div_fast(r, nty, o.ty);
+  return o;
 }
 
 __device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }

@@ -71,6 +71,9 @@ struct PathMaps {
   std::vector<CUtensorMap> e_dn;  // E_l read as the coarse level of a combine
   std::vector<CUtensorMap> z_up;  // Z_l read as the source of a REDUCE
   std::vector<CUtensorMap> g_up;  // G_l read as the source of a REDUCE
+  std::vector<CUtensorMap> z_dn1; // Z_l read as the coarse level of a level >= 1 combine (kKC1 orders)
+  std::vector<CUtensorMap> z_fn;  // Z_l read as the fine level of a combine (kKC1 orders)
+  std::vector<CUtensorMap> g_fn;  // G_l read as the fine level of a combine
   // fused level-1/level-0 combine (levels >= 3)
   CUtensorMap g1_d10{};           // G_1 on the level-1 window
   CUtensorMap z2_d10{};           // Z_2 on the level-2 window

@@ -78,10 +78,9 @@ __device__ __forceinline__ bool stage_up0(Res res, int total, unsigned char* sme
   float* hg = reinterpret_cast<float*>(smem + 2 * SM::up0_it + align128(SM::up0_hz));
   const int tid = threadIdx.x;
   auto issue = [&](const Up0Args& a, int t, int buf) {
-    const int ntx = cdiv(a.dst.w, kUpTW), nty = cdiv(a.dst.h, kUpTH);
-    const int tx = t % ntx, r = t / ntx, ty = r % nty, pl = r / nty;
+    const TileXY g = tile_of(t, cdiv(a.dst.w, kUpTW), cdiv(a.dst.h, kUpTH));
     mbar_expect_tx(&bar[buf], sizeof(float) * kUpIR * kUpIW);
-    tma_load3(itb(buf), &a.imap, 2 * tx * kUpTW - 4, 2 * ty * kUpTH - 2, pl, &bar[buf]);
+    tma_load3(itb(buf), &a.imap, 2 * g.tx * kUpTW - 4, 2 * g.ty * kUpTH - 2, g.pl, &bar[buf]);
   };
   if (b < total && tid == 0) {
     int lt;
@@ -96,9 +95,9 @@ __device__ __forceinline__ bool stage_up0(Res res, int total, unsigned char* sme
     const int buf = n & 1;
     int t;
     const Up0Args& a = *res(gt, t);
-    const int ntx = cdiv(a.dst.w, kUpTW), nty = cdiv(a.dst.h, kUpTH);
-    const int tx = t % ntx, rt = t / ntx, ty = rt % nty, pl = rt / nty;
-    const int X1 = tx * kUpTW, Y1 = ty * kUpTH;
+    const TileXY gxy = tile_of(t, cdiv(a.dst.w, kUpTW), cdiv(a.dst.h, kUpTH));
+    const int pl = gxy.pl;
+    const int X1 = gxy.tx * kUpTW, Y1 = gxy.ty * kUpTH;
     const int xs = 2 * X1 - 4, ys = 2 * Y1 - 2;
     const int nch = cdiv(a.K, kKC);
     float* it = itb(buf);
@@ -276,10 +275,11 @@ __device__ __forceinline__ bool stage_up(Res res, int total, unsigned char* smem
   auto issue = [&](int gi, int slot) {
     int li;
     const UpArgs& a = *res(gi, li);
-    const int nci = up_chunks<S>(a), nch = cdiv(a.K, KCU), t = li / nci, ch = li % nci;
-    const int ntx = cdiv(a.dst.w, kRsTW), nty = cdiv(a.dst.h, kRsTH);
-    const int tx = t % ntx, r = t / ntx, ty = r % nty, pl = r / nty;
-    const int x = 2 * tx * kRsTW - 4, y = 2 * ty * kRsTH - 2;
+    int ch;
+    const int nch = cdiv(a.K, KCU), t = div_fast(li, up_chunks<S>(a), ch);
+    const TileXY g = tile_of(t, cdiv(a.dst.w, kRsTW), cdiv(a.dst.h, kRsTH));
+    const int pl = g.pl;
+    const int x = 2 * g.tx * kRsTW - 4, y = 2 * g.ty * kRsTH - 2;
     unsigned char* dst = smem + slot * SM::up_slot;
     if (ch < nch) {
       mbar_expect_tx(&bar[slot], (uint32_t)(sizeof(CT) * KCU * kRsIR * kRsBW));
@@ -297,10 +297,11 @@ __device__ __forceinline__ bool stage_up(Res res, int total, unsigned char* smem
     const int slot = i % kUpSlots;
     int li;
     const UpArgs& a = *res(b + i * G, li);
-    const int nci = up_chunks<S>(a), nch = cdiv(a.K, KCU), t = li / nci, ch = li % nci;
-    const int ntx = cdiv(a.dst.w, kRsTW), nty = cdiv(a.dst.h, kRsTH);
-    const int tx = t % ntx, rt = t / ntx, ty = rt % nty, pl = rt / nty;
-    const int X1 = tx * kRsTW, Y1 = ty * kRsTH;
+    int ch;
+    const int nch = cdiv(a.K, KCU), t = div_fast(li, up_chunks<S>(a), ch);
+    const TileXY gxy = tile_of(t, cdiv(a.dst.w, kRsTW), cdiv(a.dst.h, kRsTH));
+    const int pl = gxy.pl;
+    const int X1 = gxy.tx * kRsTW, Y1 = gxy.ty * kRsTH;
     const int xs = 2 * X1 - 4, ys = 2 * Y1 - 2;
     if (tid == 0 && i + kUpSlots - 1 < nitems) {
       fence_proxy_async();
@@ -473,24 +474,19 @@ __device__ __forceinline__ float2 conj_turns(float t) {
   return make_float2(z.x, -z.y);
 }
 
-// Uniform view of the level >= 1 and level-0 combine arguments.
+// View of the level-0 combine arguments.
 struct CombineView {
   const CUtensorMap* zmap;
   const CUtensorMap* emap;
-  const Level* fine;    // level >= 1 only
-  const float* I;       // level 0 only
-  float* O;             // level 0 only
+  const float* I;
+  float* O;
   const Level* coarse;
   unsigned* fault;
   int h, w, planes, K, has_e;
   float turns;
 };
-__device__ __forceinline__ CombineView view_of(const DownArgs& d) {
-  return CombineView{&d.zmap, &d.emap, &d.fine, nullptr, nullptr, &d.coarse, d.fault,
-                     d.fine.h, d.fine.w, d.planes, d.K, d.has_e, d.turns};
-}
 __device__ __forceinline__ CombineView view_of(const Down0Args& d) {
-  return CombineView{&d.zmap, &d.emap, nullptr, d.I, d.O, &d.coarse, d.fault,
+  return CombineView{&d.zmap, &d.emap, d.I, d.O, &d.coarse, d.fault,
                      d.h0, d.w0, d.planes, d.K, d.has_e, d.turns};
 }
 __device__ __forceinline__ int combine_tiles(int h, int w, int planes) {
@@ -498,23 +494,24 @@ __device__ __forceinline__ int combine_tiles(int h, int w, int planes) {
 }
 __device__ __forceinline__ int combine_tiles(const CombineView& v) { return combine_tiles(v.h, v.w, v.planes); }
 
-template <typename S, bool LEVEL0, bool COH, typename Res>
-__device__ __forceinline__ bool stage_combine(Res res, int total, unsigned char* smem, uint64_t* bar,
-                                              Pipe& pp, int b, int G) {
+// Level-0 combine alone (levels == 2, where E_1 = 0 and no level-1 combine
+// exists, and the batched path).
+template <typename S, typename Res>
+__device__ __forceinline__ bool stage_combine0(Res res, int total, unsigned char* smem, uint64_t* bar,
+                                               Pipe& pp, int b, int G) {
   using CT = typename Cplx<S>::T;
   using SM = Smem<sizeof(CT)>;
   auto bufp = [&](int buf) { return smem + buf * SM::dn_buf; };
   const int tid = threadIdx.x;
   if (b >= total) return true;
   auto issue = [&](const CombineView& v, int lt, int ch, bool first, int buf) {
-    const int ntx = cdiv(v.w + kDnX0, kDnOW), nty = cdiv(v.h, kDnOH);
-    const int tx = lt % ntx, r = lt / ntx, ty = r % nty, pl = r / nty;
-    const int cx0 = (tx * kDnOW - kDnX0) / 2 - 1, cy0 = ty * (kDnOH / 2) - 1;
+    const TileXY g = tile_of(lt, cdiv(v.w + kDnX0, kDnOW), cdiv(v.h, kDnOH));
+    const int cx0 = (g.tx * kDnOW - kDnX0) / 2 - 1, cy0 = g.ty * (kDnOH / 2) - 1;
     const bool e = first && v.has_e;
     mbar_expect_tx(&bar[buf], (uint32_t)(sizeof(CT) * kKC * kDnCH * kDnCW +
                                          (e ? sizeof(float) * kDnCH * kDnCW : 0)));
-    tma_load4(bufp(buf), v.zmap, cx0, cy0, ch * kKC, pl, &bar[buf]);
-    if (e) tma_load3(bufp(buf) + SM::dn_z, v.emap, cx0, cy0, pl, &bar[buf]);
+    tma_load4(bufp(buf), v.zmap, cx0, cy0, ch * kKC, g.pl, &bar[buf]);
+    if (e) tma_load3(bufp(buf) + SM::dn_z, v.emap, cx0, cy0, g.pl, &bar[buf]);
   };
   int t = b, lt = 0;
   CombineView v = res(t, lt);
@@ -526,15 +523,18 @@ __device__ __forceinline__ bool stage_combine(Res res, int total, unsigned char*
 
   const int tc = tid % (kDnOW / 4), tr = tid / (kDnOW / 4);
   float2 we[4], wo[4], Pe[4], Po[4], base[4];
-  int xq[4], y0c = 0, y1c = 0, fy = 0, fx = 0, pl = 0;
+  int fy = 0, fx = 0, pl = 0, X0 = 0, Y0 = 0;
   for (int i = 0;; ++i) {
     const int buf = i & 1;
-    const int ntx = cdiv(v.w + kDnX0, kDnOW), nty = cdiv(v.h, kDnOH);
-    const int tx = lt % ntx, rt = lt / ntx, ty = rt % nty;
-    pl = rt / nty;
-    const int X0 = tx * kDnOW - kDnX0, Y0 = ty * kDnOH;
-    const int cx0 = X0 / 2 - 1, cy0 = Y0 / 2 - 1;
     const bool first = ch == nch - 1, last = ch == 0;
+    const int h = v.h, w = v.w;
+    if (first) {
+      const TileXY g = tile_of(lt, cdiv(w + kDnX0, kDnOW), cdiv(h, kDnOH));
+      pl = g.pl;
+      X0 = g.tx * kDnOW - kDnX0;
+      Y0 = g.ty * kDnOH;
+    }
+    const int cx0 = X0 / 2 - 1, cy0 = Y0 / 2 - 1;
     const bool has_next = !last || t + G < total;
     if (tid == 0 && has_next) {
       fence_proxy_async();
@@ -546,24 +546,20 @@ __device__ __forceinline__ bool stage_combine(Res res, int total, unsigned char*
         issue(vn, ln, cdiv(vn.K, kKC) - 1, true, buf ^ 1);
       }
     }
-    const int h = v.h, w = v.w;
     if (first) {
-      // Per-tile state: e^{-i w_1 g} from the guide value g, Horner sums, base value.
+      // Per-tile state: e^{-i w_1 I}, Horner sums, base value I.
       fy = Y0 + 2 * tr;
       fx = X0 + 4 * tc;
-      y0c = min(fy, h - 1);
-      y1c = min(fy + 1, h - 1);
-      const long long gpitch = LEVEL0 ? (long long)w : (long long)v.fine->pitch;
-      const float* gsrc = LEVEL0 ? v.I + (long long)pl * h * w : v.fine->G + (long long)pl * v.fine->gplane;
+      const int y0c = min(fy, h - 1), y1c = min(fy + 1, h - 1);
+      const float* gsrc = v.I + (long long)pl * h * w;
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
-        xq[q] = min(max(fx + q, 0), w - 1);
-        const float g0 = COH ? __ldcg(gsrc + y0c * gpitch + xq[q]) : __ldg(gsrc + y0c * gpitch + xq[q]);
-        const float g1 = COH ? __ldcg(gsrc + y1c * gpitch + xq[q]) : __ldg(gsrc + y1c * gpitch + xq[q]);
+        const int xq = min(max(fx + q, 0), w - 1);
+        const float g0 = __ldg(gsrc + (long long)y0c * w + xq), g1 = __ldg(gsrc + (long long)y1c * w + xq);
         we[q] = conj_turns(v.turns * g0);
         wo[q] = conj_turns(v.turns * g1);
         Pe[q] = Po[q] = splat(0.f);
-        base[q] = LEVEL0 ? make_float2(g0, g1) : splat(0.f);
+        base[q] = make_float2(g0, g1);
       }
     }
     if (!mbar_wait_cta(&bar[buf], pp.use[buf] & 1, v.fault)) {
@@ -587,76 +583,29 @@ __device__ __forceinline__ bool stage_combine(Res res, int total, unsigned char*
     // Orders k >= K of the highest chunk are staged as zeros (4-D map) and
     // come first in the descending Horner run, where they leave P at zero.
     const CT* zw = zb + tr * kDnCW + 2 * tc;
-    if constexpr (LEVEL0) {
 #pragma unroll
-      for (int kk = kKC - 1; kk >= 0; --kk) {
-        float2 ue[4], uo[4];
-        expand_2x4<S>(zw + kk * kDnCH * kDnCW, ue, uo);
+    for (int kk = kKC - 1; kk >= 0; --kk) {
+      float2 ue[4], uo[4];
+      expand_2x4<S>(zw + kk * kDnCH * kDnCW, ue, uo);
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          Pe[q] = horner(Pe[q], we[q], ue[q]);
-          Po[q] = horner(Po[q], wo[q], uo[q]);
-        }
-      }
-    } else {
-      // one order at a time: the fine-level loads of all orders would not fit in registers
-#pragma unroll 1
-      for (int kk = kKC - 1; kk >= 0; --kk) {
-        float2 ue[4], uo[4];
-        expand_2x4<S>(zw + kk * kDnCH * kDnCW, ue, uo);
-        const int k = ch * kKC + kk;
-        const bool kin = k < v.K;
-        const CT* Zk = reinterpret_cast<const CT*>(v.fine->Z) + (long long)pl * v.fine->zplane +
-                       (long long)(kin ? k : 0) * v.fine->zk;
-        const CT* r0 = Zk + (long long)y0c * v.fine->pitch;
-        const CT* r1 = Zk + (long long)y1c * v.fine->pitch;
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          CT zz0, zz1;
-          if constexpr (COH) {
-            if constexpr (sizeof(CT) == 8) {
-              const float2 f0 = __ldcg(reinterpret_cast<const float2*>(r0 + xq[q]));
-              const float2 f1 = __ldcg(reinterpret_cast<const float2*>(r1 + xq[q]));
-              zz0 = *reinterpret_cast<const CT*>(&f0);
-              zz1 = *reinterpret_cast<const CT*>(&f1);
-            } else {
-              const unsigned u0 = __ldcg(reinterpret_cast<const unsigned*>(r0 + xq[q]));
-              const unsigned u1 = __ldcg(reinterpret_cast<const unsigned*>(r1 + xq[q]));
-              zz0 = *reinterpret_cast<const CT*>(&u0);
-              zz1 = *reinterpret_cast<const CT*>(&u1);
-            }
-          } else {
-            zz0 = r0[xq[q]];
-            zz1 = r1[xq[q]];
-          }
-          const float2 sc = expand_scale_pair(q);
-          const float2 z0 = kin ? Cplx<S>::cvt(zz0) : splat(0.f), z1 = kin ? Cplx<S>::cvt(zz1) : splat(0.f);
-          Pe[q] = horner(Pe[q], we[q], fma2(splat(-sc.x), ue[q], z0));
-          Po[q] = horner(Po[q], wo[q], fma2(splat(-sc.y), uo[q], z1));
-        }
+      for (int q = 0; q < 4; ++q) {
+        Pe[q] = horner(Pe[q], we[q], ue[q]);
+        Po[q] = horner(Po[q], wo[q], uo[q]);
       }
     }
     if (last) {
-      float* dst;
-      long long dpitch;
-      if constexpr (LEVEL0) {
-        dst = v.O + (long long)pl * h * w;
-        dpitch = w;
-      } else {
-        dst = v.fine->E + (long long)pl * v.fine->gplane;
-        dpitch = v.fine->pitch;
-      }
+      float* dst = v.O + (long long)pl * h * w;
 #pragma unroll
       for (int rr = 0; rr < 2; ++rr) {
         const int y = fy + rr;
         if (y < h) {
-          float* d = dst + (long long)y * dpitch;
+          float* d = dst + (long long)y * w;
 #pragma unroll
           for (int q = 0; q < 4; ++q) {
             const int x = fx + q;
-            float delta = rr ? im_mul(Po[q], wo[q]) : im_mul(Pe[q], we[q]);
-            // level 0: the EXPAND weight and the sign of D_k are applied here
-            if constexpr (LEVEL0) delta *= -(rr ? expand_scale_pair(q).y : expand_scale_pair(q).x);
+            // the EXPAND weight and the sign of D_k are applied here
+            const float2 sc = expand_scale_pair(q);
+            const float delta = rr ? -sc.y * im_mul(Po[q], wo[q]) : -sc.x * im_mul(Pe[q], we[q]);
             if (x >= 0 && x < w) d[x] = (rr ? base[q].y : base[q].x) + delta;
           }
         }
@@ -670,6 +619,176 @@ __device__ __forceinline__ bool stage_combine(Res res, int total, unsigned char*
       if (t >= total) break;
       v = res(t, lt);
       nch = cdiv(v.K, kKC);
+      ch = nch - 1;
+    }
+  }
+  return true;
+}
+
+// ---------------------------------------------------------------------------------------
+// Combine at a level l >= 1 (Eq. (14) middle case, with the residual collapse):
+// E_l = sum_k Im(e^{-i k w_1 g} a_k (Z_{l,k} - up Z_{l+1,k})) + up E_{l+1}.
+// Item = (tile of 64 x 32 level-l pixels, chunk of kKC1 orders), chunks from
+// the highest order down.  Every operand is staged by TMA: the fine Z_l box
+// (68 x 32 from (X0 - 2, Y0)) and the coarse Z_{l+1} window of each chunk,
+// and with the first chunk the fine G_l box and the coarse E_{l+1} window, so
+// the loads of the next chunk overlap the current one.  Thread mapping, EXPAND
+// and Horner as in the level-0 combine; the EXPAND weight is applied per order
+// before the difference with Z_l.
+template <typename S, typename Res>
+__device__ __forceinline__ bool stage_combine1(Res res, int total, unsigned char* smem, uint64_t* bar,
+                                               Pipe& pp, int b, int G) {
+  using CT = typename Cplx<S>::T;
+  using SM = Smem<sizeof(CT)>;
+  constexpr size_t kOffC = SM::dn1_zf, kOffE = kOffC + SM::dn1_zc, kOffG = kOffE + SM::dn1_e;
+  auto bufp = [&](int buf) { return smem + buf * SM::dn1_buf; };
+  volatile int* abortp = abort_flag(bar);
+  const int tid = threadIdx.x;
+  if (b >= total) return true;
+  auto issue = [&](const DownArgs& a, int lt, int ch, bool first, int buf) {
+    const TileXY g = tile_of(lt, cdiv(a.fine.w + kDnX0, kDnOW), cdiv(a.fine.h, kDnOH));
+    const int X0 = g.tx * kDnOW - kDnX0, Y0 = g.ty * kDnOH;
+    const int cx0 = X0 / 2 - 1, cy0 = Y0 / 2 - 1;
+    const bool e = first && a.has_e;
+    uint32_t bytes = (uint32_t)(sizeof(CT) * kKC1 * (kDnOH * kD0IW + kDnCH * kDnCW));
+    if (first) bytes += (uint32_t)(sizeof(float) * kDnOH * kD0IW);
+    if (e) bytes += (uint32_t)(sizeof(float) * kDnCH * kDnCW);
+    mbar_expect_tx(&bar[buf], bytes);
+    unsigned char* p = bufp(buf);
+    // x = X0 - 2 = 64 tx - 8: 16-byte aligned for every element size
+    tma_load4(p, &a.zfmap, X0 - 2, Y0, ch * kKC1, g.pl, &bar[buf]);
+    tma_load4(p + kOffC, &a.zmap, cx0, cy0, ch * kKC1, g.pl, &bar[buf]);
+    if (first) tma_load3(p + kOffG, &a.gfmap, X0 - 2, Y0, g.pl, &bar[buf]);
+    if (e) tma_load3(p + kOffE, &a.emap, cx0, cy0, g.pl, &bar[buf]);
+  };
+  int t = b, lt = 0;
+  const DownArgs* a = res(t, lt);
+  int nch = cdiv(a->K, kKC1), ch = nch - 1;
+  if (tid == 0) {
+    fence_proxy_async();
+    issue(*a, lt, ch, true, 0);
+  }
+
+  const int tc = tid % (kDnOW / 4), tr = tid / (kDnOW / 4);
+  float2 we[4], wo[4], Pe[4], Po[4], base[4];
+  int fy = 0, fx = 0, pl = 0, X0 = 0, Y0 = 0;
+  for (int i = 0;; ++i) {
+    const int buf = i & 1;
+    const bool first = ch == nch - 1, last = ch == 0;
+    const int h = a->fine.h, w = a->fine.w;
+    if (first) {
+      const TileXY g = tile_of(lt, cdiv(w + kDnX0, kDnOW), cdiv(h, kDnOH));
+      pl = g.pl;
+      X0 = g.tx * kDnOW - kDnX0;
+      Y0 = g.ty * kDnOH;
+      fy = Y0 + 2 * tr;
+      fx = X0 + 4 * tc;
+    }
+    const int cx0 = X0 / 2 - 1, cy0 = Y0 / 2 - 1;
+    const bool has_next = !last || t + G < total;
+    if (tid == 0 && has_next) {
+      fence_proxy_async();
+      if (!last) {
+        issue(*a, lt, ch - 1, false, buf ^ 1);
+      } else {
+        int ln;
+        const DownArgs* an = res(t + G, ln);
+        issue(*an, ln, cdiv(an->K, kKC1) - 1, true, buf ^ 1);
+      }
+    }
+    mbar_wait_thread(&bar[buf], pp.use[buf] & 1, a->fault, abortp);
+    ++pp.use[buf];
+    const CT* zf = reinterpret_cast<const CT*>(bufp(buf));
+    CT* zc = reinterpret_cast<CT*>(bufp(buf) + kOffC);
+    float* eb = reinterpret_cast<float*>(bufp(buf) + kOffE);
+    const Level& coarse = a->coarse;
+    auto my = [&](int y) { return ext_coarse(y, coarse.h, h); };
+    auto mx = [&](int x) { return ext_coarse(x, coarse.w, w); };
+    fix_borders(zc, kKC1, kDnCH, kDnCW, cx0, cy0, coarse.w, coarse.h, my, mx);
+    if (first) {
+      // staged fine pixel (fy + rr, fx + q) at row 2 tr + rr, column 4 tc + 2 + q
+      // (zero outside the level; those pixels are not stored)
+      const float* gb = reinterpret_cast<const float*>(bufp(buf) + kOffG) + 2 * tr * kD0IW + 4 * tc + 2;
+      const float2 a0 = *reinterpret_cast<const float2*>(gb), a1 = *reinterpret_cast<const float2*>(gb + 2);
+      const float2 c0 = *reinterpret_cast<const float2*>(gb + kD0IW);
+      const float2 c1 = *reinterpret_cast<const float2*>(gb + kD0IW + 2);
+      const float ge[4] = {a0.x, a0.y, a1.x, a1.y}, go[4] = {c0.x, c0.y, c1.x, c1.y};
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        we[q] = conj_turns(a->turns * ge[q]);
+        wo[q] = conj_turns(a->turns * go[q]);
+        Pe[q] = Po[q] = splat(0.f);
+        base[q] = splat(0.f);
+      }
+      if (a->has_e) {
+        fix_borders(eb, 1, kDnCH, kDnCW, cx0, cy0, coarse.w, coarse.h, my, mx);
+        expand_e_2x4(eb + tr * kDnCW + 2 * tc, base);
+      }
+    }
+    // Orders k >= K of the highest chunk are staged as zeros (4-D maps) and
+    // come first in the descending Horner run, where they leave P at zero.
+    const CT* zw = zc + tr * kDnCW + 2 * tc;
+    const CT* zfw = zf + 2 * tr * kD0IW + 4 * tc + 2;
+#pragma unroll
+    for (int kk = kKC1 - 1; kk >= 0; --kk) {
+      float2 ue[4], uo[4];
+      expand_2x4<S>(zw + kk * kDnCH * kDnCW, ue, uo);
+      float2 fe[4], fo[4];
+#pragma unroll
+      for (int rr = 0; rr < 2; ++rr) {
+        const CT* r = zfw + kk * kDnOH * kD0IW + rr * kD0IW;
+        float2* f = rr ? fo : fe;
+        if constexpr (sizeof(CT) == 8) {
+          // (row * 68 + 4 tc + 2) complex of 8 bytes: 16-byte aligned
+          const float4 q0 = *reinterpret_cast<const float4*>(r);
+          const float4 q1 = *reinterpret_cast<const float4*>(r + 2);
+          f[0] = make_float2(q0.x, q0.y); f[1] = make_float2(q0.z, q0.w);
+          f[2] = make_float2(q1.x, q1.y); f[3] = make_float2(q1.z, q1.w);
+        } else {
+          // 8-byte aligned: two pairs of 4-byte complex samples
+          const uint2 q0 = *reinterpret_cast<const uint2*>(r);
+          const uint2 q1 = *reinterpret_cast<const uint2*>(r + 2);
+          f[0] = Cplx<S>::cvt(*reinterpret_cast<const CT*>(&q0.x));
+          f[1] = Cplx<S>::cvt(*reinterpret_cast<const CT*>(&q0.y));
+          f[2] = Cplx<S>::cvt(*reinterpret_cast<const CT*>(&q1.x));
+          f[3] = Cplx<S>::cvt(*reinterpret_cast<const CT*>(&q1.y));
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const float2 sc = expand_scale_pair(q);
+        Pe[q] = horner(Pe[q], we[q], fma2(splat(-sc.x), ue[q], fe[q]));
+        Po[q] = horner(Po[q], wo[q], fma2(splat(-sc.y), uo[q], fo[q]));
+      }
+    }
+    if (last) {
+      float* dst = a->fine.E + (long long)pl * a->fine.gplane;
+#pragma unroll
+      for (int rr = 0; rr < 2; ++rr) {
+        const int y = fy + rr;
+        if (y < h) {
+          float* d = dst + (long long)y * a->fine.pitch;
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const int x = fx + q;
+            const float delta = rr ? im_mul(Po[q], wo[q]) : im_mul(Pe[q], we[q]);
+            if (x >= 0 && x < w) d[x] = (rr ? base[q].y : base[q].x) + delta;
+          }
+        }
+      }
+    }
+    __syncthreads();
+    if (*abortp) {
+      if (tid == 0 && has_next) drain(&bar[buf ^ 1], pp.use[buf ^ 1] & 1);
+      return false;
+    }
+    if (!last) {
+      --ch;
+    } else {
+      t += G;
+      if (t >= total) break;
+      a = res(t, lt);
+      nch = cdiv(a->K, kKC1);
       ch = nch - 1;
     }
   }
@@ -707,8 +826,8 @@ __device__ __forceinline__ bool stage_down10(Res res, int total, unsigned char* 
   const int tid = threadIdx.x;
   if (b >= total) return true;
   auto issue = [&](const Down10Args& a, int lt, int ch, bool first, int buf) {
-    const int ntx = cdiv(a.w0 + kDnX0, kDnOW), nty = cdiv(a.h0, kDnOH);
-    const int tx = lt % ntx, r = lt / ntx, ty = r % nty, pl = r / nty;
+    const TileXY g = tile_of(lt, cdiv(a.w0 + kDnX0, kDnOW), cdiv(a.h0, kDnOH));
+    const int tx = g.tx, ty = g.ty, pl = g.pl;
     const int cx0 = (tx * kDnOW - kDnX0) / 2 - 1, cy0 = ty * (kDnOH / 2) - 1;
     const int c2x = cx0 / 2 - 2, c2y = (cy0 - 1) / 2;
     const bool e2 = first && a.has_e2, in = first && a.use_tma;
@@ -741,17 +860,19 @@ __device__ __forceinline__ bool stage_down10(Res res, int total, unsigned char* 
   float2 we[4], wo[4], Pe[4], Po[4], base[4];
   float2 w1[2][2], P1[2][2];
   float up_e2[2][2];
-  int fy = 0, fx = 0, pl = 0;
+  int fy = 0, fx = 0, pl = 0, X0 = 0, Y0 = 0;
   for (int i = 0;; ++i) {
     const int buf = i & 1;
     const int h0 = a->h0, w0 = a->w0;
-    const int ntx = cdiv(w0 + kDnX0, kDnOW), nty = cdiv(h0, kDnOH);
-    const int tx = lt % ntx, rt = lt / ntx, ty = rt % nty;
-    pl = rt / nty;
-    const int X0 = tx * kDnOW - kDnX0, Y0 = ty * kDnOH;
+    const bool first = ch == nch - 1, last = ch == 0;
+    if (first) {
+      const TileXY g = tile_of(lt, cdiv(w0 + kDnX0, kDnOW), cdiv(h0, kDnOH));
+      pl = g.pl;
+      X0 = g.tx * kDnOW - kDnX0;
+      Y0 = g.ty * kDnOH;
+    }
     const int cx0 = X0 / 2 - 1, cy0 = Y0 / 2 - 1;
     const int c2x = cx0 / 2 - 2, c2y = (cy0 - 1) / 2;
-    const bool first = ch == nch - 1, last = ch == 0;
     const bool has_next = !last || t + G < total;
     if (tid == 0 && has_next) {
       fence_proxy_async();
@@ -969,12 +1090,11 @@ template <typename S>
 __global__ void __launch_bounds__(kThreads, 2) k_down(const __grid_constant__ DownArgs a) {
   using SM = Smem<sizeof(typename Cplx<S>::T)>;
   extern __shared__ __align__(128) unsigned char smem[];
-  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + SM::dn - 64);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + SM::dn1 - 64);
   init_bars(bar);
   Pipe pp{};
-  const CombineView v = view_of(a);
-  stage_combine<S, false, false>([&](int g, int& l) { l = g; return v; }, combine_tiles(v), smem, bar,
-                                 pp, blockIdx.x, gridDim.x);
+  stage_combine1<S>([&](int g, int& l) { l = g; return &a; }, combine_tiles(a.fine.h, a.fine.w, a.planes),
+                    smem, bar, pp, blockIdx.x, gridDim.x);
 }
 
 template <typename S>
@@ -985,8 +1105,8 @@ __global__ void __launch_bounds__(kThreads, 3) k_down0(const __grid_constant__ D
   init_bars(bar);
   Pipe pp{};
   const CombineView v = view_of(a);
-  stage_combine<S, true, false>([&](int g, int& l) { l = g; return v; }, combine_tiles(v), smem, bar,
-                                pp, blockIdx.x, gridDim.x);
+  stage_combine0<S>([&](int g, int& l) { l = g; return v; }, combine_tiles(v), smem, bar, pp, blockIdx.x,
+                    gridDim.x);
 }
 
 template <typename S>
@@ -1050,18 +1170,20 @@ template <typename S>
 __global__ void __launch_bounds__(kThreads, 2) k_down_batch(const BatchTable<DownArgs> tb) {
   using SM = Smem<sizeof(typename Cplx<S>::T)>;
   extern __shared__ __align__(128) unsigned char smem[];
-  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + SM::dn - 64);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + SM::dn1 - 64);
   fence_maps(tb, [](const DownArgs& a) {
     fence_tensormap(&a.zmap);
     fence_tensormap(&a.emap);
+    fence_tensormap(&a.zfmap);
+    fence_tensormap(&a.gfmap);
   });
   init_bars(bar);
   Pipe pp{};
-  stage_combine<S, false, false>(
+  stage_combine1<S>(
       [&](int g, int& l) {
         const int j = find_entry(tb.prefix, tb.n, g);
         l = g - __ldg(tb.prefix + j);
-        return view_of(tb.args[j]);
+        return tb.args + j;
       },
       tb.total, smem, bar, pp, blockIdx.x, gridDim.x);
 }
@@ -1077,7 +1199,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_down0_batch(const BatchTable<Do
   });
   init_bars(bar);
   Pipe pp{};
-  stage_combine<S, true, false>(
+  stage_combine0<S>(
       [&](int g, int& l) {
         const int j = find_entry(tb.prefix, tb.n, g);
         l = g - __ldg(tb.prefix + j);
@@ -1128,7 +1250,7 @@ __device__ __forceinline__ bool grid_barrier(unsigned* count, unsigned* gen, uns
 template <typename S>
 __global__ void __launch_bounds__(kThreads, 2) k_chain(const __grid_constant__ ChainArgs a) {
   using SM = Smem<sizeof(typename Cplx<S>::T)>;
-  constexpr size_t kS = SM::up > SM::dn ? SM::up : SM::dn;
+  constexpr size_t kS = SM::up > SM::dn1 ? SM::up : SM::dn1;
   extern __shared__ __align__(128) unsigned char smem[];
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem + kS - 64);
   init_bars(bar);
@@ -1141,9 +1263,9 @@ __global__ void __launch_bounds__(kThreads, 2) k_chain(const __grid_constant__ C
     if (!grid_barrier(a.sync, a.sync + 1, G, a.fault)) return;
   }
   for (int st = 0; st < a.n_dn; ++st) {
-    const CombineView v = view_of(a.dn[st]);
-    if (!stage_combine<S, false, true>([&](int g, int& l) { l = g; return v; }, combine_tiles(v),
-                                       smem, bar, pp, b, G))
+    const DownArgs* d = &a.dn[st];
+    if (!stage_combine1<S>([&](int g, int& l) { l = g; return d; },
+                           combine_tiles(d->fine.h, d->fine.w, d->planes), smem, bar, pp, b, G))
       return;
     if (st + 1 < a.n_dn && !grid_barrier(a.sync, a.sync + 1, G, a.fault)) return;
   }
@@ -1186,8 +1308,8 @@ cudaError_t FLLF_LAUNCH_NAME(up)(const UpArgs& a, cudaStream_t s) {
 
 cudaError_t FLLF_LAUNCH_NAME(down)(const DownArgs& a, cudaStream_t s) {
   const int tiles = cdiv(a.fine.w + kDnX0, kDnOW) * cdiv(a.fine.h, kDnOH) * a.planes;
-  const int grid = persistent_grid(k_down<FLLF_STORAGE>, SMS::dn, tiles);
-  k_down<FLLF_STORAGE><<<grid, kThreads, SMS::dn, s>>>(a);
+  const int grid = persistent_grid(k_down<FLLF_STORAGE>, SMS::dn1, tiles);
+  k_down<FLLF_STORAGE><<<grid, kThreads, SMS::dn1, s>>>(a);
   return cudaGetLastError();
 }
 
@@ -1206,7 +1328,7 @@ cudaError_t FLLF_LAUNCH_NAME(down10)(const Down10Args& a, cudaStream_t s) {
 }
 
 cudaError_t FLLF_LAUNCH_NAME(chain)(const ChainArgs& a, cudaStream_t s) {
-  constexpr size_t kChainSmem = SMS::up > SMS::dn ? SMS::up : SMS::dn;
+  constexpr size_t kChainSmem = SMS::up > SMS::dn1 ? SMS::up : SMS::dn1;
   static int grid = 0;
   if (grid == 0) {
     int dev = 0, sms = 0, per = 0;
@@ -1238,8 +1360,8 @@ cudaError_t FLLF_LAUNCH_NAME(up_batch)(const BatchTable<UpArgs>& tb, cudaStream_
 }
 cudaError_t FLLF_LAUNCH_NAME(down_batch)(const BatchTable<DownArgs>& tb, cudaStream_t s) {
   if (tb.total <= 0) return cudaSuccess;
-  const int grid = persistent_grid(k_down_batch<FLLF_STORAGE>, SMS::dn, tb.total);
-  k_down_batch<FLLF_STORAGE><<<grid, kThreads, SMS::dn, s>>>(tb);
+  const int grid = persistent_grid(k_down_batch<FLLF_STORAGE>, SMS::dn1, tb.total);
+  k_down_batch<FLLF_STORAGE><<<grid, kThreads, SMS::dn1, s>>>(tb);
   return cudaGetLastError();
 }
 cudaError_t FLLF_LAUNCH_NAME(down0_batch)(const BatchTable<Down0Args>& tb, cudaStream_t s) {

@@ -113,6 +113,9 @@ bool build_maps(const fllf_params& p, const std::vector<Level>& lv, PathMaps* m)
   m->e_dn.assign(L, CUtensorMap{});
   m->z_up.assign(L, CUtensorMap{});
   m->g_up.assign(L, CUtensorMap{});
+  m->z_dn1.assign(L, CUtensorMap{});
+  m->z_fn.assign(L, CUtensorMap{});
+  m->g_fn.assign(L, CUtensorMap{});
   const bool f32 = p.precision == FLLF_FP32;
   const size_t zs = f32 ? 8 : 4;
   const CUtensorMapDataType zdt = f32 ? CU_TENSOR_MAP_DATA_TYPE_INT64 : CU_TENSOR_MAP_DATA_TYPE_UINT32;
@@ -126,6 +129,18 @@ bool build_maps(const fllf_params& p, const std::vector<Level>& lv, PathMaps* m)
     if (!encode4(&m->z_dn[l], zdt, v.Z, v.w, v.h, p.K, p.C, zrow, zs * (uint64_t)v.zk,
                  zs * (uint64_t)v.zplane, kDnCW, kDnCH, kKC))
       return false;
+    // level >= 1 combines: Z_l as the coarse window (l >= 2), Z_l and G_l as the fine boxes (l <= L-2)
+    if (l >= 2 && !encode4(&m->z_dn1[l], zdt, v.Z, v.w, v.h, p.K, p.C, zrow, zs * (uint64_t)v.zk,
+                           zs * (uint64_t)v.zplane, kDnCW, kDnCH, kKC1))
+      return false;
+    if (l <= L - 2) {
+      if (!encode4(&m->z_fn[l], zdt, v.Z, v.w, v.h, p.K, p.C, zrow, zs * (uint64_t)v.zk,
+                   zs * (uint64_t)v.zplane, kD0IW, kDnOH, kKC1))
+        return false;
+      if (!encode3(&m->g_fn[l], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, v.G, v.w, v.h, p.C, grow, gplane,
+                   kD0IW, kDnOH, 1))
+        return false;
+    }
     // as the source of a REDUCE: 68 x 35 box, up_kc orders; plus the guide
     if (l <= L - 2) {
       if (!encode3(&m->z_up[l], zdt, zs, v.Z, v.w, v.h, zplanes, zrow, zplane, kRsBW, kRsIR, up_kc))
@@ -220,11 +235,12 @@ cudaError_t enqueue_path(const fllf_params& p, const std::vector<Level>& lv, con
   };
   auto down_args = [&](int l) {
     DownArgs d{};
-    d.zmap = maps.z_dn[l + 1];
+    d.zmap = maps.z_dn1[l + 1];
     d.emap = maps.e_dn[l + 1];
+    d.zfmap = maps.z_fn[l];
+    d.gfmap = maps.g_fn[l];
     d.fine = lv[l];
     d.coarse = lv[l + 1];
-    d.a = d_a;
     d.planes = C;
     d.K = p.K;
     d.turns = turns;
@@ -291,7 +307,6 @@ cudaError_t enqueue_path(const fllf_params& p, const std::vector<Level>& lv, con
   d0.w0 = p.W;
   d0.planes = C;
   d0.coarse = lv[1];
-  d0.a = d_a;
   d0.K = p.K;
   d0.turns = turns;
   d0.has_e = (L >= 3) ? 1 : 0;
