@@ -63,38 +63,97 @@ def level_sizes(H, W, L):
     return out
 
 
+CHAIN_PIXELS = 1 << 21   # levels whose pixels over all planes fit this run in the chained launch
+
+
+def stage_split(cfg):
+    """Which levels each stage kind covers, as the library launches them.
+
+    Returns (up_levels, chain_up, chain_down, down_levels, fused): REDUCE
+    l -> l+1 for l in up_levels / chain_up, level-l combines for l in
+    chain_down / down_levels, and whether the level-0 stage also runs the
+    level-1 combine (levels >= 3)."""
+    L, C = cfg["levels"], cfg["C"]
+    sz = level_sizes(cfg["H"], cfg["W"], L)
+    c0 = L - 1
+    for l in range(2, L - 1):
+        if sz[l][0] * sz[l][1] * C <= CHAIN_PIXELS:
+            c0 = l
+            break
+    c0 = max(c0, L - 1 - 12)
+    up_levels = [l for l in range(1, L - 1) if l < c0]
+    chain_up = list(range(c0, L - 1)) if c0 <= L - 2 else []
+    chain_down = list(range(L - 2, c0 - 1, -1)) if c0 <= L - 2 else []
+    fused = L >= 3
+    hi = c0 - 1 if c0 <= L - 2 else L - 2
+    down_levels = list(range(hi, (2 if fused else 1) - 1, -1))
+    return up_levels, chain_up, chain_down, down_levels, fused
+
+
 def stage_work(cfg, zbytes):
     """Algorithmic FP32 ops and bytes per stage kind for one frame (all planes).
 
-    Ops (FMA = 1; the method's separable stencil count):
-      trig per evaluated pixel      16 (sincospi) + 2 (K - 1) (Chebyshev, cos and sin)
+    Ops (FMA = 1; the method's separable stencil count with Horner's rule
+    over the orders):
+      trig per evaluated pixel      16 (sincospi and its fix-up); the REDUCE of
+                                    level 0 adds 2 (K - 1) for the recurrence
+                                    over the orders
       REDUCE per output per image   13 (2 horizontal x 4 + vertical 4 + scale)
-      EXPAND-combine per fine pixel
-        per complex order           9 at level 0 (6 expand + 3 product-accumulate),
-                                    11 at level >= 1 (+2 for Z_l - up(Z_{l+1}))
-        residual expand + add       4
-    Bytes: each input element read once and each output written once.
+      combine per pixel and order   10 at level 0 (6 EXPAND + 4 complex
+                                    multiply-add), 12 at level >= 1 (+2 for
+                                    Z_l - up(Z_{l+1}))
+      residual EXPAND + add         4 per pixel
+    Bytes: each input element read once and each output written once; the
+    level-1 combine inside the level-0 stage reads G_1, Z_1 (shared with the
+    level-0 EXPAND), Z_2 and E_2, and writes nothing.
     """
     L, K, C = cfg["levels"], cfg["K"], cfg["C"]
     sz = level_sizes(cfg["H"], cfg["W"], L)
     n = [h * w for h, w in sz]
-    trig = 16 + 2 * (K - 1)
+    trig = 16
+    up_levels, chain_up, chain_down, down_levels, fused = stage_split(cfg)
     ops = dict.fromkeys(STAGES, 0.0)
     byt = dict.fromkeys(STAGES, 0.0)
-    ops["up0"] = n[0] * trig + n[1] * 13 * (2 * K + 1)
-    byt["up0"] = 4 * n[0] + 4 * n[1] + zbytes * K * n[1]
-    for l in range(1, L - 1):
+
+    def reduce_work(l):
         g = 1 if l + 1 <= L - 2 else 0
-        ops["up"] += n[l + 1] * 13 * (2 * K + g)
-        byt["up"] += (4 * n[l] * g + zbytes * K * n[l]) + (4 * n[l + 1] * g + zbytes * K * n[l + 1])
-    for l in range(1, L - 1):
+        return (n[l + 1] * 13 * (2 * K + g),
+                (4 * n[l] * g + zbytes * K * n[l]) + (4 * n[l + 1] * g + zbytes * K * n[l + 1]))
+
+    def combine_work(l):
         e = 1 if l + 1 <= L - 2 else 0
-        ops["down"] += n[l] * (trig + 11 * K + 4 * e)
-        byt["down"] += (4 * n[l] + zbytes * K * n[l] + zbytes * K * n[l + 1] + 4 * n[l + 1] * e
-                        + 4 * n[l])
-    e1 = 1 if L >= 3 else 0
-    ops["down0"] = n[0] * (trig + 9 * K + 4 * e1)
-    byt["down0"] = 4 * n[0] + zbytes * K * n[1] + 4 * n[1] * e1 + 4 * n[0]
+        return (n[l] * (trig + 12 * K + 4 * e),
+                4 * n[l] + zbytes * K * n[l] + zbytes * K * n[l + 1] + 4 * n[l + 1] * e + 4 * n[l])
+
+    if L >= 2:
+        ops["up0"] = n[0] * (trig + 2 * (K - 1)) + n[1] * 13 * (2 * K + 1)
+        byt["up0"] = 4 * n[0] + 4 * n[1] + zbytes * K * n[1]
+    for l in up_levels:
+        o, b = reduce_work(l)
+        ops["up"] += o
+        byt["up"] += b
+    for l in chain_up:
+        o, b = reduce_work(l)
+        ops["chain"] += o
+        byt["chain"] += b
+    for l in chain_down:
+        o, b = combine_work(l)
+        ops["chain"] += o
+        byt["chain"] += b
+    for l in down_levels:
+        o, b = combine_work(l)
+        ops["down"] += o
+        byt["down"] += b
+    if L >= 2:
+        e1 = 1 if L >= 3 else 0
+        ops["down0"] = n[0] * (trig + 10 * K + 4 * e1)
+        byt["down0"] = 4 * n[0] + zbytes * K * n[1] + 4 * n[0]
+        if fused:
+            e2 = 1 if L >= 4 else 0
+            ops["down0"] += n[1] * (trig + 12 * K + 4 * e2)
+            byt["down0"] += 4 * n[1] + zbytes * K * n[2] + 4 * n[2] * e2
+        else:
+            byt["down0"] += 4 * n[1] * e1
     return {k: v * C for k, v in ops.items()}, {k: v * C for k, v in byt.items()}
 
 

@@ -186,7 +186,7 @@ constexpr int kRsTW = 30, kRsTH = 16;
 constexpr int kRsIR = 2 * kRsTH + 3;      // fine rows read (35)
 constexpr int kRsBW = 68;                 // staged fine columns (box from 2*X1-4)
 constexpr int kRsVW = 64;                 // vertical-pass columns (63 used)
-constexpr int kUpSlots = 4;               // TMA ring slots of the REDUCE stage (3 loads in flight)
+constexpr int kUpSlots = 2;               // TMA ring slots of the REDUCE stage (1 load in flight)
 
 // combine: 64 x 32 fine outputs per tile; fine tile origin 64*tx-6 so that the
 // coarse window origin 32*tx-4 is 16-byte aligned for both element sizes.
