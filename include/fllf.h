@@ -93,6 +93,16 @@ fllf_status fllf_params_validate(const fllf_params *p);
  * coeff_mode).  a_out: host array of p->K doubles, written on FLLF_OK. */
 fllf_status fllf_coeffs(const fllf_params *p, double *a_out);
 
+/* Fourier period of Eq. (12): the T minimising
+ *     E_K(T) = erfc(pi sigma_r (2K + 1) / T) + erfc((T - R) / sigma_r)
+ * for an R-tone image (R = 1 for images in [0, 1], 256 for 8-bit ones),
+ * the bound on the cosine-series error of the Gaussian w_r used by
+ * Eqs. (9)-(10).  Host only (no device work).  sigma_r > 0, R > 0, finite,
+ * 1 <= K <= 64, T_out non-NULL; otherwise FLLF_EINVAL.  *T_out is written
+ * on FLLF_OK.  Example: sigma_r = 30, K = 10, R = 256 gives 405.5 (the
+ * paper prints 405.9 for its experiments). */
+fllf_status fllf_optimal_period(double sigma_r, int K, double R, double *T_out);
+
 /* Bytes of device scratch a plan for this parameter set allocates: the
  * guide pyramid G_l (l >= 1), the Fourier pyramids Z_l (K complex planes
  * per level l >= 1, in the storage precision) and the residual pyramid

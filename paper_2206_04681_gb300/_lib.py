@@ -76,6 +76,8 @@ _SIGS = {
     "fllf_plan_enable_timing": (ctypes.c_int, [_P, ctypes.c_int]),
     "fllf_plan_stage_times": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_double),
                                              ctypes.POINTER(ctypes.c_int)]),
+    "fllf_optimal_period": (ctypes.c_int, [ctypes.c_double, ctypes.c_int, ctypes.c_double,
+                                           ctypes.POINTER(ctypes.c_double)]),
 }
 
 STAGES = ("up0", "up", "down", "down0", "chain")
@@ -130,6 +132,13 @@ def fllf_coeffs(p):
     out = (ctypes.c_double * p.K)()
     _check(lib().fllf_coeffs(ctypes.byref(p), out))
     return list(out)
+
+
+def fllf_optimal_period(sigma_r, K, R):
+    """Eq. (12) period for an R-tone image (host only)."""
+    out = ctypes.c_double()
+    _check(lib().fllf_optimal_period(float(sigma_r), int(K), float(R), ctypes.byref(out)))
+    return out.value
 
 
 def fllf_plan_scratch_bytes(p):

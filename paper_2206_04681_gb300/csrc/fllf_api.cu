@@ -228,6 +228,52 @@ static fllf_status check_fault(fllf_plan* plan) {
   return FLLF_OK;
 }
 
+namespace {
+
+// Period of Eq. (12): T minimising E(T) = erfc(a / T) + erfc((T - R) / sigma)
+// with a = pi sigma (2K + 1).  For R < T < a the first term's slope,
+// (2/sqrt(pi)) (a / T^2) exp(-a^2 / T^2), rises with T and the second's
+// magnitude, (2/sqrt(pi)) exp(-(T - R)^2 / sigma^2) / sigma, falls, so the
+// minimum is the single root of
+//   h(T) = log(a / T^2) - a^2 / T^2 + log(sigma) + (T - R)^2 / sigma^2,
+// found by bisection in float64 (log space keeps both slopes from
+// underflowing).  Without a sign change in (R, min(a, R + 40 sigma)) the
+// minimum of E is searched directly by golden sections instead.
+double optimal_period(double sigma, int K, double R) {
+  const double a = M_PI * sigma * (2.0 * K + 1.0);
+  auto E = [&](double T) { return std::erfc(a / T) + std::erfc((T - R) / sigma); };
+  auto h = [&](double T) {
+    const double u = a / T, v = (T - R) / sigma;
+    return std::log(a / (T * T)) - u * u + std::log(sigma) + v * v;
+  };
+  double lo = R * (1.0 + 1e-12) + 1e-300, hi = std::min(a, R + 40.0 * sigma);
+  if (hi > lo && h(lo) < 0.0 && h(hi) > 0.0) {
+    for (int it = 0; it < 200 && hi - lo > 1e-14 * hi; ++it) {
+      const double mid = 0.5 * (lo + hi);
+      (h(mid) < 0.0 ? lo : hi) = mid;
+    }
+    return 0.5 * (lo + hi);
+  }
+  lo = R;
+  hi = R + 40.0 * sigma + a;
+  const double g = 0.5 * (std::sqrt(5.0) - 1.0);
+  double c = hi - g * (hi - lo), d = lo + g * (hi - lo);
+  for (int it = 0; it < 400 && hi - lo > 1e-13 * hi; ++it) {
+    if (E(c) < E(d)) {
+      hi = d;
+      d = c;
+      c = hi - g * (hi - lo);
+    } else {
+      lo = c;
+      c = d;
+      d = lo + g * (hi - lo);
+    }
+  }
+  return 0.5 * (lo + hi);
+}
+
+}  // namespace
+
 extern "C" {
 
 const char* fllf_status_str(fllf_status s) {
@@ -252,6 +298,14 @@ fllf_status fllf_coeffs(const fllf_params* p, double* a_out) {
   if (st != FLLF_OK) return st;
   if (!a_out) return fail(FLLF_EINVAL, "a_out is NULL");
   compute_coeffs(*p, a_out);
+  return FLLF_OK;
+}
+
+fllf_status fllf_optimal_period(double sigma_r, int K, double R, double* T_out) {
+  if (!T_out) return fail(FLLF_EINVAL, "T_out is NULL");
+  if (!(sigma_r > 0.0) || !std::isfinite(sigma_r) || !(R > 0.0) || !std::isfinite(R) || K < 1 || K > 64)
+    return fail(FLLF_EINVAL, "fllf_optimal_period needs sigma_r > 0, R > 0 (finite) and 1 <= K <= 64");
+  *T_out = optimal_period(sigma_r, K, R);
   return FLLF_OK;
 }
 

@@ -97,3 +97,36 @@ def test_null_arguments_rejected(lib):
     assert lib.fllf_plan_destroy(None) == pkg.FLLF_OK
     assert lib.fllf_run(None, None, None, None) == pkg.FLLF_EINVAL
     assert lib.fllf_poll(ctypes.c_uint64(123456789), 0) == pkg.FLLF_EINVAL
+
+
+def _golden_periods():
+    path = os.path.join(ROOT, "tests", "golden", "period_sigma30.txt")
+    rows = [l.split() for l in open(path) if l.strip() and not l.startswith("#")]
+    return [(float(s), int(k), float(r), float(t)) for s, k, r, t in rows]
+
+
+@pytest.mark.parametrize("sigma,K,R,T_paper", _golden_periods())
+def test_optimal_period_matches_paper(lib, sigma, K, R, T_paper):
+    # Eq. (12) at the paper's experimental setting; it prints T = 405.9
+    T = pkg.fllf_optimal_period(sigma, K, R)
+    assert abs(T - T_paper) / T_paper < 2e-3
+
+
+@pytest.mark.parametrize("sigma,K,R", [(30.0, 10, 256.0), (0.2, 8, 1.0), (0.1, 4, 1.0),
+                                       (0.4, 16, 1.0), (15.0, 10, 256.0), (0.05, 64, 1.0)])
+def test_optimal_period_matches_oracle(lib, sigma, K, R):
+    T = pkg.fllf_optimal_period(sigma, K, R)
+    T_ref = o.optimal_period(sigma, K, R)
+    assert abs(T - T_ref) <= 1e-6 * T_ref
+    # it is a minimum of E_K(T): both neighbours are no lower
+    e = o.period_error(T, sigma, K, R)
+    for d in (1e-3, -1e-3):
+        assert o.period_error(T * (1 + d), sigma, K, R) >= e - 1e-15
+
+
+def test_optimal_period_rejects_bad_arguments(lib):
+    for args in ((0.0, 8, 1.0), (-1.0, 8, 1.0), (0.2, 0, 1.0), (0.2, 65, 1.0), (0.2, 8, 0.0),
+                 (float("nan"), 8, 1.0), (0.2, 8, float("inf"))):
+        with pytest.raises(pkg.FllfError) as e:
+            pkg.fllf_optimal_period(*args)
+        assert e.value.status == pkg.FLLF_EINVAL
