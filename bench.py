@@ -42,9 +42,10 @@ def parse():
     ap.add_argument("--precision", choices=["fp32", "fp16", "bf16"], default="fp32")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
-    ap.add_argument("--workload", choices=["uhd", "batch", "serve"], default="uhd",
+    ap.add_argument("--workload", choices=["uhd", "batch", "serve", "sweep"], default="uhd",
                     help="uhd: the 4K RGB headline (plus a short served stream); batch: 64 mixed "
-                         "images, batched vs looped; serve: Poisson request streams")
+                         "images, batched vs looped; serve: Poisson request streams; sweep: "
+                         "storage precision error over K x sigma_r x m against the float64 oracle")
     ap.add_argument("--serve-seconds", type=float, default=None,
                     help="length of each served stream (default 30 s; 4 s in the uhd line)")
     ap.add_argument("--serve-rates", type=str, default=None,
@@ -720,6 +721,106 @@ def run_serve(args):
     return 0
 
 
+SWEEP = dict(K=(4, 8, 16), sigma_r=(0.1, 0.2, 0.4), m=(0.5, 3.0), levels=8, T=2.0,
+             crop=(824, 1664, 512))   # centred 512 x 512 crop: rows 824.., cols 1664..
+
+
+def _sweep_oracle_job(job):
+    """Float64 oracle output for one (plane or crop, parameter set) job."""
+    import numpy as np
+    import oracle
+    kind, x, levels, K, m, sigma_r, T = job
+    x = x.astype(np.float64)
+    if kind == "fourier":
+        a = oracle.coeffs_quadrature(m, sigma_r, T, K)
+        return oracle.fourier_llf(x, levels, a, T)
+    # naive LLF with the exact remap detail (Sec. II-C), windowed
+    return oracle.naive_llf(x, levels, lambda d: oracle.remap_detail(d, m, sigma_r))
+
+
+def run_sweep(args):
+    """Error of the three Fourier-pyramid storage precisions against the
+    float64 oracle on the 3840 x 2160 x 3 frame for every (K, sigma_r, m) of
+    the sweep, and against naive LLF (exact remap) on a centred 512 x 512
+    crop of channel 0.  One JSON line with max-abs and PSNR per case."""
+    import numpy as np
+    pool = oracle_pool()                      # spawned before any GPU work
+    import torch
+    import paper_2206_04681_gb300 as pkg
+    from paper_2206_04681_gb300 import build
+    from paper_2206_04681_gb300.synth import synth_image
+    build.build_library()
+    torch.cuda.set_device(0)
+    cfg = WORKLOAD
+    img = synth_image(cfg["H"], cfg["W"], cfg["C"], cfg["polygons"], cfg["seed"])
+    y0, x0, n = SWEEP["crop"]
+    crop = np.ascontiguousarray(img[:1, y0:y0 + n, x0:x0 + n])
+    L, T = SWEEP["levels"], SWEEP["T"]
+    combos = [(K, s, m) for K in SWEEP["K"] for s in SWEEP["sigma_r"] for m in SWEEP["m"]]
+    jobs = []
+    for K, sg, m in combos:
+        jobs += [("fourier", img[c], L, K, m, sg, T) for c in range(cfg["C"])]
+        jobs.append(("naive", crop[0], L, K, m, sg, T))
+    t0 = time.perf_counter()
+    results = pool.imap(_sweep_oracle_job, jobs)
+    x_full = torch.from_numpy(img).cuda()
+    x_crop = torch.from_numpy(crop).cuda()
+
+    def gpu(x, K, sg, m, prec):
+        p = pkg.make_params(x.shape[1], x.shape[2], x.shape[0], L, K, m, sg, T, prec)
+        plan = pkg.fllf_plan_create(p, 0)
+        try:
+            y = torch.empty_like(x)
+            pkg.run_tensor(plan, x, y)
+            torch.cuda.synchronize()
+            return y.cpu().numpy().astype(np.float64)
+        finally:
+            pkg.fllf_plan_destroy(plan)
+
+    def stats(err):
+        mse = float(np.mean(err ** 2))
+        return {"max_abs": float(np.max(np.abs(err))),
+                "psnr_db": float("inf") if mse == 0 else 10 * np.log10(1.0 / mse)}
+
+    rows = []
+    precs = ("fp32", "fp16", "bf16")
+    for K, sg, m in combos:
+        outs = {pr: gpu(x_full, K, sg, m, pr) for pr in precs}
+        crops = {pr: gpu(x_crop, K, sg, m, pr) for pr in precs}
+        sse = dict.fromkeys(precs, 0.0)
+        mx = dict.fromkeys(precs, 0.0)
+        for c in range(cfg["C"]):
+            ref = next(results)
+            for pr in precs:
+                e = outs[pr][c] - ref
+                sse[pr] += float(np.sum(e * e))
+                mx[pr] = max(mx[pr], float(np.max(np.abs(e))))
+        naive = next(results)
+        row = {"K": K, "sigma_r": sg, "m": m}
+        for pr in precs:
+            mse = sse[pr] / img.size
+            row[pr] = {"max_abs": mx[pr], "psnr_db": float("inf") if mse == 0 else 10 * np.log10(1.0 / mse)}
+        row["crop_vs_naive_psnr_db"] = {pr: stats(crops[pr][0] - naive)["psnr_db"] for pr in precs}
+        rows.append(row)
+    pool.close()
+    worst = {pr: min(r[pr]["psnr_db"] for r in rows) for pr in precs}
+    line = {"metric": "max-abs and PSNR vs the float64 oracle, Fourier-pyramid storage sweep",
+            "value": worst["fp16"], "unit": "dB (lowest fp16 PSNR over the sweep)", "n_gpus": 1,
+            "steps": len(combos), "warmup": 0, "ms_per_step": None, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "uhd_rgb_3840x2160x3_L8_sweep", "levels": L, "T": T,
+                       "K": list(SWEEP["K"]), "sigma_r": list(SWEEP["sigma_r"]), "m": list(SWEEP["m"]),
+                       "crop": f"channel 0, rows {y0}..{y0 + n - 1}, cols {x0}..{x0 + n - 1}, levels {L}",
+                       "oracle": "float64 Fourier LLF (Eq. (14)) on the whole frame; naive LLF with "
+                                 "the exact remap on the crop"},
+            "worst_psnr_db": worst,
+            "worst_max_abs": {pr: max(r[pr]["max_abs"] for r in rows) for pr in precs},
+            "oracle_seconds": time.perf_counter() - t0,
+            "sweep": rows}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -728,6 +829,8 @@ def main():
         return run_batch(args)
     if args.workload == "serve":
         return run_serve(args)
+    if args.workload == "sweep":
+        return run_sweep(args)
     return run_ours(args)
 
 
