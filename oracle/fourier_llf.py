@@ -61,3 +61,34 @@ def fourier_llf(img, levels, a, T):
         return np.stack([fourier_llf(ch, levels, a, T) for ch in img])
     lap_o, _ = fourier_llf_levels(img, levels, a, T)
     return collapse(lap_o)
+
+
+def fourier_llf_adaptive(img, levels, c, T, gain):
+    """Pixel-by-pixel enhancement with Fourier LLF (Sec. III-B), float64.
+
+    The pyramids do not depend on the remap, so only the coefficients change
+    per pixel: with the gain m replaced by m_p, every level below the top is
+
+        L_l[O]_p = L_l[I]_p + (m_{l,p} - 1) sum_k c_k [ cos(omega_k g) L_l[sin(omega_k I)]_p
+                                                     - sin(omega_k g) L_l[cos(omega_k I)]_p ],
+
+    where c_k are the coefficients of the unit detail d exp(-d^2/(2 sigma_r^2))
+    (the a_k of m - 1 = 1) and m_{l,p} = G_l[gain]_p (reading: the Gaussian
+    pyramid of the level-0 gain map).  ``img``: (H, W) or (C, H, W); ``gain``:
+    (H, W), shared by the channels.
+    """
+    img = np.asarray(img, dtype=np.float64)
+    if img.ndim == 3:
+        return np.stack([fourier_llf_adaptive(ch, levels, c, T, gain) for ch in img])
+    gm = gaussian_pyramid(np.asarray(gain, dtype=np.float64), levels)
+    g = gaussian_pyramid(img, levels)
+    lap_i = laplacian_from_gaussian(g)
+    out = [lap_i[l].copy() for l in range(levels - 1)]
+    for ck, om in zip(c, omegas(T, len(c))):
+        lap_c = laplacian_from_gaussian(gaussian_pyramid(np.cos(om * img), levels))
+        lap_s = laplacian_from_gaussian(gaussian_pyramid(np.sin(om * img), levels))
+        for l in range(levels - 1):
+            cg, sg = np.cos(om * g[l]), np.sin(om * g[l])
+            out[l] += (gm[l] - 1.0) * ck * (cg * lap_s[l] - sg * lap_c[l])
+    out.append(g[-1])
+    return collapse(out)

@@ -29,9 +29,13 @@ from .pyramid import gaussian_pyramid, reduce, expand, collapse, coarse_size
 _MAX_BATCH_ELEMS = 1 << 22
 
 
-def _laplacian_at(windows, g, f, level, ly, lx):
-    """Coefficient L_level[w + f(w - g)] at local level positions (ly, lx), batched."""
-    r = windows + f(windows - g[:, None, None])
+def _laplacian_at(windows, g, f, level, ly, lx, s=None):
+    """Coefficient L_level[w + s f(w - g)] at local level positions (ly, lx), batched.
+
+    ``s`` (one value per coefficient, default 1) scales the remap detail: the
+    pixel-by-pixel parameter of Sec. III-B."""
+    d = f(windows - g[:, None, None])
+    r = windows + (d if s is None else s[:, None, None] * d)
     for _ in range(level):
         r = reduce(r)
     coarse = reduce(r)
@@ -48,13 +52,15 @@ def _window_1d(p, level, n, margin):
     return lo, hi
 
 
-def _level_coefficients(img, gl, level, f, window):
-    """L_level[O] for every pixel of one level (level < top)."""
+def _level_coefficients(img, gl, level, f, window, scale=None):
+    """L_level[O] for every pixel of one level (level < top); ``scale``: per-pixel
+    detail scale at this level (same shape as gl) or None."""
     h0, w0 = img.shape
     hl, wl = gl.shape
     py, px = np.meshgrid(np.arange(hl), np.arange(wl), indexing="ij")
     py, px = py.ravel(), px.ravel()
     g = gl[py, px]
+    sc = None if scale is None else np.asarray(scale, dtype=np.float64)[py, px]
     out = np.empty(hl * wl)
     if window:
         margin = 6 * 2 ** level - 2
@@ -74,19 +80,35 @@ def _level_coefficients(img, gl, level, f, window):
             win = img[rows[:, :, None], cols[:, None, :]]
             ly = py[idx] - y0[idx] // 2 ** level
             lx = px[idx] - x0[idx] // 2 ** level
-            out[idx] = _laplacian_at(win, g[idx], f, level, ly, lx)
+            out[idx] = _laplacian_at(win, g[idx], f, level, ly, lx, None if sc is None else sc[idx])
     return out.reshape(hl, wl)
 
 
-def naive_llf(img, levels, f, window=True):
-    """Naive LLF of a plane (H, W) or planar channels (C, H, W); float64."""
+def naive_llf(img, levels, f, window=True, scale=None):
+    """Naive LLF of a plane (H, W) or planar channels (C, H, W); float64.
+
+    ``scale``: optional list of per-level arrays (level l shaped like G_l);
+    the coefficient at (l, p) then remaps with r = I + scale[l]_p f(I - g),
+    i.e. a pixel-by-pixel remap parameter (Sec. III-B)."""
     img = np.asarray(img, dtype=np.float64)
     if img.ndim == 3:
-        return np.stack([naive_llf(ch, levels, f, window) for ch in img])
+        return np.stack([naive_llf(ch, levels, f, window, scale) for ch in img])
     g = gaussian_pyramid(img, levels)
-    lap_o = [_level_coefficients(img, g[l], l, f, window) for l in range(levels - 1)]
+    lap_o = [_level_coefficients(img, g[l], l, f, window, None if scale is None else scale[l])
+             for l in range(levels - 1)]
     lap_o.append(g[-1])
     return collapse(lap_o)
 
 
-__all__ = ["naive_llf", "coarse_size"]
+def naive_llf_adaptive(img, levels, gain, sigma_r, window=True):
+    """Parameter-adaptive naive LLF (Sec. III-B): the gain m of the remap
+    becomes m_p.  ``gain`` is the level-0 map (H, W); at level l the gain is
+    G_l[gain]_p (reading: the Gaussian pyramid of the map, which keeps a
+    constant map constant), and the coefficient at (l, p) remaps with
+    f(d) = (G_l[gain]_p - 1) d exp(-d^2 / (2 sigma_r^2))."""
+    gm = gaussian_pyramid(np.asarray(gain, dtype=np.float64), levels)
+    unit = lambda d: d * np.exp(-d * d / (2.0 * sigma_r * sigma_r))
+    return naive_llf(img, levels, unit, window, [x - 1.0 for x in gm])
+
+
+__all__ = ["naive_llf", "naive_llf_adaptive", "coarse_size"]

@@ -111,3 +111,52 @@ def test_enhancement_increases_local_contrast():
     before = np.mean(np.abs(o.laplacian_pyramid(img, 2)[0]))
     after = np.mean(np.abs(o.laplacian_pyramid(out, 2)[0]))
     assert after > 1.3 * before
+
+
+# ---- pixel-by-pixel enhancement (Sec. III-B) ----------------------------------------
+def _gain_map(h, w, seed, lo=0.5, hi=4.0):
+    """A smooth, non-constant gain map in [lo, hi] (values of the paper's m range)."""
+    rng = np.random.default_rng(seed)
+    y, x = np.mgrid[0:h, 0:w]
+    a, b, ph = rng.uniform(0.05, 0.3), rng.uniform(0.05, 0.3), rng.uniform(0, 6.3)
+    return lo + (hi - lo) * 0.5 * (1 + np.sin(a * y + ph) * np.cos(b * x))
+
+
+@pytest.mark.parametrize("h,w,levels,K", [(16, 16, 3, 3), (21, 17, 3, 4), (40, 33, 4, 8),
+                                          (13, 50, 4, 6)])
+def test_adaptive_fourier_equals_adaptive_naive_with_truncated_remap(h, w, levels, K):
+    # Per pixel the remap detail is (m_p - 1) times the unit detail, whose
+    # K-term series has coefficients c_k: the adaptive Fourier LLF must equal
+    # the per-pixel naive LLF run with that truncated series, at roundoff.
+    img = _img(h, w, 7 * h + w)
+    gain = _gain_map(h, w, h * w)
+    c = o.coeffs_quadrature(2.0, 0.2, 2.0, K)        # m - 1 = 1: the unit detail
+    unit_k = lambda d: o.fourier_detail(d, c, 2.0)
+    gm = o.gaussian_pyramid(gain, levels)
+    out_f = o.fourier_llf_adaptive(img, levels, c, 2.0, gain)
+    out_n = o.naive_llf(img, levels, unit_k, window=False, scale=[x - 1.0 for x in gm])
+    np.testing.assert_allclose(out_f, out_n, rtol=0, atol=1e-12)
+
+
+@pytest.mark.parametrize("m", [0.5, 3.0])
+def test_adaptive_with_constant_gain_is_the_fixed_filter(m):
+    img = _img(37, 29, 11)
+    gain = np.full(img.shape, m)
+    c = o.coeffs_quadrature(2.0, 0.15, 2.0, 8)
+    a = o.coeffs_quadrature(m, 0.15, 2.0, 8)
+    np.testing.assert_allclose(o.fourier_llf_adaptive(img, 5, c, 2.0, gain),
+                               o.fourier_llf(img, 5, a, 2.0), rtol=0, atol=1e-12)
+    f = lambda d: o.remap_detail(d, m, 0.15)
+    np.testing.assert_allclose(o.naive_llf_adaptive(img, 4, gain, 0.15, window=False),
+                               o.naive_llf(img, 4, f, window=False), rtol=0, atol=1e-13)
+
+
+def test_adaptive_unit_gain_returns_input_and_windowed_naive_matches():
+    img = _img(48, 40, 3)
+    c = o.coeffs_quadrature(2.0, 0.2, 2.0, 6)
+    out = o.fourier_llf_adaptive(img, 5, c, 2.0, np.ones_like(img))
+    np.testing.assert_allclose(out, img, rtol=0, atol=1e-13)
+    gain = _gain_map(48, 40, 5)
+    full = o.naive_llf_adaptive(img, 4, gain, 0.1, window=False)
+    win = o.naive_llf_adaptive(img, 4, gain, 0.1, window=True)
+    np.testing.assert_allclose(win, full, rtol=0, atol=1e-13)
