@@ -130,6 +130,22 @@ fllf_status fllf_plan_coeffs(const fllf_plan *plan, double *a_out);
  * streams. */
 fllf_status fllf_run(fllf_plan *plan, const float *d_in, float *d_out, void *stream);
 
+/* Pixel-by-pixel enhancement (Sec. III-B): filters like fllf_run, but the
+ * remap gain m is a per-pixel map instead of the plan's constant.  The
+ * Gaussian Fourier pyramids do not depend on the remap, so only the
+ * coefficients change: at level l < top the Fourier term of Eq. (14) is
+ * scaled by (m_{l,p} - 1) / (m - 1), where m is the plan's gain and
+ * m_{l,p} = G_l[gain]_p is the Gaussian pyramid of the map at that pixel
+ * (a constant map reproduces fllf_run with that gain).
+ *   d_gain: device H x W float32 map (row pitch W) of the gain m_p, shared
+ *           by the C planes; read only.
+ *   The plan's m must differ from 1 (FLLF_EINVAL otherwise); sigma_r, T and
+ *   K stay the plan's.  The map's pyramid lives in a plan-owned device
+ *   buffer allocated on the first call.  d_in, d_out and d_gain must not
+ *   overlap d_out.  Stream-ordered like fllf_run. */
+fllf_status fllf_run_adaptive(fllf_plan *plan, const float *d_in, const float *d_gain, float *d_out,
+                              void *stream);
+
 /* End-to-end variant for host buffers: copies h_in to a plan-owned device
  * buffer, filters, copies the result to h_out and waits for the stream.
  * Allocates the two device I/O buffers on first use (kept by the plan). */

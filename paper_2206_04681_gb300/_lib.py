@@ -78,6 +78,7 @@ _SIGS = {
                                              ctypes.POINTER(ctypes.c_int)]),
     "fllf_optimal_period": (ctypes.c_int, [ctypes.c_double, ctypes.c_int, ctypes.c_double,
                                            ctypes.POINTER(ctypes.c_double)]),
+    "fllf_run_adaptive": (ctypes.c_int, [_P, _P, _P, _P, _P]),
 }
 
 STAGES = ("up0", "up", "down", "down0", "chain")
@@ -132,6 +133,11 @@ def fllf_coeffs(p):
     out = (ctypes.c_double * p.K)()
     _check(lib().fllf_coeffs(ctypes.byref(p), out))
     return list(out)
+
+
+def fllf_run_adaptive(plan, d_in, d_gain, d_out, stream=None):
+    """Pixel-by-pixel enhancement with a device gain map (Sec. III-B)."""
+    _check(lib().fllf_run_adaptive(plan, _P(d_in), _P(d_gain), _P(d_out), _P(stream or 0)))
 
 
 def fllf_optimal_period(sigma_r, K, R):

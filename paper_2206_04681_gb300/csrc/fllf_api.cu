@@ -209,6 +209,7 @@ void free_plan(fllf_plan* pl) {
   if (pl->scratch) cudaFree(pl->scratch);
   if (pl->d_io_in) cudaFree(pl->d_io_in);
   if (pl->d_io_out) cudaFree(pl->d_io_out);
+  if (pl->d_mpyr) cudaFree(pl->d_mpyr);
   delete pl->timer;
   delete pl;
 }
@@ -422,6 +423,48 @@ fllf_status fllf_run(fllf_plan* plan, const float* d_in, float* d_out, void* str
   if (!guard.ok) return fail(FLLF_ECUDA, "cudaSetDevice failed");
   cudaError_t e = enqueue_path(plan->p, plan->lv, plan->maps, plan->d_a, plan->d_fault, d_in, d_out,
                                reinterpret_cast<cudaStream_t>(stream), plan->timer);
+  if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
+  return FLLF_OK;
+}
+
+fllf_status fllf_run_adaptive(fllf_plan* plan, const float* d_in, const float* d_gain, float* d_out,
+                              void* stream) {
+  if (!plan) return fail(FLLF_EINVAL, "plan is NULL");
+  if (!d_in || !d_out || !d_gain) return fail(FLLF_EINVAL, "input, gain or output pointer is NULL");
+  const fllf_params& p = plan->p;
+  if (p.m == 1.0)
+    return fail(FLLF_EINVAL, "fllf_run_adaptive needs a plan with m != 1 (its coefficients are rescaled "
+                             "per pixel by (m_p - 1) / (m - 1))");
+  const size_t n = (size_t)p.H * p.W * p.C;
+  const char *a = reinterpret_cast<const char*>(d_in), *b = reinterpret_cast<const char*>(d_out);
+  const char* g = reinterpret_cast<const char*>(d_gain);
+  if (a < b + n * sizeof(float) && b < a + n * sizeof(float))
+    return fail(FLLF_EINVAL, "input and output buffers overlap");
+  if (g < b + n * sizeof(float) && b < g + (size_t)p.H * p.W * sizeof(float))
+    return fail(FLLF_EINVAL, "gain map and output buffers overlap");
+  DeviceGuard guard(plan->device);
+  if (!guard.ok) return fail(FLLF_ECUDA, "cudaSetDevice failed");
+  const int L = p.levels;
+  std::vector<Level> lv = plan->lv;
+  std::vector<size_t> off(L, 0);
+  size_t bytes = 0;
+  for (int l = 1; l <= L - 2; ++l) {
+    off[l] = bytes;
+    bytes += align256(sizeof(float) * (size_t)lv[l].h * lv[l].pitch);
+  }
+  if (bytes && !plan->d_mpyr) {
+    cudaError_t e = cudaMalloc(&plan->d_mpyr, bytes);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      plan->d_mpyr = nullptr;
+      return fail(FLLF_ENOMEM, "gain-map pyramid allocation failed");
+    }
+  }
+  for (int l = 1; l <= L - 2; ++l)
+    lv[l].M = reinterpret_cast<const float*>(reinterpret_cast<unsigned char*>(plan->d_mpyr) + off[l]);
+  cudaError_t e = enqueue_path(p, lv, plan->maps, plan->d_a, plan->d_fault, d_in, d_out,
+                               reinterpret_cast<cudaStream_t>(stream), plan->timer, d_gain,
+                               (float)(1.0 / (p.m - 1.0)));
   if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
   return FLLF_OK;
 }

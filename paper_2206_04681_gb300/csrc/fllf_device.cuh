@@ -64,6 +64,7 @@ struct Level {
   float* G;             // guide level G_l[I] (null at level 0)
   void* Z;              // K complex Fourier planes
   float* E;             // residual E_l (null at l = levels-1)
+  const float* M;       // gain map G_l[M] of pixel-adaptive runs (one plane, this pitch), else null
 };
 
 // Kernel arguments.  Tensor maps describe the level buffers as 3-D tensors
@@ -102,6 +103,7 @@ struct DownArgs {
   int planes, K;
   float turns;
   int has_e;            // E_{l+1} exists (l+1 <= levels-2)
+  float mscale;         // 1/(m - 1): the gain map's scale of the Fourier term (fine.M set)
   unsigned* fault;
 };
 
@@ -115,6 +117,8 @@ struct Down0Args {
   int K;
   float turns;
   int has_e;            // E_1 exists (levels >= 3)
+  const float* M0;      // level-0 gain map (pitch w0) of pixel-adaptive runs, else null
+  float mscale;         // 1/(m - 1)
   unsigned* fault;
 };
 
@@ -135,6 +139,9 @@ struct Down10Args {
   float turns;
   int has_e2;           // E_2 exists (levels >= 4)
   int use_tma;          // input rows 16-byte aligned (w0 % 4 == 0, aligned base)
+  const float* M0;      // level-0 gain map (pitch w0) of pixel-adaptive runs, else null;
+                        // the level-1 map is l1.M
+  float mscale;         // 1/(m - 1)
   unsigned* fault;
 };
 

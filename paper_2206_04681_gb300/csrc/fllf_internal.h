@@ -83,10 +83,14 @@ struct PathMaps {
 bool build_maps(const fllf_params& p, const std::vector<Level>& lv, PathMaps* m);
 
 // Enqueues the whole Fourier LLF path of one image on stream s.  `fault`
-// is a device word that kernels set when a bounded wait runs out.
+// is a device word that kernels set when a bounded wait runs out.  With a
+// gain map d_gain (H x W, pitch W) the levels' M pointers must hold its
+// pyramid buffers (levels 1..levels-2); the path builds the pyramid and
+// scales each level's Fourier term by (m_{l,p} - 1) * mscale.
 cudaError_t enqueue_path(const fllf_params& p, const std::vector<Level>& lv, const PathMaps& maps,
                          const float* d_a, unsigned* fault, const float* d_in, float* d_out,
-                         cudaStream_t s, StageHook* hook = nullptr);
+                         cudaStream_t s, StageHook* hook = nullptr, const float* d_gain = nullptr,
+                         float mscale = 0.f);
 
 // ---- batched argument tables (shared by batches and the server) ---------------
 enum BatchStageKind { kStageUp0 = 0, kStageUp = 1, kStageDown = 2, kStageDown0 = 3 };
@@ -129,4 +133,5 @@ struct fllf_plan {
   fllf::StageTimer* timer = nullptr;  // per-stage timing diagnostics (optional)
   fllf::PathMaps maps;                // TMA tensor maps of the level buffers
   unsigned* d_fault = nullptr;        // device status block (fault word, grid-barrier words)
+  float* d_mpyr = nullptr;            // gain-map pyramid of pixel-adaptive runs (first use)
 };

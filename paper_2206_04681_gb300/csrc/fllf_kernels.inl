@@ -11,6 +11,10 @@
 // counts).
 #include "fllf_launch.h"
 
+#ifndef FLLF_STORAGE_IS_F32
+#define FLLF_STORAGE_IS_F32 0
+#endif
+
 namespace fllf {
 
 namespace {
@@ -482,12 +486,13 @@ struct CombineView {
   float* O;
   const Level* coarse;
   unsigned* fault;
+  const float* M0;
   int h, w, planes, K, has_e;
-  float turns;
+  float turns, mscale;
 };
 __device__ __forceinline__ CombineView view_of(const Down0Args& d) {
-  return CombineView{&d.zmap, &d.emap, d.I, d.O, &d.coarse, d.fault,
-                     d.h0, d.w0, d.planes, d.K, d.has_e, d.turns};
+  return CombineView{&d.zmap, &d.emap, d.I, d.O, &d.coarse, d.fault, d.M0,
+                     d.h0, d.w0, d.planes, d.K, d.has_e, d.turns, d.mscale};
 }
 __device__ __forceinline__ int combine_tiles(int h, int w, int planes) {
   return cdiv(w + kDnX0, kDnOW) * cdiv(h, kDnOH) * planes;
@@ -605,8 +610,11 @@ __device__ __forceinline__ bool stage_combine0(Res res, int total, unsigned char
             const int x = fx + q;
             // the EXPAND weight and the sign of D_k are applied here
             const float2 sc = expand_scale_pair(q);
-            const float delta = rr ? -sc.y * im_mul(Po[q], wo[q]) : -sc.x * im_mul(Pe[q], we[q]);
-            if (x >= 0 && x < w) d[x] = (rr ? base[q].y : base[q].x) + delta;
+            float delta = rr ? -sc.y * im_mul(Po[q], wo[q]) : -sc.x * im_mul(Pe[q], we[q]);
+            if (x >= 0 && x < w) {
+              if (v.M0) delta *= (__ldg(v.M0 + (long long)y * w + x) - 1.f) * v.mscale;
+              d[x] = (rr ? base[q].y : base[q].x) + delta;
+            }
           }
         }
       }
@@ -771,8 +779,12 @@ __device__ __forceinline__ bool stage_combine1(Res res, int total, unsigned char
 #pragma unroll
           for (int q = 0; q < 4; ++q) {
             const int x = fx + q;
-            const float delta = rr ? im_mul(Po[q], wo[q]) : im_mul(Pe[q], we[q]);
-            if (x >= 0 && x < w) d[x] = (rr ? base[q].y : base[q].x) + delta;
+            float delta = rr ? im_mul(Po[q], wo[q]) : im_mul(Pe[q], we[q]);
+            if (x >= 0 && x < w) {
+              if (a->fine.M)
+                delta *= (__ldg(a->fine.M + (long long)y * a->fine.pitch + x) - 1.f) * a->mscale;
+              d[x] = (rr ? base[q].y : base[q].x) + delta;
+            }
           }
         }
       }
@@ -1020,8 +1032,11 @@ __device__ __forceinline__ bool stage_down10(Res res, int total, unsigned char* 
 #pragma unroll
           for (int cc = 0; cc < 2; ++cc) {
             const int y1 = cy0 + 2 * br + rr, x1 = cx0 + 2 * bc + cc;
-            if (y1 >= 0 && y1 < L1.h && x1 >= 0 && x1 < L1.w)
-              e1[(2 * br + rr) * kDnCW + 2 * bc + cc] = im_mul(P1[rr][cc], w1[rr][cc]) + up_e2[rr][cc];
+            if (y1 >= 0 && y1 < L1.h && x1 >= 0 && x1 < L1.w) {
+              float d1 = im_mul(P1[rr][cc], w1[rr][cc]);
+              if (L1.M) d1 *= (__ldg(L1.M + (long long)y1 * L1.pitch + x1) - 1.f) * a->mscale;
+              e1[(2 * br + rr) * kDnCW + 2 * bc + cc] = d1 + up_e2[rr][cc];
+            }
           }
       }
       __syncthreads();
@@ -1038,8 +1053,11 @@ __device__ __forceinline__ bool stage_down10(Res res, int total, unsigned char* 
           for (int q = 0; q < 4; ++q) {
             const int x = fx + q;
             const float2 sc = expand_scale_pair(q);
-            const float delta = rr ? -sc.y * im_mul(Po[q], wo[q]) : -sc.x * im_mul(Pe[q], we[q]);
-            if (x >= 0 && x < w0) d[x] = (rr ? base[q].y + ue[q].y : base[q].x + ue[q].x) + delta;
+            float delta = rr ? -sc.y * im_mul(Po[q], wo[q]) : -sc.x * im_mul(Pe[q], we[q]);
+            if (x >= 0 && x < w0) {
+              if (a->M0) delta *= (__ldg(a->M0 + (long long)y * w0 + x) - 1.f) * a->mscale;
+              d[x] = (rr ? base[q].y + ue[q].y : base[q].x + ue[q].x) + delta;
+            }
           }
         }
       }
@@ -1271,6 +1289,31 @@ __global__ void __launch_bounds__(kThreads, 2) k_chain(const __grid_constant__ C
   }
 }
 
+#if FLLF_STORAGE_IS_F32
+// ---------------------------------------------------------------------------------------
+// REDUCE (Eq. (1)) of one float plane: the gain map's Gaussian pyramid for
+// pixel-adaptive runs.  One thread per output, 5 x 5 binomial taps with
+// reflect-101 at the source size.
+__global__ void __launch_bounds__(kThreads) k_map_reduce(const float* __restrict__ src, int sh, int sw,
+                                                          int spitch, float* __restrict__ dst, int dh,
+                                                          int dw, int dpitch) {
+  const int idx = blockIdx.x * kThreads + threadIdx.x;
+  if (idx >= dh * dw) return;
+  const int y = idx / dw, x = idx - y * dw;
+  const float k5[5] = {1.f, 4.f, 6.f, 4.f, 1.f};
+  float acc = 0.f;
+#pragma unroll
+  for (int i = 0; i < 5; ++i) {
+    const float* row = src + (long long)refl_fast(2 * y + i - 2, sh) * spitch;
+    float h = 0.f;
+#pragma unroll
+    for (int j = 0; j < 5; ++j) h = fmaf(k5[j], __ldg(row + refl_fast(2 * x + j - 2, sw)), h);
+    acc = fmaf(k5[i], h, acc);
+  }
+  dst[(long long)y * dpitch + x] = acc * (1.f / 256.f);
+}
+#endif
+
 // Persistent grid: at most (resident CTAs per SM) x (SMs) CTAs.
 template <typename Kern>
 int persistent_grid(Kern kern, size_t smem, int items) {
@@ -1344,6 +1387,15 @@ cudaError_t FLLF_LAUNCH_NAME(chain)(const ChainArgs& a, cudaStream_t s) {
                                               dim3(grid), dim3(kThreads), args, kChainSmem, s);
   return e != cudaSuccess ? e : cudaGetLastError();
 }
+
+#if FLLF_STORAGE_IS_F32
+cudaError_t launch_map_reduce(const float* src, int sh, int sw, int spitch, float* dst, int dh, int dw,
+                              int dpitch, cudaStream_t s) {
+  const int n = dh * dw;
+  k_map_reduce<<<cdiv(n, kThreads), kThreads, 0, s>>>(src, sh, sw, spitch, dst, dh, dw, dpitch);
+  return cudaGetLastError();
+}
+#endif
 
 // Batched launches: the grid covers every work item of the table.
 cudaError_t FLLF_LAUNCH_NAME(up0_batch)(const BatchTable<Up0Args>& tb, cudaStream_t s) {

@@ -19,6 +19,9 @@ namespace fllf {
   cudaError_t launch_up_batch_##suffix(const BatchTable<UpArgs>& t, cudaStream_t s);     \
   cudaError_t launch_down_batch_##suffix(const BatchTable<DownArgs>& t, cudaStream_t s); \
   cudaError_t launch_down0_batch_##suffix(const BatchTable<Down0Args>& t, cudaStream_t s);
+// REDUCE of one float plane (the gain map of pixel-adaptive runs).
+cudaError_t launch_map_reduce(const float* src, int sh, int sw, int spitch, float* dst, int dh, int dw,
+                              int dpitch, cudaStream_t s);
 FLLF_DECLARE_LAUNCHERS(f32)
 FLLF_DECLARE_LAUNCHERS(f16)
 FLLF_DECLARE_LAUNCHERS(bf16)

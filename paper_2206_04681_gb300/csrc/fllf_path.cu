@@ -175,7 +175,7 @@ bool build_maps(const fllf_params& p, const std::vector<Level>& lv, PathMaps* m)
 
 cudaError_t enqueue_path(const fllf_params& p, const std::vector<Level>& lv, const PathMaps& maps,
                          const float* d_a, unsigned* fault, const float* d_in, float* d_out,
-                         cudaStream_t s, StageHook* hook) {
+                         cudaStream_t s, StageHook* hook, const float* d_gain, float mscale) {
   const int L = p.levels, C = p.C, prec = p.precision;
   const float turns = (float)(2.0 / p.T);
   if (L == 1) {
@@ -206,6 +206,16 @@ cudaError_t enqueue_path(const fllf_params& p, const std::vector<Level>& lv, con
   mark(FLLF_STAGE_UP0, true);
   if ((e = launch_up0(prec, u0, s)) != cudaSuccess) return e;
   mark(FLLF_STAGE_UP0, false);
+  if (d_gain) {
+    // Gaussian pyramid of the gain map, levels 1..L-2 (the levels that combine)
+    for (int l = 1; l <= L - 2; ++l) {
+      const float* src = l == 1 ? d_gain : lv[l - 1].M;
+      const int sp = l == 1 ? p.W : lv[l - 1].pitch;
+      if ((e = launch_map_reduce(src, lv[l - 1].h, lv[l - 1].w, sp, const_cast<float*>(lv[l].M), lv[l].h,
+                                 lv[l].w, lv[l].pitch, s)) != cudaSuccess)
+        return e;
+    }
+  }
 
   // Levels >= c0 run as one chained cooperative launch: from the first level
   // (>= 2) whose pixels over all planes fit in 2^21, the REDUCE stages up to
@@ -245,6 +255,7 @@ cudaError_t enqueue_path(const fllf_params& p, const std::vector<Level>& lv, con
     d.K = p.K;
     d.turns = turns;
     d.has_e = (l + 1 <= L - 2) ? 1 : 0;
+    d.mscale = mscale;
     d.fault = fault;
     return d;
   };
@@ -288,6 +299,8 @@ cudaError_t enqueue_path(const fllf_params& p, const std::vector<Level>& lv, con
     d.K = p.K;
     d.turns = turns;
     d.has_e2 = (L >= 4) ? 1 : 0;
+    d.M0 = d_gain;
+    d.mscale = mscale;
     d.use_tma = (u0.use_tma && encode3(&d.imap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, d_in, p.W, p.H, C,
                                        4ull * p.W, 4ull * p.W * p.H, kD0IW, kDnOH, 1))
                     ? 1
@@ -310,6 +323,8 @@ cudaError_t enqueue_path(const fllf_params& p, const std::vector<Level>& lv, con
   d0.K = p.K;
   d0.turns = turns;
   d0.has_e = (L >= 3) ? 1 : 0;
+  d0.M0 = d_gain;
+  d0.mscale = mscale;
   d0.fault = fault;
   mark(FLLF_STAGE_DOWN0, true);
   if ((e = launch_down0(prec, d0, s)) != cudaSuccess) return e;

@@ -153,3 +153,33 @@ def request_stream(rate, duration, seed=5, max_side=8192, min_side=512):
                         levels=auto_levels(h, w), K=int(rng.choice([4, 8, 16])),
                         m=float(rng.uniform(0.5, 4.0)),
                         sigma_r=float(rng.uniform(0.05, 0.4)), T=2.0))
+
+
+def variance_gain_map(img, m_lo=1.0, m_hi=3.0, radius=3, var_ref=None):
+    """Per-pixel gain map for pixel-adaptive enhancement, as in the paper's
+    experiment: the degree of enhancement follows the variance of the pixels
+    in a local window, and low variance gets a small enhancement.
+
+    ``img``: (H, W) or (C, H, W); the variance is taken over a
+    (2 radius + 1)^2 box of the channel mean (edges replicated).  The gain is
+    m_lo + (m_hi - m_lo) * min(var / var_ref, 1), with var_ref the 90th
+    percentile of the variance unless given.  Returns (H, W) float32.
+    """
+    x = np.asarray(img, dtype=np.float64)
+    if x.ndim == 3:
+        x = x.mean(axis=0)
+    k = 2 * radius + 1
+    pad = np.pad(x, radius, mode="edge")
+    s1 = np.zeros_like(x)
+    s2 = np.zeros_like(x)
+    h, w = x.shape
+    for dy in range(k):
+        for dx in range(k):
+            v = pad[dy:dy + h, dx:dx + w]
+            s1 += v
+            s2 += v * v
+    mean = s1 / (k * k)
+    var = np.maximum(s2 / (k * k) - mean * mean, 0.0)
+    ref = float(np.percentile(var, 90)) if var_ref is None else float(var_ref)
+    t = np.minimum(var / max(ref, 1e-12), 1.0)
+    return (m_lo + (m_hi - m_lo) * t).astype(np.float32)
