@@ -17,6 +17,7 @@ It is a plain, slow, obviously-correct restatement of Sumiya et al.,
 * ``naive_llf``    naive LLF, the per-pixel per-level procedure of Sec. II-C,
                    on the whole image or on exact dependency windows.
 * ``*_adaptive``   the pixel-by-pixel parameter of Sec. III-B (a gain map).
+* ``fourier_llf_luma``  colour by LLF on the Y of YUV (Sec. IV).
 
 Every function is pinned by ``tests/test_oracle_*.py`` against facts the
 paper or the mathematics fixes (library routines, closed forms, invariants,
@@ -29,7 +30,8 @@ from .pyramid import (reflect101, reduce, expand, gaussian_pyramid,
 from .remap import (remap_detail, remap, omegas, coeffs_quadrature,
                     coeffs_closed_form, fourier_detail, period_error,
                     optimal_period, coeff_tail_bound)
-from .fourier_llf import fourier_llf, fourier_llf_levels, fourier_llf_adaptive
+from .fourier_llf import (fourier_llf, fourier_llf_levels, fourier_llf_adaptive, fourier_llf_luma,
+                          rgb_to_yuv, yuv_to_rgb, LUMA_BT601)
 from .naive_llf import naive_llf, naive_llf_adaptive
 
 __all__ = [
@@ -38,5 +40,6 @@ __all__ = [
     "remap_detail", "remap", "omegas", "coeffs_quadrature",
     "coeffs_closed_form", "fourier_detail", "period_error", "optimal_period",
     "coeff_tail_bound", "fourier_llf", "fourier_llf_levels", "naive_llf",
-    "fourier_llf_adaptive", "naive_llf_adaptive",
+    "fourier_llf_adaptive", "naive_llf_adaptive", "fourier_llf_luma", "rgb_to_yuv",
+    "yuv_to_rgb", "LUMA_BT601",
 ]

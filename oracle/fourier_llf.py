@@ -92,3 +92,32 @@ def fourier_llf_adaptive(img, levels, c, T, gain):
             out[l] += (gm[l] - 1.0) * ck * (cg * lap_s[l] - sg * lap_c[l])
     out.append(g[-1])
     return collapse(out)
+
+
+# BT.601 luma weights (reading: the paper's YUV is the BT.601 one).
+LUMA_BT601 = (0.299, 0.587, 0.114)
+
+
+def rgb_to_yuv(rgb):
+    """BT.601 YUV of a planar (3, H, W) RGB image: Y = 0.299 R + 0.587 G +
+    0.114 B, U = 0.492 (B - Y), V = 0.877 (R - Y)."""
+    r, g, b = (np.asarray(c, dtype=np.float64) for c in rgb)
+    y = LUMA_BT601[0] * r + LUMA_BT601[1] * g + LUMA_BT601[2] * b
+    return np.stack([y, 0.492 * (b - y), 0.877 * (r - y)])
+
+
+def yuv_to_rgb(yuv):
+    """Inverse of ``rgb_to_yuv`` (solves its 3 x 3 matrix)."""
+    m = np.array([[LUMA_BT601[0], LUMA_BT601[1], LUMA_BT601[2]],
+                  [-0.492 * LUMA_BT601[0], -0.492 * LUMA_BT601[1], 0.492 * (1 - LUMA_BT601[2])],
+                  [0.877 * (1 - LUMA_BT601[0]), -0.877 * LUMA_BT601[1], -0.877 * LUMA_BT601[2]]])
+    flat = np.asarray(yuv, dtype=np.float64).reshape(3, -1)
+    return np.linalg.solve(m, flat).reshape(np.shape(yuv))
+
+
+def fourier_llf_luma(rgb, levels, a, T):
+    """Colour processing of the paper's experiments (Sec. IV): LLF on the Y
+    channel of YUV, the other components kept; float64, planar (3, H, W)."""
+    yuv = rgb_to_yuv(rgb)
+    yuv[0] = fourier_llf(yuv[0], levels, a, T)
+    return yuv_to_rgb(yuv)

@@ -160,3 +160,34 @@ def test_adaptive_unit_gain_returns_input_and_windowed_naive_matches():
     full = o.naive_llf_adaptive(img, 4, gain, 0.1, window=False)
     win = o.naive_llf_adaptive(img, 4, gain, 0.1, window=True)
     np.testing.assert_allclose(win, full, rtol=0, atol=1e-13)
+
+
+# ---- colour by luma (Sec. IV: LLF on Y of YUV, U and V kept) -------------------------
+def test_yuv_round_trip_and_luma_of_gray():
+    rng = np.random.default_rng(0)
+    rgb = rng.uniform(0, 1, (3, 9, 7))
+    np.testing.assert_allclose(o.yuv_to_rgb(o.rgb_to_yuv(rgb)), rgb, rtol=0, atol=1e-14)
+    gray = np.repeat(rng.uniform(0, 1, (1, 5, 6)), 3, axis=0)
+    yuv = o.rgb_to_yuv(gray)
+    np.testing.assert_allclose(yuv[0], gray[0], rtol=0, atol=1e-15)   # weights sum to 1
+    np.testing.assert_allclose(yuv[1:], 0.0, rtol=0, atol=1e-15)
+
+
+def test_luma_mode_of_a_gray_image_filters_each_channel_alike():
+    img = _img(40, 36, 2)
+    a = o.coeffs_quadrature(3.0, 0.2, 2.0, 6)
+    out = o.fourier_llf_luma(np.stack([img] * 3), 5, a, 2.0)
+    ref = o.fourier_llf(img, 5, a, 2.0)
+    for c in range(3):
+        np.testing.assert_allclose(out[c], ref, rtol=0, atol=1e-13)
+
+
+def test_luma_mode_adds_the_luma_change_to_every_channel():
+    # U and V kept => every channel moves by Y' - Y (the form the library uses)
+    rgb = synth_image(33, 45, 3, polygons=4, seed=6).astype(np.float64)
+    a = o.coeffs_quadrature(2.5, 0.15, 2.0, 8)
+    out = o.fourier_llf_luma(rgb, 5, a, 2.0)
+    y = sum(w * c for w, c in zip(o.LUMA_BT601, rgb))
+    dy = o.fourier_llf(y, 5, a, 2.0) - y
+    np.testing.assert_allclose(out, rgb + dy[None], rtol=0, atol=1e-13)
+    np.testing.assert_allclose(o.fourier_llf_luma(rgb, 5, a * 0.0, 2.0), rgb, rtol=0, atol=1e-13)
