@@ -146,6 +146,17 @@ fllf_status fllf_run(fllf_plan *plan, const float *d_in, float *d_out, void *str
 fllf_status fllf_run_adaptive(fllf_plan *plan, const float *d_in, const float *d_gain, float *d_out,
                               void *stream);
 
+/* Colour by luma, the colour processing of the paper's experiments
+ * (Sec. IV): LLF is applied to the Y channel of YUV and the other
+ * components are kept.  YUV is BT.601 (Y = 0.299 R + 0.587 G + 0.114 B);
+ * keeping U and V means every output channel is the input channel plus
+ * Y' - Y, with Y' the filtered luma.
+ *   plan: C == 1 (it filters the H x W luma plane), otherwise FLLF_EINVAL.
+ *   d_rgb_in, d_rgb_out: device planar RGB, 3 x H x W float32, not
+ *   overlapping.  Two plan-owned H x W luma buffers are allocated on the
+ *   first call.  Stream-ordered like fllf_run. */
+fllf_status fllf_run_luma(fllf_plan *plan, const float *d_rgb_in, float *d_rgb_out, void *stream);
+
 /* End-to-end variant for host buffers: copies h_in to a plan-owned device
  * buffer, filters, copies the result to h_out and waits for the stream.
  * Allocates the two device I/O buffers on first use (kept by the plan). */

@@ -8,7 +8,7 @@ memory and streams.
 """
 
 from ._lib import (FllfError, fllf_params, make_params, lib, fllf_params_validate, fllf_coeffs,
-                   fllf_optimal_period, fllf_run_adaptive,
+                   fllf_optimal_period, fllf_run_adaptive, fllf_run_luma,
                    fllf_plan_scratch_bytes, fllf_plan_create, fllf_plan_destroy,
                    fllf_plan_params, fllf_plan_coeffs, fllf_run, fllf_run_host, fllf_submit,
                    fllf_poll, fllf_batch_create, fllf_batch_destroy, fllf_batch_run,

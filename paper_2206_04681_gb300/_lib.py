@@ -79,6 +79,7 @@ _SIGS = {
     "fllf_optimal_period": (ctypes.c_int, [ctypes.c_double, ctypes.c_int, ctypes.c_double,
                                            ctypes.POINTER(ctypes.c_double)]),
     "fllf_run_adaptive": (ctypes.c_int, [_P, _P, _P, _P, _P]),
+    "fllf_run_luma": (ctypes.c_int, [_P, _P, _P, _P]),
 }
 
 STAGES = ("up0", "up", "down", "down0", "chain")
@@ -138,6 +139,11 @@ def fllf_coeffs(p):
 def fllf_run_adaptive(plan, d_in, d_gain, d_out, stream=None):
     """Pixel-by-pixel enhancement with a device gain map (Sec. III-B)."""
     _check(lib().fllf_run_adaptive(plan, _P(d_in), _P(d_gain), _P(d_out), _P(stream or 0)))
+
+
+def fllf_run_luma(plan, d_rgb_in, d_rgb_out, stream=None):
+    """Colour by luma: LLF on Y of BT.601 YUV, U and V kept (C == 1 plan)."""
+    _check(lib().fllf_run_luma(plan, _P(d_rgb_in), _P(d_rgb_out), _P(stream or 0)))
 
 
 def fllf_optimal_period(sigma_r, K, R):

@@ -210,6 +210,7 @@ void free_plan(fllf_plan* pl) {
   if (pl->d_io_in) cudaFree(pl->d_io_in);
   if (pl->d_io_out) cudaFree(pl->d_io_out);
   if (pl->d_mpyr) cudaFree(pl->d_mpyr);
+  if (pl->d_luma) cudaFree(pl->d_luma);
   delete pl->timer;
   delete pl;
 }
@@ -466,6 +467,39 @@ fllf_status fllf_run_adaptive(fllf_plan* plan, const float* d_in, const float* d
                                reinterpret_cast<cudaStream_t>(stream), plan->timer, d_gain,
                                (float)(1.0 / (p.m - 1.0)));
   if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
+  return FLLF_OK;
+}
+
+fllf_status fllf_run_luma(fllf_plan* plan, const float* d_rgb_in, float* d_rgb_out, void* stream) {
+  if (!plan) return fail(FLLF_EINVAL, "plan is NULL");
+  if (!d_rgb_in || !d_rgb_out) return fail(FLLF_EINVAL, "input or output pointer is NULL");
+  const fllf_params& p = plan->p;
+  if (p.C != 1) return fail(FLLF_EINVAL, "fllf_run_luma needs a plan with C == 1 (it filters the luma plane)");
+  const size_t n = (size_t)p.H * p.W;
+  const char *a = reinterpret_cast<const char*>(d_rgb_in), *b = reinterpret_cast<const char*>(d_rgb_out);
+  if (a < b + 3 * n * sizeof(float) && b < a + 3 * n * sizeof(float))
+    return fail(FLLF_EINVAL, "input and output buffers overlap");
+  DeviceGuard guard(plan->device);
+  if (!guard.ok) return fail(FLLF_ECUDA, "cudaSetDevice failed");
+  if (!plan->d_luma) {
+    cudaError_t e = cudaMalloc(&plan->d_luma, 2 * n * sizeof(float));
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      plan->d_luma = nullptr;
+      return fail(FLLF_ENOMEM, "luma buffer allocation failed");
+    }
+  }
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  float* y = plan->d_luma;
+  float* yf = plan->d_luma + n;
+  static const float kLuma[3] = {0.299f, 0.587f, 0.114f};  // BT.601
+  cudaError_t e;
+  if ((e = launch_luma(d_rgb_in, y, (long long)n, kLuma, s)) != cudaSuccess) return cuda_fail(e, "luma");
+  if ((e = enqueue_path(p, plan->lv, plan->maps, plan->d_a, plan->d_fault, y, yf, s, plan->timer)) !=
+      cudaSuccess)
+    return cuda_fail(e, "kernel launch");
+  if ((e = launch_luma_apply(d_rgb_in, y, yf, d_rgb_out, (long long)n, s)) != cudaSuccess)
+    return cuda_fail(e, "luma apply");
   return FLLF_OK;
 }
 

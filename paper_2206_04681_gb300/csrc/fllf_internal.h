@@ -134,4 +134,5 @@ struct fllf_plan {
   fllf::PathMaps maps;                // TMA tensor maps of the level buffers
   unsigned* d_fault = nullptr;        // device status block (fault word, grid-barrier words)
   float* d_mpyr = nullptr;            // gain-map pyramid of pixel-adaptive runs (first use)
+  float* d_luma = nullptr;            // Y and filtered Y of colour-by-luma runs (first use)
 };

@@ -9,6 +9,8 @@
 // kernels (arguments in the parameter block), many images for the batched
 // kernels (argument tables in device memory, with prefix sums of the item
 // counts).
+#include <algorithm>
+
 #include "fllf_launch.h"
 
 #ifndef FLLF_STORAGE_IS_F32
@@ -1312,6 +1314,24 @@ __global__ void __launch_bounds__(kThreads) k_map_reduce(const float* __restrict
   }
   dst[(long long)y * dpitch + x] = acc * (1.f / 256.f);
 }
+
+// Colour by luma (LLF on Y of YUV, U and V kept): Y = w . RGB of a planar
+// RGB image (n pixels per plane), and back: every channel moves by Y' - Y.
+__global__ void __launch_bounds__(kThreads) k_luma(const float* __restrict__ rgb, float* __restrict__ y,
+                                                   long long n, float wr, float wg, float wb) {
+  for (long long i = blockIdx.x * (long long)kThreads + threadIdx.x; i < n; i += (long long)gridDim.x * kThreads)
+    y[i] = fmaf(wr, __ldg(rgb + i), fmaf(wg, __ldg(rgb + n + i), wb * __ldg(rgb + 2 * n + i)));
+}
+__global__ void __launch_bounds__(kThreads) k_luma_apply(const float* __restrict__ rgb,
+                                                         const float* __restrict__ y,
+                                                         const float* __restrict__ yf, float* __restrict__ out,
+                                                         long long n) {
+  for (long long i = blockIdx.x * (long long)kThreads + threadIdx.x; i < n; i += (long long)gridDim.x * kThreads) {
+    const float d = __ldg(yf + i) - __ldg(y + i);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) out[c * n + i] = __ldg(rgb + c * n + i) + d;
+  }
+}
 #endif
 
 // Persistent grid: at most (resident CTAs per SM) x (SMs) CTAs.
@@ -1389,6 +1409,17 @@ cudaError_t FLLF_LAUNCH_NAME(chain)(const ChainArgs& a, cudaStream_t s) {
 }
 
 #if FLLF_STORAGE_IS_F32
+cudaError_t launch_luma(const float* rgb, float* y, long long n, const float w[3], cudaStream_t s) {
+  const int grid = (int)std::min<long long>(cdiv((int)std::min<long long>(n, 1LL << 30), kThreads), 152 * 8);
+  k_luma<<<grid, kThreads, 0, s>>>(rgb, y, n, w[0], w[1], w[2]);
+  return cudaGetLastError();
+}
+cudaError_t launch_luma_apply(const float* rgb, const float* y, const float* yf, float* out, long long n,
+                              cudaStream_t s) {
+  const int grid = (int)std::min<long long>(cdiv((int)std::min<long long>(n, 1LL << 30), kThreads), 152 * 8);
+  k_luma_apply<<<grid, kThreads, 0, s>>>(rgb, y, yf, out, n);
+  return cudaGetLastError();
+}
 cudaError_t launch_map_reduce(const float* src, int sh, int sw, int spitch, float* dst, int dh, int dw,
                               int dpitch, cudaStream_t s) {
   const int n = dh * dw;

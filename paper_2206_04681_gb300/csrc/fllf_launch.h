@@ -22,6 +22,10 @@ namespace fllf {
 // REDUCE of one float plane (the gain map of pixel-adaptive runs).
 cudaError_t launch_map_reduce(const float* src, int sh, int sw, int spitch, float* dst, int dh, int dw,
                               int dpitch, cudaStream_t s);
+// Luma of a planar RGB image (n pixels per plane), and the luma change added back.
+cudaError_t launch_luma(const float* rgb, float* y, long long n, const float w[3], cudaStream_t s);
+cudaError_t launch_luma_apply(const float* rgb, const float* y, const float* yf, float* out, long long n,
+                              cudaStream_t s);
 FLLF_DECLARE_LAUNCHERS(f32)
 FLLF_DECLARE_LAUNCHERS(f16)
 FLLF_DECLARE_LAUNCHERS(bf16)
