@@ -90,6 +90,7 @@ struct UpArgs {
   Level dst;            // level l+1
   int planes, K;
   int write_g;          // G_{l+1} needed (l+1 <= levels-2)
+  int reverse;          // visit the work items last to first (L2 reuse of the level just written)
   unsigned* fault;
 };
 

@@ -827,7 +827,7 @@ __device__ __forceinline__ bool stage_combine1(Res res, int total, unsigned char
 // EXPAND sources, and every thread finishes O = I + Delta_0 + up(E_1) for its
 // 2 x 4 level-0 pixels.  E_1 never goes to memory, and each Z_1 sample is
 // read once for both levels.
-template <typename S, typename Res>
+template <typename S, bool ADAPT, typename Res>
 __device__ __forceinline__ bool stage_down10(Res res, int total, unsigned char* smem, uint64_t* bar,
                                             Pipe& pp, int b, int G) {
   using CT = typename Cplx<S>::T;
@@ -1036,7 +1036,7 @@ __device__ __forceinline__ bool stage_down10(Res res, int total, unsigned char* 
             const int y1 = cy0 + 2 * br + rr, x1 = cx0 + 2 * bc + cc;
             if (y1 >= 0 && y1 < L1.h && x1 >= 0 && x1 < L1.w) {
               float d1 = im_mul(P1[rr][cc], w1[rr][cc]);
-              if (L1.M) d1 *= (__ldg(L1.M + (long long)y1 * L1.pitch + x1) - 1.f) * a->mscale;
+              if constexpr (ADAPT) d1 *= (__ldg(L1.M + (long long)y1 * L1.pitch + x1) - 1.f) * a->mscale;
               e1[(2 * br + rr) * kDnCW + 2 * bc + cc] = d1 + up_e2[rr][cc];
             }
           }
@@ -1057,7 +1057,7 @@ __device__ __forceinline__ bool stage_down10(Res res, int total, unsigned char* 
             const float2 sc = expand_scale_pair(q);
             float delta = rr ? -sc.y * im_mul(Po[q], wo[q]) : -sc.x * im_mul(Pe[q], we[q]);
             if (x >= 0 && x < w0) {
-              if (a->M0) delta *= (__ldg(a->M0 + (long long)y * w0 + x) - 1.f) * a->mscale;
+              if constexpr (ADAPT) delta *= (__ldg(a->M0 + (long long)y * w0 + x) - 1.f) * a->mscale;
               d[x] = (rr ? base[q].y + ue[q].y : base[q].x + ue[q].x) + delta;
             }
           }
@@ -1102,8 +1102,11 @@ __global__ void __launch_bounds__(kThreads) k_up(const __grid_constant__ UpArgs 
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem + SM::up - 64);
   init_bars(bar);
   Pipe pp{};
-  stage_up<S>([&](int g, int& l) { l = g; return &a; }, up_items<S>(a), smem, bar, pp, blockIdx.x,
-              gridDim.x);
+  const int n = up_items<S>(a);
+  // reversed order: the items of the level the previous kernel wrote last are
+  // read first, while they are still in L2
+  stage_up<S>([&](int g, int& l) { l = a.reverse ? n - 1 - g : g; return &a; }, n, smem, bar, pp,
+              blockIdx.x, gridDim.x);
 }
 
 template <typename S>
@@ -1129,14 +1132,15 @@ __global__ void __launch_bounds__(kThreads, 3) k_down0(const __grid_constant__ D
                     gridDim.x);
 }
 
-template <typename S>
+// ADAPT: pixel-adaptive gain map (Down10Args::M0 and l1.M set).
+template <typename S, bool ADAPT>
 __global__ void __launch_bounds__(kThreads, 2) k_down10(const __grid_constant__ Down10Args a) {
   using SM = Smem<sizeof(typename Cplx<S>::T)>;
   extern __shared__ __align__(128) unsigned char smem[];
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem + SM::d10 - 64);
   init_bars(bar);
   Pipe pp{};
-  stage_down10<S>([&](int g, int& l) { l = g; return &a; }, combine_tiles(a.h0, a.w0, a.planes), smem, bar,
+  stage_down10<S, ADAPT>([&](int g, int& l) { l = g; return &a; }, combine_tiles(a.h0, a.w0, a.planes), smem, bar,
                   pp, blockIdx.x, gridDim.x);
 }
 
@@ -1334,16 +1338,18 @@ __global__ void __launch_bounds__(kThreads) k_luma_apply(const float* __restrict
 }
 #endif
 
-// Persistent grid: at most (resident CTAs per SM) x (SMs) CTAs.
-template <typename Kern>
-int persistent_grid(Kern kern, size_t smem, int items) {
+// Persistent grid: at most (resident CTAs per SM) x (SMs) CTAs.  The cache
+// (and the dynamic shared-memory attribute it sets) is per kernel function:
+// the kernel is the template argument, not just its type.
+template <auto Kern>
+int persistent_grid(size_t smem, int items) {
   static int cached = 0;
   if (cached == 0) {
     int dev = 0, sms = 0, per = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, kThreads, smem);
+    cudaFuncSetAttribute(Kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, Kern, kThreads, smem);
     cached = (per > 0 ? per : 1) * (sms > 0 ? sms : 1);
   }
   return items < cached ? items : cached;
@@ -1356,7 +1362,7 @@ using SMS = Smem<sizeof(CTS)>;
 
 cudaError_t FLLF_LAUNCH_NAME(up0)(const Up0Args& a, cudaStream_t s) {
   const int tiles = cdiv(a.dst.w, kUpTW) * cdiv(a.dst.h, kUpTH) * a.planes;
-  const int grid = persistent_grid(k_up0<FLLF_STORAGE>, SMS::up0, tiles);
+  const int grid = persistent_grid<k_up0<FLLF_STORAGE>>(SMS::up0, tiles);
   k_up0<FLLF_STORAGE><<<grid, kThreads, SMS::up0, s>>>(a);
   return cudaGetLastError();
 }
@@ -1364,29 +1370,34 @@ cudaError_t FLLF_LAUNCH_NAME(up0)(const Up0Args& a, cudaStream_t s) {
 cudaError_t FLLF_LAUNCH_NAME(up)(const UpArgs& a, cudaStream_t s) {
   const int items = cdiv(a.dst.w, kRsTW) * cdiv(a.dst.h, kRsTH) * a.planes *
                     (cdiv(a.K, SMS::up_kc) + (a.write_g ? 1 : 0));
-  const int grid = persistent_grid(k_up<FLLF_STORAGE>, SMS::up, items);
+  const int grid = persistent_grid<k_up<FLLF_STORAGE>>(SMS::up, items);
   k_up<FLLF_STORAGE><<<grid, kThreads, SMS::up, s>>>(a);
   return cudaGetLastError();
 }
 
 cudaError_t FLLF_LAUNCH_NAME(down)(const DownArgs& a, cudaStream_t s) {
   const int tiles = cdiv(a.fine.w + kDnX0, kDnOW) * cdiv(a.fine.h, kDnOH) * a.planes;
-  const int grid = persistent_grid(k_down<FLLF_STORAGE>, SMS::dn1, tiles);
+  const int grid = persistent_grid<k_down<FLLF_STORAGE>>(SMS::dn1, tiles);
   k_down<FLLF_STORAGE><<<grid, kThreads, SMS::dn1, s>>>(a);
   return cudaGetLastError();
 }
 
 cudaError_t FLLF_LAUNCH_NAME(down0)(const Down0Args& a, cudaStream_t s) {
   const int tiles = cdiv(a.w0 + kDnX0, kDnOW) * cdiv(a.h0, kDnOH) * a.planes;
-  const int grid = persistent_grid(k_down0<FLLF_STORAGE>, SMS::dn, tiles);
+  const int grid = persistent_grid<k_down0<FLLF_STORAGE>>(SMS::dn, tiles);
   k_down0<FLLF_STORAGE><<<grid, kThreads, SMS::dn, s>>>(a);
   return cudaGetLastError();
 }
 
 cudaError_t FLLF_LAUNCH_NAME(down10)(const Down10Args& a, cudaStream_t s) {
   const int tiles = cdiv(a.w0 + kDnX0, kDnOW) * cdiv(a.h0, kDnOH) * a.planes;
-  const int grid = persistent_grid(k_down10<FLLF_STORAGE>, SMS::d10, tiles);
-  k_down10<FLLF_STORAGE><<<grid, kThreads, SMS::d10, s>>>(a);
+  if (a.M0) {
+    const int grid = persistent_grid<k_down10<FLLF_STORAGE, true>>(SMS::d10, tiles);
+    k_down10<FLLF_STORAGE, true><<<grid, kThreads, SMS::d10, s>>>(a);
+  } else {
+    const int grid = persistent_grid<k_down10<FLLF_STORAGE, false>>(SMS::d10, tiles);
+    k_down10<FLLF_STORAGE, false><<<grid, kThreads, SMS::d10, s>>>(a);
+  }
   return cudaGetLastError();
 }
 
@@ -1431,25 +1442,25 @@ cudaError_t launch_map_reduce(const float* src, int sh, int sw, int spitch, floa
 // Batched launches: the grid covers every work item of the table.
 cudaError_t FLLF_LAUNCH_NAME(up0_batch)(const BatchTable<Up0Args>& tb, cudaStream_t s) {
   if (tb.total <= 0) return cudaSuccess;
-  const int grid = persistent_grid(k_up0_batch<FLLF_STORAGE>, SMS::up0, tb.total);
+  const int grid = persistent_grid<k_up0_batch<FLLF_STORAGE>>(SMS::up0, tb.total);
   k_up0_batch<FLLF_STORAGE><<<grid, kThreads, SMS::up0, s>>>(tb);
   return cudaGetLastError();
 }
 cudaError_t FLLF_LAUNCH_NAME(up_batch)(const BatchTable<UpArgs>& tb, cudaStream_t s) {
   if (tb.total <= 0) return cudaSuccess;
-  const int grid = persistent_grid(k_up_batch<FLLF_STORAGE>, SMS::up, tb.total);
+  const int grid = persistent_grid<k_up_batch<FLLF_STORAGE>>(SMS::up, tb.total);
   k_up_batch<FLLF_STORAGE><<<grid, kThreads, SMS::up, s>>>(tb);
   return cudaGetLastError();
 }
 cudaError_t FLLF_LAUNCH_NAME(down_batch)(const BatchTable<DownArgs>& tb, cudaStream_t s) {
   if (tb.total <= 0) return cudaSuccess;
-  const int grid = persistent_grid(k_down_batch<FLLF_STORAGE>, SMS::dn1, tb.total);
+  const int grid = persistent_grid<k_down_batch<FLLF_STORAGE>>(SMS::dn1, tb.total);
   k_down_batch<FLLF_STORAGE><<<grid, kThreads, SMS::dn1, s>>>(tb);
   return cudaGetLastError();
 }
 cudaError_t FLLF_LAUNCH_NAME(down0_batch)(const BatchTable<Down0Args>& tb, cudaStream_t s) {
   if (tb.total <= 0) return cudaSuccess;
-  const int grid = persistent_grid(k_down0_batch<FLLF_STORAGE>, SMS::dn, tb.total);
+  const int grid = persistent_grid<k_down0_batch<FLLF_STORAGE>>(SMS::dn, tb.total);
   k_down0_batch<FLLF_STORAGE><<<grid, kThreads, SMS::dn, s>>>(tb);
   return cudaGetLastError();
 }

@@ -260,7 +260,8 @@ cudaError_t enqueue_path(const fllf_params& p, const std::vector<Level>& lv, con
     return d;
   };
   for (int l = 1; l <= L - 2 && l < c0; ++l) {
-    const UpArgs u = up_args(l);
+    UpArgs u = up_args(l);
+    u.reverse = (l == 1) ? 1 : 0;   // the level-0 REDUCE wrote Z_1 first to last
     mark(FLLF_STAGE_UP, true);
     if ((e = launch_up(prec, u, s)) != cudaSuccess) return e;
     mark(FLLF_STAGE_UP, false);

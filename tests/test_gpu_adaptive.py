@@ -106,3 +106,26 @@ def test_adaptive_rejects_unit_gain_plan_and_null_map():
         assert e.value.status == pkg.FLLF_EINVAL
     finally:
         pkg.fllf_plan_destroy(plan)
+
+
+def test_adaptive_then_fixed_runs_in_one_process():
+    # both variants of the fused level-0/1 kernel launch after each other
+    # (each sets its own shared-memory limit)
+    img = synth_image(150, 220, 1, polygons=5, seed=4)
+    gain = variance_gain_map(img, 1.0, 3.0)
+    p = pkg.make_params(150, 220, 1, 6, 8, 3.0, 0.2, 2.0)
+    plan = pkg.fllf_plan_create(p, 0)
+    try:
+        x = torch.from_numpy(img).cuda()
+        g = torch.from_numpy(gain).cuda()
+        ya, yf = torch.empty_like(x), torch.empty_like(x)
+        s = torch.cuda.current_stream().cuda_stream
+        pkg.fllf_run_adaptive(plan, x.data_ptr(), g.data_ptr(), ya.data_ptr(), s)
+        pkg.fllf_run(plan, x.data_ptr(), yf.data_ptr(), s)
+        torch.cuda.synchronize()
+        a = np.array(o.coeffs_quadrature(3.0, 0.2, 2.0, 8))
+        ref = o.fourier_llf(img.astype(np.float64), 6, a, 2.0)
+        assert float(np.max(np.abs(yf.cpu().numpy() - ref))) <= FP32_TOL
+        assert float(np.max(np.abs(ya.cpu().numpy() - oracle_adaptive(img, gain, 6, 8, 0.2)))) <= FP32_TOL
+    finally:
+        pkg.fllf_plan_destroy(plan)
