@@ -294,10 +294,65 @@ enum {
  * kernel launch on the run's stream.  Adds no synchronisation. */
 fllf_status fllf_plan_enable_timing(fllf_plan *plan, int enable);
 
+/* Times only the stage kinds whose bit is set in `mask` (bit k = stage kind
+ * k; 0 disables timing), so that a measurement of one kernel adds no events
+ * around the others. */
+fllf_status fllf_plan_set_timing_mask(fllf_plan *plan, unsigned mask);
+
 /* Waits for the recorded events, then writes per stage kind the summed
  * kernel time in milliseconds (ms[FLLF_NSTAGE]) and the number of launches
  * (launches[FLLF_NSTAGE]) since the last call, and clears the record. */
 fllf_status fllf_plan_stage_times(fllf_plan *plan, double *ms, int *launches);
+
+/* ---- Launch tuning and the autotuner ---------------------------------------
+ * The kernels' tile shapes and orders per chunk are fixed at compile time
+ * (they set the TMA box geometry and the thread mappings).  What a plan can
+ * tune at run time is how the path is launched:
+ *   chain_pixels    levels >= 2 whose planes hold at most this many pixels
+ *                   (over all C planes) run in one chained cooperative launch
+ *                   with grid barriers between stages; 0 = no chained launch.
+ *                   Default 2^21.
+ *   ctas_per_sm[k]  resident CTAs per SM of the persistent grid of stage kind
+ *                   k (FLLF_STAGE_*); 0 = as many as fit (default).
+ *   reduce_reverse  1 (default): the level 1 -> 2 REDUCE visits its work
+ *                   items last to first, reading what the level-0 REDUCE
+ *                   wrote last while it is still in L2.
+ * Every setting computes the same output, bit for bit. */
+typedef struct {
+  long long chain_pixels;
+  int ctas_per_sm[FLLF_NSTAGE];
+  int reduce_reverse;
+} fllf_tuning;
+
+/* Reads / replaces a plan's launch tuning.  set: chain_pixels >= 0,
+ * ctas_per_sm 0..32, reduce_reverse 0 or 1; otherwise FLLF_EINVAL. */
+fllf_status fllf_plan_get_tuning(const fllf_plan *plan, fllf_tuning *out);
+fllf_status fllf_plan_set_tuning(fllf_plan *plan, const fllf_tuning *t);
+
+/* Autotuner: times the plan on d_in -> d_out (device buffers as for
+ * fllf_run; d_out is overwritten many times) with CUDA events on `stream`,
+ * `reps` timed runs per candidate after one untimed run, each timed run
+ * after an L2 flush (it allocates a buffer of twice the L2 size for the
+ * search and frees it; FLLF_ENOMEM if that fails).  It searches by
+ * coordinate descent, from the plan's current tuning, over the chain start
+ * (0, 2^15, 2^17, 2^19, 2^21, 2^23 pixels), the resident CTAs per SM of each
+ * stage kind (1 .. as many as fit) and the REDUCE order.  A candidate
+ * replaces the setting only if it is at least 1% faster.  The plan keeps
+ * the best setting; *best_ms (may be NULL) receives its time per run.
+ * Synchronises the stream.  reps 1..10000. */
+fllf_status fllf_plan_autotune(fllf_plan *plan, const float *d_in, float *d_out, int reps, void *stream,
+                               double *best_ms);
+
+/* Batches: resident CTAs per SM of the four batched stage kinds (level-0
+ * REDUCE, REDUCE, combine at levels >= 1, combine at level 0), 0 = as many
+ * as fit.  Changing them makes the next fllf_batch_run capture its CUDA
+ * graph again.  The batch autotuner times fllf_batch_run on the given
+ * buffers (as for fllf_batch_run; outputs overwritten) and keeps the best
+ * caps, with the same search and 1% rule as fllf_plan_autotune. */
+fllf_status fllf_batch_get_ctas(const fllf_batch *batch, int *ctas_per_sm /* [4] */);
+fllf_status fllf_batch_set_ctas(fllf_batch *batch, const int *ctas_per_sm /* [4] */);
+fllf_status fllf_batch_autotune(fllf_batch *batch, const float *const *d_in, float *const *d_out, int reps,
+                                void *stream, double *best_ms);
 
 #ifdef __cplusplus
 }

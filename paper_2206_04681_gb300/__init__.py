@@ -8,7 +8,10 @@ memory and streams.
 """
 
 from ._lib import (FllfError, fllf_params, make_params, lib, fllf_params_validate, fllf_coeffs,
-                   fllf_optimal_period, fllf_run_adaptive, fllf_run_luma,
+                   fllf_optimal_period, fllf_run_adaptive, fllf_run_luma, fllf_tuning,
+                   fllf_plan_get_tuning, fllf_plan_set_tuning, fllf_plan_autotune,
+                   fllf_plan_set_timing_mask,
+                   fllf_batch_get_ctas, fllf_batch_set_ctas, fllf_batch_autotune,
                    fllf_plan_scratch_bytes, fllf_plan_create, fllf_plan_destroy,
                    fllf_plan_params, fllf_plan_coeffs, fllf_run, fllf_run_host, fllf_submit,
                    fllf_poll, fllf_batch_create, fllf_batch_destroy, fllf_batch_run,

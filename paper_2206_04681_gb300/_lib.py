@@ -80,9 +80,27 @@ _SIGS = {
                                            ctypes.POINTER(ctypes.c_double)]),
     "fllf_run_adaptive": (ctypes.c_int, [_P, _P, _P, _P, _P]),
     "fllf_run_luma": (ctypes.c_int, [_P, _P, _P, _P]),
+    "fllf_plan_set_timing_mask": (ctypes.c_int, [_P, ctypes.c_uint]),
+    "fllf_plan_get_tuning": (ctypes.c_int, [_P, _P]),
+    "fllf_plan_set_tuning": (ctypes.c_int, [_P, _P]),
+    "fllf_plan_autotune": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, _P, ctypes.POINTER(ctypes.c_double)]),
+    "fllf_batch_get_ctas": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int)]),
+    "fllf_batch_set_ctas": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int)]),
+    "fllf_batch_autotune": (ctypes.c_int, [_P, ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.c_int, _P,
+                                           ctypes.POINTER(ctypes.c_double)]),
 }
 
 STAGES = ("up0", "up", "down", "down0", "chain")
+
+
+class fllf_tuning(ctypes.Structure):
+    _fields_ = [("chain_pixels", ctypes.c_longlong), ("ctas_per_sm", ctypes.c_int * 5),
+                ("reduce_reverse", ctypes.c_int)]
+
+    def as_dict(self):
+        return {"chain_pixels": int(self.chain_pixels),
+                "ctas_per_sm": {s: int(self.ctas_per_sm[i]) for i, s in enumerate(STAGES)},
+                "reduce_reverse": int(self.reduce_reverse)}
 
 _lib = None
 
@@ -144,6 +162,53 @@ def fllf_run_adaptive(plan, d_in, d_gain, d_out, stream=None):
 def fllf_run_luma(plan, d_rgb_in, d_rgb_out, stream=None):
     """Colour by luma: LLF on Y of BT.601 YUV, U and V kept (C == 1 plan)."""
     _check(lib().fllf_run_luma(plan, _P(d_rgb_in), _P(d_rgb_out), _P(stream or 0)))
+
+
+def fllf_plan_set_timing_mask(plan, stages):
+    """Time only the given stage kinds (names from STAGES); empty disables."""
+    mask = 0
+    for st in stages:
+        mask |= 1 << STAGES.index(st)
+    _check(lib().fllf_plan_set_timing_mask(plan, ctypes.c_uint(mask)))
+
+
+def fllf_plan_get_tuning(plan):
+    t = fllf_tuning()
+    _check(lib().fllf_plan_get_tuning(plan, ctypes.byref(t)))
+    return t
+
+
+def fllf_plan_set_tuning(plan, t):
+    _check(lib().fllf_plan_set_tuning(plan, ctypes.byref(t)))
+
+
+def fllf_plan_autotune(plan, d_in, d_out, reps=10, stream=None):
+    """Autotunes the plan's launch shape on the given device buffers; returns
+    (tuning, best ms per run)."""
+    ms = ctypes.c_double()
+    _check(lib().fllf_plan_autotune(plan, _P(d_in), _P(d_out), int(reps), _P(stream or 0), ctypes.byref(ms)))
+    return fllf_plan_get_tuning(plan), ms.value
+
+
+def fllf_batch_get_ctas(batch):
+    out = (ctypes.c_int * 4)()
+    _check(lib().fllf_batch_get_ctas(batch, out))
+    return list(out)
+
+
+def fllf_batch_set_ctas(batch, ctas):
+    arr = (ctypes.c_int * 4)(*ctas)
+    _check(lib().fllf_batch_set_ctas(batch, arr))
+
+
+def fllf_batch_autotune(batch, d_in, d_out, reps=5, stream=None):
+    """Autotunes the batch's per-stage CTA caps; returns (caps, best ms per run)."""
+    n = len(d_in)
+    ins = (_P * n)(*[_P(p) for p in d_in])
+    outs = (_P * n)(*[_P(p) for p in d_out])
+    ms = ctypes.c_double()
+    _check(lib().fllf_batch_autotune(batch, ins, outs, int(reps), _P(stream or 0), ctypes.byref(ms)))
+    return fllf_batch_get_ctas(batch), ms.value
 
 
 def fllf_optimal_period(sigma_r, K, R):

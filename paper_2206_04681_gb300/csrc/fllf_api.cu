@@ -423,7 +423,8 @@ fllf_status fllf_run(fllf_plan* plan, const float* d_in, float* d_out, void* str
   DeviceGuard guard(plan->device);
   if (!guard.ok) return fail(FLLF_ECUDA, "cudaSetDevice failed");
   cudaError_t e = enqueue_path(plan->p, plan->lv, plan->maps, plan->d_a, plan->d_fault, d_in, d_out,
-                               reinterpret_cast<cudaStream_t>(stream), plan->timer);
+                               reinterpret_cast<cudaStream_t>(stream), plan->timer, nullptr, 0.f,
+                               &plan->tune);
   if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
   return FLLF_OK;
 }
@@ -465,7 +466,7 @@ fllf_status fllf_run_adaptive(fllf_plan* plan, const float* d_in, const float* d
     lv[l].M = reinterpret_cast<const float*>(reinterpret_cast<unsigned char*>(plan->d_mpyr) + off[l]);
   cudaError_t e = enqueue_path(p, lv, plan->maps, plan->d_a, plan->d_fault, d_in, d_out,
                                reinterpret_cast<cudaStream_t>(stream), plan->timer, d_gain,
-                               (float)(1.0 / (p.m - 1.0)));
+                               (float)(1.0 / (p.m - 1.0)), &plan->tune);
   if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
   return FLLF_OK;
 }
@@ -495,8 +496,8 @@ fllf_status fllf_run_luma(fllf_plan* plan, const float* d_rgb_in, float* d_rgb_o
   static const float kLuma[3] = {0.299f, 0.587f, 0.114f};  // BT.601
   cudaError_t e;
   if ((e = launch_luma(d_rgb_in, y, (long long)n, kLuma, s)) != cudaSuccess) return cuda_fail(e, "luma");
-  if ((e = enqueue_path(p, plan->lv, plan->maps, plan->d_a, plan->d_fault, y, yf, s, plan->timer)) !=
-      cudaSuccess)
+  if ((e = enqueue_path(p, plan->lv, plan->maps, plan->d_a, plan->d_fault, y, yf, s, plan->timer,
+                        nullptr, 0.f, &plan->tune)) != cudaSuccess)
     return cuda_fail(e, "kernel launch");
   if ((e = launch_luma_apply(d_rgb_in, y, yf, d_rgb_out, (long long)n, s)) != cudaSuccess)
     return cuda_fail(e, "luma apply");
@@ -528,7 +529,7 @@ fllf_status fllf_run_host(fllf_plan* plan, const float* h_in, float* h_out, void
   if ((e = cudaMemcpyAsync(plan->d_io_in, h_in, bytes, cudaMemcpyHostToDevice, s)) != cudaSuccess)
     return cuda_fail(e, "host-to-device copy");
   if ((e = enqueue_path(plan->p, plan->lv, plan->maps, plan->d_a, plan->d_fault, plan->d_io_in,
-                        plan->d_io_out, s, plan->timer)) != cudaSuccess)
+                        plan->d_io_out, s, plan->timer, nullptr, 0.f, &plan->tune)) != cudaSuccess)
     return cuda_fail(e, "kernel launch");
   if ((e = cudaMemcpyAsync(h_out, plan->d_io_out, bytes, cudaMemcpyDeviceToHost, s)) != cudaSuccess)
     return cuda_fail(e, "device-to-host copy");
@@ -589,11 +590,20 @@ fllf_status fllf_plan_enable_timing(fllf_plan* plan, int enable) {
   DeviceGuard guard(plan->device);
   if (enable && !plan->timer) plan->timer = new (std::nothrow) StageTimer();
   if (enable && !plan->timer) return fail(FLLF_ENOMEM, "timer allocation failed");
+  if (enable) plan->timer->mask = 0xffffffffu;
   if (!enable) {
     delete plan->timer;
     plan->timer = nullptr;
   }
   return FLLF_OK;
+}
+
+fllf_status fllf_plan_set_timing_mask(fllf_plan* plan, unsigned mask) {
+  if (!plan) return fail(FLLF_EINVAL, "plan is NULL");
+  if (mask == 0) return fllf_plan_enable_timing(plan, 0);
+  const fllf_status st = fllf_plan_enable_timing(plan, 1);
+  if (st == FLLF_OK) plan->timer->mask = mask;
+  return st;
 }
 
 fllf_status fllf_plan_stage_times(fllf_plan* plan, double* ms, int* launches) {

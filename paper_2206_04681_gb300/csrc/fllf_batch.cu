@@ -33,28 +33,29 @@ size_t push(std::vector<unsigned char>& blob, const T* data, size_t n, size_t al
   return off;
 }
 
-cudaError_t launch_stage_at(const unsigned char* d_base, const StageRec& st, int prec, cudaStream_t s) {
+cudaError_t launch_stage_at(const unsigned char* d_base, const StageRec& st, int prec, cudaStream_t s,
+                            int cps) {
   const int* prefix = reinterpret_cast<const int*>(d_base + st.prefix_off);
   switch (st.kind) {
     case kStageUp0: {
       BatchTable<Up0Args> t{reinterpret_cast<const Up0Args*>(d_base + st.args_off), prefix, st.n, st.total};
-      return prec == FLLF_FP16 ? launch_up0_batch_f16(t, s)
-             : prec == FLLF_BF16 ? launch_up0_batch_bf16(t, s) : launch_up0_batch_f32(t, s);
+      return prec == FLLF_FP16 ? launch_up0_batch_f16(t, s, cps)
+             : prec == FLLF_BF16 ? launch_up0_batch_bf16(t, s, cps) : launch_up0_batch_f32(t, s, cps);
     }
     case kStageUp: {
       BatchTable<UpArgs> t{reinterpret_cast<const UpArgs*>(d_base + st.args_off), prefix, st.n, st.total};
-      return prec == FLLF_FP16 ? launch_up_batch_f16(t, s)
-             : prec == FLLF_BF16 ? launch_up_batch_bf16(t, s) : launch_up_batch_f32(t, s);
+      return prec == FLLF_FP16 ? launch_up_batch_f16(t, s, cps)
+             : prec == FLLF_BF16 ? launch_up_batch_bf16(t, s, cps) : launch_up_batch_f32(t, s, cps);
     }
     case kStageDown: {
       BatchTable<DownArgs> t{reinterpret_cast<const DownArgs*>(d_base + st.args_off), prefix, st.n, st.total};
-      return prec == FLLF_FP16 ? launch_down_batch_f16(t, s)
-             : prec == FLLF_BF16 ? launch_down_batch_bf16(t, s) : launch_down_batch_f32(t, s);
+      return prec == FLLF_FP16 ? launch_down_batch_f16(t, s, cps)
+             : prec == FLLF_BF16 ? launch_down_batch_bf16(t, s, cps) : launch_down_batch_f32(t, s, cps);
     }
     default: {
       BatchTable<Down0Args> t{reinterpret_cast<const Down0Args*>(d_base + st.args_off), prefix, st.n, st.total};
-      return prec == FLLF_FP16 ? launch_down0_batch_f16(t, s)
-             : prec == FLLF_BF16 ? launch_down0_batch_bf16(t, s) : launch_down0_batch_f32(t, s);
+      return prec == FLLF_FP16 ? launch_down0_batch_f16(t, s, cps)
+             : prec == FLLF_BF16 ? launch_down0_batch_bf16(t, s, cps) : launch_down0_batch_f32(t, s, cps);
     }
   }
 }
@@ -202,9 +203,9 @@ void set_blob_io(BatchBlob& bb, const float* const* d_in, float* const* d_out) {
 }
 
 cudaError_t launch_batch_stages(const std::vector<StageRec>& stages, const unsigned char* d_base,
-                                int prec, cudaStream_t s) {
+                                int prec, cudaStream_t s, const int* cps) {
   for (const StageRec& st : stages) {
-    const cudaError_t e = launch_stage_at(d_base, st, prec, s);
+    const cudaError_t e = launch_stage_at(d_base, st, prec, s, cps ? cps[st.kind] : 0);
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
@@ -247,6 +248,7 @@ struct fllf_batch {
   bool copied_pending = false;
   cudaStream_t cap = nullptr;
   cudaGraphExec_t graph = nullptr;
+  int cps[4] = {0, 0, 0, 0};       // resident-CTA cap per batched stage kind (0: as many as fit)
 };
 
 static void free_batch(fllf_batch* b) {
@@ -370,7 +372,7 @@ fllf_status fllf_batch_run(fllf_batch* b, const float* const* d_in, float* const
     cudaGraph_t g = nullptr;
     if ((e = cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeRelaxed)) != cudaSuccess)
       return bfail(FLLF_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e));
-    const cudaError_t le = launch_batch_stages(bb.stages, b->d_mem, b->precision, b->cap);
+    const cudaError_t le = launch_batch_stages(bb.stages, b->d_mem, b->precision, b->cap, b->cps);
     e = cudaStreamEndCapture(b->cap, &g);
     if (le != cudaSuccess || e != cudaSuccess) {
       if (g) cudaGraphDestroy(g);
@@ -387,6 +389,96 @@ fllf_status fllf_batch_run(fllf_batch* b, const float* const* d_in, float* const
   if ((e = cudaGraphLaunch(b->graph, s)) != cudaSuccess)
     return bfail(FLLF_ECUDA, std::string("graph launch: ") + cudaGetErrorString(e));
   return FLLF_OK;
+}
+
+fllf_status fllf_batch_get_ctas(const fllf_batch* b, int* ctas_per_sm) {
+  if (!b || !ctas_per_sm) return bfail(FLLF_EINVAL, "batch or ctas_per_sm is NULL");
+  std::copy(b->cps, b->cps + 4, ctas_per_sm);
+  return FLLF_OK;
+}
+
+fllf_status fllf_batch_set_ctas(fllf_batch* b, const int* ctas_per_sm) {
+  if (!b || !ctas_per_sm) return bfail(FLLF_EINVAL, "batch or ctas_per_sm is NULL");
+  for (int k = 0; k < 4; ++k)
+    if (ctas_per_sm[k] < 0 || ctas_per_sm[k] > 32) return bfail(FLLF_EINVAL, "ctas_per_sm must be 0..32");
+  if (!std::equal(ctas_per_sm, ctas_per_sm + 4, b->cps)) {
+    DeviceScope scope(b->device);
+    // the launch shapes are baked into the captured graph: capture again
+    if (b->graph) {
+      cudaStreamSynchronize(b->cap);
+      cudaGraphExecDestroy(b->graph);
+      b->graph = nullptr;
+    }
+    std::copy(ctas_per_sm, ctas_per_sm + 4, b->cps);
+  }
+  return FLLF_OK;
+}
+
+fllf_status fllf_batch_autotune(fllf_batch* b, const float* const* d_in, float* const* d_out, int reps,
+                                void* stream, double* best_ms) {
+  if (!b || !d_in || !d_out) return bfail(FLLF_EINVAL, "batch, d_in or d_out is NULL");
+  if (reps < 1 || reps > 10000) return bfail(FLLF_EINVAL, "reps must be 1..10000");
+  DeviceScope scope(b->device);
+  if (!scope.ok) return bfail(FLLF_ECUDA, "cudaSetDevice failed");
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    if (e0) cudaEventDestroy(e0);
+    return bfail(FLLF_ECUDA, "autotune: event creation failed");
+  }
+  // L2 flush before every timed run (twice the L2, allocated for the search)
+  int l2 = 0;
+  cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, b->device);
+  const size_t fbytes = 2 * (size_t)(l2 > 0 ? l2 : (64 << 20));
+  void* flush = nullptr;
+  if (cudaMalloc(&flush, fbytes) != cudaSuccess) {
+    cudaGetLastError();
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return bfail(FLLF_ENOMEM, "autotune: the L2 flush buffer could not be allocated");
+  }
+  // ms per batched run with the given caps (negative on failure)
+  auto measure = [&](const int* cps) -> double {
+    if (fllf_batch_set_ctas(b, cps) != FLLF_OK) return -1.0;
+    if (fllf_batch_run(b, d_in, d_out, stream) != FLLF_OK) return -1.0;  // captures the graph
+    double sum = 0.0;
+    for (int i = 0; i < reps; ++i) {
+      float t = 0.f;
+      if (cudaMemsetAsync(flush, i & 0xff, fbytes, s) != cudaSuccess || cudaEventRecord(e0, s) != cudaSuccess ||
+          fllf_batch_run(b, d_in, d_out, stream) != FLLF_OK || cudaEventRecord(e1, s) != cudaSuccess ||
+          cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&t, e0, e1) != cudaSuccess)
+        return -1.0;
+      sum += t;
+    }
+    return sum / reps;
+  };
+  int best[4];
+  std::copy(b->cps, b->cps + 4, best);
+  double best_t = measure(best);
+  bool ok = best_t >= 0;
+  for (int kind = 0; kind < 4 && ok; ++kind) {
+    const int occ = stage_occupancy(b->precision, kind, true);
+    for (int c = 1; c <= occ && ok; ++c) {
+      int t[4];
+      std::copy(best, best + 4, t);
+      t[kind] = c == occ ? 0 : c;
+      if (t[kind] == best[kind]) continue;
+      const double m = measure(t);
+      ok = m >= 0;
+      if (ok && m < 0.99 * best_t) {   // at least 1% faster
+        std::copy(t, t + 4, best);
+        best_t = m;
+      }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaStreamSynchronize(s);
+  cudaFree(flush);
+  const fllf_status st = fllf_batch_set_ctas(b, best);
+  if (!ok) return bfail(FLLF_ECUDA, "autotune: a timed batched run failed");
+  if (best_ms) *best_ms = best_t;
+  return st;
 }
 
 fllf_status fllf_batch_check(fllf_batch* b) {

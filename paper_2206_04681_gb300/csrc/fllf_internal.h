@@ -35,6 +35,7 @@ struct StageTimer : StageHook {
   std::vector<Pair> pending;
   cudaEvent_t open = nullptr;
   bool failed = false;
+  unsigned mask = 0xffffffffu;  // stage kinds to time (bit k = stage kind k)
   cudaEvent_t get() {
     if (!pool.empty()) {
       cudaEvent_t ev = pool.back();
@@ -46,6 +47,7 @@ struct StageTimer : StageHook {
     return ev;
   }
   void mark(int stage, bool begin, cudaStream_t s) override {
+    if (!((mask >> stage) & 1u)) return;
     cudaEvent_t ev = get();
     if (!ev) return;
     cudaEventRecord(ev, s);
@@ -82,6 +84,19 @@ struct PathMaps {
 // Encodes the maps for the level buffers in `lv` (device addresses).
 bool build_maps(const fllf_params& p, const std::vector<Level>& lv, PathMaps* m);
 
+// Launch tuning of a plan (the autotuner's knobs).  chain_px: levels >= 2
+// whose planes hold at most this many pixels in all run in the chained
+// launch (0: none); cps[kind]: resident-CTA cap per SM of the stage kind's
+// persistent grid (0: as many as fit); reverse: the level 1->2 REDUCE visits
+// its items last to first.
+struct Tuning {
+  long long chain_px = 1ll << 21;
+  int cps[5] = {0, 0, 0, 0, 0};
+  int reverse = 1;
+};
+// Resident CTAs per SM of a stage kind's kernel for a storage precision.
+int stage_occupancy(int prec, int kind, bool batched);
+
 // Enqueues the whole Fourier LLF path of one image on stream s.  `fault`
 // is a device word that kernels set when a bounded wait runs out.  With a
 // gain map d_gain (H x W, pitch W) the levels' M pointers must hold its
@@ -90,7 +105,7 @@ bool build_maps(const fllf_params& p, const std::vector<Level>& lv, PathMaps* m)
 cudaError_t enqueue_path(const fllf_params& p, const std::vector<Level>& lv, const PathMaps& maps,
                          const float* d_a, unsigned* fault, const float* d_in, float* d_out,
                          cudaStream_t s, StageHook* hook = nullptr, const float* d_gain = nullptr,
-                         float mscale = 0.f);
+                         float mscale = 0.f, const Tuning* tune = nullptr);
 
 // ---- batched argument tables (shared by batches and the server) ---------------
 enum BatchStageKind { kStageUp0 = 0, kStageUp = 1, kStageDown = 2, kStageDown0 = 3 };
@@ -114,7 +129,7 @@ void set_blob_fault(BatchBlob& bb, unsigned* d_fault);
 void set_blob_io(BatchBlob& bb, const float* const* d_in, float* const* d_out);
 // Enqueues the batched stage kernels reading the tables uploaded at d_base.
 cudaError_t launch_batch_stages(const std::vector<StageRec>& stages, const unsigned char* d_base,
-                                int prec, cudaStream_t s);
+                                int prec, cudaStream_t s, const int* cps = nullptr);
 
 }  // namespace fllf
 
@@ -135,4 +150,5 @@ struct fllf_plan {
   unsigned* d_fault = nullptr;        // device status block (fault word, grid-barrier words)
   float* d_mpyr = nullptr;            // gain-map pyramid of pixel-adaptive runs (first use)
   float* d_luma = nullptr;            // Y and filtered Y of colour-by-luma runs (first use)
+  fllf::Tuning tune;                  // launch tuning (fllf_plan_set_tuning / fllf_plan_autotune)
 };

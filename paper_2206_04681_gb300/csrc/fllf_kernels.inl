@@ -139,15 +139,16 @@ __device__ __forceinline__ bool stage_up0(Res res, int total, unsigned char* sme
     // inputs (columns 8s+2 .. 8s+12 of the staged row) are read as four 16-byte
     // words: rows are 72 floats apart, so scalar reads of consecutive rows
     // would hit the same 4 banks.
-    const int r = tid & 31, s = tid >> 5;
-    const bool item = r < kUpIR;
+    // Lane 31 repeats row 30 (kUpIR = 31 rows) into the unused staging row
+    // 31, which keeps the pass free of divergence.
+    const int r = tid & 31, s = tid >> 5, rl = min(r, kUpIR - 1);
     float2* hzw = hz + s * (kKC * kUpRun * kUpCS);  // [order][column][fine row]
     float* hgw = hg + s * (kUpRun * kUpCS);          // [column][fine row]
     float2 zc[kUpIPX], zp[kUpIPX], tc[kUpIPX];
-    if (item) {
+    {
       float v[kUpIPX];
       {
-        const float4* row = reinterpret_cast<const float4*>(it + r * kUpIW + 2 * kUpRun * s);
+        const float4* row = reinterpret_cast<const float4*>(it + rl * kUpIW + 2 * kUpRun * s);
         const float4 q0 = row[0], q1 = row[1], q2 = row[2], q3 = row[3];
         v[0] = q0.z; v[1] = q0.w;
         v[2] = q1.x; v[3] = q1.y; v[4] = q1.z; v[5] = q1.w;
@@ -173,8 +174,10 @@ __device__ __forceinline__ bool stage_up0(Res res, int total, unsigned char* sme
     // 16-byte bank groups.
     const int vq = tid & 3, vgrp = (tid >> 2) & 1, vkk = (tid >> 3) & 3;
     const int xo = X1 + kUpRun * s + vq;
+    // interior tile: every store of the vertical pass is in range (CTA-uniform)
+    const bool full = X1 + kUpTW <= a.dst.w && Y1 + kUpTH <= a.dst.h;
     for (int ch = 0; ch < nch; ++ch) {
-      if (item) {
+      {
 #pragma unroll
         for (int kk = 0; kk < kKC; ++kk) {
 #pragma unroll
@@ -192,11 +195,13 @@ __device__ __forceinline__ bool stage_up0(Res res, int total, unsigned char* sme
       __syncwarp();
       {
         const int k = ch * kKC + vkk;
-        if (k < a.K && xo < a.dst.w) {
+        // a full chunk of orders on an interior tile stores without guards
+        const bool uniform = full && (ch + 1) * kKC <= a.K;
+        if (uniform || (k < a.K && xo < a.dst.w)) {
           // order k is stored weighted by its coefficient: a_k Z_{1,k}
           const float sk = __ldg(a.a + k) * (1.f / 256.f);
           CT* Zk = reinterpret_cast<CT*>(a.dst.Z) + (long long)pl * a.dst.zplane +
-                   (long long)k * a.dst.zk + xo;
+                   (long long)k * a.dst.zk + xo + (long long)(Y1 + vgrp * kUpVRows) * a.dst.pitch;
           const float4* p =
               reinterpret_cast<const float4*>(hzw + (vkk * kUpRun + vq) * kUpCS + 2 * kUpVRows * vgrp);
           float2 w[2 * kUpVRows + 4];
@@ -206,11 +211,11 @@ __device__ __forceinline__ bool stage_up0(Res res, int total, unsigned char* sme
             w[2 * u] = make_float2(q4.x, q4.y);
             w[2 * u + 1] = make_float2(q4.z, q4.w);
           }
+          const int rows = uniform ? kUpVRows : min(kUpVRows, a.dst.h - (Y1 + vgrp * kUpVRows));
 #pragma unroll
           for (int j = 0; j < kUpVRows; ++j) {
-            const int y = Y1 + vgrp * kUpVRows + j;
-            if (y < a.dst.h)
-              Cplx<S>::st(Zk + (long long)y * a.dst.pitch,
+            if (j < rows)
+              Cplx<S>::st(Zk + j * a.dst.pitch,
                           mul2(splat(sk), tap5(w[2 * j], w[2 * j + 1], w[2 * j + 2], w[2 * j + 3], w[2 * j + 4])));
           }
         }
@@ -1338,21 +1343,32 @@ __global__ void __launch_bounds__(kThreads) k_luma_apply(const float* __restrict
 }
 #endif
 
-// Persistent grid: at most (resident CTAs per SM) x (SMs) CTAs.  The cache
-// (and the dynamic shared-memory attribute it sets) is per kernel function:
-// the kernel is the template argument, not just its type.
+// Persistent grid: at most (resident CTAs per SM) x (SMs) CTAs, or `cps`
+// CTAs per SM when 0 < cps < the resident count.  The cache (and the dynamic
+// shared-memory attribute it sets) is per kernel function: the kernel is the
+// template argument, not just its type.
 template <auto Kern>
-int persistent_grid(size_t smem, int items) {
-  static int cached = 0;
-  if (cached == 0) {
-    int dev = 0, sms = 0, per = 0;
+int resident_per_sm(size_t smem, int* sms_out) {
+  static int per = 0, sms = 0;
+  if (per == 0) {
+    int dev = 0, p = 0, n = 0;
     cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
     cudaFuncSetAttribute(Kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, Kern, kThreads, smem);
-    cached = (per > 0 ? per : 1) * (sms > 0 ? sms : 1);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&p, Kern, kThreads, smem);
+    sms = n > 0 ? n : 1;
+    per = p > 0 ? p : 1;
   }
-  return items < cached ? items : cached;
+  if (sms_out) *sms_out = sms;
+  return per;
+}
+template <auto Kern>
+int persistent_grid(size_t smem, int items, int cps = 0) {
+  int sms = 1;
+  int per = resident_per_sm<Kern>(smem, &sms);
+  if (cps > 0 && cps < per) per = cps;
+  const int grid = per * sms;
+  return items < grid ? items : grid;
 }
 
 }  // namespace
@@ -1360,63 +1376,76 @@ int persistent_grid(size_t smem, int items) {
 using CTS = typename Cplx<FLLF_STORAGE>::T;
 using SMS = Smem<sizeof(CTS)>;
 
-cudaError_t FLLF_LAUNCH_NAME(up0)(const Up0Args& a, cudaStream_t s) {
+cudaError_t FLLF_LAUNCH_NAME(up0)(const Up0Args& a, cudaStream_t s, int cps) {
   const int tiles = cdiv(a.dst.w, kUpTW) * cdiv(a.dst.h, kUpTH) * a.planes;
-  const int grid = persistent_grid<k_up0<FLLF_STORAGE>>(SMS::up0, tiles);
+  const int grid = persistent_grid<k_up0<FLLF_STORAGE>>(SMS::up0, tiles, cps);
   k_up0<FLLF_STORAGE><<<grid, kThreads, SMS::up0, s>>>(a);
   return cudaGetLastError();
 }
 
-cudaError_t FLLF_LAUNCH_NAME(up)(const UpArgs& a, cudaStream_t s) {
+cudaError_t FLLF_LAUNCH_NAME(up)(const UpArgs& a, cudaStream_t s, int cps) {
   const int items = cdiv(a.dst.w, kRsTW) * cdiv(a.dst.h, kRsTH) * a.planes *
                     (cdiv(a.K, SMS::up_kc) + (a.write_g ? 1 : 0));
-  const int grid = persistent_grid<k_up<FLLF_STORAGE>>(SMS::up, items);
+  const int grid = persistent_grid<k_up<FLLF_STORAGE>>(SMS::up, items, cps);
   k_up<FLLF_STORAGE><<<grid, kThreads, SMS::up, s>>>(a);
   return cudaGetLastError();
 }
 
-cudaError_t FLLF_LAUNCH_NAME(down)(const DownArgs& a, cudaStream_t s) {
+cudaError_t FLLF_LAUNCH_NAME(down)(const DownArgs& a, cudaStream_t s, int cps) {
   const int tiles = cdiv(a.fine.w + kDnX0, kDnOW) * cdiv(a.fine.h, kDnOH) * a.planes;
-  const int grid = persistent_grid<k_down<FLLF_STORAGE>>(SMS::dn1, tiles);
+  const int grid = persistent_grid<k_down<FLLF_STORAGE>>(SMS::dn1, tiles, cps);
   k_down<FLLF_STORAGE><<<grid, kThreads, SMS::dn1, s>>>(a);
   return cudaGetLastError();
 }
 
-cudaError_t FLLF_LAUNCH_NAME(down0)(const Down0Args& a, cudaStream_t s) {
+cudaError_t FLLF_LAUNCH_NAME(down0)(const Down0Args& a, cudaStream_t s, int cps) {
   const int tiles = cdiv(a.w0 + kDnX0, kDnOW) * cdiv(a.h0, kDnOH) * a.planes;
-  const int grid = persistent_grid<k_down0<FLLF_STORAGE>>(SMS::dn, tiles);
+  const int grid = persistent_grid<k_down0<FLLF_STORAGE>>(SMS::dn, tiles, cps);
   k_down0<FLLF_STORAGE><<<grid, kThreads, SMS::dn, s>>>(a);
   return cudaGetLastError();
 }
 
-cudaError_t FLLF_LAUNCH_NAME(down10)(const Down10Args& a, cudaStream_t s) {
+cudaError_t FLLF_LAUNCH_NAME(down10)(const Down10Args& a, cudaStream_t s, int cps) {
   const int tiles = cdiv(a.w0 + kDnX0, kDnOW) * cdiv(a.h0, kDnOH) * a.planes;
   if (a.M0) {
-    const int grid = persistent_grid<k_down10<FLLF_STORAGE, true>>(SMS::d10, tiles);
+    const int grid = persistent_grid<k_down10<FLLF_STORAGE, true>>(SMS::d10, tiles, cps);
     k_down10<FLLF_STORAGE, true><<<grid, kThreads, SMS::d10, s>>>(a);
   } else {
-    const int grid = persistent_grid<k_down10<FLLF_STORAGE, false>>(SMS::d10, tiles);
+    const int grid = persistent_grid<k_down10<FLLF_STORAGE, false>>(SMS::d10, tiles, cps);
     k_down10<FLLF_STORAGE, false><<<grid, kThreads, SMS::d10, s>>>(a);
   }
   return cudaGetLastError();
 }
 
-cudaError_t FLLF_LAUNCH_NAME(chain)(const ChainArgs& a, cudaStream_t s) {
+cudaError_t FLLF_LAUNCH_NAME(chain)(const ChainArgs& a, cudaStream_t s, int cps) {
   constexpr size_t kChainSmem = SMS::up > SMS::dn1 ? SMS::up : SMS::dn1;
-  static int grid = 0;
-  if (grid == 0) {
-    int dev = 0, sms = 0, per = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaFuncSetAttribute(k_chain<FLLF_STORAGE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)kChainSmem);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_chain<FLLF_STORAGE>, kThreads, kChainSmem);
-    grid = (per > 0 ? per : 1) * (sms > 0 ? sms : 1);
-  }
+  int sms = 1;
+  int per = resident_per_sm<k_chain<FLLF_STORAGE>>(kChainSmem, &sms);
+  if (cps > 0 && cps < per) per = cps;
+  const int grid = per * sms;   // cooperative: every CTA resident
   void* args[] = {const_cast<ChainArgs*>(&a)};
   cudaError_t e = cudaLaunchCooperativeKernel(reinterpret_cast<const void*>(k_chain<FLLF_STORAGE>),
                                               dim3(grid), dim3(kThreads), args, kChainSmem, s);
   return e != cudaSuccess ? e : cudaGetLastError();
+}
+
+// Resident CTAs per SM of a stage kind's kernel (kind: 0 up0, 1 up, 2 down,
+// 3 down0 -- the fused level-0/1 kernel for the per-image path --, 4 chain).
+int FLLF_LAUNCH_NAME(occupancy)(int kind, int batched) {
+  switch (kind) {
+    case 0: return batched ? resident_per_sm<k_up0_batch<FLLF_STORAGE>>(SMS::up0, nullptr)
+                           : resident_per_sm<k_up0<FLLF_STORAGE>>(SMS::up0, nullptr);
+    case 1: return batched ? resident_per_sm<k_up_batch<FLLF_STORAGE>>(SMS::up, nullptr)
+                           : resident_per_sm<k_up<FLLF_STORAGE>>(SMS::up, nullptr);
+    case 2: return batched ? resident_per_sm<k_down_batch<FLLF_STORAGE>>(SMS::dn1, nullptr)
+                           : resident_per_sm<k_down<FLLF_STORAGE>>(SMS::dn1, nullptr);
+    case 3: return batched ? resident_per_sm<k_down0_batch<FLLF_STORAGE>>(SMS::dn, nullptr)
+                           : resident_per_sm<k_down10<FLLF_STORAGE, false>>(SMS::d10, nullptr);
+    default: {
+      constexpr size_t kChainSmem = SMS::up > SMS::dn1 ? SMS::up : SMS::dn1;
+      return resident_per_sm<k_chain<FLLF_STORAGE>>(kChainSmem, nullptr);
+    }
+  }
 }
 
 #if FLLF_STORAGE_IS_F32
@@ -1440,27 +1469,27 @@ cudaError_t launch_map_reduce(const float* src, int sh, int sw, int spitch, floa
 #endif
 
 // Batched launches: the grid covers every work item of the table.
-cudaError_t FLLF_LAUNCH_NAME(up0_batch)(const BatchTable<Up0Args>& tb, cudaStream_t s) {
+cudaError_t FLLF_LAUNCH_NAME(up0_batch)(const BatchTable<Up0Args>& tb, cudaStream_t s, int cps) {
   if (tb.total <= 0) return cudaSuccess;
-  const int grid = persistent_grid<k_up0_batch<FLLF_STORAGE>>(SMS::up0, tb.total);
+  const int grid = persistent_grid<k_up0_batch<FLLF_STORAGE>>(SMS::up0, tb.total, cps);
   k_up0_batch<FLLF_STORAGE><<<grid, kThreads, SMS::up0, s>>>(tb);
   return cudaGetLastError();
 }
-cudaError_t FLLF_LAUNCH_NAME(up_batch)(const BatchTable<UpArgs>& tb, cudaStream_t s) {
+cudaError_t FLLF_LAUNCH_NAME(up_batch)(const BatchTable<UpArgs>& tb, cudaStream_t s, int cps) {
   if (tb.total <= 0) return cudaSuccess;
-  const int grid = persistent_grid<k_up_batch<FLLF_STORAGE>>(SMS::up, tb.total);
+  const int grid = persistent_grid<k_up_batch<FLLF_STORAGE>>(SMS::up, tb.total, cps);
   k_up_batch<FLLF_STORAGE><<<grid, kThreads, SMS::up, s>>>(tb);
   return cudaGetLastError();
 }
-cudaError_t FLLF_LAUNCH_NAME(down_batch)(const BatchTable<DownArgs>& tb, cudaStream_t s) {
+cudaError_t FLLF_LAUNCH_NAME(down_batch)(const BatchTable<DownArgs>& tb, cudaStream_t s, int cps) {
   if (tb.total <= 0) return cudaSuccess;
-  const int grid = persistent_grid<k_down_batch<FLLF_STORAGE>>(SMS::dn1, tb.total);
+  const int grid = persistent_grid<k_down_batch<FLLF_STORAGE>>(SMS::dn1, tb.total, cps);
   k_down_batch<FLLF_STORAGE><<<grid, kThreads, SMS::dn1, s>>>(tb);
   return cudaGetLastError();
 }
-cudaError_t FLLF_LAUNCH_NAME(down0_batch)(const BatchTable<Down0Args>& tb, cudaStream_t s) {
+cudaError_t FLLF_LAUNCH_NAME(down0_batch)(const BatchTable<Down0Args>& tb, cudaStream_t s, int cps) {
   if (tb.total <= 0) return cudaSuccess;
-  const int grid = persistent_grid<k_down0_batch<FLLF_STORAGE>>(SMS::dn, tb.total);
+  const int grid = persistent_grid<k_down0_batch<FLLF_STORAGE>>(SMS::dn, tb.total, cps);
   k_down0_batch<FLLF_STORAGE><<<grid, kThreads, SMS::dn, s>>>(tb);
   return cudaGetLastError();
 }

@@ -7,18 +7,21 @@
 
 namespace fllf {
 
-// One set of launchers per storage precision of the Fourier pyramids.
-#define FLLF_DECLARE_LAUNCHERS(suffix)                                    \
-  cudaError_t launch_up0_##suffix(const Up0Args& a, cudaStream_t s);     \
-  cudaError_t launch_up_##suffix(const UpArgs& a, cudaStream_t s);       \
-  cudaError_t launch_down_##suffix(const DownArgs& a, cudaStream_t s);   \
-  cudaError_t launch_down0_##suffix(const Down0Args& a, cudaStream_t s);   \
-  cudaError_t launch_down10_##suffix(const Down10Args& a, cudaStream_t s); \
-  cudaError_t launch_chain_##suffix(const ChainArgs& a, cudaStream_t s);                  \
-  cudaError_t launch_up0_batch_##suffix(const BatchTable<Up0Args>& t, cudaStream_t s);   \
-  cudaError_t launch_up_batch_##suffix(const BatchTable<UpArgs>& t, cudaStream_t s);     \
-  cudaError_t launch_down_batch_##suffix(const BatchTable<DownArgs>& t, cudaStream_t s); \
-  cudaError_t launch_down0_batch_##suffix(const BatchTable<Down0Args>& t, cudaStream_t s);
+// One set of launchers per storage precision of the Fourier pyramids.  `cps`
+// caps the persistent grid at that many resident CTAs per SM (0: as many as
+// fit); launch_occupancy_<suffix>(kind, batched) reports how many fit.
+#define FLLF_DECLARE_LAUNCHERS(suffix)                                                                   \
+  cudaError_t launch_up0_##suffix(const Up0Args& a, cudaStream_t s, int cps);                            \
+  cudaError_t launch_up_##suffix(const UpArgs& a, cudaStream_t s, int cps);                              \
+  cudaError_t launch_down_##suffix(const DownArgs& a, cudaStream_t s, int cps);                          \
+  cudaError_t launch_down0_##suffix(const Down0Args& a, cudaStream_t s, int cps);                        \
+  cudaError_t launch_down10_##suffix(const Down10Args& a, cudaStream_t s, int cps);                      \
+  cudaError_t launch_chain_##suffix(const ChainArgs& a, cudaStream_t s, int cps);                        \
+  cudaError_t launch_up0_batch_##suffix(const BatchTable<Up0Args>& t, cudaStream_t s, int cps);          \
+  cudaError_t launch_up_batch_##suffix(const BatchTable<UpArgs>& t, cudaStream_t s, int cps);            \
+  cudaError_t launch_down_batch_##suffix(const BatchTable<DownArgs>& t, cudaStream_t s, int cps);        \
+  cudaError_t launch_down0_batch_##suffix(const BatchTable<Down0Args>& t, cudaStream_t s, int cps);      \
+  int launch_occupancy_##suffix(int kind, int batched);
 // REDUCE of one float plane (the gain map of pixel-adaptive runs).
 cudaError_t launch_map_reduce(const float* src, int sh, int sw, int spitch, float* dst, int dh, int dw,
                               int dpitch, cudaStream_t s);

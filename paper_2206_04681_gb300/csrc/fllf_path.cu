@@ -62,50 +62,58 @@ bool encode3(CUtensorMap* m, CUtensorMapDataType dt, size_t esize, const void* b
              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-cudaError_t launch_up0(int prec, const Up0Args& a, cudaStream_t s) {
+cudaError_t launch_up0(int prec, const Up0Args& a, cudaStream_t s, int cps) {
   switch (prec) {
-    case FLLF_FP16: return launch_up0_f16(a, s);
-    case FLLF_BF16: return launch_up0_bf16(a, s);
-    default: return launch_up0_f32(a, s);
+    case FLLF_FP16: return launch_up0_f16(a, s, cps);
+    case FLLF_BF16: return launch_up0_bf16(a, s, cps);
+    default: return launch_up0_f32(a, s, cps);
   }
 }
-cudaError_t launch_up(int prec, const UpArgs& a, cudaStream_t s) {
+cudaError_t launch_up(int prec, const UpArgs& a, cudaStream_t s, int cps) {
   switch (prec) {
-    case FLLF_FP16: return launch_up_f16(a, s);
-    case FLLF_BF16: return launch_up_bf16(a, s);
-    default: return launch_up_f32(a, s);
+    case FLLF_FP16: return launch_up_f16(a, s, cps);
+    case FLLF_BF16: return launch_up_bf16(a, s, cps);
+    default: return launch_up_f32(a, s, cps);
   }
 }
-cudaError_t launch_down(int prec, const DownArgs& a, cudaStream_t s) {
+cudaError_t launch_down(int prec, const DownArgs& a, cudaStream_t s, int cps) {
   switch (prec) {
-    case FLLF_FP16: return launch_down_f16(a, s);
-    case FLLF_BF16: return launch_down_bf16(a, s);
-    default: return launch_down_f32(a, s);
+    case FLLF_FP16: return launch_down_f16(a, s, cps);
+    case FLLF_BF16: return launch_down_bf16(a, s, cps);
+    default: return launch_down_f32(a, s, cps);
   }
 }
-cudaError_t launch_chain(int prec, const ChainArgs& a, cudaStream_t s) {
+cudaError_t launch_chain(int prec, const ChainArgs& a, cudaStream_t s, int cps) {
   switch (prec) {
-    case FLLF_FP16: return launch_chain_f16(a, s);
-    case FLLF_BF16: return launch_chain_bf16(a, s);
-    default: return launch_chain_f32(a, s);
+    case FLLF_FP16: return launch_chain_f16(a, s, cps);
+    case FLLF_BF16: return launch_chain_bf16(a, s, cps);
+    default: return launch_chain_f32(a, s, cps);
   }
 }
-cudaError_t launch_down10(int prec, const Down10Args& a, cudaStream_t s) {
+cudaError_t launch_down10(int prec, const Down10Args& a, cudaStream_t s, int cps) {
   switch (prec) {
-    case FLLF_FP16: return launch_down10_f16(a, s);
-    case FLLF_BF16: return launch_down10_bf16(a, s);
-    default: return launch_down10_f32(a, s);
+    case FLLF_FP16: return launch_down10_f16(a, s, cps);
+    case FLLF_BF16: return launch_down10_bf16(a, s, cps);
+    default: return launch_down10_f32(a, s, cps);
   }
 }
-cudaError_t launch_down0(int prec, const Down0Args& a, cudaStream_t s) {
+cudaError_t launch_down0(int prec, const Down0Args& a, cudaStream_t s, int cps) {
   switch (prec) {
-    case FLLF_FP16: return launch_down0_f16(a, s);
-    case FLLF_BF16: return launch_down0_bf16(a, s);
-    default: return launch_down0_f32(a, s);
+    case FLLF_FP16: return launch_down0_f16(a, s, cps);
+    case FLLF_BF16: return launch_down0_bf16(a, s, cps);
+    default: return launch_down0_f32(a, s, cps);
   }
 }
 
 }  // namespace
+
+int stage_occupancy(int prec, int kind, bool batched) {
+  switch (prec) {
+    case FLLF_FP16: return launch_occupancy_f16(kind, batched ? 1 : 0);
+    case FLLF_BF16: return launch_occupancy_bf16(kind, batched ? 1 : 0);
+    default: return launch_occupancy_f32(kind, batched ? 1 : 0);
+  }
+}
 
 bool build_maps(const fllf_params& p, const std::vector<Level>& lv, PathMaps* m) {
   const int L = p.levels;
@@ -175,7 +183,15 @@ bool build_maps(const fllf_params& p, const std::vector<Level>& lv, PathMaps* m)
 
 cudaError_t enqueue_path(const fllf_params& p, const std::vector<Level>& lv, const PathMaps& maps,
                          const float* d_a, unsigned* fault, const float* d_in, float* d_out,
-                         cudaStream_t s, StageHook* hook, const float* d_gain, float mscale) {
+                         cudaStream_t s, StageHook* hook, const float* d_gain, float mscale,
+                         const Tuning* tune) {
+  static const Tuning kDefault = [] {
+    Tuning t;
+    const char* v = getenv("FLLF_CHAIN_PIXELS");  // override of the default chain threshold
+    if (v) t.chain_px = atoll(v);
+    return t;
+  }();
+  const Tuning& tn = tune ? *tune : kDefault;
   const int L = p.levels, C = p.C, prec = p.precision;
   const float turns = (float)(2.0 / p.T);
   if (L == 1) {
@@ -204,7 +220,7 @@ cudaError_t enqueue_path(const fllf_params& p, const std::vector<Level>& lv, con
                    ? 1
                    : 0;
   mark(FLLF_STAGE_UP0, true);
-  if ((e = launch_up0(prec, u0, s)) != cudaSuccess) return e;
+  if ((e = launch_up0(prec, u0, s, tn.cps[FLLF_STAGE_UP0])) != cudaSuccess) return e;
   mark(FLLF_STAGE_UP0, false);
   if (d_gain) {
     // Gaussian pyramid of the gain map, levels 1..L-2 (the levels that combine)
@@ -220,10 +236,7 @@ cudaError_t enqueue_path(const fllf_params& p, const std::vector<Level>& lv, con
   // Levels >= c0 run as one chained cooperative launch: from the first level
   // (>= 2) whose pixels over all planes fit in 2^21, the REDUCE stages up to
   // the top and the combines back down to c0.
-  static const long long chain_px = [] {
-    const char* v = getenv("FLLF_CHAIN_PIXELS");  // tuning override of the 2^21 threshold
-    return v ? atoll(v) : (1ll << 21);
-  }();
+  const long long chain_px = tn.chain_px;
   int c0 = L - 1;
   for (int l = 2; l <= L - 2; ++l)
     if ((long long)lv[l].h * lv[l].w * C <= chain_px) {
@@ -261,9 +274,9 @@ cudaError_t enqueue_path(const fllf_params& p, const std::vector<Level>& lv, con
   };
   for (int l = 1; l <= L - 2 && l < c0; ++l) {
     UpArgs u = up_args(l);
-    u.reverse = (l == 1) ? 1 : 0;   // the level-0 REDUCE wrote Z_1 first to last
+    u.reverse = (l == 1 && tn.reverse) ? 1 : 0;   // the level-0 REDUCE wrote Z_1 first to last
     mark(FLLF_STAGE_UP, true);
-    if ((e = launch_up(prec, u, s)) != cudaSuccess) return e;
+    if ((e = launch_up(prec, u, s, tn.cps[FLLF_STAGE_UP])) != cudaSuccess) return e;
     mark(FLLF_STAGE_UP, false);
   }
   if (c0 <= L - 2) {
@@ -273,7 +286,7 @@ cudaError_t enqueue_path(const fllf_params& p, const std::vector<Level>& lv, con
     ca.sync = fault + 32;
     ca.fault = fault;
     mark(FLLF_STAGE_CHAIN, true);
-    if ((e = launch_chain(prec, ca, s)) != cudaSuccess) return e;
+    if ((e = launch_chain(prec, ca, s, tn.cps[FLLF_STAGE_CHAIN])) != cudaSuccess) return e;
     mark(FLLF_STAGE_CHAIN, false);
   }
   // With levels >= 3 the level-1 combine runs inside the level-0 tiles.
@@ -281,7 +294,7 @@ cudaError_t enqueue_path(const fllf_params& p, const std::vector<Level>& lv, con
   for (int l = (c0 <= L - 2 ? c0 - 1 : L - 2); l >= down_lo; --l) {
     const DownArgs d = down_args(l);
     mark(FLLF_STAGE_DOWN, true);
-    if ((e = launch_down(prec, d, s)) != cudaSuccess) return e;
+    if ((e = launch_down(prec, d, s, tn.cps[FLLF_STAGE_DOWN])) != cudaSuccess) return e;
     mark(FLLF_STAGE_DOWN, false);
   }
   if (L >= 3) {
@@ -308,7 +321,7 @@ cudaError_t enqueue_path(const fllf_params& p, const std::vector<Level>& lv, con
                     : 0;
     d.fault = fault;
     mark(FLLF_STAGE_DOWN0, true);
-    if ((e = launch_down10(prec, d, s)) != cudaSuccess) return e;
+    if ((e = launch_down10(prec, d, s, tn.cps[FLLF_STAGE_DOWN0])) != cudaSuccess) return e;
     mark(FLLF_STAGE_DOWN0, false);
     return cudaSuccess;
   }
@@ -328,7 +341,7 @@ cudaError_t enqueue_path(const fllf_params& p, const std::vector<Level>& lv, con
   d0.mscale = mscale;
   d0.fault = fault;
   mark(FLLF_STAGE_DOWN0, true);
-  if ((e = launch_down0(prec, d0, s)) != cudaSuccess) return e;
+  if ((e = launch_down0(prec, d0, s, tn.cps[FLLF_STAGE_DOWN0])) != cudaSuccess) return e;
   mark(FLLF_STAGE_DOWN0, false);
   return cudaSuccess;
 }

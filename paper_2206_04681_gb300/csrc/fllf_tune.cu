@@ -1,0 +1,186 @@
+// fllf_tune.cu -- launch tuning of plans and batches, and the autotuner.
+//
+// The kernels' tile shapes and orders per chunk are compile-time constants:
+// they fix the TMA box geometry and the thread mappings.  What varies at
+// run time is how the work is launched, and the autotuner picks that by
+// timing the plan (or batch) on the caller's own images with CUDA events:
+//   * where the chained launch of the small levels starts (levels >= 2 whose
+//     planes hold at most chain_pixels pixels run in one cooperative launch
+//     with grid barriers; larger levels run one launch per stage);
+//   * the persistent grid of every stage kind: how many CTAs per SM are
+//     resident (fewer leaves each CTA more L2 and DRAM bandwidth, more
+//     hides latency);
+//   * the order in which the level 1 -> 2 REDUCE visits its work items
+//     (last to first reads what the level-0 REDUCE wrote last from L2).
+// Each timed run starts after an L2 flush (a write of twice the L2 size to a
+// buffer the tuner allocates for the search and frees after it).  The
+// search is coordinate descent from the current setting; a candidate
+// replaces it only when it is at least 1% faster, so timing noise does not
+// move the setting.  Every setting computes the same output, bit for bit.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <functional>
+#include <string>
+#include <vector>
+
+#include "fllf.h"
+#include "fllf_internal.h"
+
+using namespace fllf;
+
+namespace {
+
+fllf_status tfail(fllf_status s, const std::string& why) {
+  set_last_error(why);
+  return s;
+}
+
+struct Guard {
+  int prev = -1;
+  bool ok = false;
+  explicit Guard(int dev) {
+    cudaGetDevice(&prev);
+    ok = cudaSetDevice(dev) == cudaSuccess;
+  }
+  ~Guard() {
+    if (prev >= 0) cudaSetDevice(prev);
+  }
+};
+
+// Milliseconds per call of `run`: one untimed call, then `reps` calls each
+// timed on its own with events, right after a write of `flush_bytes` to
+// `flush` (twice the L2), so that every timed call starts with a cold L2 as
+// in steady use on frames larger than the cache; negative on a CUDA error.
+double time_calls(const std::function<cudaError_t()>& run, int reps, cudaStream_t s, void* flush,
+                  size_t flush_bytes) {
+  std::vector<cudaEvent_t> ev(2 * reps, nullptr);
+  bool ok = true;
+  for (auto& e : ev) ok = ok && cudaEventCreate(&e) == cudaSuccess;
+  ok = ok && run() == cudaSuccess;
+  for (int i = 0; i < reps && ok; ++i) {
+    if (flush) ok = cudaMemsetAsync(flush, i & 0xff, flush_bytes, s) == cudaSuccess;
+    ok = ok && cudaEventRecord(ev[2 * i], s) == cudaSuccess && run() == cudaSuccess &&
+         cudaEventRecord(ev[2 * i + 1], s) == cudaSuccess;
+  }
+  double ms = -1.0;
+  if (ok && cudaEventSynchronize(ev[2 * reps - 1]) == cudaSuccess) {
+    double sum = 0.0;
+    for (int i = 0; i < reps && ok; ++i) {
+      float t = 0.f;
+      ok = cudaEventElapsedTime(&t, ev[2 * i], ev[2 * i + 1]) == cudaSuccess;
+      sum += t;
+    }
+    if (ok) ms = sum / reps;
+  }
+  for (auto e : ev)
+    if (e) cudaEventDestroy(e);
+  return ms;
+}
+
+// A device buffer of twice the L2 size for the flushes (freed by the owner).
+size_t flush_size(int device) {
+  int l2 = 0;
+  cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, device);
+  return 2 * (size_t)(l2 > 0 ? l2 : (64 << 20));
+}
+
+constexpr double kGain = 0.99;  // a candidate must be >= 1% faster to be taken
+
+void to_public(const Tuning& t, fllf_tuning* o) {
+  o->chain_pixels = t.chain_px;
+  for (int k = 0; k < FLLF_NSTAGE; ++k) o->ctas_per_sm[k] = t.cps[k];
+  o->reduce_reverse = t.reverse;
+}
+
+}  // namespace
+
+extern "C" {
+
+fllf_status fllf_plan_get_tuning(const fllf_plan* plan, fllf_tuning* out) {
+  if (!plan || !out) return tfail(FLLF_EINVAL, "plan or out is NULL");
+  to_public(plan->tune, out);
+  return FLLF_OK;
+}
+
+fllf_status fllf_plan_set_tuning(fllf_plan* plan, const fllf_tuning* t) {
+  if (!plan || !t) return tfail(FLLF_EINVAL, "plan or tuning is NULL");
+  if (t->chain_pixels < 0) return tfail(FLLF_EINVAL, "chain_pixels must be >= 0");
+  for (int k = 0; k < FLLF_NSTAGE; ++k)
+    if (t->ctas_per_sm[k] < 0 || t->ctas_per_sm[k] > 32) return tfail(FLLF_EINVAL, "ctas_per_sm must be 0..32");
+  if (t->reduce_reverse != 0 && t->reduce_reverse != 1) return tfail(FLLF_EINVAL, "reduce_reverse must be 0 or 1");
+  plan->tune.chain_px = t->chain_pixels;
+  for (int k = 0; k < FLLF_NSTAGE; ++k) plan->tune.cps[k] = t->ctas_per_sm[k];
+  plan->tune.reverse = t->reduce_reverse;
+  return FLLF_OK;
+}
+
+fllf_status fllf_plan_autotune(fllf_plan* plan, const float* d_in, float* d_out, int reps, void* stream,
+                               double* best_ms) {
+  if (!plan || !d_in || !d_out) return tfail(FLLF_EINVAL, "plan, input or output is NULL");
+  if (reps < 1 || reps > 10000) return tfail(FLLF_EINVAL, "reps must be 1..10000");
+  Guard guard(plan->device);
+  if (!guard.ok) return tfail(FLLF_ECUDA, "cudaSetDevice failed");
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  const fllf_params& p = plan->p;
+  const size_t fbytes = flush_size(plan->device);
+  void* flush = nullptr;
+  if (cudaMalloc(&flush, fbytes) != cudaSuccess) {
+    cudaGetLastError();
+    return tfail(FLLF_ENOMEM, "autotune: the L2 flush buffer could not be allocated");
+  }
+  auto measure = [&](const Tuning& t) {
+    return time_calls(
+        [&] {
+          return enqueue_path(p, plan->lv, plan->maps, plan->d_a, plan->d_fault, d_in, d_out, s, nullptr,
+                              nullptr, 0.f, &t);
+        },
+        reps, s, flush, fbytes);
+  };
+  Tuning best = plan->tune;
+  double best_t = measure(best);
+  if (best_t < 0) {
+    cudaFree(flush);
+    return tfail(FLLF_ECUDA, "autotune: a timed run failed");
+  }
+  auto consider = [&](const Tuning& t) {
+    const double m = measure(t);
+    if (m < 0) return false;
+    if (m < kGain * best_t) {
+      best = t;
+      best_t = m;
+    }
+    return true;
+  };
+  bool ok = true;
+  // 1. where the chained launch of the small levels starts
+  for (long long px : {0ll, 1ll << 15, 1ll << 17, 1ll << 19, 1ll << 21, 1ll << 23}) {
+    Tuning t = best;
+    t.chain_px = px;
+    ok = ok && consider(t);
+  }
+  // 2. resident CTAs per SM of each stage kind
+  for (int kind = 0; kind < FLLF_NSTAGE && ok; ++kind) {
+    const int occ = stage_occupancy(p.precision, kind, false);
+    for (int c = 1; c <= occ && ok; ++c) {
+      Tuning t = best;
+      t.cps[kind] = c == occ ? 0 : c;
+      if (t.cps[kind] == best.cps[kind]) continue;
+      ok = consider(t);
+    }
+  }
+  // 3. visiting order of the level 1 -> 2 REDUCE
+  if (ok) {
+    Tuning t = best;
+    t.reverse = 1 - t.reverse;
+    ok = consider(t);
+  }
+  plan->tune = best;
+  cudaStreamSynchronize(s);
+  cudaFree(flush);
+  if (!ok) return tfail(FLLF_ECUDA, "autotune: a timed run failed");
+  if (best_ms) *best_ms = best_t;
+  return FLLF_OK;
+}
+
+}  // extern "C"
