@@ -208,13 +208,11 @@ static_assert((kDnOW / 4) * (kDnOH / 2) == kThreads, "combine thread mapping");
 // of the level-1 threads over the 34 x 18 used level-1 cells.
 constexpr int kD2W = 20, kD2H = 11;
 constexpr int kB1X = 17, kB1Y = 9;
-constexpr int kB1PerWarp = 20;            // level-1 blocks per warp (lanes 0..19)
 constexpr int kKC1 = 2;                   // orders per chunk of the level >= 1 combine
 constexpr int kD0IW = kDnOW + 4;          // staged level-0 input columns (from X0 - 2)
 static_assert(kB1X * kB1Y <= kThreads && 2 * kB1X == kDnCW - 2 && 2 * kB1Y == kDnCH,
               "level-1 blocks cover the used window");
 static_assert(kB1X + 2 < kD2W && kB1Y + 1 < kD2H, "level-1 blocks read inside the level-2 window");
-static_assert(kB1PerWarp * (kThreads / 32) >= kB1X * kB1Y && kB1PerWarp <= 32, "level-1 blocks over the warps");
 
 __host__ __device__ constexpr int cdiv(int a, int b) { return (a + b - 1) / b; }
 __host__ __device__ constexpr size_t align128(size_t x) { return (x + 127) & ~size_t(127); }

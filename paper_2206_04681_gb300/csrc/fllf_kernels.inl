@@ -872,9 +872,11 @@ __device__ __forceinline__ bool stage_down10(Res res, int total, unsigned char* 
   }
 
   const int tc = tid % (kDnOW / 4), tr = tid / (kDnOW / 4);
-  // level-1 blocks 20 w .. 20 w + 19 on lanes 0..19 of warp w
-  const int lane = tid & 31, b1 = (tid >> 5) * kB1PerWarp + lane;
-  const bool l1t = lane < kB1PerWarp && b1 < kB1X * kB1Y;
+  // level-1 blocks on threads 0..152 (warps 0-4 at full width): the other
+  // warps go straight to the level-0 combine, and their issue slots serve the
+  // SM's other CTA meanwhile
+  const int b1 = tid;
+  const bool l1t = tid < kB1X * kB1Y;
   const int bc = b1 % kB1X, br = b1 / kB1X;
   float2 we[4], wo[4], Pe[4], Po[4], base[4];
   float2 w1[2][2], P1[2][2];
