@@ -42,6 +42,15 @@ static_assert(kUpSlots <= 6, "barrier area: 64 bytes");
 __device__ __forceinline__ volatile int* abort_flag(uint64_t* bar) {
   return reinterpret_cast<volatile int*>(&bar[6]);
 }
+// Kernel entry: the CTA's barriers, then the launch dependency.  Every
+// kernel of the path is launched with programmatic stream serialization, so
+// its CTAs may be resident before the previous kernel of the stream has
+// finished: griddepcontrol.wait blocks until that kernel has completed and its
+// memory is visible, before any global access of this one (reads of what it
+// wrote and writes of what it read alike).  launch_dependents then lets the
+// next kernel's CTAs be scheduled (onto SMs this grid leaves free, and as its
+// CTAs exit), so their launch and set-up overlap this kernel.  Both are no-ops
+// in a kernel launched without the attribute.
 __device__ __forceinline__ void init_bars(uint64_t* bar) {
   if (threadIdx.x == 0) {
     for (int j = 0; j < kUpSlots; ++j) mbar_init(&bar[j], 1);
@@ -49,6 +58,8 @@ __device__ __forceinline__ void init_bars(uint64_t* bar) {
     fence_mbar_init();
   }
   __syncthreads();
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 }
 
 // Entry j of a prefix table holding item x (prefix[0] = 0, prefix[n] = total).
@@ -1373,6 +1384,23 @@ int persistent_grid(size_t smem, int items, int cps = 0) {
   return items < grid ? items : grid;
 }
 
+// Launch with programmatic stream serialization (the kernel enters through
+// init_bars, which waits for the previous kernel of the stream).
+template <typename... P, typename... A>
+cudaError_t launch_pdl(void (*kern)(P...), int grid, size_t smem, cudaStream_t s, A&&... args) {
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(kThreads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, static_cast<A&&>(args)...);
+}
+
 }  // namespace
 
 using CTS = typename Cplx<FLLF_STORAGE>::T;
@@ -1381,42 +1409,37 @@ using SMS = Smem<sizeof(CTS)>;
 cudaError_t FLLF_LAUNCH_NAME(up0)(const Up0Args& a, cudaStream_t s, int cps) {
   const int tiles = cdiv(a.dst.w, kUpTW) * cdiv(a.dst.h, kUpTH) * a.planes;
   const int grid = persistent_grid<k_up0<FLLF_STORAGE>>(SMS::up0, tiles, cps);
-  k_up0<FLLF_STORAGE><<<grid, kThreads, SMS::up0, s>>>(a);
-  return cudaGetLastError();
+  return launch_pdl(k_up0<FLLF_STORAGE>, grid, SMS::up0, s, a);
 }
 
 cudaError_t FLLF_LAUNCH_NAME(up)(const UpArgs& a, cudaStream_t s, int cps) {
   const int items = cdiv(a.dst.w, kRsTW) * cdiv(a.dst.h, kRsTH) * a.planes *
                     (cdiv(a.K, SMS::up_kc) + (a.write_g ? 1 : 0));
   const int grid = persistent_grid<k_up<FLLF_STORAGE>>(SMS::up, items, cps);
-  k_up<FLLF_STORAGE><<<grid, kThreads, SMS::up, s>>>(a);
-  return cudaGetLastError();
+  return launch_pdl(k_up<FLLF_STORAGE>, grid, SMS::up, s, a);
 }
 
 cudaError_t FLLF_LAUNCH_NAME(down)(const DownArgs& a, cudaStream_t s, int cps) {
   const int tiles = cdiv(a.fine.w + kDnX0, kDnOW) * cdiv(a.fine.h, kDnOH) * a.planes;
   const int grid = persistent_grid<k_down<FLLF_STORAGE>>(SMS::dn1, tiles, cps);
-  k_down<FLLF_STORAGE><<<grid, kThreads, SMS::dn1, s>>>(a);
-  return cudaGetLastError();
+  return launch_pdl(k_down<FLLF_STORAGE>, grid, SMS::dn1, s, a);
 }
 
 cudaError_t FLLF_LAUNCH_NAME(down0)(const Down0Args& a, cudaStream_t s, int cps) {
   const int tiles = cdiv(a.w0 + kDnX0, kDnOW) * cdiv(a.h0, kDnOH) * a.planes;
   const int grid = persistent_grid<k_down0<FLLF_STORAGE>>(SMS::dn, tiles, cps);
-  k_down0<FLLF_STORAGE><<<grid, kThreads, SMS::dn, s>>>(a);
-  return cudaGetLastError();
+  return launch_pdl(k_down0<FLLF_STORAGE>, grid, SMS::dn, s, a);
 }
 
 cudaError_t FLLF_LAUNCH_NAME(down10)(const Down10Args& a, cudaStream_t s, int cps) {
   const int tiles = cdiv(a.w0 + kDnX0, kDnOW) * cdiv(a.h0, kDnOH) * a.planes;
   if (a.M0) {
     const int grid = persistent_grid<k_down10<FLLF_STORAGE, true>>(SMS::d10, tiles, cps);
-    k_down10<FLLF_STORAGE, true><<<grid, kThreads, SMS::d10, s>>>(a);
+    return launch_pdl(k_down10<FLLF_STORAGE, true>, grid, SMS::d10, s, a);
   } else {
     const int grid = persistent_grid<k_down10<FLLF_STORAGE, false>>(SMS::d10, tiles, cps);
-    k_down10<FLLF_STORAGE, false><<<grid, kThreads, SMS::d10, s>>>(a);
+    return launch_pdl(k_down10<FLLF_STORAGE, false>, grid, SMS::d10, s, a);
   }
-  return cudaGetLastError();
 }
 
 cudaError_t FLLF_LAUNCH_NAME(chain)(const ChainArgs& a, cudaStream_t s, int cps) {
@@ -1474,26 +1497,22 @@ cudaError_t launch_map_reduce(const float* src, int sh, int sw, int spitch, floa
 cudaError_t FLLF_LAUNCH_NAME(up0_batch)(const BatchTable<Up0Args>& tb, cudaStream_t s, int cps) {
   if (tb.total <= 0) return cudaSuccess;
   const int grid = persistent_grid<k_up0_batch<FLLF_STORAGE>>(SMS::up0, tb.total, cps);
-  k_up0_batch<FLLF_STORAGE><<<grid, kThreads, SMS::up0, s>>>(tb);
-  return cudaGetLastError();
+  return launch_pdl(k_up0_batch<FLLF_STORAGE>, grid, SMS::up0, s, tb);
 }
 cudaError_t FLLF_LAUNCH_NAME(up_batch)(const BatchTable<UpArgs>& tb, cudaStream_t s, int cps) {
   if (tb.total <= 0) return cudaSuccess;
   const int grid = persistent_grid<k_up_batch<FLLF_STORAGE>>(SMS::up, tb.total, cps);
-  k_up_batch<FLLF_STORAGE><<<grid, kThreads, SMS::up, s>>>(tb);
-  return cudaGetLastError();
+  return launch_pdl(k_up_batch<FLLF_STORAGE>, grid, SMS::up, s, tb);
 }
 cudaError_t FLLF_LAUNCH_NAME(down_batch)(const BatchTable<DownArgs>& tb, cudaStream_t s, int cps) {
   if (tb.total <= 0) return cudaSuccess;
   const int grid = persistent_grid<k_down_batch<FLLF_STORAGE>>(SMS::dn1, tb.total, cps);
-  k_down_batch<FLLF_STORAGE><<<grid, kThreads, SMS::dn1, s>>>(tb);
-  return cudaGetLastError();
+  return launch_pdl(k_down_batch<FLLF_STORAGE>, grid, SMS::dn1, s, tb);
 }
 cudaError_t FLLF_LAUNCH_NAME(down0_batch)(const BatchTable<Down0Args>& tb, cudaStream_t s, int cps) {
   if (tb.total <= 0) return cudaSuccess;
   const int grid = persistent_grid<k_down0_batch<FLLF_STORAGE>>(SMS::dn, tb.total, cps);
-  k_down0_batch<FLLF_STORAGE><<<grid, kThreads, SMS::dn, s>>>(tb);
-  return cudaGetLastError();
+  return launch_pdl(k_down0_batch<FLLF_STORAGE>, grid, SMS::dn, s, tb);
 }
 
 }  // namespace fllf
