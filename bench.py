@@ -30,7 +30,7 @@ METRIC = "Mpixel/s Fourier LLF K=8 4K RGB at PSNR≥60dB vs FP64; serving p50/p9
 UNIT = "Mpixel/s"
 WORKLOAD = dict(H=2160, W=3840, C=3, polygons=40, seed=2, levels=8, K=8, m=3.0, sigma_r=0.2, T=2.0)
 N_FRAMES = 4          # distinct input/output frames cycled per step (4 x 99.5 MB > 129 MB L2)
-STAGES = ("up0", "up", "down", "down0", "chain")
+STAGES = ("up0", "up", "down", "down0", "chain", "down_s")
 
 
 def parse():
@@ -66,21 +66,23 @@ def level_sizes(H, W, L):
     return out
 
 
-CHAIN_PIXELS = 1 << 21   # levels whose pixels over all planes fit this run in the chained launch
+CHAIN_PIXELS = 1 << 21   # default: levels whose pixels over all planes fit this run chained
+SMALL_PIXELS = 1 << 19   # default: other combines at levels >= 2 this small run on 32 x 16 tiles
 
 
-def stage_split(cfg):
+def stage_split(cfg, chain_px=CHAIN_PIXELS, small_px=SMALL_PIXELS):
     """Which levels each stage kind covers, as the library launches them.
 
-    Returns (up_levels, chain_up, chain_down, down_levels, fused): REDUCE
-    l -> l+1 for l in up_levels / chain_up, level-l combines for l in
-    chain_down / down_levels, and whether the level-0 stage also runs the
-    level-1 combine (levels >= 3)."""
+    Returns (up_levels, chain_up, chain_down, down_levels, small_levels,
+    fused): REDUCE l -> l+1 for l in up_levels / chain_up, level-l combines
+    for l in chain_down / down_levels (64 x 32 tiles) / small_levels (32 x 16
+    tiles), and whether the level-0 stage also runs the level-1 combine
+    (levels >= 3)."""
     L, C = cfg["levels"], cfg["C"]
     sz = level_sizes(cfg["H"], cfg["W"], L)
     c0 = L - 1
     for l in range(2, L - 1):
-        if sz[l][0] * sz[l][1] * C <= CHAIN_PIXELS:
+        if sz[l][0] * sz[l][1] * C <= chain_px:
             c0 = l
             break
     c0 = max(c0, L - 1 - 12)
@@ -89,11 +91,13 @@ def stage_split(cfg):
     chain_down = list(range(L - 2, c0 - 1, -1)) if c0 <= L - 2 else []
     fused = L >= 3
     hi = c0 - 1 if c0 <= L - 2 else L - 2
-    down_levels = list(range(hi, (2 if fused else 1) - 1, -1))
-    return up_levels, chain_up, chain_down, down_levels, fused
+    down_all = list(range(hi, (2 if fused else 1) - 1, -1))
+    small_levels = [l for l in down_all if l >= 2 and sz[l][0] * sz[l][1] * C <= small_px]
+    down_levels = [l for l in down_all if l not in small_levels]
+    return up_levels, chain_up, chain_down, down_levels, small_levels, fused
 
 
-def stage_work(cfg, zbytes):
+def stage_work(cfg, zbytes, chain_px=CHAIN_PIXELS, small_px=SMALL_PIXELS):
     """Algorithmic FP32 ops and bytes per stage kind for one frame (all planes).
 
     Ops (FMA = 1; the method's separable stencil count with Horner's rule
@@ -114,7 +118,7 @@ def stage_work(cfg, zbytes):
     sz = level_sizes(cfg["H"], cfg["W"], L)
     n = [h * w for h, w in sz]
     trig = 16
-    up_levels, chain_up, chain_down, down_levels, fused = stage_split(cfg)
+    up_levels, chain_up, chain_down, down_levels, small_levels, fused = stage_split(cfg, chain_px, small_px)
     ops = dict.fromkeys(STAGES, 0.0)
     byt = dict.fromkeys(STAGES, 0.0)
 
@@ -147,6 +151,10 @@ def stage_work(cfg, zbytes):
         o, b = combine_work(l)
         ops["down"] += o
         byt["down"] += b
+    for l in small_levels:
+        o, b = combine_work(l)
+        ops["down_s"] += o
+        byt["down_s"] += b
     if L >= 2:
         e1 = 1 if L >= 3 else 0
         ops["down0"] = n[0] * (trig + 10 * K + 4 * e1)
@@ -400,10 +408,11 @@ def run_ours(args):
         t = torch.tensor([e2e_s], device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         e2e_s = float(t.item())
+    tn = pkg.fllf_plan_get_tuning(plan)
     pkg.fllf_plan_destroy(plan)
 
     zbytes = 8 if args.precision == "fp32" else 4
-    ops, byt = stage_work(cfg, zbytes)
+    ops, byt = stage_work(cfg, zbytes, tn.chain_pixels, tn.small_pixels)
     dom_ms, dom_launches = stage[dom]                  # timed region, dominant kernel only
     per_launch_s = dom_ms / max(dom_launches, 1) * 1e-3
     launches_per_step = {s: pre[s][1] / pre_steps for s in STAGES}

@@ -287,7 +287,8 @@ enum {
   FLLF_STAGE_DOWN = 2,  /* level l >= 1: Eq. (14) product-sum fused with the collapse */
   FLLF_STAGE_DOWN0 = 3, /* level 0: Eq. (14) l = 0 case + final collapse, writes O */
   FLLF_STAGE_CHAIN = 4, /* the small levels (REDUCE up, then combines down) in one launch */
-  FLLF_NSTAGE = 5
+  FLLF_STAGE_DOWN_S = 5, /* level l >= 2 below small_pixels: FLLF_STAGE_DOWN on 32 x 16 tiles */
+  FLLF_NSTAGE = 6
 };
 
 /* When enabled, every run of the plan records CUDA events around each
@@ -317,15 +318,24 @@ fllf_status fllf_plan_stage_times(fllf_plan *plan, double *ms, int *launches);
  *   reduce_reverse  1 (default): the level 1 -> 2 REDUCE visits its work
  *                   items last to first, reading what the level-0 REDUCE
  *                   wrote last while it is still in L2.
+ *   small_pixels    combines at levels >= 2 (outside the chained launch)
+ *                   whose planes hold at most this many pixels run on
+ *                   32 x 16 tiles with two pixels per thread
+ *                   (FLLF_STAGE_DOWN_S) instead of 64 x 32 tiles with eight:
+ *                   four times the tiles and a quarter of each thread's
+ *                   serial work, for levels too small to fill the GPU.
+ *                   Default 2^19; 0 = never.
  * Every setting computes the same output, bit for bit. */
 typedef struct {
   long long chain_pixels;
   int ctas_per_sm[FLLF_NSTAGE];
   int reduce_reverse;
+  long long small_pixels;
 } fllf_tuning;
 
 /* Reads / replaces a plan's launch tuning.  set: chain_pixels >= 0,
- * ctas_per_sm 0..32, reduce_reverse 0 or 1; otherwise FLLF_EINVAL. */
+ * small_pixels >= 0, ctas_per_sm 0..32, reduce_reverse 0 or 1; otherwise
+ * FLLF_EINVAL. */
 fllf_status fllf_plan_get_tuning(const fllf_plan *plan, fllf_tuning *out);
 fllf_status fllf_plan_set_tuning(fllf_plan *plan, const fllf_tuning *t);
 
@@ -335,8 +345,9 @@ fllf_status fllf_plan_set_tuning(fllf_plan *plan, const fllf_tuning *t);
  * after an L2 flush (it allocates a buffer of twice the L2 size for the
  * search and frees it; FLLF_ENOMEM if that fails).  It searches by
  * coordinate descent, from the plan's current tuning, over the chain start
- * (0, 2^15, 2^17, 2^19, 2^21, 2^23 pixels), the resident CTAs per SM of each
- * stage kind (1 .. as many as fit) and the REDUCE order.  A candidate
+ * (0, 2^15, 2^17, 2^19, 2^21, 2^23 pixels), the small-tile threshold (0 or
+ * the pixel count of a combined level >= 2), the resident CTAs per SM of
+ * each stage kind (1 .. as many as fit) and the REDUCE order.  A candidate
  * replaces the setting only if it is at least 1% faster.  The plan keeps
  * the best setting; *best_ms (may be NULL) receives its time per run.
  * Synchronises the stream.  reps 1..10000. */

@@ -90,15 +90,15 @@ _SIGS = {
                                            ctypes.POINTER(ctypes.c_double)]),
 }
 
-STAGES = ("up0", "up", "down", "down0", "chain")
+STAGES = ("up0", "up", "down", "down0", "chain", "down_s")
 
 
 class fllf_tuning(ctypes.Structure):
-    _fields_ = [("chain_pixels", ctypes.c_longlong), ("ctas_per_sm", ctypes.c_int * 5),
-                ("reduce_reverse", ctypes.c_int)]
+    _fields_ = [("chain_pixels", ctypes.c_longlong), ("ctas_per_sm", ctypes.c_int * len(STAGES)),
+                ("reduce_reverse", ctypes.c_int), ("small_pixels", ctypes.c_longlong)]
 
     def as_dict(self):
-        return {"chain_pixels": int(self.chain_pixels),
+        return {"chain_pixels": int(self.chain_pixels), "small_pixels": int(self.small_pixels),
                 "ctas_per_sm": {s: int(self.ctas_per_sm[i]) for i, s in enumerate(STAGES)},
                 "reduce_reverse": int(self.reduce_reverse)}
 

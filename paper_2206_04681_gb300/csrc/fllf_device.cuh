@@ -94,6 +94,9 @@ struct UpArgs {
   unsigned* fault;
 };
 
+// The boxes are those of the 64 x 32 combine (k_down), or of the 32 x 16
+// small-level combine (k_down_s: 20 x 10 x kKCS, 20 x 10, 36 x 16 x kKCS and
+// 36 x 16).
 struct DownArgs {
   CUtensorMap zmap;     // coarse Z_{l+1}: 36 x 18 x kKC1 window
   CUtensorMap emap;     // coarse E_{l+1}: 36 x 18 window
@@ -214,6 +217,18 @@ static_assert(kB1X * kB1Y <= kThreads && 2 * kB1X == kDnCW - 2 && 2 * kB1Y == kD
               "level-1 blocks cover the used window");
 static_assert(kB1X + 2 < kD2W && kB1Y + 1 < kD2H, "level-1 blocks read inside the level-2 window");
 
+// combine at the small levels (>= 1): 32 x 16 fine outputs per tile and one
+// fine column by two rows per thread (more tiles and a quarter of the work
+// per thread of the 64 x 32 combine, for levels too small to fill the GPU
+// with those).  Tile origin 32*tx-6, so the coarse window starts at 16*tx-4
+// (16-byte aligned for both element sizes).
+constexpr int kSmW = 32, kSmH = 16;
+constexpr int kSmIW = kSmW + 4;           // staged fine columns (from X0 - 2)
+constexpr int kSmCW = 20;                 // staged coarse columns (18 used)
+constexpr int kSmCH = kSmH / 2 + 2;       // staged coarse rows (10)
+constexpr int kKCS = 4;                   // orders per chunk of the small combine
+static_assert(kSmW * (kSmH / 2) == kThreads, "small combine thread mapping");
+
 __host__ __device__ constexpr int cdiv(int a, int b) { return (a + b - 1) / b; }
 __host__ __device__ constexpr size_t align128(size_t x) { return (x + 127) & ~size_t(127); }
 
@@ -245,6 +260,13 @@ struct Smem {
   static constexpr size_t dn1_g = align128(sizeof(float) * kDnOH * kD0IW);
   static constexpr size_t dn1_buf = dn1_zf + dn1_zc + dn1_e + dn1_g;
   static constexpr size_t dn1 = 2 * dn1_buf + 64;
+  // small-level combine: the same four boxes on 32 x 16 tiles
+  static constexpr size_t sm_zf = align128((size_t)ESZ * kKCS * kSmH * kSmIW);
+  static constexpr size_t sm_zc = align128((size_t)ESZ * kKCS * kSmCH * kSmCW);
+  static constexpr size_t sm_e = align128(sizeof(float) * kSmCH * kSmCW);
+  static constexpr size_t sm_g = align128(sizeof(float) * kSmH * kSmIW);
+  static constexpr size_t sm_buf = sm_zf + sm_zc + sm_e + sm_g;
+  static constexpr size_t dns = 2 * sm_buf + 64;
   // fused level-1/level-0 combine
   static constexpr size_t d10_z1 = dn_z;
   static constexpr size_t d10_z2 = align128((size_t)ESZ * kKC * kD2H * kD2W);

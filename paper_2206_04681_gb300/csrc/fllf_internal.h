@@ -76,6 +76,11 @@ struct PathMaps {
   std::vector<CUtensorMap> z_dn1; // Z_l read as the coarse level of a level >= 1 combine (kKC1 orders)
   std::vector<CUtensorMap> z_fn;  // Z_l read as the fine level of a combine (kKC1 orders)
   std::vector<CUtensorMap> g_fn;  // G_l read as the fine level of a combine
+  // the same four roles on the 32 x 16 tiles of the small-level combine (kKCS orders)
+  std::vector<CUtensorMap> z_cs;  // Z_l as the coarse level (20 x 10 window)
+  std::vector<CUtensorMap> e_cs;  // E_l as the coarse level (20 x 10 window)
+  std::vector<CUtensorMap> z_fs;  // Z_l as the fine level (36 x 16 box)
+  std::vector<CUtensorMap> g_fs;  // G_l as the fine level (36 x 16 box)
   // fused level-1/level-0 combine (levels >= 3)
   CUtensorMap g1_d10{};           // G_1 on the level-1 window
   CUtensorMap z2_d10{};           // Z_2 on the level-2 window
@@ -86,12 +91,14 @@ bool build_maps(const fllf_params& p, const std::vector<Level>& lv, PathMaps* m)
 
 // Launch tuning of a plan (the autotuner's knobs).  chain_px: levels >= 2
 // whose planes hold at most this many pixels in all run in the chained
-// launch (0: none); cps[kind]: resident-CTA cap per SM of the stage kind's
-// persistent grid (0: as many as fit); reverse: the level 1->2 REDUCE visits
-// its items last to first.
+// launch (0: none); small_px: the other combines at levels >= 2 with at most
+// this many pixels run on the 32 x 16 tiles (0: none); cps[kind]:
+// resident-CTA cap per SM of the stage kind's persistent grid (0: as many as
+// fit); reverse: the level 1->2 REDUCE visits its items last to first.
 struct Tuning {
   long long chain_px = 1ll << 21;
-  int cps[5] = {0, 0, 0, 0, 0};
+  long long small_px = 1ll << 19;
+  int cps[FLLF_NSTAGE] = {0, 0, 0, 0, 0, 0};
   int reverse = 1;
 };
 // Resident CTAs per SM of a stage kind's kernel for a storage precision.

@@ -826,6 +826,166 @@ __device__ __forceinline__ bool stage_combine1(Res res, int total, unsigned char
 }
 
 // ---------------------------------------------------------------------------------------
+// Combine at a small level l >= 1 (Eq. (14), l >= 1 case), on 32 x 16 tiles.
+// Item = tile; its orders are staged kKCS at a time (highest chunk first, in a
+// ring of two slots) and every thread runs the whole descending Horner sum
+// for its two fine pixels (column X0 + tc, rows Y0 + 2 tr and + 1).  Each
+// arithmetic step is the one the 64 x 32 combine takes for the same pixel, in
+// the same order (EXPAND: vertical sums per coarse column, then the
+// horizontal 1-6-1 or 1-1 sum; D = f - s u; Horner; Im(P w); base + delta),
+// so both give the same bits and a level may run on either.  The horizontal
+// sum is written once for both column parities: u = a v1 + (b v0 + v2) with
+// (a, b) = (6, 1) for an even column and (1, 0) for an odd one, whose
+// v1 + (0 v0 + v2) rounds exactly as v1 + v2.
+template <typename S, typename Res>
+__device__ __forceinline__ bool stage_combine_s(Res res, int total, unsigned char* smem, uint64_t* bar,
+                                                Pipe& pp, int b, int G) {
+  using CT = typename Cplx<S>::T;
+  using SM = Smem<sizeof(CT)>;
+  constexpr size_t kOffC = SM::sm_zf, kOffE = kOffC + SM::sm_zc, kOffG = kOffE + SM::sm_e;
+  auto bufp = [&](int buf) { return smem + buf * SM::sm_buf; };
+  volatile int* abortp = abort_flag(bar);
+  const int tid = threadIdx.x;
+  if (b >= total) return true;
+  auto issue = [&](const DownArgs& a, int lt, int ch, bool first, int buf) {
+    const TileXY g = tile_of(lt, cdiv(a.fine.w + kDnX0, kSmW), cdiv(a.fine.h, kSmH));
+    const int X0 = g.tx * kSmW - kDnX0, Y0 = g.ty * kSmH;
+    const int cx0 = X0 / 2 - 1, cy0 = Y0 / 2 - 1;
+    const bool e = first && a.has_e;
+    uint32_t bytes = (uint32_t)(sizeof(CT) * kKCS * (kSmH * kSmIW + kSmCH * kSmCW));
+    if (first) bytes += (uint32_t)(sizeof(float) * kSmH * kSmIW);
+    if (e) bytes += (uint32_t)(sizeof(float) * kSmCH * kSmCW);
+    mbar_expect_tx(&bar[buf], bytes);
+    unsigned char* p = bufp(buf);
+    // x = X0 - 2 = 32 tx - 8 and cx0 = 16 tx - 4: 16-byte aligned for every element size
+    tma_load4(p, &a.zfmap, X0 - 2, Y0, ch * kKCS, g.pl, &bar[buf]);
+    tma_load4(p + kOffC, &a.zmap, cx0, cy0, ch * kKCS, g.pl, &bar[buf]);
+    if (first) tma_load3(p + kOffG, &a.gfmap, X0 - 2, Y0, g.pl, &bar[buf]);
+    if (e) tma_load3(p + kOffE, &a.emap, cx0, cy0, g.pl, &bar[buf]);
+  };
+  int t = b, lt = 0;
+  const DownArgs* a = res(t, lt);
+  int nch = cdiv(a->K, kKCS), ch = nch - 1;
+  if (tid == 0) {
+    fence_proxy_async();
+    issue(*a, lt, ch, true, 0);
+  }
+
+  // X0 is even, so the column's parity is that of tc; its EXPAND reads the
+  // staged coarse columns c0 .. c0 + 2 (an odd column uses the last two) and
+  // rows tr .. tr + 2 (the odd row uses the last two).
+  const int tc = tid % kSmW, tr = tid / kSmW, odd = tc & 1, c0 = tc >> 1;
+  const float2 ha = splat(odd ? 1.f : 6.f), hb = splat(odd ? 0.f : 1.f);
+  const float2 sc = expand_scale_pair(odd);
+  float2 we = splat(0.f), wo = splat(0.f), Pe = splat(0.f), Po = splat(0.f), base = splat(0.f);
+  int fy = 0, fx = 0, pl = 0, X0 = 0, Y0 = 0;
+  for (int i = 0;; ++i) {
+    const int buf = i & 1;
+    const bool first = ch == nch - 1, last = ch == 0;
+    const int h = a->fine.h, w = a->fine.w;
+    if (first) {
+      const TileXY g = tile_of(lt, cdiv(w + kDnX0, kSmW), cdiv(h, kSmH));
+      pl = g.pl;
+      X0 = g.tx * kSmW - kDnX0;
+      Y0 = g.ty * kSmH;
+      fy = Y0 + 2 * tr;
+      fx = X0 + tc;
+    }
+    const int cx0 = X0 / 2 - 1, cy0 = Y0 / 2 - 1;
+    const bool has_next = !last || t + G < total;
+    if (tid == 0 && has_next) {
+      fence_proxy_async();
+      if (!last) {
+        issue(*a, lt, ch - 1, false, buf ^ 1);
+      } else {
+        int ln;
+        const DownArgs* an = res(t + G, ln);
+        issue(*an, ln, cdiv(an->K, kKCS) - 1, true, buf ^ 1);
+      }
+    }
+    mbar_wait_thread(&bar[buf], pp.use[buf] & 1, a->fault, abortp);
+    ++pp.use[buf];
+    const CT* zf = reinterpret_cast<const CT*>(bufp(buf));
+    CT* zc = reinterpret_cast<CT*>(bufp(buf) + kOffC);
+    float* eb = reinterpret_cast<float*>(bufp(buf) + kOffE);
+    const Level& coarse = a->coarse;
+    auto my = [&](int y) { return ext_coarse(y, coarse.h, h); };
+    auto mx = [&](int x) { return ext_coarse(x, coarse.w, w); };
+    fix_borders(zc, kKCS, kSmCH, kSmCW, cx0, cy0, coarse.w, coarse.h, my, mx);
+    if (first) {
+      // staged fine pixel (fy + rr, fx) at row 2 tr + rr, column tc + 2 (zero
+      // outside the level; those pixels are not stored)
+      const float* gb = reinterpret_cast<const float*>(bufp(buf) + kOffG) + 2 * tr * kSmIW + tc + 2;
+      we = conj_turns(a->turns * gb[0]);
+      wo = conj_turns(a->turns * gb[kSmIW]);
+      Pe = Po = splat(0.f);
+      base = splat(0.f);
+      if (a->has_e) {
+        fix_borders(eb, 1, kSmCH, kSmCW, cx0, cy0, coarse.w, coarse.h, my, mx);
+        const float* ew = eb + tr * kSmCW + c0;
+        float2 p[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          const float e0 = ew[c], e1 = ew[kSmCW + c], e2 = ew[2 * kSmCW + c];
+          p[c] = make_float2(fmaf(6.f, e1, e0 + e2), e1 + e2);
+        }
+        base = mul2(sc, fma2(ha, p[1], fma2(hb, p[0], p[2])));
+      }
+    }
+    // Orders k >= K of the highest chunk are staged as zeros (4-D maps) and
+    // come first in the descending Horner run, where they leave P at zero.
+    const CT* zw = zc + tr * kSmCW + c0;
+    const CT* zfw = zf + 2 * tr * kSmIW + tc + 2;
+#pragma unroll
+    for (int kk = kKCS - 1; kk >= 0; --kk) {
+      const CT* zr = zw + kk * kSmCH * kSmCW;
+      float2 ve[3], vo[3];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        const float2 q0 = Cplx<S>::cvt(zr[c]);
+        const float2 q1 = Cplx<S>::cvt(zr[kSmCW + c]);
+        const float2 q2 = Cplx<S>::cvt(zr[2 * kSmCW + c]);
+        ve[c] = fma2(splat(6.f), q1, add2(q0, q2));
+        vo[c] = add2(q1, q2);
+      }
+      const float2 ue = fma2(ha, ve[1], fma2(hb, ve[0], ve[2]));
+      const float2 uo = fma2(ha, vo[1], fma2(hb, vo[0], vo[2]));
+      const CT* fr = zfw + kk * kSmH * kSmIW;
+      const float2 fe = Cplx<S>::cvt(fr[0]), fo = Cplx<S>::cvt(fr[kSmIW]);
+      Pe = horner(Pe, we, fma2(splat(-sc.x), ue, fe));
+      Po = horner(Po, wo, fma2(splat(-sc.y), uo, fo));
+    }
+    if (last && fx >= 0 && fx < w) {
+      float* dst = a->fine.E + (long long)pl * a->fine.gplane + fx;
+#pragma unroll
+      for (int rr = 0; rr < 2; ++rr) {
+        const int y = fy + rr;
+        if (y < h) {
+          float delta = rr ? im_mul(Po, wo) : im_mul(Pe, we);
+          if (a->fine.M) delta *= (__ldg(a->fine.M + (long long)y * a->fine.pitch + fx) - 1.f) * a->mscale;
+          dst[(long long)y * a->fine.pitch] = (rr ? base.y : base.x) + delta;
+        }
+      }
+    }
+    __syncthreads();
+    if (*abortp) {
+      if (tid == 0 && has_next) drain(&bar[buf ^ 1], pp.use[buf ^ 1] & 1);
+      return false;
+    }
+    if (!last) {
+      --ch;
+    } else {
+      t += G;
+      if (t >= total) break;
+      a = res(t, lt);
+      nch = cdiv(a->K, kKCS);
+      ch = nch - 1;
+    }
+  }
+  return true;
+}
+
+// ---------------------------------------------------------------------------------------
 // Fused combine at levels 1 and 0 (Eq. (14), both cases; levels >= 3).
 // Item = (tile of 64 x 32 level-0 pixels, chunk of kKC orders) as in the
 // level-0 combine.  The level-0 EXPAND reads the 36 x 18 staged window of
@@ -1138,6 +1298,21 @@ __global__ void __launch_bounds__(kThreads, 2) k_down(const __grid_constant__ Do
                     smem, bar, pp, blockIdx.x, gridDim.x);
 }
 
+__device__ __forceinline__ int small_tiles(int h, int w, int planes) {
+  return cdiv(w + kDnX0, kSmW) * cdiv(h, kSmH) * planes;
+}
+
+template <typename S>
+__global__ void __launch_bounds__(kThreads) k_down_s(const __grid_constant__ DownArgs a) {
+  using SM = Smem<sizeof(typename Cplx<S>::T)>;
+  extern __shared__ __align__(128) unsigned char smem[];
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + SM::dns - 64);
+  init_bars(bar);
+  Pipe pp{};
+  stage_combine_s<S>([&](int g, int& l) { l = g; return &a; }, small_tiles(a.fine.h, a.fine.w, a.planes),
+                     smem, bar, pp, blockIdx.x, gridDim.x);
+}
+
 template <typename S>
 __global__ void __launch_bounds__(kThreads, 3) k_down0(const __grid_constant__ Down0Args a) {
   using SM = Smem<sizeof(typename Cplx<S>::T)>;
@@ -1425,6 +1600,12 @@ cudaError_t FLLF_LAUNCH_NAME(down)(const DownArgs& a, cudaStream_t s, int cps) {
   return launch_pdl(k_down<FLLF_STORAGE>, grid, SMS::dn1, s, a);
 }
 
+cudaError_t FLLF_LAUNCH_NAME(down_s)(const DownArgs& a, cudaStream_t s, int cps) {
+  const int tiles = cdiv(a.fine.w + kDnX0, kSmW) * cdiv(a.fine.h, kSmH) * a.planes;
+  const int grid = persistent_grid<k_down_s<FLLF_STORAGE>>(SMS::dns, tiles, cps);
+  return launch_pdl(k_down_s<FLLF_STORAGE>, grid, SMS::dns, s, a);
+}
+
 cudaError_t FLLF_LAUNCH_NAME(down0)(const Down0Args& a, cudaStream_t s, int cps) {
   const int tiles = cdiv(a.w0 + kDnX0, kDnOW) * cdiv(a.h0, kDnOH) * a.planes;
   const int grid = persistent_grid<k_down0<FLLF_STORAGE>>(SMS::dn, tiles, cps);
@@ -1455,7 +1636,8 @@ cudaError_t FLLF_LAUNCH_NAME(chain)(const ChainArgs& a, cudaStream_t s, int cps)
 }
 
 // Resident CTAs per SM of a stage kind's kernel (kind: 0 up0, 1 up, 2 down,
-// 3 down0 -- the fused level-0/1 kernel for the per-image path --, 4 chain).
+// 3 down0 -- the fused level-0/1 kernel for the per-image path --, 4 chain,
+// 5 the small-level combine).
 int FLLF_LAUNCH_NAME(occupancy)(int kind, int batched) {
   switch (kind) {
     case 0: return batched ? resident_per_sm<k_up0_batch<FLLF_STORAGE>>(SMS::up0, nullptr)
@@ -1466,10 +1648,11 @@ int FLLF_LAUNCH_NAME(occupancy)(int kind, int batched) {
                            : resident_per_sm<k_down<FLLF_STORAGE>>(SMS::dn1, nullptr);
     case 3: return batched ? resident_per_sm<k_down0_batch<FLLF_STORAGE>>(SMS::dn, nullptr)
                            : resident_per_sm<k_down10<FLLF_STORAGE, false>>(SMS::d10, nullptr);
-    default: {
+    case 4: {
       constexpr size_t kChainSmem = SMS::up > SMS::dn1 ? SMS::up : SMS::dn1;
       return resident_per_sm<k_chain<FLLF_STORAGE>>(kChainSmem, nullptr);
     }
+    default: return resident_per_sm<k_down_s<FLLF_STORAGE>>(SMS::dns, nullptr);
   }
 }
 

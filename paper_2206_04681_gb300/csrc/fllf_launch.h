@@ -14,6 +14,7 @@ namespace fllf {
   cudaError_t launch_up0_##suffix(const Up0Args& a, cudaStream_t s, int cps);                            \
   cudaError_t launch_up_##suffix(const UpArgs& a, cudaStream_t s, int cps);                              \
   cudaError_t launch_down_##suffix(const DownArgs& a, cudaStream_t s, int cps);                          \
+  cudaError_t launch_down_s_##suffix(const DownArgs& a, cudaStream_t s, int cps);                        \
   cudaError_t launch_down0_##suffix(const Down0Args& a, cudaStream_t s, int cps);                        \
   cudaError_t launch_down10_##suffix(const Down10Args& a, cudaStream_t s, int cps);                      \
   cudaError_t launch_chain_##suffix(const ChainArgs& a, cudaStream_t s, int cps);                        \

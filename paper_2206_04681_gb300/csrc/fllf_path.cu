@@ -83,6 +83,13 @@ cudaError_t launch_down(int prec, const DownArgs& a, cudaStream_t s, int cps) {
     default: return launch_down_f32(a, s, cps);
   }
 }
+cudaError_t launch_down_s(int prec, const DownArgs& a, cudaStream_t s, int cps) {
+  switch (prec) {
+    case FLLF_FP16: return launch_down_s_f16(a, s, cps);
+    case FLLF_BF16: return launch_down_s_bf16(a, s, cps);
+    default: return launch_down_s_f32(a, s, cps);
+  }
+}
 cudaError_t launch_chain(int prec, const ChainArgs& a, cudaStream_t s, int cps) {
   switch (prec) {
     case FLLF_FP16: return launch_chain_f16(a, s, cps);
@@ -124,6 +131,10 @@ bool build_maps(const fllf_params& p, const std::vector<Level>& lv, PathMaps* m)
   m->z_dn1.assign(L, CUtensorMap{});
   m->z_fn.assign(L, CUtensorMap{});
   m->g_fn.assign(L, CUtensorMap{});
+  m->z_cs.assign(L, CUtensorMap{});
+  m->e_cs.assign(L, CUtensorMap{});
+  m->z_fs.assign(L, CUtensorMap{});
+  m->g_fs.assign(L, CUtensorMap{});
   const bool f32 = p.precision == FLLF_FP32;
   const size_t zs = f32 ? 8 : 4;
   const CUtensorMapDataType zdt = f32 ? CU_TENSOR_MAP_DATA_TYPE_INT64 : CU_TENSOR_MAP_DATA_TYPE_UINT32;
@@ -149,6 +160,18 @@ bool build_maps(const fllf_params& p, const std::vector<Level>& lv, PathMaps* m)
                    kD0IW, kDnOH, 1))
         return false;
     }
+    // the small-level combine (levels >= 2 as the fine level, >= 3 as the coarse one)
+    if (l >= 3 && !encode4(&m->z_cs[l], zdt, v.Z, v.w, v.h, p.K, p.C, zrow, zs * (uint64_t)v.zk,
+                           zs * (uint64_t)v.zplane, kSmCW, kSmCH, kKCS))
+      return false;
+    if (l >= 2 && l <= L - 2) {
+      if (!encode4(&m->z_fs[l], zdt, v.Z, v.w, v.h, p.K, p.C, zrow, zs * (uint64_t)v.zk,
+                   zs * (uint64_t)v.zplane, kSmIW, kSmH, kKCS))
+        return false;
+      if (!encode3(&m->g_fs[l], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, v.G, v.w, v.h, p.C, grow, gplane,
+                   kSmIW, kSmH, 1))
+        return false;
+    }
     // as the source of a REDUCE: 68 x 35 box, up_kc orders; plus the guide
     if (l <= L - 2) {
       if (!encode3(&m->z_up[l], zdt, zs, v.Z, v.w, v.h, zplanes, zrow, zplane, kRsBW, kRsIR, up_kc))
@@ -160,6 +183,9 @@ bool build_maps(const fllf_params& p, const std::vector<Level>& lv, PathMaps* m)
     if (v.E) {
       if (!encode3(&m->e_dn[l], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, v.E, v.w, v.h, p.C, grow, gplane,
                    kDnCW, kDnCH, 1))
+        return false;
+      if (l >= 3 && !encode3(&m->e_cs[l], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, v.E, v.w, v.h, p.C, grow,
+                             gplane, kSmCW, kSmCH, 1))
         return false;
     }
   }
@@ -292,7 +318,18 @@ cudaError_t enqueue_path(const fllf_params& p, const std::vector<Level>& lv, con
   // With levels >= 3 the level-1 combine runs inside the level-0 tiles.
   const int down_lo = L >= 3 ? 2 : 1;
   for (int l = (c0 <= L - 2 ? c0 - 1 : L - 2); l >= down_lo; --l) {
-    const DownArgs d = down_args(l);
+    DownArgs d = down_args(l);
+    if (l >= 2 && (long long)lv[l].h * lv[l].w * C <= tn.small_px) {
+      // small level: the same combine on 32 x 16 tiles
+      d.zmap = maps.z_cs[l + 1];
+      d.emap = maps.e_cs[l + 1];
+      d.zfmap = maps.z_fs[l];
+      d.gfmap = maps.g_fs[l];
+      mark(FLLF_STAGE_DOWN_S, true);
+      if ((e = launch_down_s(prec, d, s, tn.cps[FLLF_STAGE_DOWN_S])) != cudaSuccess) return e;
+      mark(FLLF_STAGE_DOWN_S, false);
+      continue;
+    }
     mark(FLLF_STAGE_DOWN, true);
     if ((e = launch_down(prec, d, s, tn.cps[FLLF_STAGE_DOWN])) != cudaSuccess) return e;
     mark(FLLF_STAGE_DOWN, false);

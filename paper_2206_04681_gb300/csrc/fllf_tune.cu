@@ -7,6 +7,8 @@
 //   * where the chained launch of the small levels starts (levels >= 2 whose
 //     planes hold at most chain_pixels pixels run in one cooperative launch
 //     with grid barriers; larger levels run one launch per stage);
+//   * below which size a level's combine runs on 32 x 16 tiles with two
+//     pixels per thread rather than 64 x 32 tiles with eight;
 //   * the persistent grid of every stage kind: how many CTAs per SM are
 //     resident (fewer leaves each CTA more L2 and DRAM bandwidth, more
 //     hides latency);
@@ -91,6 +93,7 @@ void to_public(const Tuning& t, fllf_tuning* o) {
   o->chain_pixels = t.chain_px;
   for (int k = 0; k < FLLF_NSTAGE; ++k) o->ctas_per_sm[k] = t.cps[k];
   o->reduce_reverse = t.reverse;
+  o->small_pixels = t.small_px;
 }
 
 }  // namespace
@@ -106,12 +109,14 @@ fllf_status fllf_plan_get_tuning(const fllf_plan* plan, fllf_tuning* out) {
 fllf_status fllf_plan_set_tuning(fllf_plan* plan, const fllf_tuning* t) {
   if (!plan || !t) return tfail(FLLF_EINVAL, "plan or tuning is NULL");
   if (t->chain_pixels < 0) return tfail(FLLF_EINVAL, "chain_pixels must be >= 0");
+  if (t->small_pixels < 0) return tfail(FLLF_EINVAL, "small_pixels must be >= 0");
   for (int k = 0; k < FLLF_NSTAGE; ++k)
     if (t->ctas_per_sm[k] < 0 || t->ctas_per_sm[k] > 32) return tfail(FLLF_EINVAL, "ctas_per_sm must be 0..32");
   if (t->reduce_reverse != 0 && t->reduce_reverse != 1) return tfail(FLLF_EINVAL, "reduce_reverse must be 0 or 1");
   plan->tune.chain_px = t->chain_pixels;
   for (int k = 0; k < FLLF_NSTAGE; ++k) plan->tune.cps[k] = t->ctas_per_sm[k];
   plan->tune.reverse = t->reduce_reverse;
+  plan->tune.small_px = t->small_pixels;
   return FLLF_OK;
 }
 
@@ -159,7 +164,20 @@ fllf_status fllf_plan_autotune(fllf_plan* plan, const float* d_in, float* d_out,
     t.chain_px = px;
     ok = ok && consider(t);
   }
-  // 2. resident CTAs per SM of each stage kind
+  // 2. the size below which a combine runs on the small tiles: none, or
+  // each level size from the finest combined level (>= 2) down
+  {
+    std::vector<long long> cand{0};
+    for (int l = 2; l <= p.levels - 2; ++l) cand.push_back((long long)plan->lv[l].h * plan->lv[l].w * p.C);
+    for (long long px : cand) {
+      if (!ok) break;
+      Tuning t = best;
+      t.small_px = px;
+      if (t.small_px == best.small_px) continue;
+      ok = consider(t);
+    }
+  }
+  // 3. resident CTAs per SM of each stage kind
   for (int kind = 0; kind < FLLF_NSTAGE && ok; ++kind) {
     const int occ = stage_occupancy(p.precision, kind, false);
     for (int c = 1; c <= occ && ok; ++c) {
@@ -169,7 +187,7 @@ fllf_status fllf_plan_autotune(fllf_plan* plan, const float* d_in, float* d_out,
       ok = consider(t);
     }
   }
-  // 3. visiting order of the level 1 -> 2 REDUCE
+  // 4. visiting order of the level 1 -> 2 REDUCE
   if (ok) {
     Tuning t = best;
     t.reverse = 1 - t.reverse;

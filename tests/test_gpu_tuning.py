@@ -1,6 +1,7 @@
-"""Launch tuning and the autotuner: every launch setting (chain start, CTAs
-per SM, REDUCE order) computes the same output bit for bit, the autotuner
-keeps a valid setting, and the batch autotuner keeps per-image results."""
+"""Launch tuning and the autotuner: every launch setting (chain start,
+small-tile threshold, CTAs per SM, REDUCE order) computes the same output
+bit for bit, the autotuner keeps a valid setting, and the batch autotuner
+keeps per-image results."""
 
 import numpy as np
 import pytest
@@ -21,12 +22,17 @@ def _lib():
     build.build_library()
 
 
-def _tuning(chain, cps, rev):
+NST = len(pkg.STAGES)
+ALL = 1 << 40   # every combined level >= 2 on the small tiles
+
+
+def _tuning(chain, cps, rev, small=1 << 19):
     t = pkg.fllf_tuning()
     t.chain_pixels = chain
     for i, c in enumerate(cps):
         t.ctas_per_sm[i] = c
     t.reduce_reverse = rev
+    t.small_pixels = small
     return t
 
 
@@ -37,11 +43,12 @@ def test_every_launch_setting_gives_the_same_bits(precision):
     plan = pkg.fllf_plan_create(p, 0)
     try:
         d = pkg.fllf_plan_get_tuning(plan).as_dict()
-        assert d["chain_pixels"] == 1 << 21 and d["reduce_reverse"] == 1
+        assert d["chain_pixels"] == 1 << 21 and d["reduce_reverse"] == 1 and d["small_pixels"] == 1 << 19
         x = torch.from_numpy(img).cuda()
         outs = []
-        for t in (_tuning(1 << 21, [0] * 5, 1), _tuning(0, [0] * 5, 0), _tuning(1 << 23, [1] * 5, 1),
-                  _tuning(1 << 15, [2, 1, 1, 1, 1], 0)):
+        for t in (_tuning(1 << 21, [0] * NST, 1), _tuning(0, [0] * NST, 0), _tuning(1 << 23, [1] * NST, 1),
+                  _tuning(1 << 15, [2, 1, 1, 1, 1, 2], 0), _tuning(0, [0] * NST, 1, small=0),
+                  _tuning(0, [0] * NST, 1, small=ALL), _tuning(1 << 17, [0, 0, 0, 0, 0, 1], 1, small=ALL)):
             pkg.fllf_plan_set_tuning(plan, t)
             y = torch.full_like(x, float("nan"))
             pkg.run_tensor(plan, x, y)
@@ -54,9 +61,65 @@ def test_every_launch_setting_gives_the_same_bits(precision):
             ref = o.fourier_llf(img.astype(np.float64), 8, a, 2.0)
             assert float(np.max(np.abs(outs[0] - ref))) <= 1e-4
         with pytest.raises(pkg.FllfError):
-            pkg.fllf_plan_set_tuning(plan, _tuning(-1, [0] * 5, 1))
+            pkg.fllf_plan_set_tuning(plan, _tuning(-1, [0] * NST, 1))
         with pytest.raises(pkg.FllfError):
-            pkg.fllf_plan_set_tuning(plan, _tuning(0, [0, 0, 99, 0, 0], 1))
+            pkg.fllf_plan_set_tuning(plan, _tuning(0, [0, 0, 99, 0, 0, 0], 1))
+        with pytest.raises(pkg.FllfError):
+            pkg.fllf_plan_set_tuning(plan, _tuning(0, [0] * NST, 1, small=-1))
+    finally:
+        pkg.fllf_plan_destroy(plan)
+
+
+# The 32 x 16 small-level combine takes the same arithmetic steps as the
+# 64 x 32 one: ragged sizes (partial tiles, odd widths and heights), orders
+# padded in the top chunk (K = 5, 6) or several chunks (K = 12, 16), single
+# planes and three, every storage precision, and the pixel-adaptive gain.
+SMALL_CASES = [  # H, W, C, levels, K, m, sigma_r, precision
+    (301, 517, 3, 7, 5, 3.0, 0.2, "fp32"),
+    (200, 333, 1, 6, 12, 0.5, 0.3, "fp32"),
+    (97, 1031, 2, 6, 16, 4.0, 0.05, "fp16"),
+    (515, 131, 1, 7, 6, 2.0, 0.15, "bf16"),
+    (64, 64, 3, 6, 8, 3.0, 0.2, "fp32"),
+]
+
+
+@pytest.mark.parametrize("case", SMALL_CASES)
+def test_small_tile_combine_gives_the_same_bits(case):
+    H, W, C, L, K, m, s, prec = case
+    img = synth_image(H, W, C, polygons=6, seed=H + W)
+    plan = pkg.fllf_plan_create(pkg.make_params(H, W, C, L, K, m, s, 2.0, prec), 0)
+    try:
+        x = torch.from_numpy(img).cuda()
+        outs = []
+        for small in (0, ALL):
+            pkg.fllf_plan_set_tuning(plan, _tuning(0, [0] * NST, 1, small=small))
+            y = torch.full_like(x, float("nan"))
+            pkg.run_tensor(plan, x, y)
+            torch.cuda.synchronize()
+            outs.append(y.cpu().numpy())
+        np.testing.assert_array_equal(outs[1], outs[0])
+        assert np.all(np.isfinite(outs[0]))
+    finally:
+        pkg.fllf_plan_destroy(plan)
+
+
+def test_small_tile_combine_adaptive_gain_same_bits():
+    H, W, C = 260, 390, 1
+    img = synth_image(H, W, C, polygons=6, seed=31)
+    gain = np.linspace(0.5, 3.5, H * W, dtype=np.float32).reshape(H, W)
+    plan = pkg.fllf_plan_create(pkg.make_params(H, W, C, 7, 8, 2.5, 0.2, 2.0), 0)
+    try:
+        x = torch.from_numpy(img).cuda()
+        g = torch.from_numpy(gain).cuda()
+        outs = []
+        for small in (0, ALL):
+            pkg.fllf_plan_set_tuning(plan, _tuning(0, [0] * NST, 1, small=small))
+            y = torch.full_like(x, float("nan"))
+            pkg.fllf_run_adaptive(plan, x.data_ptr(), g.data_ptr(), y.data_ptr(),
+                                  torch.cuda.current_stream().cuda_stream)
+            torch.cuda.synchronize()
+            outs.append(y.cpu().numpy())
+        np.testing.assert_array_equal(outs[1], outs[0])
     finally:
         pkg.fllf_plan_destroy(plan)
 
@@ -75,6 +138,8 @@ def test_autotune_keeps_a_valid_setting_and_the_output():
         assert ms > 0
         d = t.as_dict()
         assert d["chain_pixels"] in (0, 1 << 15, 1 << 17, 1 << 19, 1 << 21, 1 << 23)
+        sizes = [h * w * 3 for h, w in o.level_shapes(540, 960, 7)[2:6]]
+        assert d["small_pixels"] in [0, 1 << 19] + sizes
         assert all(0 <= c <= 32 for c in d["ctas_per_sm"].values())
         z = torch.full_like(x, float("nan"))
         pkg.run_tensor(plan, x, z)
