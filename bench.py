@@ -66,8 +66,8 @@ def level_sizes(H, W, L):
     return out
 
 
-CHAIN_PIXELS = 1 << 21   # default: levels whose pixels over all planes fit this run chained
-SMALL_PIXELS = 1 << 19   # default: other combines at levels >= 2 this small run on 32 x 16 tiles
+CHAIN_PIXELS = 0         # default: levels whose pixels over all planes fit this run chained
+SMALL_PIXELS = 1 << 40   # default: other combines at levels >= 2 this small run on 32 x 16 tiles
 
 
 def stage_split(cfg, chain_px=CHAIN_PIXELS, small_px=SMALL_PIXELS):

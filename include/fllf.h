@@ -311,8 +311,10 @@ fllf_status fllf_plan_stage_times(fllf_plan *plan, double *ms, int *launches);
  * tune at run time is how the path is launched:
  *   chain_pixels    levels >= 2 whose planes hold at most this many pixels
  *                   (over all C planes) run in one chained cooperative launch
- *                   with grid barriers between stages; 0 = no chained launch.
- *                   Default 2^21.
+ *                   with grid barriers between stages; 0 = no chained launch
+ *                   (default: with programmatic dependent launch between the
+ *                   per-level kernels, separate launches measured faster at
+ *                   every size from 512 x 512 to 8K RGB).
  *   ctas_per_sm[k]  resident CTAs per SM of the persistent grid of stage kind
  *                   k (FLLF_STAGE_*); 0 = as many as fit (default).
  *   reduce_reverse  1 (default): the level 1 -> 2 REDUCE visits its work
@@ -323,8 +325,8 @@ fllf_status fllf_plan_stage_times(fllf_plan *plan, double *ms, int *launches);
  *                   32 x 16 tiles with two pixels per thread
  *                   (FLLF_STAGE_DOWN_S) instead of 64 x 32 tiles with eight:
  *                   four times the tiles and a quarter of each thread's
- *                   serial work, for levels too small to fill the GPU.
- *                   Default 2^19; 0 = never.
+ *                   serial work.  Default 2^40 (every level: the small tiles
+ *                   measured as fast or faster at every size tried); 0 = never.
  * Every setting computes the same output, bit for bit. */
 typedef struct {
   long long chain_pixels;
@@ -355,9 +357,10 @@ fllf_status fllf_plan_autotune(fllf_plan *plan, const float *d_in, float *d_out,
                                double *best_ms);
 
 /* Batches: resident CTAs per SM of the four batched stage kinds (level-0
- * REDUCE, REDUCE, combine at levels >= 1, combine at level 0), 0 = as many
- * as fit.  Changing them makes the next fllf_batch_run capture its CUDA
- * graph again.  The batch autotuner times fllf_batch_run on the given
+ * REDUCE, REDUCE, combine at levels >= 2 on 32 x 16 tiles, and the level-0
+ * stage: the fused level-1/level-0 combine, or the level-0 combine of the
+ * 2-level images), 0 = as many as fit.  Changing them makes the next
+ * fllf_batch_run capture its CUDA graph again.  The batch autotuner times fllf_batch_run on the given
  * buffers (as for fllf_batch_run; outputs overwritten) and keeps the best
  * caps, with the same search and 1% rule as fllf_plan_autotune. */
 fllf_status fllf_batch_get_ctas(const fllf_batch *batch, int *ctas_per_sm /* [4] */);

@@ -23,6 +23,7 @@ int up_items_h(const Level& dst, int planes, int K, int write_g, int prec) {
   return cdiv(dst.w, kRsTW) * cdiv(dst.h, kRsTH) * planes * (cdiv(K, kcu) + (write_g ? 1 : 0));
 }
 int combine_tiles_h(int h, int w, int planes) { return cdiv(w + kDnX0, kDnOW) * cdiv(h, kDnOH) * planes; }
+int small_tiles_h(int h, int w, int planes) { return cdiv(w + kDnX0, kSmW) * cdiv(h, kSmH) * planes; }
 
 template <typename T>
 size_t push(std::vector<unsigned char>& blob, const T* data, size_t n, size_t align) {
@@ -52,6 +53,12 @@ cudaError_t launch_stage_at(const unsigned char* d_base, const StageRec& st, int
       return prec == FLLF_FP16 ? launch_down_batch_f16(t, s, cps)
              : prec == FLLF_BF16 ? launch_down_batch_bf16(t, s, cps) : launch_down_batch_f32(t, s, cps);
     }
+    case kStageDown10: {
+      BatchTable<Down10Args> t{reinterpret_cast<const Down10Args*>(d_base + st.args_off), prefix, st.n,
+                               st.total};
+      return prec == FLLF_FP16 ? launch_down10_batch_f16(t, s, cps)
+             : prec == FLLF_BF16 ? launch_down10_batch_bf16(t, s, cps) : launch_down10_batch_f32(t, s, cps);
+    }
     default: {
       BatchTable<Down0Args> t{reinterpret_cast<const Down0Args*>(d_base + st.args_off), prefix, st.n, st.total};
       return prec == FLLF_FP16 ? launch_down0_batch_f16(t, s, cps)
@@ -66,8 +73,9 @@ void build_batch_blob(const std::vector<const fllf_plan*>& plans, int prec, Batc
   out->stages.clear();
   out->up0_img.clear();
   out->down0_img.clear();
+  out->down10_img.clear();
   out->copy_img.clear();
-  out->up0_off = out->down0_off = 0;
+  out->up0_off = out->down0_off = out->down10_off = 0;
   std::vector<unsigned char>& blob = out->blob;
   blob.clear();
   int maxL = 1;
@@ -104,7 +112,7 @@ void build_batch_blob(const std::vector<const fllf_plan*>& plans, int prec, Batc
       u.dst = pl->lv[1];
       u.K = pl->p.K;
       u.turns = (float)(2.0 / pl->p.T);
-      u.use_tma = 0;  // the input changes per run: plain loads, no per-run tensor map
+      u.use_tma = 0;  // the input and its map are set per run (set_level0_io)
       args.push_back(u);
       counts.push_back(up0_items_h(pl->lv[1], pl->p.C));
       out->up0_img.push_back(i);
@@ -131,17 +139,19 @@ void build_batch_blob(const std::vector<const fllf_plan*>& plans, int prec, Batc
     }
     add_stage(kStageUp, args, counts);
   }
-  for (int l = maxL - 2; l >= 1; --l) {
+  // combines at levels >= 2 (level 1 runs inside the fused level-0 stage of
+  // the images with >= 3 levels; images with 2 levels combine level 0 only)
+  for (int l = maxL - 2; l >= 2; --l) {
     std::vector<DownArgs> args;
     std::vector<int> counts;
     for (const fllf_plan* pl : plans) {
       const int L = pl->p.levels;
       if (l > L - 2) continue;
-      DownArgs d{};
-      d.zmap = pl->maps.z_dn1[l + 1];
-      d.emap = pl->maps.e_dn[l + 1];
-      d.zfmap = pl->maps.z_fn[l];
-      d.gfmap = pl->maps.g_fn[l];
+      DownArgs d{};   // the 32 x 16 tiles of the batched combine
+      d.zmap = pl->maps.z_cs[l + 1];
+      d.emap = pl->maps.e_cs[l + 1];
+      d.zfmap = pl->maps.z_fs[l];
+      d.gfmap = pl->maps.g_fs[l];
       d.fine = pl->lv[l];
       d.coarse = pl->lv[l + 1];
       d.planes = pl->p.C;
@@ -149,15 +159,37 @@ void build_batch_blob(const std::vector<const fllf_plan*>& plans, int prec, Batc
       d.turns = (float)(2.0 / pl->p.T);
       d.has_e = (l + 1 <= L - 2) ? 1 : 0;
       args.push_back(d);
-      counts.push_back(combine_tiles_h(pl->lv[l].h, pl->lv[l].w, pl->p.C));
+      counts.push_back(small_tiles_h(pl->lv[l].h, pl->lv[l].w, pl->p.C));
     }
     add_stage(kStageDown, args, counts);
   }
   {
+    std::vector<Down10Args> a10;
+    std::vector<int> c10;
     std::vector<Down0Args> args;
     std::vector<int> counts;
     for (int idx : out->up0_img) {
       const fllf_plan* pl = plans[idx];
+      if (pl->p.levels >= 3) {
+        Down10Args d{};
+        d.z1map = pl->maps.z_dn[1];
+        d.g1map = pl->maps.g1_d10;
+        d.z2map = pl->maps.z2_d10;
+        d.e2map = pl->maps.e2_d10;
+        d.h0 = pl->p.H;
+        d.w0 = pl->p.W;
+        d.planes = pl->p.C;
+        d.l1 = pl->lv[1];
+        d.l2 = pl->lv[2];
+        d.K = pl->p.K;
+        d.turns = (float)(2.0 / pl->p.T);
+        d.has_e2 = pl->p.levels >= 4 ? 1 : 0;
+        d.use_tma = 0;  // the input and its map are set per run (set_level0_io)
+        a10.push_back(d);
+        c10.push_back(combine_tiles_h(pl->p.H, pl->p.W, pl->p.C));
+        out->down10_img.push_back(idx);
+        continue;
+      }
       Down0Args d{};
       d.zmap = pl->maps.z_dn[1];
       d.emap = pl->maps.e_dn[1];
@@ -172,6 +204,8 @@ void build_batch_blob(const std::vector<const fllf_plan*>& plans, int prec, Batc
       counts.push_back(combine_tiles_h(pl->p.H, pl->p.W, pl->p.C));
       out->down0_img.push_back(idx);
     }
+    add_stage(kStageDown10, a10, c10);
+    if (!a10.empty()) out->down10_off = out->stages.back().args_off;
     add_stage(kStageDown0, args, counts);
     if (!args.empty()) out->down0_off = out->stages.back().args_off;
   }
@@ -185,27 +219,46 @@ void set_blob_fault(BatchBlob& bb, unsigned* d_fault) {
         case kStageUp0: reinterpret_cast<Up0Args*>(base)[j].fault = d_fault; break;
         case kStageUp: reinterpret_cast<UpArgs*>(base)[j].fault = d_fault; break;
         case kStageDown: reinterpret_cast<DownArgs*>(base)[j].fault = d_fault; break;
+        case kStageDown10: reinterpret_cast<Down10Args*>(base)[j].fault = d_fault; break;
         default: reinterpret_cast<Down0Args*>(base)[j].fault = d_fault; break;
       }
     }
   }
 }
 
-void set_blob_io(BatchBlob& bb, const float* const* d_in, float* const* d_out) {
-  if (bb.up0_img.empty()) return;
-  Up0Args* u = reinterpret_cast<Up0Args*>(bb.blob.data() + bb.up0_off);
-  Down0Args* d = reinterpret_cast<Down0Args*>(bb.blob.data() + bb.down0_off);
+void set_level0_io(const BatchBlob& bb, Up0Args* u, Down0Args* d0, Down10Args* d10, const float* const* d_in,
+                   float* const* d_out) {
+  // the input's maps for the level-0 REDUCE and the fused combine are encoded
+  // per run (the kernels order them for the tensor-map proxy before use);
+  // where the image allows none, the kernels read the input with plain loads
   for (size_t j = 0; j < bb.up0_img.size(); ++j) {
-    u[j].I = d_in[bb.up0_img[j]];
-    d[j].I = d_in[bb.down0_img[j]];
-    d[j].O = d_out[bb.down0_img[j]];
+    Up0Args& a = u[j];
+    a.I = d_in[bb.up0_img[j]];
+    a.use_tma = encode_image_map(&a.imap, a.I, a.w0, a.h0, a.planes, kUpIW, kUpIR) ? 1 : 0;
   }
+  for (size_t j = 0; j < bb.down0_img.size(); ++j) {
+    d0[j].I = d_in[bb.down0_img[j]];
+    d0[j].O = d_out[bb.down0_img[j]];
+  }
+  for (size_t j = 0; j < bb.down10_img.size(); ++j) {
+    Down10Args& a = d10[j];
+    a.I = d_in[bb.down10_img[j]];
+    a.O = d_out[bb.down10_img[j]];
+    a.use_tma = encode_image_map(&a.imap, a.I, a.w0, a.h0, a.planes, kD0IW, kDnOH) ? 1 : 0;
+  }
+}
+
+void set_blob_io(BatchBlob& bb, const float* const* d_in, float* const* d_out) {
+  unsigned char* b = bb.blob.data();
+  set_level0_io(bb, reinterpret_cast<Up0Args*>(b + bb.up0_off), reinterpret_cast<Down0Args*>(b + bb.down0_off),
+                reinterpret_cast<Down10Args*>(b + bb.down10_off), d_in, d_out);
 }
 
 cudaError_t launch_batch_stages(const std::vector<StageRec>& stages, const unsigned char* d_base,
                                 int prec, cudaStream_t s, const int* cps) {
   for (const StageRec& st : stages) {
-    const cudaError_t e = launch_stage_at(d_base, st, prec, s, cps ? cps[st.kind] : 0);
+    const int ck = st.kind == kStageDown10 ? kStageDown0 : st.kind;
+    const cudaError_t e = launch_stage_at(d_base, st, prec, s, cps ? cps[ck] : 0);
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
@@ -244,6 +297,7 @@ struct fllf_batch {
   unsigned* d_fault = nullptr;
   Up0Args* h_up0 = nullptr;        // pinned per-run mirrors of the level-0 tables
   Down0Args* h_down0 = nullptr;
+  Down10Args* h_down10 = nullptr;
   cudaEvent_t copied = nullptr;
   bool copied_pending = false;
   cudaStream_t cap = nullptr;
@@ -258,6 +312,7 @@ static void free_batch(fllf_batch* b) {
   if (b->copied) cudaEventDestroy(b->copied);
   if (b->h_up0) cudaFreeHost(b->h_up0);
   if (b->h_down0) cudaFreeHost(b->h_down0);
+  if (b->h_down10) cudaFreeHost(b->h_down10);
   if (b->d_mem) cudaFree(b->d_mem);
   delete b;
 }
@@ -298,7 +353,8 @@ fllf_status fllf_batch_create(fllf_plan* const* plans, int n, fllf_batch** out) 
   }
   const size_t nu = std::max<size_t>(1, b->bb.up0_img.size());
   if (cudaMallocHost(&b->h_up0, sizeof(Up0Args) * nu) != cudaSuccess ||
-      cudaMallocHost(&b->h_down0, sizeof(Down0Args) * nu) != cudaSuccess) {
+      cudaMallocHost(&b->h_down0, sizeof(Down0Args) * nu) != cudaSuccess ||
+      cudaMallocHost(&b->h_down10, sizeof(Down10Args) * nu) != cudaSuccess) {
     cudaGetLastError();
     free_batch(b);
     return bfail(FLLF_ENOMEM, "pinned host tables");
@@ -306,8 +362,10 @@ fllf_status fllf_batch_create(fllf_plan* const* plans, int n, fllf_batch** out) 
   if (!b->bb.up0_img.empty()) {
     const Up0Args* u = reinterpret_cast<const Up0Args*>(b->bb.blob.data() + b->bb.up0_off);
     const Down0Args* d = reinterpret_cast<const Down0Args*>(b->bb.blob.data() + b->bb.down0_off);
+    const Down10Args* f = reinterpret_cast<const Down10Args*>(b->bb.blob.data() + b->bb.down10_off);
     std::copy(u, u + b->bb.up0_img.size(), b->h_up0);
     std::copy(d, d + b->bb.down0_img.size(), b->h_down0);
+    std::copy(f, f + b->bb.down10_img.size(), b->h_down10);
   }
   if (cudaEventCreateWithFlags(&b->copied, cudaEventDisableTiming) != cudaSuccess ||
       cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) != cudaSuccess) {
@@ -343,19 +401,14 @@ fllf_status fllf_batch_run(fllf_batch* b, const float* const* d_in, float* const
   if (b->copied_pending && (e = cudaEventSynchronize(b->copied)) != cudaSuccess)
     return bfail(FLLF_ECUDA, std::string("batch copy wait: ") + cudaGetErrorString(e));
   const BatchBlob& bb = b->bb;
-  for (size_t j = 0; j < bb.up0_img.size(); ++j) {
-    b->h_up0[j].I = d_in[bb.up0_img[j]];
-    b->h_down0[j].I = d_in[bb.down0_img[j]];
-    b->h_down0[j].O = d_out[bb.down0_img[j]];
-  }
-  if (!bb.up0_img.empty()) {
-    if ((e = cudaMemcpyAsync(b->d_mem + bb.up0_off, b->h_up0, sizeof(Up0Args) * bb.up0_img.size(),
-                             cudaMemcpyHostToDevice, s)) != cudaSuccess ||
-        (e = cudaMemcpyAsync(b->d_mem + bb.down0_off, b->h_down0,
-                             sizeof(Down0Args) * bb.down0_img.size(), cudaMemcpyHostToDevice, s)) !=
-            cudaSuccess)
-      return bfail(FLLF_ECUDA, std::string("batch table update: ") + cudaGetErrorString(e));
-  }
+  set_level0_io(bb, b->h_up0, b->h_down0, b->h_down10, d_in, d_out);
+  auto upload = [&](size_t off, const void* src, size_t bytes) {
+    return bytes ? cudaMemcpyAsync(b->d_mem + off, src, bytes, cudaMemcpyHostToDevice, s) : cudaSuccess;
+  };
+  if ((e = upload(bb.up0_off, b->h_up0, sizeof(Up0Args) * bb.up0_img.size())) != cudaSuccess ||
+      (e = upload(bb.down0_off, b->h_down0, sizeof(Down0Args) * bb.down0_img.size())) != cudaSuccess ||
+      (e = upload(bb.down10_off, b->h_down10, sizeof(Down10Args) * bb.down10_img.size())) != cudaSuccess)
+    return bfail(FLLF_ECUDA, std::string("batch table update: ") + cudaGetErrorString(e));
   if ((e = cudaEventRecord(b->copied, s)) != cudaSuccess)
     return bfail(FLLF_ECUDA, std::string("batch event: ") + cudaGetErrorString(e));
   b->copied_pending = true;

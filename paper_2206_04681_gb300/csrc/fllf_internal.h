@@ -88,6 +88,10 @@ struct PathMaps {
 };
 // Encodes the maps for the level buffers in `lv` (device addresses).
 bool build_maps(const fllf_params& p, const std::vector<Level>& lv, PathMaps* m);
+// Tiled map of a planar C x H x W float image with the given box (zero fill
+// outside); false when the image does not allow one (W % 4 != 0, a base not
+// 16-byte aligned) or the encoding fails.
+bool encode_image_map(CUtensorMap* m, const float* base, int W, int H, int C, uint32_t box_w, uint32_t box_h);
 
 // Launch tuning of a plan (the autotuner's knobs).  chain_px: levels >= 2
 // whose planes hold at most this many pixels in all run in the chained
@@ -96,8 +100,8 @@ bool build_maps(const fllf_params& p, const std::vector<Level>& lv, PathMaps* m)
 // resident-CTA cap per SM of the stage kind's persistent grid (0: as many as
 // fit); reverse: the level 1->2 REDUCE visits its items last to first.
 struct Tuning {
-  long long chain_px = 1ll << 21;
-  long long small_px = 1ll << 19;
+  long long chain_px = 0;
+  long long small_px = 1ll << 40;
   int cps[FLLF_NSTAGE] = {0, 0, 0, 0, 0, 0};
   int reverse = 1;
 };
@@ -115,7 +119,9 @@ cudaError_t enqueue_path(const fllf_params& p, const std::vector<Level>& lv, con
                          float mscale = 0.f, const Tuning* tune = nullptr);
 
 // ---- batched argument tables (shared by batches and the server) ---------------
-enum BatchStageKind { kStageUp0 = 0, kStageUp = 1, kStageDown = 2, kStageDown0 = 3 };
+// kStageDown10 (the fused level-1/level-0 combine of the images with >= 3
+// levels) shares the CTA cap of kStageDown0.
+enum BatchStageKind { kStageUp0 = 0, kStageUp = 1, kStageDown = 2, kStageDown0 = 3, kStageDown10 = 4 };
 struct StageRec {
   int kind;
   size_t args_off;    // byte offset of the argument blocks in the table image
@@ -125,14 +131,19 @@ struct StageRec {
 struct BatchBlob {
   std::vector<unsigned char> blob;  // host image of the device tables
   std::vector<StageRec> stages;     // launch order
-  std::vector<int> up0_img, down0_img, copy_img;
-  size_t up0_off = 0, down0_off = 0, status_off = 0;
+  std::vector<int> up0_img, down0_img, down10_img, copy_img;
+  size_t up0_off = 0, down0_off = 0, down10_off = 0, status_off = 0;
 };
 // Argument tables for `plans` (same storage precision `prec`).
 void build_batch_blob(const std::vector<const fllf_plan*>& plans, int prec, BatchBlob* out);
 // Points every argument block's fault word at d_fault.
 void set_blob_fault(BatchBlob& bb, unsigned* d_fault);
-// Writes the level-0 input / output pointers of each image.
+// Writes the level-0 input / output pointers of each image, and the input's
+// tensor maps, into the tables u (up0), d0 (level-0 combine) and d10 (fused
+// level-1/level-0 combine), which hold bb's entries in bb's order.
+void set_level0_io(const BatchBlob& bb, Up0Args* u, Down0Args* d0, Down10Args* d10, const float* const* d_in,
+                   float* const* d_out);
+// The same on the table image inside bb.
 void set_blob_io(BatchBlob& bb, const float* const* d_in, float* const* d_out);
 // Enqueues the batched stage kernels reading the tables uploaded at d_base.
 cudaError_t launch_batch_stages(const std::vector<StageRec>& stages, const unsigned char* d_base,

@@ -1354,6 +1354,9 @@ __global__ void __launch_bounds__(kThreads) k_up0_batch(const BatchTable<Up0Args
   using SM = Smem<sizeof(typename Cplx<S>::T)>;
   extern __shared__ __align__(128) unsigned char smem[];
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem + SM::up0 - 64);
+  fence_maps(tb, [](const Up0Args& a) {
+    if (a.use_tma) fence_tensormap(&a.imap);
+  });
   init_bars(bar);
   Pipe pp{};
   stage_up0<S>([&](int g, int& l) {
@@ -1383,11 +1386,14 @@ __global__ void __launch_bounds__(kThreads) k_up_batch(const BatchTable<UpArgs> 
               tb.total, smem, bar, pp, blockIdx.x, gridDim.x);
 }
 
+// Combines at levels >= 1 of a batch: the 32 x 16 tiles (the same bits as
+// the 64 x 32 combine, and the better fill for the small levels of mixed
+// batches).
 template <typename S>
-__global__ void __launch_bounds__(kThreads, 2) k_down_batch(const BatchTable<DownArgs> tb) {
+__global__ void __launch_bounds__(kThreads) k_down_batch(const BatchTable<DownArgs> tb) {
   using SM = Smem<sizeof(typename Cplx<S>::T)>;
   extern __shared__ __align__(128) unsigned char smem[];
-  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + SM::dn1 - 64);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + SM::dns - 64);
   fence_maps(tb, [](const DownArgs& a) {
     fence_tensormap(&a.zmap);
     fence_tensormap(&a.emap);
@@ -1396,7 +1402,32 @@ __global__ void __launch_bounds__(kThreads, 2) k_down_batch(const BatchTable<Dow
   });
   init_bars(bar);
   Pipe pp{};
-  stage_combine1<S>(
+  stage_combine_s<S>(
+      [&](int g, int& l) {
+        const int j = find_entry(tb.prefix, tb.n, g);
+        l = g - __ldg(tb.prefix + j);
+        return tb.args + j;
+      },
+      tb.total, smem, bar, pp, blockIdx.x, gridDim.x);
+}
+
+// Fused level-1/level-0 combine of the batch's images with >= 3 levels (no
+// gain map; the input's map is written per run).
+template <typename S>
+__global__ void __launch_bounds__(kThreads, 2) k_down10_batch(const BatchTable<Down10Args> tb) {
+  using SM = Smem<sizeof(typename Cplx<S>::T)>;
+  extern __shared__ __align__(128) unsigned char smem[];
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + SM::d10 - 64);
+  fence_maps(tb, [](const Down10Args& a) {
+    fence_tensormap(&a.z1map);
+    fence_tensormap(&a.g1map);
+    fence_tensormap(&a.z2map);
+    if (a.has_e2) fence_tensormap(&a.e2map);
+    if (a.use_tma) fence_tensormap(&a.imap);
+  });
+  init_bars(bar);
+  Pipe pp{};
+  stage_down10<S, false>(
       [&](int g, int& l) {
         const int j = find_entry(tb.prefix, tb.n, g);
         l = g - __ldg(tb.prefix + j);
@@ -1644,9 +1675,9 @@ int FLLF_LAUNCH_NAME(occupancy)(int kind, int batched) {
                            : resident_per_sm<k_up0<FLLF_STORAGE>>(SMS::up0, nullptr);
     case 1: return batched ? resident_per_sm<k_up_batch<FLLF_STORAGE>>(SMS::up, nullptr)
                            : resident_per_sm<k_up<FLLF_STORAGE>>(SMS::up, nullptr);
-    case 2: return batched ? resident_per_sm<k_down_batch<FLLF_STORAGE>>(SMS::dn1, nullptr)
+    case 2: return batched ? resident_per_sm<k_down_batch<FLLF_STORAGE>>(SMS::dns, nullptr)
                            : resident_per_sm<k_down<FLLF_STORAGE>>(SMS::dn1, nullptr);
-    case 3: return batched ? resident_per_sm<k_down0_batch<FLLF_STORAGE>>(SMS::dn, nullptr)
+    case 3: return batched ? resident_per_sm<k_down10_batch<FLLF_STORAGE>>(SMS::d10, nullptr)
                            : resident_per_sm<k_down10<FLLF_STORAGE, false>>(SMS::d10, nullptr);
     case 4: {
       constexpr size_t kChainSmem = SMS::up > SMS::dn1 ? SMS::up : SMS::dn1;
@@ -1689,8 +1720,13 @@ cudaError_t FLLF_LAUNCH_NAME(up_batch)(const BatchTable<UpArgs>& tb, cudaStream_
 }
 cudaError_t FLLF_LAUNCH_NAME(down_batch)(const BatchTable<DownArgs>& tb, cudaStream_t s, int cps) {
   if (tb.total <= 0) return cudaSuccess;
-  const int grid = persistent_grid<k_down_batch<FLLF_STORAGE>>(SMS::dn1, tb.total, cps);
-  return launch_pdl(k_down_batch<FLLF_STORAGE>, grid, SMS::dn1, s, tb);
+  const int grid = persistent_grid<k_down_batch<FLLF_STORAGE>>(SMS::dns, tb.total, cps);
+  return launch_pdl(k_down_batch<FLLF_STORAGE>, grid, SMS::dns, s, tb);
+}
+cudaError_t FLLF_LAUNCH_NAME(down10_batch)(const BatchTable<Down10Args>& tb, cudaStream_t s, int cps) {
+  if (tb.total <= 0) return cudaSuccess;
+  const int grid = persistent_grid<k_down10_batch<FLLF_STORAGE>>(SMS::d10, tb.total, cps);
+  return launch_pdl(k_down10_batch<FLLF_STORAGE>, grid, SMS::d10, s, tb);
 }
 cudaError_t FLLF_LAUNCH_NAME(down0_batch)(const BatchTable<Down0Args>& tb, cudaStream_t s, int cps) {
   if (tb.total <= 0) return cudaSuccess;

@@ -22,6 +22,7 @@ namespace fllf {
   cudaError_t launch_up_batch_##suffix(const BatchTable<UpArgs>& t, cudaStream_t s, int cps);            \
   cudaError_t launch_down_batch_##suffix(const BatchTable<DownArgs>& t, cudaStream_t s, int cps);        \
   cudaError_t launch_down0_batch_##suffix(const BatchTable<Down0Args>& t, cudaStream_t s, int cps);      \
+  cudaError_t launch_down10_batch_##suffix(const BatchTable<Down10Args>& t, cudaStream_t s, int cps);    \
   int launch_occupancy_##suffix(int kind, int batched);
 // REDUCE of one float plane (the gain map of pixel-adaptive runs).
 cudaError_t launch_map_reduce(const float* src, int sh, int sw, int spitch, float* dst, int dh, int dw,

@@ -122,6 +122,11 @@ int stage_occupancy(int prec, int kind, bool batched) {
   }
 }
 
+bool encode_image_map(CUtensorMap* m, const float* base, int W, int H, int C, uint32_t box_w, uint32_t box_h) {
+  if ((W % 4) != 0 || (reinterpret_cast<uintptr_t>(base) & 15) != 0) return false;
+  return encode3(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, base, W, H, C, 4ull * W, 4ull * W * H, box_w, box_h, 1);
+}
+
 bool build_maps(const fllf_params& p, const std::vector<Level>& lv, PathMaps* m) {
   const int L = p.levels;
   m->z_dn.assign(L, CUtensorMap{});
@@ -160,11 +165,11 @@ bool build_maps(const fllf_params& p, const std::vector<Level>& lv, PathMaps* m)
                    kD0IW, kDnOH, 1))
         return false;
     }
-    // the small-level combine (levels >= 2 as the fine level, >= 3 as the coarse one)
-    if (l >= 3 && !encode4(&m->z_cs[l], zdt, v.Z, v.w, v.h, p.K, p.C, zrow, zs * (uint64_t)v.zk,
+    // the small-tile combine (levels >= 1 as the fine level, >= 2 as the coarse one)
+    if (l >= 2 && !encode4(&m->z_cs[l], zdt, v.Z, v.w, v.h, p.K, p.C, zrow, zs * (uint64_t)v.zk,
                            zs * (uint64_t)v.zplane, kSmCW, kSmCH, kKCS))
       return false;
-    if (l >= 2 && l <= L - 2) {
+    if (l <= L - 2) {
       if (!encode4(&m->z_fs[l], zdt, v.Z, v.w, v.h, p.K, p.C, zrow, zs * (uint64_t)v.zk,
                    zs * (uint64_t)v.zplane, kSmIW, kSmH, kKCS))
         return false;
@@ -184,7 +189,7 @@ bool build_maps(const fllf_params& p, const std::vector<Level>& lv, PathMaps* m)
       if (!encode3(&m->e_dn[l], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, v.E, v.w, v.h, p.C, grow, gplane,
                    kDnCW, kDnCH, 1))
         return false;
-      if (l >= 3 && !encode3(&m->e_cs[l], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, v.E, v.w, v.h, p.C, grow,
+      if (l >= 2 && !encode3(&m->e_cs[l], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, v.E, v.w, v.h, p.C, grow,
                              gplane, kSmCW, kSmCH, 1))
         return false;
     }
@@ -240,11 +245,7 @@ cudaError_t enqueue_path(const fllf_params& p, const std::vector<Level>& lv, con
   u0.K = p.K;
   u0.turns = turns;
   u0.fault = fault;
-  u0.use_tma = ((p.W % 4) == 0 && (reinterpret_cast<uintptr_t>(d_in) & 15) == 0 &&
-                encode3(&u0.imap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, d_in, p.W, p.H, C,
-                        4ull * p.W, 4ull * p.W * p.H, kUpIW, kUpIR, 1))
-                   ? 1
-                   : 0;
+  u0.use_tma = encode_image_map(&u0.imap, d_in, p.W, p.H, C, kUpIW, kUpIR) ? 1 : 0;
   mark(FLLF_STAGE_UP0, true);
   if ((e = launch_up0(prec, u0, s, tn.cps[FLLF_STAGE_UP0])) != cudaSuccess) return e;
   mark(FLLF_STAGE_UP0, false);
@@ -352,10 +353,7 @@ cudaError_t enqueue_path(const fllf_params& p, const std::vector<Level>& lv, con
     d.has_e2 = (L >= 4) ? 1 : 0;
     d.M0 = d_gain;
     d.mscale = mscale;
-    d.use_tma = (u0.use_tma && encode3(&d.imap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, d_in, p.W, p.H, C,
-                                       4ull * p.W, 4ull * p.W * p.H, kD0IW, kDnOH, 1))
-                    ? 1
-                    : 0;
+    d.use_tma = (u0.use_tma && encode_image_map(&d.imap, d_in, p.W, p.H, C, kD0IW, kDnOH)) ? 1 : 0;
     d.fault = fault;
     mark(FLLF_STAGE_DOWN0, true);
     if ((e = launch_down10(prec, d, s, tn.cps[FLLF_STAGE_DOWN0])) != cudaSuccess) return e;

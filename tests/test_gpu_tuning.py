@@ -26,7 +26,7 @@ NST = len(pkg.STAGES)
 ALL = 1 << 40   # every combined level >= 2 on the small tiles
 
 
-def _tuning(chain, cps, rev, small=1 << 19):
+def _tuning(chain, cps, rev, small=ALL):
     t = pkg.fllf_tuning()
     t.chain_pixels = chain
     for i, c in enumerate(cps):
@@ -43,12 +43,12 @@ def test_every_launch_setting_gives_the_same_bits(precision):
     plan = pkg.fllf_plan_create(p, 0)
     try:
         d = pkg.fllf_plan_get_tuning(plan).as_dict()
-        assert d["chain_pixels"] == 1 << 21 and d["reduce_reverse"] == 1 and d["small_pixels"] == 1 << 19
+        assert d["chain_pixels"] == 0 and d["reduce_reverse"] == 1 and d["small_pixels"] == ALL
         x = torch.from_numpy(img).cuda()
         outs = []
         for t in (_tuning(1 << 21, [0] * NST, 1), _tuning(0, [0] * NST, 0), _tuning(1 << 23, [1] * NST, 1),
                   _tuning(1 << 15, [2, 1, 1, 1, 1, 2], 0), _tuning(0, [0] * NST, 1, small=0),
-                  _tuning(0, [0] * NST, 1, small=ALL), _tuning(1 << 17, [0, 0, 0, 0, 0, 1], 1, small=ALL)):
+                  _tuning(0, [0] * NST, 1, small=1 << 19), _tuning(1 << 17, [0, 0, 0, 0, 0, 1], 1, small=ALL)):
             pkg.fllf_plan_set_tuning(plan, t)
             y = torch.full_like(x, float("nan"))
             pkg.run_tensor(plan, x, y)
@@ -139,7 +139,7 @@ def test_autotune_keeps_a_valid_setting_and_the_output():
         d = t.as_dict()
         assert d["chain_pixels"] in (0, 1 << 15, 1 << 17, 1 << 19, 1 << 21, 1 << 23)
         sizes = [h * w * 3 for h, w in o.level_shapes(540, 960, 7)[2:6]]
-        assert d["small_pixels"] in [0, 1 << 19] + sizes
+        assert d["small_pixels"] in [0, ALL] + sizes
         assert all(0 <= c <= 32 for c in d["ctas_per_sm"].values())
         z = torch.full_like(x, float("nan"))
         pkg.run_tensor(plan, x, z)
