@@ -18,6 +18,9 @@ It is a plain, slow, obviously-correct restatement of Sumiya et al.,
                    on the whole image or on exact dependency windows.
 * ``*_adaptive``   the pixel-by-pixel parameter of Sec. III-B (a gain map).
 * ``fourier_llf_luma``  colour by LLF on the Y of YUV (Sec. IV).
+* ``fast_llf``     fast LLF (Aubry et al.), the method the paper compares
+                   against (Sec. II-D): S remapped pyramids interpolated by
+                   the guide.
 
 Every function is pinned by ``tests/test_oracle_*.py`` against facts the
 paper or the mathematics fixes (library routines, closed forms, invariants,
@@ -33,6 +36,7 @@ from .remap import (remap_detail, remap, omegas, coeffs_quadrature,
 from .fourier_llf import (fourier_llf, fourier_llf_levels, fourier_llf_adaptive, fourier_llf_luma,
                           rgb_to_yuv, yuv_to_rgb, LUMA_BT601)
 from .naive_llf import naive_llf, naive_llf_adaptive
+from .fast_llf import fast_llf, fast_samples, fast_bracket
 
 __all__ = [
     "reflect101", "reduce", "expand", "gaussian_pyramid", "laplacian_pyramid",
@@ -41,5 +45,5 @@ __all__ = [
     "coeffs_closed_form", "fourier_detail", "period_error", "optimal_period",
     "coeff_tail_bound", "fourier_llf", "fourier_llf_levels", "naive_llf",
     "fourier_llf_adaptive", "naive_llf_adaptive", "fourier_llf_luma", "rgb_to_yuv",
-    "yuv_to_rgb", "LUMA_BT601",
+    "yuv_to_rgb", "LUMA_BT601", "fast_llf", "fast_samples", "fast_bracket",
 ]

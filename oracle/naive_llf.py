@@ -20,6 +20,8 @@ the windowed value equals the whole-image value; a test checks this.
 
 ``f`` is any vectorised callable d -> f(d): the exact remap detail, its
 Fourier approximation f_K, or a linear f for the closed-form check.
+``remap_fn`` (optional) replaces the whole remap by any vectorised
+(i, g) -> r(i, g), for remaps that are not a function of i - g alone.
 """
 
 import numpy as np
@@ -29,13 +31,17 @@ from .pyramid import gaussian_pyramid, reduce, expand, collapse, coarse_size
 _MAX_BATCH_ELEMS = 1 << 22
 
 
-def _laplacian_at(windows, g, f, level, ly, lx, s=None):
+def _laplacian_at(windows, g, f, level, ly, lx, s=None, remap_fn=None):
     """Coefficient L_level[w + s f(w - g)] at local level positions (ly, lx), batched.
 
     ``s`` (one value per coefficient, default 1) scales the remap detail: the
-    pixel-by-pixel parameter of Sec. III-B."""
-    d = f(windows - g[:, None, None])
-    r = windows + (d if s is None else s[:, None, None] * d)
+    pixel-by-pixel parameter of Sec. III-B.  With ``remap_fn`` the remapped
+    window is remap_fn(w, g) instead."""
+    if remap_fn is not None:
+        r = remap_fn(windows, g[:, None, None])
+    else:
+        d = f(windows - g[:, None, None])
+        r = windows + (d if s is None else s[:, None, None] * d)
     for _ in range(level):
         r = reduce(r)
     coarse = reduce(r)
@@ -52,7 +58,7 @@ def _window_1d(p, level, n, margin):
     return lo, hi
 
 
-def _level_coefficients(img, gl, level, f, window, scale=None):
+def _level_coefficients(img, gl, level, f, window, scale=None, remap_fn=None):
     """L_level[O] for every pixel of one level (level < top); ``scale``: per-pixel
     detail scale at this level (same shape as gl) or None."""
     h0, w0 = img.shape
@@ -80,21 +86,23 @@ def _level_coefficients(img, gl, level, f, window, scale=None):
             win = img[rows[:, :, None], cols[:, None, :]]
             ly = py[idx] - y0[idx] // 2 ** level
             lx = px[idx] - x0[idx] // 2 ** level
-            out[idx] = _laplacian_at(win, g[idx], f, level, ly, lx, None if sc is None else sc[idx])
+            out[idx] = _laplacian_at(win, g[idx], f, level, ly, lx, None if sc is None else sc[idx],
+                                     remap_fn)
     return out.reshape(hl, wl)
 
 
-def naive_llf(img, levels, f, window=True, scale=None):
+def naive_llf(img, levels, f, window=True, scale=None, remap_fn=None):
     """Naive LLF of a plane (H, W) or planar channels (C, H, W); float64.
 
     ``scale``: optional list of per-level arrays (level l shaped like G_l);
     the coefficient at (l, p) then remaps with r = I + scale[l]_p f(I - g),
-    i.e. a pixel-by-pixel remap parameter (Sec. III-B)."""
+    i.e. a pixel-by-pixel remap parameter (Sec. III-B).  ``remap_fn``:
+    optional (i, g) -> r(i, g) used instead of I + f(I - g)."""
     img = np.asarray(img, dtype=np.float64)
     if img.ndim == 3:
-        return np.stack([naive_llf(ch, levels, f, window, scale) for ch in img])
+        return np.stack([naive_llf(ch, levels, f, window, scale, remap_fn) for ch in img])
     g = gaussian_pyramid(img, levels)
-    lap_o = [_level_coefficients(img, g[l], l, f, window, None if scale is None else scale[l])
+    lap_o = [_level_coefficients(img, g[l], l, f, window, None if scale is None else scale[l], remap_fn)
              for l in range(levels - 1)]
     lap_o.append(g[-1])
     return collapse(lap_o)
