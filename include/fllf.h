@@ -65,6 +65,21 @@ typedef enum {
   FLLF_COEFF_CLOSED_FORM = 1 /* Eqs. (9)-(11): (m-1) 2 sigma_r^2 alpha_k omega_k */
 } fllf_coeff_mode;
 
+/* Which local Laplacian filter a plan computes. */
+typedef enum {
+  FLLF_METHOD_FOURIER = 0, /* Fourier LLF (Sec. III, Eq. (14)): 2K+1 pyramids */
+  FLLF_METHOD_FAST = 1     /* fast LLF (Sec. II-D), the paper's comparison method:
+                            * S samples g_j = j / (S - 1) of [0, 1], the Laplacian
+                            * pyramids of the remapped images r(I, g_j) with the
+                            * exact remap, linearly interpolated at each pixel
+                            * between the two samples bracketing G_l[I]_p; S + 1
+                            * pyramids.  The S sampled pyramids are held as
+                            * ceil(S/2) complex planes (pairs of samples), so a
+                            * fast plan's K is ceil(S/2); K, T and coeff_mode are
+                            * not used.  Not available in batches, the server or
+                            * fllf_run_adaptive. */
+} fllf_method;
+
 typedef struct {
   int H, W;          /* image size, >= 1 each */
   int C;             /* planes filtered independently (1 = gray, 3 = planar RGB), 1..64 */
@@ -75,6 +90,8 @@ typedef struct {
   double T;          /* Fourier period, > 0 (2 covers differences in [-1, 1]) */
   int precision;     /* fllf_precision */
   int coeff_mode;    /* fllf_coeff_mode */
+  int method;        /* fllf_method (0: Fourier LLF) */
+  int samples;       /* fast LLF: intensity samples S, 2..128 (unused by Fourier LLF) */
 } fllf_params;
 
 typedef struct fllf_plan fllf_plan;

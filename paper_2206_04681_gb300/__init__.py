@@ -7,7 +7,8 @@ the C ABI of ``include/fllf.h``).  This package holds the ctypes binding
 memory and streams.
 """
 
-from ._lib import (FllfError, fllf_params, make_params, lib, fllf_params_validate, fllf_coeffs,
+from ._lib import (FllfError, fllf_params, make_params, make_fast_params, lib,
+                   FLLF_METHOD_FOURIER, FLLF_METHOD_FAST, fllf_params_validate, fllf_coeffs,
                    fllf_optimal_period, fllf_run_adaptive, fllf_run_luma, fllf_tuning,
                    fllf_plan_get_tuning, fllf_plan_set_tuning, fllf_plan_autotune,
                    fllf_plan_set_timing_mask,

@@ -15,6 +15,7 @@ LIB_PATH = os.path.join(PKG, "libfllf.so")
 FLLF_OK, FLLF_EINVAL, FLLF_ENOMEM, FLLF_ECUDA, FLLF_EAGAIN, FLLF_ETIMEOUT, FLLF_EBUSY = range(7)
 FLLF_FP32, FLLF_FP16, FLLF_BF16 = 0, 1, 2
 FLLF_COEFF_QUADRATURE, FLLF_COEFF_CLOSED_FORM = 0, 1
+FLLF_METHOD_FOURIER, FLLF_METHOD_FAST = 0, 1
 PRECISIONS = {"fp32": FLLF_FP32, "fp16": FLLF_FP16, "bf16": FLLF_BF16}
 
 
@@ -29,7 +30,8 @@ class fllf_params(ctypes.Structure):
     _fields_ = [("H", ctypes.c_int), ("W", ctypes.c_int), ("C", ctypes.c_int),
                 ("levels", ctypes.c_int), ("K", ctypes.c_int),
                 ("m", ctypes.c_double), ("sigma_r", ctypes.c_double), ("T", ctypes.c_double),
-                ("precision", ctypes.c_int), ("coeff_mode", ctypes.c_int)]
+                ("precision", ctypes.c_int), ("coeff_mode", ctypes.c_int),
+                ("method", ctypes.c_int), ("samples", ctypes.c_int)]
 
 
 class fllf_server_stats(ctypes.Structure):
@@ -137,11 +139,17 @@ def _check(status):
 
 
 def make_params(H, W, C=1, levels=5, K=8, m=3.0, sigma_r=0.2, T=2.0, precision=FLLF_FP32,
-                coeff_mode=FLLF_COEFF_QUADRATURE):
+                coeff_mode=FLLF_COEFF_QUADRATURE, method=FLLF_METHOD_FOURIER, samples=0):
     if isinstance(precision, str):
         precision = PRECISIONS[precision]
     return fllf_params(int(H), int(W), int(C), int(levels), int(K), float(m), float(sigma_r),
-                       float(T), int(precision), int(coeff_mode))
+                       float(T), int(precision), int(coeff_mode), int(method), int(samples))
+
+
+def make_fast_params(H, W, C=1, levels=5, samples=16, m=3.0, sigma_r=0.2, precision=FLLF_FP32):
+    """Parameters of a fast LLF plan (Sec. II-D) with S = ``samples``."""
+    return make_params(H, W, C, levels, 1, m, sigma_r, 2.0, precision, FLLF_COEFF_QUADRATURE,
+                       FLLF_METHOD_FAST, samples)
 
 
 def fllf_params_validate(p):

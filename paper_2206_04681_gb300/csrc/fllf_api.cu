@@ -114,16 +114,35 @@ fllf_status validate(const fllf_params* p) {
     return fail(FLLF_EINVAL, "H and W must be in [1, 65536]");
   if (p->C < 1 || p->C > 64) return fail(FLLF_EINVAL, "C must be in [1, 64]");
   if (p->levels < 1 || p->levels > 16) return fail(FLLF_EINVAL, "levels must be in [1, 16]");
-  if (p->K < 1 || p->K > 64) return fail(FLLF_EINVAL, "K must be in [1, 64]");
+  if (p->method != FLLF_METHOD_FOURIER && p->method != FLLF_METHOD_FAST)
+    return fail(FLLF_EINVAL, "method must be FLLF_METHOD_FOURIER or FLLF_METHOD_FAST");
+  const bool fast = p->method == FLLF_METHOD_FAST;
+  if (fast && (p->samples < 2 || p->samples > 128)) return fail(FLLF_EINVAL, "samples must be in [2, 128]");
+  if (!fast && (p->K < 1 || p->K > 64)) return fail(FLLF_EINVAL, "K must be in [1, 64]");
   if (!std::isfinite(p->m)) return fail(FLLF_EINVAL, "m must be finite");
   if (!(p->sigma_r > 0.0) || !std::isfinite(p->sigma_r))
     return fail(FLLF_EINVAL, "sigma_r must be finite and > 0");
-  if (!(p->T > 0.0) || !std::isfinite(p->T)) return fail(FLLF_EINVAL, "T must be finite and > 0");
+  if (!fast && (!(p->T > 0.0) || !std::isfinite(p->T))) return fail(FLLF_EINVAL, "T must be finite and > 0");
   if (p->precision < FLLF_FP32 || p->precision > FLLF_BF16)
     return fail(FLLF_EINVAL, "precision must be FLLF_FP32, FLLF_FP16 or FLLF_BF16");
-  if (p->coeff_mode != FLLF_COEFF_QUADRATURE && p->coeff_mode != FLLF_COEFF_CLOSED_FORM)
+  if (!fast && p->coeff_mode != FLLF_COEFF_QUADRATURE && p->coeff_mode != FLLF_COEFF_CLOSED_FORM)
     return fail(FLLF_EINVAL, "coeff_mode must be quadrature or closed form");
   return FLLF_OK;
+}
+
+// A fast LLF plan holds its S sampled pyramids as ceil(S/2) complex planes:
+// every pyramid, map and kernel sees K = ceil(S/2); T and coeff_mode are
+// fixed to values that the Fourier-only code paths accept.
+fllf_params normalized(const fllf_params& p) {
+  fllf_params q = p;
+  if (p.method == FLLF_METHOD_FAST) {
+    q.K = (p.samples + 1) / 2;
+    q.T = 2.0;
+    q.coeff_mode = FLLF_COEFF_QUADRATURE;
+  } else {
+    q.samples = 0;
+  }
+  return q;
 }
 
 // Scratch layout: per level l = 1..levels-1, G_l, Z_l and (l <= levels-2) E_l
@@ -299,6 +318,7 @@ fllf_status fllf_coeffs(const fllf_params* p, double* a_out) {
   fllf_status st = validate(p);
   if (st != FLLF_OK) return st;
   if (!a_out) return fail(FLLF_EINVAL, "a_out is NULL");
+  if (p->method == FLLF_METHOD_FAST) return fail(FLLF_EINVAL, "fast LLF has no Fourier coefficients");
   compute_coeffs(*p, a_out);
   return FLLF_OK;
 }
@@ -313,14 +333,16 @@ fllf_status fllf_optimal_period(double sigma_r, int K, double R, double* T_out) 
 
 size_t fllf_plan_scratch_bytes(const fllf_params* p) {
   if (validate(p) != FLLF_OK) return 0;
-  return layout(*p, nullptr);
+  return layout(normalized(*p), nullptr);
 }
 
-fllf_status fllf_plan_create(const fllf_params* p, int device, fllf_plan** out) {
+fllf_status fllf_plan_create(const fllf_params* user, int device, fllf_plan** out) {
   if (!out) return fail(FLLF_EINVAL, "out is NULL");
   *out = nullptr;
-  fllf_status st = validate(p);
+  fllf_status st = validate(user);
   if (st != FLLF_OK) return st;
+  const fllf_params np = normalized(*user);
+  const fllf_params* p = &np;
   int ndev = 0;
   cudaError_t e = cudaGetDeviceCount(&ndev);
   if (e != cudaSuccess) return cuda_fail(e, "cudaGetDeviceCount");
@@ -332,8 +354,8 @@ fllf_status fllf_plan_create(const fllf_params* p, int device, fllf_plan** out) 
   if (!pl) return fail(FLLF_ENOMEM, "host allocation of the plan failed");
   pl->p = *p;
   pl->device = device;
-  pl->a64.assign(p->K, 0.0);
-  compute_coeffs(*p, pl->a64.data());
+  pl->a64.assign(p->K, 0.0);   // fast LLF: zeros (unused)
+  if (p->method == FLLF_METHOD_FOURIER) compute_coeffs(*p, pl->a64.data());
   std::vector<float> a32(p->K);
   for (int k = 0; k < p->K; ++k) a32[k] = (float)pl->a64[k];
 
@@ -434,6 +456,7 @@ fllf_status fllf_run_adaptive(fllf_plan* plan, const float* d_in, const float* d
   if (!plan) return fail(FLLF_EINVAL, "plan is NULL");
   if (!d_in || !d_out || !d_gain) return fail(FLLF_EINVAL, "input, gain or output pointer is NULL");
   const fllf_params& p = plan->p;
+  if (p.method != FLLF_METHOD_FOURIER) return fail(FLLF_EINVAL, "fllf_run_adaptive needs a Fourier LLF plan");
   if (p.m == 1.0)
     return fail(FLLF_EINVAL, "fllf_run_adaptive needs a plan with m != 1 (its coefficients are rescaled "
                              "per pixel by (m_p - 1) / (m - 1))");

@@ -329,6 +329,8 @@ fllf_status fllf_batch_create(fllf_plan* const* plans, int n, fllf_batch** out) 
   for (int i = 1; i < n; ++i)
     if (plans[i]->device != dev || plans[i]->p.precision != prec)
       return bfail(FLLF_EINVAL, "all plans of a batch need the same device and precision");
+  for (int i = 0; i < n; ++i)
+    if (plans[i]->p.method != FLLF_METHOD_FOURIER) return bfail(FLLF_EINVAL, "batches hold Fourier LLF plans only");
   DeviceScope scope(dev);
   if (!scope.ok) return bfail(FLLF_ECUDA, "cudaSetDevice failed");
   fllf_batch* b = new (std::nothrow) fllf_batch();

@@ -71,6 +71,16 @@ struct Level {
 // (x = column, y = row, z = plane); Z maps read by a REDUCE have
 // z = plane * K + k, Z maps read by a combine are 4-D (column, row, order,
 // plane), so that orders k >= K of a chunk read as zeros.
+// Fast LLF (Sec. II-D): S samples g_j = tau j of [0, 1] and the sampled
+// detail images F_j = f(I - g_j), f(d) = fm1 d 2^(-c2 d^2) (the Gaussian
+// detail with fm1 = m - 1, c2 = log2(e) / (2 sigma_r^2)); F_{2k} and F_{2k+1}
+// are the real and imaginary parts of complex plane k (the imaginary part of
+// the last plane is zero when S is odd).  S = 0: Fourier LLF.
+struct FastArgs {
+  int S;
+  float tau, fm1, c2;
+};
+
 struct Up0Args {
   CUtensorMap imap;     // level-0 input (valid when use_tma)
   const float* I;       // level-0 input planes, pitch w0, plane stride h0*w0
@@ -81,6 +91,7 @@ struct Up0Args {
   float turns;          // 2/T: w_1 x = pi * (turns * x)
   int use_tma;          // input rows 16-byte aligned (w0 % 4 == 0, aligned base)
   unsigned* fault;      // bounded-wait fault word
+  FastArgs fast;        // fast LLF: plane k holds (F_{2k}, F_{2k+1}) unweighted
 };
 
 struct UpArgs {
@@ -109,6 +120,7 @@ struct DownArgs {
   int has_e;            // E_{l+1} exists (l+1 <= levels-2)
   float mscale;         // 1/(m - 1): the gain map's scale of the Fourier term (fine.M set)
   unsigned* fault;
+  FastArgs fast;        // fast LLF: interpolate the bracketing samples' differences
 };
 
 struct Down0Args {
@@ -124,6 +136,7 @@ struct Down0Args {
   const float* M0;      // level-0 gain map (pitch w0) of pixel-adaptive runs, else null
   float mscale;         // 1/(m - 1)
   unsigned* fault;
+  FastArgs fast;        // fast LLF
 };
 
 // Fused combine of levels 1 and 0 (levels >= 3): the level-1 combine runs on
@@ -350,6 +363,18 @@ __device__ __forceinline__ float2 horner(float2 P, float2 w, float2 D) {
   return make_float2(fmaf(P.x, w.x, fmaf(-P.y, w.y, D.x)), fmaf(P.x, w.y, fmaf(P.y, w.x, D.y)));
 }
 __device__ __forceinline__ float im_mul(float2 P, float2 w) { return fmaf(P.x, w.y, P.y * w.x); }
+
+// Fast LLF: the sampled detail f(i - g_j) and the hat weight of sample s at
+// t = g (S - 1) clamped to [0, S-1], which is 1 - a for the lower and a for
+// the upper of the two samples bracketing g and 0 for the others.
+__device__ __forceinline__ float fast_detail(const FastArgs& f, float i, int j) {
+  const float d = fmaf(-f.tau, (float)j, i);
+  return f.fm1 * d * exp2f(-f.c2 * d * d);
+}
+__device__ __forceinline__ float fast_pos(const FastArgs& f, float g) {
+  return fminf(fmaxf(g * (float)(f.S - 1), 0.f), (float)(f.S - 1));
+}
+__device__ __forceinline__ float fast_hat(float t, int s) { return fmaxf(0.f, 1.f - fabsf(t - (float)s)); }
 
 // 5-tap binomial sums without the 1/16.
 __device__ __forceinline__ float tap5(float a, float b, float c, float d, float e) {

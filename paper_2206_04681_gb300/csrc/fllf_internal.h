@@ -13,6 +13,9 @@ namespace fllf {
 
 void set_last_error(const std::string& s);
 fllf_status validate(const fllf_params* p);
+// The parameters a plan runs with: for fast LLF, K = ceil(samples / 2) (the
+// complex planes holding the sampled pyramids).
+fllf_params normalized(const fllf_params& p);
 // a_1..a_K in float64 (quadrature over one period, or the closed form).
 void compute_coeffs(const fllf_params& p, double* a);
 // Scratch layout of a plan; returns its size in bytes.  With `out`, fills

@@ -85,7 +85,10 @@ __device__ __forceinline__ int up0_tiles(const Up0Args& a) {
   return cdiv(a.dst.w, kUpTW) * cdiv(a.dst.h, kUpTH) * a.planes;
 }
 
-template <typename S, typename Res>
+// FAST: fast LLF (Sec. II-D) instead: complex plane k of a fine pixel is
+// (F_{2k}, F_{2k+1}), the sampled detail images, computed per chunk from the
+// pixel value (no recurrence), and stored unweighted.
+template <typename S, bool FAST = false, typename Res>
 __device__ __forceinline__ bool stage_up0(Res res, int total, unsigned char* smem, uint64_t* bar,
                                           Pipe& pp, int b, int G) {
   using CT = typename Cplx<S>::T;
@@ -156,8 +159,8 @@ __device__ __forceinline__ bool stage_up0(Res res, int total, unsigned char* sme
     float2* hzw = hz + s * (kKC * kUpRun * kUpCS);  // [order][column][fine row]
     float* hgw = hg + s * (kUpRun * kUpCS);          // [column][fine row]
     float2 zc[kUpIPX], zp[kUpIPX], tc[kUpIPX];
+    float v[kUpIPX];
     {
-      float v[kUpIPX];
       {
         const float4* row = reinterpret_cast<const float4*>(it + rl * kUpIW + 2 * kUpRun * s);
         const float4 q0 = row[0], q1 = row[1], q2 = row[2], q3 = row[3];
@@ -166,12 +169,14 @@ __device__ __forceinline__ bool stage_up0(Res res, int total, unsigned char* sme
         v[6] = q2.x; v[7] = q2.y; v[8] = q2.z; v[9] = q2.w;
         v[10] = q3.x;
       }
+      if constexpr (!FAST) {
 #pragma unroll
-      for (int j = 0; j < kUpIPX; ++j) {
-        const float2 z = cos_sin_turns(a.turns * v[j]);
-        zc[j] = z;
-        zp[j] = make_float2(1.f, 0.f);
-        tc[j] = splat(2.f * z.x);
+        for (int j = 0; j < kUpIPX; ++j) {
+          const float2 z = cos_sin_turns(a.turns * v[j]);
+          zc[j] = z;
+          zp[j] = make_float2(1.f, 0.f);
+          tc[j] = splat(2.f * z.x);
+        }
       }
 #pragma unroll
       for (int q = 0; q < kUpRun; ++q)
@@ -191,15 +196,24 @@ __device__ __forceinline__ bool stage_up0(Res res, int total, unsigned char* sme
       {
 #pragma unroll
         for (int kk = 0; kk < kKC; ++kk) {
+          if constexpr (FAST) {
+            const int s0 = 2 * (ch * kKC + kk);
+            const bool s1 = s0 + 1 < a.fast.S;
+#pragma unroll
+            for (int j = 0; j < kUpIPX; ++j)
+              zc[j] = make_float2(fast_detail(a.fast, v[j], s0), s1 ? fast_detail(a.fast, v[j], s0 + 1) : 0.f);
+          }
 #pragma unroll
           for (int q = 0; q < kUpRun; ++q)
             hzw[(kk * kUpRun + q) * kUpCS + r] =
                 tap5(zc[2 * q], zc[2 * q + 1], zc[2 * q + 2], zc[2 * q + 3], zc[2 * q + 4]);
+          if constexpr (!FAST) {
 #pragma unroll
-          for (int j = 0; j < kUpIPX; ++j) {
-            const float2 zn = fma2(tc[j], zc[j], make_float2(-zp[j].x, -zp[j].y));
-            zp[j] = zc[j];
-            zc[j] = zn;
+            for (int j = 0; j < kUpIPX; ++j) {
+              const float2 zn = fma2(tc[j], zc[j], make_float2(-zp[j].x, -zp[j].y));
+              zp[j] = zc[j];
+              zc[j] = zn;
+            }
           }
         }
       }
@@ -210,7 +224,7 @@ __device__ __forceinline__ bool stage_up0(Res res, int total, unsigned char* sme
         const bool uniform = full && (ch + 1) * kKC <= a.K;
         if (uniform || (k < a.K && xo < a.dst.w)) {
           // order k is stored weighted by its coefficient: a_k Z_{1,k}
-          const float sk = __ldg(a.a + k) * (1.f / 256.f);
+          const float sk = FAST ? (1.f / 256.f) : __ldg(a.a + k) * (1.f / 256.f);
           CT* Zk = reinterpret_cast<CT*>(a.dst.Z) + (long long)pl * a.dst.zplane +
                    (long long)k * a.dst.zk + xo + (long long)(Y1 + vgrp * kUpVRows) * a.dst.pitch;
           const float4* p =
@@ -505,11 +519,12 @@ struct CombineView {
   const Level* coarse;
   unsigned* fault;
   const float* M0;
+  const FastArgs* fast;
   int h, w, planes, K, has_e;
   float turns, mscale;
 };
 __device__ __forceinline__ CombineView view_of(const Down0Args& d) {
-  return CombineView{&d.zmap, &d.emap, d.I, d.O, &d.coarse, d.fault, d.M0,
+  return CombineView{&d.zmap, &d.emap, d.I, d.O, &d.coarse, d.fault, d.M0, &d.fast,
                      d.h0, d.w0, d.planes, d.K, d.has_e, d.turns, d.mscale};
 }
 __device__ __forceinline__ int combine_tiles(int h, int w, int planes) {
@@ -518,8 +533,11 @@ __device__ __forceinline__ int combine_tiles(int h, int w, int planes) {
 __device__ __forceinline__ int combine_tiles(const CombineView& v) { return combine_tiles(v.h, v.w, v.planes); }
 
 // Level-0 combine alone (levels == 2, where E_1 = 0 and no level-1 combine
-// exists, and the batched path).
-template <typename S, typename Res>
+// exists, the batched path, and fast LLF).
+// FAST: fast LLF (Sec. II-D) at level 0: the level-0 sampled details are
+// evaluated at the pixel, (1 - a) F_j + a F_{j+1} for the samples bracketing
+// g = I_p, and the EXPAND of every plane is weighted by the same hat weights.
+template <typename S, bool FAST = false, typename Res>
 __device__ __forceinline__ bool stage_combine0(Res res, int total, unsigned char* smem, uint64_t* bar,
                                                Pipe& pp, int b, int G) {
   using CT = typename Cplx<S>::T;
@@ -579,10 +597,23 @@ __device__ __forceinline__ bool stage_combine0(Res res, int total, unsigned char
       for (int q = 0; q < 4; ++q) {
         const int xq = min(max(fx + q, 0), w - 1);
         const float g0 = __ldg(gsrc + (long long)y0c * w + xq), g1 = __ldg(gsrc + (long long)y1c * w + xq);
-        we[q] = conj_turns(v.turns * g0);
-        wo[q] = conj_turns(v.turns * g1);
         Pe[q] = Po[q] = splat(0.f);
-        base[q] = make_float2(g0, g1);
+        if constexpr (FAST) {
+          const FastArgs& fa = *v.fast;
+          auto level0 = [&](float g, float t) {   // (1 - a) F_j(p) + a F_{j+1}(p) at g = I_p
+            const int j = min((int)t, fa.S - 2);
+            const float al = t - (float)j;
+            return fmaf(al, fast_detail(fa, g, j + 1), (1.f - al) * fast_detail(fa, g, j));
+          };
+          const float t0 = fast_pos(fa, g0), t1 = fast_pos(fa, g1);
+          we[q] = make_float2(t0, 0.f);
+          wo[q] = make_float2(t1, 0.f);
+          base[q] = make_float2(g0 + level0(g0, t0), g1 + level0(g1, t1));
+        } else {
+          we[q] = conj_turns(v.turns * g0);
+          wo[q] = conj_turns(v.turns * g1);
+          base[q] = make_float2(g0, g1);
+        }
       }
     }
     if (!mbar_wait_cta(&bar[buf], pp.use[buf] & 1, v.fault)) {
@@ -610,10 +641,19 @@ __device__ __forceinline__ bool stage_combine0(Res res, int total, unsigned char
     for (int kk = kKC - 1; kk >= 0; --kk) {
       float2 ue[4], uo[4];
       expand_2x4<S>(zw + kk * kDnCH * kDnCW, ue, uo);
+      if constexpr (FAST) {
+        const int s0 = 2 * (ch * kKC + kk);
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        Pe[q] = horner(Pe[q], we[q], ue[q]);
-        Po[q] = horner(Po[q], wo[q], uo[q]);
+        for (int q = 0; q < 4; ++q) {
+          Pe[q].x = fmaf(fast_hat(we[q].x, s0 + 1), ue[q].y, fmaf(fast_hat(we[q].x, s0), ue[q].x, Pe[q].x));
+          Po[q].x = fmaf(fast_hat(wo[q].x, s0 + 1), uo[q].y, fmaf(fast_hat(wo[q].x, s0), uo[q].x, Po[q].x));
+        }
+      } else {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          Pe[q] = horner(Pe[q], we[q], ue[q]);
+          Po[q] = horner(Po[q], wo[q], uo[q]);
+        }
       }
     }
     if (last) {
@@ -628,7 +668,9 @@ __device__ __forceinline__ bool stage_combine0(Res res, int total, unsigned char
             const int x = fx + q;
             // the EXPAND weight and the sign of D_k are applied here
             const float2 sc = expand_scale_pair(q);
-            float delta = rr ? -sc.y * im_mul(Po[q], wo[q]) : -sc.x * im_mul(Pe[q], we[q]);
+            float delta;
+            if constexpr (FAST) delta = rr ? -sc.y * Po[q].x : -sc.x * Pe[q].x;
+            else delta = rr ? -sc.y * im_mul(Po[q], wo[q]) : -sc.x * im_mul(Pe[q], we[q]);
             if (x >= 0 && x < w) {
               if (v.M0) delta *= (__ldg(v.M0 + (long long)y * w + x) - 1.f) * v.mscale;
               d[x] = (rr ? base[q].y : base[q].x) + delta;
@@ -837,7 +879,12 @@ __device__ __forceinline__ bool stage_combine1(Res res, int total, unsigned char
 // sum is written once for both column parities: u = a v1 + (b v0 + v2) with
 // (a, b) = (6, 1) for an even column and (1, 0) for an odd one, whose
 // v1 + (0 v0 + v2) rounds exactly as v1 + v2.
-template <typename S, typename Res>
+//
+// FAST: fast LLF (Sec. II-D).  The planes hold the sampled detail images, and
+// the pixel's difference is interpolated between the two samples bracketing
+// g = G_l[I]_p: Delta = sum_s hat_s(g) (F_{l,s} - up F_{l+1,s}), with the hat
+// weights 1 - a, a of the bracketing pair and 0 elsewhere.
+template <typename S, bool FAST = false, typename Res>
 __device__ __forceinline__ bool stage_combine_s(Res res, int total, unsigned char* smem, uint64_t* bar,
                                                 Pipe& pp, int b, int G) {
   using CT = typename Cplx<S>::T;
@@ -916,8 +963,14 @@ __device__ __forceinline__ bool stage_combine_s(Res res, int total, unsigned cha
       // staged fine pixel (fy + rr, fx) at row 2 tr + rr, column tc + 2 (zero
       // outside the level; those pixels are not stored)
       const float* gb = reinterpret_cast<const float*>(bufp(buf) + kOffG) + 2 * tr * kSmIW + tc + 2;
-      we = conj_turns(a->turns * gb[0]);
-      wo = conj_turns(a->turns * gb[kSmIW]);
+      if constexpr (FAST) {
+        // sample positions t = g (S - 1) of the two pixels
+        we = make_float2(fast_pos(a->fast, gb[0]), 0.f);
+        wo = make_float2(fast_pos(a->fast, gb[kSmIW]), 0.f);
+      } else {
+        we = conj_turns(a->turns * gb[0]);
+        wo = conj_turns(a->turns * gb[kSmIW]);
+      }
       Pe = Po = splat(0.f);
       base = splat(0.f);
       if (a->has_e) {
@@ -952,8 +1005,15 @@ __device__ __forceinline__ bool stage_combine_s(Res res, int total, unsigned cha
       const float2 uo = fma2(ha, vo[1], fma2(hb, vo[0], vo[2]));
       const CT* fr = zfw + kk * kSmH * kSmIW;
       const float2 fe = Cplx<S>::cvt(fr[0]), fo = Cplx<S>::cvt(fr[kSmIW]);
-      Pe = horner(Pe, we, fma2(splat(-sc.x), ue, fe));
-      Po = horner(Po, wo, fma2(splat(-sc.y), uo, fo));
+      if constexpr (FAST) {
+        const int s0 = 2 * (ch * kKCS + kk);
+        const float2 de = fma2(splat(-sc.x), ue, fe), dd = fma2(splat(-sc.y), uo, fo);
+        Pe.x = fmaf(fast_hat(we.x, s0 + 1), de.y, fmaf(fast_hat(we.x, s0), de.x, Pe.x));
+        Po.x = fmaf(fast_hat(wo.x, s0 + 1), dd.y, fmaf(fast_hat(wo.x, s0), dd.x, Po.x));
+      } else {
+        Pe = horner(Pe, we, fma2(splat(-sc.x), ue, fe));
+        Po = horner(Po, wo, fma2(splat(-sc.y), uo, fo));
+      }
     }
     if (last && fx >= 0 && fx < w) {
       float* dst = a->fine.E + (long long)pl * a->fine.gplane + fx;
@@ -961,7 +1021,9 @@ __device__ __forceinline__ bool stage_combine_s(Res res, int total, unsigned cha
       for (int rr = 0; rr < 2; ++rr) {
         const int y = fy + rr;
         if (y < h) {
-          float delta = rr ? im_mul(Po, wo) : im_mul(Pe, we);
+          float delta;
+          if constexpr (FAST) delta = rr ? Po.x : Pe.x;
+          else delta = rr ? im_mul(Po, wo) : im_mul(Pe, we);
           if (a->fine.M) delta *= (__ldg(a->fine.M + (long long)y * a->fine.pitch + fx) - 1.f) * a->mscale;
           dst[(long long)y * a->fine.pitch] = (rr ? base.y : base.x) + delta;
         }
@@ -1262,14 +1324,14 @@ __device__ __forceinline__ bool stage_down10(Res res, int total, unsigned char* 
 
 // ---------------------------------------------------------------------------------------
 // Per-image kernels (arguments in the parameter block).
-template <typename S>
+template <typename S, bool FAST>
 __global__ void __launch_bounds__(kThreads) k_up0(const __grid_constant__ Up0Args a) {
   using SM = Smem<sizeof(typename Cplx<S>::T)>;
   extern __shared__ __align__(128) unsigned char smem[];
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem + SM::up0 - 64);
   init_bars(bar);
   Pipe pp{};
-  stage_up0<S>([&](int g, int& l) { l = g; return &a; }, up0_tiles(a), smem, bar, pp, blockIdx.x,
+  stage_up0<S, FAST>([&](int g, int& l) { l = g; return &a; }, up0_tiles(a), smem, bar, pp, blockIdx.x,
                gridDim.x);
 }
 
@@ -1302,18 +1364,18 @@ __device__ __forceinline__ int small_tiles(int h, int w, int planes) {
   return cdiv(w + kDnX0, kSmW) * cdiv(h, kSmH) * planes;
 }
 
-template <typename S>
+template <typename S, bool FAST>
 __global__ void __launch_bounds__(kThreads) k_down_s(const __grid_constant__ DownArgs a) {
   using SM = Smem<sizeof(typename Cplx<S>::T)>;
   extern __shared__ __align__(128) unsigned char smem[];
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem + SM::dns - 64);
   init_bars(bar);
   Pipe pp{};
-  stage_combine_s<S>([&](int g, int& l) { l = g; return &a; }, small_tiles(a.fine.h, a.fine.w, a.planes),
+  stage_combine_s<S, FAST>([&](int g, int& l) { l = g; return &a; }, small_tiles(a.fine.h, a.fine.w, a.planes),
                      smem, bar, pp, blockIdx.x, gridDim.x);
 }
 
-template <typename S>
+template <typename S, bool FAST>
 __global__ void __launch_bounds__(kThreads, 3) k_down0(const __grid_constant__ Down0Args a) {
   using SM = Smem<sizeof(typename Cplx<S>::T)>;
   extern __shared__ __align__(128) unsigned char smem[];
@@ -1321,7 +1383,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_down0(const __grid_constant__ D
   init_bars(bar);
   Pipe pp{};
   const CombineView v = view_of(a);
-  stage_combine0<S>([&](int g, int& l) { l = g; return v; }, combine_tiles(v), smem, bar, pp, blockIdx.x,
+  stage_combine0<S, FAST>([&](int g, int& l) { l = g; return v; }, combine_tiles(v), smem, bar, pp, blockIdx.x,
                     gridDim.x);
 }
 
@@ -1614,8 +1676,12 @@ using SMS = Smem<sizeof(CTS)>;
 
 cudaError_t FLLF_LAUNCH_NAME(up0)(const Up0Args& a, cudaStream_t s, int cps) {
   const int tiles = cdiv(a.dst.w, kUpTW) * cdiv(a.dst.h, kUpTH) * a.planes;
-  const int grid = persistent_grid<k_up0<FLLF_STORAGE>>(SMS::up0, tiles, cps);
-  return launch_pdl(k_up0<FLLF_STORAGE>, grid, SMS::up0, s, a);
+  if (a.fast.S > 0) {
+    const int grid = persistent_grid<k_up0<FLLF_STORAGE, true>>(SMS::up0, tiles, cps);
+    return launch_pdl(k_up0<FLLF_STORAGE, true>, grid, SMS::up0, s, a);
+  }
+  const int grid = persistent_grid<k_up0<FLLF_STORAGE, false>>(SMS::up0, tiles, cps);
+  return launch_pdl(k_up0<FLLF_STORAGE, false>, grid, SMS::up0, s, a);
 }
 
 cudaError_t FLLF_LAUNCH_NAME(up)(const UpArgs& a, cudaStream_t s, int cps) {
@@ -1633,14 +1699,22 @@ cudaError_t FLLF_LAUNCH_NAME(down)(const DownArgs& a, cudaStream_t s, int cps) {
 
 cudaError_t FLLF_LAUNCH_NAME(down_s)(const DownArgs& a, cudaStream_t s, int cps) {
   const int tiles = cdiv(a.fine.w + kDnX0, kSmW) * cdiv(a.fine.h, kSmH) * a.planes;
-  const int grid = persistent_grid<k_down_s<FLLF_STORAGE>>(SMS::dns, tiles, cps);
-  return launch_pdl(k_down_s<FLLF_STORAGE>, grid, SMS::dns, s, a);
+  if (a.fast.S > 0) {
+    const int grid = persistent_grid<k_down_s<FLLF_STORAGE, true>>(SMS::dns, tiles, cps);
+    return launch_pdl(k_down_s<FLLF_STORAGE, true>, grid, SMS::dns, s, a);
+  }
+  const int grid = persistent_grid<k_down_s<FLLF_STORAGE, false>>(SMS::dns, tiles, cps);
+  return launch_pdl(k_down_s<FLLF_STORAGE, false>, grid, SMS::dns, s, a);
 }
 
 cudaError_t FLLF_LAUNCH_NAME(down0)(const Down0Args& a, cudaStream_t s, int cps) {
   const int tiles = cdiv(a.w0 + kDnX0, kDnOW) * cdiv(a.h0, kDnOH) * a.planes;
-  const int grid = persistent_grid<k_down0<FLLF_STORAGE>>(SMS::dn, tiles, cps);
-  return launch_pdl(k_down0<FLLF_STORAGE>, grid, SMS::dn, s, a);
+  if (a.fast.S > 0) {
+    const int grid = persistent_grid<k_down0<FLLF_STORAGE, true>>(SMS::dn, tiles, cps);
+    return launch_pdl(k_down0<FLLF_STORAGE, true>, grid, SMS::dn, s, a);
+  }
+  const int grid = persistent_grid<k_down0<FLLF_STORAGE, false>>(SMS::dn, tiles, cps);
+  return launch_pdl(k_down0<FLLF_STORAGE, false>, grid, SMS::dn, s, a);
 }
 
 cudaError_t FLLF_LAUNCH_NAME(down10)(const Down10Args& a, cudaStream_t s, int cps) {
@@ -1672,7 +1746,7 @@ cudaError_t FLLF_LAUNCH_NAME(chain)(const ChainArgs& a, cudaStream_t s, int cps)
 int FLLF_LAUNCH_NAME(occupancy)(int kind, int batched) {
   switch (kind) {
     case 0: return batched ? resident_per_sm<k_up0_batch<FLLF_STORAGE>>(SMS::up0, nullptr)
-                           : resident_per_sm<k_up0<FLLF_STORAGE>>(SMS::up0, nullptr);
+                           : resident_per_sm<k_up0<FLLF_STORAGE, false>>(SMS::up0, nullptr);
     case 1: return batched ? resident_per_sm<k_up_batch<FLLF_STORAGE>>(SMS::up, nullptr)
                            : resident_per_sm<k_up<FLLF_STORAGE>>(SMS::up, nullptr);
     case 2: return batched ? resident_per_sm<k_down_batch<FLLF_STORAGE>>(SMS::dns, nullptr)
@@ -1683,7 +1757,7 @@ int FLLF_LAUNCH_NAME(occupancy)(int kind, int batched) {
       constexpr size_t kChainSmem = SMS::up > SMS::dn1 ? SMS::up : SMS::dn1;
       return resident_per_sm<k_chain<FLLF_STORAGE>>(kChainSmem, nullptr);
     }
-    default: return resident_per_sm<k_down_s<FLLF_STORAGE>>(SMS::dns, nullptr);
+    default: return resident_per_sm<k_down_s<FLLF_STORAGE, false>>(SMS::dns, nullptr);
   }
 }
 

@@ -47,10 +47,12 @@ fllf_status noalloc_fail(fllf_status s, const std::string& why) {
 
 }  // namespace
 
-extern "C" fllf_status fllf_run_noalloc(const fllf_params* p, const float* d_in, float* d_out,
+extern "C" fllf_status fllf_run_noalloc(const fllf_params* user, const float* d_in, float* d_out,
                                         void* stream) {
-  fllf_status st = fllf::validate(p);
+  fllf_status st = fllf::validate(user);
   if (st != FLLF_OK) return st;
+  const fllf_params np = fllf::normalized(*user);
+  const fllf_params* p = &np;
   if (!d_in || !d_out) return noalloc_fail(FLLF_EINVAL, "input or output pointer is NULL");
   const size_t n = sizeof(float) * (size_t)p->H * p->W * p->C;
   const char *a = reinterpret_cast<const char*>(d_in), *b = reinterpret_cast<const char*>(d_out);
@@ -88,7 +90,8 @@ extern "C" fllf_status fllf_run_noalloc(const fllf_params* p, const float* d_in,
   // the array (pageable source: the copy has read it before returning).
   double a64[64];
   float a32[64];
-  fllf::compute_coeffs(*p, a64);
+  for (int k = 0; k < p->K; ++k) a64[k] = 0.0;   // fast LLF: unused
+  if (p->method == FLLF_METHOD_FOURIER) fllf::compute_coeffs(*p, a64);
   for (int k = 0; k < p->K; ++k) a32[k] = (float)a64[k];
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   float* d_a = reinterpret_cast<float*>(base);

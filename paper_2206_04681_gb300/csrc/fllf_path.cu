@@ -212,6 +212,91 @@ bool build_maps(const fllf_params& p, const std::vector<Level>& lv, PathMaps* m)
   return true;
 }
 
+namespace {
+
+// Fast LLF (Sec. II-D): the sampled detail images' pyramids (level-0 REDUCE,
+// then the REDUCE kernels unchanged), the interpolating combines on the
+// 32 x 16 tiles from the top down to level 1, and the level-0 combine.
+cudaError_t enqueue_fast(const fllf_params& p, const std::vector<Level>& lv, const PathMaps& maps,
+                         const float* d_a, unsigned* fault, const float* d_in, float* d_out, cudaStream_t s,
+                         StageHook* hook, const Tuning& tn) {
+  const int L = p.levels, C = p.C, prec = p.precision;
+  FastArgs fa{};
+  fa.S = p.samples;
+  fa.tau = (float)(1.0 / (p.samples - 1));
+  fa.fm1 = (float)(p.m - 1.0);
+  fa.c2 = (float)(1.4426950408889634 / (2.0 * p.sigma_r * p.sigma_r));   // log2(e) / (2 sigma_r^2)
+  auto mark = [&](int st, bool b) {
+    if (hook) hook->mark(st, b, s);
+  };
+  cudaError_t e;
+  Up0Args u0{};
+  u0.I = d_in;
+  u0.a = d_a;
+  u0.h0 = p.H;
+  u0.w0 = p.W;
+  u0.planes = C;
+  u0.dst = lv[1];
+  u0.K = p.K;
+  u0.fault = fault;
+  u0.fast = fa;
+  u0.use_tma = encode_image_map(&u0.imap, d_in, p.W, p.H, C, kUpIW, kUpIR) ? 1 : 0;
+  mark(FLLF_STAGE_UP0, true);
+  if ((e = launch_up0(prec, u0, s, tn.cps[FLLF_STAGE_UP0])) != cudaSuccess) return e;
+  mark(FLLF_STAGE_UP0, false);
+  for (int l = 1; l <= L - 2; ++l) {
+    UpArgs u{};
+    u.zmap = maps.z_up[l];
+    u.gmap = maps.g_up[l];
+    u.src = lv[l];
+    u.dst = lv[l + 1];
+    u.planes = C;
+    u.K = p.K;
+    u.write_g = (l + 1 <= L - 2) ? 1 : 0;
+    u.reverse = (l == 1 && tn.reverse) ? 1 : 0;
+    u.fault = fault;
+    mark(FLLF_STAGE_UP, true);
+    if ((e = launch_up(prec, u, s, tn.cps[FLLF_STAGE_UP])) != cudaSuccess) return e;
+    mark(FLLF_STAGE_UP, false);
+  }
+  for (int l = L - 2; l >= 1; --l) {
+    DownArgs d{};
+    d.zmap = maps.z_cs[l + 1];
+    d.emap = maps.e_cs[l + 1];
+    d.zfmap = maps.z_fs[l];
+    d.gfmap = maps.g_fs[l];
+    d.fine = lv[l];
+    d.coarse = lv[l + 1];
+    d.planes = C;
+    d.K = p.K;
+    d.has_e = (l + 1 <= L - 2) ? 1 : 0;
+    d.fault = fault;
+    d.fast = fa;
+    mark(FLLF_STAGE_DOWN_S, true);
+    if ((e = launch_down_s(prec, d, s, tn.cps[FLLF_STAGE_DOWN_S])) != cudaSuccess) return e;
+    mark(FLLF_STAGE_DOWN_S, false);
+  }
+  Down0Args d0{};
+  d0.zmap = maps.z_dn[1];
+  d0.emap = maps.e_dn[1];
+  d0.I = d_in;
+  d0.O = d_out;
+  d0.h0 = p.H;
+  d0.w0 = p.W;
+  d0.planes = C;
+  d0.coarse = lv[1];
+  d0.K = p.K;
+  d0.has_e = (L >= 3) ? 1 : 0;
+  d0.fault = fault;
+  d0.fast = fa;
+  mark(FLLF_STAGE_DOWN0, true);
+  if ((e = launch_down0(prec, d0, s, tn.cps[FLLF_STAGE_DOWN0])) != cudaSuccess) return e;
+  mark(FLLF_STAGE_DOWN0, false);
+  return cudaSuccess;
+}
+
+}  // namespace
+
 cudaError_t enqueue_path(const fllf_params& p, const std::vector<Level>& lv, const PathMaps& maps,
                          const float* d_a, unsigned* fault, const float* d_in, float* d_out,
                          cudaStream_t s, StageHook* hook, const float* d_gain, float mscale,
@@ -230,6 +315,7 @@ cudaError_t enqueue_path(const fllf_params& p, const std::vector<Level>& lv, con
     return cudaMemcpyAsync(d_out, d_in, sizeof(float) * (size_t)p.H * p.W * C,
                            cudaMemcpyDeviceToDevice, s);
   }
+  if (p.method == FLLF_METHOD_FAST) return enqueue_fast(p, lv, maps, d_a, fault, d_in, d_out, s, hook, tn);
   auto mark = [&](int st, bool b) {
     if (hook) hook->mark(st, b, s);
   };

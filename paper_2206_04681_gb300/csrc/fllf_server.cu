@@ -452,6 +452,7 @@ fllf_status fllf_server_submit(fllf_server* sv, const fllf_params* p, const floa
   if (!sv || !ticket) return sfail(FLLF_EINVAL, "server or ticket is NULL");
   fllf_status st = validate(p);
   if (st != FLLF_OK) return st;
+  if (p->method != FLLF_METHOD_FOURIER) return sfail(FLLF_EINVAL, "the server runs Fourier LLF requests only");
   if (!d_in || !d_out) return sfail(FLLF_EINVAL, "input or output pointer is NULL");
   const size_t n = sizeof(float) * (size_t)p->H * p->W * p->C;
   const char *a = reinterpret_cast<const char*>(d_in), *b = reinterpret_cast<const char*>(d_out);

@@ -130,3 +130,28 @@ def test_optimal_period_rejects_bad_arguments(lib):
         with pytest.raises(pkg.FllfError) as e:
             pkg.fllf_optimal_period(*args)
         assert e.value.status == pkg.FLLF_EINVAL
+
+
+def test_fast_params_validation_and_layout(lib):
+    # fast LLF (Sec. II-D): S samples held as ceil(S/2) complex planes; K, T and
+    # coeff_mode are not used
+    p = pkg.make_fast_params(2160, 3840, 3, 8, samples=16)
+    p.K, p.T, p.coeff_mode = 0, -1.0, 7
+    assert pkg.fllf_params_validate(p) == pkg.FLLF_OK
+    q = pkg.make_params(2160, 3840, 3, 8, 8)
+    assert pkg.fllf_plan_scratch_bytes(p) == pkg.fllf_plan_scratch_bytes(q)
+    p.samples = 15   # odd: the last plane's second half is unused
+    assert pkg.fllf_plan_scratch_bytes(p) == pkg.fllf_plan_scratch_bytes(q)
+    for s in (0, 1, 129):
+        p.samples = s
+        assert pkg.fllf_params_validate(p) == pkg.FLLF_EINVAL
+    p.samples = 8
+    p.method = 2
+    assert pkg.fllf_params_validate(p) == pkg.FLLF_EINVAL
+    p.method = pkg.FLLF_METHOD_FAST
+    p.sigma_r = 0.0
+    assert pkg.fllf_params_validate(p) == pkg.FLLF_EINVAL
+    p.sigma_r = 0.2
+    with pytest.raises(pkg.FllfError) as e:
+        pkg.fllf_coeffs(p)   # no Fourier coefficients
+    assert e.value.status == pkg.FLLF_EINVAL

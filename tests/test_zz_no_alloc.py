@@ -90,3 +90,9 @@ def test_rejects_images_above_the_array_size():
         pkg.fllf_run_noalloc(p, x.data_ptr(), y.data_ptr(), torch.cuda.current_stream().cuda_stream)
     assert e.value.status == pkg.FLLF_EINVAL
     assert "scratch" in e.value.detail
+
+
+def test_fast_llf_same_as_plan():
+    img = synth_image(70, 90, 2, polygons=4, seed=45)
+    p = pkg.make_fast_params(70, 90, 2, 4, 7, 2.5, 0.25)
+    np.testing.assert_array_equal(_no_alloc(img, p), _with_plan(img, p))
