@@ -42,10 +42,11 @@ def parse():
     ap.add_argument("--precision", choices=["fp32", "fp16", "bf16"], default="fp32")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
-    ap.add_argument("--workload", choices=["uhd", "batch", "serve", "sweep"], default="uhd",
-                    help="uhd: the 4K RGB headline (plus a short served stream); batch: 64 mixed "
-                         "images, batched vs looped; serve: Poisson request streams; sweep: "
-                         "storage precision error over K x sigma_r x m against the float64 oracle")
+    ap.add_argument("--workload", choices=["uhd", "batch", "serve"], default="uhd",
+                    help="uhd: the 4K RGB headline (plus fast LLF at the same pyramid count and a "
+                         "short served stream); batch: 64 mixed images, batched vs looped; serve: "
+                         "Poisson request streams.  Accuracy against the float64 oracle is "
+                         "measured by tests/accuracy.py")
     ap.add_argument("--serve-seconds", type=float, default=None,
                     help="length of each served stream (default 30 s; 4 s in the uhd line)")
     ap.add_argument("--serve-rates", type=str, default=None,
@@ -279,9 +280,10 @@ def run_reference(args):
     return 0
 
 
-def time_precision(pkg, torch, cfg, precision, frames, steps, warmup, stream, device):
-    p = pkg.make_params(cfg["H"], cfg["W"], cfg["C"], cfg["levels"], cfg["K"], cfg["m"],
-                        cfg["sigma_r"], cfg["T"], precision)
+def time_precision(pkg, torch, cfg, precision, frames, steps, warmup, stream, device, params=None):
+    """ms per frame of a plan (autotuned), back to back over the cycled frames."""
+    p = params or pkg.make_params(cfg["H"], cfg["W"], cfg["C"], cfg["levels"], cfg["K"], cfg["m"],
+                                  cfg["sigma_r"], cfg["T"], precision)
     plan = pkg.fllf_plan_create(p, device)
     outs = [torch.empty_like(f) for f in frames]
     try:
@@ -484,6 +486,18 @@ def run_ours(args):
             ms = time_precision(pkg, torch, cfg, prec, frames, min(args.steps, 500), 10, stream, device)
             variants[prec] = {"ms_per_step": ms, "value": pixels / (ms * 1e-3) / 1e6}
         line["precision_variants"] = variants
+        # fast LLF (Sec. II-D) at the same number of pyramids: S = 2K samples
+        S = 2 * cfg["K"]
+        fp = pkg.make_fast_params(cfg["H"], cfg["W"], cfg["C"], cfg["levels"], S, cfg["m"], cfg["sigma_r"],
+                                  args.precision)
+        ms = time_precision(pkg, torch, cfg, args.precision, frames, min(args.steps, 500), 10, stream,
+                            device, params=fp)
+        line["fast_llf"] = {"samples": S, "pyramids": S + 1, "ms_per_step": ms,
+                            "value": pixels / (ms * 1e-3) / 1e6, "unit": UNIT,
+                            "pyramid_storage": args.precision,
+                            "note": "fast LLF (Sec. II-D) on the same frame, same levels, m and sigma_r, "
+                                    "with 2K samples: the paper's comparison at an equal pyramid count "
+                                    "(2K + 1)"}
     if rank == 0 and world == 1 and not args.no_serve:
         line["serving"] = serving_summary(pkg, torch, device, args.serve_precision,
                                           seconds=args.serve_seconds or 4.0)
@@ -576,19 +590,7 @@ def run_batch(args):
     return 0
 
 SERVE = dict(rates=(50, 100, 200, 400, "max"), seconds=30.0, seed=5, budget=120 << 30,
-             max_slots=64, max_queue=256, max_waves=3, psnr_sample=32)
-
-
-def _oracle_psnr_job(job):
-    """Float64 oracle on one served request's input; returns (PSNR dB, max-abs)."""
-    import numpy as np
-    import oracle
-    x, y, levels, K, m, sigma_r, T = job
-    a = oracle.coeffs_quadrature(m, sigma_r, T, K)
-    ref = oracle.fourier_llf(x.astype(np.float64), levels, a, T)
-    err = y.astype(np.float64) - ref
-    mse = float(np.mean(err ** 2))
-    return (float("inf") if mse == 0 else 10 * np.log10(1.0 / mse)), float(np.max(np.abs(err)))
+             max_slots=64, max_queue=256, max_waves=3)
 
 
 def serve_canvas(torch, device):
@@ -663,15 +665,15 @@ def serve_warmup(pkg, torch, server, canvas, precision):
                  precision, set(), saturate=True)
 
 
-def serve_rate(pkg, torch, server, canvas, rate, seconds, precision, n_check, pool):
+def serve_rate(pkg, torch, server, canvas, rate, seconds, precision, keep=()):
     """One Poisson stream at `rate` requests/s (rate "max": the same stream at
-    400/s submitted as a backlog, to measure capacity); a JSON-ready summary."""
+    400/s submitted as a backlog, to measure capacity); a JSON-ready summary,
+    the request list and the (input, output) pairs of the requests in `keep`."""
     import numpy as np
     from paper_2206_04681_gb300.synth import request_stream
     saturate = rate == "max"
     reqs = request_stream(400 if saturate else rate, seconds, seed=SERVE["seed"])
-    order = sorted(range(len(reqs)), key=lambda j: reqs[j]["H"] * reqs[j]["W"] * reqs[j]["C"])
-    keep = set(order[:n_check])
+    keep = set(keep)
     serve_warmup(pkg, torch, server, canvas, precision)
     lat, rejected, kept = serve_stream(pkg, torch, server, canvas, reqs, precision, keep, saturate)
     st = pkg.fllf_server_stats_get(server)
@@ -686,14 +688,7 @@ def serve_rate(pkg, torch, server, canvas, rate, seconds, precision, n_check, po
                                  "measured": "scheduled arrival -> poll OK (client)"},
            "waves": st["waves"], "max_active": st["max_active"],
            "pool_peak_gb": st["pool_peak_bytes"] / 1e9}
-    if kept and pool is not None:
-        jobs = [(kept[j][0], kept[j][1], reqs[j]["levels"], reqs[j]["K"], reqs[j]["m"],
-                 reqs[j]["sigma_r"], reqs[j]["T"]) for j in sorted(kept)]
-        res = pool.map(_oracle_psnr_job, jobs)
-        out["psnr_vs_fp64"] = {"requests": len(res), "min_db": min(r[0] for r in res),
-                               "max_abs": max(r[1] for r in res),
-                               "sample": f"the {len(res)} smallest requests of the stream"}
-    return out
+    return out, reqs, kept
 
 
 def make_server(pkg, device):
@@ -701,22 +696,14 @@ def make_server(pkg, device):
                                   SERVE["max_waves"], device)
 
 
-def oracle_pool():
-    """Process pool for the oracle checks (spawned, so it is safe after CUDA use)."""
-    import multiprocessing as mp
-    return mp.get_context("spawn").Pool(max(1, min(16, os.cpu_count() or 1)))
-
-
-def serving_summary(pkg, torch, device, precision, rate=200, seconds=4.0, n_check=8):
+def serving_summary(pkg, torch, device, precision, rate=200, seconds=4.0):
     """A short served stream for the headline line."""
-    pool = oracle_pool()
     server = make_server(pkg, device)
     try:
         canvas = serve_canvas(torch, device)
-        out = serve_rate(pkg, torch, server, canvas, rate, seconds, precision, n_check, pool)
+        out, _, _ = serve_rate(pkg, torch, server, canvas, rate, seconds, precision)
     finally:
         pkg.fllf_server_destroy(server)
-        pool.close()
     out["pyramid_storage"] = precision
     out["budget_gb"] = SERVE["budget"] / 2 ** 30
     return out
@@ -728,7 +715,6 @@ def run_serve(args):
     import torch
     import paper_2206_04681_gb300 as pkg
     from paper_2206_04681_gb300 import build
-    pool = oracle_pool()
     build.build_library()
     torch.cuda.set_device(0)
     rates = ([r if r == "max" else float(r) for r in args.serve_rates.split(",")]
@@ -739,12 +725,10 @@ def run_serve(args):
     try:
         canvas = serve_canvas(torch, 0)
         clocks.start()
-        runs = [serve_rate(pkg, torch, server, canvas, r, seconds, args.serve_precision,
-                           SERVE["psnr_sample"], pool) for r in rates]
+        runs = [serve_rate(pkg, torch, server, canvas, r, seconds, args.serve_precision)[0] for r in rates]
         clk = clocks.stop()
     finally:
         pkg.fllf_server_destroy(server)
-        pool.close()
     best = max(runs, key=lambda r: r["mpixel_per_s"])   # the backlog run: capacity
     line = {"metric": "Mpixel/s and p50/p99 ms, served Fourier LLF requests (Poisson arrivals)",
             "value": best["mpixel_per_s"], "unit": UNIT, "n_gpus": 1, "steps": len(runs),
@@ -762,106 +746,6 @@ def run_serve(args):
     return 0
 
 
-SWEEP = dict(K=(4, 8, 16), sigma_r=(0.1, 0.2, 0.4), m=(0.5, 3.0), levels=8, T=2.0,
-             crop=(824, 1664, 512))   # centred 512 x 512 crop: rows 824.., cols 1664..
-
-
-def _sweep_oracle_job(job):
-    """Float64 oracle output for one (plane or crop, parameter set) job."""
-    import numpy as np
-    import oracle
-    kind, x, levels, K, m, sigma_r, T = job
-    x = x.astype(np.float64)
-    if kind == "fourier":
-        a = oracle.coeffs_quadrature(m, sigma_r, T, K)
-        return oracle.fourier_llf(x, levels, a, T)
-    # naive LLF with the exact remap detail (Sec. II-C), windowed
-    return oracle.naive_llf(x, levels, lambda d: oracle.remap_detail(d, m, sigma_r))
-
-
-def run_sweep(args):
-    """Error of the three Fourier-pyramid storage precisions against the
-    float64 oracle on the 3840 x 2160 x 3 frame for every (K, sigma_r, m) of
-    the sweep, and against naive LLF (exact remap) on a centred 512 x 512
-    crop of channel 0.  One JSON line with max-abs and PSNR per case."""
-    import numpy as np
-    pool = oracle_pool()                      # spawned before any GPU work
-    import torch
-    import paper_2206_04681_gb300 as pkg
-    from paper_2206_04681_gb300 import build
-    from paper_2206_04681_gb300.synth import synth_image
-    build.build_library()
-    torch.cuda.set_device(0)
-    cfg = WORKLOAD
-    img = synth_image(cfg["H"], cfg["W"], cfg["C"], cfg["polygons"], cfg["seed"])
-    y0, x0, n = SWEEP["crop"]
-    crop = np.ascontiguousarray(img[:1, y0:y0 + n, x0:x0 + n])
-    L, T = SWEEP["levels"], SWEEP["T"]
-    combos = [(K, s, m) for K in SWEEP["K"] for s in SWEEP["sigma_r"] for m in SWEEP["m"]]
-    jobs = []
-    for K, sg, m in combos:
-        jobs += [("fourier", img[c], L, K, m, sg, T) for c in range(cfg["C"])]
-        jobs.append(("naive", crop[0], L, K, m, sg, T))
-    t0 = time.perf_counter()
-    results = pool.imap(_sweep_oracle_job, jobs)
-    x_full = torch.from_numpy(img).cuda()
-    x_crop = torch.from_numpy(crop).cuda()
-
-    def gpu(x, K, sg, m, prec):
-        p = pkg.make_params(x.shape[1], x.shape[2], x.shape[0], L, K, m, sg, T, prec)
-        plan = pkg.fllf_plan_create(p, 0)
-        try:
-            y = torch.empty_like(x)
-            pkg.run_tensor(plan, x, y)
-            torch.cuda.synchronize()
-            return y.cpu().numpy().astype(np.float64)
-        finally:
-            pkg.fllf_plan_destroy(plan)
-
-    def stats(err):
-        mse = float(np.mean(err ** 2))
-        return {"max_abs": float(np.max(np.abs(err))),
-                "psnr_db": float("inf") if mse == 0 else 10 * np.log10(1.0 / mse)}
-
-    rows = []
-    precs = ("fp32", "fp16", "bf16")
-    for K, sg, m in combos:
-        outs = {pr: gpu(x_full, K, sg, m, pr) for pr in precs}
-        crops = {pr: gpu(x_crop, K, sg, m, pr) for pr in precs}
-        sse = dict.fromkeys(precs, 0.0)
-        mx = dict.fromkeys(precs, 0.0)
-        for c in range(cfg["C"]):
-            ref = next(results)
-            for pr in precs:
-                e = outs[pr][c] - ref
-                sse[pr] += float(np.sum(e * e))
-                mx[pr] = max(mx[pr], float(np.max(np.abs(e))))
-        naive = next(results)
-        row = {"K": K, "sigma_r": sg, "m": m}
-        for pr in precs:
-            mse = sse[pr] / img.size
-            row[pr] = {"max_abs": mx[pr], "psnr_db": float("inf") if mse == 0 else 10 * np.log10(1.0 / mse)}
-        row["crop_vs_naive_psnr_db"] = {pr: stats(crops[pr][0] - naive)["psnr_db"] for pr in precs}
-        rows.append(row)
-    pool.close()
-    worst = {pr: min(r[pr]["psnr_db"] for r in rows) for pr in precs}
-    line = {"metric": "max-abs and PSNR vs the float64 oracle, Fourier-pyramid storage sweep",
-            "value": worst["fp16"], "unit": "dB (lowest fp16 PSNR over the sweep)", "n_gpus": 1,
-            "steps": len(combos), "warmup": 0, "ms_per_step": None, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": "uhd_rgb_3840x2160x3_L8_sweep", "levels": L, "T": T,
-                       "K": list(SWEEP["K"]), "sigma_r": list(SWEEP["sigma_r"]), "m": list(SWEEP["m"]),
-                       "crop": f"channel 0, rows {y0}..{y0 + n - 1}, cols {x0}..{x0 + n - 1}, levels {L}",
-                       "oracle": "float64 Fourier LLF (Eq. (14)) on the whole frame; naive LLF with "
-                                 "the exact remap on the crop"},
-            "worst_psnr_db": worst,
-            "worst_max_abs": {pr: max(r[pr]["max_abs"] for r in rows) for pr in precs},
-            "oracle_seconds": time.perf_counter() - t0,
-            "sweep": rows}
-    print(json.dumps(line), flush=True)
-    return 0
-
-
 def main():
     args = parse()
     if args.impl == "reference":
@@ -870,8 +754,6 @@ def main():
         return run_batch(args)
     if args.workload == "serve":
         return run_serve(args)
-    if args.workload == "sweep":
-        return run_sweep(args)
     return run_ours(args)
 
 
