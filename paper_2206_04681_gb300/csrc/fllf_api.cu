@@ -230,8 +230,49 @@ void free_plan(fllf_plan* pl) {
   if (pl->d_io_out) cudaFree(pl->d_io_out);
   if (pl->d_mpyr) cudaFree(pl->d_mpyr);
   if (pl->d_luma) cudaFree(pl->d_luma);
+  for (cudaEvent_t e : pl->io_ev)
+    if (e) cudaEventDestroy(e);
+  if (pl->io_h2d) cudaStreamDestroy(pl->io_h2d);
+  if (pl->io_d2h) cudaStreamDestroy(pl->io_d2h);
   delete pl->timer;
   delete pl;
+}
+
+// One-plane views of a plan (levels offset to plane c, maps of one plane) and
+// the streams and events of the host-buffer plane pipeline; built once.
+fllf_status plane_pipeline_setup(fllf_plan* pl) {
+  const int C = pl->p.C, L = pl->p.levels;
+  if ((int)pl->plane_lv.size() == C) return FLLF_OK;
+  fllf_params p1 = pl->p;
+  p1.C = 1;
+  std::vector<std::vector<Level>> lvs(C);
+  std::vector<PathMaps> maps(C);
+  for (int c = 0; c < C; ++c) {
+    lvs[c] = pl->lv;
+    for (int l = 1; l < L; ++l) {
+      Level& v = lvs[c][l];
+      const size_t zs = pl->p.precision == FLLF_FP32 ? 8 : 4;
+      if (v.G) v.G += (size_t)c * v.gplane;
+      if (v.E) v.E += (size_t)c * v.gplane;
+      if (v.Z) v.Z = static_cast<unsigned char*>(v.Z) + (size_t)c * v.zplane * zs;
+    }
+    if (L > 1 && !build_maps(p1, lvs[c], &maps[c]))
+      return fail(FLLF_ECUDA, "TMA tensor map encoding failed (cuTensorMapEncodeTiled)");
+  }
+  cudaError_t e;
+  if (!pl->io_h2d && (e = cudaStreamCreateWithFlags(&pl->io_h2d, cudaStreamNonBlocking)) != cudaSuccess)
+    return cuda_fail(e, "copy stream creation");
+  if (!pl->io_d2h && (e = cudaStreamCreateWithFlags(&pl->io_d2h, cudaStreamNonBlocking)) != cudaSuccess)
+    return cuda_fail(e, "copy stream creation");
+  while ((int)pl->io_ev.size() < 2 * C) {
+    cudaEvent_t ev = nullptr;
+    if ((e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming)) != cudaSuccess)
+      return cuda_fail(e, "cudaEventCreate");
+    pl->io_ev.push_back(ev);
+  }
+  pl->plane_lv = std::move(lvs);
+  pl->plane_maps = std::move(maps);
+  return FLLF_OK;
 }
 
 }  // namespace
@@ -549,13 +590,51 @@ fllf_status fllf_run_host(fllf_plan* plan, const float* h_in, float* h_out, void
     }
   }
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-  if ((e = cudaMemcpyAsync(plan->d_io_in, h_in, bytes, cudaMemcpyHostToDevice, s)) != cudaSuccess)
-    return cuda_fail(e, "host-to-device copy");
-  if ((e = enqueue_path(plan->p, plan->lv, plan->maps, plan->d_a, plan->d_fault, plan->d_io_in,
-                        plan->d_io_out, s, plan->timer, nullptr, 0.f, &plan->tune)) != cudaSuccess)
-    return cuda_fail(e, "kernel launch");
-  if ((e = cudaMemcpyAsync(h_out, plan->d_io_out, bytes, cudaMemcpyDeviceToHost, s)) != cudaSuccess)
-    return cuda_fail(e, "device-to-host copy");
+  const int C = plan->p.C;
+  if (C == 1 || plan->p.levels == 1) {
+    if ((e = cudaMemcpyAsync(plan->d_io_in, h_in, bytes, cudaMemcpyHostToDevice, s)) != cudaSuccess)
+      return cuda_fail(e, "host-to-device copy");
+    if ((e = enqueue_path(plan->p, plan->lv, plan->maps, plan->d_a, plan->d_fault, plan->d_io_in,
+                          plan->d_io_out, s, plan->timer, nullptr, 0.f, &plan->tune)) != cudaSuccess)
+      return cuda_fail(e, "kernel launch");
+    if ((e = cudaMemcpyAsync(h_out, plan->d_io_out, bytes, cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+      return cuda_fail(e, "device-to-host copy");
+    if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_fail(e, "stream synchronize");
+    return check_fault(plan);
+  }
+  // C >= 2: the planes are independent, so plane c's host-to-device copy, the
+  // filtering of plane c-1 and the device-to-host copy of plane c-2 overlap
+  // (two copy streams and the caller's stream; each plane runs the path on a
+  // one-plane view of the scratch, with the same arithmetic per pixel).
+  fllf_status st = plane_pipeline_setup(plan);
+  if (st != FLLF_OK) return st;
+  fllf_params p1 = plan->p;
+  p1.C = 1;
+  const size_t pn = (size_t)plan->p.H * plan->p.W, pb = sizeof(float) * pn;
+  // the copy streams start after the caller's earlier work on s
+  cudaEvent_t* ev = plan->io_ev.data();
+  if ((e = cudaEventRecord(ev[0], s)) != cudaSuccess || (e = cudaStreamWaitEvent(plan->io_h2d, ev[0], 0)) != cudaSuccess)
+    return cuda_fail(e, "stream ordering");
+  for (int c = 0; c < C; ++c) {
+    if ((e = cudaMemcpyAsync(plan->d_io_in + c * pn, h_in + c * pn, pb, cudaMemcpyHostToDevice, plan->io_h2d)) !=
+            cudaSuccess ||
+        (e = cudaEventRecord(ev[2 * c], plan->io_h2d)) != cudaSuccess)
+      return cuda_fail(e, "host-to-device copy");
+  }
+  for (int c = 0; c < C; ++c) {
+    if ((e = cudaStreamWaitEvent(s, ev[2 * c], 0)) != cudaSuccess) return cuda_fail(e, "stream ordering");
+    if ((e = enqueue_path(p1, plan->plane_lv[c], plan->plane_maps[c], plan->d_a, plan->d_fault,
+                          plan->d_io_in + c * pn, plan->d_io_out + c * pn, s, plan->timer, nullptr, 0.f,
+                          &plan->tune)) != cudaSuccess)
+      return cuda_fail(e, "kernel launch");
+    if ((e = cudaEventRecord(ev[2 * c + 1], s)) != cudaSuccess ||
+        (e = cudaStreamWaitEvent(plan->io_d2h, ev[2 * c + 1], 0)) != cudaSuccess)
+      return cuda_fail(e, "stream ordering");
+    if ((e = cudaMemcpyAsync(h_out + c * pn, plan->d_io_out + c * pn, pb, cudaMemcpyDeviceToHost,
+                             plan->io_d2h)) != cudaSuccess)
+      return cuda_fail(e, "device-to-host copy");
+  }
+  if ((e = cudaStreamSynchronize(plan->io_d2h)) != cudaSuccess) return cuda_fail(e, "stream synchronize");
   if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_fail(e, "stream synchronize");
   return check_fault(plan);
 }

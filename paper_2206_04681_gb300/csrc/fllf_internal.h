@@ -172,4 +172,10 @@ struct fllf_plan {
   float* d_mpyr = nullptr;            // gain-map pyramid of pixel-adaptive runs (first use)
   float* d_luma = nullptr;            // Y and filtered Y of colour-by-luma runs (first use)
   fllf::Tuning tune;                  // launch tuning (fllf_plan_set_tuning / fllf_plan_autotune)
+  // Host-buffer runs of C >= 2 planes: one-plane views of the scratch (levels
+  // and maps) and the copy streams of the plane pipeline (first use).
+  std::vector<std::vector<fllf::Level>> plane_lv;
+  std::vector<fllf::PathMaps> plane_maps;
+  cudaStream_t io_h2d = nullptr, io_d2h = nullptr;
+  std::vector<cudaEvent_t> io_ev;     // per plane: input copied, plane filtered
 };

@@ -10,6 +10,7 @@
 // kernels (argument tables in device memory, with prefix sums of the item
 // counts).
 #include <algorithm>
+#include <type_traits>
 
 #include "fllf_launch.h"
 
@@ -220,10 +221,10 @@ __device__ __forceinline__ bool stage_up0(Res res, int total, unsigned char* sme
       __syncwarp();
       {
         const int k = ch * kKC + vkk;
-        // a full chunk of orders on an interior tile stores without guards
-        const bool uniform = full && (ch + 1) * kKC <= a.K;
-        if (uniform || (k < a.K && xo < a.dst.w)) {
-          // order k is stored weighted by its coefficient: a_k Z_{1,k}
+        // Column q of order k, rows Y1 + 7 vgrp .. + 6: order k is stored
+        // weighted by its coefficient, a_k Z_{1,k}.  A full chunk of orders
+        // on an interior tile (CTA-uniform) takes the unguarded copy.
+        auto vstore = [&](auto guarded) {
           const float sk = FAST ? (1.f / 256.f) : __ldg(a.a + k) * (1.f / 256.f);
           CT* Zk = reinterpret_cast<CT*>(a.dst.Z) + (long long)pl * a.dst.zplane +
                    (long long)k * a.dst.zk + xo + (long long)(Y1 + vgrp * kUpVRows) * a.dst.pitch;
@@ -236,13 +237,18 @@ __device__ __forceinline__ bool stage_up0(Res res, int total, unsigned char* sme
             w[2 * u] = make_float2(q4.x, q4.y);
             w[2 * u + 1] = make_float2(q4.z, q4.w);
           }
-          const int rows = uniform ? kUpVRows : min(kUpVRows, a.dst.h - (Y1 + vgrp * kUpVRows));
+          const int rows = decltype(guarded)::value ? min(kUpVRows, a.dst.h - (Y1 + vgrp * kUpVRows)) : kUpVRows;
 #pragma unroll
           for (int j = 0; j < kUpVRows; ++j) {
-            if (j < rows)
-              Cplx<S>::st(Zk + j * a.dst.pitch,
-                          mul2(splat(sk), tap5(w[2 * j], w[2 * j + 1], w[2 * j + 2], w[2 * j + 3], w[2 * j + 4])));
+            if (!decltype(guarded)::value || j < rows)
+              Cplx<S>::st(Zk, mul2(splat(sk), tap5(w[2 * j], w[2 * j + 1], w[2 * j + 2], w[2 * j + 3], w[2 * j + 4])));
+            Zk += a.dst.pitch;
           }
+        };
+        if (full && (ch + 1) * kKC <= a.K) {
+          vstore(std::false_type{});
+        } else if (k < a.K && xo < a.dst.w) {
+          vstore(std::true_type{});
         }
         if (ch == 0 && tid % 32 < kUpRun * kUpVRows) {
           // guide: lane = (column gq, pair of coarse rows gp)

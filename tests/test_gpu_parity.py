@@ -156,3 +156,25 @@ def test_uhd_rgb_mixed_full_frame(uhd, precision):
     q = psnr(out, ref)
     print(f"4K RGB {precision}: max-abs {np.max(np.abs(out - ref)):.2e}, PSNR {q:.1f} dB")
     assert q >= 60.0
+
+
+@pytest.mark.parametrize("H,W,C,L,fast", [(37, 53, 3, 5, False), (130, 250, 2, 6, False), (64, 96, 3, 5, True)])
+def test_run_host_plane_pipeline_same_bits(H, W, C, L, fast):
+    # host buffers with C >= 2 run plane by plane with the copies overlapped;
+    # H*W odd leaves the planes of the device copy unaligned (plain loads)
+    img = synth_image(H, W, C, polygons=5, seed=H + W)
+    p = (pkg.make_fast_params(H, W, C, L, 9, 3.0, 0.2) if fast
+         else pkg.make_params(H, W, C, L, 8, 3.0, 0.2, 2.0))
+    plan = pkg.fllf_plan_create(p, 0)
+    try:
+        x = torch.from_numpy(img).cuda()
+        y = torch.empty_like(x)
+        pkg.run_tensor(plan, x, y)
+        torch.cuda.synchronize()
+        hin = torch.from_numpy(img).pin_memory()
+        for _ in range(2):
+            hout = torch.full_like(hin, float("nan")).pin_memory()
+            pkg.fllf_run_host(plan, hin.data_ptr(), hout.data_ptr(), torch.cuda.current_stream().cuda_stream)
+            np.testing.assert_array_equal(hout.numpy(), y.cpu().numpy())
+    finally:
+        pkg.fllf_plan_destroy(plan)
