@@ -477,6 +477,7 @@ __device__ __forceinline__ void mbar_wait_thread(uint64_t* b, uint32_t parity, u
 template <typename E, typename MapY, typename MapX>
 __device__ __forceinline__ void fix_borders(E* buf, int planes, int bh, int bw, int x0, int y0,
                                             int w, int h, MapY mapy, MapX mapx) {
+  if (x0 >= 0 && y0 >= 0 && x0 + bw <= w && y0 + bh <= h) return;   // window inside the level
   const int top = min(max(-y0, 0), bh), bot = min(max(y0 + bh - h, 0), bh - top);
   const int lft = min(max(-x0, 0), bw), rgt = min(max(x0 + bw - w, 0), bw - lft);
   if (top + bot > 0) {

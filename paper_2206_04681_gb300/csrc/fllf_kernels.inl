@@ -1188,9 +1188,14 @@ __device__ __forceinline__ bool stage_down10(Res res, int total, unsigned char* 
     auto mx1 = [&](int x) { return ext_coarse(x, L1.w, w0); };
     auto my2 = [&](int y) { return ext_coarse(y, L2.h, L1.h); };
     auto mx2 = [&](int x) { return ext_coarse(x, L2.w, L1.w); };
-    fix_borders(z1b, kKC, kDnCH, kDnCW, cx0, cy0, L1.w, L1.h, my1, mx1);
-    fix_borders(z2b, kKC, kD2H, kD2W, c2x, c2y, L2.w, L2.h, my2, mx2);
-    if (first && a->has_e2) fix_borders(e2b, 1, kD2H, kD2W, c2x, c2y, L2.w, L2.h, my2, mx2);
+    // tiles whose windows lie inside levels 1 and 2 (CTA-uniform) skip the border fix-ups
+    const bool inner = cx0 >= 0 && cy0 >= 0 && cx0 + kDnCW <= L1.w && cy0 + kDnCH <= L1.h && c2x >= 0 &&
+                       c2y >= 0 && c2x + kD2W <= L2.w && c2y + kD2H <= L2.h;
+    if (!inner) {
+      fix_borders(z1b, kKC, kDnCH, kDnCW, cx0, cy0, L1.w, L1.h, my1, mx1);
+      fix_borders(z2b, kKC, kD2H, kD2W, c2x, c2y, L2.w, L2.h, my2, mx2);
+      if (first && a->has_e2) fix_borders(e2b, 1, kD2H, kD2W, c2x, c2y, L2.w, L2.h, my2, mx2);
+    }
 
     // level-1 combine on the window cells (Horner over this chunk's orders)
     if (l1t) {
@@ -1288,7 +1293,7 @@ __device__ __forceinline__ bool stage_down10(Res res, int total, unsigned char* 
           }
       }
       __syncthreads();
-      fix_borders(e1, 1, kDnCH, kDnCW, cx0, cy0, L1.w, L1.h, my1, mx1);
+      if (!inner) fix_borders(e1, 1, kDnCH, kDnCW, cx0, cy0, L1.w, L1.h, my1, mx1);
       float2 ue[4];
       expand_e_2x4(e1 + tr * kDnCW + 2 * tc, ue);
       float* dst = a->O + (long long)pl * h0 * w0;
