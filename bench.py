@@ -280,6 +280,34 @@ def run_reference(args):
     return 0
 
 
+# ---- replicas over ranks (one process per GPU) ---------------------------------------
+def rank_env():
+    """(world, rank, local rank) from the torchrun environment (1, 0, 0 alone)."""
+    return (int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+def rank_seed(cfg, rank):
+    """Each rank filters its own synthetic frames: the workload seed plus the rank."""
+    return cfg["seed"] + rank
+
+
+def max_over_ranks(x, world, device):
+    """The largest value of x over the ranks (the slowest rank's time); x itself alone."""
+    if world == 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_mpixel_s(world, pixels_per_rank_step, seconds_per_step):
+    """Whole-job throughput: every rank filters one frame per step (weak scaling)."""
+    return world * pixels_per_rank_step / seconds_per_step / 1e6
+
+
 def time_precision(pkg, torch, cfg, precision, frames, steps, warmup, stream, device, params=None):
     """ms per frame of a plan (autotuned), back to back over the cycled frames."""
     p = params or pkg.make_params(cfg["H"], cfg["W"], cfg["C"], cfg["levels"], cfg["K"], cfg["m"],
@@ -316,9 +344,7 @@ def run_ours(args):
     from paper_2206_04681_gb300 import build
     from paper_2206_04681_gb300.synth import synth_image
 
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
+    world, rank, local = rank_env()
     if world > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     torch.cuda.set_device(local)
@@ -326,7 +352,7 @@ def run_ours(args):
 
     build.build_library()
     cfg = WORKLOAD
-    img = synth_image(cfg["H"], cfg["W"], cfg["C"], cfg["polygons"], cfg["seed"] + rank)
+    img = synth_image(cfg["H"], cfg["W"], cfg["C"], cfg["polygons"], rank_seed(cfg, rank))
     base = torch.from_numpy(img).cuda()
     frames = [base.clone() for _ in range(N_FRAMES)]
     outs = [torch.empty_like(base) for _ in range(N_FRAMES)]
@@ -387,13 +413,10 @@ def run_ours(args):
     total_ms = e0.elapsed_time(e1)
     stage = pkg.fllf_plan_stage_times(plan)
     pkg.fllf_plan_enable_timing(plan, False)
-    if world > 1:
-        t = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(total_ms, world, "cuda")
     ms_step = total_ms / args.steps
     pixels = cfg["H"] * cfg["W"]
-    value = world * pixels / (ms_step * 1e-3) / 1e6
+    value = whole_job_mpixel_s(world, pixels, ms_step * 1e-3)
 
     # end to end through the C ABI with host buffers (copies inside the timed region)
     hin = torch.from_numpy(img).pin_memory()
@@ -405,11 +428,7 @@ def run_ours(args):
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
         pkg.fllf_run_host(plan, hin.data_ptr(), hout.data_ptr(), stream.cuda_stream)
-    e2e_s = (time.perf_counter() - t0) / e2e_steps
-    if world > 1:
-        t = torch.tensor([e2e_s], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = max_over_ranks((time.perf_counter() - t0) / e2e_steps, world, "cuda")
     tn = pkg.fllf_plan_get_tuning(plan)
     pkg.fllf_plan_destroy(plan)
 
@@ -466,7 +485,7 @@ def run_ours(args):
                    "parallelism": "replicas" if world > 1 else "single",
                    "l2": f"inputs cycled over {N_FRAMES} frames ({N_FRAMES * 99.5:.0f} MB) plus "
                          "the plan scratch per step; working set > 129 MB L2"},
-        "e2e": {"value": world * pixels / e2e_s / 1e6, "unit": UNIT,
+        "e2e": {"value": whole_job_mpixel_s(world, pixels, e2e_s), "unit": UNIT,
                 "h2d_bytes_per_step": int(hin.numel() * 4), "d2h_bytes_per_step": int(hout.numel() * 4)},
         "gpu_launches": int(round(sum(launches_per_step.values()) * args.steps)),
         "roofline": roof,
