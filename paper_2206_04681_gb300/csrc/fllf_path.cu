@@ -301,12 +301,7 @@ cudaError_t enqueue_path(const fllf_params& p, const std::vector<Level>& lv, con
                          const float* d_a, unsigned* fault, const float* d_in, float* d_out,
                          cudaStream_t s, StageHook* hook, const float* d_gain, float mscale,
                          const Tuning* tune) {
-  static const Tuning kDefault = [] {
-    Tuning t;
-    const char* v = getenv("FLLF_CHAIN_PIXELS");  // override of the default chain threshold
-    if (v) t.chain_px = atoll(v);
-    return t;
-  }();
+  static const Tuning kDefault{};
   const Tuning& tn = tune ? *tune : kDefault;
   const int L = p.levels, C = p.C, prec = p.precision;
   const float turns = (float)(2.0 / p.T);
