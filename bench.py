@@ -421,8 +421,8 @@ def run_ours(args):
     # end to end through the C ABI with host buffers (copies inside the timed region)
     hin = torch.from_numpy(img).pin_memory()
     hout = torch.empty_like(hin).pin_memory()
-    e2e_steps = max(3, min(50, args.steps // 20))
-    for _ in range(2):
+    e2e_steps = max(20, min(50, args.steps // 20))
+    for _ in range(5):
         pkg.fllf_run_host(plan, hin.data_ptr(), hout.data_ptr(), stream.cuda_stream)
     barrier()
     t0 = time.perf_counter()

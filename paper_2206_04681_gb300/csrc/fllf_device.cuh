@@ -160,6 +160,7 @@ struct Down10Args {
                         // the level-1 map is l1.M
   float mscale;         // 1/(m - 1)
   unsigned* fault;
+  FastArgs fast;        // fast LLF: interpolating combines at levels 1 and 0
 };
 
 // Batched stage launch: argument blocks of the images that have the stage

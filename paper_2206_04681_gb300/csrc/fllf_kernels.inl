@@ -1071,7 +1071,12 @@ __device__ __forceinline__ bool stage_combine_s(Res res, int total, unsigned cha
 // EXPAND sources, and every thread finishes O = I + Delta_0 + up(E_1) for its
 // 2 x 4 level-0 pixels.  E_1 never goes to memory, and each Z_1 sample is
 // read once for both levels.
-template <typename S, bool ADAPT, typename Res>
+//
+// FAST: fast LLF (Sec. II-D): the planes hold the sampled detail images, the
+// Horner sums become the hat-weighted sums over the samples bracketing the
+// guide (as in the small-tile and level-0 combines), and level 0 adds the
+// level-0 sampled details evaluated at the pixel.
+template <typename S, bool ADAPT, bool FAST = false, typename Res>
 __device__ __forceinline__ bool stage_down10(Res res, int total, unsigned char* smem, uint64_t* bar,
                                             Pipe& pp, int b, int G) {
   using CT = typename Cplx<S>::T;
@@ -1146,10 +1151,23 @@ __device__ __forceinline__ bool stage_down10(Res res, int total, unsigned char* 
     }
     // level-0 state: e^{-i w_1 I}, Horner sums, and I itself
     auto init0 = [&](int q, float g0, float g1) {
-      we[q] = conj_turns(a->turns * g0);
-      wo[q] = conj_turns(a->turns * g1);
       Pe[q] = Po[q] = splat(0.f);
-      base[q] = make_float2(g0, g1);
+      if constexpr (FAST) {
+        const FastArgs& fa = a->fast;
+        auto level0 = [&](float g, float t) {   // (1 - a) F_j(p) + a F_{j+1}(p) at g = I_p
+          const int j = min((int)t, fa.S - 2);
+          const float al = t - (float)j;
+          return fmaf(al, fast_detail(fa, g, j + 1), (1.f - al) * fast_detail(fa, g, j));
+        };
+        const float t0 = fast_pos(fa, g0), t1 = fast_pos(fa, g1);
+        we[q] = make_float2(t0, 0.f);
+        wo[q] = make_float2(t1, 0.f);
+        base[q] = make_float2(g0 + level0(g0, t0), g1 + level0(g1, t1));
+      } else {
+        we[q] = conj_turns(a->turns * g0);
+        wo[q] = conj_turns(a->turns * g1);
+        base[q] = make_float2(g0, g1);
+      }
     };
     if (first) {
       fy = Y0 + 2 * tr;
@@ -1204,7 +1222,8 @@ __device__ __forceinline__ bool stage_down10(Res res, int total, unsigned char* 
         for (int rr = 0; rr < 2; ++rr)
 #pragma unroll
           for (int cc = 0; cc < 2; ++cc) {
-            w1[rr][cc] = conj_turns(a->turns * g1b[(2 * br + rr) * kDnCW + 2 * bc + cc]);
+            w1[rr][cc] = FAST ? make_float2(fast_pos(a->fast, g1b[(2 * br + rr) * kDnCW + 2 * bc + cc]), 0.f)
+                              : conj_turns(a->turns * g1b[(2 * br + rr) * kDnCW + 2 * bc + cc]);
             P1[rr][cc] = splat(0.f);
             up_e2[rr][cc] = 0.f;
           }
@@ -1258,8 +1277,15 @@ __device__ __forceinline__ bool stage_down10(Res res, int total, unsigned char* 
               f[1] = Cplx<S>::cvt(*reinterpret_cast<const CT*>(&q.y));
             }
 #pragma unroll
-            for (int cc = 0; cc < 2; ++cc)
-              P1[rr][cc] = horner(P1[rr][cc], w1[rr][cc], add2(f[cc], make_float2(-U[rr][cc].x, -U[rr][cc].y)));
+            for (int cc = 0; cc < 2; ++cc) {
+              const float2 d = add2(f[cc], make_float2(-U[rr][cc].x, -U[rr][cc].y));
+              if constexpr (FAST) {
+                const int s0 = 2 * (ch * kKC + kk);
+                P1[rr][cc].x = fmaf(fast_hat(w1[rr][cc].x, s0 + 1), d.y, fmaf(fast_hat(w1[rr][cc].x, s0), d.x, P1[rr][cc].x));
+              } else {
+                P1[rr][cc] = horner(P1[rr][cc], w1[rr][cc], d);
+              }
+            }
           }
         }
       }
@@ -1271,10 +1297,19 @@ __device__ __forceinline__ bool stage_down10(Res res, int total, unsigned char* 
     for (int kk = kKC - 1; kk >= 0; --kk) {
       float2 ue[4], uo[4];
       expand_2x4<S>(zw0 + kk * kDnCH * kDnCW, ue, uo);
+      if constexpr (FAST) {
+        const int s0 = 2 * (ch * kKC + kk);
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        Pe[q] = horner(Pe[q], we[q], ue[q]);
-        Po[q] = horner(Po[q], wo[q], uo[q]);
+        for (int q = 0; q < 4; ++q) {
+          Pe[q].x = fmaf(fast_hat(we[q].x, s0 + 1), ue[q].y, fmaf(fast_hat(we[q].x, s0), ue[q].x, Pe[q].x));
+          Po[q].x = fmaf(fast_hat(wo[q].x, s0 + 1), uo[q].y, fmaf(fast_hat(wo[q].x, s0), uo[q].x, Po[q].x));
+        }
+      } else {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          Pe[q] = horner(Pe[q], we[q], ue[q]);
+          Po[q] = horner(Po[q], wo[q], uo[q]);
+        }
       }
     }
 
@@ -1286,7 +1321,7 @@ __device__ __forceinline__ bool stage_down10(Res res, int total, unsigned char* 
           for (int cc = 0; cc < 2; ++cc) {
             const int y1 = cy0 + 2 * br + rr, x1 = cx0 + 2 * bc + cc;
             if (y1 >= 0 && y1 < L1.h && x1 >= 0 && x1 < L1.w) {
-              float d1 = im_mul(P1[rr][cc], w1[rr][cc]);
+              float d1 = FAST ? P1[rr][cc].x : im_mul(P1[rr][cc], w1[rr][cc]);
               if constexpr (ADAPT) d1 *= (__ldg(L1.M + (long long)y1 * L1.pitch + x1) - 1.f) * a->mscale;
               e1[(2 * br + rr) * kDnCW + 2 * bc + cc] = d1 + up_e2[rr][cc];
             }
@@ -1306,7 +1341,9 @@ __device__ __forceinline__ bool stage_down10(Res res, int total, unsigned char* 
           for (int q = 0; q < 4; ++q) {
             const int x = fx + q;
             const float2 sc = expand_scale_pair(q);
-            float delta = rr ? -sc.y * im_mul(Po[q], wo[q]) : -sc.x * im_mul(Pe[q], we[q]);
+            float delta;
+            if constexpr (FAST) delta = rr ? -sc.y * Po[q].x : -sc.x * Pe[q].x;
+            else delta = rr ? -sc.y * im_mul(Po[q], wo[q]) : -sc.x * im_mul(Pe[q], we[q]);
             if (x >= 0 && x < w0) {
               if constexpr (ADAPT) delta *= (__ldg(a->M0 + (long long)y * w0 + x) - 1.f) * a->mscale;
               d[x] = (rr ? base[q].y + ue[q].y : base[q].x + ue[q].x) + delta;
@@ -1398,15 +1435,15 @@ __global__ void __launch_bounds__(kThreads, 3) k_down0(const __grid_constant__ D
                     gridDim.x);
 }
 
-// ADAPT: pixel-adaptive gain map (Down10Args::M0 and l1.M set).
-template <typename S, bool ADAPT>
+// ADAPT: pixel-adaptive gain map (Down10Args::M0 and l1.M set); FAST: fast LLF.
+template <typename S, bool ADAPT, bool FAST>
 __global__ void __launch_bounds__(kThreads, 2) k_down10(const __grid_constant__ Down10Args a) {
   using SM = Smem<sizeof(typename Cplx<S>::T)>;
   extern __shared__ __align__(128) unsigned char smem[];
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem + SM::d10 - 64);
   init_bars(bar);
   Pipe pp{};
-  stage_down10<S, ADAPT>([&](int g, int& l) { l = g; return &a; }, combine_tiles(a.h0, a.w0, a.planes), smem, bar,
+  stage_down10<S, ADAPT, FAST>([&](int g, int& l) { l = g; return &a; }, combine_tiles(a.h0, a.w0, a.planes), smem, bar,
                   pp, blockIdx.x, gridDim.x);
 }
 
@@ -1730,12 +1767,15 @@ cudaError_t FLLF_LAUNCH_NAME(down0)(const Down0Args& a, cudaStream_t s, int cps)
 
 cudaError_t FLLF_LAUNCH_NAME(down10)(const Down10Args& a, cudaStream_t s, int cps) {
   const int tiles = cdiv(a.w0 + kDnX0, kDnOW) * cdiv(a.h0, kDnOH) * a.planes;
-  if (a.M0) {
-    const int grid = persistent_grid<k_down10<FLLF_STORAGE, true>>(SMS::d10, tiles, cps);
-    return launch_pdl(k_down10<FLLF_STORAGE, true>, grid, SMS::d10, s, a);
+  if (a.fast.S > 0) {
+    const int grid = persistent_grid<k_down10<FLLF_STORAGE, false, true>>(SMS::d10, tiles, cps);
+    return launch_pdl(k_down10<FLLF_STORAGE, false, true>, grid, SMS::d10, s, a);
+  } else if (a.M0) {
+    const int grid = persistent_grid<k_down10<FLLF_STORAGE, true, false>>(SMS::d10, tiles, cps);
+    return launch_pdl(k_down10<FLLF_STORAGE, true, false>, grid, SMS::d10, s, a);
   } else {
-    const int grid = persistent_grid<k_down10<FLLF_STORAGE, false>>(SMS::d10, tiles, cps);
-    return launch_pdl(k_down10<FLLF_STORAGE, false>, grid, SMS::d10, s, a);
+    const int grid = persistent_grid<k_down10<FLLF_STORAGE, false, false>>(SMS::d10, tiles, cps);
+    return launch_pdl(k_down10<FLLF_STORAGE, false, false>, grid, SMS::d10, s, a);
   }
 }
 
@@ -1763,7 +1803,7 @@ int FLLF_LAUNCH_NAME(occupancy)(int kind, int batched) {
     case 2: return batched ? resident_per_sm<k_down_batch<FLLF_STORAGE>>(SMS::dns, nullptr)
                            : resident_per_sm<k_down<FLLF_STORAGE>>(SMS::dn1, nullptr);
     case 3: return batched ? resident_per_sm<k_down10_batch<FLLF_STORAGE>>(SMS::d10, nullptr)
-                           : resident_per_sm<k_down10<FLLF_STORAGE, false>>(SMS::d10, nullptr);
+                           : resident_per_sm<k_down10<FLLF_STORAGE, false, false>>(SMS::d10, nullptr);
     case 4: {
       constexpr size_t kChainSmem = SMS::up > SMS::dn1 ? SMS::up : SMS::dn1;
       return resident_per_sm<k_chain<FLLF_STORAGE>>(kChainSmem, nullptr);

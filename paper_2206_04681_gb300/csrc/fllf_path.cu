@@ -216,7 +216,8 @@ namespace {
 
 // Fast LLF (Sec. II-D): the sampled detail images' pyramids (level-0 REDUCE,
 // then the REDUCE kernels unchanged), the interpolating combines on the
-// 32 x 16 tiles from the top down to level 1, and the level-0 combine.
+// 32 x 16 tiles from the top down to level 2, and levels 1 and 0 in the
+// fused level-0 tiles (the level-0 combine alone with 2 levels).
 cudaError_t enqueue_fast(const fllf_params& p, const std::vector<Level>& lv, const PathMaps& maps,
                          const float* d_a, unsigned* fault, const float* d_in, float* d_out, cudaStream_t s,
                          StageHook* hook, const Tuning& tn) {
@@ -259,7 +260,9 @@ cudaError_t enqueue_fast(const fllf_params& p, const std::vector<Level>& lv, con
     if ((e = launch_up(prec, u, s, tn.cps[FLLF_STAGE_UP])) != cudaSuccess) return e;
     mark(FLLF_STAGE_UP, false);
   }
-  for (int l = L - 2; l >= 1; --l) {
+  // with >= 3 levels, level 1 runs inside the level-0 tiles (as for Fourier LLF)
+  const int down_lo = L >= 3 ? 2 : 1;
+  for (int l = L - 2; l >= down_lo; --l) {
     DownArgs d{};
     d.zmap = maps.z_cs[l + 1];
     d.emap = maps.e_cs[l + 1];
@@ -276,21 +279,42 @@ cudaError_t enqueue_fast(const fllf_params& p, const std::vector<Level>& lv, con
     if ((e = launch_down_s(prec, d, s, tn.cps[FLLF_STAGE_DOWN_S])) != cudaSuccess) return e;
     mark(FLLF_STAGE_DOWN_S, false);
   }
-  Down0Args d0{};
-  d0.zmap = maps.z_dn[1];
-  d0.emap = maps.e_dn[1];
-  d0.I = d_in;
-  d0.O = d_out;
-  d0.h0 = p.H;
-  d0.w0 = p.W;
-  d0.planes = C;
-  d0.coarse = lv[1];
-  d0.K = p.K;
-  d0.has_e = (L >= 3) ? 1 : 0;
-  d0.fault = fault;
-  d0.fast = fa;
   mark(FLLF_STAGE_DOWN0, true);
-  if ((e = launch_down0(prec, d0, s, tn.cps[FLLF_STAGE_DOWN0])) != cudaSuccess) return e;
+  if (L >= 3) {
+    Down10Args d{};
+    d.z1map = maps.z_dn[1];
+    d.g1map = maps.g1_d10;
+    d.z2map = maps.z2_d10;
+    d.e2map = maps.e2_d10;
+    d.I = d_in;
+    d.O = d_out;
+    d.h0 = p.H;
+    d.w0 = p.W;
+    d.planes = C;
+    d.l1 = lv[1];
+    d.l2 = lv[2];
+    d.K = p.K;
+    d.has_e2 = (L >= 4) ? 1 : 0;
+    d.use_tma = (u0.use_tma && encode_image_map(&d.imap, d_in, p.W, p.H, C, kD0IW, kDnOH)) ? 1 : 0;
+    d.fault = fault;
+    d.fast = fa;
+    if ((e = launch_down10(prec, d, s, tn.cps[FLLF_STAGE_DOWN0])) != cudaSuccess) return e;
+  } else {
+    Down0Args d0{};
+    d0.zmap = maps.z_dn[1];
+    d0.emap = maps.e_dn[1];
+    d0.I = d_in;
+    d0.O = d_out;
+    d0.h0 = p.H;
+    d0.w0 = p.W;
+    d0.planes = C;
+    d0.coarse = lv[1];
+    d0.K = p.K;
+    d0.has_e = 0;
+    d0.fault = fault;
+    d0.fast = fa;
+    if ((e = launch_down0(prec, d0, s, tn.cps[FLLF_STAGE_DOWN0])) != cudaSuccess) return e;
+  }
   mark(FLLF_STAGE_DOWN0, false);
   return cudaSuccess;
 }
