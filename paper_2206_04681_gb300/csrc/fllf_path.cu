@@ -365,9 +365,10 @@ cudaError_t enqueue_path(const fllf_params& p, const std::vector<Level>& lv, con
     }
   }
 
-  // Levels >= c0 run as one chained cooperative launch: from the first level
-  // (>= 2) whose pixels over all planes fit in 2^21, the REDUCE stages up to
-  // the top and the combines back down to c0.
+  // With a chain threshold (tuning; 0 by default), levels >= c0 run as one
+  // chained cooperative launch: from the first level (>= 2) whose pixels over
+  // all planes fit in chain_px, the REDUCE stages up to the top and the
+  // combines back down to c0.
   const long long chain_px = tn.chain_px;
   int c0 = L - 1;
   for (int l = 2; l <= L - 2; ++l)
