@@ -179,6 +179,7 @@ constexpr int kChainMax = 12;
 struct ChainArgs {
   UpArgs up[kChainMax];     // REDUCE stages, finest first
   DownArgs dn[kChainMax];   // combine stages, coarsest first
+  int dn_small[kChainMax];  // combine stage on the 32 x 16 tiles (its maps are those boxes)
   int n_up, n_dn;
   unsigned* sync;           // grid barrier: [0] arrivals, [1] generation (zeroed by the plan)
   unsigned* fault;

@@ -1622,9 +1622,12 @@ __global__ void __launch_bounds__(kThreads, 2) k_chain(const __grid_constant__ C
   }
   for (int st = 0; st < a.n_dn; ++st) {
     const DownArgs* d = &a.dn[st];
-    if (!stage_combine1<S>([&](int g, int& l) { l = g; return d; },
-                           combine_tiles(d->fine.h, d->fine.w, d->planes), smem, bar, pp, b, G))
-      return;
+    const bool ok = a.dn_small[st]
+                        ? stage_combine_s<S>([&](int g, int& l) { l = g; return d; },
+                                             small_tiles(d->fine.h, d->fine.w, d->planes), smem, bar, pp, b, G)
+                        : stage_combine1<S>([&](int g, int& l) { l = g; return d; },
+                                            combine_tiles(d->fine.h, d->fine.w, d->planes), smem, bar, pp, b, G);
+    if (!ok) return;
     if (st + 1 < a.n_dn && !grid_barrier(a.sync, a.sync + 1, G, a.fault)) return;
   }
 }

@@ -415,7 +415,18 @@ cudaError_t enqueue_path(const fllf_params& p, const std::vector<Level>& lv, con
   if (c0 <= L - 2) {
     ChainArgs ca{};
     for (int l = c0; l <= L - 2; ++l) ca.up[ca.n_up++] = up_args(l);
-    for (int l = L - 2; l >= c0; --l) ca.dn[ca.n_dn++] = down_args(l);
+    for (int l = L - 2; l >= c0; --l) {
+      DownArgs d = down_args(l);
+      const bool small = (long long)lv[l].h * lv[l].w * C <= tn.small_px;
+      if (small) {   // the 32 x 16 tiles, as outside the chain
+        d.zmap = maps.z_cs[l + 1];
+        d.emap = maps.e_cs[l + 1];
+        d.zfmap = maps.z_fs[l];
+        d.gfmap = maps.g_fs[l];
+      }
+      ca.dn_small[ca.n_dn] = small ? 1 : 0;
+      ca.dn[ca.n_dn++] = d;
+    }
     ca.sync = fault + 32;
     ca.fault = fault;
     mark(FLLF_STAGE_CHAIN, true);
