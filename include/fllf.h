@@ -148,7 +148,8 @@ fllf_status fllf_plan_coeffs(const fllf_plan *plan, double *a_out);
 fllf_status fllf_run(fllf_plan *plan, const float *d_in, float *d_out, void *stream);
 
 /* Pixel-by-pixel enhancement (Sec. III-B): filters like fllf_run, but the
- * remap gain m is a per-pixel map instead of the plan's constant.  The
+ * remap gain m is a per-pixel map instead of the plan's constant (Fourier
+ * LLF plans only; a fast LLF plan gets FLLF_EINVAL).  The
  * Gaussian Fourier pyramids do not depend on the remap, so only the
  * coefficients change: at level l < top the Fourier term of Eq. (14) is
  * scaled by (m_{l,p} - 1) / (m - 1), where m is the plan's gain and
@@ -175,8 +176,13 @@ fllf_status fllf_run_adaptive(fllf_plan *plan, const float *d_in, const float *d
 fllf_status fllf_run_luma(fllf_plan *plan, const float *d_rgb_in, float *d_rgb_out, void *stream);
 
 /* End-to-end variant for host buffers: copies h_in to a plan-owned device
- * buffer, filters, copies the result to h_out and waits for the stream.
- * Allocates the two device I/O buffers on first use (kept by the plan). */
+ * buffer, filters, copies the result to h_out and waits for the work.
+ * Allocates the two device I/O buffers on first use (kept by the plan).
+ * With C >= 2 planes the planes are pipelined: the plan's two copy streams
+ * (created on first use) move plane c in and plane c-2 out while `stream`
+ * filters plane c-1, each plane on a one-plane view of the plan's scratch;
+ * the output is the same as fllf_run's, bit for bit.  Pinned host buffers
+ * let the copies overlap. */
 fllf_status fllf_run_host(fllf_plan *plan, const float *h_in, float *h_out, void *stream);
 
 /* Asynchronous form of fllf_run: enqueues the work and records a
