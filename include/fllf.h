@@ -136,7 +136,8 @@ fllf_status fllf_plan_create(const fllf_params *p, int device, fllf_plan **out);
  * sure no work of the plan is still running on any stream. */
 fllf_status fllf_plan_destroy(fllf_plan *plan);
 
-/* Copies the plan's parameters / float64 coefficients (K doubles). */
+/* Copies the plan's parameters (a fast LLF plan reports K = ceil(samples/2))
+ * / float64 coefficients (K doubles; FLLF_EINVAL for a fast LLF plan). */
 fllf_status fllf_plan_params(const fllf_plan *plan, fllf_params *out);
 fllf_status fllf_plan_coeffs(const fllf_plan *plan, double *a_out);
 

@@ -472,6 +472,7 @@ fllf_status fllf_plan_params(const fllf_plan* plan, fllf_params* out) {
 
 fllf_status fllf_plan_coeffs(const fllf_plan* plan, double* a_out) {
   if (!plan || !a_out) return fail(FLLF_EINVAL, "plan or a_out is NULL");
+  if (plan->p.method != FLLF_METHOD_FOURIER) return fail(FLLF_EINVAL, "fast LLF has no Fourier coefficients");
   std::memcpy(a_out, plan->a64.data(), sizeof(double) * plan->p.K);
   return FLLF_OK;
 }

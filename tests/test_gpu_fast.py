@@ -104,6 +104,9 @@ def test_fast_plans_rejected_where_unsupported():
         with pytest.raises(pkg.FllfError) as e:
             pkg.fllf_batch_create([plan])
         assert e.value.status == pkg.FLLF_EINVAL
+        with pytest.raises(pkg.FllfError) as e:
+            pkg.fllf_plan_coeffs(plan)
+        assert e.value.status == pkg.FLLF_EINVAL
     finally:
         pkg.fllf_plan_destroy(plan)
     server = pkg.fllf_server_create(1 << 28, 4, 16, 1, 0)
