@@ -76,9 +76,16 @@ struct Level {
 // detail with fm1 = m - 1, c2 = log2(e) / (2 sigma_r^2)); F_{2k} and F_{2k+1}
 // are the real and imaginary parts of complex plane k (the imaginary part of
 // the last plane is zero when S is odd).  S = 0: Fourier LLF.
+// rec = 1: within a chunk of 2 kKC consecutive samples the Gaussian factor
+// E_j = 2^(-c2 (i - tau j)^2) follows E_{j+1} = E_j r_j, r_{j+1} = r_j k2
+// (r_j = 2^(-c2 tau (2 (tau j - i) + tau)), k2 = 2^(-2 c2 tau^2)) from one
+// exact start per chunk; the host sets it only where neither r nor the start
+// leaves the float range for any pixel in [0, 1].
 struct FastArgs {
   int S;
   float tau, fm1, c2;
+  int rec;
+  float k2;
 };
 
 struct Up0Args {

@@ -161,6 +161,9 @@ __device__ __forceinline__ bool stage_up0(Res res, int total, unsigned char* sme
     float* hgw = hg + s * (kUpRun * kUpCS);          // [column][fine row]
     float2 zc[kUpIPX], zp[kUpIPX], tc[kUpIPX];
     float v[kUpIPX];
+    // fast LLF: per pixel, the Gaussian factor of the current sample and its
+    // ratio to the next (kept within 85 registers: 3 CTAs per SM)
+    float fe[FAST ? kUpIPX : 1], fr[FAST ? kUpIPX : 1];
     {
       {
         const float4* row = reinterpret_cast<const float4*>(it + rl * kUpIW + 2 * kUpRun * s);
@@ -200,9 +203,34 @@ __device__ __forceinline__ bool stage_up0(Res res, int total, unsigned char* sme
           if constexpr (FAST) {
             const int s0 = 2 * (ch * kKC + kk);
             const bool s1 = s0 + 1 < a.fast.S;
+            if (a.fast.rec) {
+              // Gaussian factors by the multiplicative recurrence from the
+              // chunk's first sample (exact start, two exp2 per pixel and
+              // chunk): E_{j+1} = E_j r_j, r_{j+1} = r_j k2
+              if (kk == 0) {
 #pragma unroll
-            for (int j = 0; j < kUpIPX; ++j)
-              zc[j] = make_float2(fast_detail(a.fast, v[j], s0), s1 ? fast_detail(a.fast, v[j], s0 + 1) : 0.f);
+                for (int j = 0; j < kUpIPX; ++j) {
+                  const float d0 = fmaf(-a.fast.tau, (float)s0, v[j]);
+                  fe[j] = exp2f(-a.fast.c2 * d0 * d0);
+                  fr[j] = exp2f(a.fast.c2 * a.fast.tau * fmaf(2.f, d0, -a.fast.tau));
+                }
+              }
+#pragma unroll
+              for (int j = 0; j < kUpIPX; ++j) {
+                const float d0 = fmaf(-a.fast.tau, (float)s0, v[j]), d1 = d0 - a.fast.tau;
+                const float f0 = a.fast.fm1 * d0 * fe[j];
+                fe[j] *= fr[j];
+                fr[j] *= a.fast.k2;
+                const float f1 = s1 ? a.fast.fm1 * d1 * fe[j] : 0.f;
+                fe[j] *= fr[j];
+                fr[j] *= a.fast.k2;
+                zc[j] = make_float2(f0, f1);
+              }
+            } else {
+#pragma unroll
+              for (int j = 0; j < kUpIPX; ++j)
+                zc[j] = make_float2(fast_detail(a.fast, v[j], s0), s1 ? fast_detail(a.fast, v[j], s0 + 1) : 0.f);
+            }
           }
 #pragma unroll
           for (int q = 0; q < kUpRun; ++q)

@@ -4,6 +4,7 @@
 #include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 
+#include <cmath>
 #include <cstdlib>
 #include <mutex>
 #include <string>
@@ -227,6 +228,18 @@ cudaError_t enqueue_fast(const fllf_params& p, const std::vector<Level>& lv, con
   fa.tau = (float)(1.0 / (p.samples - 1));
   fa.fm1 = (float)(p.m - 1.0);
   fa.c2 = (float)(1.4426950408889634 / (2.0 * p.sigma_r * p.sigma_r));   // log2(e) / (2 sigma_r^2)
+  {
+    // The level-0 REDUCE may step the Gaussian factor through each chunk of
+    // 2 kKC samples by products instead of one exp2 per sample when, for
+    // every pixel value in [0, 1]: the ratio's exponent stays within
+    // +-60 (c2 tau (2 + tau)); and the chunk's start factor stays a normal
+    // float (exponent >= -126) wherever a factor inside the chunk is not
+    // negligible (>= 2^-24), i.e. (sqrt(24) + (2 kKC - 1) tau sqrt(c2))^2 <= 126.
+    const double c2 = 1.4426950408889634 / (2.0 * p.sigma_r * p.sigma_r), tau = 1.0 / (p.samples - 1);
+    const double spread = std::sqrt(24.0) + (2 * kKC - 1) * tau * std::sqrt(c2);
+    fa.rec = (c2 * tau * (2.0 + tau) <= 60.0 && spread * spread <= 126.0) ? 1 : 0;
+    fa.k2 = (float)std::exp2(-2.0 * c2 * tau * tau);
+  }
   auto mark = [&](int st, bool b) {
     if (hook) hook->mark(st, b, s);
   };
