@@ -1154,6 +1154,10 @@ __device__ __forceinline__ bool stage_down10(Res res, int total, unsigned char* 
   float2 w1[2][2], P1[2][2];
   float up_e2[2][2];
   int fy = 0, fx = 0, pl = 0, X0 = 0, Y0 = 0;
+  // per tile, CTA-uniform: the windows lie inside levels 1 and 2 (no border
+  // fix-ups, level-1 cells written unguarded), the 64 x 32 output lies
+  // inside the image (stored unguarded)
+  bool inner = false, full = false;
   for (int i = 0;; ++i) {
     const int buf = i & 1;
     const int h0 = a->h0, w0 = a->w0;
@@ -1163,6 +1167,10 @@ __device__ __forceinline__ bool stage_down10(Res res, int total, unsigned char* 
       pl = g.pl;
       X0 = g.tx * kDnOW - kDnX0;
       Y0 = g.ty * kDnOH;
+      const int wx = X0 / 2 - 1, wy = Y0 / 2 - 1, vx = wx / 2 - 2, vy = (wy - 1) / 2;
+      inner = wx >= 0 && wy >= 0 && wx + kDnCW <= a->l1.w && wy + kDnCH <= a->l1.h && vx >= 0 && vy >= 0 &&
+              vx + kD2W <= a->l2.w && vy + kD2H <= a->l2.h;
+      full = X0 >= 0 && X0 + kDnOW <= w0 && Y0 + kDnOH <= h0;
     }
     const int cx0 = X0 / 2 - 1, cy0 = Y0 / 2 - 1;
     const int c2x = cx0 / 2 - 2, c2y = (cy0 - 1) / 2;
@@ -1234,9 +1242,6 @@ __device__ __forceinline__ bool stage_down10(Res res, int total, unsigned char* 
     auto mx1 = [&](int x) { return ext_coarse(x, L1.w, w0); };
     auto my2 = [&](int y) { return ext_coarse(y, L2.h, L1.h); };
     auto mx2 = [&](int x) { return ext_coarse(x, L2.w, L1.w); };
-    // tiles whose windows lie inside levels 1 and 2 (CTA-uniform) skip the border fix-ups
-    const bool inner = cx0 >= 0 && cy0 >= 0 && cx0 + kDnCW <= L1.w && cy0 + kDnCH <= L1.h && c2x >= 0 &&
-                       c2y >= 0 && c2x + kD2W <= L2.w && c2y + kD2H <= L2.h;
     if (!inner) {
       fix_borders(z1b, kKC, kDnCH, kDnCW, cx0, cy0, L1.w, L1.h, my1, mx1);
       fix_borders(z2b, kKC, kD2H, kD2W, c2x, c2y, L2.w, L2.h, my2, mx2);
@@ -1342,43 +1347,53 @@ __device__ __forceinline__ bool stage_down10(Res res, int total, unsigned char* 
     }
 
     if (last) {
-      if (l1t) {
+      // E_1 = Delta_1 + up(E_2) on the window cells inside level 1
+      auto write_e1 = [&](auto guarded) {
 #pragma unroll
         for (int rr = 0; rr < 2; ++rr)
 #pragma unroll
           for (int cc = 0; cc < 2; ++cc) {
             const int y1 = cy0 + 2 * br + rr, x1 = cx0 + 2 * bc + cc;
-            if (y1 >= 0 && y1 < L1.h && x1 >= 0 && x1 < L1.w) {
+            if (!decltype(guarded)::value || (y1 >= 0 && y1 < L1.h && x1 >= 0 && x1 < L1.w)) {
               float d1 = FAST ? P1[rr][cc].x : im_mul(P1[rr][cc], w1[rr][cc]);
               if constexpr (ADAPT) d1 *= (__ldg(L1.M + (long long)y1 * L1.pitch + x1) - 1.f) * a->mscale;
               e1[(2 * br + rr) * kDnCW + 2 * bc + cc] = d1 + up_e2[rr][cc];
             }
           }
+      };
+      if (l1t) {
+        if (inner) write_e1(std::false_type{});
+        else write_e1(std::true_type{});
       }
       __syncthreads();
       if (!inner) fix_borders(e1, 1, kDnCH, kDnCW, cx0, cy0, L1.w, L1.h, my1, mx1);
       float2 ue[4];
       expand_e_2x4(e1 + tr * kDnCW + 2 * tc, ue);
       float* dst = a->O + (long long)pl * h0 * w0;
+      // O = I + Delta_0 + up(E_1) at the thread's 2 x 4 pixels inside the image
+      auto write_o = [&](auto guarded) {
 #pragma unroll
-      for (int rr = 0; rr < 2; ++rr) {
-        const int y = fy + rr;
-        if (y < h0) {
-          float* d = dst + (long long)y * w0;
+        for (int rr = 0; rr < 2; ++rr) {
+          const int y = fy + rr;
+          if (!decltype(guarded)::value || y < h0) {
+            float* d = dst + (long long)y * w0;
 #pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            const int x = fx + q;
-            const float2 sc = expand_scale_pair(q);
-            float delta;
-            if constexpr (FAST) delta = rr ? -sc.y * Po[q].x : -sc.x * Pe[q].x;
-            else delta = rr ? -sc.y * im_mul(Po[q], wo[q]) : -sc.x * im_mul(Pe[q], we[q]);
-            if (x >= 0 && x < w0) {
-              if constexpr (ADAPT) delta *= (__ldg(a->M0 + (long long)y * w0 + x) - 1.f) * a->mscale;
-              d[x] = (rr ? base[q].y + ue[q].y : base[q].x + ue[q].x) + delta;
+            for (int q = 0; q < 4; ++q) {
+              const int x = fx + q;
+              const float2 sc = expand_scale_pair(q);
+              float delta;
+              if constexpr (FAST) delta = rr ? -sc.y * Po[q].x : -sc.x * Pe[q].x;
+              else delta = rr ? -sc.y * im_mul(Po[q], wo[q]) : -sc.x * im_mul(Pe[q], we[q]);
+              if (!decltype(guarded)::value || (x >= 0 && x < w0)) {
+                if constexpr (ADAPT) delta *= (__ldg(a->M0 + (long long)y * w0 + x) - 1.f) * a->mscale;
+                d[x] = (rr ? base[q].y + ue[q].y : base[q].x + ue[q].x) + delta;
+              }
             }
           }
         }
-      }
+      };
+      if (full) write_o(std::false_type{});
+      else write_o(std::true_type{});
     }
     __syncthreads();
     if (*abortp) {
