@@ -126,3 +126,22 @@ def test_fast_llf_approaches_naive_llf_with_more_samples():
     naive = o.naive_llf(img.astype(np.float64), L, lambda d: o.remap_detail(d, m, sigma), window=False)
     errs = [float(np.max(np.abs(_run(img[None], L, S, m, sigma)[0] - naive))) for S in (4, 8, 16, 32)]
     assert errs[0] > errs[1] > errs[2] > errs[3]
+
+
+def test_autotune_on_a_fast_plan_keeps_the_output():
+    img = synth_image(300, 420, 3, polygons=6, seed=48)
+    plan = pkg.fllf_plan_create(pkg.make_fast_params(300, 420, 3, 6, 12, 3.0, 0.2), 0)
+    try:
+        x = torch.from_numpy(img).cuda()
+        ref = torch.empty_like(x)
+        pkg.run_tensor(plan, x, ref)
+        y = torch.empty_like(x)
+        t, ms = pkg.fllf_plan_autotune(plan, x.data_ptr(), y.data_ptr(), reps=2,
+                                       stream=torch.cuda.current_stream().cuda_stream)
+        assert ms > 0
+        z = torch.full_like(x, float("nan"))
+        pkg.run_tensor(plan, x, z)
+        torch.cuda.synchronize()
+        np.testing.assert_array_equal(z.cpu().numpy(), ref.cpu().numpy())
+    finally:
+        pkg.fllf_plan_destroy(plan)

@@ -98,3 +98,15 @@ def test_sampling_error_bound_and_decay():
         assert err <= (levels - 1) * tau * tau * sup_f2 / 4.0
         errs.append(err)
     assert errs[0] > errs[1] > errs[2] > errs[3]
+
+
+def test_windowed_naive_with_the_interpolated_remap():
+    # the exact dependency windows of naive LLF hold for a remap of (i, g) too
+    img = _img(44, 52, 12)
+    levels, S, m, sigma = 4, 7, 3.0, 0.2
+    samples, _ = o.fast_samples(S)
+    r = _hat_remap(samples, m, sigma)
+    whole = o.naive_llf(img, levels, None, window=False, remap_fn=r)
+    windowed = o.naive_llf(img, levels, None, window=True, remap_fn=r)
+    assert np.max(np.abs(windowed - whole)) <= 1e-12
+    assert np.max(np.abs(o.fast_llf(img, levels, S, m, sigma) - windowed)) <= 1e-12
