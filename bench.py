@@ -44,9 +44,10 @@ def parse():
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--workload", choices=["uhd", "batch", "serve"], default="uhd",
                     help="uhd: the 4K RGB headline (plus fast LLF at the same pyramid count and a "
-                         "short served stream); batch: 64 mixed images, batched vs looped; serve: "
-                         "Poisson request streams.  Accuracy against the float64 oracle is "
-                         "measured by tests/accuracy.py")
+                         "short served stream, and the timed frame's accuracy against the float64 "
+                         "oracle); batch: 64 mixed images, batched vs looped; serve: Poisson "
+                         "request streams.  The precision sweep and the served-request accuracy "
+                         "are in tests/accuracy.py")
     ap.add_argument("--serve-seconds", type=float, default=None,
                     help="length of each served stream (default 30 s; 4 s in the uhd line)")
     ap.add_argument("--serve-rates", type=str, default=None,
@@ -98,75 +99,104 @@ def stage_split(cfg, chain_px=CHAIN_PIXELS, small_px=SMALL_PIXELS):
     return up_levels, chain_up, chain_down, down_levels, small_levels, fused
 
 
-def stage_work(cfg, zbytes, chain_px=CHAIN_PIXELS, small_px=SMALL_PIXELS):
-    """Algorithmic FP32 ops and bytes per stage kind for one frame (all planes).
+def level_ops(cfg):
+    """Algorithmic FP32 ops (FMA = 1) per level-l pixel of one plane, by part.
 
-    Ops (FMA = 1; the method's separable stencil count with Horner's rule
-    over the orders):
-      trig per evaluated pixel      16 (sincospi and its fix-up); the REDUCE of
-                                    level 0 adds 2 (K - 1) for the recurrence
-                                    over the orders
-      REDUCE per output per image   13 (2 horizontal x 4 + vertical 4 + scale)
-      combine per pixel and order   10 at level 0 (6 EXPAND + 4 complex
-                                    multiply-add), 12 at level >= 1 (+2 for
-                                    Z_l - up(Z_{l+1}))
-      residual EXPAND + add         4 per pixel
-    Bytes: each input element read once and each output written once; the
-    level-1 combine inside the level-0 stage reads G_1, Z_1 (shared with the
-    level-0 EXPAND), Z_2 and E_2, and writes nothing.
-    """
+    The design-independent lower-bound count of the method (Eq. (14) with
+    2K + 1 pyramids), split by the level it is spent on:
+      trig0      level 0 only: one sincospi and 4 (K - 1) for the rotation
+                 to the higher orders                                   4K + 16
+      reduce     REDUCE l -> l+1 of the 2K + 1 images: symmetric 5-tap, 4 ops
+                 per 1-D output, N/2 horizontal + N/4 vertical outputs  3 (2K + 1)
+      combine    EXPAND of the 2K images (1.5 ops per 1-D output over
+                 N/2 + N outputs), the Laplacian difference and the
+                 product with the coefficient pair, per image  2K (2.25 + 1 + 1)
+      gtrig      the coefficient pairs (cos, sin)(w_k g) at a level l >= 1
+                                                                        4K + 16
+      resid      the residual EXPAND and the per-pixel remainder         11.25
+    Summed over the levels (x 4/3 for the per-level parts, x 1/3 for gtrig)
+    this is 24.7 K + 40 per value: 237 at K = 8, the count 25 K + 35 of the
+    method's op table up to its rounding."""
+    K = cfg["K"]
+    return {"trig0": 4 * K + 16, "reduce": 3 * (2 * K + 1), "combine": 2 * K * 4.25,
+            "gtrig": 4 * K + 16, "resid": 11.25}
+
+
+def stage_accounts(cfg, zbytes, chain_px=CHAIN_PIXELS, small_px=SMALL_PIXELS):
+    """Per stage kind, for one frame (all planes): algorithmic ops, the
+    minimum HBM bytes of the stage's image and guide operands, and the bytes
+    of the Fourier and residual pyramid operands it reads and writes.
+
+    ops: ``level_ops`` per level, attributed to the stage that spends them
+    (the level-0 trig and REDUCE to up0; REDUCE l -> l+1 to up / chain; the
+    combine, its coefficient pairs and the residual EXPAND of level l to the
+    stage that combines level l).
+    hbm_min: the input read, the output write and each guide level G_l read
+    or written by the stage, 4 B per value: the algorithmic bytes.
+    pyramid: Z_l (zbytes per complex sample, K per pixel) and E_l (4 B)
+    operand bytes, each element read once and written once: traffic the
+    method's algorithm does not need (the path materialises the pyramids).
+    Returns (ops, hbm_min, pyramid), dicts keyed by stage kind."""
     L, K, C = cfg["levels"], cfg["K"], cfg["C"]
     sz = level_sizes(cfg["H"], cfg["W"], L)
     n = [h * w for h, w in sz]
-    trig = 16
+    lo = level_ops(cfg)
     up_levels, chain_up, chain_down, down_levels, small_levels, fused = stage_split(cfg, chain_px, small_px)
     ops = dict.fromkeys(STAGES, 0.0)
-    byt = dict.fromkeys(STAGES, 0.0)
+    hbm = dict.fromkeys(STAGES, 0.0)
+    pyr = dict.fromkeys(STAGES, 0.0)
 
-    def reduce_work(l):
+    def add(stage, o, h, p):
+        ops[stage] += o
+        hbm[stage] += h
+        pyr[stage] += p
+
+    def reduce_acc(l):   # l -> l+1, l >= 1
         g = 1 if l + 1 <= L - 2 else 0
-        return (n[l + 1] * 13 * (2 * K + g),
-                (4 * n[l] * g + zbytes * K * n[l]) + (4 * n[l + 1] * g + zbytes * K * n[l + 1]))
+        return (n[l] * lo["reduce"], 4 * n[l] * g + 4 * n[l + 1] * g,
+                zbytes * K * (n[l] + n[l + 1]))
 
-    def combine_work(l):
+    def combine_acc(l):  # level l >= 1 on its own tiles: G_l read; Z_l, Z_{l+1}, E_{l+1} read, E_l written
         e = 1 if l + 1 <= L - 2 else 0
-        return (n[l] * (trig + 12 * K + 4 * e),
-                4 * n[l] + zbytes * K * n[l] + zbytes * K * n[l + 1] + 4 * n[l + 1] * e + 4 * n[l])
+        return (n[l] * (lo["combine"] + lo["gtrig"] + lo["resid"]), 4 * n[l],
+                zbytes * K * (n[l] + n[l + 1]) + 4 * n[l + 1] * e + 4 * n[l])
 
     if L >= 2:
-        ops["up0"] = n[0] * (trig + 2 * (K - 1)) + n[1] * 13 * (2 * K + 1)
-        byt["up0"] = 4 * n[0] + 4 * n[1] + zbytes * K * n[1]
+        add("up0", n[0] * (lo["trig0"] + lo["reduce"]), 4 * n[0] + 4 * n[1] * (1 if L >= 3 else 0),
+            zbytes * K * n[1])
     for l in up_levels:
-        o, b = reduce_work(l)
-        ops["up"] += o
-        byt["up"] += b
+        add("up", *reduce_acc(l))
     for l in chain_up:
-        o, b = reduce_work(l)
-        ops["chain"] += o
-        byt["chain"] += b
+        add("chain", *reduce_acc(l))
     for l in chain_down:
-        o, b = combine_work(l)
-        ops["chain"] += o
-        byt["chain"] += b
+        add("chain", *combine_acc(l))
     for l in down_levels:
-        o, b = combine_work(l)
-        ops["down"] += o
-        byt["down"] += b
+        add("down", *combine_acc(l))
     for l in small_levels:
-        o, b = combine_work(l)
-        ops["down_s"] += o
-        byt["down_s"] += b
+        add("down_s", *combine_acc(l))
     if L >= 2:
-        e1 = 1 if L >= 3 else 0
-        ops["down0"] = n[0] * (trig + 10 * K + 4 * e1)
-        byt["down0"] = 4 * n[0] + zbytes * K * n[1] + 4 * n[0]
+        # level 0: I read, O written, Z_1 (and E_1 when levels >= 3, unless fused) read
+        add("down0", n[0] * (lo["combine"] + lo["resid"]), 8 * n[0],
+            zbytes * K * n[1] + (4 * n[1] if L >= 3 and not fused else 0))
         if fused:
+            # level 1 inside the level-0 tiles: G_1 read, Z_2 and E_2 read (Z_1 shared)
             e2 = 1 if L >= 4 else 0
-            ops["down0"] += n[1] * (trig + 12 * K + 4 * e2)
-            byt["down0"] += 4 * n[1] + zbytes * K * n[2] + 4 * n[2] * e2
-        else:
-            byt["down0"] += 4 * n[1] * e1
-    return {k: v * C for k, v in ops.items()}, {k: v * C for k, v in byt.items()}
+            add("down0", n[1] * (lo["combine"] + lo["gtrig"] + lo["resid"]), 4 * n[1],
+                zbytes * K * n[2] + 4 * n[2] * e2)
+    f = lambda d: {k: v * C for k, v in d.items()}
+    return f(ops), f(hbm), f(pyr)
+
+
+def step_ops(cfg):
+    """Algorithmic ops of one whole step (every level of every plane)."""
+    ops, _, _ = stage_accounts(cfg, 8)
+    return sum(ops.values())
+
+
+# kernel launched by each stage kind (the level-0 stage is the fused
+# level-1/level-0 combine when levels >= 3)
+STAGE_KERNEL = {"up0": "k_up0", "up": "k_up", "down": "k_down", "down0": "k_down10",
+                "chain": "k_chain", "down_s": "k_down_s"}
 
 
 def hbm_min_bytes(cfg):
@@ -226,54 +256,175 @@ class ClockSampler:
                 "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows)}
 
 
-def cpu_oracle_sample():
-    """Float64 oracle on channel 0 of the 4K frame (one of three planes)."""
+# ---- the float64 oracle on the host cores (cpu_baseline, accuracy, --impl reference) ----
+def host_cores():
+    """Cores this process may run on (the pool's worker count)."""
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def _oracle_warm(_):
+    import oracle  # noqa: F401  (the import is the warm-up)
+    time.sleep(0.2)
+    return os.getpid()
+
+
+def _oracle_job(job):
+    """Worker: the float64 oracle, as it stands, on one plane (or a tile of
+    one) of the frame in shared memory; with ``ref`` set, the result is
+    written into the shared float64 reference frame."""
     import numpy as np
+    from multiprocessing import shared_memory
     import oracle
-    from paper_2206_04681_gb300.synth import synth_image
+    name, shape, c, y0, y1, x0, x1, levels, a, T, ref = job
+    shm = shared_memory.SharedMemory(name=name)
+    try:
+        x = np.ndarray(shape, dtype=np.float32, buffer=shm.buf)[c, y0:y1, x0:x1].astype(np.float64)
+    finally:
+        shm.close()
+    y = oracle.fourier_llf(x, levels, a, T)
+    if ref is not None:
+        rs = shared_memory.SharedMemory(name=ref)
+        try:
+            np.ndarray(shape, dtype=np.float64, buffer=rs.buf)[c, y0:y1, x0:x1] = y
+        finally:
+            rs.close()
+    return 0
+
+
+class OraclePool:
+    """A spawned process pool over the host cores that runs the float64
+    oracle on the planes of a frame held in shared memory."""
+
+    def __init__(self, img, cores=None):
+        import multiprocessing as mp
+        from multiprocessing import shared_memory
+        import numpy as np
+        self.cores = cores or host_cores()
+        self.shape = img.shape
+        self.shm = shared_memory.SharedMemory(create=True, size=img.nbytes)
+        np.ndarray(img.shape, dtype=np.float32, buffer=self.shm.buf)[:] = img
+        self.ref = shared_memory.SharedMemory(create=True, size=img.size * 8)
+        self.pool = mp.get_context("spawn").Pool(self.cores)
+        self.pool.map(_oracle_warm, range(self.cores), chunksize=1)
+
+    def jobs(self, specs, cfg, a):
+        return [(self.shm.name, self.shape, c, y0, y1, x0, x1, cfg["levels"], a, cfg["T"],
+                 self.ref.name if keep else None) for c, y0, y1, x0, x1, keep in specs]
+
+    def run(self, specs, cfg, a):
+        """Wall seconds of the oracle over the given (plane, tile, keep) specs."""
+        jobs = self.jobs(specs, cfg, a)
+        t0 = time.perf_counter()
+        if len(jobs) == 1:
+            self.pool.apply(_oracle_job, (jobs[0],))
+        else:
+            self.pool.map(_oracle_job, jobs, chunksize=1)
+        return time.perf_counter() - t0
+
+    def reference(self):
+        import numpy as np
+        return np.ndarray(self.shape, dtype=np.float64, buffer=self.ref.buf)
+
+    def close(self):
+        self.pool.close()
+        self.pool.join()
+        for s in (self.shm, self.ref):
+            s.close()
+            s.unlink()
+
+
+def accuracy_of(out, ref):
+    """max |GPU - oracle| and PSNR (peak 1, over every value) of a frame."""
+    import numpy as np
+    d = np.asarray(out, np.float64) - ref
+    mse = float(np.mean(d * d))
+    return {"max_abs": float(np.max(np.abs(d))),
+            "psnr_db": None if mse == 0 else float(10 * np.log10(1.0 / mse))}
+
+
+def cpu_baseline_and_accuracy(img, outs):
+    """The float64 oracle on the host cores: the 4K RGB frame's planes, one
+    per worker, on every core at once, and channel 0 alone on one core.
+    Both are bounded samples of the workload (one plane per core).  The
+    oracle's output for the three planes of the frame also gives the
+    accuracy of each GPU output in ``outs`` ({name: (C, H, W) array})."""
+    import oracle
     cfg = WORKLOAD
-    img = synth_image(cfg["H"], cfg["W"], cfg["C"], cfg["polygons"], cfg["seed"])
     a = oracle.coeffs_quadrature(cfg["m"], cfg["sigma_r"], cfg["T"], cfg["K"])
-    t0 = time.perf_counter()
-    oracle.fourier_llf(img[0].astype(np.float64), cfg["levels"], a, cfg["T"])
-    dt = time.perf_counter() - t0
-    frame_s = dt * cfg["C"]
-    return {"value": cfg["H"] * cfg["W"] / frame_s / 1e6, "unit": UNIT, "cores": 1,
-            "kind": "oracle",
-            "sample": f"float64 numpy oracle, channel 0 of the 3840x2160x3 frame "
-                      f"({dt:.1f} s; frame time = 3 x plane time)"}
+    H, W, C = cfg["H"], cfg["W"], cfg["C"]
+    op = OraclePool(img)
+    try:
+        cores = op.cores
+        one = op.run([(0, 0, H, 0, W, True)], cfg, a)
+        specs = [(i % C, 0, H, 0, W, i < C) for i in range(max(cores, C))]
+        t_all = op.run(specs, cfg, a)
+        ref = op.reference().copy()
+    finally:
+        op.close()
+    planes = len(specs)
+    base = {"value": planes * H * W / C / t_all / 1e6, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "nproc": os.cpu_count(),
+            "sample": f"float64 numpy oracle, unchanged, in a spawned pool of {cores} processes on "
+                      f"{cores} host cores: {planes} planes of the 3840x2160x3 frame at once, one "
+                      f"per process ({t_all:.1f} s wall; Mpixel/s counts a pixel once over its "
+                      f"{C} planes)",
+            "one_core": {"value": H * W / C / one / 1e6, "unit": UNIT, "cores": 1,
+                         "sample": f"channel 0 of the frame on one core ({one:.1f} s)"}}
+    acc = {name: dict(accuracy_of(o, ref), vs="float64 oracle, all 3 planes of the frame")
+           for name, o in outs.items()}
+    return base, acc
 
 
 def run_reference(args):
-    """Reference arm: the float64 CPU oracle as it stands, on host cores."""
+    """Reference arm: the float64 CPU oracle as it stands, on every host core.
+
+    Each step filters one tile-plane per core at once (960 x 540 tiles of the
+    3840 x 2160 x 3 frame, cycled over its 48 tile-planes; smaller tiles when
+    the step count is large, so that the run stays within a few minutes)."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
-    import numpy as np
     import oracle
     from paper_2206_04681_gb300.synth import synth_image
     cfg = WORKLOAD
     img = synth_image(cfg["H"], cfg["W"], cfg["C"], cfg["polygons"], cfg["seed"])
     a = oracle.coeffs_quadrature(cfg["m"], cfg["sigma_r"], cfg["T"], cfg["K"])
-    # each step: one plane of a 960 x 540 crop (a bounded sample of the frame)
-    crop = img[0, 810:1350, 1440:2400].astype(np.float64)
-    for _ in range(args.warmup):
-        oracle.fourier_llf(crop, cfg["levels"], a, cfg["T"])
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        oracle.fourier_llf(crop, cfg["levels"], a, cfg["T"])
-    dt = (time.perf_counter() - t0) / args.steps
-    value = crop.size / (dt * cfg["C"]) / 1e6   # a pixel counts once over its 3 channels
-    sample = "float64 numpy oracle on one plane of a 960x540 crop per step (RGB time = 3 x plane)"
+    n = args.steps + args.warmup
+    div = 4 if n <= 150 else 8 if n <= 600 else 16
+    th, tw = cfg["H"] // div, cfg["W"] // div
+    tiles = [(c, ty * th, (ty + 1) * th, tx * tw, (tx + 1) * tw)
+             for c in range(cfg["C"]) for ty in range(div) for tx in range(div)]
+    op = OraclePool(img)
+    k = 0
+
+    def step():
+        nonlocal k
+        specs = [tiles[(k + j) % len(tiles)] + (False,) for j in range(op.cores)]
+        k += op.cores
+        return op.run(specs, cfg, a)
+
+    try:
+        for _ in range(args.warmup):
+            step()
+        dt = sum(step() for _ in range(args.steps)) / args.steps
+    finally:
+        op.close()
+    value = op.cores * th * tw / cfg["C"] / dt / 1e6   # a pixel counts once over its 3 channels
+    sample = (f"float64 numpy oracle, unchanged, in a spawned pool of {op.cores} processes on {op.cores} "
+              f"host cores; each step filters {op.cores} tile-planes of {tw}x{th} of the frame at once")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
             "config": {"workload": "uhd_rgb_3840x2160x3_L8_K8", "H": cfg["H"], "W": cfg["W"],
                        "C": cfg["C"], "levels": cfg["levels"], "K": cfg["K"], "m": cfg["m"],
-                       "sigma_r": cfg["sigma_r"], "T": cfg["T"], "sample": "960x540 crop, 1 plane"},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": sample},
+                       "sigma_r": cfg["sigma_r"], "T": cfg["T"],
+                       "sample": f"{op.cores} tile-planes of {tw}x{th} per step"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": op.cores, "nproc": os.cpu_count(),
+                             "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -309,7 +460,8 @@ def whole_job_mpixel_s(world, pixels_per_rank_step, seconds_per_step):
 
 
 def time_precision(pkg, torch, cfg, precision, frames, steps, warmup, stream, device, params=None):
-    """ms per frame of a plan (autotuned), back to back over the cycled frames."""
+    """ms per frame of a plan (autotuned), back to back over the cycled
+    frames, and the plan's output of the first frame (host array)."""
     p = params or pkg.make_params(cfg["H"], cfg["W"], cfg["C"], cfg["levels"], cfg["K"], cfg["m"],
                                   cfg["sigma_r"], cfg["T"], precision)
     plan = pkg.fllf_plan_create(p, device)
@@ -330,9 +482,13 @@ def time_precision(pkg, torch, cfg, precision, frames, steps, warmup, stream, de
             e1.record(stream)
             e1.synchronize()
         ms = e0.elapsed_time(e1) / steps
+        with torch.cuda.stream(stream):
+            pkg.fllf_run(plan, frames[0].data_ptr(), outs[0].data_ptr(), stream.cuda_stream)
+        stream.synchronize()
+        out0 = outs[0].cpu().numpy()
     finally:
         pkg.fllf_plan_destroy(plan)
-    return ms
+    return ms, out0
 
 
 def run_ours(args):
@@ -430,15 +586,20 @@ def run_ours(args):
         pkg.fllf_run_host(plan, hin.data_ptr(), hout.data_ptr(), stream.cuda_stream)
     e2e_s = max_over_ranks((time.perf_counter() - t0) / e2e_steps, world, "cuda")
     tn = pkg.fllf_plan_get_tuning(plan)
+    # the timed frames are copies of one frame: its output is every timed step's
+    with torch.cuda.stream(stream):
+        pkg.fllf_run(plan, frames[0].data_ptr(), outs[0].data_ptr(), stream.cuda_stream)
+    stream.synchronize()
+    out_acc = outs[0].cpu().numpy()
     pkg.fllf_plan_destroy(plan)
 
     zbytes = 8 if args.precision == "fp32" else 4
-    ops, byt = stage_work(cfg, zbytes, tn.chain_pixels, tn.small_pixels)
+    ops, hbm_b, pyr_b = stage_accounts(cfg, zbytes, tn.chain_pixels, tn.small_pixels)
     dom_ms, dom_launches = stage[dom]                  # timed region, dominant kernel only
     per_launch_s = dom_ms / max(dom_launches, 1) * 1e-3
     launches_per_step = {s: pre[s][1] / pre_steps for s in STAGES}
-    ops_launch = ops[dom] / max(launches_per_step[dom], 1)
-    byt_launch = byt[dom] / max(launches_per_step[dom], 1)
+    per = max(launches_per_step[dom], 1)
+    ops_launch, hbm_launch, pyr_launch = ops[dom] / per, hbm_b[dom] / per, pyr_b[dom] / per
     sms = torch.cuda.get_device_properties(device).multi_processor_count
     peaks = {}
     try:
@@ -446,24 +607,25 @@ def run_ours(args):
     except (OSError, ValueError):
         pass
     hbm_peak = peaks.get("hbm_gbs", 6800.0)
-    hbm_src = "measured" if "hbm_gbs" in peaks else "fallback"
+    hbm_src = "of measured" if "hbm_gbs" in peaks else "of fallback"
     mhz = (clk or {}).get("sm_mhz") or peaks.get("clocks_under_load", {}).get("sm_mhz_median") or 1900.0
     alu_peak = sms * 128 * mhz * 1e6 / 1e12           # FP32 lane-ops/s (FMA = 1), in T
     alu_ach = ops_launch / per_launch_s / 1e12
-    hbm_ach = byt_launch / per_launch_s / 1e9
-    alu_frac, hbm_frac = alu_ach / alu_peak, hbm_ach / hbm_peak
-    if alu_frac >= hbm_frac:
-        roof = {"bound": "alu", "achieved": alu_ach, "peak": alu_peak, "unit": "Top/s",
-                "frac": alu_frac, "traffic": None, "kernel": dom,
-                "peak_source": f"{sms} SMs x 128 FP32 lanes x {mhz:.0f} MHz (median SM clock "
-                               "sampled in this run)",
-                "hbm_alt": {"achieved": hbm_ach, "peak": hbm_peak, "unit": "GB/s",
-                            "frac": hbm_frac, "peak_source": hbm_src}}
-    else:
-        roof = {"bound": "hbm", "achieved": hbm_ach, "peak": hbm_peak, "unit": "GB/s",
-                "frac": hbm_frac, "traffic": None, "kernel": dom, "peak_source": hbm_src,
-                "alu_alt": {"achieved": alu_ach, "peak": alu_peak, "unit": "Top/s",
-                            "frac": alu_frac}}
+    roof = {"bound": "alu", "kernel": STAGE_KERNEL[dom], "achieved": alu_ach, "peak": alu_peak,
+            "unit": "Top/s", "frac": alu_ach / alu_peak, "traffic": None,
+            "ops_per_launch": ops_launch, "launch_us": per_launch_s * 1e6,
+            "peak_source": f"{sms} SMs x 128 FP32 lanes x {mhz:.0f} MHz, the median SM clock sampled "
+                           "in this run (FMA = 1 op)",
+            "ops_source": "the method's per-level op count (bench.level_ops; 24.7 K + 40 per value "
+                          "summed over the levels)",
+            "hbm_min": {"bytes_per_launch": hbm_launch, "achieved": hbm_launch / per_launch_s / 1e9,
+                        "peak": hbm_peak, "unit": "GB/s",
+                        "frac": hbm_launch / per_launch_s / 1e9 / hbm_peak, "peak_source": hbm_src,
+                        "bytes": "input read, output write and the guide levels the kernel reads"},
+            "pyramid_traffic": {"bytes_per_launch": pyr_launch,
+                                "note": "operand bytes of the Fourier and residual pyramids the "
+                                        "kernel reads and writes: materialised intermediates, not "
+                                        "algorithmic bytes"}}
     traffic_file = os.path.join(ROOT, "profiles", "dram_traffic.txt")
     try:
         tr = json.load(open(traffic_file))
@@ -472,6 +634,7 @@ def run_ours(args):
             roof["traffic"] = tr[key]["bytes_per_launch"]
     except (OSError, ValueError):
         pass
+    all_ops = sum(ops.values())
     hbm_min = hbm_min_bytes(cfg)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -489,28 +652,34 @@ def run_ours(args):
                 "h2d_bytes_per_step": int(hin.numel() * 4), "d2h_bytes_per_step": int(hout.numel() * 4)},
         "gpu_launches": int(round(sum(launches_per_step.values()) * args.steps)),
         "roofline": roof,
+        "alu_roofline_step": {"ops_per_step": all_ops, "achieved": all_ops / (ms_step * 1e-3) / 1e12,
+                              "peak": alu_peak, "unit": "Top/s",
+                              "frac": all_ops / (ms_step * 1e-3) / 1e12 / alu_peak},
         "hbm_min_roofline": {"bytes_per_step": hbm_min, "achieved": hbm_min / (ms_step * 1e-3) / 1e9,
                              "peak": hbm_peak, "unit": "GB/s",
-                             "frac": hbm_min / (ms_step * 1e-3) / 1e9 / hbm_peak},
+                             "frac": hbm_min / (ms_step * 1e-3) / 1e9 / hbm_peak,
+                             "peak_source": hbm_src},
         "stages_ms_per_step": {s: pre[s][0] / pre_steps for s in STAGES},
         "stages_note": (f"per-stage times from a {pre_steps}-step pre-pass with every launch timed; "
                         f"the timed region records events around the {dom} launches only"),
         "clocks": clk,
     }
+    gpu_outs = {args.precision: out_acc}
     if rank == 0 and not args.no_variants and world == 1:
         variants = {}
         for prec in ("fp32", "fp16", "bf16"):
             if prec == args.precision:
                 continue
-            ms = time_precision(pkg, torch, cfg, prec, frames, min(args.steps, 500), 10, stream, device)
+            ms, o = time_precision(pkg, torch, cfg, prec, frames, min(args.steps, 500), 10, stream, device)
             variants[prec] = {"ms_per_step": ms, "value": pixels / (ms * 1e-3) / 1e6}
+            gpu_outs[prec] = o
         line["precision_variants"] = variants
         # fast LLF (Sec. II-D) at the same number of pyramids: S = 2K samples
         S = 2 * cfg["K"]
         fp = pkg.make_fast_params(cfg["H"], cfg["W"], cfg["C"], cfg["levels"], S, cfg["m"], cfg["sigma_r"],
                                   args.precision)
-        ms = time_precision(pkg, torch, cfg, args.precision, frames, min(args.steps, 500), 10, stream,
-                            device, params=fp)
+        ms, _ = time_precision(pkg, torch, cfg, args.precision, frames, min(args.steps, 500), 10, stream,
+                               device, params=fp)
         line["fast_llf"] = {"samples": S, "pyramids": S + 1, "ms_per_step": ms,
                             "value": pixels / (ms * 1e-3) / 1e6, "unit": UNIT,
                             "pyramid_storage": args.precision,
@@ -521,7 +690,10 @@ def run_ours(args):
         line["serving"] = serving_summary(pkg, torch, device, args.serve_precision,
                                           seconds=args.serve_seconds or 4.0)
     if rank == 0 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_oracle_sample()
+        line["cpu_baseline"], acc = cpu_baseline_and_accuracy(img, gpu_outs)
+        line["accuracy"] = acc[args.precision]
+        for prec, v in line.get("precision_variants", {}).items():
+            v["accuracy"] = acc[prec]
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:

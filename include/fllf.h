@@ -191,11 +191,14 @@ fllf_status fllf_run_host(fllf_plan *plan, const float *h_in, float *h_out, void
 fllf_status fllf_submit(fllf_plan *plan, const float *d_in, float *d_out, void *stream,
                         uint64_t *ticket);
 
-/* Waits up to timeout_us microseconds (0 = just test, < 0 = no limit) for
- * a submitted ticket.  FLLF_OK: done (ticket consumed); FLLF_EAGAIN: still
- * running after a zero timeout; FLLF_ETIMEOUT: still running after a
- * positive timeout; FLLF_EINVAL: unknown or already consumed ticket;
- * FLLF_ECUDA: the work failed on the device. */
+/* Waits up to timeout_us microseconds (0 = just test, < 0 = up to
+ * FLLF_POLL_MAX_US) for a submitted ticket.  FLLF_OK: done (ticket
+ * consumed); FLLF_EAGAIN: still running after a zero timeout;
+ * FLLF_ETIMEOUT: still running after the timeout (the ticket stays valid),
+ * or the work finished but one of its kernels' bounded waits gave up
+ * (ticket consumed, output undefined); FLLF_EINVAL: unknown or already
+ * consumed ticket; FLLF_ECUDA: the work failed on the device. */
+#define FLLF_POLL_MAX_US 60000000
 fllf_status fllf_poll(uint64_t ticket, int timeout_us);
 
 /* ---- Batched execution ------------------------------------------------------
@@ -224,6 +227,15 @@ fllf_status fllf_batch_run(fllf_batch *batch, const float *const *d_in, float *c
 /* After the batch's work completed: FLLF_ETIMEOUT if a kernel's bounded wait
  * ran out (the status is then cleared), else FLLF_OK. */
 fllf_status fllf_batch_check(fllf_batch *batch);
+
+/* One-shot form of the above (the batch call of the boundary, with the plans
+ * passed directly): builds a batch of the n plans, filters d_in[i] ->
+ * d_out[i] for every i on `stream`, waits for the stream, reports a bounded
+ * wait that gave up (FLLF_ETIMEOUT) and frees the batch.  Synchronous; the
+ * batch's small argument tables are allocated and freed inside.  Keep a
+ * fllf_batch for repeated runs of the same plans. */
+fllf_status fllf_batch_run_plans(fllf_plan *const *plans, const float *const *d_in, float *const *d_out,
+                                 int n, void *stream);
 
 /* ---- Serving: continuous batching of filter requests ----------------------
  * A server owns one device memory pool of `hbm_budget` bytes (allocated at
@@ -266,7 +278,7 @@ fllf_status fllf_server_destroy(fllf_server *server);
 fllf_status fllf_server_submit(fllf_server *server, const fllf_params *p, const float *d_in,
                                float *d_out, uint64_t *ticket);
 
-/* Waits up to timeout_us (0 = test only, < 0 = no limit) for a request.
+/* Waits up to timeout_us (0 = test only, < 0 = up to FLLF_POLL_MAX_US) for a request.
  * FLLF_OK: finished, d_out holds the result (ticket consumed);
  * FLLF_EAGAIN / FLLF_ETIMEOUT: still pending; FLLF_EINVAL: unknown ticket;
  * FLLF_ECUDA: the request's wave failed, or one of its kernels' bounded waits
@@ -296,10 +308,18 @@ fllf_status fllf_server_stats_reset(fllf_server *server);
  *     invalid arguments.
  *   - All calls on one GPU share the array, which keeps the last call's
  *     contents; calls whose GPU work overlaps (two streams or threads)
- *     race on it, so serialise them.  Nothing in it must start at zero.
+ *     race on it, so serialise them.  Each call starts by clearing the
+ *     array's status words; the pyramids need no clearing.
+ *   - The coefficients reach the device as a by-value kernel argument, so
+ *     nothing reads host memory after the call returns.
  *   - The first call on a device looks up the array's device address with
  *     cudaGetSymbolAddress on the current device (this may load the
- *     module), so make the first call before any stream capture. */
+ *     module), so make the first call before any stream capture.  The
+ *     address is kept until the process exits: do not call this across a
+ *     cudaDeviceReset.
+ *   - A kernel's bounded wait that gives up (about 2 s) is not reported:
+ *     the call has already returned FLLF_OK and the output is incomplete.
+ *     fllf_run_host or fllf_poll on a plan do report it (FLLF_ETIMEOUT). */
 #define FLLF_NOALLOC_SCRATCH_BYTES (32u << 20)
 fllf_status fllf_run_noalloc(const fllf_params *p, const float *d_in, float *d_out, void *stream);
 
@@ -328,6 +348,18 @@ fllf_status fllf_plan_set_timing_mask(fllf_plan *plan, unsigned mask);
  * kernel time in milliseconds (ms[FLLF_NSTAGE]) and the number of launches
  * (launches[FLLF_NSTAGE]) since the last call, and clears the record. */
 fllf_status fllf_plan_stage_times(fllf_plan *plan, double *ms, int *launches);
+
+/* Test hook for the bounded device waits (failure detection; the paper has
+ * no counterpart).  Every wait in the kernels gives up
+ * after about 2 s of SM clock, sets the plan's fault word and leaves the
+ * kernel, and the host reports FLLF_ETIMEOUT.  This sets, for the plan's next
+ * runs, a shorter limit (wait_cycles > 0, in SM cycles; 0 = the default) and
+ * a number of arrivals that the grid barriers of the chained launch
+ * (fllf_tuning.chain_pixels > 0) wait for beyond the grid (0 = none): with a
+ * positive count no barrier can complete, so each one gives up after the
+ * limit, with no copy in flight.  Both settings are cleared when a run
+ * reports the timeout.  Synchronises the device. */
+fllf_status fllf_plan_set_wait_test(fllf_plan *plan, long long wait_cycles, unsigned extra_arrivals);
 
 /* ---- Launch tuning and the autotuner ---------------------------------------
  * The kernels' tile shapes and orders per chunk are fixed at compile time

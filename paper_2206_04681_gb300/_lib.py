@@ -66,6 +66,9 @@ _SIGS = {
     "fllf_batch_destroy": (ctypes.c_int, [_P]),
     "fllf_batch_run": (ctypes.c_int, [_P, ctypes.POINTER(_P), ctypes.POINTER(_P), _P]),
     "fllf_batch_check": (ctypes.c_int, [_P]),
+    "fllf_batch_run_plans": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.POINTER(_P),
+                                            ctypes.c_int, _P]),
+    "fllf_plan_set_wait_test": (ctypes.c_int, [_P, ctypes.c_longlong, ctypes.c_uint]),
     "fllf_run_noalloc": (ctypes.c_int, [ctypes.POINTER(fllf_params), _P, _P, _P]),
     "fllf_server_create": (ctypes.c_int, [ctypes.c_int, ctypes.c_size_t, ctypes.c_int,
                                           ctypes.c_int, ctypes.c_int, ctypes.POINTER(_P)]),
@@ -289,7 +292,24 @@ def fllf_batch_check(batch):
     _check(lib().fllf_batch_check(batch))
 
 
+def fllf_batch_run_plans(plans, d_in, d_out, stream=0):
+    """One-shot batch: builds a batch of the plans, runs it on the device
+    buffers, waits for the stream and frees the batch."""
+    n = len(plans)
+    arr = (_P * n)(*[p.value if isinstance(p, _P) else p for p in plans])
+    ins = (_P * n)(*d_in)
+    outs = (_P * n)(*d_out)
+    _check(lib().fllf_batch_run_plans(arr, ins, outs, n, _P(stream)))
+
+
+def fllf_plan_set_wait_test(plan, wait_cycles=0, extra_arrivals=0):
+    """Test hook: a shorter limit for the plan's bounded device waits and
+    extra arrivals its chained launch's grid barriers wait for."""
+    _check(lib().fllf_plan_set_wait_test(plan, int(wait_cycles), int(extra_arrivals)))
+
+
 NOALLOC_SCRATCH_BYTES = 32 << 20
+POLL_MAX_US = 60_000_000   # the longest wait of fllf_poll / fllf_server_poll (negative timeouts)
 
 
 def fllf_run_noalloc(p, d_in, d_out, stream=0):

@@ -683,7 +683,8 @@ fllf_status fllf_poll(uint64_t ticket, int timeout_us) {
     if (timeout_us == 0) return FLLF_EAGAIN;
     const auto us = std::chrono::duration_cast<std::chrono::microseconds>(
                         std::chrono::steady_clock::now() - t0).count();
-    if (timeout_us > 0 && us >= timeout_us) return fail(FLLF_ETIMEOUT, "ticket still pending");
+    const long long limit = timeout_us > 0 ? timeout_us : (long long)FLLF_POLL_MAX_US;
+    if (us >= limit) return fail(FLLF_ETIMEOUT, "ticket still pending");
     std::this_thread::sleep_for(std::chrono::microseconds(20));
   }
 }
@@ -707,6 +708,21 @@ fllf_status fllf_plan_set_timing_mask(fllf_plan* plan, unsigned mask) {
   const fllf_status st = fllf_plan_enable_timing(plan, 1);
   if (st == FLLF_OK) plan->timer->mask = mask;
   return st;
+}
+
+fllf_status fllf_plan_set_wait_test(fllf_plan* plan, long long wait_cycles, unsigned extra_arrivals) {
+  if (!plan) return fail(FLLF_EINVAL, "plan is NULL");
+  if (wait_cycles < 0) return fail(FLLF_EINVAL, "wait_cycles must be >= 0");
+  DeviceGuard guard(plan->device);
+  // status words 4..5: the wait limit; word 6: extra grid-barrier arrivals
+  unsigned words[4] = {0u, 0u, extra_arrivals, 0u};
+  std::memcpy(words, &wait_cycles, sizeof(wait_cycles));
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) return cuda_fail(e, "device synchronize");
+  if ((e = cudaMemcpy(plan->d_fault + fllf::kStatusLimitWord, words, sizeof(words), cudaMemcpyHostToDevice)) !=
+      cudaSuccess)
+    return cuda_fail(e, "status block write");
+  return FLLF_OK;
 }
 
 fllf_status fllf_plan_stage_times(fllf_plan* plan, double* ms, int* launches) {

@@ -549,4 +549,26 @@ fllf_status fllf_batch_check(fllf_batch* b) {
   return FLLF_OK;
 }
 
+fllf_status fllf_batch_run_plans(fllf_plan* const* plans, const float* const* d_in, float* const* d_out, int n,
+                                 void* stream) {
+  fllf_batch* b = nullptr;
+  fllf_status st = fllf_batch_create(plans, n, &b);
+  if (st != FLLF_OK) return st;
+  st = fllf_batch_run(b, d_in, d_out, stream);
+  if (st == FLLF_OK) {
+    DeviceScope scope(b->device);
+    const cudaError_t e = cudaStreamSynchronize(reinterpret_cast<cudaStream_t>(stream));
+    st = e != cudaSuccess ? bfail(FLLF_ECUDA, std::string("stream synchronize: ") + cudaGetErrorString(e))
+                          : fllf_batch_check(b);
+  } else {
+    // the tables may be in use by work already enqueued before the failure
+    DeviceScope scope(b->device);
+    cudaStreamSynchronize(reinterpret_cast<cudaStream_t>(stream));
+  }
+  const std::string keep = st == FLLF_OK ? std::string() : std::string(fllf_last_error());
+  fllf_batch_destroy(b);
+  if (st != FLLF_OK) return bfail(st, keep);
+  return FLLF_OK;
+}
+
 }  // extern "C"

@@ -440,16 +440,34 @@ __device__ __forceinline__ void tma_load4(void* dst, const CUtensorMap* map, int
       : "memory");
 }
 
-// Bounded wait on an mbarrier phase (about 2 s of SM clock).  The outcome is
-// made uniform over the CTA; on a timeout the fault word records it and the
-// caller leaves the kernel.
+// Status block of a run (device, zeroed when it is allocated): word 0 holds
+// the fault bits a bounded wait sets when it gives up, words 1..2 a grid
+// barrier's arrivals and generation, words 4..5 an optional shorter wait
+// limit in SM cycles (0: the default of about 2 s), word 6 arrivals a grid
+// barrier waits for beyond the grid (0 normally; a test sets it to make the
+// barrier's wait run out).  All of it lies in the first 64 bytes.
+constexpr int kStatusLimitWord = 4;
+constexpr int kStatusExtraArrivals = 6;
+
+// Bounded waits give up after about 2 s of SM clock, or after the status
+// block's shorter limit.
 constexpr long long kWaitCycles = 4000000000LL;
+__device__ __forceinline__ long long wait_limit(const unsigned* status) {
+  if (!status) return kWaitCycles;
+  const long long v = *reinterpret_cast<const volatile long long*>(status + kStatusLimitWord);
+  return (v > 0 && v < kWaitCycles) ? v : kWaitCycles;
+}
+
+// Bounded wait on an mbarrier phase.  The outcome is made uniform over the
+// CTA; on a timeout the fault word records it and the caller leaves the
+// kernel.
 __device__ __forceinline__ bool mbar_wait_cta(uint64_t* b, uint32_t parity, unsigned* fault) {
   int ok = 1;
   if (!mbar_test(b, parity)) {
+    const long long lim = wait_limit(fault);
     const long long t0 = clock64();
     while (!mbar_test(b, parity)) {
-      if (clock64() - t0 > kWaitCycles) {
+      if (clock64() - t0 > lim) {
         ok = 0;
         break;
       }
@@ -467,9 +485,10 @@ __device__ __forceinline__ bool mbar_wait_cta(uint64_t* b, uint32_t parity, unsi
 __device__ __forceinline__ void mbar_wait_thread(uint64_t* b, uint32_t parity, unsigned* fault,
                                                  volatile int* abort) {
   if (mbar_test(b, parity)) return;
+  const long long lim = wait_limit(fault);
   const long long t0 = clock64();
   while (!mbar_test(b, parity)) {
-    if (*abort || clock64() - t0 > kWaitCycles) {
+    if (*abort || clock64() - t0 > lim) {
       if (fault) atomicOr(fault, 1u);
       *abort = 1;
       return;

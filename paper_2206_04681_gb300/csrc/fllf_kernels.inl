@@ -1625,16 +1625,20 @@ __device__ __forceinline__ bool grid_barrier(unsigned* count, unsigned* gen, uns
   int ok = 1;
   if (threadIdx.x == 0) {
     __threadfence();
+    // arrivals awaited: the grid, plus the status block's extra count (0
+    // normally; a test raises it so that the wait runs out)
+    const unsigned need = nblocks + *reinterpret_cast<const volatile unsigned*>(fault + kStatusExtraArrivals);
     const unsigned g = ld_acquire(gen);
-    if (atomicAdd(count, 1u) + 1u == nblocks) {
+    if (atomicAdd(count, 1u) + 1u == need) {
       atomicExch(count, 0u);
       __threadfence();
       atomicAdd(gen, 1u);
     } else {
+      const long long lim = wait_limit(fault);
       const long long t0 = clock64();
       while (ld_acquire(gen) == g) {
         __nanosleep(32);
-        if (clock64() - t0 > kWaitCycles) {
+        if (clock64() - t0 > lim) {
           ok = 0;
           atomicOr(fault, 2u);
           break;

@@ -15,12 +15,20 @@
 //     does not fit is rejected with FLLF_EINVAL before any work is queued.
 //   * All calls on one GPU share the array and it keeps the last call's
 //     contents.  Calls whose GPU work overlaps (two streams, two host
-//     threads) race on it; serialise them on one stream.  Nothing in it has
-//     to start at zero: every word a kernel reads was written earlier in the
-//     same call.
+//     threads) race on it; serialise them on one stream.  The pyramids need
+//     no clearing (every word a kernel reads was written earlier in the same
+//     call); the status words are cleared at the start of every call, by the
+//     same small kernel that writes the coefficients.
+//   * The coefficients travel to that kernel as a by-value argument, so the
+//     call reads no host memory after it returns.
 //   * The first call on a device resolves the array's device address with
 //     cudaGetSymbolAddress (with that device current), which may load the
-//     module; make that first call before any stream capture.
+//     module; make that first call before any stream capture.  The address
+//     is kept for the life of the process: do not use this entry point
+//     across a cudaDeviceReset.
+//   * A bounded wait that gives up inside the kernels (a TMA copy that never
+//     lands, about 2 s) is not reported by this call: it has returned long
+//     before.  The output is then incomplete.
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -38,11 +46,25 @@ constexpr int kMaxDevices = 64;
 std::mutex g_noalloc_mu;
 unsigned char* g_noalloc_ptr[kMaxDevices] = {};
 
-constexpr size_t kHeadBytes = 512;  // a_1..a_64 (float32) at 0, fault and barrier words at 256, then the pyramids
+constexpr size_t kHeadBytes = 512;  // a_1..a_64 (float32) at 0, the 256-byte status block at 256, then the pyramids
+constexpr int kMaxOrders = 64;
 
 fllf_status noalloc_fail(fllf_status s, const std::string& why) {
   fllf::set_last_error(why);
   return s;
+}
+
+// The coefficients of one call, passed by value.
+struct Coeffs {
+  float a[kMaxOrders];
+};
+
+// Writes a_1..a_K into the head of the array and clears its status block
+// (fault word, grid-barrier words, wait-limit words): one block of 64 threads.
+__global__ void k_noalloc_setup(float* a_dst, Coeffs c, int K, unsigned* status) {
+  const int t = threadIdx.x;
+  if (t < K) a_dst[t] = c.a[t];
+  status[t] = 0u;   // 64 words = 256 bytes
 }
 
 }  // namespace
@@ -78,29 +100,32 @@ extern "C" fllf_status fllf_run_noalloc(const fllf_params* user, const float* d_
       // for its address on the current device.
       void* ptr = nullptr;
       e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
-      if (e != cudaSuccess || !ptr)
+      if (e != cudaSuccess || !ptr) {
+        cudaGetLastError();   // leave no sticky error behind for later launch checks
         return noalloc_fail(FLLF_ECUDA, std::string("cudaGetSymbolAddress of the scratch array: ") +
                                             cudaGetErrorString(e));
+      }
       g_noalloc_ptr[dev] = static_cast<unsigned char*>(ptr);
     }
     base = g_noalloc_ptr[dev];
   }
 
-  // Coefficients in float64 on the host, uploaded as float32 into the head of
-  // the array (pageable source: the copy has read it before returning).
-  double a64[64];
-  float a32[64];
+  // Coefficients in float64 on the host, written as float32 into the head of
+  // the array by a small kernel that takes them by value and also clears the
+  // status block.
+  double a64[kMaxOrders];
+  Coeffs c{};
   for (int k = 0; k < p->K; ++k) a64[k] = 0.0;   // fast LLF: unused
   if (p->method == FLLF_METHOD_FOURIER) fllf::compute_coeffs(*p, a64);
-  for (int k = 0; k < p->K; ++k) a32[k] = (float)a64[k];
+  for (int k = 0; k < p->K; ++k) c.a[k] = (float)a64[k];
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   float* d_a = reinterpret_cast<float*>(base);
-  e = cudaMemcpyAsync(d_a, a32, sizeof(float) * p->K, cudaMemcpyHostToDevice, s);
-  if (e != cudaSuccess)
-    return noalloc_fail(FLLF_ECUDA, std::string("coefficient upload: ") + cudaGetErrorString(e));
+  unsigned* fault = reinterpret_cast<unsigned*>(base + 256);
+  k_noalloc_setup<<<1, 64, 0, s>>>(d_a, c, p->K, fault);
+  if ((e = cudaGetLastError()) != cudaSuccess)
+    return noalloc_fail(FLLF_ECUDA, std::string("coefficient set-up kernel: ") + cudaGetErrorString(e));
 
   unsigned char* pyr = base + kHeadBytes;
-  unsigned* fault = reinterpret_cast<unsigned*>(base + 256);
   const int L = p->levels;
   for (int l = 0; l < L; ++l) {
     fllf::Level& v = lv[l];

@@ -497,11 +497,9 @@ fllf_status fllf_server_poll(fllf_server* sv, uint64_t ticket, int timeout_us) {
   auto finished = [&] { return r->state == kDone || r->state == kFailed; };
   if (!finished()) {
     if (timeout_us == 0) return FLLF_EAGAIN;
-    if (timeout_us < 0) {
-      sv->cv.wait(lk, finished);
-    } else if (!sv->cv.wait_for(lk, std::chrono::microseconds(timeout_us), finished)) {
+    const long long limit = timeout_us > 0 ? timeout_us : (long long)FLLF_POLL_MAX_US;
+    if (!sv->cv.wait_for(lk, std::chrono::microseconds(limit), finished))
       return sfail(FLLF_ETIMEOUT, "request still pending");
-    }
   }
   const bool ok = r->state == kDone;
   const std::string why = r->err.empty() ? "request cancelled (server stopping)" : r->err;

@@ -1,9 +1,8 @@
 """The bench's per-stage accounting (host logic, no GPU): which levels each
-stage kind covers under a launch tuning, the launches per step, and the
-algorithmic bytes of the fused level-0/1 stage that the roofline divides
-by the kernel's duration.  The level split mirrors the library's launch
-sequence; the byte counts follow the path's definition (each input element
-read once, each output written once)."""
+stage kind covers under a launch tuning, the launches per step, the
+algorithmic op count per level that the ALU roofline divides by a kernel's
+duration, the minimum HBM bytes, and the pyramid bytes kept apart from
+them.  The level split mirrors the library's launch sequence."""
 
 import os
 import sys
@@ -16,6 +15,7 @@ sys.path.insert(0, ROOT)
 import bench  # noqa: E402
 
 CFG = bench.WORKLOAD   # 3840 x 2160 x 3, 8 levels, K = 8
+N0, N1, N2 = 3840 * 2160, 1920 * 1080, 960 * 540
 
 
 def _launches(split):
@@ -48,16 +48,44 @@ def test_tuned_splits(chain, small, n_small, n_down, n_launch):
     assert sorted(up + chain_up) == [1, 2, 3, 4, 5, 6]
 
 
-def test_fused_stage_bytes():
-    # I and O (8 B per level-0 value), Z_1 (zb * K) + G_1 per level-1 value,
-    # Z_2 (zb * K) + E_2 per level-2 value, for the 3 planes
-    n0, n1, n2 = 3840 * 2160, 1920 * 1080, 960 * 540
+def test_op_count_per_value_is_the_methods():
+    # summed over the levels, 24.67 K + 40.3 per value: the method's count of
+    # about 25 K + 35 (139 at K = 4, 238 at K = 8, 435 at K = 16)
+    for K, expect in ((4, 139.0), (8, 237.7), (16, 435.0)):
+        cfg = dict(CFG, K=K)
+        per_value = bench.step_ops(cfg) / (3 * N0)
+        assert per_value == pytest.approx(expect, rel=0.01)
+
+
+def test_op_count_is_the_same_under_every_launch_split():
+    base, _, _ = bench.stage_accounts(CFG, 8)
+    for chain, small in ((0, 0), (1 << 21, 1 << 40), (1 << 17, 1 << 19)):
+        ops, _, _ = bench.stage_accounts(CFG, 8, chain, small)
+        assert sum(ops.values()) == pytest.approx(sum(base.values()))
+
+
+def test_fused_stage_ops_and_bytes():
+    lo = bench.level_ops(CFG)
+    ops, hbm, pyr = bench.stage_accounts(CFG, 8)
+    # level 0: combine + residual; level 1: combine + coefficient pairs + residual
+    expect = 3 * (N0 * (lo["combine"] + lo["resid"]) + N1 * (lo["combine"] + lo["gtrig"] + lo["resid"]))
+    assert ops["down0"] == pytest.approx(expect)
+    assert ops["down0"] / 1e9 == pytest.approx(2.76, abs=0.01)
+    # algorithmic bytes: I read, O written, G_1 read (224 MB at 4K RGB)
+    assert hbm["down0"] == pytest.approx(3 * (8 * N0 + 4 * N1))
+    assert hbm["down0"] / 1e6 == pytest.approx(224.0, abs=0.1)
+    # pyramid bytes, reported apart: Z_1 (zb K per level-1 pixel), Z_2 and E_2
     for zb in (8, 4):
-        _, byt = bench.stage_work(CFG, zb)
-        expect = 3 * (8 * n0 + (zb * 8 + 4) * n1 + (zb * 8 + 4) * n2)
-        assert byt["down0"] == pytest.approx(expect)
-    _, byt = bench.stage_work(CFG, 8)
-    assert byt["down0"] / 1e6 == pytest.approx(727.8, abs=0.1)
+        _, _, pyr = bench.stage_accounts(CFG, zb)
+        assert pyr["down0"] == pytest.approx(3 * (zb * 8 * N1 + (zb * 8 + 4) * N2))
+
+
+def test_stage_hbm_bytes_add_up_to_the_minimum():
+    # the stages' image and guide bytes: I read twice (REDUCE and combine),
+    # O once, each guide level written once and read by the REDUCE above it
+    # and by its combine; the path's minimum counts I once and G read once
+    _, hbm, _ = bench.stage_accounts(CFG, 8)
+    assert sum(hbm.values()) >= bench.hbm_min_bytes(CFG)
 
 
 def test_hbm_min_bytes_follow_the_definition():

@@ -70,6 +70,21 @@ def test_batch_equals_per_image_runs(precision):
             pkg.fllf_plan_destroy(p)
 
 
+@pytest.mark.parametrize("precision", ["fp32", "bf16"])
+def test_one_shot_batch_equals_per_image_runs(precision):
+    plans, ins, outs, refs, imgs, params = _setup(precision)
+    try:
+        for y in outs:
+            y.fill_(float("nan"))
+        pkg.fllf_batch_run_plans(plans, [x.data_ptr() for x in ins], [y.data_ptr() for y in outs],
+                                 torch.cuda.current_stream().cuda_stream)
+        for y, r in zip(outs, refs):
+            torch.testing.assert_close(y, r, rtol=0, atol=0)
+    finally:
+        for p in plans:
+            pkg.fllf_plan_destroy(p)
+
+
 def test_batch_matches_oracle():
     plans, ins, outs, refs, imgs, params = _setup("fp32")
     batch = pkg.fllf_batch_create(plans)

@@ -50,6 +50,7 @@ def _no_alloc(img, p, x=None, y=None):
 
 
 def test_matches_fllf_run_on_two_calls_in_a_row():
+    # the same kernels on the same inputs: the same bits as fllf_run
     cases = [
         (synth_image(160, 224, 3, polygons=6, seed=31),
          pkg.make_params(160, 224, 3, 6, 8, 3.0, 0.2, 2.0, "fp32")),
@@ -62,10 +63,11 @@ def test_matches_fllf_run_on_two_calls_in_a_row():
     outs = [_no_alloc(img, p) for img, p in cases]     # two calls in a row
     for out, ref in zip(outs, refs):
         assert np.all(np.isfinite(out))
+        np.testing.assert_array_equal(out, ref)
         assert float(np.max(np.abs(out - ref))) <= TOL
     # and again after the array holds the second call's contents
     again = _no_alloc(*cases[0])
-    assert float(np.max(np.abs(again - refs[0]))) <= TOL
+    np.testing.assert_array_equal(again, refs[0])
 
 
 def test_allocates_no_device_memory_after_first_call():
@@ -74,11 +76,23 @@ def test_allocates_no_device_memory_after_first_call():
     x = torch.from_numpy(img).cuda()
     y = torch.empty_like(x)
     _no_alloc(img, p, x, y)                       # first call: symbol lookup, module load
-    free0, _ = torch.cuda.mem_get_info()
-    for _ in range(3):
-        _no_alloc(img, p, x, y)
-    free1, _ = torch.cuda.mem_get_info()
-    assert free1 == free0
+
+    def measure():
+        torch.cuda.synchronize()
+        free0, _ = torch.cuda.mem_get_info()
+        stats0 = torch.cuda.memory_stats().get("allocation.all.allocated", 0)
+        for _ in range(3):
+            _no_alloc(img, p, x, y)
+        free1, _ = torch.cuda.mem_get_info()
+        stats1 = torch.cuda.memory_stats().get("allocation.all.allocated", 0)
+        return free1 == free0, stats0 == stats1
+
+    # the free-bytes figure is the whole device's: another process's
+    # allocation in between would move it, so one retry is allowed
+    ok_free, ok_torch = measure()
+    if not ok_free:
+        ok_free, ok_torch = measure()
+    assert ok_torch and ok_free
 
 
 def test_rejects_images_above_the_array_size():
