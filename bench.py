@@ -30,7 +30,7 @@ METRIC = "Mpixel/s Fourier LLF K=8 4K RGB at PSNR≥60dB vs FP64; serving p50/p9
 UNIT = "Mpixel/s"
 WORKLOAD = dict(H=2160, W=3840, C=3, polygons=40, seed=2, levels=8, K=8, m=3.0, sigma_r=0.2, T=2.0)
 N_FRAMES = 4          # distinct input/output frames cycled per step (4 x 99.5 MB > 129 MB L2)
-STAGES = ("up0", "up", "down", "down0", "chain", "down_s")
+STAGES = ("up0", "up", "down", "down0", "chain", "down_s", "graph")
 
 
 def parse():
@@ -122,7 +122,7 @@ def level_ops(cfg):
             "gtrig": 4 * K + 16, "resid": 11.25}
 
 
-def stage_accounts(cfg, zbytes, chain_px=CHAIN_PIXELS, small_px=SMALL_PIXELS):
+def stage_accounts(cfg, zbytes, chain_px=CHAIN_PIXELS, small_px=SMALL_PIXELS, dataflow=0):
     """Per stage kind, for one frame (all planes): algorithmic ops, the
     minimum HBM bytes of the stage's image and guide operands, and the bytes
     of the Fourier and residual pyramid operands it reads and writes.
@@ -183,6 +183,15 @@ def stage_accounts(cfg, zbytes, chain_px=CHAIN_PIXELS, small_px=SMALL_PIXELS):
             e2 = 1 if L >= 4 else 0
             add("down0", n[1] * (lo["combine"] + lo["gtrig"] + lo["resid"]), 4 * n[1],
                 zbytes * K * n[2] + 4 * n[2] * e2)
+    if dataflow:
+        # one dataflow launch runs every stage (dataflow 1), or every stage but
+        # the fused level-1/level-0 combine, which follows as its own kernel (2)
+        keep = ("down0",) if dataflow == 2 and L >= 3 else ()
+        for d in (ops, hbm, pyr):
+            d["graph"] = sum(v for k, v in d.items() if k not in keep and k != "graph")
+            for k in STAGES:
+                if k != "graph" and k not in keep:
+                    d[k] = 0.0
     f = lambda d: {k: v * C for k, v in d.items()}
     return f(ops), f(hbm), f(pyr)
 
@@ -196,7 +205,7 @@ def step_ops(cfg):
 # kernel launched by each stage kind (the level-0 stage is the fused
 # level-1/level-0 combine when levels >= 3)
 STAGE_KERNEL = {"up0": "k_up0", "up": "k_up", "down": "k_down", "down0": "k_down10",
-                "chain": "k_chain", "down_s": "k_down_s"}
+                "chain": "k_chain", "down_s": "k_down_s", "graph": "k_graph"}
 
 
 def hbm_min_bytes(cfg):
@@ -594,7 +603,7 @@ def run_ours(args):
     pkg.fllf_plan_destroy(plan)
 
     zbytes = 8 if args.precision == "fp32" else 4
-    ops, hbm_b, pyr_b = stage_accounts(cfg, zbytes, tn.chain_pixels, tn.small_pixels)
+    ops, hbm_b, pyr_b = stage_accounts(cfg, zbytes, tn.chain_pixels, tn.small_pixels, tn.dataflow)
     dom_ms, dom_launches = stage[dom]                  # timed region, dominant kernel only
     per_launch_s = dom_ms / max(dom_launches, 1) * 1e-3
     launches_per_step = {s: pre[s][1] / pre_steps for s in STAGES}

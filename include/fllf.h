@@ -203,11 +203,12 @@ fllf_status fllf_poll(uint64_t ticket, int timeout_us);
 
 /* ---- Batched execution ------------------------------------------------------
  * A batch groups n plans (same device and storage precision; each with its
- * own size, levels, K and remap) so that one launch per stage kind covers
- * every image: the REDUCE and combine work items of all images share the
- * persistent grids, which keeps the GPU full when images are small or at the
- * small pyramid levels.  The launch sequence is captured in a CUDA graph at
- * the first run and replayed afterwards.  The batch uses the plans' scratch:
+ * own size, levels, K and remap) so that one launch per stage kind and level
+ * covers every image, or one persistent dataflow launch covers every stage of
+ * every image (see fllf_batch_set_mode): the REDUCE and combine work items
+ * of all images share the persistent grids, and small images and small
+ * levels fill the GPU beside large ones.  The launch sequence is captured in
+ * a CUDA graph at the first run and replayed afterwards.  The batch uses the plans' scratch:
  * a plan must not run on its own while a batch that holds it is running, and
  * the plans must outlive the batch. */
 typedef struct fllf_batch fllf_batch;
@@ -332,7 +333,8 @@ enum {
   FLLF_STAGE_DOWN0 = 3, /* level 0: Eq. (14) l = 0 case + final collapse, writes O */
   FLLF_STAGE_CHAIN = 4, /* the small levels (REDUCE up, then combines down) in one launch */
   FLLF_STAGE_DOWN_S = 5, /* level l >= 2 below small_pixels: FLLF_STAGE_DOWN on 32 x 16 tiles */
-  FLLF_NSTAGE = 6
+  FLLF_STAGE_GRAPH = 6,  /* every stage in one persistent dataflow launch (fllf_tuning.dataflow) */
+  FLLF_NSTAGE = 7
 };
 
 /* When enabled, every run of the plan records CUDA events around each
@@ -348,6 +350,18 @@ fllf_status fllf_plan_set_timing_mask(fllf_plan *plan, unsigned mask);
  * kernel time in milliseconds (ms[FLLF_NSTAGE]) and the number of launches
  * (launches[FLLF_NSTAGE]) since the last call, and clears the record. */
 fllf_status fllf_plan_stage_times(fllf_plan *plan, double *ms, int *launches);
+
+/* Host-only check of the dataflow launch's task list (no device work): builds
+ * the list for n parameter sets (one batch; n == 1 is a plan's own list) with
+ * the given task sizes (task_items[5] as in fllf_tuning, NULL = defaults) and
+ * with or without the fused level-1/level-0 combine, then runs it in order
+ * on one host worker.  FLLF_OK when every work item of every stage is in
+ * exactly one task, every task comes after the tasks whose row bands it
+ * reads, and every band reaches the count its readers wait for;
+ * FLLF_EINVAL with the reason otherwise.  *ntasks, *nbands (may be NULL):
+ * the list's size. */
+fllf_status fllf_dataflow_check(const fllf_params *ps, int n, const int *task_items, int with_d10, int *ntasks,
+                                int *nbands);
 
 /* Test hook for the bounded device waits (failure detection; the paper has
  * no counterpart).  Every wait in the kernels gives up
@@ -383,17 +397,42 @@ fllf_status fllf_plan_set_wait_test(fllf_plan *plan, long long wait_cycles, unsi
  *                   four times the tiles and a quarter of each thread's
  *                   serial work.  Default 2^40 (every level: the small tiles
  *                   measured as fast or faster at every size tried); 0 = never.
+ *   dataflow        1: every stage of a Fourier LLF run without a gain map
+ *                   in ONE persistent launch (FLLF_STAGE_GRAPH): the stages
+ *                   are cut into tasks of a few tiles of one row band; a
+ *                   band's tasks are pushed onto a device queue once every
+ *                   row band they read is complete, and the CTAs pop ready
+ *                   tasks, so the REDUCE of a level starts on the first rows
+ *                   the level below has finished and no launch boundary
+ *                   separates the levels.  2: the same without the fused
+ *                   level-1/level-0 combine, which follows as its own
+ *                   kernel.  0 (default; measured faster at 4K RGB): one
+ *                   launch per stage kind and level (the settings above).
+ *                   The same stage code on the same work items: the same
+ *                   output, bit for bit.
+ *   task_items[5]   work items per task of the dataflow launch for the
+ *                   level-0 REDUCE (tiles of 32 x 14 level-1 outputs), the
+ *                   REDUCE at levels >= 1 (tile-chunks; at level 1, halved
+ *                   per level above), the combines at levels >= 2 (32 x 16
+ *                   tiles; at level 2, halved per level above), the fused
+ *                   level-1/0 combine (64 x 32 tiles) and the level-0
+ *                   combine of 2-level images; 1..4096 each (default 4, 8,
+ *                   4, 2, 4).
  * Every setting computes the same output, bit for bit. */
 typedef struct {
   long long chain_pixels;
   int ctas_per_sm[FLLF_NSTAGE];
   int reduce_reverse;
   long long small_pixels;
+  int dataflow;
+  int task_items[5];
 } fllf_tuning;
 
 /* Reads / replaces a plan's launch tuning.  set: chain_pixels >= 0,
- * small_pixels >= 0, ctas_per_sm 0..32, reduce_reverse 0 or 1; otherwise
- * FLLF_EINVAL. */
+ * small_pixels >= 0, ctas_per_sm 0..32, reduce_reverse 0 or 1, dataflow 0
+ * or 1, task_items 1..4096; otherwise FLLF_EINVAL.  A change of task_items
+ * rebuilds the plan's task list (allocates its tables anew; synchronises the
+ * device). */
 fllf_status fllf_plan_get_tuning(const fllf_plan *plan, fllf_tuning *out);
 fllf_status fllf_plan_set_tuning(fllf_plan *plan, const fllf_tuning *t);
 
@@ -402,10 +441,13 @@ fllf_status fllf_plan_set_tuning(fllf_plan *plan, const fllf_tuning *t);
  * `reps` timed runs per candidate after one untimed run, each timed run
  * after an L2 flush (it allocates a buffer of twice the L2 size for the
  * search and frees it; FLLF_ENOMEM if that fails).  It searches by
- * coordinate descent, from the plan's current tuning, over the chain start
- * (0, 2^15, 2^17, 2^19, 2^21, 2^23 pixels), the small-tile threshold (0 or
- * the pixel count of a combined level >= 2), the resident CTAs per SM of
- * each stage kind (1 .. as many as fit) and the REDUCE order.  A candidate
+ * coordinate descent, from the plan's current tuning: first the dataflow
+ * launch against the per-stage launches; with the dataflow launch, its
+ * resident CTAs per SM and the task sizes of each stage kind; otherwise the
+ * chain start (0, 2^15, 2^17, 2^19, 2^21, 2^23 pixels), the small-tile
+ * threshold (0 or the pixel count of a combined level >= 2), the resident
+ * CTAs per SM of each stage kind (1 .. as many as fit) and the REDUCE
+ * order.  A candidate
  * replaces the setting only if it is at least 1% faster.  The plan keeps
  * the best setting; *best_ms (may be NULL) receives its time per run.
  * Synchronises the stream.  reps 1..10000. */
@@ -420,6 +462,21 @@ fllf_status fllf_plan_autotune(fllf_plan *plan, const float *d_in, float *d_out,
  * buffers (as for fllf_batch_run; outputs overwritten) and keeps the best
  * caps, with the same search and 1% rule as fllf_plan_autotune. */
 fllf_status fllf_batch_get_ctas(const fllf_batch *batch, int *ctas_per_sm /* [4] */);
+
+/* Launch mode of a batch: 1: ONE persistent dataflow launch runs every stage
+ * of every image (tasks of a few tiles of one row band, pushed onto a device
+ * queue once the row bands they read are complete, popped by the CTAs;
+ * ctas_per_sm[0] caps its grid); 2: the same without the fused
+ * level-1/level-0 combine, which follows as one batched launch
+ * (ctas_per_sm[3]); 0 (default; measured faster on mixed batches): one
+ * launch per stage kind and level over all images.
+ * task_items[5] (may be NULL): task sizes as in fllf_tuning.  Every mode
+ * computes the same output, bit for bit.  Setting a mode or task sizes
+ * synchronises the device and rebuilds the task list; the next run captures
+ * its CUDA graph again.  The batch autotuner searches the mode, the caps of
+ * the kinds the mode launches and the task sizes. */
+fllf_status fllf_batch_get_mode(const fllf_batch *batch, int *mode, int *task_items);
+fllf_status fllf_batch_set_mode(fllf_batch *batch, int mode, const int *task_items);
 fllf_status fllf_batch_set_ctas(fllf_batch *batch, const int *ctas_per_sm /* [4] */);
 fllf_status fllf_batch_autotune(fllf_batch *batch, const float *const *d_in, float *const *d_out, int reps,
                                 void *stream, double *best_ms);

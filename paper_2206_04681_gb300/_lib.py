@@ -69,6 +69,8 @@ _SIGS = {
     "fllf_batch_run_plans": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.POINTER(_P),
                                             ctypes.c_int, _P]),
     "fllf_plan_set_wait_test": (ctypes.c_int, [_P, ctypes.c_longlong, ctypes.c_uint]),
+    "fllf_dataflow_check": (ctypes.c_int, [ctypes.POINTER(fllf_params), ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                                           ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
     "fllf_run_noalloc": (ctypes.c_int, [ctypes.POINTER(fllf_params), _P, _P, _P]),
     "fllf_server_create": (ctypes.c_int, [ctypes.c_int, ctypes.c_size_t, ctypes.c_int,
                                           ctypes.c_int, ctypes.c_int, ctypes.POINTER(_P)]),
@@ -90,22 +92,27 @@ _SIGS = {
     "fllf_plan_set_tuning": (ctypes.c_int, [_P, _P]),
     "fllf_plan_autotune": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, _P, ctypes.POINTER(ctypes.c_double)]),
     "fllf_batch_get_ctas": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int)]),
+    "fllf_batch_get_mode": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
+    "fllf_batch_set_mode": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
     "fllf_batch_set_ctas": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int)]),
     "fllf_batch_autotune": (ctypes.c_int, [_P, ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.c_int, _P,
                                            ctypes.POINTER(ctypes.c_double)]),
 }
 
-STAGES = ("up0", "up", "down", "down0", "chain", "down_s")
+STAGES = ("up0", "up", "down", "down0", "chain", "down_s", "graph")
+TASK_KINDS = ("up0", "up", "down_s", "down10", "down0")
 
 
 class fllf_tuning(ctypes.Structure):
     _fields_ = [("chain_pixels", ctypes.c_longlong), ("ctas_per_sm", ctypes.c_int * len(STAGES)),
-                ("reduce_reverse", ctypes.c_int), ("small_pixels", ctypes.c_longlong)]
+                ("reduce_reverse", ctypes.c_int), ("small_pixels", ctypes.c_longlong),
+                ("dataflow", ctypes.c_int), ("task_items", ctypes.c_int * len(TASK_KINDS))]
 
     def as_dict(self):
         return {"chain_pixels": int(self.chain_pixels), "small_pixels": int(self.small_pixels),
                 "ctas_per_sm": {s: int(self.ctas_per_sm[i]) for i, s in enumerate(STAGES)},
-                "reduce_reverse": int(self.reduce_reverse)}
+                "reduce_reverse": int(self.reduce_reverse), "dataflow": int(self.dataflow),
+                "task_items": {s: int(self.task_items[i]) for i, s in enumerate(TASK_KINDS)}}
 
 _lib = None
 
@@ -207,6 +214,19 @@ def fllf_batch_get_ctas(batch):
     return list(out)
 
 
+def fllf_batch_get_mode(batch):
+    """(mode, task_items) of a batch's launch."""
+    m = ctypes.c_int()
+    ti = (ctypes.c_int * 5)()
+    _check(lib().fllf_batch_get_mode(batch, ctypes.byref(m), ti))
+    return m.value, list(ti)
+
+
+def fllf_batch_set_mode(batch, mode, task_items=None):
+    ti = (ctypes.c_int * 5)(*task_items) if task_items is not None else None
+    _check(lib().fllf_batch_set_mode(batch, int(mode), ti))
+
+
 def fllf_batch_set_ctas(batch, ctas):
     arr = (ctypes.c_int * 4)(*ctas)
     _check(lib().fllf_batch_set_ctas(batch, arr))
@@ -300,6 +320,17 @@ def fllf_batch_run_plans(plans, d_in, d_out, stream=0):
     ins = (_P * n)(*d_in)
     outs = (_P * n)(*d_out)
     _check(lib().fllf_batch_run_plans(arr, ins, outs, n, _P(stream)))
+
+
+def fllf_dataflow_check(params, task_items=None, with_d10=True):
+    """Host-only check of the dataflow task list of the parameter sets;
+    returns (tasks, bands) or raises FllfError with the reason."""
+    n = len(params)
+    arr = (fllf_params * n)(*params)
+    ti = (ctypes.c_int * 5)(*task_items) if task_items is not None else None
+    nt, nb = ctypes.c_int(), ctypes.c_int()
+    _check(lib().fllf_dataflow_check(arr, n, ti, int(bool(with_d10)), ctypes.byref(nt), ctypes.byref(nb)))
+    return nt.value, nb.value
 
 
 def fllf_plan_set_wait_test(plan, wait_cycles=0, extra_arrivals=0):

@@ -230,6 +230,7 @@ void free_plan(fllf_plan* pl) {
   if (pl->d_io_out) cudaFree(pl->d_io_out);
   if (pl->d_mpyr) cudaFree(pl->d_mpyr);
   if (pl->d_luma) cudaFree(pl->d_luma);
+  plan_graph_destroy(pl->graph);
   for (cudaEvent_t e : pl->io_ev)
     if (e) cudaEventDestroy(e);
   if (pl->io_h2d) cudaStreamDestroy(pl->io_h2d);
@@ -453,6 +454,15 @@ fllf_status fllf_plan_create(const fllf_params* user, int device, fllf_plan** ou
     free_plan(pl);
     return fail(FLLF_ECUDA, "TMA tensor map encoding failed (cuTensorMapEncodeTiled)");
   }
+  if (p->levels > 1 && p->method == FLLF_METHOD_FOURIER) {
+    // the dataflow launch: task list and argument tables of this image
+    pl->graph = plan_graph_create(pl, pl->tune.grain, pl->tune.dataflow != 2, &e);
+    if (!pl->graph) {
+      free_plan(pl);
+      return e == cudaErrorMemoryAllocation ? fail(FLLF_ENOMEM, "dataflow task table allocation failed")
+                                            : cuda_fail(e, "dataflow task table");
+    }
+  }
   *out = pl;
   return FLLF_OK;
 }
@@ -488,7 +498,7 @@ fllf_status fllf_run(fllf_plan* plan, const float* d_in, float* d_out, void* str
   if (!guard.ok) return fail(FLLF_ECUDA, "cudaSetDevice failed");
   cudaError_t e = enqueue_path(plan->p, plan->lv, plan->maps, plan->d_a, plan->d_fault, d_in, d_out,
                                reinterpret_cast<cudaStream_t>(stream), plan->timer, nullptr, 0.f,
-                               &plan->tune);
+                               &plan->tune, plan->graph);
   if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
   return FLLF_OK;
 }
@@ -596,7 +606,7 @@ fllf_status fllf_run_host(fllf_plan* plan, const float* h_in, float* h_out, void
     if ((e = cudaMemcpyAsync(plan->d_io_in, h_in, bytes, cudaMemcpyHostToDevice, s)) != cudaSuccess)
       return cuda_fail(e, "host-to-device copy");
     if ((e = enqueue_path(plan->p, plan->lv, plan->maps, plan->d_a, plan->d_fault, plan->d_io_in,
-                          plan->d_io_out, s, plan->timer, nullptr, 0.f, &plan->tune)) != cudaSuccess)
+                          plan->d_io_out, s, plan->timer, nullptr, 0.f, &plan->tune, plan->graph)) != cudaSuccess)
       return cuda_fail(e, "kernel launch");
     if ((e = cudaMemcpyAsync(h_out, plan->d_io_out, bytes, cudaMemcpyDeviceToHost, s)) != cudaSuccess)
       return cuda_fail(e, "device-to-host copy");

@@ -303,10 +303,98 @@ struct fllf_batch {
   cudaStream_t cap = nullptr;
   cudaGraphExec_t graph = nullptr;
   int cps[4] = {0, 0, 0, 0};       // resident-CTA cap per batched stage kind (0: as many as fit)
+  // the launch mode (0, the default, measured faster on mixed batches: one
+  // launch per stage kind and level; 1: the dataflow launch, every stage of
+  // every image in one launch; 2: the same without the fused level-1/level-0
+  // combine, which follows as one batched launch)
+  int mode = 0;
+  GraphGrain grain;
+  GraphBuild flow;
+  unsigned char* d_flow = nullptr;
+  size_t flow_prefix_off = 0;      // tile prefix sums of the fused combine's table (mode 2)
+  Up0Args* h_fup0 = nullptr;       // pinned per-run mirrors of the dataflow's level-0 tables
+  Down10Args* h_fd10 = nullptr;
+  Down0Args* h_fd0 = nullptr;
 };
+
+static void free_flow(fllf_batch* b) {
+  if (b->d_flow) cudaFree(b->d_flow);
+  if (b->h_fup0) cudaFreeHost(b->h_fup0);
+  if (b->h_fd10) cudaFreeHost(b->h_fd10);
+  if (b->h_fd0) cudaFreeHost(b->h_fd0);
+  b->d_flow = nullptr;
+  b->h_fup0 = nullptr;
+  b->h_fd10 = nullptr;
+  b->h_fd0 = nullptr;
+  b->flow = GraphBuild{};
+}
+
+// Builds and uploads the batch's dataflow task list for its mode and grain.
+static fllf_status build_flow(fllf_batch* b) {
+  free_flow(b);
+  std::vector<const fllf_plan*> plans(b->plans.begin(), b->plans.end());
+  build_graph(plans, b->precision, b->grain, false, b->mode != 2, &b->flow);
+  if (!b->flow.ok) return bfail(FLLF_EINVAL, "internal error: dataflow task list");
+  // tile prefix sums of the fused combine's table, for its batched launch
+  std::vector<int> pre(b->flow.n_d10 + 1, 0);
+  for (int j = 0; j < b->flow.n_d10; ++j) {
+    const fllf_params& p = b->plans[b->flow.d10_img[j]]->p;
+    pre[j + 1] = pre[j] + cdiv(p.W + kDnX0, kDnOW) * cdiv(p.H, kDnOH) * p.C;
+  }
+  b->flow_prefix_off = push(b->flow.blob, pre.data(), pre.size(), 16);
+  cudaError_t e;
+  if ((e = cudaMalloc(&b->d_flow, b->flow.blob.size())) != cudaSuccess) {
+    cudaGetLastError();
+    b->d_flow = nullptr;
+    return bfail(FLLF_ENOMEM, "dataflow table allocation failed");
+  }
+  // every argument block's fault word is the batch's
+  unsigned char* hb = b->flow.blob.data();
+  auto fault = [&](auto* a, int n) {
+    for (int j = 0; j < n; ++j) a[j].fault = b->d_fault;
+  };
+  fault(reinterpret_cast<Up0Args*>(hb + b->flow.up0_off), b->flow.n_up0);
+  fault(reinterpret_cast<UpArgs*>(hb + b->flow.ups_off), b->flow.n_ups);
+  fault(reinterpret_cast<DownArgs*>(hb + b->flow.dns_off), b->flow.n_dns);
+  fault(reinterpret_cast<Down10Args*>(hb + b->flow.d10_off), b->flow.n_d10);
+  fault(reinterpret_cast<Down0Args*>(hb + b->flow.d0_off), b->flow.n_d0);
+  if ((e = cudaMemcpy(b->d_flow, hb, b->flow.blob.size(), cudaMemcpyHostToDevice)) != cudaSuccess)
+    return bfail(FLLF_ECUDA, std::string("dataflow table upload: ") + cudaGetErrorString(e));
+  const size_t n0 = std::max(1, b->flow.n_up0), n10 = std::max(1, b->flow.n_d10), nd0 = std::max(1, b->flow.n_d0);
+  if (cudaMallocHost(&b->h_fup0, sizeof(Up0Args) * n0) != cudaSuccess ||
+      cudaMallocHost(&b->h_fd10, sizeof(Down10Args) * n10) != cudaSuccess ||
+      cudaMallocHost(&b->h_fd0, sizeof(Down0Args) * nd0) != cudaSuccess) {
+    cudaGetLastError();
+    return bfail(FLLF_ENOMEM, "pinned dataflow tables");
+  }
+  std::copy(reinterpret_cast<const Up0Args*>(hb + b->flow.up0_off),
+            reinterpret_cast<const Up0Args*>(hb + b->flow.up0_off) + b->flow.n_up0, b->h_fup0);
+  std::copy(reinterpret_cast<const Down10Args*>(hb + b->flow.d10_off),
+            reinterpret_cast<const Down10Args*>(hb + b->flow.d10_off) + b->flow.n_d10, b->h_fd10);
+  std::copy(reinterpret_cast<const Down0Args*>(hb + b->flow.d0_off),
+            reinterpret_cast<const Down0Args*>(hb + b->flow.d0_off) + b->flow.n_d0, b->h_fd0);
+  return FLLF_OK;
+}
+
+// The dataflow launch of the batch (and, in mode 2, the batched fused combine).
+static cudaError_t launch_flow(fllf_batch* b, cudaStream_t s) {
+  GraphArgs g = graph_args(b->flow, b->d_flow, b->d_fault);
+  const bool with_d10 = b->mode != 2;
+  cudaError_t e = launch_graph(b->precision, g, sizeof(unsigned) * b->flow.rt_words, s, b->cps[kStageUp0], with_d10);
+  if (e != cudaSuccess || with_d10 || b->flow.n_d10 == 0) return e;
+  const int* pre = reinterpret_cast<const int*>(b->d_flow + b->flow_prefix_off);
+  const int total = reinterpret_cast<const int*>(b->flow.blob.data() + b->flow_prefix_off)[b->flow.n_d10];
+  BatchTable<Down10Args> t{g.d10s, pre, b->flow.n_d10, total};
+  switch (b->precision) {
+    case FLLF_FP16: return launch_down10_batch_f16(t, s, b->cps[kStageDown0]);
+    case FLLF_BF16: return launch_down10_batch_bf16(t, s, b->cps[kStageDown0]);
+    default: return launch_down10_batch_f32(t, s, b->cps[kStageDown0]);
+  }
+}
 
 static void free_batch(fllf_batch* b) {
   if (!b) return;
+  free_flow(b);
   if (b->graph) cudaGraphExecDestroy(b->graph);
   if (b->cap) cudaStreamDestroy(b->cap);
   if (b->copied) cudaEventDestroy(b->copied);
@@ -374,6 +462,12 @@ fllf_status fllf_batch_create(fllf_plan* const* plans, int n, fllf_batch** out) 
     free_batch(b);
     return bfail(FLLF_ECUDA, "batch event / stream creation failed");
   }
+  const fllf_status fs = build_flow(b);
+  if (fs != FLLF_OK) {
+    const std::string why = fllf_last_error();
+    free_batch(b);
+    return bfail(fs, why);
+  }
   *out = b;
   return FLLF_OK;
 }
@@ -403,14 +497,41 @@ fllf_status fllf_batch_run(fllf_batch* b, const float* const* d_in, float* const
   if (b->copied_pending && (e = cudaEventSynchronize(b->copied)) != cudaSuccess)
     return bfail(FLLF_ECUDA, std::string("batch copy wait: ") + cudaGetErrorString(e));
   const BatchBlob& bb = b->bb;
-  set_level0_io(bb, b->h_up0, b->h_down0, b->h_down10, d_in, d_out);
-  auto upload = [&](size_t off, const void* src, size_t bytes) {
-    return bytes ? cudaMemcpyAsync(b->d_mem + off, src, bytes, cudaMemcpyHostToDevice, s) : cudaSuccess;
-  };
-  if ((e = upload(bb.up0_off, b->h_up0, sizeof(Up0Args) * bb.up0_img.size())) != cudaSuccess ||
-      (e = upload(bb.down0_off, b->h_down0, sizeof(Down0Args) * bb.down0_img.size())) != cudaSuccess ||
-      (e = upload(bb.down10_off, b->h_down10, sizeof(Down10Args) * bb.down10_img.size())) != cudaSuccess)
-    return bfail(FLLF_ECUDA, std::string("batch table update: ") + cudaGetErrorString(e));
+  if (b->mode == 0) {
+    set_level0_io(bb, b->h_up0, b->h_down0, b->h_down10, d_in, d_out);
+    auto upload = [&](size_t off, const void* src, size_t bytes) {
+      return bytes ? cudaMemcpyAsync(b->d_mem + off, src, bytes, cudaMemcpyHostToDevice, s) : cudaSuccess;
+    };
+    if ((e = upload(bb.up0_off, b->h_up0, sizeof(Up0Args) * bb.up0_img.size())) != cudaSuccess ||
+        (e = upload(bb.down0_off, b->h_down0, sizeof(Down0Args) * bb.down0_img.size())) != cudaSuccess ||
+        (e = upload(bb.down10_off, b->h_down10, sizeof(Down10Args) * bb.down10_img.size())) != cudaSuccess)
+      return bfail(FLLF_ECUDA, std::string("batch table update: ") + cudaGetErrorString(e));
+  } else {
+    // the dataflow tables' level-0 blocks: this run's inputs, outputs and input maps
+    const GraphBuild& f = b->flow;
+    for (int j = 0; j < f.n_up0; ++j) {
+      Up0Args& a = b->h_fup0[j];
+      a.I = d_in[f.up0_img[j]];
+      a.use_tma = encode_image_map(&a.imap, a.I, a.w0, a.h0, a.planes, kUpIW, kUpIR) ? 1 : 0;
+    }
+    for (int j = 0; j < f.n_d10; ++j) {
+      Down10Args& a = b->h_fd10[j];
+      a.I = d_in[f.d10_img[j]];
+      a.O = d_out[f.d10_img[j]];
+      a.use_tma = encode_image_map(&a.imap, a.I, a.w0, a.h0, a.planes, kD0IW, kDnOH) ? 1 : 0;
+    }
+    for (int j = 0; j < f.n_d0; ++j) {
+      b->h_fd0[j].I = d_in[f.d0_img[j]];
+      b->h_fd0[j].O = d_out[f.d0_img[j]];
+    }
+    auto upload = [&](size_t off, const void* src, size_t bytes) {
+      return bytes ? cudaMemcpyAsync(b->d_flow + off, src, bytes, cudaMemcpyHostToDevice, s) : cudaSuccess;
+    };
+    if ((e = upload(f.up0_off, b->h_fup0, sizeof(Up0Args) * f.n_up0)) != cudaSuccess ||
+        (e = upload(f.d10_off, b->h_fd10, sizeof(Down10Args) * f.n_d10)) != cudaSuccess ||
+        (e = upload(f.d0_off, b->h_fd0, sizeof(Down0Args) * f.n_d0)) != cudaSuccess)
+      return bfail(FLLF_ECUDA, std::string("batch table update: ") + cudaGetErrorString(e));
+  }
   if ((e = cudaEventRecord(b->copied, s)) != cudaSuccess)
     return bfail(FLLF_ECUDA, std::string("batch event: ") + cudaGetErrorString(e));
   b->copied_pending = true;
@@ -427,7 +548,8 @@ fllf_status fllf_batch_run(fllf_batch* b, const float* const* d_in, float* const
     cudaGraph_t g = nullptr;
     if ((e = cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeRelaxed)) != cudaSuccess)
       return bfail(FLLF_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e));
-    const cudaError_t le = launch_batch_stages(bb.stages, b->d_mem, b->precision, b->cap, b->cps);
+    const cudaError_t le = b->mode == 0 ? launch_batch_stages(bb.stages, b->d_mem, b->precision, b->cap, b->cps)
+                                        : launch_flow(b, b->cap);
     e = cudaStreamEndCapture(b->cap, &g);
     if (le != cudaSuccess || e != cudaSuccess) {
       if (g) cudaGraphDestroy(g);
@@ -443,6 +565,46 @@ fllf_status fllf_batch_run(fllf_batch* b, const float* const* d_in, float* const
   }
   if ((e = cudaGraphLaunch(b->graph, s)) != cudaSuccess)
     return bfail(FLLF_ECUDA, std::string("graph launch: ") + cudaGetErrorString(e));
+  return FLLF_OK;
+}
+
+fllf_status fllf_batch_get_mode(const fllf_batch* b, int* mode, int* task_items) {
+  if (!b || !mode) return bfail(FLLF_EINVAL, "batch or mode is NULL");
+  *mode = b->mode;
+  if (task_items) {
+    const int g[5] = {b->grain.up0, b->grain.up, b->grain.dns, b->grain.d10, b->grain.d0};
+    std::copy(g, g + 5, task_items);
+  }
+  return FLLF_OK;
+}
+
+fllf_status fllf_batch_set_mode(fllf_batch* b, int mode, const int* task_items) {
+  if (!b) return bfail(FLLF_EINVAL, "batch is NULL");
+  if (mode < 0 || mode > 2) return bfail(FLLF_EINVAL, "mode must be 0, 1 or 2");
+  GraphGrain g = b->grain;
+  if (task_items) {
+    for (int k = 0; k < 5; ++k)
+      if (task_items[k] < 1 || task_items[k] > 4096) return bfail(FLLF_EINVAL, "task_items must be 1..4096");
+    g.up0 = task_items[0];
+    g.up = task_items[1];
+    g.dns = task_items[2];
+    g.d10 = task_items[3];
+    g.d0 = task_items[4];
+  }
+  const bool regrain = g.up0 != b->grain.up0 || g.up != b->grain.up || g.dns != b->grain.dns ||
+                       g.d10 != b->grain.d10 || g.d0 != b->grain.d0 || ((mode == 2) != (b->mode == 2));
+  if (mode == b->mode && !regrain) return FLLF_OK;
+  DeviceScope scope(b->device);
+  // the launch sequence is captured in the graph, and the tables may be in use
+  cudaDeviceSynchronize();
+  if (b->graph) {
+    cudaGraphExecDestroy(b->graph);
+    b->graph = nullptr;
+  }
+  b->copied_pending = false;
+  b->mode = mode;
+  b->grain = g;
+  if (regrain) return build_flow(b);
   return FLLF_OK;
 }
 
@@ -511,8 +673,34 @@ fllf_status fllf_batch_autotune(fllf_batch* b, const float* const* d_in, float* 
   std::copy(b->cps, b->cps + 4, best);
   double best_t = measure(best);
   bool ok = best_t >= 0;
+  // 1. the launch mode (one launch per stage kind and level, the dataflow
+  // launch, the dataflow launch followed by the batched fused combine), each
+  // with every CTA cap at "as many as fit"
+  {
+    int mode_best = b->mode;
+    const int zero[4] = {0, 0, 0, 0};
+    for (int m = 0; m <= 2 && ok; ++m) {
+      if (m == mode_best) continue;
+      const int prev = b->mode;
+      ok = fllf_batch_set_mode(b, m, nullptr) == FLLF_OK;
+      const double t = ok ? measure(zero) : -1.0;
+      ok = ok && t >= 0;
+      if (ok && t < 0.99 * best_t) {
+        mode_best = m;
+        best_t = t;
+        std::copy(zero, zero + 4, best);
+      } else if (ok) {
+        ok = fllf_batch_set_mode(b, prev, nullptr) == FLLF_OK;
+      }
+    }
+    if (ok) ok = fllf_batch_set_mode(b, mode_best, nullptr) == FLLF_OK && fllf_batch_set_ctas(b, best) == FLLF_OK;
+  }
+  // 2. the CTA caps of the kinds the mode launches (the dataflow kernel takes
+  // the first cap, its batched fused combine the fourth)
   for (int kind = 0; kind < 4 && ok; ++kind) {
-    const int occ = stage_occupancy(b->precision, kind, true);
+    if (b->mode != 0 && kind != 0 && !(b->mode == 2 && kind == 3)) continue;
+    const int occ = b->mode != 0 && kind == 0 ? stage_occupancy(b->precision, FLLF_STAGE_GRAPH, false)
+                                              : stage_occupancy(b->precision, kind, true);
     for (int c = 1; c <= occ && ok; ++c) {
       int t[4];
       std::copy(best, best + 4, t);
@@ -526,11 +714,31 @@ fllf_status fllf_batch_autotune(fllf_batch* b, const float* const* d_in, float* 
       }
     }
   }
+  if (ok) ok = fllf_batch_set_ctas(b, best) == FLLF_OK;
+  // 3. the dataflow launch's task sizes
+  if (ok && b->mode != 0) {
+    const std::vector<std::vector<int>> cand = {{1, 2, 4, 8, 16}, {2, 4, 8, 16, 32}, {1, 2, 4, 8}, {1, 2, 4}};
+    for (int k = 0; k < 4 && ok; ++k)
+      for (int v : cand[k]) {
+        int cur[5];
+        int mode = 0;
+        fllf_batch_get_mode(b, &mode, cur);
+        if (cur[k] == v) continue;
+        int t[5];
+        std::copy(cur, cur + 5, t);
+        t[k] = v;
+        ok = fllf_batch_set_mode(b, mode, t) == FLLF_OK;
+        const double m = ok ? measure(best) : -1.0;
+        ok = ok && m >= 0;
+        if (ok && m < 0.99 * best_t) best_t = m;
+        else if (ok) ok = fllf_batch_set_mode(b, mode, cur) == FLLF_OK;
+      }
+  }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   cudaStreamSynchronize(s);
   cudaFree(flush);
-  const fllf_status st = fllf_batch_set_ctas(b, best);
+  const fllf_status st = ok ? fllf_batch_set_ctas(b, best) : FLLF_ECUDA;
   if (!ok) return bfail(FLLF_ECUDA, "autotune: a timed batched run failed");
   if (best_ms) *best_ms = best_t;
   return st;

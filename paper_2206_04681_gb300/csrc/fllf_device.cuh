@@ -180,6 +180,47 @@ struct BatchTable {
   int n, total;
 };
 
+// Dataflow launch: one persistent grid runs every stage of one or many images
+// as tasks (a run of consecutive work items of one row band of one stage).
+// A band becomes ready when every band it reads is complete; its tasks are
+// then pushed onto a device queue, from which the CTAs pop ready tasks only.
+// The bands that read nothing (the level-0 REDUCE) are the queue's seeds.
+enum GraphKind { kGUp0 = 0, kGUp = 1, kGDownS = 2, kGDown10 = 3, kGDown0 = 4 };
+struct GraphTask {
+  int kind;        // GraphKind
+  int args;        // index into the kind's argument table (-1: the inline block of GraphArgs)
+  int first, count;// work items [first, first + count) of the stage
+  int band;        // the row band the task belongs to
+};
+struct GraphBand {
+  unsigned total;  // work items of the band
+  int task0, ntasks;  // its tasks: [task0, task0 + ntasks)
+  int ndeps;       // bands it reads
+  int cons0, cons1;   // bands that read it: cons[cons0 .. cons1)
+};
+
+struct GraphArgs {
+  Up0Args up0;          // inline level-0 argument blocks of a single image (inline0 = 1)
+  Down10Args d10;
+  Down0Args d0;
+  const Up0Args* up0s;  // argument tables in device memory
+  const UpArgs* ups;
+  const DownArgs* dns;
+  const Down10Args* d10s;
+  const Down0Args* d0s;
+  const GraphTask* tasks;
+  const GraphBand* bands;
+  const int* cons;      // consumer band lists
+  const int* seeds;     // the seed tasks, in the order they are popped
+  // run state (zeroed before every run): [0] queue head, [1] queue tail,
+  // then per band the items done and the bands it reads that are complete,
+  // then the queue slots (task + 1; 0 = not yet pushed)
+  unsigned* rt;
+  unsigned* fault;
+  int ntasks, nbands, nseeds;
+  int inline0;
+};
+
 // Chained small levels: REDUCE stages then combine stages in one cooperative
 // launch, with a grid barrier between consecutive stages.
 constexpr int kChainMax = 12;

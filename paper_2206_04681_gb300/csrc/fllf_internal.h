@@ -96,6 +96,50 @@ bool build_maps(const fllf_params& p, const std::vector<Level>& lv, PathMaps* m)
 // 16-byte aligned) or the encoding fails.
 bool encode_image_map(CUtensorMap* m, const float* base, int W, int H, int C, uint32_t box_w, uint32_t box_h);
 
+// ---- dataflow launch (one persistent grid over every stage) -------------------
+// Work items per task of each stage kind (the REDUCE at levels >= 1 and the
+// small-tile combines: at their finest level, halved per level above).
+struct GraphGrain {
+  int up0 = 4, up = 8, dns = 4, d10 = 2, d0 = 4;
+};
+// The host image of a dataflow launch: argument tables, the ordered task
+// list, the dependency list and the zeroed completion counters.
+struct GraphBuild {
+  std::vector<unsigned char> blob;
+  size_t up0_off = 0, ups_off = 0, dns_off = 0, d10_off = 0, d0_off = 0, tasks_off = 0, bands_off = 0,
+         cons_off = 0, seeds_off = 0, rt_off = 0;
+  size_t rt_words = 0;       // the run state, zeroed before every run
+  int ntasks = 0, nbands = 0, nseeds = 0, n_up0 = 0, n_ups = 0, n_dns = 0, n_d10 = 0, n_d0 = 0;
+  bool ok = false;
+  bool with_d10 = true;      // the fused level-1/level-0 combine is part of the task list
+  Up0Args up0_inline{};      // level-0 argument blocks when they are passed inline (one image)
+  Down10Args d10_inline{};
+  Down0Args d0_inline{};
+  std::vector<int> up0_img, d10_img, d0_img, copy_img;  // image of each table entry / single-level images
+};
+// Builds the task graph of the plans (same storage precision, Fourier LLF,
+// no gain map).  inline0: one image whose level-0 argument blocks travel in
+// the kernel parameters (set per run) instead of the tables.  with_d10: the
+// fused level-1/level-0 combine of the images with >= 3 levels is in the
+// task list (otherwise the caller launches it after the dataflow kernel).
+void build_graph(const std::vector<const fllf_plan*>& plans, int prec, const GraphGrain& gr, bool inline0,
+                 bool with_d10, GraphBuild* out);
+// Runs the queue on one (host) worker: true when every task is made ready
+// exactly once, only after the bands it reads are complete, and every band
+// completes.
+bool check_graph(const GraphBuild& gb, std::string* why);
+// Kernel arguments for the tables uploaded at d_base (inline blocks copied).
+GraphArgs graph_args(const GraphBuild& gb, const unsigned char* d_base, unsigned* d_fault);
+// Clears the run state and launches the dataflow kernel.
+cudaError_t launch_graph(int prec, const GraphArgs& g, size_t rt_bytes, cudaStream_t s, int cps,
+                         bool with_d10);
+// A plan's own dataflow launch (one image, level-0 blocks inline).
+struct PlanGraph {
+  GraphBuild gb;
+  unsigned char* d_mem = nullptr;
+  GraphArgs args{};   // table pointers; the level-0 blocks are completed per run
+};
+
 // Launch tuning of a plan (the autotuner's knobs).  chain_px: levels >= 2
 // whose planes hold at most this many pixels in all run in the chained
 // launch (0: none); small_px: the other combines at levels >= 2 with at most
@@ -107,9 +151,19 @@ struct Tuning {
   long long small_px = 1ll << 40;
   int cps[FLLF_NSTAGE] = {0, 0, 0, 0, 0, 0};
   int reverse = 1;
+  // 0: the per-stage kernels (default: measured faster); 1: one persistent
+  // dataflow launch; 2: the dataflow launch without the fused level-1/level-0
+  // combine, which follows as its own kernel
+  int dataflow = 0;
+  GraphGrain grain;   // work items per task of the dataflow launch
 };
 // Resident CTAs per SM of a stage kind's kernel for a storage precision.
 int stage_occupancy(int prec, int kind, bool batched);
+
+// Builds and uploads a plan's own dataflow launch (Fourier LLF, >= 2 levels);
+// null with *err set on failure.  Destroy frees its device tables.
+PlanGraph* plan_graph_create(const fllf_plan* plan, const GraphGrain& gr, bool with_d10, cudaError_t* err);
+void plan_graph_destroy(PlanGraph* g);
 
 // Enqueues the whole Fourier LLF path of one image on stream s.  `fault`
 // is a device word that kernels set when a bounded wait runs out.  With a
@@ -119,7 +173,7 @@ int stage_occupancy(int prec, int kind, bool batched);
 cudaError_t enqueue_path(const fllf_params& p, const std::vector<Level>& lv, const PathMaps& maps,
                          const float* d_a, unsigned* fault, const float* d_in, float* d_out,
                          cudaStream_t s, StageHook* hook = nullptr, const float* d_gain = nullptr,
-                         float mscale = 0.f, const Tuning* tune = nullptr);
+                         float mscale = 0.f, const Tuning* tune = nullptr, const PlanGraph* graph = nullptr);
 
 // ---- batched argument tables (shared by batches and the server) ---------------
 // kStageDown10 (the fused level-1/level-0 combine of the images with >= 3
@@ -172,6 +226,7 @@ struct fllf_plan {
   float* d_mpyr = nullptr;            // gain-map pyramid of pixel-adaptive runs (first use)
   float* d_luma = nullptr;            // Y and filtered Y of colour-by-luma runs (first use)
   fllf::Tuning tune;                  // launch tuning (fllf_plan_set_tuning / fllf_plan_autotune)
+  fllf::PlanGraph* graph = nullptr;   // the plan's dataflow launch (Fourier LLF, >= 2 levels)
   // Host-buffer runs of C >= 2 planes: one-plane views of the scratch (levels
   // and maps) and the copy streams of the plane pipeline (first use).
   std::vector<std::vector<fllf::Level>> plane_lv;

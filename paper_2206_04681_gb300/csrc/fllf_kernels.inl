@@ -1679,6 +1679,157 @@ __global__ void __launch_bounds__(kThreads, 2) k_chain(const __grid_constant__ C
   }
 }
 
+// ---------------------------------------------------------------------------------------
+// Dataflow launch (one persistent grid for every stage of one or many images).
+// A CTA pops the next ready task from the device queue, runs its work items
+// through the same stage function as the per-stage kernels (so the output is
+// the same, bit for bit), and adds them to its band's count.  The CTA whose
+// task completes a band marks the band complete in every band that reads it;
+// a reader band whose inputs are now all complete has its tasks pushed.  A
+// popped task never waits for another task, so no CTA depends on another
+// being resident; a CTA waits (bounded) only for a queue slot to be filled,
+// and every slot is filled once, by a CTA that is running a task.
+// One task of each stage kind, kept out of line: each is register-allocated
+// on its own (the fused combine alone needs about 125 registers), instead of
+// all five inside one loop body.
+template <typename S>
+__device__ __noinline__ bool graph_up0(const GraphArgs& g, const GraphTask& t, unsigned char* smem, uint64_t* bar,
+                                       Pipe& pp) {
+  const Up0Args* a = t.args < 0 ? &g.up0 : g.up0s + t.args;
+  return stage_up0<S>([&](int gi, int& l) { l = gi; return a; }, t.first + t.count, smem, bar, pp, t.first, 1);
+}
+template <typename S>
+__device__ __noinline__ bool graph_up(const GraphArgs& g, const GraphTask& t, unsigned char* smem, uint64_t* bar,
+                                      Pipe& pp) {
+  const UpArgs* a = g.ups + t.args;
+  return stage_up<S>([&](int gi, int& l) { l = gi; return a; }, t.first + t.count, smem, bar, pp, t.first, 1);
+}
+template <typename S>
+__device__ __noinline__ bool graph_down_s(const GraphArgs& g, const GraphTask& t, unsigned char* smem,
+                                          uint64_t* bar, Pipe& pp) {
+  const DownArgs* a = g.dns + t.args;
+  return stage_combine_s<S>([&](int gi, int& l) { l = gi; return a; }, t.first + t.count, smem, bar, pp,
+                            t.first, 1);
+}
+template <typename S>
+__device__ __noinline__ bool graph_down10(const GraphArgs& g, const GraphTask& t, unsigned char* smem,
+                                          uint64_t* bar, Pipe& pp) {
+  const Down10Args* a = t.args < 0 ? &g.d10 : g.d10s + t.args;
+  return stage_down10<S, false>([&](int gi, int& l) { l = gi; return a; }, t.first + t.count, smem, bar, pp,
+                                t.first, 1);
+}
+template <typename S>
+__device__ __noinline__ bool graph_down0(const GraphArgs& g, const GraphTask& t, unsigned char* smem,
+                                         uint64_t* bar, Pipe& pp) {
+  const Down0Args* a = t.args < 0 ? &g.d0 : g.d0s + t.args;
+  return stage_combine0<S>([&](int gi, int& l) { l = gi; return view_of(*a); }, t.first + t.count, smem, bar,
+                           pp, t.first, 1);
+}
+
+// D10: the task list holds the fused level-1/level-0 combine (otherwise it
+// runs as its own kernel after this one, with the registers it needs).
+__device__ __forceinline__ unsigned atom_add_acq_rel(unsigned* p, unsigned v) {
+  unsigned old;
+  asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+  return old;
+}
+
+template <typename S, bool D10>
+__global__ void __launch_bounds__(kThreads, 2) k_graph(const __grid_constant__ GraphArgs g) {
+  using SM = Smem<sizeof(typename Cplx<S>::T)>;
+  constexpr size_t kS = std::max(std::max(std::max(SM::up0, SM::up), std::max(SM::dns, SM::d10)), SM::dn);
+  extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ GraphTask s_t;
+  __shared__ int s_state;   // 1: a task to run, 0: the queue is exhausted, -1: a wait gave up
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + kS - 64);
+  init_bars(bar);
+  Pipe pp{};
+  unsigned* head = g.rt;
+  unsigned* tail = g.rt + 1;
+  unsigned* band_done = g.rt + 2;
+  unsigned* band_in = band_done + g.nbands;
+  unsigned* slot = band_in + g.nbands;
+  // Thread 0 takes a queue index for the next task as soon as the current one
+  // starts (the slot may still be empty: it is read after the current task).
+  // Safe, since every slot below ntasks is filled eventually: while tasks
+  // remain, some band whose inputs are complete has tasks not yet pushed only
+  // if a task of an input band is still running, and that task pushes it.
+  int next = 0;
+  if (threadIdx.x == 0) next = (int)atomicAdd(head, 1u);
+  for (;;) {
+    if (threadIdx.x == 0) {
+      const int idx = next;
+      int task = -1, st = 1;
+      if (idx >= g.ntasks) {
+        st = 0;
+      } else if (idx < g.nseeds) {
+        task = g.seeds[idx];
+      } else {
+        // a slot is filled once, by the CTA that makes its band ready
+        unsigned v = ld_acquire(slot + (idx - g.nseeds));
+        if (v == 0u) {
+          const long long lim = wait_limit(g.fault);
+          const long long t0 = clock64();
+          while ((v = ld_acquire(slot + (idx - g.nseeds))) == 0u) {
+            __nanosleep(64);
+            if (clock64() - t0 > lim) {
+              atomicOr(g.fault, 4u);
+              st = -1;
+              break;
+            }
+          }
+        }
+        task = (int)v - 1;
+      }
+      if (st == 1) {
+        s_t = g.tasks[task];
+        // what the producers wrote (generic proxy) is read by this task's TMA copies
+        asm volatile("fence.proxy.async.global;" ::: "memory");
+        next = (int)atomicAdd(head, 1u);
+      }
+      s_state = st;
+    }
+    __syncthreads();
+    if (s_state <= 0) return;
+    const GraphTask& t = s_t;
+    bool r;
+    switch (t.kind) {
+      case kGUp0: r = graph_up0<S>(g, t, smem, bar, pp); break;
+      case kGUp: r = graph_up<S>(g, t, smem, bar, pp); break;
+      case kGDownS: r = graph_down_s<S>(g, t, smem, bar, pp); break;
+      case kGDown10:
+        if constexpr (D10) r = graph_down10<S>(g, t, smem, bar, pp);
+        else r = false;
+        break;
+      default: r = graph_down0<S>(g, t, smem, bar, pp); break;
+    }
+    if (!r) return;
+    // publish: every thread's stores of the task, then the band's count; the
+    // task that completes the band pushes the bands it made ready
+    asm volatile("fence.proxy.async.global;" ::: "memory");
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      // release: this CTA's stores (ordered before by the barrier); acquire:
+      // the other producers' stores, when this task completes the band
+      const GraphBand b = g.bands[t.band];
+      if (atom_add_acq_rel(band_done + t.band, (unsigned)t.count) + (unsigned)t.count == b.total) {
+        for (int c = b.cons0; c < b.cons1; ++c) {
+          const int rb = g.cons[c];
+          const GraphBand r = g.bands[rb];
+          if (atom_add_acq_rel(band_in + rb, 1u) + 1u == (unsigned)r.ndeps) {
+            const unsigned pos = atomicAdd(tail, (unsigned)r.ntasks);
+            for (int j = 0; j < r.ntasks; ++j)
+              asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(slot + pos + j),
+                           "r"((unsigned)(r.task0 + j + 1))
+                           : "memory");
+          }
+        }
+      }
+    }
+    __syncthreads();   // s_t is written again by the next pop
+  }
+}
+
 #if FLLF_STORAGE_IS_F32
 // ---------------------------------------------------------------------------------------
 // REDUCE (Eq. (1)) of one float plane: the gain map's Gaussian pyramid for
@@ -1841,6 +1992,18 @@ cudaError_t FLLF_LAUNCH_NAME(chain)(const ChainArgs& a, cudaStream_t s, int cps)
   return e != cudaSuccess ? e : cudaGetLastError();
 }
 
+// Dataflow launch: a persistent grid of the resident CTAs (at most `cps` per
+// SM), programmatic stream serialization as for the per-stage kernels.
+cudaError_t FLLF_LAUNCH_NAME(graph)(const GraphArgs& a, cudaStream_t s, int cps, int with_d10) {
+  constexpr size_t kS = std::max(std::max(std::max(SMS::up0, SMS::up), std::max(SMS::dns, SMS::d10)), SMS::dn);
+  if (with_d10) {
+    const int grid = persistent_grid<k_graph<FLLF_STORAGE, true>>(kS, a.ntasks, cps);
+    return grid > 0 ? launch_pdl(k_graph<FLLF_STORAGE, true>, grid, kS, s, a) : cudaSuccess;
+  }
+  const int grid = persistent_grid<k_graph<FLLF_STORAGE, false>>(kS, a.ntasks, cps);
+  return grid > 0 ? launch_pdl(k_graph<FLLF_STORAGE, false>, grid, kS, s, a) : cudaSuccess;
+}
+
 // Resident CTAs per SM of a stage kind's kernel (kind: 0 up0, 1 up, 2 down,
 // 3 down0 -- the fused level-0/1 kernel for the per-image path --, 4 chain,
 // 5 the small-level combine).
@@ -1857,6 +2020,10 @@ int FLLF_LAUNCH_NAME(occupancy)(int kind, int batched) {
     case 4: {
       constexpr size_t kChainSmem = SMS::up > SMS::dn1 ? SMS::up : SMS::dn1;
       return resident_per_sm<k_chain<FLLF_STORAGE>>(kChainSmem, nullptr);
+    }
+    case 6: {
+      constexpr size_t kS = std::max(std::max(std::max(SMS::up0, SMS::up), std::max(SMS::dns, SMS::d10)), SMS::dn);
+      return resident_per_sm<k_graph<FLLF_STORAGE, true>>(kS, nullptr);
     }
     default: return resident_per_sm<k_down_s<FLLF_STORAGE, false>>(SMS::dns, nullptr);
   }

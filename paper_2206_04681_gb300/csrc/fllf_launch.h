@@ -18,6 +18,7 @@ namespace fllf {
   cudaError_t launch_down0_##suffix(const Down0Args& a, cudaStream_t s, int cps);                        \
   cudaError_t launch_down10_##suffix(const Down10Args& a, cudaStream_t s, int cps);                      \
   cudaError_t launch_chain_##suffix(const ChainArgs& a, cudaStream_t s, int cps);                        \
+  cudaError_t launch_graph_##suffix(const GraphArgs& a, cudaStream_t s, int cps, int with_d10);          \
   cudaError_t launch_up0_batch_##suffix(const BatchTable<Up0Args>& t, cudaStream_t s, int cps);          \
   cudaError_t launch_up_batch_##suffix(const BatchTable<UpArgs>& t, cudaStream_t s, int cps);            \
   cudaError_t launch_down_batch_##suffix(const BatchTable<DownArgs>& t, cudaStream_t s, int cps);        \

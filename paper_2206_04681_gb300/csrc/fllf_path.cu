@@ -337,7 +337,7 @@ cudaError_t enqueue_fast(const fllf_params& p, const std::vector<Level>& lv, con
 cudaError_t enqueue_path(const fllf_params& p, const std::vector<Level>& lv, const PathMaps& maps,
                          const float* d_a, unsigned* fault, const float* d_in, float* d_out,
                          cudaStream_t s, StageHook* hook, const float* d_gain, float mscale,
-                         const Tuning* tune) {
+                         const Tuning* tune, const PlanGraph* graph) {
   static const Tuning kDefault{};
   const Tuning& tn = tune ? *tune : kDefault;
   const int L = p.levels, C = p.C, prec = p.precision;
@@ -352,6 +352,36 @@ cudaError_t enqueue_path(const fllf_params& p, const std::vector<Level>& lv, con
     if (hook) hook->mark(st, b, s);
   };
   cudaError_t e;
+
+  if (graph && tn.dataflow && !d_gain) {
+    // one persistent dataflow launch over every stage (the plan's task list;
+    // the level-0 argument blocks carry this run's input and output), or
+    // over every stage but the fused level-1/level-0 combine, which then
+    // follows as its own kernel
+    GraphArgs g = graph->args;
+    g.up0.I = d_in;
+    g.up0.use_tma = encode_image_map(&g.up0.imap, d_in, p.W, p.H, C, kUpIW, kUpIR) ? 1 : 0;
+    if (L >= 3) {
+      g.d10.I = d_in;
+      g.d10.O = d_out;
+      g.d10.use_tma = (g.up0.use_tma && encode_image_map(&g.d10.imap, d_in, p.W, p.H, C, kD0IW, kDnOH)) ? 1 : 0;
+    } else {
+      g.d0.I = d_in;
+      g.d0.O = d_out;
+    }
+    const bool with_d10 = graph->gb.with_d10;
+    mark(FLLF_STAGE_GRAPH, true);
+    if ((e = launch_graph(prec, g, sizeof(unsigned) * graph->gb.rt_words, s, tn.cps[FLLF_STAGE_GRAPH],
+                          with_d10)) != cudaSuccess)
+      return e;
+    mark(FLLF_STAGE_GRAPH, false);
+    if (L >= 3 && !with_d10) {
+      mark(FLLF_STAGE_DOWN0, true);
+      if ((e = launch_down10(prec, g.d10, s, tn.cps[FLLF_STAGE_DOWN0])) != cudaSuccess) return e;
+      mark(FLLF_STAGE_DOWN0, false);
+    }
+    return cudaSuccess;
+  }
 
   Up0Args u0{};
   u0.I = d_in;

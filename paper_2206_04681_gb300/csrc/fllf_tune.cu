@@ -94,6 +94,41 @@ void to_public(const Tuning& t, fllf_tuning* o) {
   for (int k = 0; k < FLLF_NSTAGE; ++k) o->ctas_per_sm[k] = t.cps[k];
   o->reduce_reverse = t.reverse;
   o->small_pixels = t.small_px;
+  o->dataflow = t.dataflow;
+  const int g[5] = {t.grain.up0, t.grain.up, t.grain.dns, t.grain.d10, t.grain.d0};
+  for (int k = 0; k < 5; ++k) o->task_items[k] = g[k];
+}
+
+GraphGrain grain_of(const fllf_tuning* t) {
+  GraphGrain g;
+  g.up0 = t->task_items[0];
+  g.up = t->task_items[1];
+  g.dns = t->task_items[2];
+  g.d10 = t->task_items[3];
+  g.d0 = t->task_items[4];
+  return g;
+}
+bool same_grain(const GraphGrain& a, const GraphGrain& b) {
+  return a.up0 == b.up0 && a.up == b.up && a.dns == b.dns && a.d10 == b.d10 && a.d0 == b.d0;
+}
+
+// Replaces the plan's dataflow task list by one with the given task sizes
+// and fused-combine mode (dataflow 2: the fused level-1/level-0 combine runs
+// as its own kernel).
+fllf_status regrain(fllf_plan* plan, const GraphGrain& g, int dataflow) {
+  const bool with_d10 = dataflow != 2;
+  if (!plan->graph || (same_grain(plan->tune.grain, g) && plan->graph->gb.with_d10 == with_d10)) {
+    plan->tune.grain = g;
+    return FLLF_OK;
+  }
+  cudaError_t e = cudaDeviceSynchronize();   // the old tables may be in use
+  if (e != cudaSuccess) return tfail(FLLF_ECUDA, std::string("device synchronize: ") + cudaGetErrorString(e));
+  PlanGraph* ng = plan_graph_create(plan, g, with_d10, &e);
+  if (!ng) return tfail(FLLF_ENOMEM, std::string("dataflow task table: ") + cudaGetErrorString(e));
+  plan_graph_destroy(plan->graph);
+  plan->graph = ng;
+  plan->tune.grain = g;
+  return FLLF_OK;
 }
 
 }  // namespace
@@ -113,6 +148,15 @@ fllf_status fllf_plan_set_tuning(fllf_plan* plan, const fllf_tuning* t) {
   for (int k = 0; k < FLLF_NSTAGE; ++k)
     if (t->ctas_per_sm[k] < 0 || t->ctas_per_sm[k] > 32) return tfail(FLLF_EINVAL, "ctas_per_sm must be 0..32");
   if (t->reduce_reverse != 0 && t->reduce_reverse != 1) return tfail(FLLF_EINVAL, "reduce_reverse must be 0 or 1");
+  if (t->dataflow < 0 || t->dataflow > 2) return tfail(FLLF_EINVAL, "dataflow must be 0, 1 or 2");
+  for (int k = 0; k < 5; ++k)
+    if (t->task_items[k] < 1 || t->task_items[k] > 4096) return tfail(FLLF_EINVAL, "task_items must be 1..4096");
+  {
+    Guard guard(plan->device);
+    const fllf_status st = regrain(plan, grain_of(t), t->dataflow);
+    if (st != FLLF_OK) return st;
+  }
+  plan->tune.dataflow = t->dataflow;
   plan->tune.chain_px = t->chain_pixels;
   for (int k = 0; k < FLLF_NSTAGE; ++k) plan->tune.cps[k] = t->ctas_per_sm[k];
   plan->tune.reverse = t->reduce_reverse;
@@ -134,22 +178,23 @@ fllf_status fllf_plan_autotune(fllf_plan* plan, const float* d_in, float* d_out,
     cudaGetLastError();
     return tfail(FLLF_ENOMEM, "autotune: the L2 flush buffer could not be allocated");
   }
-  auto measure = [&](const Tuning& t) {
+  PlanGraph* best_graph = plan->graph;   // the task list the best setting runs with
+  auto measure = [&](const Tuning& t, const PlanGraph* g) {
     return time_calls(
         [&] {
           return enqueue_path(p, plan->lv, plan->maps, plan->d_a, plan->d_fault, d_in, d_out, s, nullptr,
-                              nullptr, 0.f, &t);
+                              nullptr, 0.f, &t, g);
         },
         reps, s, flush, fbytes);
   };
   Tuning best = plan->tune;
-  double best_t = measure(best);
+  double best_t = measure(best, best_graph);
   if (best_t < 0) {
     cudaFree(flush);
     return tfail(FLLF_ECUDA, "autotune: a timed run failed");
   }
   auto consider = [&](const Tuning& t) {
-    const double m = measure(t);
+    const double m = measure(t, best_graph);
     if (m < 0) return false;
     if (m < kGain * best_t) {
       best = t;
@@ -158,6 +203,83 @@ fllf_status fllf_plan_autotune(fllf_plan* plan, const float* d_in, float* d_out,
     return true;
   };
   bool ok = true;
+  // keeps the candidate (and its task list) when it is at least 1% faster
+  auto consider_graph = [&](const Tuning& t, PlanGraph* g) {
+    const double m = measure(t, g);
+    if (m < 0) {
+      cudaStreamSynchronize(s);
+      plan_graph_destroy(g);
+      return false;
+    }
+    cudaStreamSynchronize(s);
+    if (m < kGain * best_t) {
+      if (best_graph != plan->graph && best_graph != g) plan_graph_destroy(best_graph);
+      best_graph = g;
+      best = t;
+      best_t = m;
+    } else if (g != best_graph && g != plan->graph) {
+      plan_graph_destroy(g);
+    }
+    return true;
+  };
+  // 0. one dataflow launch, the dataflow launch followed by the fused
+  // level-1/level-0 combine, or one launch per stage kind and level
+  if (best_graph) {
+    for (int mode = 0; mode <= 2 && ok; ++mode) {
+      if (mode == best.dataflow) continue;
+      Tuning t = best;
+      t.dataflow = mode;
+      if (mode == 0) {
+        ok = consider(t);
+        continue;
+      }
+      cudaError_t e;
+      PlanGraph* g = plan_graph_create(plan, t.grain, mode != 2, &e);
+      ok = g != nullptr && consider_graph(t, g);
+    }
+  }
+  if (ok && best_graph && best.dataflow) {
+    // its resident CTAs per SM, then the task size of each stage kind (a
+    // new task list per candidate)
+    const int occ = stage_occupancy(p.precision, FLLF_STAGE_GRAPH, false);
+    for (int c = 1; c <= occ && ok; ++c) {
+      Tuning t = best;
+      t.cps[FLLF_STAGE_GRAPH] = c == occ ? 0 : c;
+      if (t.cps[FLLF_STAGE_GRAPH] == best.cps[FLLF_STAGE_GRAPH]) continue;
+      ok = consider(t);
+    }
+    const std::vector<std::vector<int>> cand = {{1, 2, 4, 8, 16}, {2, 4, 8, 16, 32}, {1, 2, 4, 8}, {1, 2, 4}};
+    for (int k = 0; k < 4 && ok; ++k)
+      for (int v : cand[k]) {
+        if (!ok) break;
+        Tuning t = best;
+        int* f[4] = {&t.grain.up0, &t.grain.up, &t.grain.dns, &t.grain.d10};
+        if (*f[k] == v) continue;
+        *f[k] = v;
+        cudaError_t e;
+        PlanGraph* g = plan_graph_create(plan, t.grain, best.dataflow != 2, &e);
+        ok = g != nullptr && consider_graph(t, g);
+      }
+  }
+  if (best.dataflow && best_graph) {
+    // the per-stage settings below do not apply to the dataflow launch
+    if (best_graph != plan->graph) {
+      cudaStreamSynchronize(s);
+      plan_graph_destroy(plan->graph);
+      plan->graph = best_graph;
+    }
+    plan->tune = best;
+    cudaStreamSynchronize(s);
+    cudaFree(flush);
+    if (!ok) return tfail(FLLF_ECUDA, "autotune: a timed run failed");
+    if (best_ms) *best_ms = best_t;
+    return FLLF_OK;
+  }
+  if (best_graph != plan->graph) {   // a task list tried but the per-stage launches won
+    cudaStreamSynchronize(s);
+    plan_graph_destroy(best_graph);
+    best.grain = plan->tune.grain;
+  }
   // 1. where the chained launch of the small levels starts
   for (long long px : {0ll, 1ll << 15, 1ll << 17, 1ll << 19, 1ll << 21, 1ll << 23}) {
     Tuning t = best;
@@ -178,7 +300,7 @@ fllf_status fllf_plan_autotune(fllf_plan* plan, const float* d_in, float* d_out,
     }
   }
   // 3. resident CTAs per SM of each stage kind
-  for (int kind = 0; kind < FLLF_NSTAGE && ok; ++kind) {
+  for (int kind = 0; kind < FLLF_STAGE_GRAPH && ok; ++kind) {
     const int occ = stage_occupancy(p.precision, kind, false);
     for (int c = 1; c <= occ && ok; ++c) {
       Tuning t = best;

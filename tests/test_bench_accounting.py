@@ -92,3 +92,17 @@ def test_hbm_min_bytes_follow_the_definition():
     # input read + output write + guide pyramid (levels >= 1) written and read once
     got = bench.hbm_min_bytes(CFG)
     assert got / 1e6 == pytest.approx(265.4, abs=1.0)
+
+
+@pytest.mark.parametrize("mode", [1, 2])
+def test_dataflow_accounting_moves_the_work_into_one_kernel(mode):
+    base = bench.stage_accounts(CFG, 8)
+    flow = bench.stage_accounts(CFG, 8, dataflow=mode)
+    for b, f in zip(base, flow):
+        assert sum(f.values()) == pytest.approx(sum(b.values()))
+    ops = flow[0]
+    if mode == 1:
+        assert ops["graph"] == pytest.approx(sum(base[0].values()))
+    else:   # the fused level-1/level-0 combine stays its own kernel
+        assert ops["down0"] == pytest.approx(base[0]["down0"])
+        assert ops["graph"] == pytest.approx(sum(base[0].values()) - base[0]["down0"])

@@ -50,11 +50,15 @@ def _setup(precision):
     return plans, ins, outs, refs, imgs, params
 
 
-@pytest.mark.parametrize("precision", ["fp32", "fp16"])
-def test_batch_equals_per_image_runs(precision):
+@pytest.mark.parametrize("precision,mode", [("fp32", 0), ("fp32", 1), ("fp32", 2), ("fp16", 1), ("bf16", 2)])
+def test_batch_equals_per_image_runs(precision, mode):
+    # every launch mode (per stage kind and level; one dataflow launch; the
+    # dataflow launch and the batched fused combine): the per-image bits
     plans, ins, outs, refs, imgs, params = _setup(precision)
     batch = pkg.fllf_batch_create(plans)
     try:
+        pkg.fllf_batch_set_mode(batch, mode, [3, 5, 2, 1, 3] if mode == 2 else None)
+        assert pkg.fllf_batch_get_mode(batch)[0] == mode
         s = torch.cuda.current_stream().cuda_stream
         for rep in range(3):
             for y in outs:
