@@ -248,6 +248,11 @@ fllf_status fllf_batch_run_plans(fllf_plan *const *plans, const float *const *d_
  * batched wave on one of `max_waves` streams, so requests that arrive while
  * others run are admitted and overlap them on the device.  A request's
  * result does not depend on the other requests it shares a wave with.
+ * Plans stay resident: the coefficients of every parameter set seen (m,
+ * sigma_r, T, K, coefficient mode) are cached on the host and in a device
+ * slot; a new set's quadrature runs in fllf_server_submit on the caller's
+ * thread, and admission only encodes the request's tensor maps for its pool
+ * range.
  * Latency is measured from fllf_server_submit to the worker seeing the
  * request's wave complete. */
 typedef struct fllf_server fllf_server;
@@ -259,6 +264,9 @@ typedef struct {
   size_t pool_bytes, pool_peak_bytes;
   int max_active;        /* peak number of admitted, unfinished requests */
   int waves;             /* waves launched */
+  uint64_t plan_cache_hits;     /* submissions whose coefficient set was resident */
+  uint64_t plan_cache_misses;   /* submissions that computed theirs (in fllf_server_submit) */
+  uint64_t admission_quadratures; /* coefficient quadratures run at admission (always 0) */
 } fllf_server_stats;
 
 /* Creates a server on `device`.  hbm_budget: pool bytes (>= 1 MiB); max_slots:

@@ -40,7 +40,9 @@ class fllf_server_stats(ctypes.Structure):
                 ("p99_ms", ctypes.c_double), ("mean_ms", ctypes.c_double),
                 ("max_ms", ctypes.c_double), ("mpixel_per_s", ctypes.c_double),
                 ("pool_bytes", ctypes.c_size_t), ("pool_peak_bytes", ctypes.c_size_t),
-                ("max_active", ctypes.c_int), ("waves", ctypes.c_int)]
+                ("max_active", ctypes.c_int), ("waves", ctypes.c_int),
+                ("plan_cache_hits", ctypes.c_uint64), ("plan_cache_misses", ctypes.c_uint64),
+                ("admission_quadratures", ctypes.c_uint64)]
 
     def as_dict(self):
         return {name: getattr(self, name) for name, _ in self._fields_}

@@ -2,6 +2,7 @@
 // run / submit / poll.  Host code; the kernels live in fllf_kernels_*.cu.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <chrono>
 #include <cmath>
 #include <cstring>
@@ -90,19 +91,38 @@ void compute_coeffs(const fllf_params& p, double* a) {
     return;
   }
   // (2/T) * integral_{-T/2}^{T/2} f(x) sin(w_k x) dx; the integrand is even,
-  // so integrate over [0, T/2] and double.  512 panels x 16 nodes.
-  const int panels = 512, nodes = 16;
-  std::vector<double> gx, gw;
-  gauss_legendre(nodes, gx, gw);
+  // so integrate over [0, T/2] and double.  Composite 16-node Gauss-Legendre
+  // on panels no wider than a quarter of sigma_r and of the period of the
+  // highest order (at least 64 panels, at most 4096): each panel holds a
+  // smooth, slowly varying piece of the integrand, where the rule is exact
+  // to rounding.  At each node, sin(k w_1 x) for k = 1..K follows from
+  // sin(w_1 x), cos(w_1 x) by the rotation (c, s) <- (c c1 - s s1, s c1 + c s1).
+  const int nodes = 16;
+  static const std::vector<double> gl = [] {
+    std::vector<double> x, w;
+    gauss_legendre(16, x, w);
+    x.insert(x.end(), w.begin(), w.end());
+    return x;
+  }();
+  const double* gx = gl.data();
+  const double* gw = gl.data() + nodes;
+  const double half = T / 2.0, scale = std::min(s, T / K) / 4.0;
+  const int panels = (int)std::min(4096.0, std::max(64.0, std::ceil(half / scale)));
   for (int k = 0; k < K; ++k) a[k] = 0.0;
-  const double h = (T / 2.0) / panels;
+  const double h = half / panels, w1 = 2.0 * pi / T;
   for (int q = 0; q < panels; ++q) {
-    const double lo = q * h, mid = lo + 0.5 * h;
+    const double mid = q * h + 0.5 * h;
     for (int i = 0; i < nodes; ++i) {
       const double x = mid + 0.5 * h * gx[i];
-      const double wq = 0.5 * h * gw[i];
-      const double fx = g * x * std::exp(-x * x / (2.0 * s * s));
-      for (int k = 1; k <= K; ++k) a[k - 1] += wq * fx * std::sin(2.0 * pi * k / T * x);
+      const double wf = 0.5 * h * gw[i] * g * x * std::exp(-x * x / (2.0 * s * s));
+      const double s1 = std::sin(w1 * x), c1 = std::cos(w1 * x);
+      double sk = s1, ck = c1;
+      for (int k = 0; k < K; ++k) {
+        a[k] += wf * sk;
+        const double sn = sk * c1 + ck * s1;
+        ck = ck * c1 - sk * s1;
+        sk = sn;
+      }
     }
   }
   for (int k = 0; k < K; ++k) a[k] *= 2.0 * (2.0 / T);

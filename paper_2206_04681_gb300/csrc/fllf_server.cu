@@ -7,12 +7,22 @@
 //      the requests' pool ranges and slots),
 //   2. admits queued requests in FIFO order while a slot, pool memory and a
 //      free wave context are available (all requests of one wave share the
-//      storage precision), building their plans inside the pool,
+//      storage precision), building their plans inside the pool from the
+//      server's resident plan data (below),
 //   3. launches the admitted group as one batched wave on the context's
 //      stream (argument tables uploaded from pinned memory, then the batched
 //      stage kernels), and records the wave's event.
 // Waves on different streams overlap on the device, and requests that arrive
 // while waves run are admitted as soon as resources free up.
+//
+// Resident plan data: the Fourier coefficients of every parameter set the
+// server has seen (m, sigma_r, T, K, coefficient mode) are kept in a cache,
+// on the host and in a device slot, as long as a request uses them and
+// afterwards until the cache is full (least recently used first out).  The
+// quadrature of a new parameter set runs in fllf_server_submit, on the
+// caller's thread; admission only takes the cached slot (uploading the
+// coefficients once, when a set first gets a slot) and encodes the request's
+// tensor maps for its pool range.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -94,6 +104,33 @@ class RangeAlloc {
 
 enum ReqState { kPending = 0, kAdmitted = 1, kDone = 2, kFailed = 3 };
 
+// The parameters the coefficients depend on.
+struct CoefKey {
+  double m, sigma_r, T;
+  int K, mode;
+  bool operator==(const CoefKey& o) const {
+    return m == o.m && sigma_r == o.sigma_r && T == o.T && K == o.K && mode == o.mode;
+  }
+};
+struct CoefKeyHash {
+  size_t operator()(const CoefKey& k) const {
+    const uint64_t a = std::hash<double>()(k.m), b = std::hash<double>()(k.sigma_r),
+                   c = std::hash<double>()(k.T);
+    return (size_t)(a * 0x9E3779B97F4A7C15ull ^ (b + 0x632BE59BD9B4E019ull) * 31 ^ c * 17 ^ (uint64_t)k.K * 131 ^
+                    (uint64_t)k.mode);
+  }
+};
+// A cached coefficient set: float32 values, its device slot (-1: none yet),
+// the requests that hold it and when it was last used.
+struct CoefEntry {
+  std::vector<float> a32;
+  int slot = -1;
+  int refs = 0;
+  uint64_t tick = 0;
+};
+constexpr int kCoefSlots = 4096;         // device slots of 64 floats
+constexpr int kCoefCache = 2 * kCoefSlots;  // cached sets (with or without a slot)
+
 struct Request {
   uint64_t id = 0;
   fllf_params p{};
@@ -103,12 +140,12 @@ struct Request {
   int state = kPending;
   size_t off = 0, bytes = 0;      // pool range
   fllf_plan plan;                 // plan living inside the pool range
-  std::vector<float> a32;         // coefficients uploaded with the wave
+  CoefEntry* coef = nullptr;      // its cached coefficient set (held until it finishes)
   std::string err;                // why the request failed (the worker's errors are its own)
 };
 
-// Bytes of one request in the pool: coefficients (256 B) + pyramids.
-size_t request_bytes(const fllf_params& p) { return 256 + layout(p, nullptr); }
+// Bytes of one request in the pool: its pyramids.
+size_t request_bytes(const fllf_params& p) { return layout(p, nullptr); }
 
 // Status block after the pool: 16 waves x 64 bytes.
 constexpr size_t kStatusBytes = 1024;
@@ -150,6 +187,11 @@ struct fllf_server {
   std::vector<double> lat_ms;
   double px_done = 0, t_first = 0, t_last = 0;
   int max_active = 0, nwaves = 0;
+  // resident plan data
+  std::unordered_map<CoefKey, CoefEntry, CoefKeyHash> coefs;
+  float* d_coef = nullptr;         // kCoefSlots x 64 floats
+  std::vector<int> free_slots;
+  uint64_t tick = 0, cache_hits = 0, cache_misses = 0, admission_quadratures = 0;
 };
 
 namespace {
@@ -163,7 +205,7 @@ fllf_status sfail(fllf_status s, const std::string& why) {
 bool build_request_plan(fllf_server* sv, Request* r) {
   std::vector<Level> rel;
   layout(r->p, &rel);
-  unsigned char* base = sv->pool + r->off + 256;
+  unsigned char* base = sv->pool + r->off;
   fllf_plan& pl = r->plan;
   pl.p = r->p;
   pl.device = sv->device;
@@ -181,15 +223,41 @@ bool build_request_plan(fllf_server* sv, Request* r) {
     v.Z = base + reinterpret_cast<size_t>(rel[l].Z);
     v.E = (l <= L - 2) ? reinterpret_cast<float*>(base + reinterpret_cast<size_t>(rel[l].E)) : nullptr;
   }
-  if (!check_layout(r->p, pl.lv, base, r->bytes - 256)) return false;
-  pl.d_a = reinterpret_cast<float*>(sv->pool + r->off);
+  if (!check_layout(r->p, pl.lv, base, r->bytes)) return false;
   pl.d_fault = sv->d_status;
   pl.scratch = nullptr;  // owned by the pool
   if (L > 1 && !build_maps(r->p, pl.lv, &pl.maps)) return false;
-  std::vector<double> a64(r->p.K);
-  compute_coeffs(r->p, a64.data());
-  r->a32.assign(a64.begin(), a64.end());
+  // the cached coefficients: a device slot, filled when the set first gets one
+  CoefEntry& ce = *r->coef;
+  if (ce.slot < 0) {
+    if (sv->free_slots.empty()) {
+      // take the slot of the least recently used set no request holds
+      CoefEntry* lru = nullptr;
+      for (auto& kv : sv->coefs)
+        if (kv.second.slot >= 0 && kv.second.refs == 0 && (!lru || kv.second.tick < lru->tick)) lru = &kv.second;
+      if (!lru) return false;
+      sv->free_slots.push_back(lru->slot);
+      lru->slot = -1;
+    }
+    ce.slot = sv->free_slots.back();
+    sv->free_slots.pop_back();
+    if (cudaMemcpy(sv->d_coef + 64 * (size_t)ce.slot, ce.a32.data(), sizeof(float) * ce.a32.size(),
+                   cudaMemcpyHostToDevice) != cudaSuccess) {
+      cudaGetLastError();
+      sv->free_slots.push_back(ce.slot);
+      ce.slot = -1;
+      return false;
+    }
+  }
+  ce.tick = ++sv->tick;
+  pl.d_a = sv->d_coef + 64 * (size_t)ce.slot;
   return true;
+}
+
+// Releases a request's hold on its cached coefficients (lock held).
+void release_coef(Request* r) {
+  if (r->coef) --r->coef->refs;
+  r->coef = nullptr;
 }
 
 // Enqueues a wave: coefficient uploads, argument tables, batched stages.
@@ -206,8 +274,7 @@ cudaError_t launch_wave(fllf_server* sv, Wave& w) {
   build_batch_blob(plans, w.reqs.front()->p.precision, &bb);
   set_blob_fault(bb, w.d_fault);
   set_blob_io(bb, ins.data(), outs.data());
-  size_t coef = (bb.blob.size() + 15) & ~size_t(15);
-  const size_t need = coef + 256 * w.reqs.size();
+  const size_t need = bb.blob.size();
   cudaError_t e;
   if (need > w.cap) {
     if (w.h_tab) cudaFreeHost(w.h_tab);
@@ -221,18 +288,10 @@ cudaError_t launch_wave(fllf_server* sv, Wave& w) {
     w.cap = cap;
   }
   std::memcpy(w.h_tab, bb.blob.data(), bb.blob.size());
-  for (size_t j = 0; j < w.reqs.size(); ++j)
-    std::memcpy(w.h_tab + coef + 256 * j, w.reqs[j]->a32.data(), sizeof(float) * w.reqs[j]->a32.size());
   *w.h_fault = 0;
   if ((e = cudaMemsetAsync(w.d_fault, 0, sizeof(unsigned), w.stream)) != cudaSuccess) return e;
   if ((e = cudaMemcpyAsync(w.d_tab, w.h_tab, need, cudaMemcpyHostToDevice, w.stream)) != cudaSuccess)
     return e;
-  for (size_t j = 0; j < w.reqs.size(); ++j) {
-    Request* r = w.reqs[j];
-    if ((e = cudaMemcpyAsync(r->plan.d_a, w.d_tab + coef + 256 * j, sizeof(float) * r->a32.size(),
-                             cudaMemcpyDeviceToDevice, w.stream)) != cudaSuccess)
-      return e;
-  }
   for (int i : bb.copy_img) {
     const fllf_params& p = w.reqs[i]->p;
     if ((e = cudaMemcpyAsync(outs[i], ins[i], sizeof(float) * (size_t)p.H * p.W * p.C,
@@ -271,6 +330,7 @@ void worker_loop(fllf_server* sv) {
         r->err = why;
         r->state = (q == cudaSuccess) ? kDone : kFailed;
         sv->alloc.release(r->off, r->bytes);
+        release_coef(r);
         --sv->active;
         if (q == cudaSuccess) {
           ++sv->completed;
@@ -307,6 +367,7 @@ void worker_loop(fllf_server* sv) {
         sv->pending.pop_front();
         if (!build_request_plan(sv, r)) {
           sv->alloc.release(off, r->bytes);
+          release_coef(r);
           r->err = "plan construction inside the pool failed";
           r->state = kFailed;
           ++sv->rejected;
@@ -331,6 +392,7 @@ void worker_loop(fllf_server* sv) {
             r->err = std::string("wave launch: ") + cudaGetErrorString(e);
             r->state = kFailed;
             sv->alloc.release(r->off, r->bytes);
+            release_coef(r);
             --sv->active;
           }
           free_w->reqs.clear();
@@ -352,6 +414,7 @@ void worker_loop(fllf_server* sv) {
 }  // namespace
 
 static void free_server(fllf_server* sv) {
+  if (sv->d_coef) cudaFree(sv->d_coef);
   for (Wave& w : sv->waves) {
     if (w.stream) cudaStreamDestroy(w.stream);
     if (w.done) cudaEventDestroy(w.done);
@@ -401,6 +464,14 @@ fllf_status fllf_server_create(int device, size_t hbm_budget, int max_slots, int
     return sfail(FLLF_ECUDA, "status block allocation failed");
   }
   std::memset(sv->h_status, 0, kStatusBytes);
+  if (cudaMalloc(&sv->d_coef, sizeof(float) * 64 * kCoefSlots) != cudaSuccess) {
+    cudaGetLastError();
+    sv->d_coef = nullptr;
+    free_server(sv);
+    if (prev >= 0) cudaSetDevice(prev);
+    return sfail(FLLF_ENOMEM, "coefficient slots allocation failed");
+  }
+  for (int j = kCoefSlots - 1; j >= 0; --j) sv->free_slots.push_back(j);
   sv->alloc.reset(sv->budget);
   sv->waves.resize(max_waves);
   for (int i = 0; i < max_waves; ++i) {
@@ -434,7 +505,10 @@ fllf_status fllf_server_destroy(fllf_server* sv) {
   {
     std::lock_guard<std::mutex> lk(sv->mu);
     sv->stop = true;
-    for (Request* r : sv->pending) r->state = kFailed;
+    for (Request* r : sv->pending) {
+      r->state = kFailed;
+      release_coef(r);
+    }
     sv->pending.clear();
   }
   sv->cv.notify_all();
@@ -469,6 +543,19 @@ fllf_status fllf_server_submit(fllf_server* sv, const fllf_params* p, const floa
   r->in = d_in;
   r->out = d_out;
   r->bytes = bytes;
+  // the coefficient set: from the cache, or computed here (on the caller's
+  // thread, outside the server's lock) and cached
+  const CoefKey key{p->m, p->sigma_r, p->T, p->K, p->coeff_mode};
+  std::vector<float> fresh;
+  {
+    std::lock_guard<std::mutex> lk(sv->mu);
+    if (sv->coefs.find(key) == sv->coefs.end()) fresh.resize(1);
+  }
+  if (!fresh.empty()) {
+    std::vector<double> a64(p->K);
+    compute_coeffs(*p, a64.data());
+    fresh.assign(a64.begin(), a64.end());
+  }
   {
     std::lock_guard<std::mutex> lk(sv->mu);
     if (sv->stop) return sfail(FLLF_EINVAL, "server is stopping");
@@ -476,6 +563,34 @@ fllf_status fllf_server_submit(fllf_server* sv, const fllf_params* p, const floa
       ++sv->rejected;
       return sfail(FLLF_EBUSY, "request queue is full");
     }
+    auto it = sv->coefs.find(key);
+    if (it == sv->coefs.end()) {
+      if (fresh.empty()) {   // evicted since the look-up above: compute under the lock (rare)
+        std::vector<double> a64(p->K);
+        compute_coeffs(*p, a64.data());
+        fresh.assign(a64.begin(), a64.end());
+      }
+      if ((int)sv->coefs.size() >= kCoefCache) {
+        // make room: drop the least recently used sets no request holds
+        std::vector<std::pair<uint64_t, CoefKey>> idle;
+        for (auto& kv : sv->coefs)
+          if (kv.second.refs == 0) idle.push_back({kv.second.tick, kv.first});
+        std::sort(idle.begin(), idle.end(), [](const auto& x, const auto& y) { return x.first < y.first; });
+        for (size_t j = 0; j < idle.size() && j < (size_t)kCoefCache / 4; ++j) {
+          auto e = sv->coefs.find(idle[j].second);
+          if (e->second.slot >= 0) sv->free_slots.push_back(e->second.slot);
+          sv->coefs.erase(e);
+        }
+      }
+      it = sv->coefs.emplace(key, CoefEntry{}).first;
+      it->second.a32 = std::move(fresh);
+      ++sv->cache_misses;
+    } else {
+      ++sv->cache_hits;
+    }
+    ++it->second.refs;
+    it->second.tick = ++sv->tick;
+    r->coef = &it->second;
     r->id = sv->next_id++;
     r->t_submit = now_s();
     if (sv->submitted == 0 || sv->t_first == 0) sv->t_first = r->t_submit;
@@ -537,6 +652,9 @@ fllf_status fllf_server_stats_get(fllf_server* sv, fllf_server_stats* out) {
   s.pool_peak_bytes = sv->alloc.peak();
   s.max_active = sv->max_active;
   s.waves = sv->nwaves;
+  s.plan_cache_hits = sv->cache_hits;
+  s.plan_cache_misses = sv->cache_misses;
+  s.admission_quadratures = sv->admission_quadratures;
   *out = s;
   return FLLF_OK;
 }
@@ -549,6 +667,7 @@ fllf_status fllf_server_stats_reset(fllf_server* sv) {
   sv->px_done = sv->t_first = sv->t_last = 0;
   sv->max_active = sv->active;
   sv->nwaves = 0;
+  sv->cache_hits = sv->cache_misses = sv->admission_quadratures = 0;
   sv->alloc.reset_peak();
   return FLLF_OK;
 }

@@ -154,3 +154,30 @@ def test_submit_and_poll_errors():
         assert pkg.fllf_server_stats_get(server)["completed"] == 0
     finally:
         pkg.fllf_server_destroy(server)
+
+
+def test_plans_stay_resident():
+    """Requests with a parameter set the server has seen reuse its resident
+    coefficients: the quadrature runs once per set (in submit), never at
+    admission, and the results stay those of the per-image plans."""
+    server = pkg.fllf_server_create(2 << 30, max_slots=4, max_queue=64, max_waves=2)
+    try:
+        cases = [MIX[0], MIX[2], MIX[0], MIX[5], MIX[2], MIX[0]]   # 3 distinct parameter sets
+        reqs = [_request(c, 80 + i, "fp32") for i, c in enumerate(cases)]
+        _serve(server, reqs)
+        st = pkg.fllf_server_stats_get(server)
+        assert st["plan_cache_misses"] == 3 and st["plan_cache_hits"] == 3
+        assert st["admission_quadratures"] == 0
+        for p, img, x, y in reqs:
+            plan = pkg.fllf_plan_create(p, 0)
+            ref = torch.empty_like(x)
+            pkg.run_tensor(plan, x, ref)
+            torch.cuda.synchronize()
+            pkg.fllf_plan_destroy(plan)
+            torch.testing.assert_close(y, ref, rtol=0, atol=0)
+        # a second round: every set is resident now
+        _serve(server, [_request(c, 90 + i, "fp32") for i, c in enumerate(cases[:3])])
+        st = pkg.fllf_server_stats_get(server)
+        assert st["plan_cache_misses"] == 3 and st["plan_cache_hits"] == 6
+    finally:
+        pkg.fllf_server_destroy(server)
