@@ -49,7 +49,7 @@ def parse():
                          "request streams.  The precision sweep and the served-request accuracy "
                          "are in tests/accuracy.py")
     ap.add_argument("--serve-seconds", type=float, default=None,
-                    help="length of each served stream (default 30 s; 4 s in the uhd line)")
+                    help="length of each served stream (default 30 s; 2.5 s per rate in the uhd line)")
     ap.add_argument("--serve-rates", type=str, default=None,
                     help="comma-separated arrival rates in requests/s, or max for a backlog "
                          "(default 50,100,200,400,max)")
@@ -697,7 +697,7 @@ def run_ours(args):
                                     "(2K + 1)"}
     if rank == 0 and world == 1 and not args.no_serve:
         line["serving"] = serving_summary(pkg, torch, device, args.serve_precision,
-                                          seconds=args.serve_seconds or 4.0)
+                                          seconds=args.serve_seconds or 2.5)
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"], acc = cpu_baseline_and_accuracy(img, gpu_outs)
         line["accuracy"] = acc[args.precision]
@@ -887,7 +887,9 @@ def serve_rate(pkg, torch, server, canvas, rate, seconds, precision, keep=()):
                                  "p99": float(np.percentile(lat, 99)) if lat else None,
                                  "measured": "scheduled arrival -> poll OK (client)"},
            "waves": st["waves"], "max_active": st["max_active"],
-           "pool_peak_gb": st["pool_peak_bytes"] / 1e9}
+           "pool_peak_gb": st["pool_peak_bytes"] / 1e9,
+           "plan_cache": {"hits": st["plan_cache_hits"], "misses": st["plan_cache_misses"],
+                          "admission_quadratures": st["admission_quadratures"]}}
     return out, reqs, kept
 
 
@@ -896,17 +898,19 @@ def make_server(pkg, device):
                                   SERVE["max_waves"], device)
 
 
-def serving_summary(pkg, torch, device, precision, rate=200, seconds=4.0):
-    """A short served stream for the headline line."""
+def serving_summary(pkg, torch, device, precision, rates=(50, 200, 400), seconds=2.5):
+    """Short served streams at a low, middle and high arrival rate for the
+    headline line."""
     server = make_server(pkg, device)
+    runs = []
     try:
         canvas = serve_canvas(torch, device)
-        out, _, _ = serve_rate(pkg, torch, server, canvas, rate, seconds, precision)
+        for rate in rates:
+            out, _, _ = serve_rate(pkg, torch, server, canvas, rate, seconds, precision)
+            runs.append(out)
     finally:
         pkg.fllf_server_destroy(server)
-    out["pyramid_storage"] = precision
-    out["budget_gb"] = SERVE["budget"] / 2 ** 30
-    return out
+    return {"pyramid_storage": precision, "budget_gb": SERVE["budget"] / 2 ** 30, "runs": runs}
 
 
 def run_serve(args):

@@ -139,8 +139,16 @@ def run_serve(rate=200, seconds=8.0, n_check=32, precision="fp16"):
     build.build_library()
     torch.cuda.set_device(0)
     reqs = request_stream(rate, seconds, seed=bench.SERVE["seed"])
-    order = sorted(range(len(reqs)), key=lambda j: reqs[j]["H"] * reqs[j]["W"] * reqs[j]["C"])
-    keep = order[:n_check]
+    # a seeded random sample of the stream, with at least n_big requests whose
+    # longer side is >= 4096 (the smallest of those by area, to bound the
+    # float64 oracle's memory and time on the host)
+    rng = np.random.default_rng(bench.SERVE["seed"] + 7)
+    big = sorted((j for j in range(len(reqs)) if max(reqs[j]["H"], reqs[j]["W"]) >= 4096),
+                 key=lambda j: reqs[j]["H"] * reqs[j]["W"] * reqs[j]["C"])
+    n_big = min(len(big), max(4, n_check // 8))
+    keep = list(big[:n_big])
+    rest = [j for j in range(len(reqs)) if j not in set(keep)]
+    keep += [int(j) for j in rng.choice(rest, size=min(len(rest), n_check - n_big), replace=False)]
     server = bench.make_server(pkg, 0)
     try:
         canvas = bench.serve_canvas(torch, 0)
@@ -155,9 +163,14 @@ def run_serve(rate=200, seconds=8.0, n_check=32, precision="fp16"):
     print(json.dumps({
         "report": "served requests against the float64 oracle",
         "config": {"rate_per_s": rate, "seconds": seconds, "pyramid_storage": precision,
-                   "sample": f"the {len(res)} smallest requests of the stream"},
+                   "sample": f"{len(res)} requests: the {n_big} smallest with a side >= 4096 and a "
+                             f"seeded random choice of the others"},
         "requests_checked": len(res), "min_psnr_db": min(r[0] for r in res),
-        "max_abs": max(r[1] for r in res), "serve": out}), flush=True)
+        "max_abs": max(r[1] for r in res),
+        "largest_checked": max(f"{reqs[j]['C']}x{reqs[j]['H']}x{reqs[j]['W']}" for j in idx),
+        "checked": [{"C": reqs[j]["C"], "H": reqs[j]["H"], "W": reqs[j]["W"], "K": reqs[j]["K"],
+                     "psnr_db": r[0], "max_abs": r[1]} for j, r in zip(idx, res)],
+        "serve": out}), flush=True)
     return 0
 
 
