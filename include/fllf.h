@@ -424,8 +424,8 @@ fllf_status fllf_plan_set_wait_test(fllf_plan *plan, long long wait_cycles, unsi
  *                   per level above), the combines at levels >= 2 (32 x 16
  *                   tiles; at level 2, halved per level above), the fused
  *                   level-1/0 combine (64 x 32 tiles) and the level-0
- *                   combine of 2-level images; 1..4096 each (default 4, 8,
- *                   4, 2, 4).
+ *                   combine of 2-level images; 1..4096 each, 0 = the
+ *                   default (4, 8, 4, 2, 4).
  * Every setting computes the same output, bit for bit. */
 typedef struct {
   long long chain_pixels;
@@ -437,8 +437,8 @@ typedef struct {
 } fllf_tuning;
 
 /* Reads / replaces a plan's launch tuning.  set: chain_pixels >= 0,
- * small_pixels >= 0, ctas_per_sm 0..32, reduce_reverse 0 or 1, dataflow 0
- * or 1, task_items 1..4096; otherwise FLLF_EINVAL.  A change of task_items
+ * small_pixels >= 0, ctas_per_sm 0..32, reduce_reverse 0 or 1, dataflow 0,
+ * 1 or 2, task_items 0..4096; otherwise FLLF_EINVAL.  A change of task_items
  * rebuilds the plan's task list (allocates its tables anew; synchronises the
  * device). */
 fllf_status fllf_plan_get_tuning(const fllf_plan *plan, fllf_tuning *out);

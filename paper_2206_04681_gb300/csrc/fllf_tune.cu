@@ -99,13 +99,12 @@ void to_public(const Tuning& t, fllf_tuning* o) {
   for (int k = 0; k < 5; ++k) o->task_items[k] = g[k];
 }
 
+// Task sizes of a public tuning (0: the default of that kind).
 GraphGrain grain_of(const fllf_tuning* t) {
   GraphGrain g;
-  g.up0 = t->task_items[0];
-  g.up = t->task_items[1];
-  g.dns = t->task_items[2];
-  g.d10 = t->task_items[3];
-  g.d0 = t->task_items[4];
+  int* f[5] = {&g.up0, &g.up, &g.dns, &g.d10, &g.d0};
+  for (int k = 0; k < 5; ++k)
+    if (t->task_items[k] > 0) *f[k] = t->task_items[k];
   return g;
 }
 bool same_grain(const GraphGrain& a, const GraphGrain& b) {
@@ -150,7 +149,7 @@ fllf_status fllf_plan_set_tuning(fllf_plan* plan, const fllf_tuning* t) {
   if (t->reduce_reverse != 0 && t->reduce_reverse != 1) return tfail(FLLF_EINVAL, "reduce_reverse must be 0 or 1");
   if (t->dataflow < 0 || t->dataflow > 2) return tfail(FLLF_EINVAL, "dataflow must be 0, 1 or 2");
   for (int k = 0; k < 5; ++k)
-    if (t->task_items[k] < 1 || t->task_items[k] > 4096) return tfail(FLLF_EINVAL, "task_items must be 1..4096");
+    if (t->task_items[k] < 0 || t->task_items[k] > 4096) return tfail(FLLF_EINVAL, "task_items must be 0..4096");
   {
     Guard guard(plan->device);
     const fllf_status st = regrain(plan, grain_of(t), t->dataflow);

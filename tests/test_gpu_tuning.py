@@ -26,13 +26,16 @@ NST = len(pkg.STAGES)
 ALL = 1 << 40   # every combined level >= 2 on the small tiles
 
 
-def _tuning(chain, cps, rev, small=ALL):
-    t = pkg.fllf_tuning()
+def _tuning(chain, cps, rev, small=ALL, dataflow=0, items=(0, 0, 0, 0, 0)):
+    t = pkg.fllf_tuning()   # task sizes 0: the defaults
     t.chain_pixels = chain
     for i, c in enumerate(cps):
         t.ctas_per_sm[i] = c
     t.reduce_reverse = rev
     t.small_pixels = small
+    t.dataflow = dataflow
+    for i, v in enumerate(items):
+        t.task_items[i] = v
     return t
 
 
@@ -48,7 +51,8 @@ def test_every_launch_setting_gives_the_same_bits(precision):
         outs = []
         for t in (_tuning(1 << 21, [0] * NST, 1), _tuning(0, [0] * NST, 0), _tuning(1 << 23, [1] * NST, 1),
                   _tuning(1 << 15, [2, 1, 1, 1, 1, 2], 0), _tuning(0, [0] * NST, 1, small=0),
-                  _tuning(0, [0] * NST, 1, small=1 << 19), _tuning(1 << 17, [0, 0, 0, 0, 0, 1], 1, small=ALL)):
+                  _tuning(0, [0] * NST, 1, small=1 << 19), _tuning(1 << 17, [0, 0, 0, 0, 0, 1], 1, small=ALL),
+                  _tuning(0, [0] * NST, 1, dataflow=1), _tuning(0, [0] * NST, 1, dataflow=2, items=(2, 16, 1, 1, 1))):
             pkg.fllf_plan_set_tuning(plan, t)
             y = torch.full_like(x, float("nan"))
             pkg.run_tensor(plan, x, y)
