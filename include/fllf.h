@@ -361,15 +361,16 @@ fllf_status fllf_plan_stage_times(fllf_plan *plan, double *ms, int *launches);
 
 /* Host-only check of the dataflow launch's task list (no device work): builds
  * the list for n parameter sets (one batch; n == 1 is a plan's own list) with
- * the given task sizes (task_items[5] as in fllf_tuning, NULL = defaults) and
- * with or without the fused level-1/level-0 combine, then runs it in order
- * on one host worker.  FLLF_OK when every work item of every stage is in
+ * the given task sizes (task_items[5] as in fllf_tuning, NULL = defaults),
+ * with or without the fused level-1/level-0 combine, and from first_level up
+ * (0: every stage; 2..15: the list of dataflow mode 3), then runs it in
+ * order on one host worker.  FLLF_OK when every work item of every stage is in
  * exactly one task, every task comes after the tasks whose row bands it
  * reads, and every band reaches the count its readers wait for;
  * FLLF_EINVAL with the reason otherwise.  *ntasks, *nbands (may be NULL):
  * the list's size. */
-fllf_status fllf_dataflow_check(const fllf_params *ps, int n, const int *task_items, int with_d10, int *ntasks,
-                                int *nbands);
+fllf_status fllf_dataflow_check(const fllf_params *ps, int n, const int *task_items, int with_d10,
+                                int first_level, int *ntasks, int *nbands);
 
 /* Test hook for the bounded device waits (failure detection; the paper has
  * no counterpart).  Every wait in the kernels gives up
@@ -414,8 +415,12 @@ fllf_status fllf_plan_set_wait_test(fllf_plan *plan, long long wait_cycles, unsi
  *                   the level below has finished and no launch boundary
  *                   separates the levels.  2: the same without the fused
  *                   level-1/level-0 combine, which follows as its own
- *                   kernel.  0 (default; measured faster at 4K RGB): one
- *                   launch per stage kind and level (the settings above).
+ *                   kernel.  3: the stages below dataflow_level as their own
+ *                   kernels and one dataflow launch for the REDUCE from that
+ *                   level to the top and the combines back down to it (the
+ *                   small, latency-bound levels).  0 (default; measured
+ *                   faster at 4K RGB): one launch per stage kind and level
+ *                   (the settings above).
  *                   The same stage code on the same work items: the same
  *                   output, bit for bit.
  *   task_items[5]   work items per task of the dataflow launch for the
@@ -426,6 +431,8 @@ fllf_status fllf_plan_set_wait_test(fllf_plan *plan, long long wait_cycles, unsi
  *                   level-1/0 combine (64 x 32 tiles) and the level-0
  *                   combine of 2-level images; 1..4096 each, 0 = the
  *                   default (4, 8, 4, 2, 4).
+ *   dataflow_level  first level of the dataflow launch of mode 3: 2..15, or
+ *                   0 for the default (3).
  * Every setting computes the same output, bit for bit. */
 typedef struct {
   long long chain_pixels;
@@ -434,11 +441,13 @@ typedef struct {
   long long small_pixels;
   int dataflow;
   int task_items[5];
+  int dataflow_level;
 } fllf_tuning;
 
 /* Reads / replaces a plan's launch tuning.  set: chain_pixels >= 0,
- * small_pixels >= 0, ctas_per_sm 0..32, reduce_reverse 0 or 1, dataflow 0,
- * 1 or 2, task_items 0..4096; otherwise FLLF_EINVAL.  A change of task_items
+ * small_pixels >= 0, ctas_per_sm 0..32, reduce_reverse 0 or 1, dataflow 0
+ * to 3, task_items 0..4096, dataflow_level 0 or 2..15; otherwise
+ * FLLF_EINVAL.  A change of task_items
  * rebuilds the plan's task list (allocates its tables anew; synchronises the
  * device). */
 fllf_status fllf_plan_get_tuning(const fllf_plan *plan, fllf_tuning *out);

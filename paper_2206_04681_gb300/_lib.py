@@ -72,7 +72,8 @@ _SIGS = {
                                             ctypes.c_int, _P]),
     "fllf_plan_set_wait_test": (ctypes.c_int, [_P, ctypes.c_longlong, ctypes.c_uint]),
     "fllf_dataflow_check": (ctypes.c_int, [ctypes.POINTER(fllf_params), ctypes.c_int, ctypes.POINTER(ctypes.c_int),
-                                           ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
+                                           ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                                           ctypes.POINTER(ctypes.c_int)]),
     "fllf_run_noalloc": (ctypes.c_int, [ctypes.POINTER(fllf_params), _P, _P, _P]),
     "fllf_server_create": (ctypes.c_int, [ctypes.c_int, ctypes.c_size_t, ctypes.c_int,
                                           ctypes.c_int, ctypes.c_int, ctypes.POINTER(_P)]),
@@ -108,13 +109,15 @@ TASK_KINDS = ("up0", "up", "down_s", "down10", "down0")
 class fllf_tuning(ctypes.Structure):
     _fields_ = [("chain_pixels", ctypes.c_longlong), ("ctas_per_sm", ctypes.c_int * len(STAGES)),
                 ("reduce_reverse", ctypes.c_int), ("small_pixels", ctypes.c_longlong),
-                ("dataflow", ctypes.c_int), ("task_items", ctypes.c_int * len(TASK_KINDS))]
+                ("dataflow", ctypes.c_int), ("task_items", ctypes.c_int * len(TASK_KINDS)),
+                ("dataflow_level", ctypes.c_int)]
 
     def as_dict(self):
         return {"chain_pixels": int(self.chain_pixels), "small_pixels": int(self.small_pixels),
                 "ctas_per_sm": {s: int(self.ctas_per_sm[i]) for i, s in enumerate(STAGES)},
                 "reduce_reverse": int(self.reduce_reverse), "dataflow": int(self.dataflow),
-                "task_items": {s: int(self.task_items[i]) for i, s in enumerate(TASK_KINDS)}}
+                "task_items": {s: int(self.task_items[i]) for i, s in enumerate(TASK_KINDS)},
+                "dataflow_level": int(self.dataflow_level)}
 
 _lib = None
 
@@ -324,14 +327,15 @@ def fllf_batch_run_plans(plans, d_in, d_out, stream=0):
     _check(lib().fllf_batch_run_plans(arr, ins, outs, n, _P(stream)))
 
 
-def fllf_dataflow_check(params, task_items=None, with_d10=True):
+def fllf_dataflow_check(params, task_items=None, with_d10=True, first_level=0):
     """Host-only check of the dataflow task list of the parameter sets;
     returns (tasks, bands) or raises FllfError with the reason."""
     n = len(params)
     arr = (fllf_params * n)(*params)
     ti = (ctypes.c_int * 5)(*task_items) if task_items is not None else None
     nt, nb = ctypes.c_int(), ctypes.c_int()
-    _check(lib().fllf_dataflow_check(arr, n, ti, int(bool(with_d10)), ctypes.byref(nt), ctypes.byref(nb)))
+    _check(lib().fllf_dataflow_check(arr, n, ti, int(bool(with_d10)), int(first_level), ctypes.byref(nt),
+                                     ctypes.byref(nb)))
     return nt.value, nb.value
 
 

@@ -476,7 +476,9 @@ fllf_status fllf_plan_create(const fllf_params* user, int device, fllf_plan** ou
   }
   if (p->levels > 1 && p->method == FLLF_METHOD_FOURIER) {
     // the dataflow launch: task list and argument tables of this image
-    pl->graph = plan_graph_create(pl, pl->tune.grain, pl->tune.dataflow != 2, &e);
+    GraphGrain g = pl->tune.grain;
+    g.lo = pl->tune.dataflow == 3 ? (g.lo >= 2 ? g.lo : 3) : 0;
+    pl->graph = plan_graph_create(pl, g, pl->tune.dataflow != 2, &e);
     if (!pl->graph) {
       free_plan(pl);
       return e == cudaErrorMemoryAllocation ? fail(FLLF_ENOMEM, "dataflow task table allocation failed")

@@ -61,6 +61,7 @@ void build_graph(const std::vector<const fllf_plan*>& plans, int prec, const Gra
                  bool with_d10, GraphBuild* out) {
   *out = GraphBuild{};
   out->with_d10 = with_d10;
+  out->lo = gr.lo;
   const int kcu = prec == FLLF_FP32 ? Smem<8>::up_kc : Smem<4>::up_kc;
   std::vector<Up0Args> a_up0;
   std::vector<UpArgs> a_up;
@@ -92,7 +93,8 @@ void build_graph(const std::vector<const fllf_plan*>& plans, int prec, const Gra
     }
     is[i].up.assign(L, -1);
     is[i].dns.assign(L, -1);
-    {
+    const int lo = gr.lo;   // > 0: only the levels from lo up
+    if (lo == 0) {
       Up0Args u{};
       u.a = pl->d_a;
       u.h0 = p.H;
@@ -123,7 +125,7 @@ void build_graph(const std::vector<const fllf_plan*>& plans, int prec, const Gra
       }
       is[i].up0 = add_stage(s);
     }
-    for (int l = 1; l <= L - 2; ++l) {
+    for (int l = std::max(1, lo); l <= L - 2; ++l) {
       UpArgs u{};
       u.zmap = pl->maps.z_up[l];
       u.gmap = pl->maps.g_up[l];
@@ -151,7 +153,7 @@ void build_graph(const std::vector<const fllf_plan*>& plans, int prec, const Gra
       s.scale = l + 1;
       is[i].up[l] = add_stage(s);
     }
-    for (int l = L - 2; l >= 2; --l) {
+    for (int l = L - 2; l >= std::max(2, lo); --l) {
       DownArgs d{};
       d.zmap = pl->maps.z_cs[l + 1];
       d.emap = pl->maps.e_cs[l + 1];
@@ -180,6 +182,7 @@ void build_graph(const std::vector<const fllf_plan*>& plans, int prec, const Gra
       s.scale = l;
       is[i].dns[l] = add_stage(s);
     }
+    if (lo > 0) continue;   // the level-0 stage runs as its own kernel
     GStage s;
     s.img = i;
     s.ntx = cdiv(p.W + kDnX0, kDnOW);
@@ -248,6 +251,7 @@ void build_graph(const std::vector<const fllf_plan*>& plans, int prec, const Gra
   std::vector<std::vector<int>> band_producers(ncounters);
   std::vector<int> band_stage(ncounters, -1);
   auto add_rows = [&](std::vector<int>& ctrs, int sidx, int pl, int lo, int hi, int h) {
+    if (sidx < 0) return;   // produced by a kernel that ran before this launch
     const GStage& ps = st[sidx];
     lo = std::max(lo, 0);
     hi = std::min(hi, h - 1);
@@ -511,7 +515,7 @@ cudaError_t launch_graph(int prec, const GraphArgs& g, size_t rt_bytes, cudaStre
 using namespace fllf;
 
 extern "C" fllf_status fllf_dataflow_check(const fllf_params* ps, int n, const int* task_items, int with_d10,
-                                           int* ntasks, int* nbands) {
+                                           int first_level, int* ntasks, int* nbands) {
   if (!ps || n < 1 || n > 4096) {
     set_last_error("need 1..4096 parameter sets");
     return FLLF_EINVAL;
@@ -548,6 +552,11 @@ extern "C" fllf_status fllf_dataflow_check(const fllf_params* ps, int n, const i
     g.d10 = task_items[3];
     g.d0 = task_items[4];
   }
+  if (first_level != 0 && (first_level < 2 || first_level > 15)) {
+    set_last_error("first_level must be 0 or 2..15");
+    return FLLF_EINVAL;
+  }
+  g.lo = first_level;
   GraphBuild gb;
   build_graph(ptrs, ps[0].precision, g, n == 1, with_d10 != 0, &gb);
   std::string why;

@@ -101,6 +101,10 @@ bool encode_image_map(CUtensorMap* m, const float* base, int W, int H, int C, ui
 // small-tile combines: at their finest level, halved per level above).
 struct GraphGrain {
   int up0 = 4, up = 8, dns = 4, d10 = 2, d0 = 4;
+  // 0: every stage; lo >= 2: only the REDUCE from level lo up and the
+  // combines from the top down to level lo (the stages below run as their
+  // own kernels, before and after)
+  int lo = 0;
 };
 // The host image of a dataflow launch: argument tables, the ordered task
 // list, the dependency list and the zeroed completion counters.
@@ -112,6 +116,7 @@ struct GraphBuild {
   int ntasks = 0, nbands = 0, nseeds = 0, n_up0 = 0, n_ups = 0, n_dns = 0, n_d10 = 0, n_d0 = 0;
   bool ok = false;
   bool with_d10 = true;      // the fused level-1/level-0 combine is part of the task list
+  int lo = 0;                // first level of the task list (0: every stage)
   Up0Args up0_inline{};      // level-0 argument blocks when they are passed inline (one image)
   Down10Args d10_inline{};
   Down0Args d0_inline{};
@@ -153,7 +158,9 @@ struct Tuning {
   int reverse = 1;
   // 0: the per-stage kernels (default: measured faster); 1: one persistent
   // dataflow launch; 2: the dataflow launch without the fused level-1/level-0
-  // combine, which follows as its own kernel
+  // combine, which follows as its own kernel; 3: the per-stage kernels for
+  // the levels below grain.lo and one dataflow launch for the levels from
+  // grain.lo up
   int dataflow = 0;
   GraphGrain grain;   // work items per task of the dataflow launch
 };

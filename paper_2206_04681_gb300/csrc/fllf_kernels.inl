@@ -1291,11 +1291,15 @@ __device__ __forceinline__ bool stage_down10(Res res, int total, unsigned char* 
             vo[c] = add2(q0, q1);
             ve[c] = fma2(splat(6.f), q1, add2(q0, q2));
           }
+          // unscaled EXPAND sums; the weights 1/16, 1/4, 1/64, 1/16 are powers
+          // of two, so D = f - w U below is the same number whether w U is
+          // rounded first or folded into one fused multiply-add
           float2 U[2][2];
-          U[0][0] = mul2(splat(1.f / 16.f), fma2(splat(6.f), vo[1], add2(vo[0], vo[2])));
-          U[0][1] = mul2(splat(1.f / 4.f), add2(vo[1], vo[2]));
-          U[1][0] = mul2(splat(1.f / 64.f), fma2(splat(6.f), ve[1], add2(ve[0], ve[2])));
-          U[1][1] = mul2(splat(1.f / 16.f), add2(ve[1], ve[2]));
+          U[0][0] = fma2(splat(6.f), vo[1], add2(vo[0], vo[2]));
+          U[0][1] = add2(vo[1], vo[2]);
+          U[1][0] = fma2(splat(6.f), ve[1], add2(ve[0], ve[2]));
+          U[1][1] = add2(ve[1], ve[2]);
+          constexpr float kUw[2][2] = {{-1.f / 16.f, -1.f / 4.f}, {-1.f / 64.f, -1.f / 16.f}};
           const CT* zc = zc1 + kk * kDnCH * kDnCW;
 #pragma unroll
           for (int rr = 0; rr < 2; ++rr) {
@@ -1311,7 +1315,7 @@ __device__ __forceinline__ bool stage_down10(Res res, int total, unsigned char* 
             }
 #pragma unroll
             for (int cc = 0; cc < 2; ++cc) {
-              const float2 d = add2(f[cc], make_float2(-U[rr][cc].x, -U[rr][cc].y));
+              const float2 d = fma2(splat(kUw[rr][cc]), U[rr][cc], f[cc]);
               if constexpr (FAST) {
                 const int s0 = 2 * (ch * kKC + kk);
                 P1[rr][cc].x = fmaf(fast_hat(w1[rr][cc].x, s0 + 1), d.y, fmaf(fast_hat(w1[rr][cc].x, s0), d.x, P1[rr][cc].x));

@@ -353,7 +353,7 @@ cudaError_t enqueue_path(const fllf_params& p, const std::vector<Level>& lv, con
   };
   cudaError_t e;
 
-  if (graph && tn.dataflow && !d_gain) {
+  if (graph && (tn.dataflow == 1 || tn.dataflow == 2) && !d_gain) {
     // one persistent dataflow launch over every stage (the plan's task list;
     // the level-0 argument blocks carry this run's input and output), or
     // over every stage but the fused level-1/level-0 combine, which then
@@ -412,14 +412,24 @@ cudaError_t enqueue_path(const fllf_params& p, const std::vector<Level>& lv, con
   // chained cooperative launch: from the first level (>= 2) whose pixels over
   // all planes fit in chain_px, the REDUCE stages up to the top and the
   // combines back down to c0.
+  //
+  // With dataflow 3, the levels from the plan's task-list level up (>= 2) run
+  // instead as one dataflow launch: the REDUCE from that level to the top and
+  // the combines back down to it, each task starting once the row bands it
+  // reads are complete.
+  const bool flow_small = graph && tn.dataflow == 3 && !d_gain && graph->gb.lo >= 2 && graph->gb.lo <= L - 2;
   const long long chain_px = tn.chain_px;
   int c0 = L - 1;
-  for (int l = 2; l <= L - 2; ++l)
-    if ((long long)lv[l].h * lv[l].w * C <= chain_px) {
-      c0 = l;
-      break;
-    }
-  if (L - 1 - c0 > kChainMax) c0 = L - 1 - kChainMax;
+  if (flow_small) {
+    c0 = graph->gb.lo;
+  } else {
+    for (int l = 2; l <= L - 2; ++l)
+      if ((long long)lv[l].h * lv[l].w * C <= chain_px) {
+        c0 = l;
+        break;
+      }
+    if (L - 1 - c0 > kChainMax) c0 = L - 1 - kChainMax;
+  }
   auto up_args = [&](int l) {
     UpArgs u{};
     u.zmap = maps.z_up[l];
@@ -455,7 +465,13 @@ cudaError_t enqueue_path(const fllf_params& p, const std::vector<Level>& lv, con
     if ((e = launch_up(prec, u, s, tn.cps[FLLF_STAGE_UP])) != cudaSuccess) return e;
     mark(FLLF_STAGE_UP, false);
   }
-  if (c0 <= L - 2) {
+  if (c0 <= L - 2 && flow_small) {
+    mark(FLLF_STAGE_GRAPH, true);
+    if ((e = launch_graph(prec, graph->args, sizeof(unsigned) * graph->gb.rt_words, s, tn.cps[FLLF_STAGE_GRAPH],
+                          false)) != cudaSuccess)
+      return e;
+    mark(FLLF_STAGE_GRAPH, false);
+  } else if (c0 <= L - 2) {
     ChainArgs ca{};
     for (int l = c0; l <= L - 2; ++l) ca.up[ca.n_up++] = up_args(l);
     for (int l = L - 2; l >= c0; --l) {

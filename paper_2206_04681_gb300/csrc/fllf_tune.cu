@@ -97,6 +97,7 @@ void to_public(const Tuning& t, fllf_tuning* o) {
   o->dataflow = t.dataflow;
   const int g[5] = {t.grain.up0, t.grain.up, t.grain.dns, t.grain.d10, t.grain.d0};
   for (int k = 0; k < 5; ++k) o->task_items[k] = g[k];
+  o->dataflow_level = t.grain.lo;
 }
 
 // Task sizes of a public tuning (0: the default of that kind).
@@ -105,24 +106,35 @@ GraphGrain grain_of(const fllf_tuning* t) {
   int* f[5] = {&g.up0, &g.up, &g.dns, &g.d10, &g.d0};
   for (int k = 0; k < 5; ++k)
     if (t->task_items[k] > 0) *f[k] = t->task_items[k];
+  g.lo = t->dataflow_level;
   return g;
 }
 bool same_grain(const GraphGrain& a, const GraphGrain& b) {
-  return a.up0 == b.up0 && a.up == b.up && a.dns == b.dns && a.d10 == b.d10 && a.d0 == b.d0;
+  return a.up0 == b.up0 && a.up == b.up && a.dns == b.dns && a.d10 == b.d10 && a.d0 == b.d0 && a.lo == b.lo;
 }
 
 // Replaces the plan's dataflow task list by one with the given task sizes
 // and fused-combine mode (dataflow 2: the fused level-1/level-0 combine runs
 // as its own kernel).
+// The task list a mode runs: every stage (modes 1, 2), or the levels from
+// grain.lo up (mode 3; level 3 when unset).
+GraphGrain built_grain(const GraphGrain& g, int dataflow) {
+  GraphGrain b = g;
+  b.lo = dataflow == 3 ? (g.lo >= 2 ? g.lo : 3) : 0;
+  return b;
+}
+
 fllf_status regrain(fllf_plan* plan, const GraphGrain& g, int dataflow) {
   const bool with_d10 = dataflow != 2;
-  if (!plan->graph || (same_grain(plan->tune.grain, g) && plan->graph->gb.with_d10 == with_d10)) {
+  const GraphGrain b = built_grain(g, dataflow);
+  if (!plan->graph || (same_grain(plan->tune.grain, g) && plan->graph->gb.with_d10 == with_d10 &&
+                       plan->graph->gb.lo == b.lo)) {
     plan->tune.grain = g;
     return FLLF_OK;
   }
   cudaError_t e = cudaDeviceSynchronize();   // the old tables may be in use
   if (e != cudaSuccess) return tfail(FLLF_ECUDA, std::string("device synchronize: ") + cudaGetErrorString(e));
-  PlanGraph* ng = plan_graph_create(plan, g, with_d10, &e);
+  PlanGraph* ng = plan_graph_create(plan, b, with_d10, &e);
   if (!ng) return tfail(FLLF_ENOMEM, std::string("dataflow task table: ") + cudaGetErrorString(e));
   plan_graph_destroy(plan->graph);
   plan->graph = ng;
@@ -147,7 +159,9 @@ fllf_status fllf_plan_set_tuning(fllf_plan* plan, const fllf_tuning* t) {
   for (int k = 0; k < FLLF_NSTAGE; ++k)
     if (t->ctas_per_sm[k] < 0 || t->ctas_per_sm[k] > 32) return tfail(FLLF_EINVAL, "ctas_per_sm must be 0..32");
   if (t->reduce_reverse != 0 && t->reduce_reverse != 1) return tfail(FLLF_EINVAL, "reduce_reverse must be 0 or 1");
-  if (t->dataflow < 0 || t->dataflow > 2) return tfail(FLLF_EINVAL, "dataflow must be 0, 1 or 2");
+  if (t->dataflow < 0 || t->dataflow > 3) return tfail(FLLF_EINVAL, "dataflow must be 0, 1, 2 or 3");
+  if (t->dataflow_level != 0 && (t->dataflow_level < 2 || t->dataflow_level > 15))
+    return tfail(FLLF_EINVAL, "dataflow_level must be 0 or 2..15");
   for (int k = 0; k < 5; ++k)
     if (t->task_items[k] < 0 || t->task_items[k] > 4096) return tfail(FLLF_EINVAL, "task_items must be 0..4096");
   {
@@ -224,18 +238,22 @@ fllf_status fllf_plan_autotune(fllf_plan* plan, const float* d_in, float* d_out,
   // 0. one dataflow launch, the dataflow launch followed by the fused
   // level-1/level-0 combine, or one launch per stage kind and level
   if (best_graph) {
-    for (int mode = 0; mode <= 2 && ok; ++mode) {
-      if (mode == best.dataflow) continue;
-      Tuning t = best;
-      t.dataflow = mode;
-      if (mode == 0) {
-        ok = consider(t);
-        continue;
+    for (int mode = 0; mode <= 3 && ok; ++mode)
+      for (int lo : {2, 3, 4}) {
+        if (!ok || (mode != 3 && lo != 2)) continue;
+        Tuning t = best;
+        t.dataflow = mode;
+        if (mode == 3) t.grain.lo = lo;
+        if (mode == best.dataflow && (mode != 3 || lo == best.grain.lo)) continue;
+        if (mode == 0) {
+          ok = consider(t);
+          continue;
+        }
+        if (mode == 3 && lo > p.levels - 2) continue;
+        cudaError_t e;
+        PlanGraph* g = plan_graph_create(plan, built_grain(t.grain, mode), mode != 2, &e);
+        ok = g != nullptr && consider_graph(t, g);
       }
-      cudaError_t e;
-      PlanGraph* g = plan_graph_create(plan, t.grain, mode != 2, &e);
-      ok = g != nullptr && consider_graph(t, g);
-    }
   }
   if (ok && best_graph && best.dataflow) {
     // its resident CTAs per SM, then the task size of each stage kind (a
@@ -256,7 +274,7 @@ fllf_status fllf_plan_autotune(fllf_plan* plan, const float* d_in, float* d_out,
         if (*f[k] == v) continue;
         *f[k] = v;
         cudaError_t e;
-        PlanGraph* g = plan_graph_create(plan, t.grain, best.dataflow != 2, &e);
+        PlanGraph* g = plan_graph_create(plan, built_grain(t.grain, best.dataflow), best.dataflow != 2, &e);
         ok = g != nullptr && consider_graph(t, g);
       }
   }

@@ -31,6 +31,11 @@ def test_every_level_count(H, W):
             continue
         for with_d10 in (True, False):
             pkg.fllf_dataflow_check([p], with_d10=with_d10)
+        # the small levels alone (dataflow mode 3)
+        for lo in (2, 3, 4):
+            if lo <= L - 2:
+                nt, nb = pkg.fllf_dataflow_check([p], first_level=lo)
+                assert nt >= nb > 0
 
 
 @pytest.mark.parametrize("items", [[1, 1, 1, 1, 1], [4, 8, 4, 2, 4], [7, 13, 3, 5, 2], [64, 4096, 64, 64, 64]])

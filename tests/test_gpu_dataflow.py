@@ -62,7 +62,7 @@ def test_modes_give_the_same_bits(precision):
         try:
             x = torch.from_numpy(img).cuda()
             ref = _run(plan, x, mode=0)[0]
-            for mode in (1, 2):
+            for mode in (1, 2, 3):
                 for out in _run(plan, x, mode=mode, runs=2):
                     np.testing.assert_array_equal(out, ref, err_msg=f"case {i} mode {mode}")
         finally:
@@ -77,7 +77,7 @@ def test_task_sizes_give_the_same_bits(items):
     try:
         x = torch.from_numpy(img).cuda()
         ref = _run(plan, x, mode=0)[0]
-        for mode in (1, 2):
+        for mode in (1, 2, 3):
             np.testing.assert_array_equal(_run(plan, x, mode=mode, items=items)[0], ref)
     finally:
         pkg.fllf_plan_destroy(plan)
@@ -105,7 +105,7 @@ def test_uhd_frame_same_bits():
     try:
         x = torch.from_numpy(img).cuda()
         ref = _run(plan, x, mode=0)[0]
-        for mode in (1, 2):
+        for mode in (1, 2, 3):
             outs = _run(plan, x, mode=mode, runs=3)
             for out in outs:
                 np.testing.assert_array_equal(out, ref)
