@@ -433,6 +433,12 @@ fllf_status fllf_plan_set_wait_test(fllf_plan *plan, long long wait_cycles, unsi
  *                   default (4, 8, 4, 2, 4).
  *   dataflow_level  first level of the dataflow launch of mode 3: 2..15, or
  *                   0 for the default (3).
+ *   reduce_bands    > 1: the level-0 REDUCE and the level 1 -> 2 REDUCE run
+ *                   in this many row bands (all planes in turn), each band
+ *                   of the level-1 REDUCE launched right after the level-0
+ *                   band that completes its inputs, so that it reads Z_1
+ *                   while it is still in L2; 0 or 1: one launch each
+ *                   (default).  0..256.
  * Every setting computes the same output, bit for bit. */
 typedef struct {
   long long chain_pixels;
@@ -442,12 +448,13 @@ typedef struct {
   int dataflow;
   int task_items[5];
   int dataflow_level;
+  int reduce_bands;
 } fllf_tuning;
 
 /* Reads / replaces a plan's launch tuning.  set: chain_pixels >= 0,
  * small_pixels >= 0, ctas_per_sm 0..32, reduce_reverse 0 or 1, dataflow 0
- * to 3, task_items 0..4096, dataflow_level 0 or 2..15; otherwise
- * FLLF_EINVAL.  A change of task_items
+ * to 3, task_items 0..4096, dataflow_level 0 or 2..15, reduce_bands 0..256;
+ * otherwise FLLF_EINVAL.  A change of task_items
  * rebuilds the plan's task list (allocates its tables anew; synchronises the
  * device). */
 fllf_status fllf_plan_get_tuning(const fllf_plan *plan, fllf_tuning *out);
@@ -463,8 +470,8 @@ fllf_status fllf_plan_set_tuning(fllf_plan *plan, const fllf_tuning *t);
  * resident CTAs per SM and the task sizes of each stage kind; otherwise the
  * chain start (0, 2^15, 2^17, 2^19, 2^21, 2^23 pixels), the small-tile
  * threshold (0 or the pixel count of a combined level >= 2), the resident
- * CTAs per SM of each stage kind (1 .. as many as fit) and the REDUCE
- * order.  A candidate
+ * CTAs per SM of each stage kind (1 .. as many as fit), the REDUCE order and
+ * the REDUCE row bands (1, 2, 4, 6, 8, 12, 16).  A candidate
  * replaces the setting only if it is at least 1% faster.  The plan keeps
  * the best setting; *best_ms (may be NULL) receives its time per run.
  * Synchronises the stream.  reps 1..10000. */

@@ -110,14 +110,14 @@ class fllf_tuning(ctypes.Structure):
     _fields_ = [("chain_pixels", ctypes.c_longlong), ("ctas_per_sm", ctypes.c_int * len(STAGES)),
                 ("reduce_reverse", ctypes.c_int), ("small_pixels", ctypes.c_longlong),
                 ("dataflow", ctypes.c_int), ("task_items", ctypes.c_int * len(TASK_KINDS)),
-                ("dataflow_level", ctypes.c_int)]
+                ("dataflow_level", ctypes.c_int), ("reduce_bands", ctypes.c_int)]
 
     def as_dict(self):
         return {"chain_pixels": int(self.chain_pixels), "small_pixels": int(self.small_pixels),
                 "ctas_per_sm": {s: int(self.ctas_per_sm[i]) for i, s in enumerate(STAGES)},
                 "reduce_reverse": int(self.reduce_reverse), "dataflow": int(self.dataflow),
                 "task_items": {s: int(self.task_items[i]) for i, s in enumerate(TASK_KINDS)},
-                "dataflow_level": int(self.dataflow_level)}
+                "dataflow_level": int(self.dataflow_level), "reduce_bands": int(self.reduce_bands)}
 
 _lib = None
 

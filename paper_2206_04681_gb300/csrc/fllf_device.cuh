@@ -99,6 +99,7 @@ struct Up0Args {
   int use_tma;          // input rows 16-byte aligned (w0 % 4 == 0, aligned base)
   unsigned* fault;      // bounded-wait fault word
   FastArgs fast;        // fast LLF: plane k holds (F_{2k}, F_{2k+1}) unweighted
+  int item0, item1;     // the launch's tiles [item0, item1) (item1 = 0: every tile)
 };
 
 struct UpArgs {
@@ -110,6 +111,7 @@ struct UpArgs {
   int write_g;          // G_{l+1} needed (l+1 <= levels-2)
   int reverse;          // visit the work items last to first (L2 reuse of the level just written)
   unsigned* fault;
+  int item0, item1;     // the launch's work items [item0, item1) (item1 = 0: every item)
 };
 
 // The boxes are those of the 64 x 32 combine (k_down), or of the 32 x 16
@@ -249,6 +251,7 @@ constexpr int kUpIW = 72;                 // staged input columns (box from 2*X1
 static_assert(kUpItems <= kThreads, "REDUCE items exceed the block");
 static_assert(kUpSeg * 32 == kThreads && kUpIR <= 32, "up0 items: one warp per run segment, one lane per row");
 static_assert(kKC * 2 * kUpRun == 32 && kUpRun * kUpVRows <= 32, "up0 vertical pass: one warp per segment");
+static_assert(kKC % 2 == 0, "up0 order recurrence: the two registers' roles repeat every chunk");
 static_assert(2 * kUpVRows + 2 * (kUpVRows + 2) <= kUpCS && 4 * (kUpVRows - 1) + 8 <= kUpCS &&
                   kUpIR <= kUpCS,
               "up0 vertical reads stay in the staged column");

@@ -163,6 +163,9 @@ struct Tuning {
   // grain.lo up
   int dataflow = 0;
   GraphGrain grain;   // work items per task of the dataflow launch
+  // > 1: the level-0 and level 1 -> 2 REDUCE in this many row bands, each
+  // level-1 band right after the level-0 band it reads (its Z_1 from L2)
+  int bands = 1;
 };
 // Resident CTAs per SM of a stage kind's kernel for a storage precision.
 int stage_occupancy(int prec, int kind, bool batched);

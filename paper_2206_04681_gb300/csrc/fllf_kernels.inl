@@ -159,7 +159,12 @@ __device__ __forceinline__ bool stage_up0(Res res, int total, unsigned char* sme
     const int r = tid & 31, s = tid >> 5, rl = min(r, kUpIR - 1);
     float2* hzw = hz + s * (kKC * kUpRun * kUpCS);  // [order][column][fine row]
     float* hgw = hg + s * (kUpRun * kUpCS);          // [column][fine row]
-    float2 zc[kUpIPX], zp[kUpIPX], tc[kUpIPX];
+    // Orders by the recurrence z_{k+1} = 2 cos(w_1 x) z_k - z_{k-1} held in two
+    // registers per pixel that take turns: at an even step of a chunk zb holds
+    // the current order and za the one before, and za <- t zb - za moves to
+    // the next; at an odd step the roles swap.  A chunk has an even number of
+    // steps, so each chunk starts with the same roles (no register copies).
+    float2 zb[kUpIPX], za[kUpIPX], tc[kUpIPX];
     float v[kUpIPX];
     // fast LLF: per pixel, the Gaussian factor of the current sample and its
     // ratio to the next (kept within 85 registers: 3 CTAs per SM)
@@ -177,8 +182,8 @@ __device__ __forceinline__ bool stage_up0(Res res, int total, unsigned char* sme
 #pragma unroll
         for (int j = 0; j < kUpIPX; ++j) {
           const float2 z = cos_sin_turns(a.turns * v[j]);
-          zc[j] = z;
-          zp[j] = make_float2(1.f, 0.f);
+          zb[j] = z;
+          za[j] = make_float2(1.f, 0.f);
           tc[j] = splat(2.f * z.x);
         }
       }
@@ -224,24 +229,25 @@ __device__ __forceinline__ bool stage_up0(Res res, int total, unsigned char* sme
                 const float f1 = s1 ? a.fast.fm1 * d1 * fe[j] : 0.f;
                 fe[j] *= fr[j];
                 fr[j] *= a.fast.k2;
-                zc[j] = make_float2(f0, f1);
+                zb[j] = make_float2(f0, f1);
               }
             } else {
 #pragma unroll
               for (int j = 0; j < kUpIPX; ++j)
-                zc[j] = make_float2(fast_detail(a.fast, v[j], s0), s1 ? fast_detail(a.fast, v[j], s0 + 1) : 0.f);
+                zb[j] = make_float2(fast_detail(a.fast, v[j], s0), s1 ? fast_detail(a.fast, v[j], s0 + 1) : 0.f);
             }
           }
+          // the current order: zb at an even step, za at an odd one (fast LLF: zb)
+          const float2* zk = (FAST || (kk & 1) == 0) ? zb : za;
 #pragma unroll
           for (int q = 0; q < kUpRun; ++q)
             hzw[(kk * kUpRun + q) * kUpCS + r] =
-                tap5(zc[2 * q], zc[2 * q + 1], zc[2 * q + 2], zc[2 * q + 3], zc[2 * q + 4]);
+                tap5(zk[2 * q], zk[2 * q + 1], zk[2 * q + 2], zk[2 * q + 3], zk[2 * q + 4]);
           if constexpr (!FAST) {
 #pragma unroll
             for (int j = 0; j < kUpIPX; ++j) {
-              const float2 zn = fma2(tc[j], zc[j], make_float2(-zp[j].x, -zp[j].y));
-              zp[j] = zc[j];
-              zc[j] = zn;
+              if ((kk & 1) == 0) za[j] = fma2(tc[j], zb[j], make_float2(-za[j].x, -za[j].y));
+              else zb[j] = fma2(tc[j], za[j], make_float2(-zb[j].x, -zb[j].y));
             }
           }
         }
@@ -1426,7 +1432,8 @@ __global__ void __launch_bounds__(kThreads) k_up0(const __grid_constant__ Up0Arg
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem + SM::up0 - 64);
   init_bars(bar);
   Pipe pp{};
-  stage_up0<S, FAST>([&](int g, int& l) { l = g; return &a; }, up0_tiles(a), smem, bar, pp, blockIdx.x,
+  const int hi = a.item1 > 0 ? a.item1 : up0_tiles(a);
+  stage_up0<S, FAST>([&](int g, int& l) { l = g; return &a; }, hi, smem, bar, pp, a.item0 + blockIdx.x,
                gridDim.x);
 }
 
@@ -1438,10 +1445,11 @@ __global__ void __launch_bounds__(kThreads) k_up(const __grid_constant__ UpArgs 
   init_bars(bar);
   Pipe pp{};
   const int n = up_items<S>(a);
+  const int hi = a.item1 > 0 ? a.item1 : n;
   // reversed order: the items of the level the previous kernel wrote last are
   // read first, while they are still in L2
-  stage_up<S>([&](int g, int& l) { l = a.reverse ? n - 1 - g : g; return &a; }, n, smem, bar, pp,
-              blockIdx.x, gridDim.x);
+  stage_up<S>([&](int g, int& l) { l = a.reverse ? n - 1 - g : g; return &a; }, hi, smem, bar, pp,
+              a.item0 + blockIdx.x, gridDim.x);
 }
 
 template <typename S>
@@ -1928,7 +1936,8 @@ using CTS = typename Cplx<FLLF_STORAGE>::T;
 using SMS = Smem<sizeof(CTS)>;
 
 cudaError_t FLLF_LAUNCH_NAME(up0)(const Up0Args& a, cudaStream_t s, int cps) {
-  const int tiles = cdiv(a.dst.w, kUpTW) * cdiv(a.dst.h, kUpTH) * a.planes;
+  const int tiles = (a.item1 > 0 ? a.item1 : cdiv(a.dst.w, kUpTW) * cdiv(a.dst.h, kUpTH) * a.planes) - a.item0;
+  if (tiles <= 0) return cudaSuccess;
   if (a.fast.S > 0) {
     const int grid = persistent_grid<k_up0<FLLF_STORAGE, true>>(SMS::up0, tiles, cps);
     return launch_pdl(k_up0<FLLF_STORAGE, true>, grid, SMS::up0, s, a);
@@ -1938,8 +1947,9 @@ cudaError_t FLLF_LAUNCH_NAME(up0)(const Up0Args& a, cudaStream_t s, int cps) {
 }
 
 cudaError_t FLLF_LAUNCH_NAME(up)(const UpArgs& a, cudaStream_t s, int cps) {
-  const int items = cdiv(a.dst.w, kRsTW) * cdiv(a.dst.h, kRsTH) * a.planes *
-                    (cdiv(a.K, SMS::up_kc) + (a.write_g ? 1 : 0));
+  const int all = cdiv(a.dst.w, kRsTW) * cdiv(a.dst.h, kRsTH) * a.planes * (cdiv(a.K, SMS::up_kc) + (a.write_g ? 1 : 0));
+  const int items = (a.item1 > 0 ? a.item1 : all) - a.item0;
+  if (items <= 0) return cudaSuccess;
   const int grid = persistent_grid<k_up<FLLF_STORAGE>>(SMS::up, items, cps);
   return launch_pdl(k_up<FLLF_STORAGE>, grid, SMS::up, s, a);
 }

@@ -4,6 +4,7 @@
 #include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdlib>
 #include <mutex>
@@ -394,9 +395,60 @@ cudaError_t enqueue_path(const fllf_params& p, const std::vector<Level>& lv, con
   u0.turns = turns;
   u0.fault = fault;
   u0.use_tma = encode_image_map(&u0.imap, d_in, p.W, p.H, C, kUpIW, kUpIR) ? 1 : 0;
-  mark(FLLF_STAGE_UP0, true);
-  if ((e = launch_up0(prec, u0, s, tn.cps[FLLF_STAGE_UP0])) != cudaSuccess) return e;
-  mark(FLLF_STAGE_UP0, false);
+  // The level 1 -> 2 REDUCE exists with >= 3 levels, and the chained or
+  // dataflow launches only start at level 2 or above.
+  const bool banded = tn.bands > 1 && L >= 3;
+  if (!banded) {
+    mark(FLLF_STAGE_UP0, true);
+    if ((e = launch_up0(prec, u0, s, tn.cps[FLLF_STAGE_UP0])) != cudaSuccess) return e;
+    mark(FLLF_STAGE_UP0, false);
+  } else {
+    // Row bands: the level-0 REDUCE of tile rows [r0, r1) of all planes in
+    // turn (plane-major), each followed by the level 1 -> 2 REDUCE of the
+    // level-2 tile rows whose level-1 inputs are then complete.
+    const int ntx0 = cdiv(lv[1].w, kUpTW), nty0 = cdiv(lv[1].h, kUpTH), rows0 = nty0 * C;
+    const int kcu = prec == FLLF_FP32 ? Smem<8>::up_kc : Smem<4>::up_kc;
+    const int ntx2 = cdiv(lv[2].w, kRsTW), nty2 = cdiv(lv[2].h, kRsTH), rows2 = nty2 * C;
+    const int per2 = ntx2 * (cdiv(p.K, kcu) + ((2 <= L - 2) ? 1 : 0));
+    UpArgs u1{};
+    u1.zmap = maps.z_up[1];
+    u1.gmap = maps.g_up[1];
+    u1.src = lv[1];
+    u1.dst = lv[2];
+    u1.planes = C;
+    u1.K = p.K;
+    u1.write_g = (2 <= L - 2) ? 1 : 0;
+    u1.fault = fault;
+    // level-0 REDUCE tile rows (plane-major index) a level-2 tile row reads
+    auto needs = [&](int r2) {
+      const int pl = r2 / nty2, ty2 = r2 % nty2;
+      const int last1 = std::min(lv[1].h - 1, 2 * std::min(kRsTH * ty2 + kRsTH - 1, lv[2].h - 1) + 2);
+      return pl * nty0 + last1 / kUpTH;
+    };
+    const int nb = std::min(tn.bands, rows0);
+    int done2 = 0;
+    for (int c = 0; c < nb; ++c) {
+      const int r0 = (int)((long long)rows0 * c / nb), r1 = (int)((long long)rows0 * (c + 1) / nb);
+      Up0Args ub = u0;
+      ub.item0 = r0 * ntx0;
+      ub.item1 = r1 * ntx0;
+      mark(FLLF_STAGE_UP0, true);
+      if ((e = launch_up0(prec, ub, s, tn.cps[FLLF_STAGE_UP0])) != cudaSuccess) return e;
+      mark(FLLF_STAGE_UP0, false);
+      int ready2 = done2;
+      while (ready2 < rows2 && needs(ready2) < r1) ++ready2;
+      if (c == nb - 1) ready2 = rows2;
+      if (ready2 > done2) {
+        UpArgs ua = u1;
+        ua.item0 = done2 * per2;
+        ua.item1 = ready2 * per2;
+        mark(FLLF_STAGE_UP, true);
+        if ((e = launch_up(prec, ua, s, tn.cps[FLLF_STAGE_UP])) != cudaSuccess) return e;
+        mark(FLLF_STAGE_UP, false);
+        done2 = ready2;
+      }
+    }
+  }
   if (d_gain) {
     // Gaussian pyramid of the gain map, levels 1..L-2 (the levels that combine)
     for (int l = 1; l <= L - 2; ++l) {
@@ -460,6 +512,12 @@ cudaError_t enqueue_path(const fllf_params& p, const std::vector<Level>& lv, con
   };
   for (int l = 1; l <= L - 2 && l < c0; ++l) {
     UpArgs u = up_args(l);
+    if (l == 1 && banded) {
+      // The level 1 -> 2 REDUCE in row bands, each launched right after the
+      // level-0 REDUCE band it reads (below), while that band's Z_1 is still
+      // in L2: nothing to launch here.
+      continue;
+    }
     u.reverse = (l == 1 && tn.reverse) ? 1 : 0;   // the level-0 REDUCE wrote Z_1 first to last
     mark(FLLF_STAGE_UP, true);
     if ((e = launch_up(prec, u, s, tn.cps[FLLF_STAGE_UP])) != cudaSuccess) return e;

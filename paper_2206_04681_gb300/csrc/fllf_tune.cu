@@ -98,6 +98,7 @@ void to_public(const Tuning& t, fllf_tuning* o) {
   const int g[5] = {t.grain.up0, t.grain.up, t.grain.dns, t.grain.d10, t.grain.d0};
   for (int k = 0; k < 5; ++k) o->task_items[k] = g[k];
   o->dataflow_level = t.grain.lo;
+  o->reduce_bands = t.bands;
 }
 
 // Task sizes of a public tuning (0: the default of that kind).
@@ -162,6 +163,7 @@ fllf_status fllf_plan_set_tuning(fllf_plan* plan, const fllf_tuning* t) {
   if (t->dataflow < 0 || t->dataflow > 3) return tfail(FLLF_EINVAL, "dataflow must be 0, 1, 2 or 3");
   if (t->dataflow_level != 0 && (t->dataflow_level < 2 || t->dataflow_level > 15))
     return tfail(FLLF_EINVAL, "dataflow_level must be 0 or 2..15");
+  if (t->reduce_bands < 0 || t->reduce_bands > 256) return tfail(FLLF_EINVAL, "reduce_bands must be 0..256");
   for (int k = 0; k < 5; ++k)
     if (t->task_items[k] < 0 || t->task_items[k] > 4096) return tfail(FLLF_EINVAL, "task_items must be 0..4096");
   {
@@ -170,6 +172,7 @@ fllf_status fllf_plan_set_tuning(fllf_plan* plan, const fllf_tuning* t) {
     if (st != FLLF_OK) return st;
   }
   plan->tune.dataflow = t->dataflow;
+  plan->tune.bands = t->reduce_bands > 1 ? t->reduce_bands : 1;
   plan->tune.chain_px = t->chain_pixels;
   for (int k = 0; k < FLLF_NSTAGE; ++k) plan->tune.cps[k] = t->ctas_per_sm[k];
   plan->tune.reverse = t->reduce_reverse;
@@ -330,6 +333,13 @@ fllf_status fllf_plan_autotune(fllf_plan* plan, const float* d_in, float* d_out,
   if (ok) {
     Tuning t = best;
     t.reverse = 1 - t.reverse;
+    ok = consider(t);
+  }
+  // 5. the level-0 and level 1 -> 2 REDUCE in row bands
+  for (int nb : {1, 2, 4, 6, 8, 12, 16}) {
+    if (!ok || nb == best.bands || p.levels < 3) continue;
+    Tuning t = best;
+    t.bands = nb;
     ok = consider(t);
   }
   plan->tune = best;

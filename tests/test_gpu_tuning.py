@@ -26,8 +26,9 @@ NST = len(pkg.STAGES)
 ALL = 1 << 40   # every combined level >= 2 on the small tiles
 
 
-def _tuning(chain, cps, rev, small=ALL, dataflow=0, items=(0, 0, 0, 0, 0)):
+def _tuning(chain, cps, rev, small=ALL, dataflow=0, items=(0, 0, 0, 0, 0), bands=0):
     t = pkg.fllf_tuning()   # task sizes 0: the defaults
+    t.reduce_bands = bands
     t.chain_pixels = chain
     for i, c in enumerate(cps):
         t.ctas_per_sm[i] = c
@@ -52,7 +53,9 @@ def test_every_launch_setting_gives_the_same_bits(precision):
         for t in (_tuning(1 << 21, [0] * NST, 1), _tuning(0, [0] * NST, 0), _tuning(1 << 23, [1] * NST, 1),
                   _tuning(1 << 15, [2, 1, 1, 1, 1, 2], 0), _tuning(0, [0] * NST, 1, small=0),
                   _tuning(0, [0] * NST, 1, small=1 << 19), _tuning(1 << 17, [0, 0, 0, 0, 0, 1], 1, small=ALL),
-                  _tuning(0, [0] * NST, 1, dataflow=1), _tuning(0, [0] * NST, 1, dataflow=2, items=(2, 16, 1, 1, 1))):
+                  _tuning(0, [0] * NST, 1, dataflow=1), _tuning(0, [0] * NST, 1, dataflow=2, items=(2, 16, 1, 1, 1)),
+                  _tuning(0, [0] * NST, 1, bands=4), _tuning(1 << 21, [0] * NST, 0, bands=7),
+                  _tuning(0, [0] * NST, 1, dataflow=3, bands=3)):
             pkg.fllf_plan_set_tuning(plan, t)
             y = torch.full_like(x, float("nan"))
             pkg.run_tensor(plan, x, y)
