@@ -761,11 +761,21 @@ def run_batch(args):
 
     steps = max(3, min(args.steps, 50))
     warm = max(3, min(args.warmup, 5))
+    # every launch mode of the batch, each timed with every CTA cap at "as many
+    # as fit": 0 one launch per stage kind and level, 1 one dataflow launch,
+    # 2 the dataflow launch and the batched fused level-1/level-0 combine
+    modes = {}
+    for mode in (0, 1, 2):
+        pkg.fllf_batch_set_mode(batch, mode)
+        modes[mode] = timed(lambda: pkg.fllf_batch_run(batch, pin, pout, stream.cuda_stream), steps, warm)
+        pkg.fllf_batch_check(batch)
+    pkg.fllf_batch_set_mode(batch, 0)
     caps = None
     if not args.no_autotune:   # the batch's launch shapes (setup, outside the timed region)
         caps, _ = pkg.fllf_batch_autotune(batch, pin, pout, reps=3, stream=stream.cuda_stream)
         for pl, x, y in zip(plans, pin, pout):
             pkg.fllf_plan_autotune(pl, x, y, reps=3, stream=stream.cuda_stream)
+    mode, task_items = pkg.fllf_batch_get_mode(batch)
     clocks = ClockSampler(0)
     clocks.start()
     ms_batch = timed(lambda: pkg.fllf_batch_run(batch, pin, pout, stream.cuda_stream), steps, warm)
@@ -783,8 +793,14 @@ def run_batch(args):
             "config": {"workload": "batch64_mixed_sizes", "images": len(items), "pixels": pixels,
                        "sides": "log-uniform 256..4096, aspect 0.5..2", "K": "4 or 8",
                        "pyramid_storage": args.precision,
-                       "batch_ctas_per_sm": caps or "default (no autotune)"},
-            "looped_per_image": {"ms_per_step": ms_loop, "value": pixels / ms_loop / 1e3},
+                       "batch_ctas_per_sm": caps or "default (no autotune)",
+                       "batch_mode": mode, "task_items": task_items},
+            "modes_ms_per_step": {"per_stage_levels": modes[0], "dataflow": modes[1],
+                                  "dataflow_then_fused_combine": modes[2],
+                                  "note": "each mode with every CTA cap at 'as many as fit', before "
+                                          "the autotuner"},
+            "looped_per_image": {"ms_per_step": ms_loop, "value": pixels / ms_loop / 1e3,
+                                 "note": "fllf_run per image, each plan autotuned"},
             "speedup_vs_loop": ms_loop / ms_batch, "clocks": clk}
     print(json.dumps(line), flush=True)
     return 0
