@@ -500,6 +500,43 @@ def time_precision(pkg, torch, cfg, precision, frames, steps, warmup, stream, de
     return ms, out0
 
 
+def launch_modes(pkg, torch, cfg, frames, steps, stream, device, precision):
+    """ms per frame of the same plan under each launch mode, all computing the
+    same bits: the per-stage kernels (the default), the dataflow launch of
+    every stage, the dataflow launch followed by the fused level-1/level-0
+    combine, the per-stage kernels with one dataflow launch for the levels
+    from 3 up, and the level-0 / level 1 -> 2 REDUCE in 4 row bands."""
+    p = pkg.make_params(cfg["H"], cfg["W"], cfg["C"], cfg["levels"], cfg["K"], cfg["m"], cfg["sigma_r"],
+                        cfg["T"], precision)
+    plan = pkg.fllf_plan_create(p, device)
+    outs = [torch.empty_like(f) for f in frames]
+    res = {}
+    try:
+        for name, mode, level, bands in (("per_stage", 0, 0, 1), ("dataflow", 1, 0, 1),
+                                          ("dataflow_then_fused_combine", 2, 0, 1),
+                                          ("dataflow_levels_from_3", 3, 3, 1), ("reduce_bands_4", 0, 0, 4)):
+            t = pkg.fllf_plan_get_tuning(plan)
+            t.dataflow, t.dataflow_level, t.reduce_bands = mode, level, bands
+            pkg.fllf_plan_set_tuning(plan, t)
+            with torch.cuda.stream(stream):
+                for i in range(10):
+                    pkg.fllf_run(plan, frames[i % len(frames)].data_ptr(), outs[i % len(frames)].data_ptr(),
+                                 stream.cuda_stream)
+                stream.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                for i in range(steps):
+                    pkg.fllf_run(plan, frames[i % len(frames)].data_ptr(), outs[i % len(frames)].data_ptr(),
+                                 stream.cuda_stream)
+                e1.record(stream)
+                e1.synchronize()
+            res[name] = e0.elapsed_time(e1) / steps
+    finally:
+        pkg.fllf_plan_destroy(plan)
+    res["note"] = "ms per frame, default task sizes and CTA caps, no autotune; every mode gives the same bits"
+    return res
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -683,6 +720,8 @@ def run_ours(args):
             variants[prec] = {"ms_per_step": ms, "value": pixels / (ms * 1e-3) / 1e6}
             gpu_outs[prec] = o
         line["precision_variants"] = variants
+        line["launch_modes"] = launch_modes(pkg, torch, cfg, frames, min(args.steps, 300), stream, device,
+                                            args.precision)
         # fast LLF (Sec. II-D) at the same number of pyramids: S = 2K samples
         S = 2 * cfg["K"]
         fp = pkg.make_fast_params(cfg["H"], cfg["W"], cfg["C"], cfg["levels"], S, cfg["m"], cfg["sigma_r"],
