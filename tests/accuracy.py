@@ -167,7 +167,7 @@ def run_serve(rate=200, seconds=8.0, n_check=32, precision="fp16"):
                              f"seeded random choice of the others"},
         "requests_checked": len(res), "min_psnr_db": min(r[0] for r in res),
         "max_abs": max(r[1] for r in res),
-        "largest_checked": max(f"{reqs[j]['C']}x{reqs[j]['H']}x{reqs[j]['W']}" for j in idx),
+        "largest_checked": "{C}x{H}x{W}".format(**max((reqs[j] for j in idx), key=lambda q: q["C"] * q["H"] * q["W"])),
         "checked": [{"C": reqs[j]["C"], "H": reqs[j]["H"], "W": reqs[j]["W"], "K": reqs[j]["K"],
                      "psnr_db": r[0], "max_abs": r[1]} for j, r in zip(idx, res)],
         "serve": out}), flush=True)
