@@ -191,6 +191,30 @@ fllf_status fllf_run_host(fllf_plan *plan, const float *h_in, float *h_out, void
 fllf_status fllf_submit(fllf_plan *plan, const float *d_in, float *d_out, void *stream,
                         uint64_t *ticket);
 
+/* Asynchronous end-to-end form for host buffers, for a stream of frames.
+ * Enqueues three steps and returns with *ticket for fllf_poll, which
+ * reports the frame done once h_out holds its result:
+ *   1. the copy of h_in into one of the plan's two device staging slots
+ *      (the plan's host-to-device copy stream);
+ *   2. the filtering of the whole frame on `stream` (fllf_run's path, the
+ *      same bits);
+ *   3. the copy of the result to h_out (the device-to-host copy stream).
+ * Successive submits take the slots in turn, so frame n+1's input copy and
+ * frame n-1's output copy overlap frame n's filtering.  A slot is reused
+ * only after its previous frame was filtered (input) and copied back
+ * (output); events order this on the device, without a host wait.
+ *   h_in, h_out: host, H x W x C float32 planar; h_in must stay unchanged
+ *   and h_out unread until the ticket is done.  Pinned memory lets the
+ *   copies run asynchronously; pageable memory works, with copies that
+ *   block the caller.
+ *   Allocates the two slots (4 frame buffers) and the copy streams on the
+ *   first call (kept by the plan; FLLF_ENOMEM if the slots do not fit).
+ *   Like fllf_run, one plan's runs share its scratch: submit them on one
+ *   stream.  A kernel's bounded wait that gave up is reported by fllf_poll
+ *   (FLLF_ETIMEOUT). */
+fllf_status fllf_submit_host(fllf_plan *plan, const float *h_in, float *h_out, void *stream,
+                             uint64_t *ticket);
+
 /* Waits up to timeout_us microseconds (0 = just test, < 0 = up to
  * FLLF_POLL_MAX_US) for a submitted ticket.  FLLF_OK: done (ticket
  * consumed); FLLF_EAGAIN: still running after a zero timeout;

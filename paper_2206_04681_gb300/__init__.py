@@ -15,7 +15,7 @@ from ._lib import (FllfError, fllf_params, make_params, make_fast_params, lib,
                    fllf_batch_get_ctas, fllf_batch_set_ctas, fllf_batch_autotune,
                    fllf_batch_get_mode, fllf_batch_set_mode,
                    fllf_plan_scratch_bytes, fllf_plan_create, fllf_plan_destroy,
-                   fllf_plan_params, fllf_plan_coeffs, fllf_run, fllf_run_host, fllf_submit,
+                   fllf_plan_params, fllf_plan_coeffs, fllf_run, fllf_run_host, fllf_submit, fllf_submit_host,
                    fllf_poll, fllf_batch_create, fllf_batch_destroy, fllf_batch_run,
                    fllf_batch_check, fllf_batch_run_plans, fllf_plan_set_wait_test, fllf_dataflow_check, POLL_MAX_US,
                    fllf_run_noalloc, NOALLOC_SCRATCH_BYTES,

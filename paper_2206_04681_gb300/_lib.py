@@ -63,6 +63,7 @@ _SIGS = {
     "fllf_run": (ctypes.c_int, [_P, _P, _P, _P]),
     "fllf_run_host": (ctypes.c_int, [_P, _P, _P, _P]),
     "fllf_submit": (ctypes.c_int, [_P, _P, _P, _P, ctypes.POINTER(ctypes.c_uint64)]),
+    "fllf_submit_host": (ctypes.c_int, [_P, _P, _P, _P, ctypes.POINTER(ctypes.c_uint64)]),
     "fllf_poll": (ctypes.c_int, [ctypes.c_uint64, ctypes.c_int]),
     "fllf_batch_create": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int, ctypes.POINTER(_P)]),
     "fllf_batch_destroy": (ctypes.c_int, [_P]),
@@ -292,6 +293,12 @@ def fllf_run_host(plan, h_in, h_out, stream=0):
 def fllf_submit(plan, d_in, d_out, stream=0):
     t = ctypes.c_uint64()
     _check(lib().fllf_submit(plan, _P(d_in), _P(d_out), _P(stream), ctypes.byref(t)))
+    return t.value
+
+
+def fllf_submit_host(plan, h_in, h_out, stream=0):
+    t = ctypes.c_uint64()
+    _check(lib().fllf_submit_host(plan, _P(h_in), _P(h_out), _P(stream), ctypes.byref(t)))
     return t.value
 
 

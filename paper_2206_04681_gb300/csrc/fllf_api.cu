@@ -253,10 +253,62 @@ void free_plan(fllf_plan* pl) {
   plan_graph_destroy(pl->graph);
   for (cudaEvent_t e : pl->io_ev)
     if (e) cudaEventDestroy(e);
+  for (HostSlot& h : pl->host_slots) {
+    if (h.d_in) cudaFree(h.d_in);
+    if (h.d_out) cudaFree(h.d_out);
+    for (cudaEvent_t e : {h.copied_in, h.filtered, h.copied_out})
+      if (e) cudaEventDestroy(e);
+  }
   if (pl->io_h2d) cudaStreamDestroy(pl->io_h2d);
   if (pl->io_d2h) cudaStreamDestroy(pl->io_d2h);
   delete pl->timer;
   delete pl;
+}
+
+// The two copy streams of the host-buffer paths (first use).
+fllf_status copy_streams(fllf_plan* pl) {
+  cudaError_t e;
+  if (!pl->io_h2d && (e = cudaStreamCreateWithFlags(&pl->io_h2d, cudaStreamNonBlocking)) != cudaSuccess)
+    return cuda_fail(e, "copy stream creation");
+  if (!pl->io_d2h && (e = cudaStreamCreateWithFlags(&pl->io_d2h, cudaStreamNonBlocking)) != cudaSuccess)
+    return cuda_fail(e, "copy stream creation");
+  return FLLF_OK;
+}
+
+// The staging slots of fllf_submit_host (first use): all or none.
+fllf_status host_slots_setup(fllf_plan* pl) {
+  if (!pl->host_slots.empty()) return FLLF_OK;
+  fllf_status st = copy_streams(pl);
+  if (st != FLLF_OK) return st;
+  const size_t bytes = sizeof(float) * (size_t)pl->p.H * pl->p.W * pl->p.C;
+  std::vector<HostSlot> slots(kHostSlots);
+  auto undo = [&]() {
+    for (HostSlot& h : slots) {
+      if (h.d_in) cudaFree(h.d_in);
+      if (h.d_out) cudaFree(h.d_out);
+      for (cudaEvent_t e : {h.copied_in, h.filtered, h.copied_out})
+        if (e) cudaEventDestroy(e);
+    }
+  };
+  for (HostSlot& h : slots) {
+    if (cudaMalloc(&h.d_in, bytes) != cudaSuccess || cudaMalloc(&h.d_out, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      undo();
+      return fail(FLLF_ENOMEM, "host staging slot allocation failed");
+    }
+    for (cudaEvent_t* e : {&h.copied_in, &h.filtered, &h.copied_out}) {
+      const cudaError_t ce = cudaEventCreateWithFlags(e, cudaEventDisableTiming);
+      if (ce != cudaSuccess) {
+        cudaGetLastError();
+        *e = nullptr;
+        undo();
+        return cuda_fail(ce, "cudaEventCreate");
+      }
+    }
+  }
+  pl->host_slots = std::move(slots);
+  pl->next_slot = 0;
+  return FLLF_OK;
 }
 
 // One-plane views of a plan (levels offset to plane c, maps of one plane) and
@@ -280,11 +332,9 @@ fllf_status plane_pipeline_setup(fllf_plan* pl) {
     if (L > 1 && !build_maps(p1, lvs[c], &maps[c]))
       return fail(FLLF_ECUDA, "TMA tensor map encoding failed (cuTensorMapEncodeTiled)");
   }
+  fllf_status st = copy_streams(pl);
+  if (st != FLLF_OK) return st;
   cudaError_t e;
-  if (!pl->io_h2d && (e = cudaStreamCreateWithFlags(&pl->io_h2d, cudaStreamNonBlocking)) != cudaSuccess)
-    return cuda_fail(e, "copy stream creation");
-  if (!pl->io_d2h && (e = cudaStreamCreateWithFlags(&pl->io_d2h, cudaStreamNonBlocking)) != cudaSuccess)
-    return cuda_fail(e, "copy stream creation");
   while ((int)pl->io_ev.size() < 2 * C) {
     cudaEvent_t ev = nullptr;
     if ((e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming)) != cudaSuccess)
@@ -682,6 +732,50 @@ fllf_status fllf_submit(fllf_plan* plan, const float* d_in, float* d_out, void* 
   cudaError_t e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
   if (e != cudaSuccess) return cuda_fail(e, "cudaEventCreate");
   if ((e = cudaEventRecord(ev, reinterpret_cast<cudaStream_t>(stream))) != cudaSuccess) {
+    cudaEventDestroy(ev);
+    return cuda_fail(e, "cudaEventRecord");
+  }
+  std::lock_guard<std::mutex> lk(g_ticket_mu);
+  *ticket = g_next_ticket++;
+  g_tickets[*ticket] = Ticket{ev, plan->device, plan};
+  return FLLF_OK;
+}
+
+fllf_status fllf_submit_host(fllf_plan* plan, const float* h_in, float* h_out, void* stream,
+                             uint64_t* ticket) {
+  if (!plan) return fail(FLLF_EINVAL, "plan is NULL");
+  if (!h_in || !h_out || !ticket) return fail(FLLF_EINVAL, "input, output or ticket pointer is NULL");
+  DeviceGuard guard(plan->device);
+  if (!guard.ok) return fail(FLLF_ECUDA, "cudaSetDevice failed");
+  fllf_status st = host_slots_setup(plan);
+  if (st != FLLF_OK) return st;
+  HostSlot& h = plan->host_slots[plan->next_slot];
+  const size_t bytes = sizeof(float) * (size_t)plan->p.H * plan->p.W * plan->p.C;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  cudaError_t e;
+  // input: after the slot's previous frame was filtered (its input read)
+  if ((e = cudaStreamWaitEvent(plan->io_h2d, h.filtered, 0)) != cudaSuccess ||
+      (e = cudaMemcpyAsync(h.d_in, h_in, bytes, cudaMemcpyHostToDevice, plan->io_h2d)) != cudaSuccess ||
+      (e = cudaEventRecord(h.copied_in, plan->io_h2d)) != cudaSuccess)
+    return cuda_fail(e, "host-to-device copy");
+  // filtering: after the input arrived and the slot's previous output left
+  if ((e = cudaStreamWaitEvent(s, h.copied_in, 0)) != cudaSuccess ||
+      (e = cudaStreamWaitEvent(s, h.copied_out, 0)) != cudaSuccess)
+    return cuda_fail(e, "stream ordering");
+  if ((e = enqueue_path(plan->p, plan->lv, plan->maps, plan->d_a, plan->d_fault, h.d_in, h.d_out, s, plan->timer,
+                        nullptr, 0.f, &plan->tune, plan->graph)) != cudaSuccess)
+    return cuda_fail(e, "kernel launch");
+  if ((e = cudaEventRecord(h.filtered, s)) != cudaSuccess) return cuda_fail(e, "stream ordering");
+  // output: after the filtering
+  if ((e = cudaStreamWaitEvent(plan->io_d2h, h.filtered, 0)) != cudaSuccess ||
+      (e = cudaMemcpyAsync(h_out, h.d_out, bytes, cudaMemcpyDeviceToHost, plan->io_d2h)) != cudaSuccess ||
+      (e = cudaEventRecord(h.copied_out, plan->io_d2h)) != cudaSuccess)
+    return cuda_fail(e, "device-to-host copy");
+  plan->next_slot = (plan->next_slot + 1) % kHostSlots;
+  cudaEvent_t ev;
+  if ((e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming)) != cudaSuccess)
+    return cuda_fail(e, "cudaEventCreate");
+  if ((e = cudaEventRecord(ev, plan->io_d2h)) != cudaSuccess) {
     cudaEventDestroy(ev);
     return cuda_fail(e, "cudaEventRecord");
   }

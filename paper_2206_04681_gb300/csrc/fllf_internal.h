@@ -220,6 +220,18 @@ cudaError_t launch_batch_stages(const std::vector<StageRec>& stages, const unsig
 
 // A filter plan (opaque to callers): parameters, float32 coefficients on the
 // device, the scratch pyramids, their TMA maps and a device status block.
+namespace fllf {
+// A staging slot of fllf_submit_host: device copies of one frame's input and
+// output, and the events that order the slot's reuse (input copied, frame
+// filtered, output copied back).
+struct HostSlot {
+  float* d_in = nullptr;
+  float* d_out = nullptr;
+  cudaEvent_t copied_in = nullptr, filtered = nullptr, copied_out = nullptr;
+};
+constexpr int kHostSlots = 2;
+}  // namespace fllf
+
 struct fllf_plan {
   fllf_params p{};
   int device = 0;
@@ -243,4 +255,7 @@ struct fllf_plan {
   std::vector<fllf::PathMaps> plane_maps;
   cudaStream_t io_h2d = nullptr, io_d2h = nullptr;
   std::vector<cudaEvent_t> io_ev;     // per plane: input copied, plane filtered
+  // fllf_submit_host: staging slots used in turn (first use)
+  std::vector<fllf::HostSlot> host_slots;
+  int next_slot = 0;
 };

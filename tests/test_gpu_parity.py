@@ -131,6 +131,44 @@ def test_run_host_submit_poll_and_errors():
         pkg.fllf_plan_destroy(plan)
 
 
+def test_submit_host_stream_of_frames():
+    """Frames through the staging slots in turn (two in flight, more frames
+    than slots): each result equals fllf_run's bit for bit, and the first is
+    checked against the oracle."""
+    H, W, C, L, K = 120, 136, 3, 5, 8
+    p = pkg.make_params(H, W, C, L, K, 3.0, 0.2, 2.0)
+    plan = pkg.fllf_plan_create(p, 0)
+    try:
+        imgs = [synth_image(H, W, C, polygons=4 + i, seed=20 + i) for i in range(5)]
+        refs = []
+        for img in imgs:
+            x = torch.from_numpy(img).cuda()
+            y = torch.empty_like(x)
+            pkg.run_tensor(plan, x, y)
+            torch.cuda.synchronize()
+            refs.append(y.cpu().numpy())
+        hins = [torch.from_numpy(img).pin_memory() for img in imgs]
+        houts = [torch.full_like(h, float("nan")).pin_memory() for h in hins]
+        s = torch.cuda.Stream()
+        pending = []
+        for i in range(len(imgs)):
+            if len(pending) == 2:
+                assert pkg.fllf_poll(pending.pop(0), -1) == pkg.FLLF_OK
+            pending.append(pkg.fllf_submit_host(plan, hins[i].data_ptr(), houts[i].data_ptr(), s.cuda_stream))
+        for t in pending:
+            assert pkg.fllf_poll(t, -1) == pkg.FLLF_OK
+        for i in range(len(imgs)):
+            np.testing.assert_array_equal(houts[i].numpy(), refs[i])
+        a = np.array(o.coeffs_quadrature(3.0, 0.2, 2.0, K))
+        ref0 = o.fourier_llf(imgs[0].astype(np.float64), L, a, 2.0)
+        assert float(np.max(np.abs(houts[0].numpy() - ref0))) <= FP32_TOL
+        with pytest.raises(pkg.FllfError) as e:
+            pkg.fllf_submit_host(plan, 0, houts[0].data_ptr(), s.cuda_stream)
+        assert e.value.status == pkg.FLLF_EINVAL
+    finally:
+        pkg.fllf_plan_destroy(plan)
+
+
 @pytest.fixture(scope="module")
 def uhd():
     cfg = UHD_RGB
