@@ -211,7 +211,10 @@ fllf_status fllf_submit(fllf_plan *plan, const float *d_in, float *d_out, void *
  *   first call (kept by the plan; FLLF_ENOMEM if the slots do not fit).
  *   Like fllf_run, one plan's runs share its scratch: submit them on one
  *   stream.  A kernel's bounded wait that gave up is reported by fllf_poll
- *   (FLLF_ETIMEOUT). */
+ *   (FLLF_ETIMEOUT): after each frame a one-thread kernel copies the plan's
+ *   fault word into a host-mapped word (64 per plan, one per pending
+ *   ticket), which fllf_poll reads without a device-to-host copy; tickets
+ *   beyond 64 pending read the device word. */
 fllf_status fllf_submit_host(fllf_plan *plan, const float *h_in, float *h_out, void *stream,
                              uint64_t *ticket);
 

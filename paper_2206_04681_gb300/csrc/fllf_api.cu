@@ -237,6 +237,7 @@ struct Ticket {
   cudaEvent_t ev;
   int device;
   fllf_plan* plan;
+  int snap = -1;  // the plan's snapshot word of the fault word, or -1 (read the device word)
 };
 std::unordered_map<uint64_t, Ticket> g_tickets;
 uint64_t g_next_ticket = 1;
@@ -259,6 +260,7 @@ void free_plan(fllf_plan* pl) {
     for (cudaEvent_t e : {h.copied_in, h.filtered, h.copied_out})
       if (e) cudaEventDestroy(e);
   }
+  if (pl->h_snap) cudaFreeHost(pl->h_snap);
   if (pl->io_h2d) cudaStreamDestroy(pl->io_h2d);
   if (pl->io_d2h) cudaStreamDestroy(pl->io_d2h);
   delete pl->timer;
@@ -306,6 +308,20 @@ fllf_status host_slots_setup(fllf_plan* pl) {
       }
     }
   }
+  unsigned* h = nullptr;
+  unsigned* d = nullptr;
+  if (cudaHostAlloc(reinterpret_cast<void**>(&h), sizeof(unsigned) * kSnapWords, cudaHostAllocMapped) !=
+          cudaSuccess ||
+      cudaHostGetDevicePointer(reinterpret_cast<void**>(&d), h, 0) != cudaSuccess) {
+    cudaGetLastError();
+    if (h) cudaFreeHost(h);
+    undo();
+    return fail(FLLF_ENOMEM, "host-mapped status words allocation failed");
+  }
+  pl->h_snap = h;
+  pl->d_snap = d;
+  pl->snap_free.clear();
+  for (int i = kSnapWords - 1; i >= 0; --i) pl->snap_free.push_back(i);
   pl->host_slots = std::move(slots);
   pl->next_slot = 0;
   return FLLF_OK;
@@ -772,16 +788,39 @@ fllf_status fllf_submit_host(fllf_plan* plan, const float* h_in, float* h_out, v
       (e = cudaEventRecord(h.copied_out, plan->io_d2h)) != cudaSuccess)
     return cuda_fail(e, "device-to-host copy");
   plan->next_slot = (plan->next_slot + 1) % kHostSlots;
+  // the fault word as it stands after this frame, copied into a host-mapped
+  // word that fllf_poll reads (no device-to-host copy behind the frame copies);
+  // without a free word, fllf_poll reads the device word instead
+  int snap = -1;
+  {
+    std::lock_guard<std::mutex> lk(g_ticket_mu);
+    if (!plan->snap_free.empty()) {
+      snap = plan->snap_free.back();
+      plan->snap_free.pop_back();
+    }
+  }
+  auto give_back = [&]() {
+    if (snap < 0) return;
+    std::lock_guard<std::mutex> lk(g_ticket_mu);
+    plan->snap_free.push_back(snap);
+  };
+  if (snap >= 0 && (e = launch_status_snapshot(plan->d_fault, plan->d_snap + snap, plan->io_d2h)) != cudaSuccess) {
+    give_back();
+    return cuda_fail(e, "status snapshot");
+  }
   cudaEvent_t ev;
-  if ((e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming)) != cudaSuccess)
+  if ((e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming)) != cudaSuccess) {
+    give_back();
     return cuda_fail(e, "cudaEventCreate");
+  }
   if ((e = cudaEventRecord(ev, plan->io_d2h)) != cudaSuccess) {
     cudaEventDestroy(ev);
+    give_back();
     return cuda_fail(e, "cudaEventRecord");
   }
   std::lock_guard<std::mutex> lk(g_ticket_mu);
   *ticket = g_next_ticket++;
-  g_tickets[*ticket] = Ticket{ev, plan->device, plan};
+  g_tickets[*ticket] = Ticket{ev, plan->device, plan, snap};
   return FLLF_OK;
 }
 
@@ -798,12 +837,19 @@ fllf_status fllf_poll(uint64_t ticket, int timeout_us) {
   for (;;) {
     cudaError_t e = cudaEventQuery(tk.ev);
     if (e == cudaSuccess || (e != cudaErrorNotReady)) {
+      unsigned snapped = 1;
       {
         std::lock_guard<std::mutex> lk(g_ticket_mu);
         g_tickets.erase(ticket);
+        if (tk.snap >= 0) {
+          snapped = reinterpret_cast<volatile unsigned*>(tk.plan->h_snap)[tk.snap];
+          tk.plan->snap_free.push_back(tk.snap);
+        }
       }
       cudaEventDestroy(tk.ev);
       if (e != cudaSuccess) return cuda_fail(e, "submitted work failed");
+      // a clean snapshot needs no device read; a set one is read and cleared there
+      if (tk.snap >= 0 && snapped == 0) return FLLF_OK;
       return check_fault(tk.plan);
     }
     if (timeout_us == 0) return FLLF_EAGAIN;

@@ -230,6 +230,7 @@ struct HostSlot {
   cudaEvent_t copied_in = nullptr, filtered = nullptr, copied_out = nullptr;
 };
 constexpr int kHostSlots = 2;
+constexpr int kSnapWords = 64;  // host-mapped fault-word snapshots, one per pending host-buffer ticket
 }  // namespace fllf
 
 struct fllf_plan {
@@ -258,4 +259,9 @@ struct fllf_plan {
   // fllf_submit_host: staging slots used in turn (first use)
   std::vector<fllf::HostSlot> host_slots;
   int next_slot = 0;
+  // fault-word snapshots of pending fllf_submit_host tickets: pinned,
+  // device-mapped words and the free ones (guarded by the ticket lock)
+  unsigned* h_snap = nullptr;
+  unsigned* d_snap = nullptr;
+  std::vector<int> snap_free;
 };

@@ -1883,6 +1883,12 @@ __global__ void __launch_bounds__(kThreads) k_luma_apply(const float* __restrict
     for (int c = 0; c < 3; ++c) out[c * n + i] = __ldg(rgb + c * n + i) + d;
   }
 }
+
+// Copies a status block's fault word into a host-mapped word, so that a
+// frame's completion can be checked on the host without a device-to-host copy.
+__global__ void k_status_snapshot(const unsigned* __restrict__ status, unsigned* __restrict__ host_word) {
+  *host_word = *reinterpret_cast<const volatile unsigned*>(status);
+}
 #endif
 
 // Persistent grid: at most (resident CTAs per SM) x (SMs) CTAs, or `cps`
@@ -2053,6 +2059,10 @@ cudaError_t launch_luma_apply(const float* rgb, const float* y, const float* yf,
                               cudaStream_t s) {
   const int grid = (int)std::min<long long>(cdiv((int)std::min<long long>(n, 1LL << 30), kThreads), 152 * 8);
   k_luma_apply<<<grid, kThreads, 0, s>>>(rgb, y, yf, out, n);
+  return cudaGetLastError();
+}
+cudaError_t launch_status_snapshot(const unsigned* status, unsigned* host_word, cudaStream_t s) {
+  k_status_snapshot<<<1, 1, 0, s>>>(status, host_word);
   return cudaGetLastError();
 }
 cudaError_t launch_map_reduce(const float* src, int sh, int sw, int spitch, float* dst, int dh, int dw,

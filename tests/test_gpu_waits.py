@@ -89,6 +89,49 @@ def test_timeout_through_submit_and_poll():
         pkg.fllf_plan_destroy(plan)
 
 
+def test_timeout_through_submit_host():
+    """Streamed host-buffer frames: the poll reads the fault word from its
+    host-mapped snapshot, reports the timeout, and the next frame is clean."""
+    img = synth_image(H, W, C, polygons=5, seed=73)
+    plan = _chained_plan()
+    try:
+        ref = _host_run(plan, img)
+        hin = torch.from_numpy(img).pin_memory()
+        hout = torch.full_like(hin, float("nan")).pin_memory()
+        pkg.fllf_plan_set_wait_test(plan, 100_000, 1)
+        t = pkg.fllf_submit_host(plan, hin.data_ptr(), hout.data_ptr(), 0)
+        assert pkg.fllf_poll(t, 10_000_000) == pkg.FLLF_ETIMEOUT
+        t = pkg.fllf_submit_host(plan, hin.data_ptr(), hout.data_ptr(), 0)
+        assert pkg.fllf_poll(t, 10_000_000) == pkg.FLLF_OK
+        np.testing.assert_array_equal(hout.numpy(), ref)
+    finally:
+        pkg.fllf_plan_destroy(plan)
+
+
+def test_submit_host_more_pending_tickets_than_snapshot_words():
+    """70 frames submitted before any poll: the first 64 tickets take the
+    plan's host-mapped snapshot words, the rest read the device word; every
+    poll succeeds and every output is the synchronous run's."""
+    h, w = 40, 56
+    img = synth_image(h, w, 1, polygons=3, seed=74)
+    plan = pkg.fllf_plan_create(pkg.make_params(h, w, 1, 4, 4, 3.0, 0.2, 2.0, "fp32"), 0)
+    try:
+        ref = _host_run(plan, img)
+        hin = torch.from_numpy(img).pin_memory()
+        outs = [torch.full_like(hin, float("nan")).pin_memory() for _ in range(70)]
+        tickets = [pkg.fllf_submit_host(plan, hin.data_ptr(), o.data_ptr(), 0) for o in outs]
+        for t in tickets:
+            assert pkg.fllf_poll(t, 10_000_000) == pkg.FLLF_OK
+        for o in outs:
+            np.testing.assert_array_equal(o.numpy(), ref)
+        # the words came back: another round takes them again
+        tickets = [pkg.fllf_submit_host(plan, hin.data_ptr(), o.data_ptr(), 0) for o in outs[:8]]
+        for t in tickets:
+            assert pkg.fllf_poll(t, 10_000_000) == pkg.FLLF_OK
+    finally:
+        pkg.fllf_plan_destroy(plan)
+
+
 def test_wait_hook_rejects_a_negative_limit():
     plan = _chained_plan()
     try:
