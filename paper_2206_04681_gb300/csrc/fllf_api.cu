@@ -251,6 +251,7 @@ void free_plan(fllf_plan* pl) {
   if (pl->d_io_out) cudaFree(pl->d_io_out);
   if (pl->d_mpyr) cudaFree(pl->d_mpyr);
   if (pl->d_luma) cudaFree(pl->d_luma);
+  if (pl->d_stage) cudaFree(pl->d_stage);
   plan_graph_destroy(pl->graph);
   for (cudaEvent_t e : pl->io_ev)
     if (e) cudaEventDestroy(e);
@@ -536,6 +537,17 @@ fllf_status fllf_plan_create(const fllf_params* user, int device, fllf_plan** ou
     free_plan(pl);
     return cuda_fail(e, "fault word clear");
   }
+  if (p->levels > 1 && (p->W % 4) != 0) {
+    // rows of W floats do not start on 16-byte boundaries: the input is
+    // staged at a padded pitch for the level-0 TMA loads
+    const size_t bytes = sizeof(float) * (size_t)staged_pitch(p->W) * p->H * p->C;
+    if ((e = cudaMalloc(&pl->d_stage, bytes)) != cudaSuccess) {
+      cudaGetLastError();
+      pl->d_stage = nullptr;
+      free_plan(pl);
+      return fail(FLLF_ENOMEM, "input staging buffer allocation failed");
+    }
+  }
   if (p->levels > 1 && !build_maps(*p, pl->lv, &pl->maps)) {
     free_plan(pl);
     return fail(FLLF_ECUDA, "TMA tensor map encoding failed (cuTensorMapEncodeTiled)");
@@ -586,7 +598,7 @@ fllf_status fllf_run(fllf_plan* plan, const float* d_in, float* d_out, void* str
   if (!guard.ok) return fail(FLLF_ECUDA, "cudaSetDevice failed");
   cudaError_t e = enqueue_path(plan->p, plan->lv, plan->maps, plan->d_a, plan->d_fault, d_in, d_out,
                                reinterpret_cast<cudaStream_t>(stream), plan->timer, nullptr, 0.f,
-                               &plan->tune, plan->graph);
+                               &plan->tune, plan->graph, plan->d_stage);
   if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
   return FLLF_OK;
 }
@@ -629,7 +641,7 @@ fllf_status fllf_run_adaptive(fllf_plan* plan, const float* d_in, const float* d
     lv[l].M = reinterpret_cast<const float*>(reinterpret_cast<unsigned char*>(plan->d_mpyr) + off[l]);
   cudaError_t e = enqueue_path(p, lv, plan->maps, plan->d_a, plan->d_fault, d_in, d_out,
                                reinterpret_cast<cudaStream_t>(stream), plan->timer, d_gain,
-                               (float)(1.0 / (p.m - 1.0)), &plan->tune);
+                               (float)(1.0 / (p.m - 1.0)), &plan->tune, nullptr, plan->d_stage);
   if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
   return FLLF_OK;
 }
@@ -660,7 +672,7 @@ fllf_status fllf_run_luma(fllf_plan* plan, const float* d_rgb_in, float* d_rgb_o
   cudaError_t e;
   if ((e = launch_luma(d_rgb_in, y, (long long)n, kLuma, s)) != cudaSuccess) return cuda_fail(e, "luma");
   if ((e = enqueue_path(p, plan->lv, plan->maps, plan->d_a, plan->d_fault, y, yf, s, plan->timer,
-                        nullptr, 0.f, &plan->tune)) != cudaSuccess)
+                        nullptr, 0.f, &plan->tune, nullptr, plan->d_stage)) != cudaSuccess)
     return cuda_fail(e, "kernel launch");
   if ((e = launch_luma_apply(d_rgb_in, y, yf, d_rgb_out, (long long)n, s)) != cudaSuccess)
     return cuda_fail(e, "luma apply");
@@ -694,7 +706,8 @@ fllf_status fllf_run_host(fllf_plan* plan, const float* h_in, float* h_out, void
     if ((e = cudaMemcpyAsync(plan->d_io_in, h_in, bytes, cudaMemcpyHostToDevice, s)) != cudaSuccess)
       return cuda_fail(e, "host-to-device copy");
     if ((e = enqueue_path(plan->p, plan->lv, plan->maps, plan->d_a, plan->d_fault, plan->d_io_in,
-                          plan->d_io_out, s, plan->timer, nullptr, 0.f, &plan->tune, plan->graph)) != cudaSuccess)
+                          plan->d_io_out, s, plan->timer, nullptr, 0.f, &plan->tune, plan->graph,
+                          plan->d_stage)) != cudaSuccess)
       return cuda_fail(e, "kernel launch");
     if ((e = cudaMemcpyAsync(h_out, plan->d_io_out, bytes, cudaMemcpyDeviceToHost, s)) != cudaSuccess)
       return cuda_fail(e, "device-to-host copy");
@@ -724,7 +737,9 @@ fllf_status fllf_run_host(fllf_plan* plan, const float* h_in, float* h_out, void
     if ((e = cudaStreamWaitEvent(s, ev[2 * c], 0)) != cudaSuccess) return cuda_fail(e, "stream ordering");
     if ((e = enqueue_path(p1, plan->plane_lv[c], plan->plane_maps[c], plan->d_a, plan->d_fault,
                           plan->d_io_in + c * pn, plan->d_io_out + c * pn, s, plan->timer, nullptr, 0.f,
-                          &plan->tune)) != cudaSuccess)
+                          &plan->tune, nullptr,
+                          plan->d_stage ? plan->d_stage + (size_t)c * staged_pitch(p1.W) * p1.H : nullptr)) !=
+        cudaSuccess)
       return cuda_fail(e, "kernel launch");
     if ((e = cudaEventRecord(ev[2 * c + 1], s)) != cudaSuccess ||
         (e = cudaStreamWaitEvent(plan->io_d2h, ev[2 * c + 1], 0)) != cudaSuccess)
@@ -779,7 +794,7 @@ fllf_status fllf_submit_host(fllf_plan* plan, const float* h_in, float* h_out, v
       (e = cudaStreamWaitEvent(s, h.copied_out, 0)) != cudaSuccess)
     return cuda_fail(e, "stream ordering");
   if ((e = enqueue_path(plan->p, plan->lv, plan->maps, plan->d_a, plan->d_fault, h.d_in, h.d_out, s, plan->timer,
-                        nullptr, 0.f, &plan->tune, plan->graph)) != cudaSuccess)
+                        nullptr, 0.f, &plan->tune, plan->graph, plan->d_stage)) != cudaSuccess)
     return cuda_fail(e, "kernel launch");
   if ((e = cudaEventRecord(h.filtered, s)) != cudaSuccess) return cuda_fail(e, "stream ordering");
   // output: after the filtering

@@ -94,7 +94,14 @@ bool build_maps(const fllf_params& p, const std::vector<Level>& lv, PathMaps* m)
 // Tiled map of a planar C x H x W float image with the given box (zero fill
 // outside); false when the image does not allow one (W % 4 != 0, a base not
 // 16-byte aligned) or the encoding fails.
-bool encode_image_map(CUtensorMap* m, const float* base, int W, int H, int C, uint32_t box_w, uint32_t box_h);
+// Level-0 image map (x = column, y = row, z = plane) with a row pitch of
+// `pitch` floats (0: W).  False when the rows do not start on 16-byte
+// boundaries (pitch % 4 != 0 or a misaligned base): the kernels then read
+// the input with plain loads.
+bool encode_image_map(CUtensorMap* m, const float* base, int W, int H, int C, uint32_t box_w, uint32_t box_h,
+                      int pitch = 0);
+// Row pitch (floats) of a plan's input staging copy: W rounded up to 4.
+inline int staged_pitch(int W) { return (W + 3) & ~3; }
 
 // ---- dataflow launch (one persistent grid over every stage) -------------------
 // Work items per task of each stage kind (the REDUCE at levels >= 1 and the
@@ -180,10 +187,14 @@ void plan_graph_destroy(PlanGraph* g);
 // gain map d_gain (H x W, pitch W) the levels' M pointers must hold its
 // pyramid buffers (levels 1..levels-2); the path builds the pyramid and
 // scales each level's Fourier term by (m_{l,p} - 1) * mscale.
+// With d_stage (C x H x staged_pitch(W) floats), an input whose rows are not
+// 16-byte aligned is first copied there at the padded pitch, so that the
+// level-0 kernels load it by TMA.
 cudaError_t enqueue_path(const fllf_params& p, const std::vector<Level>& lv, const PathMaps& maps,
                          const float* d_a, unsigned* fault, const float* d_in, float* d_out,
                          cudaStream_t s, StageHook* hook = nullptr, const float* d_gain = nullptr,
-                         float mscale = 0.f, const Tuning* tune = nullptr, const PlanGraph* graph = nullptr);
+                         float mscale = 0.f, const Tuning* tune = nullptr, const PlanGraph* graph = nullptr,
+                         float* d_stage = nullptr);
 
 // ---- batched argument tables (shared by batches and the server) ---------------
 // kStageDown10 (the fused level-1/level-0 combine of the images with >= 3
@@ -248,6 +259,7 @@ struct fllf_plan {
   unsigned* d_fault = nullptr;        // device status block (fault word, grid-barrier words)
   float* d_mpyr = nullptr;            // gain-map pyramid of pixel-adaptive runs (first use)
   float* d_luma = nullptr;            // Y and filtered Y of colour-by-luma runs (first use)
+  float* d_stage = nullptr;           // input staged at a 16-byte row pitch (W % 4 != 0 only)
   fllf::Tuning tune;                  // launch tuning (fllf_plan_set_tuning / fllf_plan_autotune)
   fllf::PlanGraph* graph = nullptr;   // the plan's dataflow launch (Fourier LLF, >= 2 levels)
   // Host-buffer runs of C >= 2 planes: one-plane views of the scratch (levels

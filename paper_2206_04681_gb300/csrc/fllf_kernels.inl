@@ -1884,6 +1884,30 @@ __global__ void __launch_bounds__(kThreads) k_luma_apply(const float* __restrict
   }
 }
 
+// Input staging: dense rows of W floats to rows of `pitch` floats (pitch a
+// multiple of 4, so every row starts on a 16-byte boundary).  A CTA copies a
+// row at a time, four loads in flight per thread.
+__global__ void __launch_bounds__(kThreads) k_pad_rows(const float* __restrict__ src, int W, long long rows,
+                                                       float* __restrict__ dst, int pitch) {
+  for (long long r = blockIdx.x; r < rows; r += gridDim.x) {
+    const float* sr = src + r * W;
+    float* dr = dst + r * pitch;
+    for (int c0 = threadIdx.x; c0 < W; c0 += 4 * kThreads) {
+      float v[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int c = c0 + u * kThreads;
+        v[u] = c < W ? __ldg(sr + c) : 0.f;
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int c = c0 + u * kThreads;
+        if (c < W) dr[c] = v[u];
+      }
+    }
+  }
+}
+
 // Copies a status block's fault word into a host-mapped word, so that a
 // frame's completion can be checked on the host without a device-to-host copy.
 __global__ void k_status_snapshot(const unsigned* __restrict__ status, unsigned* __restrict__ host_word) {
@@ -2059,6 +2083,12 @@ cudaError_t launch_luma_apply(const float* rgb, const float* y, const float* yf,
                               cudaStream_t s) {
   const int grid = (int)std::min<long long>(cdiv((int)std::min<long long>(n, 1LL << 30), kThreads), 152 * 8);
   k_luma_apply<<<grid, kThreads, 0, s>>>(rgb, y, yf, out, n);
+  return cudaGetLastError();
+}
+cudaError_t launch_pad_rows(const float* src, int W, long long rows, float* dst, int pitch, cudaStream_t s) {
+  if (rows <= 0 || W <= 0) return cudaSuccess;
+  const int grid = (int)std::min<long long>(rows, 152 * 8);
+  k_pad_rows<<<grid, kThreads, 0, s>>>(src, W, rows, dst, pitch);
   return cudaGetLastError();
 }
 cudaError_t launch_status_snapshot(const unsigned* status, unsigned* host_word, cudaStream_t s) {

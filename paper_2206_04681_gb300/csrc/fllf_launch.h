@@ -32,6 +32,8 @@ cudaError_t launch_map_reduce(const float* src, int sh, int sw, int spitch, floa
 cudaError_t launch_luma(const float* rgb, float* y, long long n, const float w[3], cudaStream_t s);
 cudaError_t launch_luma_apply(const float* rgb, const float* y, const float* yf, float* out, long long n,
                               cudaStream_t s);
+// Copies `rows` dense rows of W floats to a row pitch of `pitch` floats.
+cudaError_t launch_pad_rows(const float* src, int W, long long rows, float* dst, int pitch, cudaStream_t s);
 // Copies status[0] (the fault word) into a host-mapped word (one thread).
 cudaError_t launch_status_snapshot(const unsigned* status, unsigned* host_word, cudaStream_t s);
 FLLF_DECLARE_LAUNCHERS(f32)

@@ -124,9 +124,12 @@ int stage_occupancy(int prec, int kind, bool batched) {
   }
 }
 
-bool encode_image_map(CUtensorMap* m, const float* base, int W, int H, int C, uint32_t box_w, uint32_t box_h) {
-  if ((W % 4) != 0 || (reinterpret_cast<uintptr_t>(base) & 15) != 0) return false;
-  return encode3(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, base, W, H, C, 4ull * W, 4ull * W * H, box_w, box_h, 1);
+bool encode_image_map(CUtensorMap* m, const float* base, int W, int H, int C, uint32_t box_w, uint32_t box_h,
+                      int pitch) {
+  if (pitch <= 0) pitch = W;
+  if ((pitch % 4) != 0 || pitch < W || (reinterpret_cast<uintptr_t>(base) & 15) != 0) return false;
+  return encode3(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, base, W, H, C, 4ull * pitch, 4ull * pitch * H, box_w,
+                 box_h, 1);
 }
 
 bool build_maps(const fllf_params& p, const std::vector<Level>& lv, PathMaps* m) {
@@ -222,7 +225,7 @@ namespace {
 // fused level-0 tiles (the level-0 combine alone with 2 levels).
 cudaError_t enqueue_fast(const fllf_params& p, const std::vector<Level>& lv, const PathMaps& maps,
                          const float* d_a, unsigned* fault, const float* d_in, float* d_out, cudaStream_t s,
-                         StageHook* hook, const Tuning& tn) {
+                         StageHook* hook, const Tuning& tn, const float* tin, int tpitch) {
   const int L = p.levels, C = p.C, prec = p.precision;
   FastArgs fa{};
   fa.S = p.samples;
@@ -255,7 +258,7 @@ cudaError_t enqueue_fast(const fllf_params& p, const std::vector<Level>& lv, con
   u0.K = p.K;
   u0.fault = fault;
   u0.fast = fa;
-  u0.use_tma = encode_image_map(&u0.imap, d_in, p.W, p.H, C, kUpIW, kUpIR) ? 1 : 0;
+  u0.use_tma = encode_image_map(&u0.imap, tin, p.W, p.H, C, kUpIW, kUpIR, tpitch) ? 1 : 0;
   mark(FLLF_STAGE_UP0, true);
   if ((e = launch_up0(prec, u0, s, tn.cps[FLLF_STAGE_UP0])) != cudaSuccess) return e;
   mark(FLLF_STAGE_UP0, false);
@@ -309,7 +312,7 @@ cudaError_t enqueue_fast(const fllf_params& p, const std::vector<Level>& lv, con
     d.l2 = lv[2];
     d.K = p.K;
     d.has_e2 = (L >= 4) ? 1 : 0;
-    d.use_tma = (u0.use_tma && encode_image_map(&d.imap, d_in, p.W, p.H, C, kD0IW, kDnOH)) ? 1 : 0;
+    d.use_tma = (u0.use_tma && encode_image_map(&d.imap, tin, p.W, p.H, C, kD0IW, kDnOH, tpitch)) ? 1 : 0;
     d.fault = fault;
     d.fast = fa;
     if ((e = launch_down10(prec, d, s, tn.cps[FLLF_STAGE_DOWN0])) != cudaSuccess) return e;
@@ -338,7 +341,7 @@ cudaError_t enqueue_fast(const fllf_params& p, const std::vector<Level>& lv, con
 cudaError_t enqueue_path(const fllf_params& p, const std::vector<Level>& lv, const PathMaps& maps,
                          const float* d_a, unsigned* fault, const float* d_in, float* d_out,
                          cudaStream_t s, StageHook* hook, const float* d_gain, float mscale,
-                         const Tuning* tune, const PlanGraph* graph) {
+                         const Tuning* tune, const PlanGraph* graph, float* d_stage) {
   static const Tuning kDefault{};
   const Tuning& tn = tune ? *tune : kDefault;
   const int L = p.levels, C = p.C, prec = p.precision;
@@ -348,11 +351,24 @@ cudaError_t enqueue_path(const fllf_params& p, const std::vector<Level>& lv, con
     return cudaMemcpyAsync(d_out, d_in, sizeof(float) * (size_t)p.H * p.W * C,
                            cudaMemcpyDeviceToDevice, s);
   }
-  if (p.method == FLLF_METHOD_FAST) return enqueue_fast(p, lv, maps, d_a, fault, d_in, d_out, s, hook, tn);
   auto mark = [&](int st, bool b) {
     if (hook) hook->mark(st, b, s);
   };
   cudaError_t e;
+  // The level-0 kernels load the input by TMA when its rows start on 16-byte
+  // boundaries; otherwise a staging buffer takes a copy at a padded pitch
+  // (one pass, counted with the level-0 REDUCE), else they use plain loads.
+  const float* tin = d_in;
+  int tpitch = p.W;
+  if (d_stage && ((p.W % 4) != 0 || (reinterpret_cast<uintptr_t>(d_in) & 15) != 0)) {
+    tpitch = staged_pitch(p.W);
+    mark(FLLF_STAGE_UP0, true);
+    if ((e = launch_pad_rows(d_in, p.W, (long long)p.H * C, d_stage, tpitch, s)) != cudaSuccess) return e;
+    mark(FLLF_STAGE_UP0, false);
+    tin = d_stage;
+  }
+  if (p.method == FLLF_METHOD_FAST)
+    return enqueue_fast(p, lv, maps, d_a, fault, d_in, d_out, s, hook, tn, tin, tpitch);
 
   if (graph && (tn.dataflow == 1 || tn.dataflow == 2) && !d_gain) {
     // one persistent dataflow launch over every stage (the plan's task list;
@@ -361,11 +377,11 @@ cudaError_t enqueue_path(const fllf_params& p, const std::vector<Level>& lv, con
     // follows as its own kernel
     GraphArgs g = graph->args;
     g.up0.I = d_in;
-    g.up0.use_tma = encode_image_map(&g.up0.imap, d_in, p.W, p.H, C, kUpIW, kUpIR) ? 1 : 0;
+    g.up0.use_tma = encode_image_map(&g.up0.imap, tin, p.W, p.H, C, kUpIW, kUpIR, tpitch) ? 1 : 0;
     if (L >= 3) {
       g.d10.I = d_in;
       g.d10.O = d_out;
-      g.d10.use_tma = (g.up0.use_tma && encode_image_map(&g.d10.imap, d_in, p.W, p.H, C, kD0IW, kDnOH)) ? 1 : 0;
+      g.d10.use_tma = (g.up0.use_tma && encode_image_map(&g.d10.imap, tin, p.W, p.H, C, kD0IW, kDnOH, tpitch)) ? 1 : 0;
     } else {
       g.d0.I = d_in;
       g.d0.O = d_out;
@@ -394,7 +410,7 @@ cudaError_t enqueue_path(const fllf_params& p, const std::vector<Level>& lv, con
   u0.K = p.K;
   u0.turns = turns;
   u0.fault = fault;
-  u0.use_tma = encode_image_map(&u0.imap, d_in, p.W, p.H, C, kUpIW, kUpIR) ? 1 : 0;
+  u0.use_tma = encode_image_map(&u0.imap, tin, p.W, p.H, C, kUpIW, kUpIR, tpitch) ? 1 : 0;
   // The level 1 -> 2 REDUCE exists with >= 3 levels, and the chained or
   // dataflow launches only start at level 2 or above.
   const bool banded = tn.bands > 1 && L >= 3;
@@ -587,7 +603,7 @@ cudaError_t enqueue_path(const fllf_params& p, const std::vector<Level>& lv, con
     d.has_e2 = (L >= 4) ? 1 : 0;
     d.M0 = d_gain;
     d.mscale = mscale;
-    d.use_tma = (u0.use_tma && encode_image_map(&d.imap, d_in, p.W, p.H, C, kD0IW, kDnOH)) ? 1 : 0;
+    d.use_tma = (u0.use_tma && encode_image_map(&d.imap, tin, p.W, p.H, C, kD0IW, kDnOH, tpitch)) ? 1 : 0;
     d.fault = fault;
     mark(FLLF_STAGE_DOWN0, true);
     if ((e = launch_down10(prec, d, s, tn.cps[FLLF_STAGE_DOWN0])) != cudaSuccess) return e;

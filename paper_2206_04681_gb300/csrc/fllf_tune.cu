@@ -199,7 +199,7 @@ fllf_status fllf_plan_autotune(fllf_plan* plan, const float* d_in, float* d_out,
     return time_calls(
         [&] {
           return enqueue_path(p, plan->lv, plan->maps, plan->d_a, plan->d_fault, d_in, d_out, s, nullptr,
-                              nullptr, 0.f, &t, g);
+                              nullptr, 0.f, &t, g, plan->d_stage);
         },
         reps, s, flush, fbytes);
   };
