@@ -96,6 +96,34 @@ void build_batch_blob(const std::vector<const fllf_plan*>& plans, int prec, Batc
   const std::vector<unsigned> status(64, 0u);
   out->status_off = push(blob, status.data(), status.size(), 256);
   {
+    // input staging of the images whose plans stage their input (rows not
+    // 16-byte aligned); the sources are set per run
+    out->stage.assign(plans.size(), nullptr);
+    out->pad_img.clear();
+    out->pad_off = out->pad_prefix_off = 0;
+    out->pad_total = 0;
+    std::vector<PadRow> rows;
+    std::vector<int> pre(1, 0);
+    for (int i = 0; i < (int)plans.size(); ++i) {
+      const fllf_plan* pl = plans[i];
+      if (pl->p.levels < 2 || !pl->d_stage) continue;
+      out->stage[i] = pl->d_stage;
+      out->pad_img.push_back(i);
+      PadRow r{};
+      r.dst = pl->d_stage;
+      r.W = pl->p.W;
+      r.pitch = staged_pitch(pl->p.W);
+      r.rows = pl->p.H * pl->p.C;
+      rows.push_back(r);
+      pre.push_back(pre.back() + r.rows);
+    }
+    if (!rows.empty()) {
+      out->pad_off = push(blob, rows.data(), rows.size(), 64);
+      out->pad_prefix_off = push(blob, pre.data(), pre.size(), 16);
+      out->pad_total = pre.back();
+    }
+  }
+  {
     std::vector<Up0Args> args;
     std::vector<int> counts;
     for (int i = 0; i < (int)plans.size(); ++i) {
@@ -226,15 +254,23 @@ void set_blob_fault(BatchBlob& bb, unsigned* d_fault) {
   }
 }
 
-void set_level0_io(const BatchBlob& bb, Up0Args* u, Down0Args* d0, Down10Args* d10, const float* const* d_in,
-                   float* const* d_out) {
+bool encode_level0_map(const BatchBlob& bb, int img, const float* in, int W, int H, int C, CUtensorMap* m,
+                       uint32_t box_w, uint32_t box_h) {
+  float* st = img < (int)bb.stage.size() ? bb.stage[img] : nullptr;
+  return st ? encode_image_map(m, st, W, H, C, box_w, box_h, staged_pitch(W))
+            : encode_image_map(m, in, W, H, C, box_w, box_h);
+}
+
+void set_level0_io(const BatchBlob& bb, Up0Args* u, Down0Args* d0, Down10Args* d10, PadRow* pad,
+                   const float* const* d_in, float* const* d_out) {
   // the input's maps for the level-0 REDUCE and the fused combine are encoded
-  // per run (the kernels order them for the tensor-map proxy before use);
-  // where the image allows none, the kernels read the input with plain loads
+  // per run (the kernels order them for the tensor-map proxy before use), at
+  // the staging copy for images that have one; where the image allows no
+  // map, the kernels read the input with plain loads
   for (size_t j = 0; j < bb.up0_img.size(); ++j) {
     Up0Args& a = u[j];
     a.I = d_in[bb.up0_img[j]];
-    a.use_tma = encode_image_map(&a.imap, a.I, a.w0, a.h0, a.planes, kUpIW, kUpIR) ? 1 : 0;
+    a.use_tma = encode_level0_map(bb, bb.up0_img[j], a.I, a.w0, a.h0, a.planes, &a.imap, kUpIW, kUpIR) ? 1 : 0;
   }
   for (size_t j = 0; j < bb.down0_img.size(); ++j) {
     d0[j].I = d_in[bb.down0_img[j]];
@@ -244,14 +280,25 @@ void set_level0_io(const BatchBlob& bb, Up0Args* u, Down0Args* d0, Down10Args* d
     Down10Args& a = d10[j];
     a.I = d_in[bb.down10_img[j]];
     a.O = d_out[bb.down10_img[j]];
-    a.use_tma = encode_image_map(&a.imap, a.I, a.w0, a.h0, a.planes, kD0IW, kDnOH) ? 1 : 0;
+    a.use_tma =
+        encode_level0_map(bb, bb.down10_img[j], a.I, a.w0, a.h0, a.planes, &a.imap, kD0IW, kDnOH) ? 1 : 0;
   }
+  if (pad)
+    for (size_t j = 0; j < bb.pad_img.size(); ++j) pad[j].src = d_in[bb.pad_img[j]];
 }
 
 void set_blob_io(BatchBlob& bb, const float* const* d_in, float* const* d_out) {
   unsigned char* b = bb.blob.data();
   set_level0_io(bb, reinterpret_cast<Up0Args*>(b + bb.up0_off), reinterpret_cast<Down0Args*>(b + bb.down0_off),
-                reinterpret_cast<Down10Args*>(b + bb.down10_off), d_in, d_out);
+                reinterpret_cast<Down10Args*>(b + bb.down10_off),
+                bb.pad_img.empty() ? nullptr : reinterpret_cast<PadRow*>(b + bb.pad_off), d_in, d_out);
+}
+
+cudaError_t launch_batch_pad(const BatchBlob& bb, const unsigned char* d_base, cudaStream_t s) {
+  if (bb.pad_img.empty()) return cudaSuccess;
+  return launch_pad_batch(reinterpret_cast<const PadRow*>(d_base + bb.pad_off),
+                          reinterpret_cast<const int*>(d_base + bb.pad_prefix_off), (int)bb.pad_img.size(),
+                          bb.pad_total, s);
 }
 
 cudaError_t launch_batch_stages(const std::vector<StageRec>& stages, const unsigned char* d_base,
@@ -298,6 +345,7 @@ struct fllf_batch {
   Up0Args* h_up0 = nullptr;        // pinned per-run mirrors of the level-0 tables
   Down0Args* h_down0 = nullptr;
   Down10Args* h_down10 = nullptr;
+  PadRow* h_pad = nullptr;         // pinned per-run mirror of the input staging table
   cudaEvent_t copied = nullptr;
   bool copied_pending = false;
   cudaStream_t cap = nullptr;
@@ -401,6 +449,7 @@ static void free_batch(fllf_batch* b) {
   if (b->h_up0) cudaFreeHost(b->h_up0);
   if (b->h_down0) cudaFreeHost(b->h_down0);
   if (b->h_down10) cudaFreeHost(b->h_down10);
+  if (b->h_pad) cudaFreeHost(b->h_pad);
   if (b->d_mem) cudaFree(b->d_mem);
   delete b;
 }
@@ -444,7 +493,8 @@ fllf_status fllf_batch_create(fllf_plan* const* plans, int n, fllf_batch** out) 
   const size_t nu = std::max<size_t>(1, b->bb.up0_img.size());
   if (cudaMallocHost(&b->h_up0, sizeof(Up0Args) * nu) != cudaSuccess ||
       cudaMallocHost(&b->h_down0, sizeof(Down0Args) * nu) != cudaSuccess ||
-      cudaMallocHost(&b->h_down10, sizeof(Down10Args) * nu) != cudaSuccess) {
+      cudaMallocHost(&b->h_down10, sizeof(Down10Args) * nu) != cudaSuccess ||
+      cudaMallocHost(&b->h_pad, sizeof(PadRow) * std::max<size_t>(1, b->bb.pad_img.size())) != cudaSuccess) {
     cudaGetLastError();
     free_batch(b);
     return bfail(FLLF_ENOMEM, "pinned host tables");
@@ -456,6 +506,10 @@ fllf_status fllf_batch_create(fllf_plan* const* plans, int n, fllf_batch** out) 
     std::copy(u, u + b->bb.up0_img.size(), b->h_up0);
     std::copy(d, d + b->bb.down0_img.size(), b->h_down0);
     std::copy(f, f + b->bb.down10_img.size(), b->h_down10);
+  }
+  if (!b->bb.pad_img.empty()) {
+    const PadRow* r = reinterpret_cast<const PadRow*>(b->bb.blob.data() + b->bb.pad_off);
+    std::copy(r, r + b->bb.pad_img.size(), b->h_pad);
   }
   if (cudaEventCreateWithFlags(&b->copied, cudaEventDisableTiming) != cudaSuccess ||
       cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) != cudaSuccess) {
@@ -498,7 +552,7 @@ fllf_status fllf_batch_run(fllf_batch* b, const float* const* d_in, float* const
     return bfail(FLLF_ECUDA, std::string("batch copy wait: ") + cudaGetErrorString(e));
   const BatchBlob& bb = b->bb;
   if (b->mode == 0) {
-    set_level0_io(bb, b->h_up0, b->h_down0, b->h_down10, d_in, d_out);
+    set_level0_io(bb, b->h_up0, b->h_down0, b->h_down10, b->h_pad, d_in, d_out);
     auto upload = [&](size_t off, const void* src, size_t bytes) {
       return bytes ? cudaMemcpyAsync(b->d_mem + off, src, bytes, cudaMemcpyHostToDevice, s) : cudaSuccess;
     };
@@ -512,13 +566,14 @@ fllf_status fllf_batch_run(fllf_batch* b, const float* const* d_in, float* const
     for (int j = 0; j < f.n_up0; ++j) {
       Up0Args& a = b->h_fup0[j];
       a.I = d_in[f.up0_img[j]];
-      a.use_tma = encode_image_map(&a.imap, a.I, a.w0, a.h0, a.planes, kUpIW, kUpIR) ? 1 : 0;
+      a.use_tma = encode_level0_map(bb, f.up0_img[j], a.I, a.w0, a.h0, a.planes, &a.imap, kUpIW, kUpIR) ? 1 : 0;
     }
     for (int j = 0; j < f.n_d10; ++j) {
       Down10Args& a = b->h_fd10[j];
       a.I = d_in[f.d10_img[j]];
       a.O = d_out[f.d10_img[j]];
-      a.use_tma = encode_image_map(&a.imap, a.I, a.w0, a.h0, a.planes, kD0IW, kDnOH) ? 1 : 0;
+      a.use_tma =
+          encode_level0_map(bb, f.d10_img[j], a.I, a.w0, a.h0, a.planes, &a.imap, kD0IW, kDnOH) ? 1 : 0;
     }
     for (int j = 0; j < f.n_d0; ++j) {
       b->h_fd0[j].I = d_in[f.d0_img[j]];
@@ -530,6 +585,13 @@ fllf_status fllf_batch_run(fllf_batch* b, const float* const* d_in, float* const
     if ((e = upload(f.up0_off, b->h_fup0, sizeof(Up0Args) * f.n_up0)) != cudaSuccess ||
         (e = upload(f.d10_off, b->h_fd10, sizeof(Down10Args) * f.n_d10)) != cudaSuccess ||
         (e = upload(f.d0_off, b->h_fd0, sizeof(Down0Args) * f.n_d0)) != cudaSuccess)
+      return bfail(FLLF_ECUDA, std::string("batch table update: ") + cudaGetErrorString(e));
+  }
+  if (!bb.pad_img.empty()) {
+    // this run's staging sources
+    for (size_t j = 0; j < bb.pad_img.size(); ++j) b->h_pad[j].src = d_in[bb.pad_img[j]];
+    if ((e = cudaMemcpyAsync(b->d_mem + bb.pad_off, b->h_pad, sizeof(PadRow) * bb.pad_img.size(),
+                             cudaMemcpyHostToDevice, s)) != cudaSuccess)
       return bfail(FLLF_ECUDA, std::string("batch table update: ") + cudaGetErrorString(e));
   }
   if ((e = cudaEventRecord(b->copied, s)) != cudaSuccess)
@@ -548,8 +610,10 @@ fllf_status fllf_batch_run(fllf_batch* b, const float* const* d_in, float* const
     cudaGraph_t g = nullptr;
     if ((e = cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeRelaxed)) != cudaSuccess)
       return bfail(FLLF_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e));
-    const cudaError_t le = b->mode == 0 ? launch_batch_stages(bb.stages, b->d_mem, b->precision, b->cap, b->cps)
-                                        : launch_flow(b, b->cap);
+    cudaError_t le = launch_batch_pad(bb, b->d_mem, b->cap);
+    if (le == cudaSuccess)
+      le = b->mode == 0 ? launch_batch_stages(bb.stages, b->d_mem, b->precision, b->cap, b->cps)
+                        : launch_flow(b, b->cap);
     e = cudaStreamEndCapture(b->cap, &g);
     if (le != cudaSuccess || e != cudaSuccess) {
       if (g) cudaGraphDestroy(g);

@@ -88,6 +88,14 @@ struct FastArgs {
   float k2;
 };
 
+// Input staging of one image of a batch: `rows` dense rows of W floats from
+// src to rows of `pitch` floats (a multiple of 4) at dst.
+struct PadRow {
+  const float* src;
+  float* dst;
+  int W, pitch, rows, pad_;
+};
+
 struct Up0Args {
   CUtensorMap imap;     // level-0 input (valid when use_tma)
   const float* I;       // level-0 input planes, pitch w0, plane stride h0*w0

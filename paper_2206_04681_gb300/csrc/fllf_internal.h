@@ -211,6 +211,12 @@ struct BatchBlob {
   std::vector<StageRec> stages;     // launch order
   std::vector<int> up0_img, down0_img, down10_img, copy_img;
   size_t up0_off = 0, down0_off = 0, down10_off = 0, status_off = 0;
+  // input staging (images whose plan has d_stage): per image the staging
+  // buffer or null, and the PadRow table with its row prefix sums
+  std::vector<float*> stage;
+  std::vector<int> pad_img;
+  size_t pad_off = 0, pad_prefix_off = 0;
+  int pad_total = 0;
 };
 // Argument tables for `plans` (same storage precision `prec`).
 void build_batch_blob(const std::vector<const fllf_plan*>& plans, int prec, BatchBlob* out);
@@ -219,8 +225,16 @@ void set_blob_fault(BatchBlob& bb, unsigned* d_fault);
 // Writes the level-0 input / output pointers of each image, and the input's
 // tensor maps, into the tables u (up0), d0 (level-0 combine) and d10 (fused
 // level-1/level-0 combine), which hold bb's entries in bb's order.
-void set_level0_io(const BatchBlob& bb, Up0Args* u, Down0Args* d0, Down10Args* d10, const float* const* d_in,
-                   float* const* d_out);
+// With staging, the maps point at the staging buffers and pad (bb's PadRow
+// entries, may be null when bb has none) gets this run's sources.
+void set_level0_io(const BatchBlob& bb, Up0Args* u, Down0Args* d0, Down10Args* d10, PadRow* pad,
+                   const float* const* d_in, float* const* d_out);
+// The level-0 input map of image `img` of bb for a box, at its staging
+// buffer when it has one (then use_tma needs the staging copy first).
+bool encode_level0_map(const BatchBlob& bb, int img, const float* in, int W, int H, int C, CUtensorMap* m,
+                       uint32_t box_w, uint32_t box_h);
+// Enqueues the batch's input staging copies (one launch; none without).
+cudaError_t launch_batch_pad(const BatchBlob& bb, const unsigned char* d_base, cudaStream_t s);
 // The same on the table image inside bb.
 void set_blob_io(BatchBlob& bb, const float* const* d_in, float* const* d_out);
 // Enqueues the batched stage kernels reading the tables uploaded at d_base.

@@ -1908,6 +1908,31 @@ __global__ void __launch_bounds__(kThreads) k_pad_rows(const float* __restrict__
   }
 }
 
+// The staging copies of a batch: global row r of the table's images.
+__global__ void __launch_bounds__(kThreads) k_pad_batch(const PadRow* __restrict__ tab,
+                                                        const int* __restrict__ prefix, int n, int total) {
+  for (int r = blockIdx.x; r < total; r += gridDim.x) {
+    const int j = find_entry(prefix, n, r);
+    const PadRow e = tab[j];
+    const int lr = r - __ldg(prefix + j);
+    const float* sr = e.src + (long long)lr * e.W;
+    float* dr = e.dst + (long long)lr * e.pitch;
+    for (int c0 = threadIdx.x; c0 < e.W; c0 += 4 * kThreads) {
+      float v[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int c = c0 + u * kThreads;
+        v[u] = c < e.W ? __ldg(sr + c) : 0.f;
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int c = c0 + u * kThreads;
+        if (c < e.W) dr[c] = v[u];
+      }
+    }
+  }
+}
+
 // Copies a status block's fault word into a host-mapped word, so that a
 // frame's completion can be checked on the host without a device-to-host copy.
 __global__ void k_status_snapshot(const unsigned* __restrict__ status, unsigned* __restrict__ host_word) {
@@ -2089,6 +2114,11 @@ cudaError_t launch_pad_rows(const float* src, int W, long long rows, float* dst,
   if (rows <= 0 || W <= 0) return cudaSuccess;
   const int grid = (int)std::min<long long>(rows, 152 * 8);
   k_pad_rows<<<grid, kThreads, 0, s>>>(src, W, rows, dst, pitch);
+  return cudaGetLastError();
+}
+cudaError_t launch_pad_batch(const PadRow* tab, const int* prefix, int n, int total, cudaStream_t s) {
+  if (n <= 0 || total <= 0) return cudaSuccess;
+  k_pad_batch<<<std::min(total, 152 * 8), kThreads, 0, s>>>(tab, prefix, n, total);
   return cudaGetLastError();
 }
 cudaError_t launch_status_snapshot(const unsigned* status, unsigned* host_word, cudaStream_t s) {

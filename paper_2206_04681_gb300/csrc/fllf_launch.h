@@ -34,6 +34,8 @@ cudaError_t launch_luma_apply(const float* rgb, const float* y, const float* yf,
                               cudaStream_t s);
 // Copies `rows` dense rows of W floats to a row pitch of `pitch` floats.
 cudaError_t launch_pad_rows(const float* src, int W, long long rows, float* dst, int pitch, cudaStream_t s);
+// The staging copies of a batch: n PadRow entries, prefix[n + 1] row sums.
+cudaError_t launch_pad_batch(const PadRow* tab, const int* prefix, int n, int total, cudaStream_t s);
 // Copies status[0] (the fault word) into a host-mapped word (one thread).
 cudaError_t launch_status_snapshot(const unsigned* status, unsigned* host_word, cudaStream_t s);
 FLLF_DECLARE_LAUNCHERS(f32)

@@ -145,7 +145,12 @@ struct Request {
 };
 
 // Bytes of one request in the pool: its pyramids.
-size_t request_bytes(const fllf_params& p) { return layout(p, nullptr); }
+// Pyramid scratch, then (rows not 16-byte aligned) the input staging copy.
+size_t stage_offset(const fllf_params& p) { return (layout(p, nullptr) + 255) & ~size_t(255); }
+size_t request_bytes(const fllf_params& p) {
+  if (p.levels < 2 || (p.W % 4) == 0) return layout(p, nullptr);
+  return stage_offset(p) + sizeof(float) * (size_t)staged_pitch(p.W) * p.H * p.C;
+}
 
 // Status block after the pool: 16 waves x 64 bytes.
 constexpr size_t kStatusBytes = 1024;
@@ -226,6 +231,7 @@ bool build_request_plan(fllf_server* sv, Request* r) {
   if (!check_layout(r->p, pl.lv, base, r->bytes)) return false;
   pl.d_fault = sv->d_status;
   pl.scratch = nullptr;  // owned by the pool
+  pl.d_stage = (L > 1 && (r->p.W % 4) != 0) ? reinterpret_cast<float*>(base + stage_offset(r->p)) : nullptr;
   if (L > 1 && !build_maps(r->p, pl.lv, &pl.maps)) return false;
   // the cached coefficients: a device slot, filled when the set first gets one
   CoefEntry& ce = *r->coef;
@@ -298,6 +304,7 @@ cudaError_t launch_wave(fllf_server* sv, Wave& w) {
                              cudaMemcpyDeviceToDevice, w.stream)) != cudaSuccess)
       return e;
   }
+  if ((e = launch_batch_pad(bb, w.d_tab, w.stream)) != cudaSuccess) return e;
   if ((e = launch_batch_stages(bb.stages, w.d_tab, w.reqs.front()->p.precision, w.stream)) !=
       cudaSuccess)
     return e;

@@ -63,7 +63,10 @@ def test_batch_equals_per_image_runs(precision, mode):
         for rep in range(3):
             for y in outs:
                 y.fill_(float("nan"))
-            pkg.fllf_batch_run(batch, [x.data_ptr() for x in ins], [y.data_ptr() for y in outs], s)
+            # the second run reads copies at other addresses (the level-0
+            # maps and staging sources are set per run)
+            cur = [x.clone() for x in ins] if rep == 1 else ins
+            pkg.fllf_batch_run(batch, [x.data_ptr() for x in cur], [y.data_ptr() for y in outs], s)
             torch.cuda.synchronize()
             pkg.fllf_batch_check(batch)
             for y, r in zip(outs, refs):

@@ -196,6 +196,40 @@ def test_uhd_rgb_mixed_full_frame(uhd, precision):
     assert q >= 60.0
 
 
+@pytest.mark.parametrize("W", [96, 95, 94, 93])
+@pytest.mark.parametrize("fast", [False, True])
+def test_input_load_routes_same_bits(W, fast):
+    """The level-0 kernels read the input by TMA (rows on 16-byte
+    boundaries), from the plan's staging copy (W % 4 != 0) or with plain
+    loads (W % 4 == 0 at a misaligned address): every route gives the same
+    bits, and the first matches the oracle."""
+    H, C, L = 70, 3, 5
+    img = synth_image(H, W, C, polygons=5, seed=W)
+    p = (pkg.make_fast_params(H, W, C, L, 9, 3.0, 0.2) if fast
+         else pkg.make_params(H, W, C, L, 8, 3.0, 0.2, 2.0))
+    plan = pkg.fllf_plan_create(p, 0)
+    try:
+        n = img.size
+        buf = torch.zeros(n + 4, dtype=torch.float32, device="cuda")
+        out = torch.empty(n + 4, dtype=torch.float32, device="cuda")
+        s = torch.cuda.current_stream().cuda_stream
+        res = []
+        for off in (0, 1, 3):   # 16-byte aligned start, then 4 and 12 bytes past it
+            buf.zero_()
+            buf[off:off + n].copy_(torch.from_numpy(img.reshape(-1)))
+            pkg.fllf_run(plan, buf.data_ptr() + 4 * off, out.data_ptr() + 4 * off, s)
+            torch.cuda.synchronize()
+            res.append(out[off:off + n].cpu().numpy().reshape(img.shape))
+        for r in res[1:]:
+            np.testing.assert_array_equal(r, res[0])
+        if not fast:
+            a = np.array(o.coeffs_quadrature(3.0, 0.2, 2.0, 8))
+            ref = o.fourier_llf(img.astype(np.float64), L, a, 2.0)
+            assert float(np.max(np.abs(res[0] - ref))) <= FP32_TOL
+    finally:
+        pkg.fllf_plan_destroy(plan)
+
+
 @pytest.mark.parametrize("H,W,C,L,fast", [(37, 53, 3, 5, False), (130, 250, 2, 6, False), (64, 96, 3, 5, True)])
 def test_run_host_plane_pipeline_same_bits(H, W, C, L, fast):
     # host buffers with C >= 2 run plane by plane with the copies overlapped;
