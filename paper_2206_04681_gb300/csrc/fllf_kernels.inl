@@ -74,6 +74,32 @@ __device__ __forceinline__ int find_entry(const int* prefix, int n, int x) {
   return lo;
 }
 
+// Work item -> argument block of a batched stage.  The item range of the
+// last entry is kept, so that the consecutive items of one image (the common
+// case) skip the search.
+template <typename A>
+struct EntryCache {
+  BatchTable<A> tb;
+  int j = 0, lo = 0, hi = 0;
+  __device__ __forceinline__ const A* operator()(int g, int& l) {
+    if (g < lo || g >= hi) {
+      j = find_entry(tb.prefix, tb.n, g);
+      lo = __ldg(tb.prefix + j);
+      hi = __ldg(tb.prefix + j + 1);
+    }
+    l = g - lo;
+    return tb.args + j;
+  }
+};
+// Stages reading their arguments through an EntryCache (a table in global
+// memory) copy an item's scalars by value: the copy stays in registers across
+// the stage's global stores, which could otherwise alias the table.  Kernels
+// with their arguments in the parameter space read them in place.
+template <class R>
+struct CopiesArgs : std::false_type {};
+template <class A>
+struct CopiesArgs<EntryCache<A>> : std::true_type {};
+
 // ---------------------------------------------------------------------------------------
 // up0: level 0 -> 1.  Item = tile of 32 x 14 level-1 outputs.  Item (row r,
 // segment s) of the horizontal pass holds 11 fine pixels of one staged input
@@ -115,7 +141,7 @@ __device__ __forceinline__ bool stage_up0(Res res, int total, unsigned char* sme
   for (int gt = b; gt < total; gt += G, ++n) {
     const int buf = n & 1;
     int t;
-    const Up0Args& a = *res(gt, t);
+    std::conditional_t<CopiesArgs<Res>::value, const Up0Args, const Up0Args&> a = *res(gt, t);
     const TileXY gxy = tile_of(t, cdiv(a.dst.w, kUpTW), cdiv(a.dst.h, kUpTH));
     const int pl = gxy.pl;
     const int X1 = gxy.tx * kUpTW, Y1 = gxy.ty * kUpTH;
@@ -372,7 +398,7 @@ __device__ __forceinline__ bool stage_up(Res res, int total, unsigned char* smem
   for (int i = 0; i < nitems; ++i) {
     const int slot = i % kUpSlots;
     int li;
-    const UpArgs& a = *res(b + i * G, li);
+    std::conditional_t<CopiesArgs<Res>::value, const UpArgs, const UpArgs&> a = *res(b + i * G, li);
     int ch;
     const int nch = cdiv(a.K, KCU), t = div_fast(li, up_chunks<S>(a), ch);
     const TileXY gxy = tile_of(t, cdiv(a.dst.w, kRsTW), cdiv(a.dst.h, kRsTH));
@@ -951,11 +977,17 @@ __device__ __forceinline__ bool stage_combine_s(Res res, int total, unsigned cha
     if (e) tma_load3(p + kOffE, &a.emap, cx0, cy0, g.pl, &bar[buf]);
   };
   int t = b, lt = 0;
-  const DownArgs* a = res(t, lt);
+  // the tile's arguments (a by-value copy of the scalars for a batched
+  // table); the tensor maps are read at ap
+  constexpr bool kCopy = CopiesArgs<Res>::value;
+  const DownArgs* ap = res(t, lt);
+  DownArgs av;
+  if constexpr (kCopy) av = *ap;
+  const DownArgs* a = kCopy ? &av : ap;
   int nch = cdiv(a->K, kKCS), ch = nch - 1;
   if (tid == 0) {
     fence_proxy_async();
-    issue(*a, lt, ch, true, 0);
+    issue(*ap, lt, ch, true, 0);
   }
 
   // X0 is even, so the column's parity is that of tc; its EXPAND reads the
@@ -983,7 +1015,7 @@ __device__ __forceinline__ bool stage_combine_s(Res res, int total, unsigned cha
     if (tid == 0 && has_next) {
       fence_proxy_async();
       if (!last) {
-        issue(*a, lt, ch - 1, false, buf ^ 1);
+        issue(*ap, lt, ch - 1, false, buf ^ 1);
       } else {
         int ln;
         const DownArgs* an = res(t + G, ln);
@@ -1079,7 +1111,9 @@ __device__ __forceinline__ bool stage_combine_s(Res res, int total, unsigned cha
     } else {
       t += G;
       if (t >= total) break;
-      a = res(t, lt);
+      ap = res(t, lt);
+      if constexpr (kCopy) av = *ap;
+      else a = ap;
       nch = cdiv(a->K, kKCS);
       ch = nch - 1;
     }
@@ -1142,11 +1176,17 @@ __device__ __forceinline__ bool stage_down10(Res res, int total, unsigned char* 
     if (in) tma_load3(p + kOffI, &a.imap, tx * kDnOW - kDnX0 - 2, ty * kDnOH, pl, &bar[buf]);
   };
   int t = b, lt = 0;
-  const Down10Args* a = res(t, lt);
+  // the tile's arguments (a by-value copy of the scalars for a batched
+  // table); the tensor maps are read at ap
+  constexpr bool kCopy = CopiesArgs<Res>::value;
+  const Down10Args* ap = res(t, lt);
+  Down10Args av;
+  if constexpr (kCopy) av = *ap;
+  const Down10Args* a = kCopy ? &av : ap;
   int nch = cdiv(a->K, kKC), ch = nch - 1;
   if (tid == 0) {
     fence_proxy_async();
-    issue(*a, lt, ch, true, 0);
+    issue(*ap, lt, ch, true, 0);
   }
 
   const int tc = tid % (kDnOW / 4), tr = tid / (kDnOW / 4);
@@ -1184,7 +1224,7 @@ __device__ __forceinline__ bool stage_down10(Res res, int total, unsigned char* 
     if (tid == 0 && has_next) {
       fence_proxy_async();
       if (!last) {
-        issue(*a, lt, ch - 1, false, buf ^ 1);
+        issue(*ap, lt, ch - 1, false, buf ^ 1);
       } else {
         int ln;
         const Down10Args* an = res(t + G, ln);
@@ -1415,7 +1455,9 @@ __device__ __forceinline__ bool stage_down10(Res res, int total, unsigned char* 
     } else {
       t += G;
       if (t >= total) break;
-      a = res(t, lt);
+      ap = res(t, lt);
+      if constexpr (kCopy) av = *ap;
+      else a = ap;
       nch = cdiv(a->K, kKC);
       ch = nch - 1;
     }
@@ -1524,11 +1566,7 @@ __global__ void __launch_bounds__(kThreads) k_up0_batch(const BatchTable<Up0Args
   });
   init_bars(bar);
   Pipe pp{};
-  stage_up0<S>([&](int g, int& l) {
-                 const int j = find_entry(tb.prefix, tb.n, g);
-                 l = g - __ldg(tb.prefix + j);
-                 return tb.args + j;
-               },
+  stage_up0<S>(EntryCache<Up0Args>{tb},
                tb.total, smem, bar, pp, blockIdx.x, gridDim.x);
 }
 
@@ -1543,11 +1581,7 @@ __global__ void __launch_bounds__(kThreads) k_up_batch(const BatchTable<UpArgs> 
   });
   init_bars(bar);
   Pipe pp{};
-  stage_up<S>([&](int g, int& l) {
-                const int j = find_entry(tb.prefix, tb.n, g);
-                l = g - __ldg(tb.prefix + j);
-                return tb.args + j;
-              },
+  stage_up<S>(EntryCache<UpArgs>{tb},
               tb.total, smem, bar, pp, blockIdx.x, gridDim.x);
 }
 
@@ -1568,11 +1602,7 @@ __global__ void __launch_bounds__(kThreads) k_down_batch(const BatchTable<DownAr
   init_bars(bar);
   Pipe pp{};
   stage_combine_s<S>(
-      [&](int g, int& l) {
-        const int j = find_entry(tb.prefix, tb.n, g);
-        l = g - __ldg(tb.prefix + j);
-        return tb.args + j;
-      },
+      EntryCache<DownArgs>{tb},
       tb.total, smem, bar, pp, blockIdx.x, gridDim.x);
 }
 
@@ -1593,11 +1623,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_down10_batch(const BatchTable<D
   init_bars(bar);
   Pipe pp{};
   stage_down10<S, false>(
-      [&](int g, int& l) {
-        const int j = find_entry(tb.prefix, tb.n, g);
-        l = g - __ldg(tb.prefix + j);
-        return tb.args + j;
-      },
+      EntryCache<Down10Args>{tb},
       tb.total, smem, bar, pp, blockIdx.x, gridDim.x);
 }
 
