@@ -1192,10 +1192,14 @@ __device__ __forceinline__ bool stage_down10(Res res, int total, unsigned char* 
   const int tc = tid % (kDnOW / 4), tr = tid / (kDnOW / 4);
   // level-1 blocks on threads 0..152 (warps 0-4 at full width): the other
   // warps go straight to the level-0 combine, and their issue slots serve the
-  // SM's other CTA meanwhile
-  const int b1 = tid;
+  // SM's other CTA meanwhile.  Threads 0..143 take block columns 0..15, a
+  // half-warp per block row, so that a half-warp's window loads are one
+  // contiguous run (no bank conflicts); threads 144..152 take column 16.
+  static_assert(kB1X == 17, "level-1 block mapping");
+  constexpr int kB1Main = (kB1X - 1) * kB1Y;
   const bool l1t = tid < kB1X * kB1Y;
-  const int bc = b1 % kB1X, br = b1 / kB1X;
+  const int bc = tid < kB1Main ? (tid & 15) : kB1X - 1;
+  const int br = tid < kB1Main ? (tid >> 4) : tid - kB1Main;
   float2 we[4], wo[4], Pe[4], Po[4], base[4];
   float2 w1[2][2], P1[2][2];
   float up_e2[2][2];
