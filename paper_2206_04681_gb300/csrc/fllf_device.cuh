@@ -255,7 +255,10 @@ constexpr int kUpIPX = 2 * kUpRun + 3;    // fine inputs per item (11)
 constexpr int kUpItems = kUpIR * kUpSeg;  // 248 horizontal items
 constexpr int kUpVRows = kUpTH / 2;       // coarse rows per vertical thread (7)
 constexpr int kUpCS = 36;                 // staged rows per column (36 x 8 B: 2 mod 8 bank groups)
-constexpr int kUpIW = 72;                 // staged input columns (box from 2*X1-4, 16-B aligned)
+// staged input columns (box from 2*X1-4, 16-B aligned; 70 are read): a row
+// pitch of 76 floats (12 banks mod 32) puts the 8 rows of a quarter-warp's
+// 16-byte loads on distinct banks, where 72 (8 mod 32) made them 2-way
+constexpr int kUpIW = 76;
 static_assert(kUpItems <= kThreads, "REDUCE items exceed the block");
 static_assert(kUpSeg * 32 == kThreads && kUpIR <= 32, "up0 items: one warp per run segment, one lane per row");
 static_assert(kKC * 2 * kUpRun == 32 && kUpRun * kUpVRows <= 32, "up0 vertical pass: one warp per segment");
