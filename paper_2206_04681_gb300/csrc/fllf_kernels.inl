@@ -63,6 +63,14 @@ __device__ __forceinline__ void init_bars(uint64_t* bar) {
   asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 }
 
+// Brings a tensor map of the kernel's parameters into the TMA unit's
+// descriptor cache.  Issued before the launch dependency is waited for (the
+// maps are parameters, not data of the previous kernel), so the fetch
+// overlaps that kernel's tail instead of delaying the first copy.
+__device__ __forceinline__ void prefetch_map(const CUtensorMap* m) {
+  asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(m)) : "memory");
+}
+
 // Entry j of a prefix table holding item x (prefix[0] = 0, prefix[n] = total).
 __device__ __forceinline__ int find_entry(const int* prefix, int n, int x) {
   int lo = 0, hi = n - 1;
@@ -1476,6 +1484,7 @@ __global__ void __launch_bounds__(kThreads) k_up0(const __grid_constant__ Up0Arg
   using SM = Smem<sizeof(typename Cplx<S>::T)>;
   extern __shared__ __align__(128) unsigned char smem[];
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem + SM::up0 - 64);
+  if (threadIdx.x == 0 && a.use_tma) prefetch_map(&a.imap);
   init_bars(bar);
   Pipe pp{};
   const int hi = a.item1 > 0 ? a.item1 : up0_tiles(a);
@@ -1488,6 +1497,10 @@ __global__ void __launch_bounds__(kThreads) k_up(const __grid_constant__ UpArgs 
   using SM = Smem<sizeof(typename Cplx<S>::T)>;
   extern __shared__ __align__(128) unsigned char smem[];
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem + SM::up - 64);
+  if (threadIdx.x == 0) {
+    prefetch_map(&a.zmap);
+    if (a.write_g) prefetch_map(&a.gmap);
+  }
   init_bars(bar);
   Pipe pp{};
   const int n = up_items<S>(a);
@@ -1518,6 +1531,12 @@ __global__ void __launch_bounds__(kThreads) k_down_s(const __grid_constant__ Dow
   using SM = Smem<sizeof(typename Cplx<S>::T)>;
   extern __shared__ __align__(128) unsigned char smem[];
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem + SM::dns - 64);
+  if (threadIdx.x == 0) {
+    prefetch_map(&a.zfmap);
+    prefetch_map(&a.zmap);
+    prefetch_map(&a.gfmap);
+    if (a.has_e) prefetch_map(&a.emap);
+  }
   init_bars(bar);
   Pipe pp{};
   stage_combine_s<S, FAST>([&](int g, int& l) { l = g; return &a; }, small_tiles(a.fine.h, a.fine.w, a.planes),
@@ -1542,6 +1561,13 @@ __global__ void __launch_bounds__(kThreads, 2) k_down10(const __grid_constant__ 
   using SM = Smem<sizeof(typename Cplx<S>::T)>;
   extern __shared__ __align__(128) unsigned char smem[];
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem + SM::d10 - 64);
+  if (threadIdx.x == 0) {
+    prefetch_map(&a.z1map);
+    prefetch_map(&a.z2map);
+    prefetch_map(&a.g1map);
+    if (a.has_e2) prefetch_map(&a.e2map);
+    if (a.use_tma) prefetch_map(&a.imap);
+  }
   init_bars(bar);
   Pipe pp{};
   stage_down10<S, ADAPT, FAST>([&](int g, int& l) { l = g; return &a; }, combine_tiles(a.h0, a.w0, a.planes), smem, bar,
