@@ -366,16 +366,19 @@ fllf_status plane_pipeline_setup(fllf_plan* pl) {
 }  // namespace
 
 
+// Clears the plan's status block (fault word and grid-barrier words) and
+// reports the timeout a kernel's bounded wait recorded there.
+static fllf_status report_fault(fllf_plan* plan) {
+  cudaMemset(plan->d_fault, 0, 256);
+  return fail(FLLF_ETIMEOUT, "a kernel's bounded wait for a shared-memory copy ran out");
+}
+
 // Reads and clears the plan's fault word (after the plan's work completed).
 static fllf_status check_fault(fllf_plan* plan) {
   unsigned f = 0;
   cudaError_t e = cudaMemcpy(&f, plan->d_fault, sizeof(unsigned), cudaMemcpyDeviceToHost);
   if (e != cudaSuccess) return cuda_fail(e, "fault word read");
-  if (f) {
-    cudaMemset(plan->d_fault, 0, 256);  // fault word and the grid-barrier words
-    return fail(FLLF_ETIMEOUT, "a kernel's bounded wait for a shared-memory copy ran out");
-  }
-  return FLLF_OK;
+  return f ? report_fault(plan) : FLLF_OK;
 }
 
 namespace {
@@ -863,8 +866,9 @@ fllf_status fllf_poll(uint64_t ticket, int timeout_us) {
       }
       cudaEventDestroy(tk.ev);
       if (e != cudaSuccess) return cuda_fail(e, "submitted work failed");
-      // a clean snapshot needs no device read; a set one is read and cleared there
-      if (tk.snap >= 0 && snapped == 0) return FLLF_OK;
+      // the snapshot decides for a host-frame ticket (a set word is reported
+      // even when an earlier poll already cleared the device word)
+      if (tk.snap >= 0) return snapped ? report_fault(tk.plan) : FLLF_OK;
       return check_fault(tk.plan);
     }
     if (timeout_us == 0) return FLLF_EAGAIN;

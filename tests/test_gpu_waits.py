@@ -101,6 +101,15 @@ def test_timeout_through_submit_host():
         pkg.fllf_plan_set_wait_test(plan, 100_000, 1)
         t = pkg.fllf_submit_host(plan, hin.data_ptr(), hout.data_ptr(), 0)
         assert pkg.fllf_poll(t, 10_000_000) == pkg.FLLF_ETIMEOUT
+        # two faulting frames, polled newest first: the first report clears
+        # the device word, and the older ticket still reports its own
+        # timeout from its snapshot
+        pkg.fllf_plan_set_wait_test(plan, 100_000, 1)
+        hout2 = torch.full_like(hin, float("nan")).pin_memory()
+        t1 = pkg.fllf_submit_host(plan, hin.data_ptr(), hout.data_ptr(), 0)
+        t2 = pkg.fllf_submit_host(plan, hin.data_ptr(), hout2.data_ptr(), 0)
+        assert pkg.fllf_poll(t2, 10_000_000) == pkg.FLLF_ETIMEOUT
+        assert pkg.fllf_poll(t1, 10_000_000) == pkg.FLLF_ETIMEOUT
         t = pkg.fllf_submit_host(plan, hin.data_ptr(), hout.data_ptr(), 0)
         assert pkg.fllf_poll(t, 10_000_000) == pkg.FLLF_OK
         np.testing.assert_array_equal(hout.numpy(), ref)
