@@ -187,7 +187,12 @@ fllf_status fllf_run_luma(fllf_plan *plan, const float *d_rgb_in, float *d_rgb_o
 fllf_status fllf_run_host(fllf_plan *plan, const float *h_in, float *h_out, void *stream);
 
 /* Asynchronous form of fllf_run: enqueues the work and records a
- * completion event; *ticket identifies it for fllf_poll. */
+ * completion event; *ticket identifies it for fllf_poll.  After the run a
+ * one-thread kernel copies the plan's fault word into a host-mapped word
+ * (64 per plan, one per pending ticket of fllf_submit or fllf_submit_host;
+ * allocated on first use), which fllf_poll reads without a device-to-host
+ * copy; so each ticket reports a bounded wait that gave up in its own run or
+ * an earlier one.  Tickets beyond 64 pending read the device word. */
 fllf_status fllf_submit(fllf_plan *plan, const float *d_in, float *d_out, void *stream,
                         uint64_t *ticket);
 
@@ -211,10 +216,8 @@ fllf_status fllf_submit(fllf_plan *plan, const float *d_in, float *d_out, void *
  *   first call (kept by the plan; FLLF_ENOMEM if the slots do not fit).
  *   Like fllf_run, one plan's runs share its scratch: submit them on one
  *   stream.  A kernel's bounded wait that gave up is reported by fllf_poll
- *   (FLLF_ETIMEOUT): after each frame a one-thread kernel copies the plan's
- *   fault word into a host-mapped word (64 per plan, one per pending
- *   ticket), which fllf_poll reads without a device-to-host copy; tickets
- *   beyond 64 pending read the device word. */
+ *   (FLLF_ETIMEOUT), from the frame's fault-word snapshot as for
+ *   fllf_submit. */
 fllf_status fllf_submit_host(fllf_plan *plan, const float *h_in, float *h_out, void *stream,
                              uint64_t *ticket);
 

@@ -309,6 +309,15 @@ fllf_status host_slots_setup(fllf_plan* pl) {
       }
     }
   }
+  pl->host_slots = std::move(slots);
+  pl->next_slot = 0;
+  return FLLF_OK;
+}
+
+// The plan's host-mapped fault-word snapshots (first use).  Without them
+// (allocation failed) tickets read the device word instead.
+void snap_setup(fllf_plan* pl) {
+  if (pl->h_snap) return;
   unsigned* h = nullptr;
   unsigned* d = nullptr;
   if (cudaHostAlloc(reinterpret_cast<void**>(&h), sizeof(unsigned) * kSnapWords, cudaHostAllocMapped) !=
@@ -316,15 +325,51 @@ fllf_status host_slots_setup(fllf_plan* pl) {
       cudaHostGetDevicePointer(reinterpret_cast<void**>(&d), h, 0) != cudaSuccess) {
     cudaGetLastError();
     if (h) cudaFreeHost(h);
-    undo();
-    return fail(FLLF_ENOMEM, "host-mapped status words allocation failed");
+    return;
   }
+  std::lock_guard<std::mutex> lk(g_ticket_mu);
   pl->h_snap = h;
   pl->d_snap = d;
   pl->snap_free.clear();
   for (int i = kSnapWords - 1; i >= 0; --i) pl->snap_free.push_back(i);
-  pl->host_slots = std::move(slots);
-  pl->next_slot = 0;
+}
+
+// Ends a submitted run on stream s: a snapshot of the plan's fault word into
+// a free host-mapped word (none free: the poll reads the device word), a
+// completion event, and the ticket.
+fllf_status enqueue_ticket(fllf_plan* plan, cudaStream_t s, uint64_t* ticket) {
+  snap_setup(plan);
+  int snap = -1;
+  {
+    std::lock_guard<std::mutex> lk(g_ticket_mu);
+    if (!plan->snap_free.empty()) {
+      snap = plan->snap_free.back();
+      plan->snap_free.pop_back();
+    }
+  }
+  auto give_back = [&]() {
+    if (snap < 0) return;
+    std::lock_guard<std::mutex> lk(g_ticket_mu);
+    plan->snap_free.push_back(snap);
+  };
+  cudaError_t e;
+  if (snap >= 0 && (e = launch_status_snapshot(plan->d_fault, plan->d_snap + snap, s)) != cudaSuccess) {
+    give_back();
+    return cuda_fail(e, "status snapshot");
+  }
+  cudaEvent_t ev;
+  if ((e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming)) != cudaSuccess) {
+    give_back();
+    return cuda_fail(e, "cudaEventCreate");
+  }
+  if ((e = cudaEventRecord(ev, s)) != cudaSuccess) {
+    cudaEventDestroy(ev);
+    give_back();
+    return cuda_fail(e, "cudaEventRecord");
+  }
+  std::lock_guard<std::mutex> lk(g_ticket_mu);
+  *ticket = g_next_ticket++;
+  g_tickets[*ticket] = Ticket{ev, plan->device, plan, snap};
   return FLLF_OK;
 }
 
@@ -762,17 +807,7 @@ fllf_status fllf_submit(fllf_plan* plan, const float* d_in, float* d_out, void* 
   fllf_status st = fllf_run(plan, d_in, d_out, stream);
   if (st != FLLF_OK) return st;
   DeviceGuard guard(plan->device);
-  cudaEvent_t ev;
-  cudaError_t e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
-  if (e != cudaSuccess) return cuda_fail(e, "cudaEventCreate");
-  if ((e = cudaEventRecord(ev, reinterpret_cast<cudaStream_t>(stream))) != cudaSuccess) {
-    cudaEventDestroy(ev);
-    return cuda_fail(e, "cudaEventRecord");
-  }
-  std::lock_guard<std::mutex> lk(g_ticket_mu);
-  *ticket = g_next_ticket++;
-  g_tickets[*ticket] = Ticket{ev, plan->device, plan};
-  return FLLF_OK;
+  return enqueue_ticket(plan, reinterpret_cast<cudaStream_t>(stream), ticket);
 }
 
 fllf_status fllf_submit_host(fllf_plan* plan, const float* h_in, float* h_out, void* stream,
@@ -806,40 +841,10 @@ fllf_status fllf_submit_host(fllf_plan* plan, const float* h_in, float* h_out, v
       (e = cudaEventRecord(h.copied_out, plan->io_d2h)) != cudaSuccess)
     return cuda_fail(e, "device-to-host copy");
   plan->next_slot = (plan->next_slot + 1) % kHostSlots;
-  // the fault word as it stands after this frame, copied into a host-mapped
-  // word that fllf_poll reads (no device-to-host copy behind the frame copies);
-  // without a free word, fllf_poll reads the device word instead
-  int snap = -1;
-  {
-    std::lock_guard<std::mutex> lk(g_ticket_mu);
-    if (!plan->snap_free.empty()) {
-      snap = plan->snap_free.back();
-      plan->snap_free.pop_back();
-    }
-  }
-  auto give_back = [&]() {
-    if (snap < 0) return;
-    std::lock_guard<std::mutex> lk(g_ticket_mu);
-    plan->snap_free.push_back(snap);
-  };
-  if (snap >= 0 && (e = launch_status_snapshot(plan->d_fault, plan->d_snap + snap, plan->io_d2h)) != cudaSuccess) {
-    give_back();
-    return cuda_fail(e, "status snapshot");
-  }
-  cudaEvent_t ev;
-  if ((e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming)) != cudaSuccess) {
-    give_back();
-    return cuda_fail(e, "cudaEventCreate");
-  }
-  if ((e = cudaEventRecord(ev, plan->io_d2h)) != cudaSuccess) {
-    cudaEventDestroy(ev);
-    give_back();
-    return cuda_fail(e, "cudaEventRecord");
-  }
-  std::lock_guard<std::mutex> lk(g_ticket_mu);
-  *ticket = g_next_ticket++;
-  g_tickets[*ticket] = Ticket{ev, plan->device, plan, snap};
-  return FLLF_OK;
+  // the fault word as it stands after this frame goes to a host-mapped word
+  // that fllf_poll reads, so no device-to-host copy queues behind the frame
+  // copies on the copy engine
+  return enqueue_ticket(plan, plan->io_d2h, ticket);
 }
 
 fllf_status fllf_poll(uint64_t ticket, int timeout_us) {

@@ -82,6 +82,14 @@ def test_timeout_through_submit_and_poll():
         with pytest.raises(pkg.FllfError) as e:
             pkg.fllf_poll(t, 0)
         assert e.value.status == pkg.FLLF_EINVAL
+        # two faulting runs polled newest first: each reports its timeout
+        # (from its fault-word snapshot, though the first report clears the
+        # device word)
+        pkg.fllf_plan_set_wait_test(plan, 100_000, 1)
+        t1 = pkg.fllf_submit(plan, x.data_ptr(), y.data_ptr(), s)
+        t2 = pkg.fllf_submit(plan, x.data_ptr(), y.data_ptr(), s)
+        assert pkg.fllf_poll(t2, 10_000_000) == pkg.FLLF_ETIMEOUT
+        assert pkg.fllf_poll(t1, 10_000_000) == pkg.FLLF_ETIMEOUT
         t = pkg.fllf_submit(plan, x.data_ptr(), y.data_ptr(), s)
         assert pkg.fllf_poll(t, 10_000_000) == pkg.FLLF_OK
         np.testing.assert_array_equal(y.cpu().numpy(), ref)
