@@ -138,6 +138,7 @@ void build_batch_blob(const std::vector<const fllf_plan*>& plans, int prec, Batc
       u.w0 = pl->p.W;
       u.planes = pl->p.C;
       u.dst = pl->lv[1];
+      u.zstmap = pl->maps.z_st1;
       u.K = pl->p.K;
       u.turns = (float)(2.0 / pl->p.T);
       u.use_tma = 0;  // the input and its map are set per run (set_level0_io)

@@ -98,6 +98,7 @@ struct PadRow {
 
 struct Up0Args {
   CUtensorMap imap;     // level-0 input (valid when use_tma)
+  CUtensorMap zstmap;   // Z_1 as a TMA store target: (4 columns, kUpTH rows, kKC orders) boxes
   const float* I;       // level-0 input planes, pitch w0, plane stride h0*w0
   const float* a;       // a_1..a_K (float32): order k is stored as a_k Z_{1,k}
   int h0, w0, planes;
@@ -316,7 +317,10 @@ struct Smem {
   static constexpr size_t up0_it = align128(sizeof(float) * kUpIR * kUpIW);
   static constexpr size_t up0_hz = sizeof(float2) * kKC * kUpTW * kUpCS;
   static constexpr size_t up0_hg = sizeof(float) * kUpTW * kUpCS;
-  static constexpr size_t up0 = 2 * up0_it + align128(up0_hz) + align128(up0_hg) + 64;
+  // the vertical pass's Z_1 outputs of one chunk, per warp a (4, kUpTH,
+  // kKC) box for its TMA store; two chunks in flight
+  static constexpr size_t up0_st = (size_t)ESZ * kUpRun * kUpTH * kKC * (kThreads / 32);
+  static constexpr size_t up0 = 2 * up0_it + align128(up0_hz) + align128(up0_hg) + 2 * align128(up0_st) + 64;
   // up
   static constexpr int up_kc = ESZ == 8 ? 1 : 2;  // orders per chunk
   // ring slot: one chunk of orders, or the guide plane (smaller)
@@ -494,6 +498,23 @@ __device__ __forceinline__ void tma_load4(void* dst, const CUtensorMap* map, int
       "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(v), "r"(saddr(b))
       : "memory");
 }
+
+// TMA store of a 4-D box from shared memory (bulk-group completion), and
+// the bulk-group accounting of the issuing thread: commit the stores issued
+// so far as a group; wait until at most N groups are pending, for their
+// reads of shared memory (.read) or for their completion.
+__device__ __forceinline__ void tma_store4(const CUtensorMap* map, const void* src, int x, int y, int z, int v) {
+  asm volatile("cp.async.bulk.tensor.4d.global.shared::cta.bulk_group [%0, {%2, %3, %4, %5}], [%1];" ::"l"(
+                   reinterpret_cast<uint64_t>(map)),
+               "r"(saddr(src)), "r"(x), "r"(y), "r"(z), "r"(v)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void bulk_wait_read() {
+  asm volatile("cp.async.bulk.wait_group.read %0;" ::"n"(N) : "memory");
+}
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
 
 // Status block of a run (device, zeroed when it is allocated): word 0 holds
 // the fault bits a bounded wait sets when it gives up, words 1..2 a grid

@@ -102,6 +102,7 @@ void build_graph(const std::vector<const fllf_plan*>& plans, int prec, const Gra
       u.planes = C;
       u.dst = pl->lv[1];
       u.dst.M = nullptr;
+      u.zstmap = pl->maps.z_st1;
       u.K = p.K;
       u.turns = turns;
       u.fault = pl->d_fault;

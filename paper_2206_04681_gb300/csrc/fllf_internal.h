@@ -84,6 +84,7 @@ struct PathMaps {
   std::vector<CUtensorMap> e_cs;  // E_l as the coarse level (20 x 10 window)
   std::vector<CUtensorMap> z_fs;  // Z_l as the fine level (36 x 16 box)
   std::vector<CUtensorMap> g_fs;  // G_l as the fine level (36 x 16 box)
+  CUtensorMap z_st1{};            // Z_1 written by the level-0 REDUCE (TMA store boxes)
   // fused level-1/level-0 combine (levels >= 3)
   CUtensorMap g1_d10{};           // G_1 on the level-1 window
   CUtensorMap z2_d10{};           // Z_2 on the level-2 window

@@ -131,7 +131,12 @@ __device__ __forceinline__ bool stage_up0(Res res, int total, unsigned char* sme
   auto itb = [&](int buf) { return reinterpret_cast<float*>(smem + buf * SM::up0_it); };
   float2* hz = reinterpret_cast<float2*>(smem + 2 * SM::up0_it);
   float* hg = reinterpret_cast<float*>(smem + 2 * SM::up0_it + align128(SM::up0_hz));
+  // per warp and chunk the (4 columns, kUpTH rows, kKC orders) box of Z_1 it
+  // writes, stored by TMA; two chunks in flight (buffers by chunk parity)
+  CT* stg = reinterpret_cast<CT*>(smem + 2 * SM::up0_it + align128(SM::up0_hz) + align128(SM::up0_hg));
+  constexpr int kStBox = kUpRun * kUpTH * kKC;
   const int tid = threadIdx.x;
+  int nst = 0;  // chunks stored by this CTA
   auto issue = [&](const Up0Args& a, int t, int buf) {
     const TileXY g = tile_of(t, cdiv(a.dst.w, kUpTW), cdiv(a.dst.h, kUpTH));
     mbar_expect_tx(&bar[buf], sizeof(float) * kUpIR * kUpIW);
@@ -149,7 +154,8 @@ __device__ __forceinline__ bool stage_up0(Res res, int total, unsigned char* sme
   for (int gt = b; gt < total; gt += G, ++n) {
     const int buf = n & 1;
     int t;
-    std::conditional_t<CopiesArgs<Res>::value, const Up0Args, const Up0Args&> a = *res(gt, t);
+    const Up0Args* ap = res(gt, t);  // the tensor maps are read here
+    std::conditional_t<CopiesArgs<Res>::value, const Up0Args, const Up0Args&> a = *ap;
     const TileXY gxy = tile_of(t, cdiv(a.dst.w, kUpTW), cdiv(a.dst.h, kUpTH));
     const int pl = gxy.pl;
     const int X1 = gxy.tx * kUpTW, Y1 = gxy.ty * kUpTH;
@@ -168,6 +174,7 @@ __device__ __forceinline__ bool stage_up0(Res res, int total, unsigned char* sme
     if (a.use_tma) {
       if (!mbar_wait_cta(&bar[buf], pp.use[buf] & 1, a.fault)) {
         if (tid == 0 && gn < total) drain(&bar[buf ^ 1], pp.use[buf ^ 1] & 1);
+        if ((tid & 31) == 0) bulk_wait_all();
         return false;
       }
       ++pp.use[buf];
@@ -232,9 +239,6 @@ __device__ __forceinline__ bool stage_up0(Res res, int total, unsigned char* sme
     // stride of 36 float2 the 8 lanes of a quarter-warp read 8 distinct
     // 16-byte bank groups.
     const int vq = tid & 3, vgrp = (tid >> 2) & 1, vkk = (tid >> 3) & 3;
-    const int xo = X1 + kUpRun * s + vq;
-    // interior tile: every store of the vertical pass is in range (CTA-uniform)
-    const bool full = X1 + kUpTW <= a.dst.w && Y1 + kUpTH <= a.dst.h;
     for (int ch = 0; ch < nch; ++ch) {
       {
 #pragma unroll
@@ -290,12 +294,15 @@ __device__ __forceinline__ bool stage_up0(Res res, int total, unsigned char* sme
       {
         const int k = ch * kKC + vkk;
         // Column q of order k, rows Y1 + 7 vgrp .. + 6: order k is stored
-        // weighted by its coefficient, a_k Z_{1,k}.  A full chunk of orders
-        // on an interior tile (CTA-uniform) takes the unguarded copy.
-        auto vstore = [&](auto guarded) {
-          const float sk = FAST ? (1.f / 256.f) : __ldg(a.a + k) * (1.f / 256.f);
-          CT* Zk = reinterpret_cast<CT*>(a.dst.Z) + (long long)pl * a.dst.zplane +
-                   (long long)k * a.dst.zk + xo + (long long)(Y1 + vgrp * kUpVRows) * a.dst.pitch;
+        // weighted by its coefficient, a_k Z_{1,k}, into the warp's staging
+        // box [order][row][column]; the TMA store leaves out what falls
+        // outside level 1 or beyond order K.
+        CT* sb = stg + ((nst & 1) * (kThreads / 32) + s) * kStBox;
+        // the box written from this buffer two chunks ago has been read
+        if ((tid & 31) == 0) bulk_wait_read<1>();
+        __syncwarp();
+        {
+          const float sk = FAST ? (1.f / 256.f) : (k < a.K ? __ldg(a.a + k) : 0.f) * (1.f / 256.f);
           const float4* p =
               reinterpret_cast<const float4*>(hzw + (vkk * kUpRun + vq) * kUpCS + 2 * kUpVRows * vgrp);
           float2 w[2 * kUpVRows + 4];
@@ -305,19 +312,19 @@ __device__ __forceinline__ bool stage_up0(Res res, int total, unsigned char* sme
             w[2 * u] = make_float2(q4.x, q4.y);
             w[2 * u + 1] = make_float2(q4.z, q4.w);
           }
-          const int rows = decltype(guarded)::value ? min(kUpVRows, a.dst.h - (Y1 + vgrp * kUpVRows)) : kUpVRows;
+          CT* o = sb + (vkk * kUpTH + vgrp * kUpVRows) * kUpRun + vq;
 #pragma unroll
-          for (int j = 0; j < kUpVRows; ++j) {
-            if (!decltype(guarded)::value || j < rows)
-              Cplx<S>::st(Zk, mul2(splat(sk), tap5(w[2 * j], w[2 * j + 1], w[2 * j + 2], w[2 * j + 3], w[2 * j + 4])));
-            Zk += a.dst.pitch;
-          }
-        };
-        if (full && (ch + 1) * kKC <= a.K) {
-          vstore(std::false_type{});
-        } else if (k < a.K && xo < a.dst.w) {
-          vstore(std::true_type{});
+          for (int j = 0; j < kUpVRows; ++j)
+            Cplx<S>::st(o + j * kUpRun,
+                        mul2(splat(sk), tap5(w[2 * j], w[2 * j + 1], w[2 * j + 2], w[2 * j + 3], w[2 * j + 4])));
         }
+        fence_proxy_async();
+        __syncwarp();
+        if ((tid & 31) == 0) {
+          tma_store4(&ap->zstmap, sb, X1 + kUpRun * s, Y1, ch * kKC, pl);
+          bulk_commit();
+        }
+        ++nst;
         if (ch == 0 && tid % 32 < kUpRun * kUpVRows) {
           // guide: lane = (column gq, pair of coarse rows gp)
           const int gq = (tid & 31) % kUpRun, gp = (tid & 31) / kUpRun, xg = X1 + kUpRun * s + gq;
@@ -344,6 +351,8 @@ __device__ __forceinline__ bool stage_up0(Res res, int total, unsigned char* sme
       __syncwarp();
     }
   }
+  // the stores have completed (and read their staging) before the stage ends
+  if ((tid & 31) == 0) bulk_wait_all();
   return true;
 }
 
@@ -1593,6 +1602,7 @@ __global__ void __launch_bounds__(kThreads) k_up0_batch(const BatchTable<Up0Args
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem + SM::up0 - 64);
   fence_maps(tb, [](const Up0Args& a) {
     if (a.use_tma) fence_tensormap(&a.imap);
+    fence_tensormap(&a.zstmap);
   });
   init_bars(bar);
   Pipe pp{};

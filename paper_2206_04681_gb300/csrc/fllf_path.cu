@@ -149,6 +149,11 @@ bool build_maps(const fllf_params& p, const std::vector<Level>& lv, PathMaps* m)
   const size_t zs = f32 ? 8 : 4;
   const CUtensorMapDataType zdt = f32 ? CU_TENSOR_MAP_DATA_TYPE_INT64 : CU_TENSOR_MAP_DATA_TYPE_UINT32;
   const uint32_t up_kc = f32 ? 1 : 2;
+  // Z_1 as the level-0 REDUCE writes it: per warp a box of its 4 level-1
+  // columns, the tile's kUpTH rows and a chunk of kKC orders
+  if (L >= 2 && !encode4(&m->z_st1, zdt, lv[1].Z, lv[1].w, lv[1].h, p.K, p.C, zs * lv[1].pitch,
+                         zs * (uint64_t)lv[1].zk, zs * (uint64_t)lv[1].zplane, kUpRun, kUpTH, kKC))
+    return false;
   for (int l = 1; l < L; ++l) {
     const Level& v = lv[l];
     const uint64_t zrow = zs * v.pitch, zplane = zs * (uint64_t)v.zk;
@@ -255,6 +260,7 @@ cudaError_t enqueue_fast(const fllf_params& p, const std::vector<Level>& lv, con
   u0.w0 = p.W;
   u0.planes = C;
   u0.dst = lv[1];
+  u0.zstmap = maps.z_st1;
   u0.K = p.K;
   u0.fault = fault;
   u0.fast = fa;
@@ -407,6 +413,7 @@ cudaError_t enqueue_path(const fllf_params& p, const std::vector<Level>& lv, con
   u0.w0 = p.W;
   u0.planes = C;
   u0.dst = lv[1];
+  u0.zstmap = maps.z_st1;
   u0.K = p.K;
   u0.turns = turns;
   u0.fault = fault;
