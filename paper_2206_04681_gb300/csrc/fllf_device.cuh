@@ -321,6 +321,8 @@ struct Smem {
   // kKC) box for its TMA store; two chunks in flight
   static constexpr size_t up0_st = (size_t)ESZ * kUpRun * kUpTH * kKC * (kThreads / 32);
   static constexpr size_t up0 = 2 * up0_it + align128(up0_hz) + align128(up0_hg) + 2 * align128(up0_st) + 64;
+  // fast LLF (80 registers): one chunk in flight, which keeps 3 CTAs per SM
+  static constexpr size_t up0_fast = 2 * up0_it + align128(up0_hz) + align128(up0_hg) + align128(up0_st) + 64;
   // up
   static constexpr int up_kc = ESZ == 8 ? 1 : 2;  // orders per chunk
   // ring slot: one chunk of orders, or the guide plane (smaller)

@@ -297,9 +297,11 @@ __device__ __forceinline__ bool stage_up0(Res res, int total, unsigned char* sme
         // weighted by its coefficient, a_k Z_{1,k}, into the warp's staging
         // box [order][row][column]; the TMA store leaves out what falls
         // outside level 1 or beyond order K.
-        CT* sb = stg + ((nst & 1) * (kThreads / 32) + s) * kStBox;
-        // the box written from this buffer two chunks ago has been read
-        if ((tid & 31) == 0) bulk_wait_read<1>();
+        // fast LLF keeps one staging buffer (shared memory for 3 CTAs per SM)
+        constexpr int kStBufs = FAST ? 1 : 2;
+        CT* sb = stg + ((nst % kStBufs) * (kThreads / 32) + s) * kStBox;
+        // the box written from this buffer kStBufs chunks ago has been read
+        if ((tid & 31) == 0) bulk_wait_read<kStBufs - 1>();
         __syncwarp();
         {
           const float sk = FAST ? (1.f / 256.f) : (k < a.K ? __ldg(a.a + k) : 0.f) * (1.f / 256.f);
@@ -1492,7 +1494,7 @@ template <typename S, bool FAST>
 __global__ void __launch_bounds__(kThreads) k_up0(const __grid_constant__ Up0Args a) {
   using SM = Smem<sizeof(typename Cplx<S>::T)>;
   extern __shared__ __align__(128) unsigned char smem[];
-  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + SM::up0 - 64);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + (FAST ? SM::up0_fast : SM::up0) - 64);
   if (threadIdx.x == 0 && a.use_tma) prefetch_map(&a.imap);
   init_bars(bar);
   Pipe pp{};
@@ -2060,8 +2062,8 @@ cudaError_t FLLF_LAUNCH_NAME(up0)(const Up0Args& a, cudaStream_t s, int cps) {
   const int tiles = (a.item1 > 0 ? a.item1 : cdiv(a.dst.w, kUpTW) * cdiv(a.dst.h, kUpTH) * a.planes) - a.item0;
   if (tiles <= 0) return cudaSuccess;
   if (a.fast.S > 0) {
-    const int grid = persistent_grid<k_up0<FLLF_STORAGE, true>>(SMS::up0, tiles, cps);
-    return launch_pdl(k_up0<FLLF_STORAGE, true>, grid, SMS::up0, s, a);
+    const int grid = persistent_grid<k_up0<FLLF_STORAGE, true>>(SMS::up0_fast, tiles, cps);
+    return launch_pdl(k_up0<FLLF_STORAGE, true>, grid, SMS::up0_fast, s, a);
   }
   const int grid = persistent_grid<k_up0<FLLF_STORAGE, false>>(SMS::up0, tiles, cps);
   return launch_pdl(k_up0<FLLF_STORAGE, false>, grid, SMS::up0, s, a);
