@@ -30,8 +30,8 @@ METRIC = "Mpixel/s Fourier LLF K=8 4K RGB at PSNR≥60dB vs FP64; serving p50/p9
 UNIT = "Mpixel/s"
 WORKLOAD = dict(H=2160, W=3840, C=3, polygons=40, seed=2, levels=8, K=8, m=3.0, sigma_r=0.2, T=2.0)
 E2E_DEPTH = 4         # frames in flight in the end-to-end stream (host buffers)
-FRAMES_IN_FLIGHT = 2  # plans and streams filtering successive frames (N_FRAMES is a multiple)
-N_FRAMES = 4          # distinct input/output frames cycled per step (4 x 99.5 MB > 129 MB L2)
+FRAMES_IN_FLIGHT = 3  # plans and streams filtering successive frames (N_FRAMES is a multiple)
+N_FRAMES = 6          # distinct input/output frames cycled per step (6 x 99.5 MB > 129 MB L2)
 STAGES = ("up0", "up", "down", "down0", "chain", "down_s", "graph")
 
 
