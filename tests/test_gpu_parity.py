@@ -173,6 +173,36 @@ def test_submit_host_stream_of_frames(H, W, C, precision):
         pkg.fllf_plan_destroy(plan)
 
 
+def test_frames_in_flight_on_concurrent_plans():
+    """Successive frames on three plans and three streams (each plan its own
+    scratch), as a pipeline over a stream of frames runs them: every output
+    equals the one-stream run of its frame, bit for bit."""
+    H, W, C, L, K = 150, 212, 3, 6, 8
+    imgs = [synth_image(H, W, C, polygons=5, seed=40 + i) for i in range(6)]
+    p = pkg.make_params(H, W, C, L, K, 3.0, 0.2, 2.0)
+    plans = [pkg.fllf_plan_create(p, 0) for _ in range(3)]
+    try:
+        xs = [torch.from_numpy(im).cuda() for im in imgs]
+        refs = []
+        for x in xs:
+            y = torch.empty_like(x)
+            pkg.run_tensor(plans[0], x, y)
+            torch.cuda.synchronize()
+            refs.append(y.cpu().numpy())
+        streams = [torch.cuda.Stream() for _ in plans]
+        outs = [torch.full_like(x, float("nan")) for x in xs]
+        for rep in range(2):
+            for i, (x, y) in enumerate(zip(xs, outs)):
+                j = i % 3
+                pkg.fllf_run(plans[j], x.data_ptr(), y.data_ptr(), streams[j].cuda_stream)
+            torch.cuda.synchronize()
+            for y, r in zip(outs, refs):
+                np.testing.assert_array_equal(y.cpu().numpy(), r)
+    finally:
+        for q in plans:
+            pkg.fllf_plan_destroy(q)
+
+
 @pytest.fixture(scope="module")
 def uhd():
     cfg = UHD_RGB
