@@ -518,6 +518,11 @@ __device__ __forceinline__ void bulk_wait_read() {
 }
 __device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
 
+// the per-warp Z_1 staging boxes of the level-0 REDUCE are TMA store sources,
+// which must start on 128-byte boundaries
+static_assert(Smem<8>::up0_st / (kThreads / 32) % 128 == 0 && Smem<4>::up0_st / (kThreads / 32) % 128 == 0,
+              "TMA store sources start on 128-byte boundaries");
+
 // Status block of a run (device, zeroed when it is allocated): word 0 holds
 // the fault bits a bounded wait sets when it gives up, words 1..2 a grid
 // barrier's arrivals and generation, words 4..5 an optional shorter wait
