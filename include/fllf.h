@@ -133,7 +133,8 @@ size_t fllf_plan_scratch_bytes(const fllf_params *p);
 fllf_status fllf_plan_create(const fllf_params *p, int device, fllf_plan **out);
 
 /* Frees the plan and its scratch; NULL is accepted.  The caller must make
- * sure no work of the plan is still running on any stream. */
+ * sure no work of the plan is still running on any stream, and poll every
+ * ticket of the plan (fllf_submit, fllf_submit_host) to completion first. */
 fllf_status fllf_plan_destroy(fllf_plan *plan);
 
 /* Copies the plan's parameters (a fast LLF plan reports K = ceil(samples/2))
